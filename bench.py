@@ -1,0 +1,427 @@
+"""Benchmark of the fastCAT CBCT hot path on GB300.
+
+One step = the whole path over one synthetic scan: polyenergetic projection
+with the fused energy integral, detector blur + scatter, Poisson noise, FDK
+filter, FDK backprojection and HU (fc_project + fc_reconstruct).  The
+workload is the Catphan-like kV case (256 x 256 x 10 voxels of 0.0625 cm,
+360 projections on a 512 x 384 detector of 0.4 mm, 30 energy bins).
+
+Metric: rays*bins/s = n_angles * n_v * n_u * n_E / step time (whole job,
+summed over ranks); FDK voxel updates/s are reported beside it.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank simulates its own scan (weak scaling, no
+data-path collective); rank 0 prints one JSON line.  ``--impl reference``
+times the FP64 CPU oracle as the reference arm.
+"""
+from __future__ import annotations
+
+import argparse
+import dataclasses
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_2011_04736_gb300 import workloads as W  # noqa: E402
+
+METRIC = "poly-projection rays·bins/s & FDK voxel-upd/s; surrogate vs plain @≤1e-3 err"
+UNIT = "rays*bins/s"
+WORKLOAD = "catphan_kv"
+L2_FLUSH_BYTES = 256 << 20
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def _workload_desc(wl):
+    g = wl.geom
+    return {"workload": "%s: %dx%dx%d voxels of %.4g cm, %d projections, %dx%d detector of %.3g cm, "
+                        "%d energy bins, SAD %g / SDD %g cm, noise seed %d"
+                        % (wl.name, g.nx, g.ny, g.nz, g.dx, g.n_angles, g.n_u, g.n_v, g.du, wl.n_e,
+                           g.sad, g.sdd, wl.seed),
+            "rays_per_step": g.n_rays, "energy_bins": wl.n_e, "voxels": g.n_voxels,
+            "n_angles": g.n_angles}
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons (200 ms period)."""
+
+    FIELDS = ("pci.bus_id,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, bus_id=None):
+        self.bus_id = (bus_id or "").lower()
+        self.samples = []
+        self.proc = None
+        self.marks = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.th = threading.Thread(target=self._read, daemon=True)
+        self.th.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            if self.bus_id and not parts[0].lower().endswith(self.bus_id[-12:]):
+                continue
+            self.samples.append((time.time(), parts))
+
+    def mark(self):
+        self.marks.append(time.time())
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self, t0, t1):
+        sel = [p for (t, p) in self.samples if t0 <= t <= t1] or [p for (_, p) in self.samples]
+        if not sel:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [num(p[1]) for p in sel if num(p[1]) is not None]
+        mx = [num(p[2]) for p in sel if num(p[2]) is not None]
+        reasons = set()
+        for p in sel:
+            for name, v in zip(("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown",
+                                "sw_power_cap"), p[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(sel)}
+
+
+# ------------------------------------------------------------------ roofline
+def _kernel_models(wl):
+    """Algorithmic bytes and FLOPs per launch of each kernel for one step."""
+    g = wl.geom
+    px = g.n_angles * g.n_v * g.n_u
+    rp = int(math.ceil(4 * wl.psf_sigma_px)) if wl.psf_sigma_px > 0 else 0
+    rs = int(math.ceil(4 * wl.scatter_sigma_px)) if wl.scatter_sigma_px > 0 else 0
+    taps = (2 * rp + 1) + (2 * rs + 1)
+    zmax = (g.nz - 1) / 2 * g.dz
+    rmax = math.hypot(g.nx * g.dx / 2, g.ny * g.dy / 2)
+    vmax = zmax * g.sdd / (g.sad - rmax) / g.dv
+    lo = max(0, int(math.floor((g.n_v - 1) / 2 - vmax)) - 2)
+    hi = min(g.n_v - 1, int(math.ceil((g.n_v - 1) / 2 + vmax)) + 2)
+    rows = hi - lo + 1
+    fpx = g.n_angles * rows * g.n_u
+    odd = g.n_u if (g.n_u - 1) % 2 == 1 else g.n_u - 1
+    return {
+        # labels once + T written once
+        "project": {"bytes": g.n_voxels + 4 * px, "flops": None, "bound": "hbm"},
+        # T read, two intermediates written; 2 flops per tap per output
+        "blur_rows": {"bytes": 12 * px, "flops": 2 * taps * px, "bound": "alu"},
+        # two intermediates read, counts written
+        "blur_cols": {"bytes": 12 * px, "flops": 2 * taps * px, "bound": "alu"},
+        # reachable rows: counts read, filtered written; odd taps + centre
+        "fdk_filter": {"bytes": 8 * fpx, "flops": 2 * (odd + 1) * fpx, "bound": "alu"},
+        # filtered reachable rows read once, FP64 volume written once
+        "backproject": {"bytes": 4 * fpx + 8 * g.n_voxels, "flops": None, "bound": "hbm"},
+        "hu": {"bytes": 8 * 2 * g.n_voxels + 4 * g.n_voxels, "flops": None, "bound": "hbm"},
+    }
+
+
+def _traffic(kernel):
+    """ncu DRAM bytes per launch from profiles/ncu_traffic.json, or None when
+    absent or taken from a different source revision of the kernel."""
+    p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p))
+    ent = d.get("kernels", {}).get(kernel)
+    if not ent:
+        return None
+    src = os.path.join(ROOT, "paper_2011_04736_gb300", "csrc", ent.get("source", ""))
+    if not os.path.exists(src):
+        return None
+    if hashlib.sha256(open(src, "rb").read()).hexdigest()[:16] != ent.get("source_sha"):
+        return None
+    return ent.get("dram_bytes_per_launch")
+
+
+# ------------------------------------------------------------------ oracle arm
+def _oracle_sample(wl, n_angles):
+    """Oracle pipeline on the first n_angles projections of the workload:
+    projection + energy sum, blur + scatter, Poisson noise and FDK over those
+    projections.  Returns seconds."""
+    import oracle
+    oracle.build()
+    g = dataclasses.replace(wl.geom, n_angles=n_angles,
+                              arc=wl.geom.arc * n_angles / wl.geom.n_angles)
+    lab = wl.make_phantom()
+    w, d = wl.spectrum()
+    mu = wl.mu()
+    t0 = time.perf_counter()
+    T = oracle.project_T(g, lab, w, d, mu)
+    I = oracle.intensity(T, wl.psf_sigma_px, wl.scatter_sigma_px, wl.spr, wl.n0)
+    K = oracle.poisson(I.astype(np.float32), wl.seed)
+    oracle.fdk(g, K.astype(np.float64), oracle.i_flood(wl.n0, wl.spr))
+    return time.perf_counter() - t0
+
+
+def cpu_baseline(wl, n_angles):
+    import oracle
+    t = _oracle_sample(wl, n_angles)
+    g = wl.geom
+    units = n_angles * g.n_v * g.n_u * wl.n_e
+    return {"value": units / t, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
+            "sample": "%d of %d projections through the FP64 oracle (projection + energy sum, "
+                      "blur + scatter, binary32 Poisson, FDK over those projections), %.2f s"
+                      % (n_angles, g.n_angles, t)}
+
+
+# ------------------------------------------------------------------ distributed
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    if ws <= 1:
+        return 0, 1, None
+    import torch
+    import torch.distributed as dist
+    backend = "nccl" if torch.cuda.is_available() else "gloo"
+    dist.init_process_group(backend=backend)
+    return dist.get_rank(), dist.get_world_size(), dist
+
+
+def aggregate(dist, value, op="max"):
+    """Max (or sum) of a host float over ranks; identity without a group."""
+    if dist is None:
+        return value
+    import torch
+    dev = "cuda" if torch.cuda.is_available() and dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([value], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX if op == "max" else dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def _barrier(dist):
+    if dist is not None:
+        dist.barrier()
+
+
+# ------------------------------------------------------------------ main arms
+def run_reference(args):
+    rank, world, dist = _dist()
+    if rank != 0:
+        return 0
+    wl = W.WORKLOADS[args.workload]
+    g = wl.geom
+    units = args.ref_angles * g.n_v * g.n_u * wl.n_e
+    for _ in range(args.warmup):
+        _oracle_sample(wl, max(1, args.ref_angles // 4))
+    times = [_oracle_sample(wl, args.ref_angles) for _ in range(args.steps)]
+    import oracle
+    t = sum(times) / len(times)
+    val = units / t
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": _workload_desc(wl),
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
+                             "sample": "%d of %d projections per step through the FP64 oracle"
+                                       % (args.ref_angles, g.n_angles)},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def run_ours(args):
+    rank, world, dist = _dist()
+    import torch
+    from paper_2011_04736_gb300 import fastcat as fc
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU")
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    fc.load()
+    wl = W.WORKLOADS[args.workload]
+    g = wl.geom
+    lab = wl.make_phantom()
+    stream = torch.cuda.Stream()
+    sc = fc.Scanner(wl, labels=lab, device=local, noise=True, stream=stream)
+    h = sc.h
+    vol = torch.empty((g.nz, g.ny, g.nx), dtype=torch.float64, device="cuda")
+    hu = torch.empty((g.nz, g.ny, g.nx), dtype=torch.float32, device="cuda")
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+
+    def step():
+        fc.fc_project(h, 0, g.n_angles, fc.FC_OUT_NONE, None, stream)
+        fc.fc_reconstruct(h, None, vol_mu=vol, vol_hu=hu, stream=stream)
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            step()
+    torch.cuda.synchronize()
+
+    bus = None
+    try:
+        bus = torch.cuda.get_device_properties(local).pci_bus_id
+    except Exception:
+        pass
+    clocks = ClockSampler(bus)
+    clocks.start()
+    time.sleep(0.3)
+    fc.fc_profile_enable(h, True)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    _barrier(dist)
+    torch.cuda.synchronize()
+    t_wall0 = time.time()
+    with torch.cuda.stream(stream):
+        for i in range(args.steps):
+            flush.fill_(float(i))           # evict L2 between timed steps (untimed)
+            evs[i][0].record(stream)
+            step()
+            evs[i][1].record(stream)
+    torch.cuda.synchronize()
+    _barrier(dist)
+    t_wall1 = time.time()
+    dev_ms = sum(a.elapsed_time(b) for a, b in evs)
+    kern = fc.fc_profile_read(h)
+    fc.fc_profile_enable(h, False)
+    ms_step = aggregate(dist, dev_ms / args.steps, "max")
+
+    # e2e through the public API with host buffers (pinned)
+    lab_h = torch.from_numpy(lab).pin_memory().numpy()
+    vol_h = torch.empty((g.nz, g.ny, g.nx), dtype=torch.float64).pin_memory().numpy()
+    for _ in range(2):
+        fc.fc_set_phantom(h, lab_h, sc.n_mat, stream)
+        fc.fc_project(h, 0, g.n_angles, fc.FC_OUT_NONE, None, stream)
+        fc.fc_reconstruct(h, None, vol_mu=vol_h, stream=stream)
+    _barrier(dist)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        fc.fc_set_phantom(h, lab_h, sc.n_mat, stream)          # H2D: labels
+        fc.fc_project(h, 0, g.n_angles, fc.FC_OUT_NONE, None, stream)
+        fc.fc_reconstruct(h, None, vol_mu=vol_h, stream=stream)  # D2H: volume (syncs)
+    torch.cuda.synchronize()
+    e2e_s = aggregate(dist, (time.perf_counter() - t0) / args.steps, "max")
+    _barrier(dist)
+    clocks.stop()
+
+    units = g.n_rays * wl.n_e
+    value = units * world / (ms_step / 1e3)
+    vox_rate = g.n_voxels * g.n_angles * world / (ms_step / 1e3)
+    peaks, peak_src = _peaks()
+    models = _kernel_models(wl)
+    kernels = {}
+    for name, (ms, n) in kern.items():
+        if n == 0 or name not in models:
+            continue
+        per = ms / args.steps
+        m = models[name]
+        ent = {"ms_per_step": per, "share": None, "launches_per_step": n / args.steps,
+               "gbs": m["bytes"] / (per / 1e3) / 1e9}
+        if m["flops"]:
+            ent["gflops"] = m["flops"] / (per / 1e3) / 1e9
+        kernels[name] = ent
+    tot = sum(k["ms_per_step"] for k in kernels.values())
+    for k in kernels.values():
+        k["share"] = k["ms_per_step"] / tot if tot else None
+    top = max(kernels, key=lambda k: kernels[k]["ms_per_step"])
+    m = models[top]
+    per_s = kernels[top]["ms_per_step"] / 1e3
+    launches = kernels[top]["launches_per_step"]
+    if m["bound"] == "alu":
+        fmax = float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
+        peak = 152 * 128 * 2 * fmax / 1e12  # FP32 FMA lanes x 2 flops x clock
+        achieved = m["flops"] / per_s / 1e12
+        unit = "TFLOP/s"
+        peak_note = "FP32 FMA peak 152 SM x 128 lanes x 2 x %.0f MHz (derived)" % (fmax / 1e6)
+    else:
+        peak = float(peaks["hbm_gbs"])
+        achieved = m["bytes"] / per_s / 1e9
+        unit = "GB/s"
+        peak_note = "HBM copy bandwidth (%s)" % peak_src
+    traffic = _traffic(top)
+    roof = {"kernel": top, "bound": m["bound"], "achieved": achieved, "peak": peak, "unit": unit,
+            "frac": achieved / peak, "traffic": (traffic / launches if traffic else None),
+            "peak_source": peak_note,
+            "algorithmic": {"bytes_per_launch": m["bytes"] / launches,
+                            "flops_per_launch": (m["flops"] / launches if m["flops"] else None)}}
+    launches_total = int(sum(n for (_, n) in kern.values()))
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": dict(_workload_desc(wl), l2="flushed by a 256 MiB write between timed steps",
+                       parallelism="replicas (one independent scan per GPU)"),
+        "fdk_voxel_updates_per_s": vox_rate,
+        "clocks": clocks.summary(t_wall0, t_wall1),
+        "e2e": {"value": units * world / e2e_s, "unit": UNIT,
+                "h2d_bytes_per_step": int(lab.nbytes), "d2h_bytes_per_step": int(vol_h.nbytes)},
+        "gpu_launches": launches_total,
+        "roofline": roof,
+        "kernels": kernels,
+    }
+    sc.close()
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(wl, args.cpu_angles)
+    if rank == 0:
+        print(json.dumps(line))
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--workload", default=WORKLOAD, choices=sorted(W.WORKLOADS))
+    ap.add_argument("--cpu-angles", type=int, default=96,
+                    help="projections in the oracle CPU-baseline sample")
+    ap.add_argument("--ref-angles", type=int, default=8,
+                    help="projections per reference-arm step")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args(argv)
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,195 @@
+/*
+ * fastcat.h -- C ABI of the GB300 (sm_103a) fastCAT CBCT hot path.
+ *
+ * The operations follow O'Connell & Bazalova-Carter, "FastCAT: Fast Cone
+ * Beam CT (CBCT) Simulation" (arXiv 2011.04736):
+ *   Sec. II.F  Raytracing: line integrals of attenuation along every
+ *              source-to-pixel ray, one projection per energy, combined by
+ *              the energy-weighting equation I_f = sum_E phi(E) eta(E) I(E).
+ *   Sec. II.E/G  detector optical spread and scatter added to the intensity
+ *              profiles; Poisson noise from the particle counts (Sec. II.H,
+ *              fluence equation H = N / (A / A_p)); conversion back to
+ *              projections with the flood field; FDK reconstruction
+ *              [Feldkamp 1984]; HU normalised on the water region.
+ *
+ * Conventions (all lengths in cm, angles in rad):
+ *   angle k:   theta_k = theta0 + arc * k / n_angles
+ *   source:    SAD * (cos theta, sin theta, 0)
+ *   detector:  centre -(SDD - SAD) * (cos, sin, 0), u axis (-sin, cos, 0),
+ *              v axis (0, 0, 1); pixel (iu, iv) centre at
+ *              ((iu - (n_u - 1) / 2) du, (iv - (n_v - 1) / 2) dv)
+ *   volume:    centred at the origin, voxel (ix, iy, iz) centre at
+ *              ((ix - (nx - 1) / 2) dx, ...), voxel intervals half-open
+ *   layouts:   projections float [angle][v][u] (u fastest);
+ *              volumes [z][y][x] (x fastest); labels uint8 [z][y][x]
+ *
+ * Every call returns FC_OK (0) or a negative FC_E* code; fc_last_error()
+ * then returns a message for the calling thread.  Memory passed in is owned
+ * by the caller and only read (inputs) or written (outputs) during the call;
+ * the library copies what it keeps.  A handle must not be used by two
+ * threads at once.  All device work runs on the caller's stream (a
+ * cudaStream_t passed as void*, NULL = the legacy default stream); calls
+ * that write host memory synchronise that stream before returning.
+ */
+#ifndef FASTCAT_H
+#define FASTCAT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define FC_OK        0
+#define FC_EINVAL   -1   /* bad argument, shape or state transition */
+#define FC_ENOMEM   -2   /* device allocation failed */
+#define FC_ECUDA    -3   /* a CUDA runtime call or kernel launch failed */
+#define FC_ESTATE   -4   /* a required set_* call has not been made */
+#define FC_ETIMEOUT -5   /* a bounded device-side wait gave up */
+
+/* where a pointer lives */
+#define FC_HOST   0
+#define FC_DEVICE 1
+
+/* what fc_project returns */
+#define FC_OUT_NONE      0  /* keep results on the device only */
+#define FC_OUT_PRIMARY   1  /* T: flood-normalised primary signal */
+#define FC_OUT_INTENSITY 2  /* I = N0 (G_psf * T + SPR G_sc * T), noise-free */
+#define FC_OUT_COUNTS    3  /* Poisson(I) if noise is on, else I */
+
+/* limits */
+#define FC_MAX_MATERIALS 8
+#define FC_MAX_BINS      256
+#define FC_MAX_SIGMA_PX  64.0
+
+typedef struct fc_handle fc_handle;
+
+typedef struct fc_geometry {
+    double sad_cm;          /* source to rotation axis */
+    double sdd_cm;          /* source to detector, > sad_cm */
+    int32_t n_u, n_v;       /* detector pixels (u across, v along z) */
+    double du_cm, dv_cm;    /* pixel pitch */
+    int32_t n_angles;       /* projections */
+    double theta0_rad;      /* first angle */
+    double arc_rad;         /* angular range covered by n_angles (2 pi for FDK) */
+    int32_t nx, ny, nz;     /* voxel grid */
+    double dx_cm, dy_cm, dz_cm;
+} fc_geometry;
+
+typedef struct fc_spectrum_detector {
+    int32_t n_e;            /* energy bins, 1 .. FC_MAX_BINS */
+    int32_t n_mat;          /* materials (columns of mu), 1 .. FC_MAX_MATERIALS */
+    const double *w;        /* [n_e] fluence weights phi(E) (host) */
+    const double *d;        /* [n_e] detector response eta(E) (host) */
+    const double *mu;       /* [n_e][n_mat] linear attenuation, 1/cm (host) */
+    double psf_sigma_px;    /* detector optical spread, Gaussian sigma in pixels */
+    double scatter_sigma_px;/* scatter kernel, Gaussian sigma in pixels */
+    double spr;             /* scatter-to-primary ratio */
+    double n0;              /* flood photons per pixel (H) */
+    uint64_t seed;          /* Poisson noise seed */
+    int32_t noise;          /* 1: FC_OUT_COUNTS draws Poisson noise */
+} fc_spectrum_detector;
+
+/* Create a handle bound to CUDA device `device`.  *out receives it.
+ * Errors: FC_EINVAL (null out, bad device), FC_ECUDA. */
+int fc_create(fc_handle **out, int device);
+
+/* Release the handle and every device buffer it owns.  NULL is accepted. */
+int fc_destroy(fc_handle *h);
+
+/* Message describing the last failure on this thread ("" if none). */
+const char *fc_last_error(void);
+
+/* Scan geometry (Sec. II.F raytracing set-up; Sec. II.G FDK).  Copies *g.
+ * Reallocates projection and volume buffers when sizes change.
+ * Errors: FC_EINVAL (non-positive sizes or pitches, sdd <= sad, volume not
+ * strictly between source and detector), FC_ENOMEM. */
+int fc_set_geometry(fc_handle *h, const fc_geometry *g);
+
+/* Labelled phantom (Sec. II.D: integer array 0 .. n-1 plus a material map).
+ * labels: uint8 [nz][ny][nx] in host (where = FC_HOST) or device memory;
+ * copied into the handle.  Every label must be < n_mat; violations are
+ * detected on the device and reported as FC_EINVAL.
+ * Errors: FC_ESTATE (no geometry), FC_EINVAL, FC_ECUDA. */
+int fc_set_phantom(fc_handle *h, const uint8_t *labels, int n_mat, int where,
+                   void *stream);
+
+/* Spectrum, attenuation table, detector response, blur, scatter and noise
+ * settings (Sec. II.A-B, II.E, II.F energy weighting, II.H).  Arrays are
+ * read from host memory and copied.  w and d must be >= 0 with
+ * sum_E w d > 0; mu >= 0; sigmas in [0, FC_MAX_SIGMA_PX]; spr >= 0; n0 > 0.
+ * Errors: FC_EINVAL. */
+int fc_set_spectrum_detector(fc_handle *h, const fc_spectrum_detector *s);
+
+/* Simulate projections angle_begin .. angle_begin + angle_count - 1:
+ *   T = sum_E w D exp(-sum_m mu_m(E) L_m) / sum_E w D  (projector with the
+ *       energy integral fused; L_m = path length in material m, Siddon),
+ *   I = N0 (G_psf (x) T + SPR G_scatter (x) T)  (separable, clamp-to-edge),
+ *   K = Poisson(I) (Philox4x32-10 counters (iu, iv, k, j), if noise is on).
+ * Results stay in the handle for fc_reconstruct; `out_kind` selects which
+ * one (if any) is also copied to `out` ([angle_count][n_v][n_u] float, in
+ * host or device memory per `out_where`).
+ * Errors: FC_ESTATE, FC_EINVAL (range, out_kind), FC_ECUDA. */
+int fc_project(fc_handle *h, int angle_begin, int angle_count, int out_kind,
+               float *out, int out_where, void *stream);
+
+/* FDK reconstruction (Sec. II.G): p = ln(I_flood / max(K, 1)),
+ * I_flood = N0 (1 + SPR); cosine weight SAD / sqrt(SAD^2 + u^2 + v^2) at the
+ * isocentre; Ram-Lak row filter; voxel-driven bilinear backprojection with
+ * weight (SAD / U)^2 and factor arc / (2 n_angles), accumulated in FP64.
+ * counts: [n_angles][n_v][n_u] float in host or device memory, or NULL to
+ * use the handle's last FC_OUT_COUNTS result.  vol_mu (double [nz][ny][nx],
+ * 1/cm) and vol_hu (float, HU normalised on the water region) may each be
+ * NULL; `out_where` applies to both.
+ * Errors: FC_ESTATE, FC_EINVAL, FC_ECUDA. */
+int fc_reconstruct(fc_handle *h, const float *counts, int counts_where,
+                   double *vol_mu, float *vol_hu, int out_where, void *stream);
+
+/* Water region used for HU (Sec. II.G): voxels whose centre lies within
+ * radius_cm of the rotation axis, excluding floor(z_margin * nz) slices at
+ * each end.  Default 1.0 cm and 0.1.  Errors: FC_EINVAL. */
+int fc_set_water_roi(fc_handle *h, double radius_cm, double z_margin);
+
+/* Poisson noise alone (Sec. II.H): counts[k][iv][iu] ~ Poisson(lam[..])
+ * with the same counter-based stream as fc_project (projection index
+ * angle0 + k).  lam and counts are device pointers of
+ * n_angles * n_v * n_u floats; they may alias.  Errors: FC_EINVAL, FC_ECUDA. */
+int fc_poisson(const float *lam, float *counts, int n_angles, int n_v, int n_u,
+               int angle0, uint64_t seed, void *stream);
+
+/* Per-material path lengths of the rays of projections angle_begin ..
+ * angle_begin + angle_count - 1 (the traversal of fc_project without the
+ * energy integral), written to the device buffer L
+ * ([angle_count][n_v][n_u][n_mat] float, cm).  Errors: FC_ESTATE, FC_EINVAL,
+ * FC_ECUDA. */
+int fc_project_lengths(fc_handle *h, int angle_begin, int angle_count, float *L,
+                       void *stream);
+
+/* Kernel-time tracing.  While enabled, every kernel the handle launches is
+ * bracketed by CUDA events recorded on the launching stream.  Kernel ids: */
+#define FC_K_PROJECT     0  /* projector + energy integral */
+#define FC_K_BLUR_ROWS   1  /* detector blur, row pass */
+#define FC_K_BLUR_COLS   2  /* detector blur, column pass (+ Poisson) */
+#define FC_K_FDK_FILTER  3  /* log, cosine weight, Ram-Lak filter */
+#define FC_K_BACKPROJECT 4  /* FDK backprojection */
+#define FC_K_HU          5  /* water-region mean and HU (two kernels) */
+#define FC_K_LENGTHS     6  /* path-length emission (fc_project_lengths) */
+#define FC_K_COUNT       7
+
+/* Enable (1) or disable (0) tracing; enabling discards pending records.
+ * Errors: FC_EINVAL. */
+int fc_profile_enable(fc_handle *h, int enable);
+
+/* Wait for every traced launch, then write, per kernel id, the summed device
+ * time in milliseconds to ms[FC_K_COUNT] and the number of kernel launches
+ * to launches[FC_K_COUNT] (either may be NULL), and reset the totals.
+ * Errors: FC_EINVAL, FC_ECUDA. */
+int fc_profile_read(fc_handle *h, double *ms, int64_t *launches);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FASTCAT_H */

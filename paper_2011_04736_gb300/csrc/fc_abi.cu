@@ -1,0 +1,608 @@
+// C ABI of libfastcat (declarations and conventions in include/fastcat.h).
+//
+// The handle owns device copies of the phantom and the per-angle
+// trigonometry, plus the projection-sized and volume-sized buffers of the
+// pipeline (primary signal, the two row-blur intermediates, counts, filtered
+// projections, volume, HU).  Geometry and spectrum are reduced here, once,
+// to the binary32 tables the kernels read; every per-ray, per-pixel and
+// per-voxel step runs in the kernels.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <string>
+#include <vector>
+
+#include "fc_internal.cuh"
+
+namespace fc {
+cudaError_t launch_fdk_filter_rows(const FdkParams &p, const float *counts, float *filt, int v_lo,
+                                   int v_hi, cudaStream_t s);
+void fdk_row_range(const DevGeom &g, int *v_lo, int *v_hi);
+}  // namespace fc
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+
+#define FC_CK(call)                                                                   \
+    do {                                                                              \
+        cudaError_t e_ = (call);                                                      \
+        if (e_ != cudaSuccess)                                                        \
+            return fail(e_ == cudaErrorMemoryAllocation ? FC_ENOMEM : FC_ECUDA,       \
+                        "%s: %s", #call, cudaGetErrorString(e_));                     \
+    } while (0)
+
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = false;
+    explicit DeviceGuard(int dev)
+    {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        ok = cudaSetDevice(dev) == cudaSuccess;
+    }
+    ~DeviceGuard()
+    {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+template <class T>
+void dfree(T *&p)
+{
+    if (p) cudaFree((void *)p);
+    p = nullptr;
+}
+
+}  // namespace
+
+struct fc_handle {
+    int device = 0;
+    bool has_geom = false, has_phantom = false, has_spec = false, has_counts = false;
+    fc_geometry g{};
+    fc::DevGeom dg{};
+    int phantom_mat = 0;
+    // spectrum / detector
+    int n_e = 0, n_mat = 0;
+    std::vector<float> wd;     // [n_e]
+    std::vector<float> mu2;    // [n_e][kMaxMat]
+    double psf = 0.0, sc = 0.0, spr = 0.0, n0 = 1.0;
+    uint64_t seed = 0;
+    int noise = 0;
+    double water_r = 1.0, zmargin = 0.1;
+    // device buffers
+    float2 *d_trig = nullptr;
+    uint8_t *d_labels = nullptr;
+    float *d_T = nullptr, *d_tp = nullptr, *d_ts = nullptr, *d_counts = nullptr, *d_filt = nullptr;
+    double *d_vol = nullptr;
+    float *d_hu = nullptr;
+    double *d_part = nullptr;
+    unsigned int *d_flag = nullptr;
+    size_t proj_elems = 0, vol_elems = 0;
+    // kernel-time tracing
+    struct Rec {
+        int id;
+        int launches;
+        cudaEvent_t a, b;
+    };
+    bool prof = false;
+    std::vector<Rec> pending;
+    std::vector<cudaEvent_t> pool;
+    double prof_ms[FC_K_COUNT] = {0};
+    int64_t prof_n[FC_K_COUNT] = {0};
+
+    void free_all()
+    {
+        dfree(d_trig);
+        dfree(d_labels);
+        dfree(d_T);
+        dfree(d_tp);
+        dfree(d_ts);
+        dfree(d_counts);
+        dfree(d_filt);
+        dfree(d_vol);
+        dfree(d_hu);
+        dfree(d_part);
+        dfree(d_flag);
+        for (auto &r : pending) {
+            cudaEventDestroy(r.a);
+            cudaEventDestroy(r.b);
+        }
+        pending.clear();
+        for (auto e : pool) cudaEventDestroy(e);
+        pool.clear();
+    }
+};
+
+namespace {
+
+int ensure_proj_buffers(fc_handle *h)
+{
+    if (h->d_T) return FC_OK;
+    const size_t b = h->proj_elems * sizeof(float);
+    FC_CK(cudaMalloc((void **)&h->d_T, b));
+    FC_CK(cudaMalloc((void **)&h->d_tp, b));
+    FC_CK(cudaMalloc((void **)&h->d_ts, b));
+    FC_CK(cudaMalloc((void **)&h->d_counts, b));
+    return FC_OK;
+}
+
+int ensure_recon_buffers(fc_handle *h)
+{
+    if (!h->d_filt) FC_CK(cudaMalloc((void **)&h->d_filt, h->proj_elems * sizeof(float)));
+    if (!h->d_counts) FC_CK(cudaMalloc((void **)&h->d_counts, h->proj_elems * sizeof(float)));
+    if (!h->d_vol) FC_CK(cudaMalloc((void **)&h->d_vol, h->vol_elems * sizeof(double)));
+    if (!h->d_hu) FC_CK(cudaMalloc((void **)&h->d_hu, h->vol_elems * sizeof(float)));
+    if (!h->d_part) FC_CK(cudaMalloc((void **)&h->d_part, 2 * 256 * sizeof(double)));
+    return FC_OK;
+}
+
+int copy_out(void *dst, int where, const void *src, size_t bytes, cudaStream_t s)
+{
+    if (where == FC_DEVICE) {
+        FC_CK(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, s));
+    } else {
+        FC_CK(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, s));
+        FC_CK(cudaStreamSynchronize(s));
+    }
+    return FC_OK;
+}
+
+cudaEvent_t take_event(fc_handle *h)
+{
+    if (!h->pool.empty()) {
+        cudaEvent_t e = h->pool.back();
+        h->pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    return e;
+}
+
+// Records the start event of a traced launch; Trace::end records the stop.
+struct Trace {
+    fc_handle *h;
+    int id, launches;
+    cudaStream_t s;
+    cudaEvent_t a = nullptr;
+    Trace(fc_handle *h_, int id_, int n_, cudaStream_t s_) : h(h_), id(id_), launches(n_), s(s_)
+    {
+        if (h->prof && (a = take_event(h))) cudaEventRecord(a, s);
+    }
+    void end()
+    {
+        if (!a) return;
+        cudaEvent_t b = take_event(h);
+        if (!b) {
+            h->pool.push_back(a);
+            a = nullptr;
+            return;
+        }
+        cudaEventRecord(b, s);
+        h->pending.push_back({id, launches, a, b});
+        a = nullptr;
+    }
+    ~Trace()
+    {
+        if (a) h->pool.push_back(a);
+    }
+};
+
+int gauss_taps(double sigma, float *taps, int *radius)
+{
+    if (!(sigma >= 0.0) || sigma > FC_MAX_SIGMA_PX)
+        return fail(FC_EINVAL, "blur sigma %g outside [0, %g]", sigma, (double)FC_MAX_SIGMA_PX);
+    const int R = sigma > 0.0 ? (int)ceil(4.0 * sigma) : 0;
+    double sum = 0.0;
+    std::vector<double> g(2 * R + 1);
+    for (int j = -R; j <= R; ++j) {
+        g[j + R] = R == 0 ? 1.0 : exp(-(double)j * j / (2.0 * sigma * sigma));
+        sum += g[j + R];
+    }
+    for (int j = 0; j < 2 * R + 1; ++j) taps[j] = (float)(g[j] / sum);
+    *radius = R;
+    return FC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *fc_last_error(void) { return g_err.c_str(); }
+
+int fc_create(fc_handle **out, int device)
+{
+    if (!out) return fail(FC_EINVAL, "fc_create: null output pointer");
+    *out = nullptr;
+    int n = 0;
+    FC_CK(cudaGetDeviceCount(&n));
+    if (device < 0 || device >= n) return fail(FC_EINVAL, "fc_create: device %d of %d", device, n);
+    DeviceGuard dgd(device);
+    if (!dgd.ok) return fail(FC_ECUDA, "fc_create: cannot select device %d", device);
+    fc_handle *h = new fc_handle();
+    h->device = device;
+    if (cudaMalloc((void **)&h->d_flag, sizeof(unsigned int)) != cudaSuccess) {
+        delete h;
+        return fail(FC_ENOMEM, "fc_create: allocation failed");
+    }
+    *out = h;
+    g_err.clear();
+    return FC_OK;
+}
+
+int fc_destroy(fc_handle *h)
+{
+    if (!h) return FC_OK;
+    DeviceGuard dgd(h->device);
+    h->free_all();
+    delete h;
+    return FC_OK;
+}
+
+int fc_set_geometry(fc_handle *h, const fc_geometry *g)
+{
+    if (!h || !g) return fail(FC_EINVAL, "fc_set_geometry: null argument");
+    if (g->n_u <= 0 || g->n_v <= 0 || g->n_angles <= 0 || g->nx <= 0 || g->ny <= 0 || g->nz <= 0)
+        return fail(FC_EINVAL, "fc_set_geometry: sizes must be positive");
+    if (!(g->du_cm > 0) || !(g->dv_cm > 0) || !(g->dx_cm > 0) || !(g->dy_cm > 0) || !(g->dz_cm > 0))
+        return fail(FC_EINVAL, "fc_set_geometry: pitches must be positive");
+    if (!(g->sad_cm > 0) || !(g->sdd_cm > g->sad_cm) || !(g->arc_rad > 0))
+        return fail(FC_EINVAL, "fc_set_geometry: need 0 < SAD < SDD and arc > 0");
+    if (g->n_u > 8192) return fail(FC_EINVAL, "fc_set_geometry: n_u %d > 8192", g->n_u);
+    const double hx = 0.5 * g->nx * g->dx_cm, hy = 0.5 * g->ny * g->dy_cm;
+    const double rmax = sqrt(hx * hx + hy * hy);
+    if (rmax >= g->sad_cm || rmax >= g->sdd_cm - g->sad_cm)
+        return fail(FC_EINVAL, "fc_set_geometry: volume (radius %g cm) must lie strictly between "
+                               "source and detector", rmax);
+    const size_t proj = (size_t)g->n_angles * g->n_v * g->n_u;
+    const size_t vox = (size_t)g->nx * g->ny * g->nz;
+    if (vox >= ((size_t)1 << 31))
+        return fail(FC_EINVAL, "fc_set_geometry: %zu voxels exceed the 2^31 index range", vox);
+    DeviceGuard dgd(h->device);
+    const bool same_vol = h->has_geom && h->g.nx == g->nx && h->g.ny == g->ny && h->g.nz == g->nz;
+    if (proj != h->proj_elems || !h->has_geom) {
+        dfree(h->d_T);
+        dfree(h->d_tp);
+        dfree(h->d_ts);
+        dfree(h->d_counts);
+        dfree(h->d_filt);
+        h->has_counts = false;
+    }
+    if (vox != h->vol_elems) {
+        dfree(h->d_vol);
+        dfree(h->d_hu);
+    }
+    if (!same_vol) {
+        dfree(h->d_labels);
+        h->has_phantom = false;
+    }
+    dfree(h->d_trig);
+    h->g = *g;
+    h->proj_elems = proj;
+    h->vol_elems = vox;
+    fc::DevGeom &d = h->dg;
+    d.sad = (float)g->sad_cm;
+    d.sdd = (float)g->sdd_cm;
+    d.du = (float)g->du_cm;
+    d.dv = (float)g->dv_cm;
+    d.cu = (float)(0.5 * (g->n_u - 1));
+    d.cv = (float)(0.5 * (g->n_v - 1));
+    d.n_u = g->n_u;
+    d.n_v = g->n_v;
+    d.n_angles = g->n_angles;
+    d.nx = g->nx;
+    d.ny = g->ny;
+    d.nz = g->nz;
+    d.dx = (float)g->dx_cm;
+    d.dy = (float)g->dy_cm;
+    d.dz = (float)g->dz_cm;
+    d.lox = (float)(-0.5 * g->nx * g->dx_cm);
+    d.loy = (float)(-0.5 * g->ny * g->dy_cm);
+    d.loz = (float)(-0.5 * g->nz * g->dz_cm);
+    std::vector<float2> trig(g->n_angles);
+    for (int k = 0; k < g->n_angles; ++k) {
+        const double th = g->theta0_rad + g->arc_rad * (double)k / (double)g->n_angles;
+        trig[k] = make_float2((float)cos(th), (float)sin(th));
+    }
+    FC_CK(cudaMalloc((void **)&h->d_trig, sizeof(float2) * g->n_angles));
+    FC_CK(cudaMemcpy(h->d_trig, trig.data(), sizeof(float2) * g->n_angles, cudaMemcpyHostToDevice));
+    h->has_geom = true;
+    return FC_OK;
+}
+
+int fc_set_phantom(fc_handle *h, const uint8_t *labels, int n_mat, int where, void *stream)
+{
+    if (!h || !labels) return fail(FC_EINVAL, "fc_set_phantom: null argument");
+    if (!h->has_geom) return fail(FC_ESTATE, "fc_set_phantom: call fc_set_geometry first");
+    if (n_mat < 1 || n_mat > FC_MAX_MATERIALS)
+        return fail(FC_EINVAL, "fc_set_phantom: n_mat %d outside [1, %d]", n_mat, FC_MAX_MATERIALS);
+    if (where != FC_HOST && where != FC_DEVICE) return fail(FC_EINVAL, "fc_set_phantom: bad where");
+    DeviceGuard dgd(h->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (!h->d_labels) FC_CK(cudaMalloc((void **)&h->d_labels, h->vol_elems));
+    FC_CK(cudaMemcpyAsync(h->d_labels, labels, h->vol_elems,
+                          where == FC_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, s));
+    FC_CK(cudaMemsetAsync(h->d_flag, 0, sizeof(unsigned int), s));
+    FC_CK(fc::launch_check_labels(h->d_labels, h->vol_elems, n_mat, h->d_flag, s));
+    unsigned int bad = 0;
+    FC_CK(cudaMemcpyAsync(&bad, h->d_flag, sizeof(bad), cudaMemcpyDeviceToHost, s));
+    FC_CK(cudaStreamSynchronize(s));
+    if (bad) {
+        h->has_phantom = false;
+        return fail(FC_EINVAL, "fc_set_phantom: a label is >= n_mat (%d)", n_mat);
+    }
+    h->phantom_mat = n_mat;
+    h->has_phantom = true;
+    return FC_OK;
+}
+
+int fc_set_spectrum_detector(fc_handle *h, const fc_spectrum_detector *s)
+{
+    if (!h || !s || !s->w || !s->d || !s->mu) return fail(FC_EINVAL, "fc_set_spectrum_detector: null argument");
+    if (s->n_e < 1 || s->n_e > FC_MAX_BINS)
+        return fail(FC_EINVAL, "fc_set_spectrum_detector: n_e %d outside [1, %d]", s->n_e, FC_MAX_BINS);
+    if (s->n_mat < 1 || s->n_mat > FC_MAX_MATERIALS)
+        return fail(FC_EINVAL, "fc_set_spectrum_detector: n_mat %d outside [1, %d]", s->n_mat,
+                    FC_MAX_MATERIALS);
+    double den = 0.0;
+    for (int e = 0; e < s->n_e; ++e) {
+        if (!(s->w[e] >= 0) || !(s->d[e] >= 0))
+            return fail(FC_EINVAL, "fc_set_spectrum_detector: negative or NaN w/D at bin %d", e);
+        for (int m = 0; m < s->n_mat; ++m)
+            if (!(s->mu[(size_t)e * s->n_mat + m] >= 0) || !isfinite(s->mu[(size_t)e * s->n_mat + m]))
+                return fail(FC_EINVAL, "fc_set_spectrum_detector: bad mu at bin %d material %d", e, m);
+        den += s->w[e] * s->d[e];
+    }
+    if (!(den > 0) || !isfinite(den)) return fail(FC_EINVAL, "fc_set_spectrum_detector: sum w D must be > 0");
+    if (!(s->spr >= 0) || !(s->n0 > 0) || !isfinite(s->n0) || !isfinite(s->spr))
+        return fail(FC_EINVAL, "fc_set_spectrum_detector: need spr >= 0 and n0 > 0");
+    float tmp[fc::kMaxTaps];
+    int r;
+    int rc = gauss_taps(s->psf_sigma_px, tmp, &r);
+    if (rc) return rc;
+    rc = gauss_taps(s->scatter_sigma_px, tmp, &r);
+    if (rc) return rc;
+    h->n_e = s->n_e;
+    h->n_mat = s->n_mat;
+    h->wd.assign(s->n_e, 0.0f);
+    h->mu2.assign((size_t)s->n_e * fc::kMaxMat, 0.0f);
+    const double log2e = 1.4426950408889634;
+    for (int e = 0; e < s->n_e; ++e) {
+        h->wd[e] = (float)(s->w[e] * s->d[e] / den);
+        for (int m = 0; m < s->n_mat; ++m)
+            h->mu2[(size_t)e * fc::kMaxMat + m] = (float)(s->mu[(size_t)e * s->n_mat + m] * log2e);
+    }
+    h->psf = s->psf_sigma_px;
+    h->sc = s->scatter_sigma_px;
+    h->spr = s->spr;
+    h->n0 = s->n0;
+    h->seed = s->seed;
+    h->noise = s->noise ? 1 : 0;
+    h->has_spec = true;
+    return FC_OK;
+}
+
+int fc_set_water_roi(fc_handle *h, double radius_cm, double z_margin)
+{
+    if (!h) return fail(FC_EINVAL, "fc_set_water_roi: null handle");
+    if (!(radius_cm > 0) || !(z_margin >= 0) || !(z_margin < 0.5))
+        return fail(FC_EINVAL, "fc_set_water_roi: need radius > 0 and 0 <= margin < 0.5");
+    h->water_r = radius_cm;
+    h->zmargin = z_margin;
+    return FC_OK;
+}
+
+static int fill_proj_params(fc_handle *h, int a0, int na, fc::ProjParams *p)
+{
+    if (!h->has_geom || !h->has_phantom || !h->has_spec)
+        return fail(FC_ESTATE, "fc_project: geometry, phantom and spectrum must be set");
+    if (h->phantom_mat > h->n_mat)
+        return fail(FC_EINVAL, "fc_project: phantom has %d materials, attenuation table %d",
+                    h->phantom_mat, h->n_mat);
+    if (a0 < 0 || na < 0 || a0 + na > h->g.n_angles)
+        return fail(FC_EINVAL, "fc_project: angles [%d, %d) outside [0, %d)", a0, a0 + na, h->g.n_angles);
+    memset(p, 0, sizeof(*p));
+    p->g = h->dg;
+    p->trig = h->d_trig;
+    p->labels = h->d_labels;
+    p->angle0 = a0;
+    p->n_angles_launch = na;
+    p->n_mat = h->n_mat;
+    p->n_e = h->n_e;
+    for (int e = 0; e < h->n_e; ++e) {
+        p->wd[e] = h->wd[e];
+        for (int m = 0; m < fc::kMaxMat; ++m) p->mu2[e][m] = h->mu2[(size_t)e * fc::kMaxMat + m];
+    }
+    return FC_OK;
+}
+
+int fc_project(fc_handle *h, int angle_begin, int angle_count, int out_kind, float *out,
+               int out_where, void *stream)
+{
+    if (!h) return fail(FC_EINVAL, "fc_project: null handle");
+    if (out_kind < FC_OUT_NONE || out_kind > FC_OUT_COUNTS) return fail(FC_EINVAL, "fc_project: bad out_kind");
+    if (out_kind != FC_OUT_NONE && !out) return fail(FC_EINVAL, "fc_project: null output");
+    if (out_kind != FC_OUT_NONE && out_where != FC_HOST && out_where != FC_DEVICE)
+        return fail(FC_EINVAL, "fc_project: bad out_where");
+    fc::ProjParams p;
+    int rc = fill_proj_params(h, angle_begin, angle_count, &p);
+    if (rc) return rc;
+    DeviceGuard dgd(h->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    rc = ensure_proj_buffers(h);
+    if (rc) return rc;
+    const size_t plane = (size_t)h->g.n_v * h->g.n_u;
+    const size_t off = (size_t)angle_begin * plane;
+    const size_t bytes = (size_t)angle_count * plane * sizeof(float);
+    {
+        Trace t(h, FC_K_PROJECT, 1, s);
+        FC_CK(fc::launch_project(p, h->d_T, nullptr, s));
+        t.end();
+    }
+    if (out_kind == FC_OUT_PRIMARY) return angle_count ? copy_out(out, out_where, h->d_T + off, bytes, s) : FC_OK;
+    fc::BlurParams b;
+    memset(&b, 0, sizeof(b));
+    b.n_u = h->g.n_u;
+    b.n_v = h->g.n_v;
+    rc = gauss_taps(h->psf, b.gp, &b.rp);
+    if (rc) return rc;
+    rc = gauss_taps(h->sc, b.gs, &b.rs);
+    if (rc) return rc;
+    b.n0 = (float)h->n0;
+    b.spr = (float)h->spr;
+    b.seed = h->seed;
+    b.noise = (out_kind != FC_OUT_INTENSITY) && h->noise;
+    b.angle0 = angle_begin;
+    {
+        Trace t(h, FC_K_BLUR_ROWS, 1, s);
+        FC_CK(fc::launch_blur_rows(b, h->d_T + off, h->d_tp + off, h->d_ts + off, angle_count, s));
+        t.end();
+    }
+    cudaError_t e;
+    {
+        Trace t(h, FC_K_BLUR_COLS, 1, s);
+        e = fc::launch_blur_cols(b, h->d_tp + off, h->d_ts + off, h->d_counts + off, angle_count, s);
+        if (e == cudaSuccess) t.end();
+    }
+    if (e == cudaErrorInvalidValue)
+        return fail(FC_EINVAL, "fc_project: detector too tall for the column blur (n_v %d)", h->g.n_v);
+    FC_CK(e);
+    h->has_counts = true;
+    if (out_kind == FC_OUT_NONE || angle_count == 0) return FC_OK;
+    return copy_out(out, out_where, h->d_counts + off, bytes, s);
+}
+
+int fc_project_lengths(fc_handle *h, int angle_begin, int angle_count, float *L, void *stream)
+{
+    if (!h || !L) return fail(FC_EINVAL, "fc_project_lengths: null argument");
+    fc::ProjParams p;
+    int rc = fill_proj_params(h, angle_begin, angle_count, &p);
+    if (rc) return rc;
+    DeviceGuard dgd(h->device);
+    Trace t(h, FC_K_LENGTHS, 1, (cudaStream_t)stream);
+    FC_CK(fc::launch_project(p, nullptr, L, (cudaStream_t)stream));
+    t.end();
+    return FC_OK;
+}
+
+int fc_reconstruct(fc_handle *h, const float *counts, int counts_where, double *vol_mu,
+                   float *vol_hu, int out_where, void *stream)
+{
+    if (!h) return fail(FC_EINVAL, "fc_reconstruct: null handle");
+    if (!h->has_geom || !h->has_spec)
+        return fail(FC_ESTATE, "fc_reconstruct: geometry and spectrum/detector must be set");
+    if (!counts && !h->has_counts) return fail(FC_ESTATE, "fc_reconstruct: no counts simulated yet");
+    if (counts && counts_where != FC_HOST && counts_where != FC_DEVICE)
+        return fail(FC_EINVAL, "fc_reconstruct: bad counts_where");
+    if ((vol_mu || vol_hu) && out_where != FC_HOST && out_where != FC_DEVICE)
+        return fail(FC_EINVAL, "fc_reconstruct: bad out_where");
+    DeviceGuard dgd(h->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    int rc = ensure_recon_buffers(h);
+    if (rc) return rc;
+    const size_t pbytes = h->proj_elems * sizeof(float);
+    const float *src = h->d_counts;
+    if (counts && counts_where == FC_DEVICE) {
+        src = counts;
+    } else if (counts) {
+        FC_CK(cudaMemcpyAsync(h->d_counts, counts, pbytes, cudaMemcpyHostToDevice, s));
+        h->has_counts = true;
+    }
+    fc::FdkParams p;
+    p.g = h->dg;
+    p.trig = h->d_trig;
+    p.log_flood = (float)log(h->n0 * (1.0 + h->spr));
+    p.tau = (float)(h->g.du_cm * h->g.sad_cm / h->g.sdd_cm);
+    p.mag = (float)(h->g.sad_cm / h->g.sdd_cm);
+    p.scale = h->g.arc_rad / (2.0 * h->g.n_angles);
+    {
+        Trace t(h, FC_K_FDK_FILTER, 1, s);
+        FC_CK(fc::launch_fdk_filter(p, src, h->d_filt, s));
+        t.end();
+    }
+    {
+        Trace t(h, FC_K_BACKPROJECT, 1, s);
+        FC_CK(fc::launch_backproject(p, h->d_filt, h->d_vol, s));
+        t.end();
+    }
+    if (vol_hu) {
+        const int zcut = (int)floor(h->g.nz * h->zmargin);
+        const int zc = (h->g.nz > 2 * zcut) ? zcut : 0;
+        Trace t(h, FC_K_HU, 2, s);
+        FC_CK(fc::launch_hu(h->dg, h->d_vol, h->d_hu, h->d_part, (float)h->water_r, zc, s));
+        t.end();
+    }
+    if (vol_mu) {
+        rc = copy_out(vol_mu, out_where, h->d_vol, h->vol_elems * sizeof(double), s);
+        if (rc) return rc;
+    }
+    if (vol_hu) {
+        rc = copy_out(vol_hu, out_where, h->d_hu, h->vol_elems * sizeof(float), s);
+        if (rc) return rc;
+    }
+    return FC_OK;
+}
+
+int fc_profile_enable(fc_handle *h, int enable)
+{
+    if (!h) return fail(FC_EINVAL, "fc_profile_enable: null handle");
+    DeviceGuard dgd(h->device);
+    for (auto &r : h->pending) {
+        h->pool.push_back(r.a);
+        h->pool.push_back(r.b);
+    }
+    h->pending.clear();
+    for (int i = 0; i < FC_K_COUNT; ++i) {
+        h->prof_ms[i] = 0.0;
+        h->prof_n[i] = 0;
+    }
+    h->prof = enable != 0;
+    return FC_OK;
+}
+
+int fc_profile_read(fc_handle *h, double *ms, int64_t *launches)
+{
+    if (!h) return fail(FC_EINVAL, "fc_profile_read: null handle");
+    DeviceGuard dgd(h->device);
+    for (auto &r : h->pending) {
+        FC_CK(cudaEventSynchronize(r.b));
+        float t = 0.0f;
+        FC_CK(cudaEventElapsedTime(&t, r.a, r.b));
+        h->prof_ms[r.id] += t;
+        h->prof_n[r.id] += r.launches;
+        h->pool.push_back(r.a);
+        h->pool.push_back(r.b);
+    }
+    h->pending.clear();
+    for (int i = 0; i < FC_K_COUNT; ++i) {
+        if (ms) ms[i] = h->prof_ms[i];
+        if (launches) launches[i] = h->prof_n[i];
+        h->prof_ms[i] = 0.0;
+        h->prof_n[i] = 0;
+    }
+    return FC_OK;
+}
+
+int fc_poisson(const float *lam, float *counts, int n_angles, int n_v, int n_u, int angle0,
+               uint64_t seed, void *stream)
+{
+    if (!lam || !counts) return fail(FC_EINVAL, "fc_poisson: null argument");
+    if (n_angles < 0 || n_v < 0 || n_u < 0 || angle0 < 0) return fail(FC_EINVAL, "fc_poisson: negative size");
+    FC_CK(fc::launch_poisson(lam, counts, n_angles, n_v, n_u, angle0, seed, (cudaStream_t)stream));
+    return FC_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,322 @@
+// FDK reconstruction (paper Sec. II.G: projections recovered with the flood
+// field, reconstructed with FDK [Feldkamp, Davis, Kress 1984], HU
+// normalised on the water region).
+//
+//   q  = ln(I_flood / max(K, 1)) * SAD / sqrt(SAD^2 + u_i^2 + v_i^2)
+//   f  = tau * (h * q),  Ram-Lak h[0] = 1/(4 tau^2), h[odd n] = -1/(pi n tau)^2
+//   mu = arc / (2 N) * sum_k (SAD / U)^2 * bilinear(f_k; u(x), v(x))
+//
+// Filter: one CTA per detector row; the weighted row sits zero-padded in
+// shared memory and each thread produces 16 adjacent outputs from a sliding
+// register window that advances two samples per odd tap (16 FMAs per two
+// shared loads).  Only rows the backprojector can sample are filtered; the
+// backprojector treats every other row as zero, which is what it would read
+// from them after filtering because it never samples them.
+// Backprojection: one thread per (x, y) column and chunk of z; per angle
+// the column's detector abscissa and weight are computed once and the z
+// loop walks the detector column linearly.  Partial sums over 16 angles are
+// kept in binary32 and folded into binary64 accumulators.
+#include <math.h>
+
+#include "fc_internal.cuh"
+
+namespace fc {
+
+namespace {
+constexpr int kFiltOut = 16;
+constexpr int kFiltThreads = 128;
+constexpr int kMaxFiltTaps = 8192;        // odd taps for rows up to 8192 pixels
+__constant__ float c_ramp_odd[kMaxFiltTaps];   // -1 / (pi^2 j^2) for j = 1, 3, 5, ...
+
+__device__ __forceinline__ int skew(int i) { return i + (i >> 5); }
+}  // namespace
+
+// Upload the tau-free odd Ram-Lak taps once per process.
+cudaError_t upload_ramp_taps()
+{
+    static bool done = false;
+    static float h[kMaxFiltTaps];
+    if (done) return cudaSuccess;
+    for (int m = 0; m < kMaxFiltTaps; ++m) {
+        const double j = 2.0 * m + 1.0;
+        h[m] = (float)(-1.0 / (M_PI * M_PI * j * j));
+    }
+    cudaError_t e = cudaMemcpyToSymbol(c_ramp_odd, h, sizeof(h));
+    if (e == cudaSuccess) done = true;
+    return e;
+}
+
+// rows [v_lo, v_hi] of every projection; blockIdx.x = projection * nrows + r
+__global__ void __launch_bounds__(kFiltThreads)
+k_fdk_filter(const __grid_constant__ FdkParams p, const float *__restrict__ counts,
+             float *__restrict__ filt, int v_lo, int nrows)
+{
+    extern __shared__ float sx[];
+    const DevGeom &g = p.g;
+    const int n = g.n_u;
+    const int k = blockIdx.x / nrows;
+    const int iv = v_lo + (int)(blockIdx.x % nrows);
+    const size_t row = ((size_t)k * g.n_v + iv) * n;
+    // padded row: index n + j holds q[j], zeros in [0, n) and [2n, 3n + pad)
+    const float vi = ((float)iv - g.cv) * g.dv * p.mag;
+    const float sad2v = g.sad * g.sad + vi * vi;
+    const int span = 3 * n + kFiltOut + 2;
+    for (int i = threadIdx.x; i < span; i += blockDim.x) {
+        float val = 0.0f;
+        const int j = i - n;
+        if (j >= 0 && j < n) {
+            const float ui = ((float)j - g.cu) * g.du * p.mag;
+            const float K = fmaxf(counts[row + j], 1.0f);
+            val = (p.log_flood - logf(K)) * (g.sad * rsqrtf(sad2v + ui * ui));
+        }
+        sx[skew(i)] = val;
+    }
+    __syncthreads();
+    // odd offsets j in [-jm, jm], jm = largest odd <= n - 1
+    const int jm = ((n - 1) & 1) ? n - 1 : n - 2;
+    const int ntap = jm >= 1 ? (jm + 1) : 0;   // number of odd offsets (both signs)
+    const float inv_tau = 1.0f / p.tau;
+    for (int i0 = threadIdx.x * kFiltOut; i0 < n; i0 += blockDim.x * kFiltOut) {
+        float acc[kFiltOut];
+#pragma unroll
+        for (int o = 0; o < kFiltOut; ++o) acc[o] = 0.25f * sx[skew(n + i0 + o)];
+        if (ntap > 0) {
+            // window holds x[base + t .. base + t + 15] (padded indices) at
+            // slots (t mod 16); t advances by 2 per odd offset j = -jm + t
+            const int base = n + i0 - jm;
+            float win[kFiltOut];
+#pragma unroll
+            for (int o = 0; o < kFiltOut; ++o) win[o] = sx[skew(base + o)];
+            int m = 0;  // offset index: j = -jm + 2 m
+            for (; m + kFiltOut / 2 <= ntap; m += kFiltOut / 2) {
+#pragma unroll
+                for (int q = 0; q < kFiltOut / 2; ++q) {
+                    const int j = -jm + 2 * (m + q);
+                    const int aj = j < 0 ? -j : j;
+                    const float h = c_ramp_odd[aj >> 1];
+#pragma unroll
+                    for (int o = 0; o < kFiltOut; ++o)
+                        acc[o] = fmaf(h, win[(o + 2 * q) % kFiltOut], acc[o]);
+                    win[(2 * q) % kFiltOut] = sx[skew(base + 2 * (m + q) + kFiltOut)];
+                    win[(2 * q + 1) % kFiltOut] = sx[skew(base + 2 * (m + q) + kFiltOut + 1)];
+                }
+            }
+            for (; m < ntap; ++m) {
+                const int j = -jm + 2 * m;
+                const int aj = j < 0 ? -j : j;
+                const float h = c_ramp_odd[aj >> 1];
+#pragma unroll
+                for (int o = 0; o < kFiltOut; ++o)
+                    acc[o] = fmaf(h, sx[skew(base + 2 * m + o)], acc[o]);
+            }
+        }
+#pragma unroll
+        for (int o = 0; o < kFiltOut; ++o)
+            if (i0 + o < n) filt[row + i0 + o] = acc[o] * inv_tau;
+    }
+}
+
+cudaError_t launch_fdk_filter_rows(const FdkParams &p, const float *counts, float *filt, int v_lo,
+                                   int v_hi, cudaStream_t s)
+{
+    const int nrows = v_hi - v_lo + 1;
+    if (nrows <= 0 || p.g.n_angles <= 0) return cudaSuccess;
+    if (p.g.n_u > kMaxFiltTaps) return cudaErrorInvalidValue;
+    cudaError_t e = upload_ramp_taps();
+    if (e != cudaSuccess) return e;
+    const int span = 3 * p.g.n_u + kFiltOut + 2;
+    const size_t smem = (size_t)(span + span / 32 + 2) * sizeof(float);
+    if (smem > 48 * 1024) {
+        e = cudaFuncSetAttribute(k_fdk_filter, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    const size_t blocks = (size_t)p.g.n_angles * nrows;
+    k_fdk_filter<<<(unsigned)blocks, kFiltThreads, smem, s>>>(p, counts, filt, v_lo, nrows);
+    return cudaGetLastError();
+}
+
+// Conservative range of detector rows the backprojector can touch.
+void fdk_row_range(const DevGeom &g, int *v_lo, int *v_hi)
+{
+    const double hx = 0.5 * g.nx * (double)g.dx, hy = 0.5 * g.ny * (double)g.dy;
+    const double rmax = sqrt(hx * hx + hy * hy);
+    const double zmax = 0.5 * (g.nz - 1) * (double)g.dz;
+    const double umin = (double)g.sad - rmax;
+    double vmax;
+    if (umin <= 0.0) {
+        *v_lo = 0;
+        *v_hi = g.n_v - 1;
+        return;
+    }
+    vmax = zmax * (double)g.sdd / umin / (double)g.dv;
+    int lo = (int)floor((double)g.cv - vmax) - 2;
+    int hi = (int)ceil((double)g.cv + vmax) + 2;
+    *v_lo = lo < 0 ? 0 : lo;
+    *v_hi = hi > g.n_v - 1 ? g.n_v - 1 : hi;
+}
+
+cudaError_t launch_fdk_filter(const FdkParams &p, const float *counts, float *filt, cudaStream_t s)
+{
+    int lo, hi;
+    fdk_row_range(p.g, &lo, &hi);
+    return launch_fdk_filter_rows(p, counts, filt, lo, hi, s);
+}
+
+namespace {
+constexpr int kZc = 8;           // z values per thread
+constexpr int kFold = 16;        // angles per binary32 partial sum
+}
+
+__global__ void __launch_bounds__(256)
+k_backproject(const __grid_constant__ FdkParams p, const float *__restrict__ f,
+              double *__restrict__ vol, int v_lo, int v_hi)
+{
+    const DevGeom &g = p.g;
+    const int ix = blockIdx.x * 32 + threadIdx.x;
+    const int iy = blockIdx.y * 8 + threadIdx.y;
+    const int iz0 = blockIdx.z * kZc;
+    if (ix >= g.nx || iy >= g.ny) return;
+    const float x = ((float)ix - 0.5f * (float)(g.nx - 1)) * g.dx;
+    const float y = ((float)iy - 0.5f * (float)(g.ny - 1)) * g.dy;
+    const float z0 = ((float)iz0 - 0.5f * (float)(g.nz - 1)) * g.dz;
+    const int nzc = min(kZc, g.nz - iz0);
+    const size_t plane = (size_t)g.n_v * g.n_u;
+    double accd[kZc];
+    float accf[kZc];
+#pragma unroll
+    for (int z = 0; z < kZc; ++z) { accd[z] = 0.0; accf[z] = 0.0f; }
+    const float sdd_du = g.sdd / g.du, sdd_dv = g.sdd / g.dv;
+    for (int k = 0; k < g.n_angles; ++k) {
+        const float2 cs = p.trig[k];
+        const float U = g.sad - (x * cs.x + y * cs.y);
+        const float ru = y * cs.x - x * cs.y;
+        const float iU = 1.0f / U;
+        const float fu = ru * iU * sdd_du + g.cu;
+        const float w = (g.sad * iU) * (g.sad * iU);
+        const float fv0 = z0 * iU * sdd_dv + g.cv;
+        const float dfv = g.dz * iU * sdd_dv;
+        const float fu0 = floorf(fu);
+        const float au = fu - fu0;
+        const int u0 = (int)fu0;
+        const bool u0ok = u0 >= 0 && u0 < g.n_u;
+        const bool u1ok = u0 + 1 >= 0 && u0 + 1 < g.n_u;
+        const float *fk = f + (size_t)k * plane;
+#pragma unroll
+        for (int z = 0; z < kZc; ++z) {
+            if (z < nzc) {
+                const float fv = fmaf((float)z, dfv, fv0);
+                const float fv0f = floorf(fv);
+                const float av = fv - fv0f;
+                const int v0 = (int)fv0f;
+                float a00 = 0.0f, a01 = 0.0f, a10 = 0.0f, a11 = 0.0f;
+                if (v0 >= v_lo && v0 <= v_hi) {
+                    const float *r = fk + (size_t)v0 * g.n_u;
+                    if (u0ok) a00 = __ldg(r + u0);
+                    if (u1ok) a01 = __ldg(r + u0 + 1);
+                }
+                if (v0 + 1 >= v_lo && v0 + 1 <= v_hi) {
+                    const float *r = fk + (size_t)(v0 + 1) * g.n_u;
+                    if (u0ok) a10 = __ldg(r + u0);
+                    if (u1ok) a11 = __ldg(r + u0 + 1);
+                }
+                const float top = fmaf(au, a01 - a00, a00);
+                const float bot = fmaf(au, a11 - a10, a10);
+                accf[z] = fmaf(w, fmaf(av, bot - top, top), accf[z]);
+            }
+        }
+        if ((k + 1) % kFold == 0) {
+#pragma unroll
+            for (int z = 0; z < kZc; ++z) { accd[z] += (double)accf[z]; accf[z] = 0.0f; }
+        }
+    }
+#pragma unroll
+    for (int z = 0; z < kZc; ++z) {
+        if (z < nzc) {
+            const double a = accd[z] + (double)accf[z];
+            vol[((size_t)(iz0 + z) * g.ny + iy) * g.nx + ix] = a * p.scale;
+        }
+    }
+}
+
+cudaError_t launch_backproject(const FdkParams &p, const float *filt, double *vol, cudaStream_t s)
+{
+    int lo, hi;
+    fdk_row_range(p.g, &lo, &hi);
+    dim3 block(32, 8);
+    dim3 grid((p.g.nx + 31) / 32, (p.g.ny + 7) / 8, (p.g.nz + kZc - 1) / kZc);
+    k_backproject<<<grid, block, 0, s>>>(p, filt, vol, lo, hi);
+    return cudaGetLastError();
+}
+
+// ---- HU: mu_w = mean over the water region; HU = 1000 (mu - mu_w) / mu_w
+namespace {
+constexpr int kRoiBlocks = 256;
+}
+
+__device__ __forceinline__ bool in_roi(const DevGeom &g, int ix, int iy, int iz, float r2, int zcut)
+{
+    if (iz < zcut || iz >= g.nz - zcut) return false;
+    const float x = ((float)ix - 0.5f * (float)(g.nx - 1)) * g.dx;
+    const float y = ((float)iy - 0.5f * (float)(g.ny - 1)) * g.dy;
+    return x * x + y * y <= r2;
+}
+
+__global__ void k_roi_partial(DevGeom g, const double *__restrict__ vol, double *partials,
+                              float r2, int zcut)
+{
+    __shared__ double ssum[256];
+    __shared__ double scnt[256];
+    const size_t n = (size_t)g.nx * g.ny * g.nz;
+    double s = 0.0, c = 0.0;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
+         i += (size_t)gridDim.x * blockDim.x) {
+        const int ix = (int)(i % g.nx);
+        const int iy = (int)((i / g.nx) % g.ny);
+        const int iz = (int)(i / ((size_t)g.nx * g.ny));
+        if (in_roi(g, ix, iy, iz, r2, zcut)) { s += vol[i]; c += 1.0; }
+    }
+    ssum[threadIdx.x] = s;
+    scnt[threadIdx.x] = c;
+    __syncthreads();
+    for (int st = blockDim.x / 2; st > 0; st >>= 1) {
+        if (threadIdx.x < st) {
+            ssum[threadIdx.x] += ssum[threadIdx.x + st];
+            scnt[threadIdx.x] += scnt[threadIdx.x + st];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        partials[2 * blockIdx.x] = ssum[0];
+        partials[2 * blockIdx.x + 1] = scnt[0];
+    }
+}
+
+__global__ void k_hu(DevGeom g, const double *__restrict__ vol, const double *__restrict__ partials,
+                     float *__restrict__ hu)
+{
+    __shared__ double mu_w;
+    if (threadIdx.x == 0) {
+        double s = 0.0, c = 0.0;
+        for (int b = 0; b < kRoiBlocks; ++b) { s += partials[2 * b]; c += partials[2 * b + 1]; }
+        mu_w = c > 0.0 ? s / c : 0.0;
+    }
+    __syncthreads();
+    const double m = mu_w;
+    const size_t n = (size_t)g.nx * g.ny * g.nz;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
+         i += (size_t)gridDim.x * blockDim.x)
+        hu[i] = m != 0.0 ? (float)(1000.0 * (vol[i] - m) / m) : 0.0f;
+}
+
+cudaError_t launch_hu(const DevGeom &g, const double *vol, float *hu, double *partials, float radius,
+                      int zcut, cudaStream_t s)
+{
+    k_roi_partial<<<kRoiBlocks, 256, 0, s>>>(g, vol, partials, radius * radius, zcut);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_hu<<<152 * 4, 256, 0, s>>>(g, vol, partials, hu);
+    return cudaGetLastError();
+}
+
+}  // namespace fc

@@ -1,0 +1,77 @@
+// Internal declarations shared by the CUDA translation units of libfastcat.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "fastcat.h"
+
+namespace fc {
+
+constexpr int kMaxMat = FC_MAX_MATERIALS;
+constexpr int kMaxBins = FC_MAX_BINS;
+constexpr int kMaxTaps = 2 * 256 + 1;  // 2 * ceil(4 * FC_MAX_SIGMA_PX) + 1
+
+// Geometry in the precision the kernels use (binary32), derived on the host
+// from the binary64 fc_geometry.
+struct DevGeom {
+    float sad, sdd;
+    float du, dv;
+    float cu, cv;           // (n_u - 1) / 2, (n_v - 1) / 2
+    int n_u, n_v, n_angles;
+    int nx, ny, nz;
+    float dx, dy, dz;
+    float lox, loy, loz;    // lower box corner = -N d / 2
+};
+
+// Projector launch parameters (passed as a __grid_constant__ kernel argument;
+// the tables are read with warp-uniform indices).
+struct ProjParams {
+    DevGeom g;
+    const float2 *trig;     // [n_angles] (cos, sin) of each angle
+    const uint8_t *labels;  // [nz][ny][nx]
+    int angle0;             // absolute index of the first angle of the launch
+    int n_angles_launch;
+    int n_mat, n_e;
+    float wd[kMaxBins];             // w D / sum(w D)
+    float mu2[kMaxBins][kMaxMat];   // mu * log2(e), zero padded
+};
+
+struct BlurParams {
+    int n_u, n_v;
+    int rp, rs;             // tap radii of the PSF and scatter kernels
+    float n0, spr;
+    uint64_t seed;
+    int noise;
+    int angle0;
+    float gp[kMaxTaps];     // PSF taps, index j + rp
+    float gs[kMaxTaps];     // scatter taps, index j + rs
+};
+
+struct FdkParams {
+    DevGeom g;
+    const float2 *trig;
+    float log_flood;        // ln(I_flood)
+    float tau;              // du * SAD / SDD
+    float mag;              // SAD / SDD
+    double scale;           // arc / (2 n_angles)
+};
+
+// launchers (return cudaError_t of the launch)
+cudaError_t launch_project(const ProjParams &p, float *T, float *L_out, cudaStream_t s);
+cudaError_t launch_blur_rows(const BlurParams &p, const float *T, float *tp, float *ts,
+                             int n_img, cudaStream_t s);
+cudaError_t launch_blur_cols(const BlurParams &p, const float *tp, const float *ts, float *out,
+                             int n_img, cudaStream_t s);
+cudaError_t launch_poisson(const float *lam, float *out, int n_img, int n_v, int n_u,
+                           int angle0, uint64_t seed, cudaStream_t s);
+cudaError_t launch_fdk_filter(const FdkParams &p, const float *counts, float *filt,
+                              cudaStream_t s);
+cudaError_t launch_backproject(const FdkParams &p, const float *filt, double *vol,
+                               cudaStream_t s);
+cudaError_t launch_hu(const DevGeom &g, const double *vol, float *hu, double *partials,
+                      float radius, int zcut, cudaStream_t s);
+cudaError_t launch_check_labels(const uint8_t *labels, size_t n, int n_mat,
+                                unsigned int *bad, cudaStream_t s);
+
+}  // namespace fc

@@ -1,0 +1,233 @@
+"""Thin Python binding of libfastcat (C ABI in include/fastcat.h).
+
+Argument marshalling only: every function forwards to the C entry point of
+the same name; all computation happens in the library's CUDA kernels.  There
+is no fallback -- if ``lib/libfastcat.so`` is missing, loading raises.
+
+Device buffers are passed as torch CUDA tensors (their data pointers), host
+buffers as numpy arrays.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "lib", "libfastcat.so")
+
+FC_OK, FC_EINVAL, FC_ENOMEM, FC_ECUDA, FC_ESTATE, FC_ETIMEOUT = 0, -1, -2, -3, -4, -5
+FC_HOST, FC_DEVICE = 0, 1
+FC_OUT_NONE, FC_OUT_PRIMARY, FC_OUT_INTENSITY, FC_OUT_COUNTS = 0, 1, 2, 3
+FC_MAX_MATERIALS, FC_MAX_BINS = 8, 256
+
+# every entry point declared in include/fastcat.h
+ENTRY_POINTS = ("fc_create", "fc_destroy", "fc_last_error", "fc_set_geometry", "fc_set_phantom",
+                "fc_set_spectrum_detector", "fc_project", "fc_reconstruct", "fc_set_water_roi",
+                "fc_poisson", "fc_project_lengths", "fc_profile_enable", "fc_profile_read")
+FC_K_NAMES = ("project", "blur_rows", "blur_cols", "fdk_filter", "backproject", "hu", "lengths")
+
+
+class FastcatError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("fastcat error %d: %s" % (code, msg))
+        self.code = code
+
+
+class fc_geometry(ctypes.Structure):
+    _fields_ = [("sad_cm", ctypes.c_double), ("sdd_cm", ctypes.c_double),
+                ("n_u", ctypes.c_int32), ("n_v", ctypes.c_int32),
+                ("du_cm", ctypes.c_double), ("dv_cm", ctypes.c_double),
+                ("n_angles", ctypes.c_int32),
+                ("theta0_rad", ctypes.c_double), ("arc_rad", ctypes.c_double),
+                ("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32),
+                ("dx_cm", ctypes.c_double), ("dy_cm", ctypes.c_double), ("dz_cm", ctypes.c_double)]
+
+
+class fc_spectrum_detector(ctypes.Structure):
+    _fields_ = [("n_e", ctypes.c_int32), ("n_mat", ctypes.c_int32),
+                ("w", ctypes.c_void_p), ("d", ctypes.c_void_p), ("mu", ctypes.c_void_p),
+                ("psf_sigma_px", ctypes.c_double), ("scatter_sigma_px", ctypes.c_double),
+                ("spr", ctypes.c_double), ("n0", ctypes.c_double),
+                ("seed", ctypes.c_uint64), ("noise", ctypes.c_int32)]
+
+
+_lib = None
+
+
+def load():
+    """Load libfastcat.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError("libfastcat.so not found at %s; build it with "
+                           "`python -c 'import __graft_entry__ as g; g.build()'`" % LIB_PATH)
+    L = ctypes.CDLL(LIB_PATH)
+    P, I = ctypes.c_void_p, ctypes.c_int
+    sig = {
+        "fc_create": (I, [ctypes.POINTER(P), I]),
+        "fc_destroy": (I, [P]),
+        "fc_last_error": (ctypes.c_char_p, []),
+        "fc_set_geometry": (I, [P, ctypes.POINTER(fc_geometry)]),
+        "fc_set_phantom": (I, [P, P, I, I, P]),
+        "fc_set_spectrum_detector": (I, [P, ctypes.POINTER(fc_spectrum_detector)]),
+        "fc_project": (I, [P, I, I, I, P, I, P]),
+        "fc_reconstruct": (I, [P, P, I, P, P, I, P]),
+        "fc_set_water_roi": (I, [P, ctypes.c_double, ctypes.c_double]),
+        "fc_poisson": (I, [P, P, I, I, I, I, ctypes.c_uint64, P]),
+        "fc_project_lengths": (I, [P, I, I, P, P]),
+        "fc_profile_enable": (I, [P, I]),
+        "fc_profile_read": (I, [P, P, P]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+def _check(rc):
+    if rc != FC_OK:
+        raise FastcatError(rc, load().fc_last_error().decode())
+    return rc
+
+
+def _ptr(x):
+    """(pointer, where) of a torch tensor (device) or numpy array (host)."""
+    if x is None:
+        return None, FC_HOST
+    if isinstance(x, np.ndarray):
+        if not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("host arrays must be C-contiguous")
+        return x.ctypes.data, FC_HOST
+    if hasattr(x, "data_ptr"):
+        if not x.is_contiguous():
+            raise ValueError("tensors must be contiguous")
+        return x.data_ptr(), (FC_DEVICE if x.is_cuda else FC_HOST)
+    raise TypeError("expected a numpy array or torch tensor, got %r" % type(x))
+
+
+def _stream(stream):
+    if stream is None:
+        return None
+    if hasattr(stream, "cuda_stream"):
+        return stream.cuda_stream
+    return int(stream)
+
+
+def make_geometry(g):
+    """fc_geometry from any object with the workloads.Geometry fields."""
+    return fc_geometry(g.sad, g.sdd, g.n_u, g.n_v, g.du, g.dv, g.n_angles, g.theta0, g.arc,
+                       g.nx, g.ny, g.nz, g.dx, g.dy, g.dz)
+
+
+# ---------------------------------------------------------------- C names
+def fc_create(device=0):
+    h = ctypes.c_void_p()
+    _check(load().fc_create(ctypes.byref(h), device))
+    return h
+
+
+def fc_destroy(h):
+    return _check(load().fc_destroy(h))
+
+
+def fc_last_error():
+    return load().fc_last_error().decode()
+
+
+def fc_set_geometry(h, geom):
+    g = geom if isinstance(geom, fc_geometry) else make_geometry(geom)
+    return _check(load().fc_set_geometry(h, ctypes.byref(g)))
+
+
+def fc_set_phantom(h, labels, n_mat, stream=None):
+    p, where = _ptr(labels)
+    return _check(load().fc_set_phantom(h, p, n_mat, where, _stream(stream)))
+
+
+def fc_set_spectrum_detector(h, w, d, mu, psf_sigma_px, scatter_sigma_px, spr, n0, seed, noise):
+    w = np.ascontiguousarray(w, np.float64)
+    d = np.ascontiguousarray(d, np.float64)
+    mu = np.ascontiguousarray(mu, np.float64)
+    s = fc_spectrum_detector(len(w), mu.shape[1], w.ctypes.data, d.ctypes.data, mu.ctypes.data,
+                             psf_sigma_px, scatter_sigma_px, spr, n0, seed, int(bool(noise)))
+    return _check(load().fc_set_spectrum_detector(h, ctypes.byref(s)))
+
+
+def fc_project(h, angle_begin, angle_count, out_kind, out=None, stream=None):
+    p, where = _ptr(out)
+    return _check(load().fc_project(h, angle_begin, angle_count, out_kind, p, where, _stream(stream)))
+
+
+def fc_reconstruct(h, counts=None, vol_mu=None, vol_hu=None, stream=None):
+    cp, cw = _ptr(counts)
+    mp, mw = _ptr(vol_mu)
+    hp, hw = _ptr(vol_hu)
+    if mp is not None and hp is not None and mw != hw:
+        raise ValueError("vol_mu and vol_hu must both be host or both be device buffers")
+    ow = mw if mp is not None else hw
+    return _check(load().fc_reconstruct(h, cp, cw, mp, hp, ow, _stream(stream)))
+
+
+def fc_set_water_roi(h, radius_cm, z_margin):
+    return _check(load().fc_set_water_roi(h, radius_cm, z_margin))
+
+
+def fc_poisson(lam, counts, n_angles, n_v, n_u, angle0, seed, stream=None):
+    lp, lw = _ptr(lam)
+    cp, cw = _ptr(counts)
+    if lw != FC_DEVICE or cw != FC_DEVICE:
+        raise ValueError("fc_poisson takes device tensors")
+    return _check(load().fc_poisson(lp, cp, n_angles, n_v, n_u, angle0, seed, _stream(stream)))
+
+
+def fc_project_lengths(h, angle_begin, angle_count, L, stream=None):
+    p, where = _ptr(L)
+    if where != FC_DEVICE:
+        raise ValueError("fc_project_lengths writes a device tensor")
+    return _check(load().fc_project_lengths(h, angle_begin, angle_count, p, _stream(stream)))
+
+
+def fc_profile_enable(h, enable=True):
+    return _check(load().fc_profile_enable(h, int(bool(enable))))
+
+
+def fc_profile_read(h):
+    """{kernel name: (ms, launches)} since the last read; resets the totals."""
+    ms = np.zeros(len(FC_K_NAMES), np.float64)
+    n = np.zeros(len(FC_K_NAMES), np.int64)
+    _check(load().fc_profile_read(h, ms.ctypes.data, n.ctypes.data))
+    return {k: (float(ms[i]), int(n[i])) for i, k in enumerate(FC_K_NAMES)}
+
+
+# ---------------------------------------------------------------- convenience
+class Scanner:
+    """A handle configured for one workload (geometry + phantom + spectrum)."""
+
+    def __init__(self, workload, labels=None, device=0, noise=None, stream=None):
+        self.w = workload
+        self.g = workload.geom
+        self.h = fc_create(device)
+        fc_set_geometry(self.h, self.g)
+        lab = workload.make_phantom() if labels is None else labels
+        self.n_mat = len(workload.labels)
+        fc_set_phantom(self.h, lab, self.n_mat, stream)
+        w, d = workload.spectrum()
+        fc_set_spectrum_detector(self.h, w, d, workload.mu(), workload.psf_sigma_px,
+                                 workload.scatter_sigma_px, workload.spr, workload.n0,
+                                 workload.seed, workload.noise if noise is None else noise)
+
+    def close(self):
+        if self.h is not None:
+            fc_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

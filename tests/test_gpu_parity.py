@@ -1,0 +1,327 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle on the
+same seeded inputs.  Tolerances: primary signal and intensity relative
+error <= 1e-4 per pixel, reconstruction |d mu| <= 5e-4 mu_water (0.5 HU),
+Poisson counts bit-identical for identical rates."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2011_04736_gb300 import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+REL_T = 1e-4
+HU_TOL = 0.5
+
+
+@pytest.fixture(scope="module")
+def fc():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2011_04736_gb300 import build, fastcat
+    build.build()
+    fastcat.load()
+    return fastcat
+
+
+def _scanner(fc, wl, lab=None, noise=None):
+    return fc.Scanner(wl, labels=wl.make_phantom() if lab is None else lab, noise=noise)
+
+
+def _project(fc, sc, kind, a0=0, na=None):
+    g = sc.g
+    na = g.n_angles - a0 if na is None else na
+    out = torch.empty((na, g.n_v, g.n_u), dtype=torch.float32, device="cuda")
+    fc.fc_project(sc.h, a0, na, kind, out)
+    torch.cuda.synchronize()
+    return out.cpu().numpy()
+
+
+def _ragged_random():
+    wl = W.scaled(W.WORKLOADS["small_kv"], n_u=70, n_v=45, n_angles=7, nx=24, ny=20, nz=16,
+                  dx=0.25, dy=0.25, dz=0.25, du=0.12, dv=0.12)
+    rng = np.random.default_rng(21)
+    g = wl.geom
+    lab = rng.integers(0, 7, size=(g.nz, g.ny, g.nx)).astype(np.uint8)
+    return wl, lab
+
+
+def test_path_lengths_ragged_random_labels(fc, orc):
+    wl, lab = _ragged_random()
+    g = wl.geom
+    sc = _scanner(fc, wl, lab)
+    try:
+        L = torch.empty((g.n_angles, g.n_v, g.n_u, 7), dtype=torch.float32, device="cuda")
+        fc.fc_project_lengths(sc.h, 0, g.n_angles, L)
+        torch.cuda.synchronize()
+        L = L.cpu().numpy().reshape(-1, 7)
+    finally:
+        sc.close()
+    k, v, u = np.meshgrid(np.arange(g.n_angles), np.arange(g.n_v), np.arange(g.n_u), indexing="ij")
+    rays = np.stack([k.ravel(), v.ravel(), u.ravel()], 1)
+    w, d = wl.spectrum()
+    Lr, _ = orc.rays(g, lab, w, d, wl.mu(), rays)
+    err = np.abs(L - Lr)
+    # binary32 traversal: errors per material transition, a few ulp of the
+    # in-volume coordinates (<= ~1e-6 cm) each
+    assert err.max() < 2e-4, err.max()
+    assert np.abs(L.sum(1) - Lr.sum(1)).max() < 2e-5
+
+
+def test_primary_ragged_random_labels(fc, orc):
+    wl, lab = _ragged_random()
+    g = wl.geom
+    sc = _scanner(fc, wl, lab)
+    try:
+        T = _project(fc, sc, fc.FC_OUT_PRIMARY)
+    finally:
+        sc.close()
+    w, d = wl.spectrum()
+    Tr = orc.project_T(g, lab, w, d, wl.mu())
+    rel = np.abs(T - Tr) / Tr
+    assert rel.max() <= REL_T, rel.max()
+
+
+@pytest.fixture(scope="module")
+def small_kv_ref(orc):
+    wl = W.WORKLOADS["small_kv"]
+    g = wl.geom
+    lab = wl.make_phantom()
+    w, d = wl.spectrum()
+    T = orc.project_T(g, lab, w, d, wl.mu())
+    I = orc.intensity(T, wl.psf_sigma_px, wl.scatter_sigma_px, wl.spr, wl.n0)
+    return wl, lab, T, I
+
+
+def test_primary_small_kv(fc, small_kv_ref):
+    wl, lab, Tr, _ = small_kv_ref
+    sc = _scanner(fc, wl, lab)
+    try:
+        T = _project(fc, sc, fc.FC_OUT_PRIMARY)
+    finally:
+        sc.close()
+    rel = np.abs(T - Tr) / Tr
+    assert rel.max() <= REL_T, rel.max()
+
+
+def test_intensity_small_kv(fc, small_kv_ref):
+    wl, lab, _, Ir = small_kv_ref
+    sc = _scanner(fc, wl, lab)
+    try:
+        I = _project(fc, sc, fc.FC_OUT_INTENSITY)
+    finally:
+        sc.close()
+    rel = np.abs(I - Ir) / Ir
+    assert rel.max() <= REL_T, rel.max()
+
+
+def test_poisson_bit_identical(fc, orc, small_kv_ref):
+    wl, _, _, Ir = small_kv_ref
+    rng = np.random.default_rng(5)
+    lam = (Ir[:20] * rng.uniform(0.0, 1.0, Ir[:20].shape) ** 6).astype(np.float32)
+    lam[0, 0, :8] = [0.0, -1.0, 1e-3, 0.5, 9.999, 10.0, 10.001, 2e7]
+    ref = orc.poisson(lam, seed=wl.seed, k0=3)
+    d_lam = torch.from_numpy(lam).cuda()
+    d_out = torch.empty_like(d_lam)
+    n, nv, nu = lam.shape
+    fc.fc_poisson(d_lam, d_out, n, nv, nu, 3, wl.seed)
+    torch.cuda.synchronize()
+    got = d_out.cpu().numpy()
+    assert np.array_equal(got.view(np.uint32), ref.view(np.uint32)), \
+        np.count_nonzero(got != ref)
+    assert (lam < 10).sum() > 100  # both sampler branches exercised
+
+
+def test_counts_fused_equals_standalone_and_repeats(fc, small_kv_ref):
+    wl, lab, _, _ = small_kv_ref
+    sc = _scanner(fc, wl, lab, noise=True)
+    try:
+        I = _project(fc, sc, fc.FC_OUT_INTENSITY)
+        K1 = _project(fc, sc, fc.FC_OUT_COUNTS)
+        K2 = np.concatenate([_project(fc, sc, fc.FC_OUT_COUNTS, 0, 37),
+                             _project(fc, sc, fc.FC_OUT_COUNTS, 37, None)])
+    finally:
+        sc.close()
+    d_I = torch.from_numpy(I).cuda()
+    d_K = torch.empty_like(d_I)
+    fc.fc_poisson(d_I, d_K, *I.shape, 0, wl.seed)
+    torch.cuda.synchronize()
+    assert np.array_equal(K1.view(np.uint32), K2.view(np.uint32))
+    assert np.array_equal(K1.view(np.uint32), d_K.cpu().numpy().view(np.uint32))
+    z = (K1 - I) / np.sqrt(I)
+    assert abs(z.mean()) < 0.01 and abs(z.std() - 1) < 0.01
+
+
+def _recon_gpu(fc, wl, counts, lab=None):
+    g = wl.geom
+    sc = _scanner(fc, wl, lab)
+    try:
+        vol = torch.empty((g.nz, g.ny, g.nx), dtype=torch.float64, device="cuda")
+        hu = torch.empty((g.nz, g.ny, g.nx), dtype=torch.float32, device="cuda")
+        fc.fc_reconstruct(sc.h, np.ascontiguousarray(counts, np.float32), vol_mu=vol, vol_hu=hu)
+        torch.cuda.synchronize()
+        return vol.cpu().numpy(), hu.cpu().numpy()
+    finally:
+        sc.close()
+
+
+def test_reconstruct_small_kv(fc, orc, small_kv_ref):
+    wl, lab, _, Ir = small_kv_ref
+    g = wl.geom
+    counts = Ir.astype(np.float32)
+    vol, hu = _recon_gpu(fc, wl, counts, lab)
+    vref = orc.fdk(g, counts.astype(np.float64), orc.i_flood(wl.n0, wl.spr))
+    mask = W.water_roi_mask(g)
+    huref, mu_w = orc.hu(vref, mask)
+    assert np.max(np.abs(vol - vref)) <= 5e-4 * mu_w, np.max(np.abs(vol - vref)) / mu_w
+    assert np.max(np.abs(hu - huref)) <= HU_TOL, np.max(np.abs(hu - huref))
+
+
+def test_reconstruct_ragged_volume(fc, orc):
+    wl = W.scaled(W.WORKLOADS["small_kv"], n_u=70, n_v=45, n_angles=30, nx=37, ny=29, nz=11,
+                  dx=0.3, dy=0.3, dz=0.3, du=0.2, dv=0.2)
+    g = wl.geom
+    lab = wl.make_phantom()
+    w, d = wl.spectrum()
+    T = orc.project_T(g, lab, w, d, wl.mu())
+    counts = orc.intensity(T, wl.psf_sigma_px, wl.scatter_sigma_px, wl.spr, wl.n0).astype(np.float32)
+    vol, _ = _recon_gpu(fc, wl, counts, lab)
+    vref = orc.fdk(g, counts.astype(np.float64), orc.i_flood(wl.n0, wl.spr))
+    mu_w = float(np.mean(vref[W.water_roi_mask(g)]))
+    assert np.max(np.abs(vol - vref)) <= 5e-4 * mu_w
+
+
+def test_beer_lambert_single_bin_uniform(fc):
+    """One energy bin, D = 1, uniform water box: T = exp(-mu * chord)."""
+    wl = W.scaled(W.WORKLOADS["small_kv"], n_u=33, n_v=9, n_angles=5, nx=16, ny=16, nz=16,
+                  dx=0.5, dy=0.5, dz=0.5, du=0.4, dv=0.4)
+    g = wl.geom
+    h = fc.fc_create(0)
+    try:
+        fc.fc_set_geometry(h, g)
+        fc.fc_set_phantom(h, np.ones((16, 16, 16), np.uint8), 2)
+        fc.fc_set_spectrum_detector(h, [1.0], [1.0], np.array([[0.0, 0.2]]), 0.0, 0.0, 0.0, 1.0, 0, 0)
+        T = torch.empty((g.n_angles, g.n_v, g.n_u), device="cuda")
+        fc.fc_project(h, 0, g.n_angles, fc.FC_OUT_PRIMARY, T)
+        torch.cuda.synchronize()
+        T = T.cpu().numpy()
+        # blur with sigma 0 and SPR 0 is the identity times N0 = 1
+        I = torch.empty_like(torch.from_numpy(T)).cuda()
+        fc.fc_project(h, 0, g.n_angles, fc.FC_OUT_INTENSITY, I)
+        torch.cuda.synchronize()
+        assert np.array_equal(I.cpu().numpy(), T)
+    finally:
+        fc.fc_destroy(h)
+    for k in range(g.n_angles):
+        th = 2 * math.pi * k / g.n_angles
+        for iv in range(g.n_v):
+            for iu in range(g.n_u):
+                u = (iu - (g.n_u - 1) / 2) * g.du
+                v = (iv - (g.n_v - 1) / 2) * g.dv
+                S = np.array([g.sad * math.cos(th), g.sad * math.sin(th), 0.0])
+                P = np.array([-(g.sdd - g.sad) * math.cos(th) - u * math.sin(th),
+                              -(g.sdd - g.sad) * math.sin(th) + u * math.cos(th), v])
+                D = P - S
+                t0, t1 = 0.0, 1.0
+                for a in range(3):
+                    lo, hi = sorted(((-4.0 - S[a]) / D[a], (4.0 - S[a]) / D[a])) if D[a] else (-1e9, 1e9)
+                    t0, t1 = max(t0, lo), min(t1, hi)
+                chord = max(0.0, t1 - t0) * np.linalg.norm(D)
+                assert T[k, iv, iu] == pytest.approx(math.exp(-0.2 * chord), rel=1e-5)
+
+
+def test_errors_are_reported(fc):
+    wl = W.WORKLOADS["small_kv"]
+    g = wl.geom
+    h = fc.fc_create(0)
+    try:
+        with pytest.raises(fc.FastcatError) as ei:
+            fc.fc_project(h, 0, 1, fc.FC_OUT_NONE)
+        assert ei.value.code == fc.FC_ESTATE
+        fc.fc_set_geometry(h, g)
+        bad = np.zeros((g.nz, g.ny, g.nx), np.uint8)
+        bad[3, 4, 5] = 9
+        with pytest.raises(fc.FastcatError) as ei:
+            fc.fc_set_phantom(h, bad, 7)
+        assert ei.value.code == fc.FC_EINVAL and "n_mat" in fc.fc_last_error()
+        fc.fc_set_phantom(h, np.ones((g.nz, g.ny, g.nx), np.uint8), 7)
+        w, d = wl.spectrum()
+        fc.fc_set_spectrum_detector(h, w, d, wl.mu(), 0.6, 20.0, 0.2, 1e5, 0, 0)
+        with pytest.raises(fc.FastcatError):
+            fc.fc_project(h, 80, 20, fc.FC_OUT_NONE)
+        with pytest.raises(fc.FastcatError):
+            fc.fc_set_spectrum_detector(h, w, d, wl.mu(), 70.0, 20.0, 0.2, 1e5, 0, 0)
+        fc.fc_project(h, 5, 0, fc.FC_OUT_NONE)  # empty range is a no-op
+    finally:
+        fc.fc_destroy(h)
+
+
+# ------------------------------------------------------------------ full size
+@pytest.fixture(scope="module")
+def catphan_full(fc):
+    wl = W.WORKLOADS["catphan_kv"]
+    lab = wl.make_phantom()
+    sc = _scanner(fc, wl, lab, noise=False)
+    try:
+        T = _project(fc, sc, fc.FC_OUT_PRIMARY)
+        I = _project(fc, sc, fc.FC_OUT_INTENSITY)
+    finally:
+        sc.close()
+    return wl, lab, T, I
+
+
+def test_full_catphan_primary_sampled(orc, catphan_full):
+    wl, lab, T, _ = catphan_full
+    g = wl.geom
+    rng = np.random.default_rng(1)
+    n = 4000
+    rays = np.stack([rng.integers(0, g.n_angles, n), rng.integers(170, 214, n),
+                     rng.integers(0, g.n_u, n)], 1)
+    # plus one full row through the insert ring at a few angles
+    extra = [(k, 192, u) for k in (0, 45, 91, 180, 359) for u in range(g.n_u)]
+    rays = np.concatenate([rays, np.array(extra)])
+    w, d = wl.spectrum()
+    _, Tr = orc.rays(g, lab, w, d, wl.mu(), rays)
+    got = T[rays[:, 0], rays[:, 1], rays[:, 2]]
+    assert np.max(np.abs(got - Tr) / Tr) <= REL_T
+
+
+def test_full_catphan_intensity_sampled(orc, catphan_full):
+    """I at sampled pixels: the oracle blurs its own T over the projections
+    that contain the samples."""
+    wl, lab, _, I = catphan_full
+    g = wl.geom
+    w, d = wl.spectrum()
+    ks = [0, 123, 301]
+    Tr = np.concatenate([orc.project_T(g, lab, w, d, wl.mu(), a0=k, na=1) for k in ks])
+    Ir = orc.intensity(Tr, wl.psf_sigma_px, wl.scatter_sigma_px, wl.spr, wl.n0)
+    got = I[ks]
+    assert np.max(np.abs(got - Ir) / Ir) <= REL_T
+
+
+def test_full_catphan_reconstruct(fc, orc, catphan_full):
+    """Full-size FDK of oracle-made noise-free counts, every voxel."""
+    wl, lab, _, _ = catphan_full
+    g = wl.geom
+    w, d = wl.spectrum()
+    Tr = orc.project_T(g, lab, w, d, wl.mu())
+    Ir = orc.intensity(Tr, wl.psf_sigma_px, wl.scatter_sigma_px, wl.spr, wl.n0)
+    counts = Ir.astype(np.float32)
+    vol, hu = _recon_gpu(fc, wl, counts, lab)
+    # oracle FDK on the detector rows the volume projects onto (others are
+    # never sampled); generous margin
+    zmax = (g.nz - 1) / 2 * g.dz
+    rmax = math.hypot(g.nx * g.dx / 2, g.ny * g.dy / 2)
+    vmax = zmax * g.sdd / (g.sad - rmax) / g.dv
+    lo = max(0, int(math.floor((g.n_v - 1) / 2 - vmax)) - 4)
+    hi = min(g.n_v - 1, int(math.ceil((g.n_v - 1) / 2 + vmax)) + 4)
+    q = orc.fdk_weight(g, counts.astype(np.float64), orc.i_flood(wl.n0, wl.spr))
+    f = np.zeros_like(q)
+    f[:, lo:hi + 1] = orc.ramp_filter(np.ascontiguousarray(q[:, lo:hi + 1]), g.du * g.sad / g.sdd)
+    vref = orc.backproject(g, f)
+    mask = W.water_roi_mask(g)
+    huref, mu_w = orc.hu(vref, mask)
+    assert np.max(np.abs(vol - vref)) <= 5e-4 * mu_w
+    assert np.max(np.abs(hu - huref)) <= HU_TOL
