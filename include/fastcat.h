@@ -171,12 +171,13 @@ int fc_project_lengths(fc_handle *h, int angle_begin, int angle_count, float *L,
  * bracketed by CUDA events recorded on the launching stream.  Kernel ids: */
 #define FC_K_PROJECT     0  /* projector + energy integral */
 #define FC_K_BLUR_ROWS   1  /* detector blur, row pass */
-#define FC_K_BLUR_COLS   2  /* detector blur, column pass (+ Poisson) */
+#define FC_K_BLUR_COLS   2  /* detector blur, column pass */
 #define FC_K_FDK_FILTER  3  /* log, cosine weight, Ram-Lak filter */
 #define FC_K_BACKPROJECT 4  /* FDK backprojection */
 #define FC_K_HU          5  /* water-region mean and HU (two kernels) */
 #define FC_K_LENGTHS     6  /* path-length emission (fc_project_lengths) */
-#define FC_K_COUNT       7
+#define FC_K_NOISE       7  /* Poisson noise */
+#define FC_K_COUNT       8
 
 /* Enable (1) or disable (0) tracing; enabling discards pending records.
  * Errors: FC_EINVAL. */

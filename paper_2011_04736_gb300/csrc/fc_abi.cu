@@ -262,6 +262,8 @@ int fc_set_geometry(fc_handle *h, const fc_geometry *g)
     if (!(g->sad_cm > 0) || !(g->sdd_cm > g->sad_cm) || !(g->arc_rad > 0))
         return fail(FC_EINVAL, "fc_set_geometry: need 0 < SAD < SDD and arc > 0");
     if (g->n_u > 8192) return fail(FC_EINVAL, "fc_set_geometry: n_u %d > 8192", g->n_u);
+    if (g->n_v > 65535 || g->n_angles > 65535)
+        return fail(FC_EINVAL, "fc_set_geometry: n_v and n_angles must be <= 65535");
     const double hx = 0.5 * g->nx * g->dx_cm, hy = 0.5 * g->ny * g->dy_cm;
     const double rmax = sqrt(hx * hx + hy * hy);
     if (rmax >= g->sad_cm || rmax >= g->sdd_cm - g->sad_cm)
@@ -312,6 +314,9 @@ int fc_set_geometry(fc_handle *h, const fc_geometry *g)
     d.lox = (float)(-0.5 * g->nx * g->dx_cm);
     d.loy = (float)(-0.5 * g->ny * g->dy_cm);
     d.loz = (float)(-0.5 * g->nz * g->dz_cm);
+    d.idx = (float)(1.0 / g->dx_cm);
+    d.idy = (float)(1.0 / g->dy_cm);
+    d.idz = (float)(1.0 / g->dz_cm);
     std::vector<float2> trig(g->n_angles);
     for (int k = 0; k < g->n_angles; ++k) {
         const double th = g->theta0_rad + g->arc_rad * (double)k / (double)g->n_angles;
@@ -420,6 +425,19 @@ static int fill_proj_params(fc_handle *h, int a0, int na, fc::ProjParams *p)
     p->labels = h->d_labels;
     p->angle0 = a0;
     p->n_angles_launch = na;
+    {
+        // A ray through row v lies at height z = v * s along the central
+        // direction, s = distance from the source / SDD; inside the voxel box
+        // s >= (SAD - r_max) / SDD.  It can meet the slab |z| <= nz dz / 2 only
+        // if |v| (SAD - r_max) / SDD <= nz dz / 2.  Two rows of margin.
+        const fc_geometry &G = h->g;
+        const double rmax = sqrt(0.25 * G.nx * G.dx_cm * G.nx * G.dx_cm +
+                                 0.25 * G.ny * G.dy_cm * G.ny * G.dy_cm);
+        const double vmax = 0.5 * G.nz * G.dz_cm * G.sdd_cm / (G.sad_cm - rmax) / G.dv_cm;
+        const double cv = 0.5 * (G.n_v - 1);
+        p->v_hit_lo = (int)floor(cv - vmax) - 2;
+        p->v_hit_hi = (int)ceil(cv + vmax) + 2;
+    }
     p->n_mat = h->n_mat;
     p->n_e = h->n_e;
     for (int e = 0; e < h->n_e; ++e) {
@@ -463,9 +481,7 @@ int fc_project(fc_handle *h, int angle_begin, int angle_count, int out_kind, flo
     if (rc) return rc;
     b.n0 = (float)h->n0;
     b.spr = (float)h->spr;
-    b.seed = h->seed;
-    b.noise = (out_kind != FC_OUT_INTENSITY) && h->noise;
-    b.angle0 = angle_begin;
+    const bool noise = (out_kind != FC_OUT_INTENSITY) && h->noise;
     {
         Trace t(h, FC_K_BLUR_ROWS, 1, s);
         FC_CK(fc::launch_blur_rows(b, h->d_T + off, h->d_tp + off, h->d_ts + off, angle_count, s));
@@ -480,6 +496,12 @@ int fc_project(fc_handle *h, int angle_begin, int angle_count, int out_kind, flo
     if (e == cudaErrorInvalidValue)
         return fail(FC_EINVAL, "fc_project: detector too tall for the column blur (n_v %d)", h->g.n_v);
     FC_CK(e);
+    if (noise) {
+        Trace t(h, FC_K_NOISE, 1, s);
+        FC_CK(fc::launch_poisson(h->d_counts + off, h->d_counts + off, angle_count, h->g.n_v,
+                                 h->g.n_u, angle_begin, h->seed, s));
+        t.end();
+    }
     h->has_counts = true;
     if (out_kind == FC_OUT_NONE || angle_count == 0) return FC_OK;
     return copy_out(out, out_where, h->d_counts + off, bytes, s);
@@ -601,6 +623,7 @@ int fc_poisson(const float *lam, float *counts, int n_angles, int n_v, int n_u, 
 {
     if (!lam || !counts) return fail(FC_EINVAL, "fc_poisson: null argument");
     if (n_angles < 0 || n_v < 0 || n_u < 0 || angle0 < 0) return fail(FC_EINVAL, "fc_poisson: negative size");
+    if (n_angles > 65535 || n_v > 65535) return fail(FC_EINVAL, "fc_poisson: n_angles and n_v must be <= 65535");
     FC_CK(fc::launch_poisson(lam, counts, n_angles, n_v, n_u, angle0, seed, (cudaStream_t)stream));
     return FC_OK;
 }

@@ -14,8 +14,8 @@
 //            stride-8 lane pattern is free of bank conflicts);
 //   columns: one CTA per (projection, tile of TW columns); both row-pass
 //            results are staged with replicated halos, each thread produces
-//            8 adjacent outputs of one column, and the epilogue forms I and
-//            optionally draws the Poisson count in the same pass.
+//            8 adjacent outputs of one column, and the epilogue forms I.
+// Poisson counts are drawn by k_poisson, one thread per pixel.
 #include <math.h>
 
 #include "fc_internal.cuh"
@@ -92,8 +92,11 @@ k_blur_rows(const __grid_constant__ BlurParams p, const float *__restrict__ T,
     }
 }
 
-// Column pass.  Tile: TW columns x (n_v + 2 R) rows of each row-pass result.
-template <int TW>
+// Column pass.  Tile: TW columns x (n_v + 2 R) rows of each row-pass result,
+// row stride ST floats.  The 32 / TW column groups of a warp work on rows
+// 8 apart; ST is chosen so those rows start 32 / (32 / TW) banks apart
+// (ST = 32, 18, 9 for TW = 32, 16, 8), which keeps shared reads conflict-free.
+template <int TW, int ST>
 __global__ void __launch_bounds__(kColThreads)
 k_blur_cols(const __grid_constant__ BlurParams p, const float *__restrict__ tp,
             const float *__restrict__ ts, float *__restrict__ out)
@@ -101,8 +104,8 @@ k_blur_cols(const __grid_constant__ BlurParams p, const float *__restrict__ tp,
     extern __shared__ float smem[];
     const int nv = p.n_v, nu = p.n_u;
     const int hp = nv + 2 * p.rp + kOut, hs = nv + 2 * p.rs + kOut;
-    float *sp = smem;              // [hp][TW]
-    float *ss = smem + hp * TW;    // [hs][TW]
+    float *sp = smem;              // [hp][ST]
+    float *ss = smem + hp * ST;    // [hs][ST]
     const int img = blockIdx.y;
     const int u_base = blockIdx.x * TW;
     const size_t plane = (size_t)nv * nu;
@@ -116,15 +119,14 @@ k_blur_cols(const __grid_constant__ BlurParams p, const float *__restrict__ tp,
     for (int r = grp; r < hp; r += ngrp) {
         int vv = r - p.rp;
         vv = vv < 0 ? 0 : (vv > nv - 1 ? nv - 1 : vv);
-        sp[r * TW + col] = gp_src[(size_t)vv * nu + uc];
+        sp[r * ST + col] = gp_src[(size_t)vv * nu + uc];
     }
     for (int r = grp; r < hs; r += ngrp) {
         int vv = r - p.rs;
         vv = vv < 0 ? 0 : (vv > nv - 1 ? nv - 1 : vv);
-        ss[r * TW + col] = gs_src[(size_t)vv * nu + uc];
+        ss[r * ST + col] = gs_src[(size_t)vv * nu + uc];
     }
     __syncthreads();
-    const int k_abs = p.angle0 + img;
     for (int v0 = grp * kOut; v0 < nv; v0 += ngrp * kOut) {
         float ap[kOut], as[kOut];
 #pragma unroll
@@ -133,7 +135,7 @@ k_blur_cols(const __grid_constant__ BlurParams p, const float *__restrict__ tp,
         {
             float win[kOut];
 #pragma unroll
-            for (int o = 0; o < kOut; ++o) win[o] = sp[(v0 + o) * TW + col];
+            for (int o = 0; o < kOut; ++o) win[o] = sp[(v0 + o) * ST + col];
             const int nt = 2 * p.rp + 1;
             int j = 0;
             for (; j + kOut <= nt; j += kOut) {
@@ -142,19 +144,19 @@ k_blur_cols(const __grid_constant__ BlurParams p, const float *__restrict__ tp,
                     const float gj = p.gp[j + q];
 #pragma unroll
                     for (int o = 0; o < kOut; ++o) ap[o] = fmaf(gj, win[(o + q) % kOut], ap[o]);
-                    win[q] = sp[(v0 + j + q + kOut) * TW + col];
+                    win[q] = sp[(v0 + j + q + kOut) * ST + col];
                 }
             }
             for (int q = 0; j + q < nt; ++q) {
                 const float gj = p.gp[j + q];
 #pragma unroll
-                for (int o = 0; o < kOut; ++o) ap[o] = fmaf(gj, sp[(v0 + j + q + o) * TW + col], ap[o]);
+                for (int o = 0; o < kOut; ++o) ap[o] = fmaf(gj, sp[(v0 + j + q + o) * ST + col], ap[o]);
             }
         }
         {
             float win[kOut];
 #pragma unroll
-            for (int o = 0; o < kOut; ++o) win[o] = ss[(v0 + o) * TW + col];
+            for (int o = 0; o < kOut; ++o) win[o] = ss[(v0 + o) * ST + col];
             const int nt = 2 * p.rs + 1;
             int j = 0;
             for (; j + kOut <= nt; j += kOut) {
@@ -163,13 +165,13 @@ k_blur_cols(const __grid_constant__ BlurParams p, const float *__restrict__ tp,
                     const float gj = p.gs[j + q];
 #pragma unroll
                     for (int o = 0; o < kOut; ++o) as[o] = fmaf(gj, win[(o + q) % kOut], as[o]);
-                    win[q] = ss[(v0 + j + q + kOut) * TW + col];
+                    win[q] = ss[(v0 + j + q + kOut) * ST + col];
                 }
             }
             for (int q = 0; j + q < nt; ++q) {
                 const float gj = p.gs[j + q];
 #pragma unroll
-                for (int o = 0; o < kOut; ++o) as[o] = fmaf(gj, ss[(v0 + j + q + o) * TW + col], as[o]);
+                for (int o = 0; o < kOut; ++o) as[o] = fmaf(gj, ss[(v0 + j + q + o) * ST + col], as[o]);
             }
         }
         if (u < nu) {
@@ -177,19 +179,29 @@ k_blur_cols(const __grid_constant__ BlurParams p, const float *__restrict__ tp,
             for (int o = 0; o < kOut; ++o) {
                 const int v = v0 + o;
                 if (v < nv) {
-                    float I = p.n0 * (ap[o] + p.spr * as[o]);
-                    if (p.noise)
-                        I = noise::poisson(I, (uint32_t)u, (uint32_t)v, (uint32_t)k_abs, p.seed);
-                    out[img * plane + (size_t)v * nu + u] = I;
+                    out[img * plane + (size_t)v * nu + u] = p.n0 * (ap[o] + p.spr * as[o]);
                 }
             }
         }
     }
 }
 
-static size_t col_smem_bytes(const BlurParams &p, int tw)
+static size_t col_smem_bytes(const BlurParams &p, int st)
 {
-    return (size_t)(2 * p.n_v + 2 * p.rp + 2 * p.rs + 2 * kOut) * tw * sizeof(float);
+    return (size_t)(2 * p.n_v + 2 * p.rp + 2 * p.rs + 2 * kOut) * st * sizeof(float);
+}
+
+template <int TW, int ST>
+static cudaError_t launch_cols_tw(const BlurParams &p, const float *tp, const float *ts, float *out,
+                                  int n_img, cudaStream_t s)
+{
+    const size_t b = col_smem_bytes(p, ST);
+    cudaError_t e = cudaFuncSetAttribute(k_blur_cols<TW, ST>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b);
+    if (e != cudaSuccess) return e;
+    dim3 grid((p.n_u + TW - 1) / TW, n_img);
+    k_blur_cols<TW, ST><<<grid, kColThreads, b, s>>>(p, tp, ts, out);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_blur_rows(const BlurParams &p, const float *T, float *tp, float *ts, int n_img,
@@ -215,54 +227,34 @@ cudaError_t launch_blur_cols(const BlurParams &p, const float *tp, const float *
                              int n_img, cudaStream_t s)
 {
     if (n_img <= 0) return cudaSuccess;
-    cudaError_t e;
+    // Prefer 16-column tiles (about 3 CTAs per SM for a 384-row detector);
+    // fall back to narrower tiles for tall detectors.
     const size_t limit = 220 * 1024;
-    dim3 grid;
-    grid.y = n_img;
-    if (col_smem_bytes(p, 32) <= limit) {
-        const size_t b = col_smem_bytes(p, 32);
-        e = cudaFuncSetAttribute(k_blur_cols<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b);
-        if (e != cudaSuccess) return e;
-        grid.x = (p.n_u + 31) / 32;
-        k_blur_cols<32><<<grid, kColThreads, b, s>>>(p, tp, ts, out);
-    } else if (col_smem_bytes(p, 16) <= limit) {
-        const size_t b = col_smem_bytes(p, 16);
-        e = cudaFuncSetAttribute(k_blur_cols<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b);
-        if (e != cudaSuccess) return e;
-        grid.x = (p.n_u + 15) / 16;
-        k_blur_cols<16><<<grid, kColThreads, b, s>>>(p, tp, ts, out);
-    } else {
-        const size_t b = col_smem_bytes(p, 8);
-        if (b > limit) return cudaErrorInvalidValue;
-        e = cudaFuncSetAttribute(k_blur_cols<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b);
-        if (e != cudaSuccess) return e;
-        grid.x = (p.n_u + 7) / 8;
-        k_blur_cols<8><<<grid, kColThreads, b, s>>>(p, tp, ts, out);
-    }
-    return cudaGetLastError();
+    if (col_smem_bytes(p, 18) <= limit / 2) return launch_cols_tw<16, 18>(p, tp, ts, out, n_img, s);
+    if (col_smem_bytes(p, 9) <= limit) return launch_cols_tw<8, 9>(p, tp, ts, out, n_img, s);
+    return cudaErrorInvalidValue;
 }
 
-__global__ void k_poisson(const float *lam, float *out, int n_img, int n_v, int n_u, int angle0,
-                          uint64_t seed)
+// One thread per pixel: x over u, blockIdx.y = row, blockIdx.z = projection.
+// lam and out may alias (each element is read before it is written).
+__global__ void __launch_bounds__(256)
+k_poisson(const float *lam, float *out, int n_v, int n_u, int angle0, uint64_t seed)
 {
-    const size_t n = (size_t)n_img * n_v * n_u;
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
-         i += (size_t)gridDim.x * blockDim.x) {
-        const int iu = (int)(i % n_u);
-        const int iv = (int)((i / n_u) % n_v);
-        const int k = (int)(i / ((size_t)n_u * n_v));
-        out[i] = noise::poisson(lam[i], (uint32_t)iu, (uint32_t)iv, (uint32_t)(angle0 + k), seed);
-    }
+    const int iu = blockIdx.x * blockDim.x + threadIdx.x;
+    if (iu >= n_u) return;
+    const int iv = blockIdx.y, k = blockIdx.z;
+    const size_t i = ((size_t)k * n_v + iv) * n_u + iu;
+    out[i] = noise::poisson(lam[i], (uint32_t)iu, (uint32_t)iv, (uint32_t)(angle0 + k), seed);
 }
 
 cudaError_t launch_poisson(const float *lam, float *out, int n_img, int n_v, int n_u, int angle0,
                            uint64_t seed, cudaStream_t s)
 {
-    const size_t n = (size_t)n_img * n_v * n_u;
-    if (n == 0) return cudaSuccess;
-    size_t blocks = (n + 255) / 256;
-    if (blocks > 152 * 16) blocks = 152 * 16;
-    k_poisson<<<(unsigned)blocks, 256, 0, s>>>(lam, out, n_img, n_v, n_u, angle0, seed);
+    if ((size_t)n_img * n_v * n_u == 0) return cudaSuccess;
+    if (n_v > 65535 || n_img > 65535) return cudaErrorInvalidValue;
+    const int threads = n_u >= 256 ? 256 : ((n_u + 31) / 32) * 32;
+    dim3 grid((n_u + threads - 1) / threads, n_v, n_img);
+    k_poisson<<<grid, threads, 0, s>>>(lam, out, n_v, n_u, angle0, seed);
     return cudaGetLastError();
 }
 

@@ -164,10 +164,11 @@ cudaError_t launch_fdk_filter(const FdkParams &p, const float *counts, float *fi
 }
 
 namespace {
-constexpr int kZc = 8;           // z values per thread
 constexpr int kFold = 16;        // angles per binary32 partial sum
 }
 
+// kZc z values per thread (the launcher balances the z chunks).
+template <int kZc>
 __global__ void __launch_bounds__(256)
 k_backproject(const __grid_constant__ FdkParams p, const float *__restrict__ f,
               double *__restrict__ vol, int v_lo, int v_hi)
@@ -187,6 +188,7 @@ k_backproject(const __grid_constant__ FdkParams p, const float *__restrict__ f,
 #pragma unroll
     for (int z = 0; z < kZc; ++z) { accd[z] = 0.0; accf[z] = 0.0f; }
     const float sdd_du = g.sdd / g.du, sdd_dv = g.sdd / g.dv;
+#pragma unroll 2
     for (int k = 0; k < g.n_angles; ++k) {
         const float2 cs = p.trig[k];
         const float U = g.sad - (x * cs.x + y * cs.y);
@@ -244,8 +246,27 @@ cudaError_t launch_backproject(const FdkParams &p, const float *filt, double *vo
     int lo, hi;
     fdk_row_range(p.g, &lo, &hi);
     dim3 block(32, 8);
-    dim3 grid((p.g.nx + 31) / 32, (p.g.ny + 7) / 8, (p.g.nz + kZc - 1) / kZc);
-    k_backproject<<<grid, block, 0, s>>>(p, filt, vol, lo, hi);
+    // z values per thread: as many as possible (the per-angle column set-up
+    // is shared by them) while keeping at least ~2 full waves of threads.
+    const long cols = (long)p.g.nx * p.g.ny;
+    const long want = 152L * 2048 * 2;
+    int zc = 8;
+    while (zc > 1 && cols * ((p.g.nz + zc - 1) / zc) < want) --zc;
+    {
+        const int nchunk = (p.g.nz + zc - 1) / zc;   // balance the chunks
+        zc = (p.g.nz + nchunk - 1) / nchunk;
+    }
+    dim3 grid((p.g.nx + 31) / 32, (p.g.ny + 7) / 8, (p.g.nz + zc - 1) / zc);
+    switch (zc) {
+    case 1: k_backproject<1><<<grid, block, 0, s>>>(p, filt, vol, lo, hi); break;
+    case 2: k_backproject<2><<<grid, block, 0, s>>>(p, filt, vol, lo, hi); break;
+    case 3: k_backproject<3><<<grid, block, 0, s>>>(p, filt, vol, lo, hi); break;
+    case 4: k_backproject<4><<<grid, block, 0, s>>>(p, filt, vol, lo, hi); break;
+    case 5: k_backproject<5><<<grid, block, 0, s>>>(p, filt, vol, lo, hi); break;
+    case 6: k_backproject<6><<<grid, block, 0, s>>>(p, filt, vol, lo, hi); break;
+    case 7: k_backproject<7><<<grid, block, 0, s>>>(p, filt, vol, lo, hi); break;
+    default: k_backproject<8><<<grid, block, 0, s>>>(p, filt, vol, lo, hi); break;
+    }
     return cudaGetLastError();
 }
 

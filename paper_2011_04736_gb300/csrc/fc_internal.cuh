@@ -22,6 +22,7 @@ struct DevGeom {
     int nx, ny, nz;
     float dx, dy, dz;
     float lox, loy, loz;    // lower box corner = -N d / 2
+    float idx, idy, idz;    // 1 / voxel pitch
 };
 
 // Projector launch parameters (passed as a __grid_constant__ kernel argument;
@@ -32,6 +33,7 @@ struct ProjParams {
     const uint8_t *labels;  // [nz][ny][nx]
     int angle0;             // absolute index of the first angle of the launch
     int n_angles_launch;
+    int v_hit_lo, v_hit_hi; // detector rows whose rays can meet the voxel slab
     int n_mat, n_e;
     float wd[kMaxBins];             // w D / sum(w D)
     float mu2[kMaxBins][kMaxMat];   // mu * log2(e), zero padded
@@ -41,9 +43,6 @@ struct BlurParams {
     int n_u, n_v;
     int rp, rs;             // tap radii of the PSF and scatter kernels
     float n0, spr;
-    uint64_t seed;
-    int noise;
-    int angle0;
     float gp[kMaxTaps];     // PSF taps, index j + rp
     float gs[kMaxTaps];     // scatter taps, index j + rs
 };

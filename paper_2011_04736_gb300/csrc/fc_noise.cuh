@@ -170,15 +170,15 @@ __device__ __forceinline__ float poisson(float lam, uint32_t iu, uint32_t iv, ui
         }
         return kf;
     }
+    // log(lam) and 1/alpha only enter the final acceptance test; they are
+    // evaluated when first needed (same values, fewer operations).
     const float slam = __fsqrt_rn(lam);
-    const float loglam = log_f32(lam);
+    float loglam = 0.0f, invalpha = 0.0f;
+    bool have_slow = false;
     float b = FMUL(2.53f, slam);
     b = FADD(0.931f, b);
     float a = FMUL(0.02483f, b);
     a = FADD(-0.059f, a);
-    float invalpha = FSUB(b, 3.4f);
-    invalpha = FDIV(1.1328f, invalpha);
-    invalpha = FADD(1.1239f, invalpha);
     float vr = FSUB(b, 2.0f);
     vr = FDIV(3.6224f, vr);
     vr = FSUB(0.9277f, vr);
@@ -198,6 +198,13 @@ __device__ __forceinline__ float poisson(float lam, uint32_t iu, uint32_t iv, ui
             const float kf = floorf(t);
             if (us >= 0.07f && V <= vr) return kf;
             if (kf < 0.0f || (us < 0.013f && V > us)) continue;
+            if (!have_slow) {
+                loglam = log_f32(lam);
+                invalpha = FSUB(b, 3.4f);
+                invalpha = FDIV(1.1328f, invalpha);
+                invalpha = FADD(1.1239f, invalpha);
+                have_slow = true;
+            }
             float den = FMUL(us, us);
             den = FDIV(a, den);
             den = FADD(den, b);

@@ -37,18 +37,18 @@ struct AxisWalk {
     int rem;     // crossings left before leaving the grid
 };
 
-__device__ __forceinline__ AxisWalk setup_axis(float A, float d, float lo, float vox, int i,
-                                               int n, int stride, float t_in)
+__device__ __forceinline__ AxisWalk setup_axis(float A, float d, float inv_d, float lo, float vox,
+                                               int i, int n, int stride, float t_in)
 {
     AxisWalk w;
     if (d > 0.0f) {
-        w.t0 = (lo + (float)(i + 1) * vox - A) / d;
-        w.dt = vox / d;
+        w.t0 = (lo + (float)(i + 1) * vox - A) * inv_d;
+        w.dt = vox * inv_d;
         w.step = stride;
         w.rem = n - 1 - i;
     } else if (d < 0.0f) {
-        w.t0 = (lo + (float)i * vox - A) / d;
-        w.dt = -vox / d;
+        w.t0 = (lo + (float)i * vox - A) * inv_d;
+        w.dt = -vox * inv_d;
         w.step = -stride;
         w.rem = i;
     } else {
@@ -78,88 +78,95 @@ k_project(const __grid_constant__ ProjParams p, float *__restrict__ T, float *__
     const int kl = blockIdx.z;
     if (iu >= g.n_u || iv >= g.n_v) return;
     const int k = p.angle0 + kl;
-    const float2 cs = p.trig[k];
-    const float c = cs.x, s = cs.y;
-
-    // pixel in the gantry frame: source (SAD, 0, 0), pixel (SAD - SDD, u, v)
-    const float u = ((float)iu - g.cu) * g.du;
-    const float v = ((float)iv - g.cv) * g.dv;
-    const float uv2 = u * u + v * v;
-    const float n2 = g.sdd * g.sdd + uv2;
-    const float len = sqrtf(n2);
-    const float inv_len = 1.0f / len;
-    const float gx = -g.sdd * inv_len, gy = u * inv_len, gz = v * inv_len;
-    // closest point to the axis: fraction sA of the way from source to pixel
-    const float sA = g.sad * g.sdd / n2;
-    const float agx = g.sad * uv2 / n2, agy = sA * u, agz = sA * v;
-    const float Ax = agx * c - agy * s, Ay = agx * s + agy * c, Az = agz;
-    const float dx = gx * c - gy * s, dy = gx * s + gy * c, dz = gz;
-
-    // clip to the source-pixel segment and to the voxel box (slab method)
-    float t_in = -sA * len, t_out = (1.0f - sA) * len;
-    bool miss = false;
-    {
-        const float A3[3] = {Ax, Ay, Az}, d3[3] = {dx, dy, dz};
-        const float lo3[3] = {g.lox, g.loy, g.loz};
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            const float hi = -lo3[a];
-            if (d3[a] != 0.0f) {
-                const float t0 = (lo3[a] - A3[a]) / d3[a];
-                const float t1 = (hi - A3[a]) / d3[a];
-                t_in = fmaxf(t_in, fminf(t0, t1));
-                t_out = fminf(t_out, fmaxf(t0, t1));
-            } else if (A3[a] < lo3[a] || A3[a] >= hi) {
-                miss = true;
-            }
-        }
-    }
 
     float L[kMaxMat];
 #pragma unroll
     for (int m = 0; m < kMaxMat; ++m) L[m] = 0.0f;
 
-    const bool hit = !miss && t_in < t_out;
+    // Rows outside [v_hit_lo, v_hit_hi] cannot meet the voxel slab (host
+    // bound with margin): their rays keep L = 0 and T = 1.
+    bool hit = iv >= p.v_hit_lo && iv <= p.v_hit_hi;
     if (hit) {
-        const float px = fmaf(t_in, dx, Ax), py = fmaf(t_in, dy, Ay), pz = fmaf(t_in, dz, Az);
-        const int ix = clampi((int)floorf((px - g.lox) / g.dx), 0, g.nx - 1);
-        const int iy = clampi((int)floorf((py - g.loy) / g.dy), 0, g.ny - 1);
-        const int iz = clampi((int)floorf((pz - g.loz) / g.dz), 0, g.nz - 1);
-        AxisWalk wx = setup_axis(Ax, dx, g.lox, g.dx, ix, g.nx, 1, t_in);
-        AxisWalk wy = setup_axis(Ay, dy, g.loy, g.dy, iy, g.ny, g.nx, t_in);
-        AxisWalk wz = setup_axis(Az, dz, g.loz, g.dz, iz, g.nz, g.nx * g.ny, t_in);
-        float tx = wx.t0, ty = wy.t0, tz = wz.t0;
-        float cx = 0.0f, cy = 0.0f, cz = 0.0f;
-        int idx = (iz * g.ny + iy) * g.nx + ix;
-        int cur = __ldg(p.labels + idx);
-        float t_run = t_in;
-        // Each pass steps at least one axis whose remaining count is > 0 or
-        // leaves, so the loop ends after at most nx + ny + nz passes and idx
-        // never leaves the grid.
-        for (;;) {
-            const float tn = fminf(tx, fminf(ty, tz));
-            if (tn >= t_out) break;
-            const bool sx = tx == tn, sy = ty == tn, sz = tz == tn;
-            if ((sx && wx.rem == 0) || (sy && wy.rem == 0) || (sz && wz.rem == 0)) {
-                t_out = tn;
-                break;
-            }
-            if (sx) { idx += wx.step; --wx.rem; cx += 1.0f; tx = fmaf(cx, wx.dt, wx.t0); }
-            if (sy) { idx += wy.step; --wy.rem; cy += 1.0f; ty = fmaf(cy, wy.dt, wy.t0); }
-            if (sz) { idx += wz.step; --wz.rem; cz += 1.0f; tz = fmaf(cz, wz.dt, wz.t0); }
-            const int lab = __ldg(p.labels + idx);
-            if (lab != cur) {
-                add_run(L, cur, tn - t_run);
-                t_run = tn;
-                cur = lab;
+        const float2 cs = p.trig[k];
+        const float c = cs.x, s = cs.y;
+        // pixel in the gantry frame: source (SAD, 0, 0), pixel (SAD - SDD, u, v)
+        const float u = ((float)iu - g.cu) * g.du;
+        const float v = ((float)iv - g.cv) * g.dv;
+        const float uv2 = u * u + v * v;
+        const float n2 = g.sdd * g.sdd + uv2;
+        const float len = sqrtf(n2);
+        const float inv_len = __frcp_rn(len);
+        const float inv_n2 = inv_len * inv_len;
+        const float gx = -g.sdd * inv_len, gy = u * inv_len, gz = v * inv_len;
+        // closest point to the axis: fraction sA of the way from source to pixel
+        const float sA = g.sad * g.sdd * inv_n2;
+        const float agx = g.sad * uv2 * inv_n2, agy = sA * u, agz = sA * v;
+        const float Ax = agx * c - agy * s, Ay = agx * s + agy * c, Az = agz;
+        const float dx = gx * c - gy * s, dy = gx * s + gy * c, dz = gz;
+        const float ix_ = __frcp_rn(dx), iy_ = __frcp_rn(dy), iz_ = __frcp_rn(dz);
+
+        // clip to the source-pixel segment and to the voxel box (slab method)
+        float t_in = -sA * len, t_out = (1.0f - sA) * len;
+        {
+            const float A3[3] = {Ax, Ay, Az}, d3[3] = {dx, dy, dz}, i3[3] = {ix_, iy_, iz_};
+            const float lo3[3] = {g.lox, g.loy, g.loz};
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                const float hi = -lo3[a];
+                if (d3[a] != 0.0f) {
+                    const float t0 = (lo3[a] - A3[a]) * i3[a];
+                    const float t1 = (hi - A3[a]) * i3[a];
+                    t_in = fmaxf(t_in, fminf(t0, t1));
+                    t_out = fminf(t_out, fmaxf(t0, t1));
+                } else if (A3[a] < lo3[a] || A3[a] >= hi) {
+                    hit = false;
+                }
             }
         }
-        add_run(L, cur, t_out - t_run);
+        hit = hit && t_in < t_out;
+        if (hit) {
+            const float px = fmaf(t_in, dx, Ax), py = fmaf(t_in, dy, Ay), pz = fmaf(t_in, dz, Az);
+            const int ix = clampi((int)floorf((px - g.lox) * g.idx), 0, g.nx - 1);
+            const int iy = clampi((int)floorf((py - g.loy) * g.idy), 0, g.ny - 1);
+            const int iz = clampi((int)floorf((pz - g.loz) * g.idz), 0, g.nz - 1);
+            AxisWalk wx = setup_axis(Ax, dx, ix_, g.lox, g.dx, ix, g.nx, 1, t_in);
+            AxisWalk wy = setup_axis(Ay, dy, iy_, g.loy, g.dy, iy, g.ny, g.nx, t_in);
+            AxisWalk wz = setup_axis(Az, dz, iz_, g.loz, g.dz, iz, g.nz, g.nx * g.ny, t_in);
+            float tx = wx.t0, ty = wy.t0, tz = wz.t0;
+            float cx = 0.0f, cy = 0.0f, cz = 0.0f;
+            int idx = (iz * g.ny + iy) * g.nx + ix;
+            int cur = __ldg(p.labels + idx);
+            float t_run = t_in;
+            // Each pass steps at least one axis whose remaining count is > 0
+            // or leaves, so the loop ends after at most nx + ny + nz passes
+            // and idx never leaves the grid.
+            for (;;) {
+                const float tn = fminf(tx, fminf(ty, tz));
+                if (tn >= t_out) break;
+                const bool sx = tx == tn, sy = ty == tn, sz = tz == tn;
+                if ((sx && wx.rem == 0) || (sy && wy.rem == 0) || (sz && wz.rem == 0)) {
+                    t_out = tn;
+                    break;
+                }
+                if (sx) { idx += wx.step; --wx.rem; cx += 1.0f; tx = fmaf(cx, wx.dt, wx.t0); }
+                if (sy) { idx += wy.step; --wy.rem; cy += 1.0f; ty = fmaf(cy, wy.dt, wy.t0); }
+                if (sz) { idx += wz.step; --wz.rem; cz += 1.0f; tz = fmaf(cz, wz.dt, wz.t0); }
+                const int lab = __ldg(p.labels + idx);
+                if (lab != cur) {
+                    add_run(L, cur, tn - t_run);
+                    t_run = tn;
+                    cur = lab;
+                }
+            }
+            add_run(L, cur, t_out - t_run);
+        }
     }
 
     const size_t ray = ((size_t)kl * g.n_v + iv) * g.n_u + iu;
     if (EMIT_L) {
-        for (int m = 0; m < p.n_mat; ++m) Lout[ray * p.n_mat + m] = L[m];
+#pragma unroll
+        for (int m = 0; m < kMaxMat; ++m)
+            if (m < p.n_mat) Lout[ray * p.n_mat + m] = L[m];
         return;
     }
     float Tv = 1.0f;

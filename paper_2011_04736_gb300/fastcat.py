@@ -26,7 +26,8 @@ FC_MAX_MATERIALS, FC_MAX_BINS = 8, 256
 ENTRY_POINTS = ("fc_create", "fc_destroy", "fc_last_error", "fc_set_geometry", "fc_set_phantom",
                 "fc_set_spectrum_detector", "fc_project", "fc_reconstruct", "fc_set_water_roi",
                 "fc_poisson", "fc_project_lengths", "fc_profile_enable", "fc_profile_read")
-FC_K_NAMES = ("project", "blur_rows", "blur_cols", "fdk_filter", "backproject", "hu", "lengths")
+FC_K_NAMES = ("project", "blur_rows", "blur_cols", "fdk_filter", "backproject", "hu", "lengths",
+              "noise")
 
 
 class FastcatError(RuntimeError):
