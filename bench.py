@@ -157,6 +157,8 @@ def _kernel_models(wl):
         # filtered reachable rows read once, FP64 volume written once
         "backproject": {"bytes": 4 * fpx + 8 * g.n_voxels, "flops": None, "bound": "hbm"},
         "hu": {"bytes": 8 * 2 * g.n_voxels + 4 * g.n_voxels, "flops": None, "bound": "hbm"},
+        # rates read, counts written
+        "noise": {"bytes": 8 * px, "flops": None, "bound": "hbm"},
     }
 
 
