@@ -96,7 +96,7 @@ k_project(const __grid_constant__ ProjParams p, float *__restrict__ T, float *__
         const float n2 = g.sdd * g.sdd + uv2;
         const float len = sqrtf(n2);
         const float inv_len = __frcp_rn(len);
-        const float inv_n2 = inv_len * inv_len;
+        const float inv_n2 = __frcp_rn(n2);
         const float gx = -g.sdd * inv_len, gy = u * inv_len, gz = v * inv_len;
         // closest point to the axis: fraction sA of the way from source to pixel
         const float sA = g.sad * g.sdd * inv_n2;
