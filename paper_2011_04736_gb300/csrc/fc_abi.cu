@@ -16,12 +16,6 @@
 
 #include "fc_internal.cuh"
 
-namespace fc {
-cudaError_t launch_fdk_filter_rows(const FdkParams &p, const float *counts, float *filt, int v_lo,
-                                   int v_hi, cudaStream_t s);
-void fdk_row_range(const DevGeom &g, int *v_lo, int *v_hi);
-}  // namespace fc
-
 namespace {
 
 thread_local std::string g_err;
@@ -84,13 +78,14 @@ struct fc_handle {
     double water_r = 1.0, zmargin = 0.1;
     // device buffers
     float2 *d_trig = nullptr;
-    uint8_t *d_labels = nullptr;
+    uint8_t *d_labels = nullptr;   // caller layout [nz][ny][nx]
+    uint8_t *d_lpad = nullptr;     // padded with a border frame (projector input)
     float *d_T = nullptr, *d_tp = nullptr, *d_ts = nullptr, *d_counts = nullptr, *d_filt = nullptr;
     double *d_vol = nullptr;
     float *d_hu = nullptr;
     double *d_part = nullptr;
     unsigned int *d_flag = nullptr;
-    size_t proj_elems = 0, vol_elems = 0;
+    size_t proj_elems = 0, vol_elems = 0, filt_elems = 0;
     // kernel-time tracing
     struct Rec {
         int id;
@@ -107,6 +102,7 @@ struct fc_handle {
     {
         dfree(d_trig);
         dfree(d_labels);
+        dfree(d_lpad);
         dfree(d_T);
         dfree(d_tp);
         dfree(d_ts);
@@ -139,9 +135,15 @@ int ensure_proj_buffers(fc_handle *h)
     return FC_OK;
 }
 
-int ensure_recon_buffers(fc_handle *h)
+int ensure_recon_buffers(fc_handle *h, cudaStream_t s)
 {
-    if (!h->d_filt) FC_CK(cudaMalloc((void **)&h->d_filt, h->proj_elems * sizeof(float)));
+    if (!h->d_filt) {
+        int lo, hi;
+        fc::fdk_row_range(h->dg, &lo, &hi);
+        h->filt_elems = (size_t)h->g.n_angles * (hi - lo + 1 + 3) * (h->g.n_u + 3);
+        FC_CK(cudaMalloc((void **)&h->d_filt, h->filt_elems * sizeof(float)));
+        FC_CK(cudaMemsetAsync(h->d_filt, 0, h->filt_elems * sizeof(float), s));
+    }
     if (!h->d_counts) FC_CK(cudaMalloc((void **)&h->d_counts, h->proj_elems * sizeof(float)));
     if (!h->d_vol) FC_CK(cudaMalloc((void **)&h->d_vol, h->vol_elems * sizeof(double)));
     if (!h->d_hu) FC_CK(cudaMalloc((void **)&h->d_hu, h->vol_elems * sizeof(float)));
@@ -280,15 +282,16 @@ int fc_set_geometry(fc_handle *h, const fc_geometry *g)
         dfree(h->d_tp);
         dfree(h->d_ts);
         dfree(h->d_counts);
-        dfree(h->d_filt);
         h->has_counts = false;
     }
+    dfree(h->d_filt);  // its size follows the reachable detector rows
     if (vox != h->vol_elems) {
         dfree(h->d_vol);
         dfree(h->d_hu);
     }
     if (!same_vol) {
         dfree(h->d_labels);
+        dfree(h->d_lpad);
         h->has_phantom = false;
     }
     dfree(h->d_trig);
@@ -338,10 +341,14 @@ int fc_set_phantom(fc_handle *h, const uint8_t *labels, int n_mat, int where, vo
     DeviceGuard dgd(h->device);
     cudaStream_t s = (cudaStream_t)stream;
     if (!h->d_labels) FC_CK(cudaMalloc((void **)&h->d_labels, h->vol_elems));
+    if (!h->d_lpad)
+        FC_CK(cudaMalloc((void **)&h->d_lpad,
+                         (size_t)(h->g.nx + 2) * (h->g.ny + 2) * (h->g.nz + 2)));
     FC_CK(cudaMemcpyAsync(h->d_labels, labels, h->vol_elems,
                           where == FC_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, s));
     FC_CK(cudaMemsetAsync(h->d_flag, 0, sizeof(unsigned int), s));
-    FC_CK(fc::launch_check_labels(h->d_labels, h->vol_elems, n_mat, h->d_flag, s));
+    FC_CK(fc::launch_pad_labels(h->d_labels, h->d_lpad, h->g.nx, h->g.ny, h->g.nz, n_mat,
+                                h->d_flag, s));
     unsigned int bad = 0;
     FC_CK(cudaMemcpyAsync(&bad, h->d_flag, sizeof(bad), cudaMemcpyDeviceToHost, s));
     FC_CK(cudaStreamSynchronize(s));
@@ -422,7 +429,7 @@ static int fill_proj_params(fc_handle *h, int a0, int na, fc::ProjParams *p)
     memset(p, 0, sizeof(*p));
     p->g = h->dg;
     p->trig = h->d_trig;
-    p->labels = h->d_labels;
+    p->labels = h->d_lpad;
     p->angle0 = a0;
     p->n_angles_launch = na;
     {
@@ -533,7 +540,7 @@ int fc_reconstruct(fc_handle *h, const float *counts, int counts_where, double *
         return fail(FC_EINVAL, "fc_reconstruct: bad out_where");
     DeviceGuard dgd(h->device);
     cudaStream_t s = (cudaStream_t)stream;
-    int rc = ensure_recon_buffers(h);
+    int rc = ensure_recon_buffers(h, s);
     if (rc) return rc;
     const size_t pbytes = h->proj_elems * sizeof(float);
     const float *src = h->d_counts;
@@ -550,6 +557,9 @@ int fc_reconstruct(fc_handle *h, const float *counts, int counts_where, double *
     p.tau = (float)(h->g.du_cm * h->g.sad_cm / h->g.sdd_cm);
     p.mag = (float)(h->g.sad_cm / h->g.sdd_cm);
     p.scale = h->g.arc_rad / (2.0 * h->g.n_angles);
+    fc::fdk_row_range(h->dg, &p.v_lo, &p.v_hi);
+    p.pw = h->g.n_u + 3;
+    p.ph = p.v_hi - p.v_lo + 1 + 3;
     {
         Trace t(h, FC_K_FDK_FILTER, 1, s);
         FC_CK(fc::launch_fdk_filter(p, src, h->d_filt, s));

@@ -235,26 +235,58 @@ cudaError_t launch_blur_cols(const BlurParams &p, const float *tp, const float *
     return cudaErrorInvalidValue;
 }
 
-// One thread per pixel: x over u, blockIdx.y = row, blockIdx.z = projection.
-// lam and out may alias (each element is read before it is written).
+// Each thread draws kPer pixels of one detector row (u = base + 32 s).  A
+// rejection draw takes a variable number of attempts, so instead of
+// finishing one pixel before the next (where every warp waits for its
+// slowest lane at each pixel), a lane that finishes a pixel starts its next
+// one in the same loop pass; a warp then runs about kPer * E[attempts] passes
+// plus the spread of the per-lane totals.  The draws themselves are exactly
+// those of noise::poisson.  lam and out may alias.
+namespace {
+constexpr int kPer = 8;
+}
+
 __global__ void __launch_bounds__(256)
 k_poisson(const float *lam, float *out, int n_v, int n_u, int angle0, uint64_t seed)
 {
-    const int iu = blockIdx.x * blockDim.x + threadIdx.x;
-    if (iu >= n_u) return;
-    const int iv = blockIdx.y, k = blockIdx.z;
-    const size_t i = ((size_t)k * n_v + iv) * n_u + iu;
-    out[i] = noise::poisson(lam[i], (uint32_t)iu, (uint32_t)iv, (uint32_t)(angle0 + k), seed);
+    const int iv = blockIdx.y * blockDim.y + threadIdx.y;
+    if (iv >= n_v) return;
+    const int k = blockIdx.z;
+    const size_t row = ((size_t)k * n_v + iv) * n_u;
+    const int u_base = blockIdx.x * (32 * kPer) + threadIdx.x;
+    const uint32_t kabs = (uint32_t)(angle0 + k);
+    noise::Ptrs st;
+    int s = 0, cur = -1;
+    for (;;) {
+        while (cur < 0 && s < kPer) {
+            const int iu = u_base + 32 * s;
+            if (iu >= n_u) { s = kPer; break; }
+            float r;
+            if (noise::poisson_begin(lam[row + iu], (uint32_t)iu, (uint32_t)iv, kabs, seed, st, r)) {
+                out[row + iu] = r;
+                ++s;
+            } else {
+                cur = iu;
+            }
+        }
+        if (cur < 0) break;
+        float r;
+        if (noise::ptrs_attempt(st, r)) {
+            out[row + cur] = r;
+            cur = -1;
+            ++s;
+        }
+    }
 }
 
 cudaError_t launch_poisson(const float *lam, float *out, int n_img, int n_v, int n_u, int angle0,
                            uint64_t seed, cudaStream_t s)
 {
     if ((size_t)n_img * n_v * n_u == 0) return cudaSuccess;
-    if (n_v > 65535 || n_img > 65535) return cudaErrorInvalidValue;
-    const int threads = n_u >= 256 ? 256 : ((n_u + 31) / 32) * 32;
-    dim3 grid((n_u + threads - 1) / threads, n_v, n_img);
-    k_poisson<<<grid, threads, 0, s>>>(lam, out, n_v, n_u, angle0, seed);
+    if ((n_v + 7) / 8 > 65535 || n_img > 65535) return cudaErrorInvalidValue;
+    dim3 block(32, 8);
+    dim3 grid((n_u + 32 * kPer - 1) / (32 * kPer), (n_v + 7) / 8, n_img);
+    k_poisson<<<grid, block, 0, s>>>(lam, out, n_v, n_u, angle0, seed);
     return cudaGetLastError();
 }
 

@@ -9,12 +9,12 @@
 // Filter: one CTA per detector row; the weighted row sits zero-padded in
 // shared memory and each thread produces 16 adjacent outputs from a sliding
 // register window that advances two samples per odd tap (16 FMAs per two
-// shared loads).  Only rows the backprojector can sample are filtered; the
-// backprojector treats every other row as zero, which is what it would read
-// from them after filtering because it never samples them.
+// shared loads).  Only rows the backprojector can sample are filtered and
+// stored (a conservative bound on the rows the voxel slab projects onto),
+// in a zero-padded layout so the bilinear taps need no bounds tests.
 // Backprojection: one thread per (x, y) column and chunk of z; per angle
 // the column's detector abscissa and weight are computed once and the z
-// loop walks the detector column linearly.  Partial sums over 16 angles are
+// loop walks the detector column linearly.  Partial sums over 64 angles are
 // kept in binary32 and folded into binary64 accumulators.
 #include <math.h>
 
@@ -49,14 +49,17 @@ cudaError_t upload_ramp_taps()
 // rows [v_lo, v_hi] of every projection; blockIdx.x = projection * nrows + r
 __global__ void __launch_bounds__(kFiltThreads)
 k_fdk_filter(const __grid_constant__ FdkParams p, const float *__restrict__ counts,
-             float *__restrict__ filt, int v_lo, int nrows)
+             float *__restrict__ filt)
 {
     extern __shared__ float sx[];
     const DevGeom &g = p.g;
     const int n = g.n_u;
+    const int nrows = p.v_hi - p.v_lo + 1;
     const int k = blockIdx.x / nrows;
-    const int iv = v_lo + (int)(blockIdx.x % nrows);
+    const int r = (int)(blockIdx.x % nrows);
+    const int iv = p.v_lo + r;
     const size_t row = ((size_t)k * g.n_v + iv) * n;
+    float *dst = filt + ((size_t)k * p.ph + (r + 1)) * p.pw + 1;
     // padded row: index n + j holds q[j], zeros in [0, n) and [2n, 3n + pad)
     const float vi = ((float)iv - g.cv) * g.dv * p.mag;
     const float sad2v = g.sad * g.sad + vi * vi;
@@ -112,14 +115,13 @@ k_fdk_filter(const __grid_constant__ FdkParams p, const float *__restrict__ coun
         }
 #pragma unroll
         for (int o = 0; o < kFiltOut; ++o)
-            if (i0 + o < n) filt[row + i0 + o] = acc[o] * inv_tau;
+            if (i0 + o < n) dst[i0 + o] = acc[o] * inv_tau;
     }
 }
 
-cudaError_t launch_fdk_filter_rows(const FdkParams &p, const float *counts, float *filt, int v_lo,
-                                   int v_hi, cudaStream_t s)
+cudaError_t launch_fdk_filter(const FdkParams &p, const float *counts, float *filt, cudaStream_t s)
 {
-    const int nrows = v_hi - v_lo + 1;
+    const int nrows = p.v_hi - p.v_lo + 1;
     if (nrows <= 0 || p.g.n_angles <= 0) return cudaSuccess;
     if (p.g.n_u > kMaxFiltTaps) return cudaErrorInvalidValue;
     cudaError_t e = upload_ramp_taps();
@@ -132,7 +134,7 @@ cudaError_t launch_fdk_filter_rows(const FdkParams &p, const float *counts, floa
         if (e != cudaSuccess) return e;
     }
     const size_t blocks = (size_t)p.g.n_angles * nrows;
-    k_fdk_filter<<<(unsigned)blocks, kFiltThreads, smem, s>>>(p, counts, filt, v_lo, nrows);
+    k_fdk_filter<<<(unsigned)blocks, kFiltThreads, smem, s>>>(p, counts, filt);
     return cudaGetLastError();
 }
 
@@ -156,22 +158,15 @@ void fdk_row_range(const DevGeom &g, int *v_lo, int *v_hi)
     *v_hi = hi > g.n_v - 1 ? g.n_v - 1 : hi;
 }
 
-cudaError_t launch_fdk_filter(const FdkParams &p, const float *counts, float *filt, cudaStream_t s)
-{
-    int lo, hi;
-    fdk_row_range(p.g, &lo, &hi);
-    return launch_fdk_filter_rows(p, counts, filt, lo, hi, s);
-}
-
 namespace {
-constexpr int kFold = 16;        // angles per binary32 partial sum
+constexpr int kFold = 64;        // angles per binary32 partial sum
 }
 
 // kZc z values per thread (the launcher balances the z chunks).
 template <int kZc>
 __global__ void __launch_bounds__(256)
 k_backproject(const __grid_constant__ FdkParams p, const float *__restrict__ f,
-              double *__restrict__ vol, int v_lo, int v_hi)
+              double *__restrict__ vol)
 {
     const DevGeom &g = p.g;
     const int ix = blockIdx.x * 32 + threadIdx.x;
@@ -182,74 +177,66 @@ k_backproject(const __grid_constant__ FdkParams p, const float *__restrict__ f,
     const float y = ((float)iy - 0.5f * (float)(g.ny - 1)) * g.dy;
     const float z0 = ((float)iz0 - 0.5f * (float)(g.nz - 1)) * g.dz;
     const int nzc = min(kZc, g.nz - iz0);
-    const size_t plane = (size_t)g.n_v * g.n_u;
-    double accd[kZc];
-    float accf[kZc];
-#pragma unroll
-    for (int z = 0; z < kZc; ++z) { accd[z] = 0.0; accf[z] = 0.0f; }
+    const size_t plane = (size_t)p.ph * p.pw;
+    // padded coordinates: column c + 1 holds detector column c, row r + 1
+    // holds detector row v_lo + r; clamping to [0, pw - 2] x [0, ph - 2]
+    // keeps both taps inside the buffer and only ever lands on zero padding
+    // where the true sample lies outside the detector (columns) or is never
+    // requested (rows).
+    const float cu1 = g.cu + 1.0f, cv1 = g.cv - (float)p.v_lo + 1.0f;
+    const float umax = (float)(p.pw - 2), vmaxp = (float)(p.ph - 2);
     const float sdd_du = g.sdd / g.du, sdd_dv = g.sdd / g.dv;
-#pragma unroll 2
-    for (int k = 0; k < g.n_angles; ++k) {
-        const float2 cs = p.trig[k];
-        const float U = g.sad - (x * cs.x + y * cs.y);
-        const float ru = y * cs.x - x * cs.y;
-        const float iU = 1.0f / U;
-        const float fu = ru * iU * sdd_du + g.cu;
-        const float w = (g.sad * iU) * (g.sad * iU);
-        const float fv0 = z0 * iU * sdd_dv + g.cv;
-        const float dfv = g.dz * iU * sdd_dv;
-        const float fu0 = floorf(fu);
-        const float au = fu - fu0;
-        const int u0 = (int)fu0;
-        const bool u0ok = u0 >= 0 && u0 < g.n_u;
-        const bool u1ok = u0 + 1 >= 0 && u0 + 1 < g.n_u;
-        const float *fk = f + (size_t)k * plane;
+    double accd[kZc];
 #pragma unroll
-        for (int z = 0; z < kZc; ++z) {
-            if (z < nzc) {
-                const float fv = fmaf((float)z, dfv, fv0);
-                const float fv0f = floorf(fv);
-                const float av = fv - fv0f;
-                const int v0 = (int)fv0f;
-                float a00 = 0.0f, a01 = 0.0f, a10 = 0.0f, a11 = 0.0f;
-                if (v0 >= v_lo && v0 <= v_hi) {
-                    const float *r = fk + (size_t)v0 * g.n_u;
-                    if (u0ok) a00 = __ldg(r + u0);
-                    if (u1ok) a01 = __ldg(r + u0 + 1);
+    for (int z = 0; z < kZc; ++z) accd[z] = 0.0;
+    for (int kb = 0; kb < g.n_angles; kb += kFold) {
+        const int ke = min(g.n_angles, kb + kFold);
+        float accf[kZc];
+#pragma unroll
+        for (int z = 0; z < kZc; ++z) accf[z] = 0.0f;
+#pragma unroll 2
+        for (int k = kb; k < ke; ++k) {
+            const float2 cs = p.trig[k];
+            const float U = g.sad - (x * cs.x + y * cs.y);
+            const float ru = y * cs.x - x * cs.y;
+            const float iU = __frcp_rn(U);
+            const float fu = fminf(fmaxf(fmaf(ru * iU, sdd_du, cu1), 0.0f), umax);
+            const float w = (g.sad * iU) * (g.sad * iU);
+            const float fv0 = fmaf(z0 * iU, sdd_dv, cv1);
+            const float dfv = g.dz * iU * sdd_dv;
+            const float fu0 = floorf(fu);
+            const float au = fu - fu0;
+            const float *fk = f + (size_t)k * plane + (int)fu0;
+#pragma unroll
+            for (int z = 0; z < kZc; ++z) {
+                if (z < nzc) {
+                    const float fv = fminf(fmaxf(fmaf((float)z, dfv, fv0), 0.0f), vmaxp);
+                    const float fvf = floorf(fv);
+                    const float av = fv - fvf;
+                    const float *r = fk + (int)fvf * p.pw;
+                    const float a00 = __ldg(r), a01 = __ldg(r + 1);
+                    const float a10 = __ldg(r + p.pw), a11 = __ldg(r + p.pw + 1);
+                    const float top = fmaf(au, a01 - a00, a00);
+                    const float bot = fmaf(au, a11 - a10, a10);
+                    accf[z] = fmaf(w, fmaf(av, bot - top, top), accf[z]);
                 }
-                if (v0 + 1 >= v_lo && v0 + 1 <= v_hi) {
-                    const float *r = fk + (size_t)(v0 + 1) * g.n_u;
-                    if (u0ok) a10 = __ldg(r + u0);
-                    if (u1ok) a11 = __ldg(r + u0 + 1);
-                }
-                const float top = fmaf(au, a01 - a00, a00);
-                const float bot = fmaf(au, a11 - a10, a10);
-                accf[z] = fmaf(w, fmaf(av, bot - top, top), accf[z]);
             }
         }
-        if ((k + 1) % kFold == 0) {
 #pragma unroll
-            for (int z = 0; z < kZc; ++z) { accd[z] += (double)accf[z]; accf[z] = 0.0f; }
-        }
+        for (int z = 0; z < kZc; ++z) accd[z] += (double)accf[z];
     }
 #pragma unroll
-    for (int z = 0; z < kZc; ++z) {
-        if (z < nzc) {
-            const double a = accd[z] + (double)accf[z];
-            vol[((size_t)(iz0 + z) * g.ny + iy) * g.nx + ix] = a * p.scale;
-        }
-    }
+    for (int z = 0; z < kZc; ++z)
+        if (z < nzc) vol[((size_t)(iz0 + z) * g.ny + iy) * g.nx + ix] = accd[z] * p.scale;
 }
 
 cudaError_t launch_backproject(const FdkParams &p, const float *filt, double *vol, cudaStream_t s)
 {
-    int lo, hi;
-    fdk_row_range(p.g, &lo, &hi);
     dim3 block(32, 8);
     // z values per thread: as many as possible (the per-angle column set-up
-    // is shared by them) while keeping at least ~2 full waves of threads.
+    // is shared by them) while keeping about 24 resident warps per SM.
     const long cols = (long)p.g.nx * p.g.ny;
-    const long want = 152L * 2048 * 2;
+    const long want = 152L * 768;
     int zc = 8;
     while (zc > 1 && cols * ((p.g.nz + zc - 1) / zc) < want) --zc;
     {
@@ -258,14 +245,14 @@ cudaError_t launch_backproject(const FdkParams &p, const float *filt, double *vo
     }
     dim3 grid((p.g.nx + 31) / 32, (p.g.ny + 7) / 8, (p.g.nz + zc - 1) / zc);
     switch (zc) {
-    case 1: k_backproject<1><<<grid, block, 0, s>>>(p, filt, vol, lo, hi); break;
-    case 2: k_backproject<2><<<grid, block, 0, s>>>(p, filt, vol, lo, hi); break;
-    case 3: k_backproject<3><<<grid, block, 0, s>>>(p, filt, vol, lo, hi); break;
-    case 4: k_backproject<4><<<grid, block, 0, s>>>(p, filt, vol, lo, hi); break;
-    case 5: k_backproject<5><<<grid, block, 0, s>>>(p, filt, vol, lo, hi); break;
-    case 6: k_backproject<6><<<grid, block, 0, s>>>(p, filt, vol, lo, hi); break;
-    case 7: k_backproject<7><<<grid, block, 0, s>>>(p, filt, vol, lo, hi); break;
-    default: k_backproject<8><<<grid, block, 0, s>>>(p, filt, vol, lo, hi); break;
+    case 1: k_backproject<1><<<grid, block, 0, s>>>(p, filt, vol); break;
+    case 2: k_backproject<2><<<grid, block, 0, s>>>(p, filt, vol); break;
+    case 3: k_backproject<3><<<grid, block, 0, s>>>(p, filt, vol); break;
+    case 4: k_backproject<4><<<grid, block, 0, s>>>(p, filt, vol); break;
+    case 5: k_backproject<5><<<grid, block, 0, s>>>(p, filt, vol); break;
+    case 6: k_backproject<6><<<grid, block, 0, s>>>(p, filt, vol); break;
+    case 7: k_backproject<7><<<grid, block, 0, s>>>(p, filt, vol); break;
+    default: k_backproject<8><<<grid, block, 0, s>>>(p, filt, vol); break;
     }
     return cudaGetLastError();
 }

@@ -11,6 +11,7 @@ namespace fc {
 constexpr int kMaxMat = FC_MAX_MATERIALS;
 constexpr int kMaxBins = FC_MAX_BINS;
 constexpr int kMaxTaps = 2 * 256 + 1;  // 2 * ceil(4 * FC_MAX_SIGMA_PX) + 1
+constexpr int kBorder = 255;           // label of the padding frame around the phantom
 
 // Geometry in the precision the kernels use (binary32), derived on the host
 // from the binary64 fc_geometry.
@@ -30,7 +31,7 @@ struct DevGeom {
 struct ProjParams {
     DevGeom g;
     const float2 *trig;     // [n_angles] (cos, sin) of each angle
-    const uint8_t *labels;  // [nz][ny][nx]
+    const uint8_t *labels;  // padded [nz + 2][ny + 2][nx + 2], kBorder frame
     int angle0;             // absolute index of the first angle of the launch
     int n_angles_launch;
     int v_hit_lo, v_hit_hi; // detector rows whose rays can meet the voxel slab
@@ -47,6 +48,10 @@ struct BlurParams {
     float gs[kMaxTaps];     // scatter taps, index j + rs
 };
 
+// Filtered projections are stored only for the detector rows the
+// backprojector can reach, [v_lo, v_hi], in a zero-padded layout
+// [angle][1 + (v_hi - v_lo + 1) + 2][1 + n_u + 2]: one zero row / column
+// before and two after, so bilinear taps need no bounds tests.
 struct FdkParams {
     DevGeom g;
     const float2 *trig;
@@ -54,7 +59,11 @@ struct FdkParams {
     float tau;              // du * SAD / SDD
     float mag;              // SAD / SDD
     double scale;           // arc / (2 n_angles)
+    int v_lo, v_hi;         // reachable detector rows
+    int pw, ph;             // padded row length n_u + 3, padded rows (v_hi - v_lo + 1) + 3
 };
+
+void fdk_row_range(const DevGeom &g, int *v_lo, int *v_hi);
 
 // launchers (return cudaError_t of the launch)
 cudaError_t launch_project(const ProjParams &p, float *T, float *L_out, cudaStream_t s);
@@ -70,7 +79,7 @@ cudaError_t launch_backproject(const FdkParams &p, const float *filt, double *vo
                                cudaStream_t s);
 cudaError_t launch_hu(const DevGeom &g, const double *vol, float *hu, double *partials,
                       float radius, int zcut, cudaStream_t s);
-cudaError_t launch_check_labels(const uint8_t *labels, size_t n, int n_mat,
-                                unsigned int *bad, cudaStream_t s);
+cudaError_t launch_pad_labels(const uint8_t *labels, uint8_t *padded, int nx, int ny, int nz,
+                              int n_mat, unsigned int *bad, cudaStream_t s);
 
 }  // namespace fc

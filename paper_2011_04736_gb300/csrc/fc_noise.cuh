@@ -149,12 +149,25 @@ __device__ __forceinline__ float log_pmf(float kf, float lam, float loglam)
     return FSUB(r, dl);
 }
 
-__device__ __forceinline__ float poisson(float lam, uint32_t iu, uint32_t iv, uint32_t k,
-                                         uint64_t seed)
+// State of one transformed-rejection draw between attempts.
+struct Ptrs {
+    float lam, b, a, vr, loglam, invalpha;
+    uint4 w;            // Philox block j
+    uint32_t iu, iv, k, j;
+    uint2 key;
+    int h;              // 0: attempt uses words (x, y) of block j, 1: words (z, w)
+    bool have_slow;     // loglam and invalpha evaluated
+};
+
+// First stage of a draw.  Returns true with the count in r when it is decided
+// without rejection sampling (rate <= 0 or NaN, rate > 1e7, rate < 10);
+// otherwise prepares s for ptrs_attempt.
+__device__ __forceinline__ bool poisson_begin(float lam, uint32_t iu, uint32_t iv, uint32_t k,
+                                              uint64_t seed, Ptrs &s, float &r)
 {
     const uint2 key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
-    if (!(lam > 0.0f)) return 0.0f;
-    if (lam > 1.0e7f) return floorf(FADD(lam, 0.5f));
+    if (!(lam > 0.0f)) { r = 0.0f; return true; }
+    if (lam > 1.0e7f) { r = floorf(FADD(lam, 0.5f)); return true; }
     if (lam < 10.0f) {
         const uint4 w = philox4x32_10(make_uint4(iu, iv, k, 0u), key);
         const float u = unif(w.x);
@@ -168,13 +181,12 @@ __device__ __forceinline__ float poisson(float lam, uint32_t iu, uint32_t iv, ui
             if (Fn == F) break;
             F = Fn;
         }
-        return kf;
+        r = kf;
+        return true;
     }
     // log(lam) and 1/alpha only enter the final acceptance test; they are
     // evaluated when first needed (same values, fewer operations).
     const float slam = __fsqrt_rn(lam);
-    float loglam = 0.0f, invalpha = 0.0f;
-    bool have_slow = false;
     float b = FMUL(2.53f, slam);
     b = FADD(0.931f, b);
     float a = FMUL(0.02483f, b);
@@ -182,39 +194,63 @@ __device__ __forceinline__ float poisson(float lam, uint32_t iu, uint32_t iv, ui
     float vr = FSUB(b, 2.0f);
     vr = FDIV(3.6224f, vr);
     vr = FSUB(0.9277f, vr);
-    for (uint32_t j = 0; j < 32u; ++j) {
-        const uint4 w = philox4x32_10(make_uint4(iu, iv, k, j), key);
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const float U = FSUB(unif(h ? w.z : w.x), 0.5f);
-            const float V = unif(h ? w.w : w.y);
-            const float us = FSUB(0.5f, fabsf(U));
-            float t = FMUL(2.0f, a);
-            t = FDIV(t, us);
-            t = FADD(t, b);
-            t = FMUL(t, U);
-            t = FADD(t, lam);
-            t = FADD(t, 0.43f);
-            const float kf = floorf(t);
-            if (us >= 0.07f && V <= vr) return kf;
-            if (kf < 0.0f || (us < 0.013f && V > us)) continue;
-            if (!have_slow) {
-                loglam = log_f32(lam);
-                invalpha = FSUB(b, 3.4f);
-                invalpha = FDIV(1.1328f, invalpha);
-                invalpha = FADD(1.1239f, invalpha);
-                have_slow = true;
-            }
-            float den = FMUL(us, us);
-            den = FDIV(a, den);
-            den = FADD(den, b);
-            float q = FMUL(V, invalpha);
-            q = FDIV(q, den);
-            const float lhs = log_f32(q);
-            if (lhs <= log_pmf(kf, lam, loglam)) return kf;
+    s.lam = lam; s.b = b; s.a = a; s.vr = vr;
+    s.loglam = 0.0f; s.invalpha = 0.0f; s.have_slow = false;
+    s.iu = iu; s.iv = iv; s.k = k; s.j = 0; s.h = 0; s.key = key;
+    return false;
+}
+
+// One PTRS attempt.  Returns true with the count in r when the draw is
+// decided (accepted, or the 64-attempt limit reached).
+__device__ __forceinline__ bool ptrs_attempt(Ptrs &s, float &r)
+{
+    if (s.h == 0) s.w = philox4x32_10(make_uint4(s.iu, s.iv, s.k, s.j), s.key);
+    const float U = FSUB(unif(s.h ? s.w.z : s.w.x), 0.5f);
+    const float V = unif(s.h ? s.w.w : s.w.y);
+    const float us = FSUB(0.5f, fabsf(U));
+    float t = FMUL(2.0f, s.a);
+    t = FDIV(t, us);
+    t = FADD(t, s.b);
+    t = FMUL(t, U);
+    t = FADD(t, s.lam);
+    t = FADD(t, 0.43f);
+    const float kf = floorf(t);
+    if (us >= 0.07f && V <= s.vr) { r = kf; return true; }
+    if (!(kf < 0.0f || (us < 0.013f && V > us))) {
+        if (!s.have_slow) {
+            s.loglam = log_f32(s.lam);
+            float ia = FSUB(s.b, 3.4f);
+            ia = FDIV(1.1328f, ia);
+            s.invalpha = FADD(1.1239f, ia);
+            s.have_slow = true;
         }
+        float den = FMUL(us, us);
+        den = FDIV(s.a, den);
+        den = FADD(den, s.b);
+        float q = FMUL(V, s.invalpha);
+        q = FDIV(q, den);
+        const float lhs = log_f32(q);
+        if (lhs <= log_pmf(kf, s.lam, s.loglam)) { r = kf; return true; }
     }
-    return floorf(FADD(lam, 0.5f));
+    if (s.h) {
+        s.h = 0;
+        if (++s.j == 32u) { r = floorf(FADD(s.lam, 0.5f)); return true; }
+    } else {
+        s.h = 1;
+    }
+    return false;
+}
+
+// Complete draw for pixel (iu, iv) of projection k.
+__device__ __forceinline__ float poisson(float lam, uint32_t iu, uint32_t iv, uint32_t k,
+                                         uint64_t seed)
+{
+    Ptrs s;
+    float r;
+    if (poisson_begin(lam, iu, iv, k, seed, s, r)) return r;
+    while (!ptrs_attempt(s, r)) {
+    }
+    return r;
 }
 
 #undef FADD

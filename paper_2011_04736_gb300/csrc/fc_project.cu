@@ -33,29 +33,25 @@ __device__ __forceinline__ void add_run(float (&L)[kMaxMat], int m, float len)
 struct AxisWalk {
     float t0;    // first crossing
     float dt;    // spacing of crossings
-    int step;    // index increment in the flattened volume
-    int rem;     // crossings left before leaving the grid
+    int step;    // index increment in the padded volume
 };
 
 __device__ __forceinline__ AxisWalk setup_axis(float A, float d, float inv_d, float lo, float vox,
-                                               int i, int n, int stride, float t_in)
+                                               int i, int stride, float t_in)
 {
     AxisWalk w;
     if (d > 0.0f) {
         w.t0 = (lo + (float)(i + 1) * vox - A) * inv_d;
         w.dt = vox * inv_d;
         w.step = stride;
-        w.rem = n - 1 - i;
     } else if (d < 0.0f) {
         w.t0 = (lo + (float)i * vox - A) * inv_d;
         w.dt = -vox * inv_d;
         w.step = -stride;
-        w.rem = i;
     } else {
         w.t0 = INFINITY;
         w.dt = 0.0f;
         w.step = 0;
-        w.rem = 0;
     }
     w.t0 = fmaxf(w.t0, t_in);
     return w;
@@ -129,36 +125,35 @@ k_project(const __grid_constant__ ProjParams p, float *__restrict__ T, float *__
             const int ix = clampi((int)floorf((px - g.lox) * g.idx), 0, g.nx - 1);
             const int iy = clampi((int)floorf((py - g.loy) * g.idy), 0, g.ny - 1);
             const int iz = clampi((int)floorf((pz - g.loz) * g.idz), 0, g.nz - 1);
-            AxisWalk wx = setup_axis(Ax, dx, ix_, g.lox, g.dx, ix, g.nx, 1, t_in);
-            AxisWalk wy = setup_axis(Ay, dy, iy_, g.loy, g.dy, iy, g.ny, g.nx, t_in);
-            AxisWalk wz = setup_axis(Az, dz, iz_, g.loz, g.dz, iz, g.nz, g.nx * g.ny, t_in);
+            const int pnx = g.nx + 2, pnxy = (g.nx + 2) * (g.ny + 2);
+            AxisWalk wx = setup_axis(Ax, dx, ix_, g.lox, g.dx, ix, 1, t_in);
+            AxisWalk wy = setup_axis(Ay, dy, iy_, g.loy, g.dy, iy, pnx, t_in);
+            AxisWalk wz = setup_axis(Az, dz, iz_, g.loz, g.dz, iz, pnxy, t_in);
             float tx = wx.t0, ty = wy.t0, tz = wz.t0;
             float cx = 0.0f, cy = 0.0f, cz = 0.0f;
-            int idx = (iz * g.ny + iy) * g.nx + ix;
+            int idx = (iz + 1) * pnxy + (iy + 1) * pnx + (ix + 1);
             int cur = __ldg(p.labels + idx);
             float t_run = t_in;
-            // Each pass steps at least one axis whose remaining count is > 0
-            // or leaves, so the loop ends after at most nx + ny + nz passes
-            // and idx never leaves the grid.
-            for (;;) {
+            // The padded volume has a one-voxel border labelled kBorder, so
+            // the walk ends when it steps into the border.  Each pass moves
+            // at least one index one voxel along the ray, so the border is
+            // reached within nx + ny + nz + 3 passes; the pass budget only
+            // guards against non-finite geometry.
+            bool open = true;
+            for (int budget = g.nx + g.ny + g.nz + 3; budget > 0; --budget) {
                 const float tn = fminf(tx, fminf(ty, tz));
-                if (tn >= t_out) break;
-                const bool sx = tx == tn, sy = ty == tn, sz = tz == tn;
-                if ((sx && wx.rem == 0) || (sy && wy.rem == 0) || (sz && wz.rem == 0)) {
-                    t_out = tn;
-                    break;
-                }
-                if (sx) { idx += wx.step; --wx.rem; cx += 1.0f; tx = fmaf(cx, wx.dt, wx.t0); }
-                if (sy) { idx += wy.step; --wy.rem; cy += 1.0f; ty = fmaf(cy, wy.dt, wy.t0); }
-                if (sz) { idx += wz.step; --wz.rem; cz += 1.0f; tz = fmaf(cz, wz.dt, wz.t0); }
+                if (tx == tn) { idx += wx.step; cx += 1.0f; tx = fmaf(cx, wx.dt, wx.t0); }
+                if (ty == tn) { idx += wy.step; cy += 1.0f; ty = fmaf(cy, wy.dt, wy.t0); }
+                if (tz == tn) { idx += wz.step; cz += 1.0f; tz = fmaf(cz, wz.dt, wz.t0); }
                 const int lab = __ldg(p.labels + idx);
                 if (lab != cur) {
                     add_run(L, cur, tn - t_run);
+                    if (lab == kBorder) { open = false; break; }
                     t_run = tn;
                     cur = lab;
                 }
             }
-            add_run(L, cur, t_out - t_run);
+            if (open) add_run(L, cur, t_out - t_run);
         }
     }
 
@@ -199,18 +194,30 @@ cudaError_t launch_project(const ProjParams &p, float *T, float *L_out, cudaStre
     return cudaGetLastError();
 }
 
-__global__ void k_check_labels(const uint8_t *__restrict__ lab, size_t n, int n_mat,
-                               unsigned int *bad)
+// Copy labels [nz][ny][nx] into the padded [nz + 2][ny + 2][nx + 2] layout
+// with a kBorder frame, flagging any label >= n_mat.
+__global__ void k_pad_labels(const uint8_t *__restrict__ lab, uint8_t *__restrict__ pad, int nx,
+                             int ny, int nz, int n_mat, unsigned int *bad)
 {
+    const size_t px = nx + 2, py = ny + 2, n = px * py * (size_t)(nz + 2);
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
-         i += (size_t)gridDim.x * blockDim.x)
-        if (lab[i] >= n_mat) atomicOr(bad, 1u);
+         i += (size_t)gridDim.x * blockDim.x) {
+        const int x = (int)(i % px) - 1;
+        const int y = (int)((i / px) % py) - 1;
+        const int z = (int)(i / (px * py)) - 1;
+        uint8_t v = kBorder;
+        if (x >= 0 && x < nx && y >= 0 && y < ny && z >= 0 && z < nz) {
+            v = lab[((size_t)z * ny + y) * nx + x];
+            if (v >= n_mat) atomicOr(bad, 1u);
+        }
+        pad[i] = v;
+    }
 }
 
-cudaError_t launch_check_labels(const uint8_t *labels, size_t n, int n_mat, unsigned int *bad,
-                                cudaStream_t s)
+cudaError_t launch_pad_labels(const uint8_t *labels, uint8_t *padded, int nx, int ny, int nz,
+                              int n_mat, unsigned int *bad, cudaStream_t s)
 {
-    k_check_labels<<<152 * 4, 256, 0, s>>>(labels, n, n_mat, bad);
+    k_pad_labels<<<152 * 4, 256, 0, s>>>(labels, padded, nx, ny, nz, n_mat, bad);
     return cudaGetLastError();
 }
 
