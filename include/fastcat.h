@@ -189,6 +189,29 @@ int fc_profile_enable(fc_handle *h, int enable);
  * Errors: FC_EINVAL, FC_ECUDA. */
 int fc_profile_read(fc_handle *h, double *ms, int64_t *launches);
 
+/* Allocation-free detector blur.  The paper has no counterpart: this entry
+ * point exists for callers that cannot allocate device memory while they
+ * run -- their device memory is owned by another allocator (for example a
+ * pool that reserved the whole GPU at start-up) or fixed by a budget that
+ * forbids allocation after initialisation.  It computes the same
+ * I = n0 (G_psf (x) T + spr G_scatter (x) T) as fc_project's FC_OUT_INTENSITY
+ * (same kernels), for T and I of n_img x n_v x n_u floats in device memory
+ * provided by the caller, without a handle, and calls no cudaMalloc,
+ * cudaFree or other allocating routine.  The two row-pass intermediates live
+ * in a file-scope device array of FC_STATIC_SCRATCH_FLOATS floats (32 MiB)
+ * that every GPU loading the library holds until the process exits; calls
+ * with 2 * n_img * n_v * n_u > FC_STATIC_SCRATCH_FLOATS fail with FC_EINVAL.
+ * The first call on a device looks up the array's device address (once per
+ * device, with that device current); make that first call before any stream
+ * capture.  Every call shares the array: calls whose kernels overlap on the
+ * GPU race on it, so order them (one stream, or events).  Runs on the current
+ * device and `stream`.  Errors: FC_EINVAL (null pointers, sizes, sigmas,
+ * spr < 0, n0 <= 0), FC_ECUDA. */
+#define FC_STATIC_SCRATCH_FLOATS (8u << 20)
+int fc_detector_blur_static(const float *T, float *I, int n_img, int n_v, int n_u,
+                            double psf_sigma_px, double scatter_sigma_px, double spr, double n0,
+                            void *stream);
+
 #ifdef __cplusplus
 }
 #endif

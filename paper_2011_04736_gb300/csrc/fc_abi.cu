@@ -62,6 +62,8 @@ void dfree(T *&p)
 
 }  // namespace
 
+void fc::set_last_error(const char *msg) { g_err = msg; }
+
 struct fc_handle {
     int device = 0;
     bool has_geom = false, has_phantom = false, has_spec = false, has_counts = false;

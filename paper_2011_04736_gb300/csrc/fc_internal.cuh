@@ -65,6 +65,9 @@ struct FdkParams {
 
 void fdk_row_range(const DevGeom &g, int *v_lo, int *v_hi);
 
+// Sets the message fc_last_error() returns on this thread.
+void set_last_error(const char *msg);
+
 // launchers (return cudaError_t of the launch)
 cudaError_t launch_project(const ProjParams &p, float *T, float *L_out, cudaStream_t s);
 cudaError_t launch_blur_rows(const BlurParams &p, const float *T, float *tp, float *ts,

@@ -25,7 +25,9 @@ FC_MAX_MATERIALS, FC_MAX_BINS = 8, 256
 # every entry point declared in include/fastcat.h
 ENTRY_POINTS = ("fc_create", "fc_destroy", "fc_last_error", "fc_set_geometry", "fc_set_phantom",
                 "fc_set_spectrum_detector", "fc_project", "fc_reconstruct", "fc_set_water_roi",
-                "fc_poisson", "fc_project_lengths", "fc_profile_enable", "fc_profile_read")
+                "fc_poisson", "fc_project_lengths", "fc_profile_enable", "fc_profile_read",
+                "fc_detector_blur_static")
+FC_STATIC_SCRATCH_FLOATS = 8 << 20
 FC_K_NAMES = ("project", "blur_rows", "blur_cols", "fdk_filter", "backproject", "hu", "lengths",
               "noise")
 
@@ -81,6 +83,8 @@ def load():
         "fc_project_lengths": (I, [P, I, I, P, P]),
         "fc_profile_enable": (I, [P, I]),
         "fc_profile_read": (I, [P, P, P]),
+        "fc_detector_blur_static": (I, [P, P, I, I, I, ctypes.c_double, ctypes.c_double,
+                                        ctypes.c_double, ctypes.c_double, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -203,6 +207,17 @@ def fc_profile_read(h):
     n = np.zeros(len(FC_K_NAMES), np.int64)
     _check(load().fc_profile_read(h, ms.ctypes.data, n.ctypes.data))
     return {k: (float(ms[i]), int(n[i])) for i, k in enumerate(FC_K_NAMES)}
+
+
+def fc_detector_blur_static(T, I, n_img, n_v, n_u, psf_sigma_px, scatter_sigma_px, spr, n0,
+                            stream=None):
+    """Allocation-free detector blur on caller-provided device tensors."""
+    tp, tw = _ptr(T)
+    ip, iw = _ptr(I)
+    if tw != FC_DEVICE or iw != FC_DEVICE:
+        raise ValueError("fc_detector_blur_static takes device tensors")
+    return _check(load().fc_detector_blur_static(tp, ip, n_img, n_v, n_u, psf_sigma_px,
+                                                 scatter_sigma_px, spr, n0, _stream(stream)))
 
 
 # ---------------------------------------------------------------- convenience
