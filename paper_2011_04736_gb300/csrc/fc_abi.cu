@@ -81,7 +81,7 @@ struct fc_handle {
     // device buffers
     float2 *d_trig = nullptr;
     uint8_t *d_labels = nullptr;   // caller layout [nz][ny][nx]
-    uint8_t *d_lpad = nullptr;     // padded with a border frame (projector input)
+    uint8_t *d_bricks = nullptr;   // 8x8x8 brick map: uniform label or mixed
     float *d_T = nullptr, *d_tp = nullptr, *d_ts = nullptr, *d_counts = nullptr, *d_filt = nullptr;
     double *d_vol = nullptr;
     float *d_hu = nullptr;
@@ -104,7 +104,7 @@ struct fc_handle {
     {
         dfree(d_trig);
         dfree(d_labels);
-        dfree(d_lpad);
+        dfree(d_bricks);
         dfree(d_T);
         dfree(d_tp);
         dfree(d_ts);
@@ -293,7 +293,7 @@ int fc_set_geometry(fc_handle *h, const fc_geometry *g)
     }
     if (!same_vol) {
         dfree(h->d_labels);
-        dfree(h->d_lpad);
+        dfree(h->d_bricks);
         h->has_phantom = false;
     }
     dfree(h->d_trig);
@@ -343,14 +343,14 @@ int fc_set_phantom(fc_handle *h, const uint8_t *labels, int n_mat, int where, vo
     DeviceGuard dgd(h->device);
     cudaStream_t s = (cudaStream_t)stream;
     if (!h->d_labels) FC_CK(cudaMalloc((void **)&h->d_labels, h->vol_elems));
-    if (!h->d_lpad)
-        FC_CK(cudaMalloc((void **)&h->d_lpad,
-                         (size_t)(h->g.nx + 2) * (h->g.ny + 2) * (h->g.nz + 2)));
+    if (!h->d_bricks)
+        FC_CK(cudaMalloc((void **)&h->d_bricks,
+                         (size_t)((h->g.nx + 7) / 8) * ((h->g.ny + 7) / 8) * ((h->g.nz + 7) / 8)));
     FC_CK(cudaMemcpyAsync(h->d_labels, labels, h->vol_elems,
                           where == FC_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, s));
     FC_CK(cudaMemsetAsync(h->d_flag, 0, sizeof(unsigned int), s));
-    FC_CK(fc::launch_pad_labels(h->d_labels, h->d_lpad, h->g.nx, h->g.ny, h->g.nz, n_mat,
-                                h->d_flag, s));
+    FC_CK(fc::launch_brick_map(h->d_labels, h->d_bricks, h->g.nx, h->g.ny, h->g.nz, n_mat,
+                               h->d_flag, s));
     unsigned int bad = 0;
     FC_CK(cudaMemcpyAsync(&bad, h->d_flag, sizeof(bad), cudaMemcpyDeviceToHost, s));
     FC_CK(cudaStreamSynchronize(s));
@@ -431,7 +431,8 @@ static int fill_proj_params(fc_handle *h, int a0, int na, fc::ProjParams *p)
     memset(p, 0, sizeof(*p));
     p->g = h->dg;
     p->trig = h->d_trig;
-    p->labels = h->d_lpad;
+    p->labels = h->d_labels;
+    p->bricks = h->d_bricks;
     p->angle0 = a0;
     p->n_angles_launch = na;
     {

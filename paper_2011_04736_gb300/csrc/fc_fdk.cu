@@ -234,9 +234,9 @@ cudaError_t launch_backproject(const FdkParams &p, const float *filt, double *vo
 {
     dim3 block(32, 8);
     // z values per thread: as many as possible (the per-angle column set-up
-    // is shared by them) while keeping about 24 resident warps per SM.
+    // is shared by them) while keeping about 48 resident warps per SM.
     const long cols = (long)p.g.nx * p.g.ny;
-    const long want = 152L * 768;
+    const long want = 152L * 1536;
     int zc = 8;
     while (zc > 1 && cols * ((p.g.nz + zc - 1) / zc) < want) --zc;
     {

@@ -11,7 +11,8 @@ namespace fc {
 constexpr int kMaxMat = FC_MAX_MATERIALS;
 constexpr int kMaxBins = FC_MAX_BINS;
 constexpr int kMaxTaps = 2 * 256 + 1;  // 2 * ceil(4 * FC_MAX_SIGMA_PX) + 1
-constexpr int kBorder = 255;           // label of the padding frame around the phantom
+constexpr int kBrick = 8;              // edge of the label bricks the projector skips
+constexpr int kMixed = 255;            // brick-map value of a brick with several labels
 
 // Geometry in the precision the kernels use (binary32), derived on the host
 // from the binary64 fc_geometry.
@@ -31,7 +32,8 @@ struct DevGeom {
 struct ProjParams {
     DevGeom g;
     const float2 *trig;     // [n_angles] (cos, sin) of each angle
-    const uint8_t *labels;  // padded [nz + 2][ny + 2][nx + 2], kBorder frame
+    const uint8_t *labels;  // [nz][ny][nx]
+    const uint8_t *bricks;  // [nz/8][ny/8][nx/8] (rounded up): uniform label or kMixed
     int angle0;             // absolute index of the first angle of the launch
     int n_angles_launch;
     int v_hit_lo, v_hit_hi; // detector rows whose rays can meet the voxel slab
@@ -82,7 +84,7 @@ cudaError_t launch_backproject(const FdkParams &p, const float *filt, double *vo
                                cudaStream_t s);
 cudaError_t launch_hu(const DevGeom &g, const double *vol, float *hu, double *partials,
                       float radius, int zcut, cudaStream_t s);
-cudaError_t launch_pad_labels(const uint8_t *labels, uint8_t *padded, int nx, int ny, int nz,
-                              int n_mat, unsigned int *bad, cudaStream_t s);
+cudaError_t launch_brick_map(const uint8_t *labels, uint8_t *bricks, int nx, int ny, int nz,
+                             int n_mat, unsigned int *bad, cudaStream_t s);
 
 }  // namespace fc

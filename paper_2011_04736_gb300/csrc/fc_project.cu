@@ -1,11 +1,14 @@
 // Polyenergetic cone-beam projector (paper Sec. II.F "Raytracing" and the
 // energy-weighting equation I_f = sum_E phi(E) eta(E) I(E)).
 //
-// One thread per detector pixel ray.  The ray is traversed voxel by voxel
-// (incremental Siddon / Amanatides-Woo order) and the path length inside
-// each material is accumulated run by run: a length is added only when the
-// material label changes, so binary32 rounding enters once per material
-// transition instead of once per voxel.  The per-material lengths stay in
+// One thread per detector pixel ray.  The ray is traversed in voxel order
+// (Siddon / Amanatides-Woo) on two levels: 8x8x8 bricks whose voxels all
+// carry one label are crossed in a single step, mixed bricks voxel by voxel.
+// Every plane crossing, coarse or fine, is t(i) = fma(i, pitch / d, (lo - A) / d)
+// for the plane's index i, so both levels agree bit for bit on brick faces.
+// The path length inside each material is accumulated run by run: a length
+// is added only when the label changes, so binary32 rounding enters once per
+// material transition instead of once per voxel.  The per-material lengths stay in
 // registers and feed the energy integral
 //     T = sum_E (w D)_E exp(-sum_m mu_m(E) L_m)        (w D normalised)
 // evaluated with exp2 and a compensated (Kahan) sum over the energy bins.
@@ -30,31 +33,11 @@ __device__ __forceinline__ void add_run(float (&L)[kMaxMat], int m, float len)
     for (int j = 0; j < kMaxMat; ++j) L[j] += (m == j) ? len : 0.0f;
 }
 
-struct AxisWalk {
-    float t0;    // first crossing
-    float dt;    // spacing of crossings
-    int step;    // index increment in the padded volume
-};
-
-__device__ __forceinline__ AxisWalk setup_axis(float A, float d, float inv_d, float lo, float vox,
-                                               int i, int stride, float t_in)
+// Crossing parameter of plane i of one axis (INFINITY if the ray is
+// parallel to that axis).
+__device__ __forceinline__ float plane_t(int i, float vs, float base, int sgn)
 {
-    AxisWalk w;
-    if (d > 0.0f) {
-        w.t0 = (lo + (float)(i + 1) * vox - A) * inv_d;
-        w.dt = vox * inv_d;
-        w.step = stride;
-    } else if (d < 0.0f) {
-        w.t0 = (lo + (float)i * vox - A) * inv_d;
-        w.dt = -vox * inv_d;
-        w.step = -stride;
-    } else {
-        w.t0 = INFINITY;
-        w.dt = 0.0f;
-        w.step = 0;
-    }
-    w.t0 = fmaxf(w.t0, t_in);
-    return w;
+    return sgn ? fmaf((float)i, vs, base) : INFINITY;
 }
 
 __device__ __forceinline__ int clampi(int v, int lo, int hi)
@@ -122,38 +105,105 @@ k_project(const __grid_constant__ ProjParams p, float *__restrict__ T, float *__
         hit = hit && t_in < t_out;
         if (hit) {
             const float px = fmaf(t_in, dx, Ax), py = fmaf(t_in, dy, Ay), pz = fmaf(t_in, dz, Az);
-            const int ix = clampi((int)floorf((px - g.lox) * g.idx), 0, g.nx - 1);
-            const int iy = clampi((int)floorf((py - g.loy) * g.idy), 0, g.ny - 1);
-            const int iz = clampi((int)floorf((pz - g.loz) * g.idz), 0, g.nz - 1);
-            const int pnx = g.nx + 2, pnxy = (g.nx + 2) * (g.ny + 2);
-            AxisWalk wx = setup_axis(Ax, dx, ix_, g.lox, g.dx, ix, 1, t_in);
-            AxisWalk wy = setup_axis(Ay, dy, iy_, g.loy, g.dy, iy, pnx, t_in);
-            AxisWalk wz = setup_axis(Az, dz, iz_, g.loz, g.dz, iz, pnxy, t_in);
-            float tx = wx.t0, ty = wy.t0, tz = wz.t0;
-            float cx = 0.0f, cy = 0.0f, cz = 0.0f;
-            int idx = (iz + 1) * pnxy + (iy + 1) * pnx + (ix + 1);
-            int cur = __ldg(p.labels + idx);
-            float t_run = t_in;
-            // The padded volume has a one-voxel border labelled kBorder, so
-            // the walk ends when it steps into the border.  Each pass moves
-            // at least one index one voxel along the ray, so the border is
-            // reached within nx + ny + nz + 3 passes; the pass budget only
-            // guards against non-finite geometry.
-            bool open = true;
-            for (int budget = g.nx + g.ny + g.nz + 3; budget > 0; --budget) {
-                const float tn = fminf(tx, fminf(ty, tz));
-                if (tx == tn) { idx += wx.step; cx += 1.0f; tx = fmaf(cx, wx.dt, wx.t0); }
-                if (ty == tn) { idx += wy.step; cy += 1.0f; ty = fmaf(cy, wy.dt, wy.t0); }
-                if (tz == tn) { idx += wz.step; cz += 1.0f; tz = fmaf(cz, wz.dt, wz.t0); }
-                const int lab = __ldg(p.labels + idx);
-                if (lab != cur) {
-                    add_run(L, cur, tn - t_run);
-                    if (lab == kBorder) { open = false; break; }
-                    t_run = tn;
-                    cur = lab;
+            const int nx = g.nx, ny = g.ny, nz = g.nz, nxy = g.nx * g.ny;
+            const int ix0 = clampi((int)floorf((px - g.lox) * g.idx), 0, nx - 1);
+            const int iy0 = clampi((int)floorf((py - g.loy) * g.idy), 0, ny - 1);
+            const int iz0 = clampi((int)floorf((pz - g.loz) * g.idz), 0, nz - 1);
+            const int sx = dx > 0.0f ? 1 : (dx < 0.0f ? -1 : 0);
+            const int sy = dy > 0.0f ? 1 : (dy < 0.0f ? -1 : 0);
+            const int sz = dz > 0.0f ? 1 : (dz < 0.0f ? -1 : 0);
+            const int ux = sx > 0, uy = sy > 0, uz = sz > 0;   // next plane = index + u
+            // t(i) = fma(i, v*, b*): v* = pitch / d, b* = (lo - A) / d
+            const float vx = g.dx * ix_, vy = g.dy * iy_, vz = g.dz * iz_;
+            const float bx_ = (g.lox - Ax) * ix_, by_ = (g.loy - Ay) * iy_, bz_ = (g.loz - Az) * iz_;
+            const int nbx = (nx + kBrick - 1) / kBrick, nby = (ny + kBrick - 1) / kBrick;
+            const int nbz = (nz + kBrick - 1) / kBrick;
+            int bx = ix0 / kBrick, by = iy0 / kBrick, bz = iz0 / kBrick;
+            // coarse crossing: far face of the current brick along the ray
+            float tcx = plane_t(ux ? min((bx + 1) * kBrick, nx) : bx * kBrick, vx, bx_, sx);
+            float tcy = plane_t(uy ? min((by + 1) * kBrick, ny) : by * kBrick, vy, by_, sy);
+            float tcz = plane_t(uz ? min((bz + 1) * kBrick, nz) : bz * kBrick, vz, bz_, sz);
+            int cur = __ldg(p.labels + (iz0 * ny + iy0) * nx + ix0);
+            float t_run = t_in, t_cur = t_in;
+            // Coarse passes: each advances one brick index by one step along
+            // the ray, so at most nbx + nby + nbz passes occur before an index
+            // leaves the grid.  Fine passes inside a brick: each advances one
+            // voxel index inside the brick (a step that would cross the brick
+            // face has t >= t_exit and ends the fine walk), at most 3 kBrick.
+            // The budgets only guard against non-finite geometry.
+            for (int cb = nbx + nby + nbz + 3; cb > 0; --cb) {
+                const float tmin = fminf(tcx, fminf(tcy, tcz));
+                const float t_exit = fmaxf(tmin, t_cur);
+                const int bl = __ldg(p.bricks + (bz * nby + by) * nbx + bx);
+                if (bl != kMixed) {
+                    if (bl != cur) {
+                        add_run(L, cur, t_cur - t_run);
+                        t_run = t_cur;
+                        cur = bl;
+                    }
+                } else if (tmin > t_cur) {
+                    // Fine walk through the brick over [t_cur, t_exit).  The
+                    // brick's faces are crossed at t >= t_exit = tmin (same
+                    // plane index, same formula as the coarse crossings), so
+                    // only interior planes are stepped and the voxel indices
+                    // stay inside the brick.  (A brick with tmin <= t_cur is
+                    // crossed over zero length and has nothing to add.)
+                    const float qx = fmaf(t_cur, dx, Ax), qy = fmaf(t_cur, dy, Ay);
+                    const float qz = fmaf(t_cur, dz, Az);
+                    int jx = clampi((int)floorf((qx - g.lox) * g.idx), bx * kBrick,
+                                    min((bx + 1) * kBrick, nx) - 1);
+                    int jy = clampi((int)floorf((qy - g.loy) * g.idy), by * kBrick,
+                                    min((by + 1) * kBrick, ny) - 1);
+                    int jz = clampi((int)floorf((qz - g.loz) * g.idz), bz * kBrick,
+                                    min((bz + 1) * kBrick, nz) - 1);
+                    float tfx = plane_t(jx + ux, vx, bx_, sx);
+                    float tfy = plane_t(jy + uy, vy, by_, sy);
+                    float tfz = plane_t(jz + uz, vz, bz_, sz);
+                    int id = jz * nxy + jy * nx + jx;
+                    int lab = __ldg(p.labels + id);
+                    if (lab != cur) {
+                        add_run(L, cur, t_cur - t_run);
+                        t_run = t_cur;
+                        cur = lab;
+                    }
+                    for (int fb = 3 * kBrick + 3; fb > 0; --fb) {
+                        const float tn = fminf(tfx, fminf(tfy, tfz));
+                        if (tn >= t_exit) break;
+                        if (tfx == tn) {
+                            jx += sx; id += sx; tfx = plane_t(jx + ux, vx, bx_, sx);
+                        } else if (tfy == tn) {
+                            jy += sy; id += sy * nx; tfy = plane_t(jy + uy, vy, by_, sy);
+                        } else {
+                            jz += sz; id += sz * nxy; tfz = plane_t(jz + uz, vz, bz_, sz);
+                        }
+                        lab = __ldg(p.labels + id);
+                        if (lab != cur) {
+                            const float tb = fmaxf(tn, t_run);
+                            add_run(L, cur, tb - t_run);
+                            t_run = tb;
+                            cur = lab;
+                        }
+                    }
                 }
+                // step to the next brick along the axis of the nearest face
+                t_cur = t_exit;
+                bool inside;
+                if (tcx == tmin) {
+                    bx += sx;
+                    inside = bx >= 0 && bx < nbx;
+                    tcx = plane_t(ux ? min((bx + 1) * kBrick, nx) : bx * kBrick, vx, bx_, sx);
+                } else if (tcy == tmin) {
+                    by += sy;
+                    inside = by >= 0 && by < nby;
+                    tcy = plane_t(uy ? min((by + 1) * kBrick, ny) : by * kBrick, vy, by_, sy);
+                } else {
+                    bz += sz;
+                    inside = bz >= 0 && bz < nbz;
+                    tcz = plane_t(uz ? min((bz + 1) * kBrick, nz) : bz * kBrick, vz, bz_, sz);
+                }
+                if (!inside) break;
             }
-            if (open) add_run(L, cur, t_out - t_run);
+            add_run(L, cur, t_cur - t_run);
         }
     }
 
@@ -194,30 +244,39 @@ cudaError_t launch_project(const ProjParams &p, float *T, float *L_out, cudaStre
     return cudaGetLastError();
 }
 
-// Copy labels [nz][ny][nx] into the padded [nz + 2][ny + 2][nx + 2] layout
-// with a kBorder frame, flagging any label >= n_mat.
-__global__ void k_pad_labels(const uint8_t *__restrict__ lab, uint8_t *__restrict__ pad, int nx,
-                             int ny, int nz, int n_mat, unsigned int *bad)
+// One thread per 8x8x8 brick: its single label, or kMixed; flags any label
+// >= n_mat.
+__global__ void k_brick_map(const uint8_t *__restrict__ lab, uint8_t *__restrict__ bricks, int nx,
+                            int ny, int nz, int n_mat, unsigned int *bad)
 {
-    const size_t px = nx + 2, py = ny + 2, n = px * py * (size_t)(nz + 2);
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
-         i += (size_t)gridDim.x * blockDim.x) {
-        const int x = (int)(i % px) - 1;
-        const int y = (int)((i / px) % py) - 1;
-        const int z = (int)(i / (px * py)) - 1;
-        uint8_t v = kBorder;
-        if (x >= 0 && x < nx && y >= 0 && y < ny && z >= 0 && z < nz) {
-            v = lab[((size_t)z * ny + y) * nx + x];
-            if (v >= n_mat) atomicOr(bad, 1u);
-        }
-        pad[i] = v;
+    const int nbx = (nx + kBrick - 1) / kBrick, nby = (ny + kBrick - 1) / kBrick;
+    const int nbz = (nz + kBrick - 1) / kBrick;
+    const int nb = nbx * nby * nbz;
+    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nb; b += gridDim.x * blockDim.x) {
+        const int bx = b % nbx, by = (b / nbx) % nby, bz = b / (nbx * nby);
+        const int x1 = min((bx + 1) * kBrick, nx), y1 = min((by + 1) * kBrick, ny);
+        const int z1 = min((bz + 1) * kBrick, nz);
+        const int first = lab[((size_t)(bz * kBrick) * ny + by * kBrick) * nx + bx * kBrick];
+        bool uniform = true, badlab = false;
+        for (int z = bz * kBrick; z < z1; ++z)
+            for (int y = by * kBrick; y < y1; ++y)
+                for (int x = bx * kBrick; x < x1; ++x) {
+                    const int v = lab[((size_t)z * ny + y) * nx + x];
+                    uniform = uniform && v == first;
+                    badlab = badlab || v >= n_mat;
+                }
+        if (badlab) atomicOr(bad, 1u);
+        bricks[b] = uniform ? (uint8_t)first : (uint8_t)kMixed;
     }
 }
 
-cudaError_t launch_pad_labels(const uint8_t *labels, uint8_t *padded, int nx, int ny, int nz,
-                              int n_mat, unsigned int *bad, cudaStream_t s)
+cudaError_t launch_brick_map(const uint8_t *labels, uint8_t *bricks, int nx, int ny, int nz,
+                             int n_mat, unsigned int *bad, cudaStream_t s)
 {
-    k_pad_labels<<<152 * 4, 256, 0, s>>>(labels, padded, nx, ny, nz, n_mat, bad);
+    const int nb = ((nx + kBrick - 1) / kBrick) * ((ny + kBrick - 1) / kBrick) *
+                   ((nz + kBrick - 1) / kBrick);
+    const int blocks = (nb + 127) / 128 < 152 * 8 ? (nb + 127) / 128 : 152 * 8;
+    k_brick_map<<<blocks, 128, 0, s>>>(labels, bricks, nx, ny, nz, n_mat, bad);
     return cudaGetLastError();
 }
 
