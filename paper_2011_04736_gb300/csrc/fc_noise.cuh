@@ -200,9 +200,27 @@ __device__ __forceinline__ bool poisson_begin(float lam, uint32_t iu, uint32_t i
     return false;
 }
 
-// One PTRS attempt.  Returns true with the count in r when the draw is
-// decided (accepted, or the 64-attempt limit reached).
-__device__ __forceinline__ bool ptrs_attempt(Ptrs &s, float &r)
+// Moves to the next attempt after a rejection; returns true with
+// r = floor(lam + 1/2) when the 64-attempt limit is reached.
+__device__ __forceinline__ bool ptrs_advance(Ptrs &s, float &r)
+{
+    if (s.h) {
+        s.h = 0;
+        if (++s.j == 32u) { r = floorf(FADD(s.lam, 0.5f)); return true; }
+    } else {
+        s.h = 1;
+    }
+    return false;
+}
+
+enum { kDone = 0, kReject = 1, kPending = 2 };
+
+// First part of one PTRS attempt: the squeeze and the quick rejections.
+// kDone: decided (r holds the count); kReject: rejected and the state moved
+// to the next attempt; kPending: the final acceptance test must be made with
+// ptrs_final(kf, us, V) before anything else happens to this draw.
+__device__ __forceinline__ int ptrs_quick(Ptrs &s, float &r, float &kf_out, float &us_out,
+                                          float &V_out)
 {
     if (s.h == 0) s.w = philox4x32_10(make_uint4(s.iu, s.iv, s.k, s.j), s.key);
     const float U = FSUB(unif(s.h ? s.w.z : s.w.x), 0.5f);
@@ -215,30 +233,43 @@ __device__ __forceinline__ bool ptrs_attempt(Ptrs &s, float &r)
     t = FADD(t, s.lam);
     t = FADD(t, 0.43f);
     const float kf = floorf(t);
-    if (us >= 0.07f && V <= s.vr) { r = kf; return true; }
-    if (!(kf < 0.0f || (us < 0.013f && V > us))) {
-        if (!s.have_slow) {
-            s.loglam = log_f32(s.lam);
-            float ia = FSUB(s.b, 3.4f);
-            ia = FDIV(1.1328f, ia);
-            s.invalpha = FADD(1.1239f, ia);
-            s.have_slow = true;
-        }
-        float den = FMUL(us, us);
-        den = FDIV(s.a, den);
-        den = FADD(den, s.b);
-        float q = FMUL(V, s.invalpha);
-        q = FDIV(q, den);
-        const float lhs = log_f32(q);
-        if (lhs <= log_pmf(kf, s.lam, s.loglam)) { r = kf; return true; }
+    if (us >= 0.07f && V <= s.vr) { r = kf; return kDone; }
+    if (kf < 0.0f || (us < 0.013f && V > us)) return ptrs_advance(s, r) ? kDone : kReject;
+    kf_out = kf;
+    us_out = us;
+    V_out = V;
+    return kPending;
+}
+
+// Final acceptance test of a pending attempt: log(V / (alpha (a / us^2 + b)))
+// against log P(k; lam).  Returns true when the draw is decided.
+__device__ __forceinline__ bool ptrs_final(Ptrs &s, float kf, float us, float V, float &r)
+{
+    if (!s.have_slow) {
+        s.loglam = log_f32(s.lam);
+        float ia = FSUB(s.b, 3.4f);
+        ia = FDIV(1.1328f, ia);
+        s.invalpha = FADD(1.1239f, ia);
+        s.have_slow = true;
     }
-    if (s.h) {
-        s.h = 0;
-        if (++s.j == 32u) { r = floorf(FADD(s.lam, 0.5f)); return true; }
-    } else {
-        s.h = 1;
-    }
-    return false;
+    float den = FMUL(us, us);
+    den = FDIV(s.a, den);
+    den = FADD(den, s.b);
+    float q = FMUL(V, s.invalpha);
+    q = FDIV(q, den);
+    const float lhs = log_f32(q);
+    if (lhs <= log_pmf(kf, s.lam, s.loglam)) { r = kf; return true; }
+    return ptrs_advance(s, r);
+}
+
+// One complete PTRS attempt; returns true when the draw is decided.
+__device__ __forceinline__ bool ptrs_attempt(Ptrs &s, float &r)
+{
+    float kf, us, V;
+    const int q = ptrs_quick(s, r, kf, us, V);
+    if (q == kDone) return true;
+    if (q == kReject) return false;
+    return ptrs_final(s, kf, us, V, r);
 }
 
 // Complete draw for pixel (iu, iv) of projection k.
