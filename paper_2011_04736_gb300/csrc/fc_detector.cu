@@ -239,11 +239,9 @@ cudaError_t launch_blur_cols(const BlurParams &p, const float *tp, const float *
 // rejection draw takes a variable number of attempts, so instead of
 // finishing one pixel before the next (where every warp waits for its
 // slowest lane at each pixel), a lane that finishes a pixel starts its next
-// one in the same loop pass.  The final acceptance test of an attempt (three
-// logs and a series, needed by ~14% of attempts) is deferred: a lane that
-// needs it waits, and the warp runs the test for all waiting lanes together
-// once they are at least half of the lanes still drawing.  The draws are
-// exactly those of noise::poisson.  lam and out may alias.
+// one in the same loop pass; a warp then runs about kPer * E[attempts] passes
+// plus the spread of the per-lane totals.  The draws themselves are exactly
+// those of noise::poisson.  lam and out may alias.
 namespace {
 constexpr int kPer = 8;
 }
@@ -252,15 +250,13 @@ __global__ void __launch_bounds__(256)
 k_poisson(const float *lam, float *out, int n_v, int n_u, int angle0, uint64_t seed)
 {
     const int iv = blockIdx.y * blockDim.y + threadIdx.y;
-    if (iv >= n_v) return;  // whole warp: blockDim.x == 32
+    if (iv >= n_v) return;
     const int k = blockIdx.z;
     const size_t row = ((size_t)k * n_v + iv) * n_u;
     const int u_base = blockIdx.x * (32 * kPer) + threadIdx.x;
     const uint32_t kabs = (uint32_t)(angle0 + k);
     noise::Ptrs st;
     int s = 0, cur = -1;
-    bool pend = false;
-    float pk = 0.0f, pus = 0.0f, pV = 0.0f;
     for (;;) {
         while (cur < 0 && s < kPer) {
             const int iu = u_base + 32 * s;
@@ -273,31 +269,12 @@ k_poisson(const float *lam, float *out, int n_v, int n_u, int angle0, uint64_t s
                 cur = iu;
             }
         }
-        const unsigned busy = __ballot_sync(0xffffffffu, cur >= 0);
-        if (busy == 0u) break;
-        if (cur >= 0 && !pend) {
-            float r;
-            const int q = noise::ptrs_quick(st, r, pk, pus, pV);
-            if (q == noise::kDone) {
-                out[row + cur] = r;
-                cur = -1;
-                ++s;
-            } else if (q == noise::kPending) {
-                pend = true;
-            }
-        }
-        const unsigned waiting = __ballot_sync(0xffffffffu, pend);
-        const unsigned drawing = __ballot_sync(0xffffffffu, cur >= 0);
-        if (waiting != 0u && (2 * __popc(waiting) >= __popc(drawing) || waiting == drawing)) {
-            if (pend) {
-                float r;
-                if (noise::ptrs_final(st, pk, pus, pV, r)) {
-                    out[row + cur] = r;
-                    cur = -1;
-                    ++s;
-                }
-                pend = false;
-            }
+        if (cur < 0) break;
+        float r;
+        if (noise::ptrs_attempt(st, r)) {
+            out[row + cur] = r;
+            cur = -1;
+            ++s;
         }
     }
 }
