@@ -177,7 +177,10 @@ int fc_project_lengths(fc_handle *h, int angle_begin, int angle_count, float *L,
 #define FC_K_HU          5  /* water-region mean and HU (two kernels) */
 #define FC_K_LENGTHS     6  /* path-length emission (fc_project_lengths) */
 #define FC_K_NOISE       7  /* Poisson noise */
-#define FC_K_COUNT       8
+#define FC_K_SURROGATE_EVAL  8  /* surrogate inference (fc_surrogate_eval) */
+#define FC_K_SURROGATE_TRAIN 9  /* surrogate training steps (4 kernels per step) */
+#define FC_K_ENERGY_SUM     10  /* exact energy sum from path lengths */
+#define FC_K_COUNT          11
 
 /* Enable (1) or disable (0) tracing; enabling discards pending records.
  * Errors: FC_EINVAL. */
@@ -188,6 +191,66 @@ int fc_profile_enable(fc_handle *h, int enable);
  * to launches[FC_K_COUNT] (either may be NULL), and reset the totals.
  * Errors: FC_EINVAL, FC_ECUDA. */
 int fc_profile_read(fc_handle *h, double *ms, int64_t *launches);
+
+/* ---- Learned surrogate of the energy integral ----
+ * The projector's energy loop evaluates, per ray, the I_f equation of
+ * Sec. II.F: T = sum_E (w D)_E exp(-sum_m mu_m(E) L_m) / sum_E (w D)_E.  The
+ * surrogate approximates ln T from the per-material path lengths L with
+ *   ln T ~ -sum_m mubar_m L_m + MLP(L * scale),
+ *   mubar_m = sum_E (w D)_E mu_m(E) / sum_E (w D)_E,
+ *   MLP 8 -> 128 -> 128 -> 128 -> 1, SiLU (sigma via tanh), bf16 weights and
+ *   activations on the tensor cores with f32 accumulation.
+ * Path lengths are float [n][n_mat] and ln T float [n], in device memory.
+ * The handle's spectrum (fc_set_spectrum_detector) must be set first.
+ *
+ * Parameter state (fc_surrogate_get/set), FC_SURROGATE_STATE floats:
+ *   [0, 34305): W1[128][8], b1[128], W2[128][128], b2, W3[128][128], b3,
+ *               w4[128], b4 (fp32 master copies; W[out][in]);
+ *   then scale[8], mubar[8], box[8] (inputs are L * scale; rays with any
+ *   L_m > box_m are evaluated exactly); then Adam first and second moments
+ *   (34305 each) and the Adam step count. */
+#define FC_SURROGATE_PARAMS 34305
+#define FC_SURROGATE_STATE  (34305 + 24 + 2 * 34305 + 1)
+
+/* Initialise the surrogate with seeded random weights (uniform, scaled by
+ * fan-in), mubar from the current spectrum, unit scale and an unbounded box.
+ * Errors: FC_ESTATE (no spectrum), FC_ENOMEM, FC_ECUDA. */
+int fc_surrogate_init(fc_handle *h, uint64_t seed);
+
+/* Train with Adam (beta 0.9 / 0.999, eps 1e-8) on the mean squared error of
+ * ln T for `steps` steps of `batch` samples drawn with replacement from the
+ * n pairs (L, lnT) by a seeded hash; learning rate lr with cosine decay over
+ * the call.  The first call after fc_surrogate_init fixes scale = 1 / max L
+ * and box = max L per material from this data.  loss_hist (host, may be
+ * NULL) receives the per-step batch MSE.  batch must be a positive multiple
+ * of 128.  Errors: FC_ESTATE, FC_EINVAL, FC_ETIMEOUT (a bounded tensor-core
+ * wait expired), FC_ENOMEM, FC_ECUDA. */
+int fc_surrogate_train(fc_handle *h, const float *L, const float *lnT, int64_t n, int steps,
+                       int batch, float lr, uint64_t seed, float *loss_hist, void *stream);
+
+/* Gradient of the mean squared error over exactly the first n samples with
+ * respect to the FC_SURROGATE_PARAMS parameters, written to grad (host), and
+ * the loss to *loss (host, may be NULL); no update.  n must be a multiple of
+ * 8.  Errors as fc_surrogate_train. */
+int fc_surrogate_grad(fc_handle *h, const float *L, const float *lnT, int64_t n, float *grad,
+                      float *loss, void *stream);
+
+/* Copy the full state (FC_SURROGATE_STATE floats, host) out of / into the
+ * handle (checkpoint and resume).  Errors: FC_EINVAL, FC_ESTATE, FC_ECUDA. */
+int fc_surrogate_get(fc_handle *h, float *state);
+int fc_surrogate_set(fc_handle *h, const float *state);
+
+/* ln T of n rays from their path lengths by the surrogate, falling back to
+ * the exact energy sum for rays outside the training box; *n_fallback (host,
+ * may be NULL; non-NULL synchronises the stream) receives how many fell
+ * back.  Errors: FC_ESTATE, FC_EINVAL, FC_ETIMEOUT, FC_ECUDA. */
+int fc_surrogate_eval(fc_handle *h, const float *L, int64_t n, float *lnT, int64_t *n_fallback,
+                      void *stream);
+
+/* ln T of n rays from their path lengths by the exact energy sum (the
+ * projector's epilogue as a separate pass).  Errors: FC_ESTATE, FC_EINVAL,
+ * FC_ECUDA. */
+int fc_energy_sum_lengths(fc_handle *h, const float *L, int64_t n, float *lnT, void *stream);
 
 /* Allocation-free detector blur.  The paper has no counterpart: this entry
  * point exists for callers that cannot allocate device memory while they

@@ -99,6 +99,19 @@ struct fc_handle {
     std::vector<cudaEvent_t> pool;
     double prof_ms[FC_K_COUNT] = {0};
     int64_t prof_n[FC_K_COUNT] = {0};
+    // learned surrogate of the energy integral
+    bool has_sur = false, sur_fitted = false;
+    int sur_step = 0;
+    float *d_P = nullptr, *d_m1 = nullptr, *d_m2 = nullptr, *d_grad = nullptr;
+    __nv_bfloat16 *d_W1b = nullptr, *d_W2b = nullptr, *d_W3b = nullptr, *d_W2Tb = nullptr,
+                  *d_W3Tb = nullptr;
+    fc::MlpWork work{};
+    int work_B = 0;
+    void *work_mem = nullptr;
+    int *d_err = nullptr;
+    unsigned int *d_cnt = nullptr;
+    float *d_loss = nullptr;
+    int loss_cap = 0;
 
     void free_all()
     {
@@ -121,6 +134,20 @@ struct fc_handle {
         pending.clear();
         for (auto e : pool) cudaEventDestroy(e);
         pool.clear();
+        dfree(d_P);
+        dfree(d_m1);
+        dfree(d_m2);
+        dfree(d_grad);
+        dfree(d_W1b);
+        dfree(d_W2b);
+        dfree(d_W3b);
+        dfree(d_W2Tb);
+        dfree(d_W3Tb);
+        if (work_mem) cudaFree(work_mem);
+        work_mem = nullptr;
+        dfree(d_err);
+        dfree(d_cnt);
+        dfree(d_loss);
     }
 };
 
@@ -628,6 +655,331 @@ int fc_profile_read(fc_handle *h, double *ms, int64_t *launches)
         h->prof_ms[i] = 0.0;
         h->prof_n[i] = 0;
     }
+    return FC_OK;
+}
+
+static_assert(fc::kMlpParams == FC_SURROGATE_PARAMS, "surrogate parameter count");
+static_assert(fc::kMlpPacked + 2 * fc::kMlpParams + 1 == FC_SURROGATE_STATE, "surrogate state size");
+
+static void fill_sur_params(fc_handle *h, fc::SurrogateParams *p)
+{
+    memset(p, 0, sizeof(*p));
+    p->W1b = h->d_W1b;
+    p->W2b = h->d_W2b;
+    p->W3b = h->d_W3b;
+    p->W2Tb = h->d_W2Tb;
+    p->W3Tb = h->d_W3Tb;
+    p->P = h->d_P;
+    p->n_mat = h->n_mat;
+    p->n_e = h->n_e;
+    for (int e = 0; e < h->n_e; ++e) {
+        p->wd[e] = h->wd[e];
+        for (int m = 0; m < fc::kMaxMat; ++m) p->mu2[e][m] = h->mu2[(size_t)e * fc::kMaxMat + m];
+    }
+}
+
+// Upload a packed parameter vector and rebuild the bf16 operand copies.
+static int sur_upload(fc_handle *h, const float *packed)
+{
+    using fc::kMlpHidden;
+    const int H = kMlpHidden;
+    std::vector<__nv_bfloat16> w1((size_t)H * 16), w2((size_t)H * H), w3((size_t)H * H),
+        w2t((size_t)H * H), w3t((size_t)H * H);
+    for (int o = 0; o < H; ++o)
+        for (int i = 0; i < 16; ++i)
+            w1[(size_t)o * 16 + i] = __float2bfloat16(i < fc::kMlpIn ? packed[fc::kOffW1 + o * fc::kMlpIn + i] : 0.0f);
+    for (int o = 0; o < H; ++o)
+        for (int i = 0; i < H; ++i) {
+            w2[(size_t)o * H + i] = w2t[(size_t)i * H + o] = __float2bfloat16(packed[fc::kOffW2 + o * H + i]);
+            w3[(size_t)o * H + i] = w3t[(size_t)i * H + o] = __float2bfloat16(packed[fc::kOffW3 + o * H + i]);
+        }
+    FC_CK(cudaMemcpy(h->d_P, packed, sizeof(float) * fc::kMlpPacked, cudaMemcpyHostToDevice));
+    FC_CK(cudaMemcpy(h->d_W1b, w1.data(), w1.size() * 2, cudaMemcpyHostToDevice));
+    FC_CK(cudaMemcpy(h->d_W2b, w2.data(), w2.size() * 2, cudaMemcpyHostToDevice));
+    FC_CK(cudaMemcpy(h->d_W3b, w3.data(), w3.size() * 2, cudaMemcpyHostToDevice));
+    FC_CK(cudaMemcpy(h->d_W2Tb, w2t.data(), w2t.size() * 2, cudaMemcpyHostToDevice));
+    FC_CK(cudaMemcpy(h->d_W3Tb, w3t.data(), w3t.size() * 2, cudaMemcpyHostToDevice));
+    return FC_OK;
+}
+
+static int sur_alloc(fc_handle *h)
+{
+    if (h->d_P) return FC_OK;
+    const int H = fc::kMlpHidden;
+    FC_CK(cudaMalloc((void **)&h->d_P, sizeof(float) * fc::kMlpPacked));
+    FC_CK(cudaMalloc((void **)&h->d_m1, sizeof(float) * fc::kMlpParams));
+    FC_CK(cudaMalloc((void **)&h->d_m2, sizeof(float) * fc::kMlpParams));
+    FC_CK(cudaMalloc((void **)&h->d_grad, sizeof(float) * fc::kMlpParams));
+    FC_CK(cudaMalloc((void **)&h->d_W1b, 2 * H * 16));
+    FC_CK(cudaMalloc((void **)&h->d_W2b, 2 * H * H));
+    FC_CK(cudaMalloc((void **)&h->d_W3b, 2 * H * H));
+    FC_CK(cudaMalloc((void **)&h->d_W2Tb, 2 * H * H));
+    FC_CK(cudaMalloc((void **)&h->d_W3Tb, 2 * H * H));
+    FC_CK(cudaMalloc((void **)&h->d_err, sizeof(int)));
+    FC_CK(cudaMalloc((void **)&h->d_cnt, sizeof(unsigned int) * 16));
+    FC_CK(cudaMemset(h->d_err, 0, sizeof(int)));
+    return FC_OK;
+}
+
+static uint64_t splitmix64(uint64_t &s)
+{
+    uint64_t z = (s += 0x9E3779B97F4A7C15ull);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+int fc_surrogate_init(fc_handle *h, uint64_t seed)
+{
+    if (!h) return fail(FC_EINVAL, "fc_surrogate_init: null handle");
+    if (!h->has_spec) return fail(FC_ESTATE, "fc_surrogate_init: set the spectrum first");
+    DeviceGuard dgd(h->device);
+    int rc = sur_alloc(h);
+    if (rc) return rc;
+    const int H = fc::kMlpHidden;
+    std::vector<float> P(fc::kMlpPacked, 0.0f);
+    uint64_t st = seed;
+    auto unif = [&](double a) {
+        return (float)(a * (2.0 * ((splitmix64(st) >> 11) * (1.0 / 9007199254740992.0)) - 1.0));
+    };
+    for (int i = 0; i < H * fc::kMlpIn; ++i) P[fc::kOffW1 + i] = unif(sqrt(3.0 / fc::kMlpIn));
+    for (int i = 0; i < H * H; ++i) P[fc::kOffW2 + i] = unif(sqrt(3.0 / H));
+    for (int i = 0; i < H * H; ++i) P[fc::kOffW3 + i] = unif(sqrt(3.0 / H));
+    for (int i = 0; i < H; ++i) P[fc::kOffW4 + i] = unif(0.1 * sqrt(3.0 / H));
+    const double log2e = 1.4426950408889634;
+    for (int m = 0; m < fc::kMaxMat; ++m) {
+        double mb = 0.0;
+        for (int e = 0; e < h->n_e; ++e) mb += (double)h->wd[e] * h->mu2[(size_t)e * fc::kMaxMat + m] / log2e;
+        P[fc::kOffScale + m] = 1.0f;
+        P[fc::kOffMubar + m] = (float)mb;
+        P[fc::kOffBox + m] = INFINITY;
+    }
+    rc = sur_upload(h, P.data());
+    if (rc) return rc;
+    FC_CK(cudaMemset(h->d_m1, 0, sizeof(float) * fc::kMlpParams));
+    FC_CK(cudaMemset(h->d_m2, 0, sizeof(float) * fc::kMlpParams));
+    h->sur_step = 0;
+    h->has_sur = true;
+    h->sur_fitted = false;
+    return FC_OK;
+}
+
+static int sur_work(fc_handle *h, int B)
+{
+    if (h->work_mem && h->work_B == B) return FC_OK;
+    if (h->work_mem) cudaFree(h->work_mem);
+    h->work_mem = nullptr;
+    const int H = fc::kMlpHidden;
+    const int n_chunks = (B + fc::kWgradChunk - 1) / fc::kWgradChunk;
+    const size_t nb = (size_t)B;
+    const size_t bytes = 2 * (16 * nb + 6 * (size_t)H * nb + 16 * nb) +
+                         4 * (4 * (size_t)n_chunks * H * H + 4 * (size_t)n_chunks * H + n_chunks) +
+                         16 * 256;  // each of the 11 pieces is rounded up to 256 bytes
+    FC_CK(cudaMalloc(&h->work_mem, bytes));
+    FC_CK(cudaMemset(h->work_mem, 0, bytes));
+    char *q = (char *)h->work_mem;
+    auto take = [&](size_t b) { char *r = q; q += (b + 255) / 256 * 256; return r; };
+    fc::MlpWork &w = h->work;
+    w.xt = (__nv_bfloat16 *)take(2 * 16 * nb);
+    w.h1t = (__nv_bfloat16 *)take(2 * H * nb);
+    w.h2t = (__nv_bfloat16 *)take(2 * H * nb);
+    w.h3t = (__nv_bfloat16 *)take(2 * H * nb);
+    w.dz1t = (__nv_bfloat16 *)take(2 * H * nb);
+    w.dz2t = (__nv_bfloat16 *)take(2 * H * nb);
+    w.dz3t = (__nv_bfloat16 *)take(2 * H * nb);
+    w.g = (__nv_bfloat16 *)take(2 * 16 * nb);
+    w.part = (float *)take(4 * 4 * (size_t)n_chunks * H * H);
+    w.rsum = (float *)take(4 * 4 * (size_t)n_chunks * H);
+    w.gsum = (float *)take(4 * (size_t)n_chunks);
+    h->work_B = B;
+    return FC_OK;
+}
+
+static int sur_check_data(fc_handle *h, const char *fn, const float *L, const float *y,
+                          bool need_y, int64_t n)
+{
+    if (!h) return fail(FC_EINVAL, "%s: null handle", fn);
+    if (!L || (need_y && !y)) return fail(FC_EINVAL, "%s: null data", fn);
+    if (n <= 0) return fail(FC_EINVAL, "%s: n must be positive", fn);
+    if (!h->has_sur) return fail(FC_ESTATE, "%s: call fc_surrogate_init first", fn);
+    return FC_OK;
+}
+
+// Per-material maximum of the training path lengths -> input scale and the
+// box outside which evaluation falls back to the exact sum (first fit only).
+static int sur_fit_box(fc_handle *h, const float *L, int64_t n, cudaStream_t s)
+{
+    if (h->sur_fitted) return FC_OK;
+    FC_CK(cudaMemsetAsync(h->d_cnt, 0, sizeof(unsigned int) * 16, s));
+    FC_CK(fc::launch_mlp_lmax(L, n, h->n_mat, h->d_cnt, s));
+    unsigned int mx[fc::kMaxMat] = {0};
+    FC_CK(cudaMemcpyAsync(mx, h->d_cnt, sizeof(mx), cudaMemcpyDeviceToHost, s));
+    FC_CK(cudaStreamSynchronize(s));
+    float tail[2 * fc::kMaxMat];
+    for (int m = 0; m < fc::kMaxMat; ++m) {
+        float v;
+        memcpy(&v, &mx[m], 4);
+        if (m >= h->n_mat) v = 0.0f;
+        tail[m] = (float)(1.0 / (v > 1e-3f ? v : 1e-3f));         // scale
+        tail[fc::kMaxMat + m] = m < h->n_mat ? v : 0.0f;           // box
+    }
+    FC_CK(cudaMemcpyAsync(h->d_P + fc::kOffScale, tail, sizeof(float) * fc::kMaxMat,
+                          cudaMemcpyHostToDevice, s));
+    FC_CK(cudaMemcpyAsync(h->d_P + fc::kOffBox, tail + fc::kMaxMat, sizeof(float) * fc::kMaxMat,
+                          cudaMemcpyHostToDevice, s));
+    FC_CK(cudaStreamSynchronize(s));
+    h->sur_fitted = true;
+    return FC_OK;
+}
+
+static int sur_read_err(fc_handle *h, cudaStream_t s, const char *fn)
+{
+    int err = 0;
+    FC_CK(cudaMemcpyAsync(&err, h->d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    FC_CK(cudaStreamSynchronize(s));
+    if (err) {
+        FC_CK(cudaMemset(h->d_err, 0, sizeof(int)));
+        return fail(FC_ETIMEOUT, "%s: a tensor-core wait exceeded its bound", fn);
+    }
+    return FC_OK;
+}
+
+int fc_surrogate_train(fc_handle *h, const float *L, const float *lnT, int64_t n, int steps,
+                       int batch, float lr, uint64_t seed, float *loss_hist, void *stream)
+{
+    int rc = sur_check_data(h, "fc_surrogate_train", L, lnT, true, n);
+    if (rc) return rc;
+    if (steps < 0 || batch <= 0 || batch % 128 != 0 || !(lr > 0.0f))
+        return fail(FC_EINVAL, "fc_surrogate_train: need steps >= 0, batch a positive multiple of 128, lr > 0");
+    DeviceGuard dgd(h->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    rc = sur_fit_box(h, L, n, s);
+    if (rc) return rc;
+    rc = sur_work(h, batch);
+    if (rc) return rc;
+    if (h->loss_cap < steps) {
+        dfree(h->d_loss);
+        FC_CK(cudaMalloc((void **)&h->d_loss, sizeof(float) * (steps > 0 ? steps : 1)));
+        h->loss_cap = steps;
+    }
+    if (steps > 0) FC_CK(cudaMemsetAsync(h->d_loss, 0, sizeof(float) * steps, s));
+    fc::SurrogateParams p;
+    fill_sur_params(h, &p);
+    Trace t(h, FC_K_SURROGATE_TRAIN, 4 * steps, s);
+    for (int k = 0; k < steps; ++k) {
+        const int tglob = ++h->sur_step;
+        const float lr_k = (float)(lr * 0.5 * (1.0 + cos(M_PI * k / (double)steps)));
+        const float bc1 = (float)(1.0 - pow(0.9, tglob)), bc2 = (float)(1.0 - pow(0.999, tglob));
+        FC_CK(fc::launch_mlp_step(p, L, lnT, n, batch, 1, seed, tglob, h->work, h->d_loss + k,
+                                  h->d_err, h->d_P, h->d_m1, h->d_m2, lr_k, bc1, bc2, nullptr,
+                                  h->d_W1b, h->d_W2b, h->d_W3b, h->d_W2Tb, h->d_W3Tb, s));
+    }
+    t.end();
+    rc = sur_read_err(h, s, "fc_surrogate_train");
+    if (rc) return rc;
+    if (loss_hist && steps > 0) {
+        FC_CK(cudaMemcpyAsync(loss_hist, h->d_loss, sizeof(float) * steps, cudaMemcpyDeviceToHost, s));
+        FC_CK(cudaStreamSynchronize(s));
+        for (int k = 0; k < steps; ++k) loss_hist[k] /= (float)batch;
+    }
+    return FC_OK;
+}
+
+int fc_surrogate_grad(fc_handle *h, const float *L, const float *lnT, int64_t n, float *grad,
+                      float *loss, void *stream)
+{
+    int rc = sur_check_data(h, "fc_surrogate_grad", L, lnT, true, n);
+    if (rc) return rc;
+    if (!grad || n % 8 != 0 || n > (1 << 24))
+        return fail(FC_EINVAL, "fc_surrogate_grad: need grad and n a multiple of 8 (<= 2^24)");
+    DeviceGuard dgd(h->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    rc = sur_work(h, (int)n);
+    if (rc) return rc;
+    if (h->loss_cap < 1) {
+        dfree(h->d_loss);
+        FC_CK(cudaMalloc((void **)&h->d_loss, sizeof(float)));
+        h->loss_cap = 1;
+    }
+    FC_CK(cudaMemsetAsync(h->d_loss, 0, sizeof(float), s));
+    fc::SurrogateParams p;
+    fill_sur_params(h, &p);
+    FC_CK(fc::launch_mlp_step(p, L, lnT, n, (int)n, 0, 0, 0, h->work, h->d_loss, h->d_err, h->d_P,
+                              h->d_m1, h->d_m2, 0.0f, 1.0f, 1.0f, h->d_grad, h->d_W1b, h->d_W2b,
+                              h->d_W3b, h->d_W2Tb, h->d_W3Tb, s));
+    FC_CK(cudaMemcpyAsync(grad, h->d_grad, sizeof(float) * fc::kMlpParams, cudaMemcpyDeviceToHost, s));
+    if (loss) FC_CK(cudaMemcpyAsync(loss, h->d_loss, sizeof(float), cudaMemcpyDeviceToHost, s));
+    FC_CK(cudaStreamSynchronize(s));
+    if (loss) *loss /= (float)n;
+    return sur_read_err(h, s, "fc_surrogate_grad");
+}
+
+int fc_surrogate_get(fc_handle *h, float *state)
+{
+    if (!h || !state) return fail(FC_EINVAL, "fc_surrogate_get: null argument");
+    if (!h->has_sur) return fail(FC_ESTATE, "fc_surrogate_get: no surrogate");
+    DeviceGuard dgd(h->device);
+    FC_CK(cudaMemcpy(state, h->d_P, sizeof(float) * fc::kMlpPacked, cudaMemcpyDeviceToHost));
+    FC_CK(cudaMemcpy(state + fc::kMlpPacked, h->d_m1, sizeof(float) * fc::kMlpParams, cudaMemcpyDeviceToHost));
+    FC_CK(cudaMemcpy(state + fc::kMlpPacked + fc::kMlpParams, h->d_m2, sizeof(float) * fc::kMlpParams,
+                     cudaMemcpyDeviceToHost));
+    state[fc::kMlpPacked + 2 * fc::kMlpParams] = (float)h->sur_step;
+    return FC_OK;
+}
+
+int fc_surrogate_set(fc_handle *h, const float *state)
+{
+    if (!h || !state) return fail(FC_EINVAL, "fc_surrogate_set: null argument");
+    if (!h->has_spec) return fail(FC_ESTATE, "fc_surrogate_set: set the spectrum first");
+    DeviceGuard dgd(h->device);
+    int rc = sur_alloc(h);
+    if (rc) return rc;
+    rc = sur_upload(h, state);
+    if (rc) return rc;
+    FC_CK(cudaMemcpy(h->d_m1, state + fc::kMlpPacked, sizeof(float) * fc::kMlpParams, cudaMemcpyHostToDevice));
+    FC_CK(cudaMemcpy(h->d_m2, state + fc::kMlpPacked + fc::kMlpParams, sizeof(float) * fc::kMlpParams,
+                     cudaMemcpyHostToDevice));
+    h->sur_step = (int)state[fc::kMlpPacked + 2 * fc::kMlpParams];
+    h->has_sur = true;
+    h->sur_fitted = true;
+    return FC_OK;
+}
+
+int fc_surrogate_eval(fc_handle *h, const float *L, int64_t n, float *lnT, int64_t *n_fallback,
+                      void *stream)
+{
+    int rc = sur_check_data(h, "fc_surrogate_eval", L, nullptr, false, n);
+    if (rc) return rc;
+    if (!lnT) return fail(FC_EINVAL, "fc_surrogate_eval: null output");
+    DeviceGuard dgd(h->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    fc::SurrogateParams p;
+    fill_sur_params(h, &p);
+    if (n_fallback) FC_CK(cudaMemsetAsync(h->d_cnt, 0, sizeof(unsigned int), s));
+    Trace t(h, FC_K_SURROGATE_EVAL, 1, s);
+    FC_CK(fc::launch_mlp_eval(p, L, n, lnT, h->d_cnt, h->d_err, s));
+    t.end();
+    if (n_fallback) {
+        unsigned int c = 0;
+        FC_CK(cudaMemcpyAsync(&c, h->d_cnt, sizeof(c), cudaMemcpyDeviceToHost, s));
+        FC_CK(cudaStreamSynchronize(s));
+        *n_fallback = c;
+        return sur_read_err(h, s, "fc_surrogate_eval");
+    }
+    return FC_OK;
+}
+
+int fc_energy_sum_lengths(fc_handle *h, const float *L, int64_t n, float *lnT, void *stream)
+{
+    if (!h || !L || !lnT || n < 0) return fail(FC_EINVAL, "fc_energy_sum_lengths: bad argument");
+    if (!h->has_spec) return fail(FC_ESTATE, "fc_energy_sum_lengths: set the spectrum first");
+    DeviceGuard dgd(h->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    fc::SurrogateParams p;
+    fill_sur_params(h, &p);
+    Trace t(h, FC_K_ENERGY_SUM, 1, s);
+    FC_CK(fc::launch_energy_sum_lengths(p, L, n, lnT, s));
+    t.end();
     return FC_OK;
 }
 

@@ -1,6 +1,7 @@
 // Internal declarations shared by the CUDA translation units of libfastcat.
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -69,6 +70,59 @@ void fdk_row_range(const DevGeom &g, int *v_lo, int *v_hi);
 
 // Sets the message fc_last_error() returns on this thread.
 void set_last_error(const char *msg);
+
+// ---- learned surrogate of the energy integral (fc_mlp.cu) ----
+constexpr int kMlpHidden = 128;
+constexpr int kMlpIn = 8;
+// packed fp32 parameter vector: W1 [128][8], b1, W2 [128][128], b2, W3, b3,
+// w4 [128], b4, then input scale [8], mubar [8] and the training box [8]
+constexpr int kOffW1 = 0;
+constexpr int kOffB1 = kOffW1 + kMlpHidden * kMlpIn;
+constexpr int kOffW2 = kOffB1 + kMlpHidden;
+constexpr int kOffB2 = kOffW2 + kMlpHidden * kMlpHidden;
+constexpr int kOffW3 = kOffB2 + kMlpHidden;
+constexpr int kOffB3 = kOffW3 + kMlpHidden * kMlpHidden;
+constexpr int kOffW4 = kOffB3 + kMlpHidden;
+constexpr int kOffB4 = kOffW4 + kMlpHidden;
+constexpr int kMlpParams = kOffB4 + 1;
+constexpr int kOffScale = kMlpParams;
+constexpr int kOffMubar = kOffScale + kMaxMat;
+constexpr int kOffBox = kOffMubar + kMaxMat;
+constexpr int kMlpPacked = kOffBox + kMaxMat;
+constexpr int kWgradChunk = 1024;   // batch columns per split-K weight-gradient CTA
+
+struct SurrogateParams {
+    const __nv_bfloat16 *W1b;   // [128][16] (inputs 8..15 zero)
+    const __nv_bfloat16 *W2b, *W3b;    // [out][in]
+    const __nv_bfloat16 *W2Tb, *W3Tb;  // [in][out]
+    const float *P;             // packed fp32 parameters
+    int n_mat, n_e;
+    float wd[kMaxBins];
+    float mu2[kMaxBins][kMaxMat];
+};
+
+// Training workspace for a batch of B samples (feature-major [rows][B]).
+struct MlpWork {
+    __nv_bfloat16 *xt;          // [16][B]
+    __nv_bfloat16 *h1t, *h2t, *h3t, *dz1t, *dz2t, *dz3t;  // [128][B]
+    __nv_bfloat16 *g;           // [16][B], row 0 = dLoss / dy_hat, rows 1..15 zero
+    float *part;                // [4][n_chunks][128][128] split-K partials
+    float *rsum;                // [4][n_chunks][128]
+    float *gsum;                // [n_chunks]
+};
+
+cudaError_t launch_mlp_eval(const SurrogateParams &p, const float *L, long long n, float *lnT,
+                            unsigned int *n_fallback, int *err, cudaStream_t s);
+cudaError_t launch_energy_sum_lengths(const SurrogateParams &p, const float *L, long long n,
+                                      float *lnT, cudaStream_t s);
+cudaError_t launch_mlp_lmax(const float *L, long long n, int n_mat, unsigned int *mx,
+                            cudaStream_t s);
+cudaError_t launch_mlp_step(const SurrogateParams &p, const float *L, const float *y, long long n,
+                            int B, int sample, unsigned long long seed, int step, const MlpWork &w,
+                            float *loss, int *err, float *P, float *m1, float *m2, float lr,
+                            float bc1, float bc2, float *grad, __nv_bfloat16 *W1b,
+                            __nv_bfloat16 *W2b, __nv_bfloat16 *W3b, __nv_bfloat16 *W2Tb,
+                            __nv_bfloat16 *W3Tb, cudaStream_t s);
 
 // launchers (return cudaError_t of the launch)
 cudaError_t launch_project(const ProjParams &p, float *T, float *L_out, cudaStream_t s);

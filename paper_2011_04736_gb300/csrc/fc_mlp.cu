@@ -1,0 +1,712 @@
+// Learned surrogate of the energy integral: ln T(L) from the per-material
+// path lengths L of a ray (the quantity the projector's energy loop
+// computes, paper Sec. II.F, I_f equation), replacing the N_E-bin sum.
+//
+//   ln T ~ -sum_m mubar_m L_m + MLP(L * scale)
+//   MLP: 8 -> 128 -> 128 -> 128 -> 1, SiLU activations,
+//   mubar = sum_E (w D)_E mu_m(E) / sum_E (w D)_E  (first-order term)
+//
+// The three 128-wide layers run on the 5th-generation tensor cores
+// (tcgen05.mma kind::f16, bf16 operands in shared memory, f32 accumulators
+// in tensor memory); biases, SiLU and the 128 -> 1 output layer run in the
+// epilogues.  One CTA handles tiles of 128 rays; thread r of the 128 owns
+// ray r of the tile (TMEM lane r).
+//
+// Training: a fused forward + backward kernel per 128-sample tile keeps the
+// three pre-activations in TMEM (384 of 512 columns) and the data-gradient
+// accumulator in the rest; it writes the activations and back-propagated
+// errors feature-major, [feature][batch], so that the weight gradients
+// dW = dZ^T H are split-K tensor-core GEMMs over the batch (k_mlp_wgrad).
+// k_mlp_adam sums the split-K partials and applies Adam.
+//
+// Every wait on the tensor core is a bounded mbarrier poll; on expiry the
+// kernel records FC_ETIMEOUT in an error word, skips the dependent work,
+// releases its TMEM and returns.
+#include <cuda_bf16.h>
+#include <math.h>
+
+#include "fc_internal.cuh"
+#include "fc_tc.cuh"
+
+namespace fc {
+
+namespace {
+
+using bf16 = __nv_bfloat16;
+
+constexpr int kH = kMlpHidden;       // 128
+constexpr int kInP = 16;             // inputs padded to one MMA K-step
+constexpr uint32_t kKgs128 = (kH / 8) * 128;   // k-group stride of a 128-row operand
+constexpr uint32_t kPolls = 1u << 24;          // bounded mbarrier polls (~0.5 s)
+
+__device__ __forceinline__ float tanh_fast(float x)
+{
+    float y;
+    asm("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// SiLU(z) = z sigma(z), sigma(z) = (1 + tanh(z / 2)) / 2
+__device__ __forceinline__ float silu(float z)
+{
+    return z * fmaf(0.5f, tanh_fast(0.5f * z), 0.5f);
+}
+
+// d SiLU / dz = sigma + z sigma (1 - sigma)
+__device__ __forceinline__ float dsilu(float z)
+{
+    const float s = fmaf(0.5f, tanh_fast(0.5f * z), 0.5f);
+    return fmaf(z * s, 1.0f - s, s);
+}
+
+__device__ __forceinline__ uint32_t pack2(float a, float b)
+{
+    const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+    return *reinterpret_cast<const uint32_t *>(&h);
+}
+
+// Copy a row-major bf16 matrix [rows][k] from global memory into the K-major
+// no-swizzle operand layout (16-byte chunks = one core-matrix row each).
+__device__ __forceinline__ void stage_kmajor(unsigned char *dst, const bf16 *src, int rows, int k,
+                                             uint32_t kgs)
+{
+    const int chunks = rows * (k / 8);
+    for (int c = threadIdx.x; c < chunks; c += blockDim.x) {
+        const int r = c / (k / 8), kc = (c % (k / 8)) * 8;
+        *reinterpret_cast<uint4 *>(dst + tc::kmajor_off(r, kc, kgs)) =
+            *reinterpret_cast<const uint4 *>(src + (size_t)r * k + kc);
+    }
+}
+
+// Issue the K/16 MMAs of D[128 x N] (+)= A[128 x K] B[N x K]^T.
+__device__ __forceinline__ void issue_gemm(uint32_t d, const unsigned char *a, uint32_t kgsa,
+                                           const unsigned char *b, uint32_t kgsb, int K, int N,
+                                           bool accumulate_first)
+{
+    const uint32_t id = tc::idesc_bf16(128, N);
+    for (int ks = 0; ks < K / 16; ++ks) {
+        const uint64_t ad = tc::sdesc(tc::smem_u32(a) + ks * 2 * kgsa, kgsa, 128);
+        const uint64_t bd = tc::sdesc(tc::smem_u32(b) + ks * 2 * kgsb, kgsb, 128);
+        tc::mma_bf16(d, ad, bd, id, (ks > 0 || accumulate_first) ? 1u : 0u);
+    }
+}
+
+// CTA-wide: make shared-memory writes visible to the tensor core and order
+// tensor-memory accesses around the barrier.
+__device__ __forceinline__ void sync_for_mma()
+{
+    tc::fence_async_smem();
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+}
+
+// Thread 0 issues a GEMM and commits; everyone waits for it.  Returns false
+// (and records the timeout) if the wait bound is exhausted.
+__device__ __forceinline__ bool run_gemm(uint32_t d, const unsigned char *a, uint32_t kgsa,
+                                         const unsigned char *b, uint32_t kgsb, int K, int N,
+                                         uint64_t *mbar, uint32_t &phase, int *err)
+{
+    if (threadIdx.x == 0) {
+        issue_gemm(d, a, kgsa, b, kgsb, K, N, false);
+        tc::mma_commit(mbar);
+    }
+    const bool ok = tc::mbar_wait(mbar, phase, kPolls);
+    phase ^= 1u;
+    tc::fence_after_sync();
+    if (!ok && threadIdx.x == 0) atomicExch(err, FC_ETIMEOUT);
+    return __syncthreads_and(ok);
+}
+
+// Per-lane TMEM address of this thread's row, column col.
+__device__ __forceinline__ uint32_t trow(uint32_t tbase, int col)
+{
+    return tbase + ((uint32_t)(threadIdx.x & ~31) << 16) + (uint32_t)col;
+}
+
+// Epilogue: h = SiLU(acc + bias) of this thread's row -> bf16 row r of a
+// K-major operand (and, if ht != nullptr, feature-major global copy
+// ht[j * ldh + col]).
+__device__ __forceinline__ void epi_silu(uint32_t tacc, const float *bias, unsigned char *dst,
+                                         bf16 *ht, size_t ldh, size_t col)
+{
+    const int r = threadIdx.x;
+#pragma unroll 1
+    for (int c0 = 0; c0 < kH; c0 += 16) {
+        float v[16];
+        tc::tmem_ld16(tacc + c0, v);
+        uint32_t p[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const float a = silu(v[2 * i] + bias[c0 + 2 * i]);
+            const float b = silu(v[2 * i + 1] + bias[c0 + 2 * i + 1]);
+            p[i] = pack2(a, b);
+            if (ht) {
+                const __nv_bfloat162 hb = *reinterpret_cast<const __nv_bfloat162 *>(&p[i]);
+                ht[(size_t)(c0 + 2 * i) * ldh + col] = hb.x;
+                ht[(size_t)(c0 + 2 * i + 1) * ldh + col] = hb.y;
+            }
+        }
+        *reinterpret_cast<uint4 *>(dst + tc::kmajor_off(r, c0, kKgs128)) =
+            make_uint4(p[0], p[1], p[2], p[3]);
+        *reinterpret_cast<uint4 *>(dst + tc::kmajor_off(r, c0 + 8, kKgs128)) =
+            make_uint4(p[4], p[5], p[6], p[7]);
+    }
+}
+
+// Exact ln T from path lengths: the projector's energy-integral epilogue.
+__device__ __forceinline__ float exact_lnT(const float (&L)[kMaxMat], const float *wd,
+                                           const float (*mu2)[kMaxMat], int n_e)
+{
+    float sum = 0.0f, comp = 0.0f;
+    for (int e = 0; e < n_e; ++e) {
+        float a = 0.0f;
+#pragma unroll
+        for (int m = 0; m < kMaxMat; ++m) a = fmaf(mu2[e][m], L[m], a);
+        const float term = wd[e] * exp2f(-a);
+        const float y = term - comp;
+        const float t = sum + y;
+        comp = (t - sum) - y;
+        sum = t;
+    }
+    return logf(sum);
+}
+
+// shared-memory map of the inference kernel (bytes)
+constexpr int kInfW1 = 0, kInfW2 = 4096, kInfW3 = 4096 + 32768, kInfX = 4096 + 2 * 32768,
+              kInfH = kInfX + 4096, kInfF = kInfH + 32768;
+constexpr int kInfSmem = kInfF + (4 * kH + 3 * kMaxMat + 8) * 4;
+
+}  // namespace
+
+// ---------------------------------------------------------------- inference
+__global__ void __launch_bounds__(128)
+k_mlp_eval(const __grid_constant__ SurrogateParams p, const float *__restrict__ L, long long n,
+           float *__restrict__ lnT, unsigned int *n_fallback, int *err)
+{
+    extern __shared__ __align__(1024) unsigned char smem[];
+    __shared__ uint64_t mbar;
+    __shared__ uint32_t tbase_s;
+    unsigned char *sW1 = smem + kInfW1, *sW2 = smem + kInfW2, *sW3 = smem + kInfW3;
+    unsigned char *sX = smem + kInfX, *sH = smem + kInfH;
+    float *fb = reinterpret_cast<float *>(smem + kInfF);
+    float *b1 = fb, *b2 = fb + kH, *b3 = fb + 2 * kH, *w4 = fb + 3 * kH;
+    float *scale = fb + 4 * kH, *mubar = scale + kMaxMat, *box = mubar + kMaxMat;
+    const int r = threadIdx.x;
+    if (r < 32) tc::tmem_alloc(&tbase_s, 128);
+    if (r == 0) tc::mbar_init(&mbar, 1);
+    stage_kmajor(sW1, p.W1b, kH, kInP, kKgs128);
+    stage_kmajor(sW2, p.W2b, kH, kH, kKgs128);
+    stage_kmajor(sW3, p.W3b, kH, kH, kKgs128);
+    const float *P = p.P;
+    for (int i = r; i < kH; i += blockDim.x) {
+        b1[i] = P[kOffB1 + i];
+        b2[i] = P[kOffB2 + i];
+        b3[i] = P[kOffB3 + i];
+        w4[i] = P[kOffW4 + i];
+    }
+    if (r < kMaxMat) {
+        scale[r] = P[kOffScale + r];
+        mubar[r] = P[kOffMubar + r];
+        box[r] = P[kOffBox + r];
+    }
+    const float b4 = P[kOffB4];
+    sync_for_mma();
+    const uint32_t tb = tbase_s;
+    uint32_t phase = 0;
+    unsigned int my_fallback = 0;
+    const long long ntiles = (n + 127) / 128;
+    for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const long long i = tile * 128 + r;
+        const bool valid = i < n;
+        float Lr[kMaxMat];
+        float ylin = 0.0f;
+        bool outside = false;
+#pragma unroll
+        for (int m = 0; m < kMaxMat; ++m) {
+            Lr[m] = (valid && m < p.n_mat) ? L[i * p.n_mat + m] : 0.0f;
+            ylin = fmaf(-mubar[m], Lr[m], ylin);
+            outside = outside || Lr[m] > box[m];
+        }
+        {
+            uint32_t q[8];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) q[k] = pack2(Lr[2 * k] * scale[2 * k], Lr[2 * k + 1] * scale[2 * k + 1]);
+#pragma unroll
+            for (int k = 4; k < 8; ++k) q[k] = 0u;
+            *reinterpret_cast<uint4 *>(sX + tc::kmajor_off(r, 0, kKgs128)) = make_uint4(q[0], q[1], q[2], q[3]);
+            *reinterpret_cast<uint4 *>(sX + tc::kmajor_off(r, 8, kKgs128)) = make_uint4(q[4], q[5], q[6], q[7]);
+        }
+        sync_for_mma();
+        if (!run_gemm(tb, sX, kKgs128, sW1, kKgs128, kInP, kH, &mbar, phase, err)) break;
+        epi_silu(trow(tb, 0), b1, sH, nullptr, 0, 0);
+        sync_for_mma();
+        if (!run_gemm(tb, sH, kKgs128, sW2, kKgs128, kH, kH, &mbar, phase, err)) break;
+        epi_silu(trow(tb, 0), b2, sH, nullptr, 0, 0);
+        sync_for_mma();
+        if (!run_gemm(tb, sH, kKgs128, sW3, kKgs128, kH, kH, &mbar, phase, err)) break;
+        float res = b4;
+#pragma unroll 1
+        for (int c0 = 0; c0 < kH; c0 += 16) {
+            float v[16];
+            tc::tmem_ld16(trow(tb, c0), v);
+#pragma unroll
+            for (int j = 0; j < 16; ++j) res = fmaf(w4[c0 + j], silu(v[j] + b3[c0 + j]), res);
+        }
+        if (valid) {
+            float y = ylin + res;
+            if (outside) {
+                y = exact_lnT(Lr, p.wd, p.mu2, p.n_e);
+                ++my_fallback;
+            }
+            lnT[i] = y;
+        }
+        tc::fence_before_sync();
+        __syncthreads();
+        tc::fence_after_sync();
+    }
+    if (my_fallback) atomicAdd(n_fallback, my_fallback);
+    tc::fence_before_sync();
+    __syncthreads();
+    if (r < 32) tc::tmem_dealloc(tb, 128);
+}
+
+// Exact ln T of each ray from its path lengths (the plain energy-sum path).
+__global__ void __launch_bounds__(256)
+k_energy_sum_lengths(const __grid_constant__ SurrogateParams p, const float *__restrict__ L,
+                     long long n, float *__restrict__ lnT)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        float Lr[kMaxMat];
+#pragma unroll
+        for (int m = 0; m < kMaxMat; ++m) Lr[m] = m < p.n_mat ? L[i * p.n_mat + m] : 0.0f;
+        lnT[i] = exact_lnT(Lr, p.wd, p.mu2, p.n_e);
+    }
+}
+
+// ---------------------------------------------------------------- training
+namespace {
+// shared-memory map of the training kernel (bytes)
+constexpr int kTrW1 = 0, kTrW2 = 4096, kTrW3 = kTrW2 + 32768, kTrW2T = kTrW3 + 32768,
+              kTrW3T = kTrW2T + 32768, kTrX = kTrW3T + 32768, kTrH = kTrX + 4096,
+              kTrD = kTrH + 32768, kTrF = kTrD + 32768;
+constexpr int kTrSmem = kTrF + (4 * kH + 2 * kMaxMat + 8) * 4;
+
+__device__ __forceinline__ unsigned long long mix64(unsigned long long z)
+{
+    z += 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+}  // namespace
+
+// One training step's forward and backward for tiles of 128 samples.
+// Writes (feature-major, [feature][batch]): xt [16][B], h1t, h2t, h3t,
+// dz1t, dz2t, dz3t [128][B], and g [16][B] whose row 0 holds dLoss/dy_hat
+// (rows 1..15 stay zero); adds the batch's summed squared error to *loss.
+__global__ void __launch_bounds__(128, 1)
+k_mlp_train(const __grid_constant__ SurrogateParams p, const float *__restrict__ L,
+            const float *__restrict__ y, long long n, int B, int sample, unsigned long long seed,
+            int step, MlpWork w, float *loss, int *err)
+{
+    extern __shared__ __align__(1024) unsigned char smem[];
+    __shared__ uint64_t mbar;
+    __shared__ uint32_t tbase_s;
+    __shared__ float red[4];
+    unsigned char *sW1 = smem + kTrW1, *sW2 = smem + kTrW2, *sW3 = smem + kTrW3;
+    unsigned char *sW2T = smem + kTrW2T, *sW3T = smem + kTrW3T;
+    unsigned char *sX = smem + kTrX, *sH = smem + kTrH, *sD = smem + kTrD;
+    float *fb = reinterpret_cast<float *>(smem + kTrF);
+    float *b1 = fb, *b2 = fb + kH, *b3 = fb + 2 * kH, *w4 = fb + 3 * kH;
+    float *scale = fb + 4 * kH, *mubar = scale + kMaxMat;
+    const int r = threadIdx.x;
+    if (r < 32) tc::tmem_alloc(&tbase_s, 512);
+    if (r == 0) tc::mbar_init(&mbar, 1);
+    stage_kmajor(sW1, p.W1b, kH, kInP, kKgs128);
+    stage_kmajor(sW2, p.W2b, kH, kH, kKgs128);
+    stage_kmajor(sW3, p.W3b, kH, kH, kKgs128);
+    stage_kmajor(sW2T, p.W2Tb, kH, kH, kKgs128);
+    stage_kmajor(sW3T, p.W3Tb, kH, kH, kKgs128);
+    const float *P = p.P;
+    for (int i = r; i < kH; i += blockDim.x) {
+        b1[i] = P[kOffB1 + i];
+        b2[i] = P[kOffB2 + i];
+        b3[i] = P[kOffB3 + i];
+        w4[i] = P[kOffW4 + i];
+    }
+    if (r < kMaxMat) {
+        scale[r] = P[kOffScale + r];
+        mubar[r] = P[kOffMubar + r];
+    }
+    const float b4 = P[kOffB4];
+    sync_for_mma();
+    const uint32_t tb = tbase_s;
+    const uint32_t tZ1 = trow(tb, 0), tZ2 = trow(tb, 128), tZ3 = trow(tb, 256), tD = trow(tb, 384);
+    uint32_t phase = 0;
+    float sq = 0.0f;
+    const int ntiles = (B + 127) / 128;
+    const float inv_b = 1.0f / (float)B;
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int col = tile * 128 + r;   // position in the batch
+        const bool valid = col < B;
+        long long idx = col;
+        if (sample) idx = (long long)(mix64(seed ^ mix64(((unsigned long long)step << 32) | (unsigned)col)) % (unsigned long long)n);
+        float Lr[kMaxMat], ylin = 0.0f;
+#pragma unroll
+        for (int m = 0; m < kMaxMat; ++m) {
+            Lr[m] = (valid && m < p.n_mat) ? L[idx * p.n_mat + m] : 0.0f;
+            ylin = fmaf(-mubar[m], Lr[m], ylin);
+        }
+        const float yt = valid ? y[idx] : 0.0f;
+        {
+            uint32_t q[8];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) q[k] = pack2(Lr[2 * k] * scale[2 * k], Lr[2 * k + 1] * scale[2 * k + 1]);
+#pragma unroll
+            for (int k = 4; k < 8; ++k) q[k] = 0u;
+            *reinterpret_cast<uint4 *>(sX + tc::kmajor_off(r, 0, kKgs128)) = make_uint4(q[0], q[1], q[2], q[3]);
+            *reinterpret_cast<uint4 *>(sX + tc::kmajor_off(r, 8, kKgs128)) = make_uint4(q[4], q[5], q[6], q[7]);
+            if (valid) {
+#pragma unroll
+                for (int k = 0; k < 8; ++k) {
+                    const __nv_bfloat162 hb = *reinterpret_cast<const __nv_bfloat162 *>(&q[k]);
+                    w.xt[(size_t)(2 * k) * B + col] = hb.x;
+                    w.xt[(size_t)(2 * k + 1) * B + col] = hb.y;
+                }
+            }
+        }
+        sync_for_mma();
+        // forward: Z1, Z2, Z3 stay in TMEM columns [0,128), [128,256), [256,384)
+        if (!run_gemm(tb, sX, kKgs128, sW1, kKgs128, kInP, kH, &mbar, phase, err)) break;
+        epi_silu(tZ1, b1, sH, valid ? w.h1t : nullptr, B, col);
+        sync_for_mma();
+        if (!run_gemm(tb + 128, sH, kKgs128, sW2, kKgs128, kH, kH, &mbar, phase, err)) break;
+        epi_silu(tZ2, b2, sH, valid ? w.h2t : nullptr, B, col);
+        sync_for_mma();
+        if (!run_gemm(tb + 256, sH, kKgs128, sW3, kKgs128, kH, kH, &mbar, phase, err)) break;
+        float res = b4;
+#pragma unroll 1
+        for (int c0 = 0; c0 < kH; c0 += 16) {
+            float v[16];
+            tc::tmem_ld16(tZ3 + c0, v);
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                const float h = silu(v[j] + b3[c0 + j]);
+                res = fmaf(w4[c0 + j], h, res);
+                if (valid) w.h3t[(size_t)(c0 + j) * B + col] = __float2bfloat16_rn(h);
+            }
+        }
+        const float e = valid ? (ylin + res - yt) : 0.0f;
+        sq = fmaf(e, e, sq);
+        const float gr = 2.0f * e * inv_b;   // dLoss / dy_hat for this sample
+        if (valid) w.g[col] = __float2bfloat16_rn(gr);
+        // dZ3 = g w4 SiLU'(Z3)
+#pragma unroll 1
+        for (int c0 = 0; c0 < kH; c0 += 16) {
+            float v[16];
+            tc::tmem_ld16(tZ3 + c0, v);
+            uint32_t q[8];
+#pragma unroll
+            for (int i2 = 0; i2 < 8; ++i2) {
+                const float a = gr * w4[c0 + 2 * i2] * dsilu(v[2 * i2] + b3[c0 + 2 * i2]);
+                const float b = gr * w4[c0 + 2 * i2 + 1] * dsilu(v[2 * i2 + 1] + b3[c0 + 2 * i2 + 1]);
+                q[i2] = pack2(a, b);
+                if (valid) {
+                    const __nv_bfloat162 hb = *reinterpret_cast<const __nv_bfloat162 *>(&q[i2]);
+                    w.dz3t[(size_t)(c0 + 2 * i2) * B + col] = hb.x;
+                    w.dz3t[(size_t)(c0 + 2 * i2 + 1) * B + col] = hb.y;
+                }
+            }
+            *reinterpret_cast<uint4 *>(sD + tc::kmajor_off(r, c0, kKgs128)) = make_uint4(q[0], q[1], q[2], q[3]);
+            *reinterpret_cast<uint4 *>(sD + tc::kmajor_off(r, c0 + 8, kKgs128)) = make_uint4(q[4], q[5], q[6], q[7]);
+        }
+        sync_for_mma();
+        // dH2 = dZ3 W3  (B operand W3^T: rows = layer input, K = layer output)
+        if (!run_gemm(tb + 384, sD, kKgs128, sW3T, kKgs128, kH, kH, &mbar, phase, err)) break;
+#pragma unroll 1
+        for (int c0 = 0; c0 < kH; c0 += 16) {
+            float dv[16], zv[16];
+            tc::tmem_ld16(tD + c0, dv);
+            tc::tmem_ld16(tZ2 + c0, zv);
+            uint32_t q[8];
+#pragma unroll
+            for (int i2 = 0; i2 < 8; ++i2) {
+                const float a = dv[2 * i2] * dsilu(zv[2 * i2] + b2[c0 + 2 * i2]);
+                const float b = dv[2 * i2 + 1] * dsilu(zv[2 * i2 + 1] + b2[c0 + 2 * i2 + 1]);
+                q[i2] = pack2(a, b);
+                if (valid) {
+                    const __nv_bfloat162 hb = *reinterpret_cast<const __nv_bfloat162 *>(&q[i2]);
+                    w.dz2t[(size_t)(c0 + 2 * i2) * B + col] = hb.x;
+                    w.dz2t[(size_t)(c0 + 2 * i2 + 1) * B + col] = hb.y;
+                }
+            }
+            *reinterpret_cast<uint4 *>(sD + tc::kmajor_off(r, c0, kKgs128)) = make_uint4(q[0], q[1], q[2], q[3]);
+            *reinterpret_cast<uint4 *>(sD + tc::kmajor_off(r, c0 + 8, kKgs128)) = make_uint4(q[4], q[5], q[6], q[7]);
+        }
+        sync_for_mma();
+        // dH1 = dZ2 W2
+        if (!run_gemm(tb + 384, sD, kKgs128, sW2T, kKgs128, kH, kH, &mbar, phase, err)) break;
+#pragma unroll 1
+        for (int c0 = 0; c0 < kH; c0 += 16) {
+            float dv[16], zv[16];
+            tc::tmem_ld16(tD + c0, dv);
+            tc::tmem_ld16(tZ1 + c0, zv);
+            if (valid) {
+#pragma unroll
+                for (int j = 0; j < 16; ++j)
+                    w.dz1t[(size_t)(c0 + j) * B + col] =
+                        __float2bfloat16_rn(dv[j] * dsilu(zv[j] + b1[c0 + j]));
+            }
+        }
+        tc::fence_before_sync();
+        __syncthreads();
+        tc::fence_after_sync();
+    }
+    // squared-error sum of this CTA -> *loss
+    float v = sq;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((r & 31) == 0) red[r >> 5] = v;
+    tc::fence_before_sync();
+    __syncthreads();
+    if (r == 0) atomicAdd(loss, red[0] + red[1] + red[2] + red[3]);
+    if (r < 32) tc::tmem_dealloc(tb, 512);
+}
+
+// Split-K weight-gradient GEMMs over the batch.  Job j (blockIdx.y):
+//   0: dW3 = dZ3^T H2 (+ db3 = row sums of dZ3^T)
+//   1: dW2 = dZ2^T H1 (+ db2)
+//   2: dW1 = dZ1^T X  (+ db1)
+//   3: dw4 = H3^T g   (column 0) and db4 = sum g
+// Chunk c (blockIdx.x) covers batch columns [c kChunk, (c + 1) kChunk);
+// results go to part[job][c][128][16 or 128] and rsum[job][c][128].
+__global__ void __launch_bounds__(128)
+k_mlp_wgrad(MlpWork w, int B, int n_chunks, int *err)
+{
+    extern __shared__ __align__(1024) unsigned char smem[];
+    __shared__ uint64_t mbar;
+    __shared__ uint32_t tbase_s;
+    const int job = blockIdx.y, c = blockIdx.x, r = threadIdx.x;
+    const bf16 *A = job == 0 ? w.dz3t : job == 1 ? w.dz2t : job == 2 ? w.dz1t : w.h3t;
+    const bf16 *Bm = job == 0 ? w.h2t : job == 1 ? w.h1t : job == 2 ? w.xt : w.g;
+    const int N = job <= 1 ? kH : 16;
+    const uint32_t kgsb = (uint32_t)(N / 8) * 128;
+    unsigned char *sA = smem, *sB = smem + 32768;
+    if (r < 32) tc::tmem_alloc(&tbase_s, 128);
+    if (r == 0) tc::mbar_init(&mbar, 1);
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tb = tbase_s;
+    uint32_t phase = 0;
+    float rs = 0.0f;
+    bool ok = true;
+    const int k0 = c * kWgradChunk;
+    for (int kk = 0; kk < kWgradChunk && ok; kk += 128) {
+        const int kb = k0 + kk;
+        // stage 128 x 128 of A (row r) and N x 128 of B; zero beyond the batch
+        for (int q = 0; q < 16; ++q) {
+            uint4 val = make_uint4(0u, 0u, 0u, 0u);
+            if (kb + q * 8 + 8 <= B)
+                val = *reinterpret_cast<const uint4 *>(A + (size_t)r * B + kb + q * 8);
+            *reinterpret_cast<uint4 *>(sA + tc::kmajor_off(r, q * 8, kKgs128)) = val;
+            const __nv_bfloat162 *h2 = reinterpret_cast<const __nv_bfloat162 *>(&val);
+#pragma unroll
+            for (int t = 0; t < 4; ++t) rs += __low2float(h2[t]) + __high2float(h2[t]);
+        }
+        if (r < N) {
+            for (int q = 0; q < 16; ++q) {
+                uint4 val = make_uint4(0u, 0u, 0u, 0u);
+                if (kb + q * 8 + 8 <= B)
+                    val = *reinterpret_cast<const uint4 *>(Bm + (size_t)r * B + kb + q * 8);
+                *reinterpret_cast<uint4 *>(sB + tc::kmajor_off(r, q * 8, kgsb)) = val;
+            }
+        }
+        sync_for_mma();
+        if (r == 0) {
+            issue_gemm(tb, sA, kKgs128, sB, kgsb, 128, N, kk > 0);
+            tc::mma_commit(&mbar);
+        }
+        ok = tc::mbar_wait(&mbar, phase, kPolls);
+        phase ^= 1u;
+        tc::fence_after_sync();
+        if (!ok && r == 0) atomicExch(err, FC_ETIMEOUT);
+        ok = __syncthreads_and(ok);
+    }
+    if (ok) {
+        float *out = w.part + ((size_t)job * n_chunks + c) * (size_t)kH * kH;
+        for (int c0 = 0; c0 < N; c0 += 16) {
+            float v[16];
+            tc::tmem_ld16(trow(tb, c0), v);
+#pragma unroll
+            for (int j = 0; j < 16; ++j) out[(size_t)r * N + c0 + j] = v[j];
+        }
+        w.rsum[((size_t)job * n_chunks + c) * kH + r] = rs;
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (r < 32) tc::tmem_dealloc(tb, 128);
+}
+
+// Sum the split-K partials; either write the gradient (grad != nullptr) or
+// apply one Adam step to the fp32 parameters and refresh the bf16 copies.
+__global__ void k_mlp_adam(MlpWork w, int n_chunks, float *P, float *m1, float *m2, float lr,
+                           float bc1, float bc2, float *grad, bf16 *W1b, bf16 *W2b, bf16 *W3b,
+                           bf16 *W2Tb, bf16 *W3Tb)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= kMlpParams) return;
+    float g = 0.0f;
+    auto part = [&](int job, int row, int colN, int N) {
+        float s = 0.0f;
+        for (int c = 0; c < n_chunks; ++c)
+            s += w.part[((size_t)job * n_chunks + c) * (size_t)kH * kH + (size_t)row * N + colN];
+        return s;
+    };
+    auto rsum = [&](int job, int row) {
+        float s = 0.0f;
+        for (int c = 0; c < n_chunks; ++c) s += w.rsum[((size_t)job * n_chunks + c) * kH + row];
+        return s;
+    };
+    if (i < kOffB1) {                       // W1 [128][8]
+        g = part(2, i / kMlpIn, i % kMlpIn, 16);
+    } else if (i < kOffW2) {
+        g = rsum(2, i - kOffB1);
+    } else if (i < kOffB2) {
+        const int j = i - kOffW2;
+        g = part(1, j / kH, j % kH, kH);
+    } else if (i < kOffW3) {
+        g = rsum(1, i - kOffB2);
+    } else if (i < kOffB3) {
+        const int j = i - kOffW3;
+        g = part(0, j / kH, j % kH, kH);
+    } else if (i < kOffW4) {
+        g = rsum(0, i - kOffB3);
+    } else if (i < kOffB4) {
+        g = part(3, i - kOffW4, 0, 16);
+    } else {
+        // db4 = sum of g over the batch (per-chunk sums from k_mlp_gsum)
+        for (int c = 0; c < n_chunks; ++c) g += w.gsum[c];
+    }
+    if (grad) {
+        grad[i] = g;
+        return;
+    }
+    const float a = 0.9f * m1[i] + 0.1f * g;
+    const float b = 0.999f * m2[i] + 0.001f * g * g;
+    m1[i] = a;
+    m2[i] = b;
+    const float pnew = P[i] - lr * (a / bc1) / (sqrtf(b / bc2) + 1e-8f);
+    P[i] = pnew;
+    const bf16 pb = __float2bfloat16_rn(pnew);
+    if (i < kOffB1) {
+        const int o = i / kMlpIn, in = i % kMlpIn;
+        W1b[o * kInP + in] = pb;
+    } else if (i >= kOffW2 && i < kOffB2) {
+        const int j = i - kOffW2, o = j / kH, in = j % kH;
+        W2b[o * kH + in] = pb;
+        W2Tb[in * kH + o] = pb;
+    } else if (i >= kOffW3 && i < kOffB3) {
+        const int j = i - kOffW3, o = j / kH, in = j % kH;
+        W3b[o * kH + in] = pb;
+        W3Tb[in * kH + o] = pb;
+    }
+}
+
+// Column sums of g over each chunk (for db4).
+__global__ void k_mlp_gsum(MlpWork w, int B, int n_chunks)
+{
+    __shared__ float red[256];
+    const int c = blockIdx.x;
+    float s = 0.0f;
+    for (int k = c * kWgradChunk + threadIdx.x; k < min(B, (c + 1) * kWgradChunk); k += blockDim.x)
+        s += __bfloat162float(w.g[k]);
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int st = blockDim.x / 2; st > 0; st >>= 1) {
+        if (threadIdx.x < st) red[threadIdx.x] += red[threadIdx.x + st];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) w.gsum[c] = red[0];
+}
+
+// Per-material maximum of L over n rows (atomicMax on the float bits of
+// non-negative values).
+__global__ void k_mlp_lmax(const float *L, long long n, int n_mat, unsigned int *mx)
+{
+    __shared__ unsigned int sm[kMaxMat];
+    if (threadIdx.x < kMaxMat) sm[threadIdx.x] = 0u;
+    __syncthreads();
+    unsigned int loc[kMaxMat] = {0u};
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+        for (int m = 0; m < n_mat; ++m) loc[m] = max(loc[m], __float_as_uint(fmaxf(L[i * n_mat + m], 0.0f)));
+    for (int m = 0; m < n_mat; ++m) atomicMax(&sm[m], loc[m]);
+    __syncthreads();
+    if (threadIdx.x < n_mat) atomicMax(&mx[threadIdx.x], sm[threadIdx.x]);
+}
+
+// ---------------------------------------------------------------- launchers
+cudaError_t launch_mlp_eval(const SurrogateParams &p, const float *L, long long n, float *lnT,
+                            unsigned int *n_fallback, int *err, cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(k_mlp_eval, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         kInfSmem);
+    if (e != cudaSuccess) return e;
+    const long long ntiles = (n + 127) / 128;
+    const int grid = (int)(ntiles < 152 * 2 ? ntiles : 152 * 2);
+    k_mlp_eval<<<grid, 128, kInfSmem, s>>>(p, L, n, lnT, n_fallback, err);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_energy_sum_lengths(const SurrogateParams &p, const float *L, long long n,
+                                      float *lnT, cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    long long blocks = (n + 255) / 256;
+    if (blocks > 152 * 16) blocks = 152 * 16;
+    k_energy_sum_lengths<<<(int)blocks, 256, 0, s>>>(p, L, n, lnT);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mlp_lmax(const float *L, long long n, int n_mat, unsigned int *mx, cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    long long blocks = (n + 255) / 256;
+    if (blocks > 152 * 8) blocks = 152 * 8;
+    k_mlp_lmax<<<(int)blocks, 256, 0, s>>>(L, n, n_mat, mx);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mlp_step(const SurrogateParams &p, const float *L, const float *y, long long n,
+                            int B, int sample, unsigned long long seed, int step, const MlpWork &w,
+                            float *loss, int *err, float *P, float *m1, float *m2, float lr,
+                            float bc1, float bc2, float *grad, bf16 *W1b, bf16 *W2b, bf16 *W3b,
+                            bf16 *W2Tb, bf16 *W3Tb, cudaStream_t s)
+{
+    cudaError_t e = cudaFuncSetAttribute(k_mlp_train, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         kTrSmem);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_mlp_wgrad, cudaFuncAttributeMaxDynamicSharedMemorySize, 65536);
+    if (e != cudaSuccess) return e;
+    const int ntiles = (B + 127) / 128;
+    k_mlp_train<<<ntiles < 152 ? ntiles : 152, 128, kTrSmem, s>>>(p, L, y, n, B, sample, seed, step,
+                                                                  w, loss, err);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const int n_chunks = (B + kWgradChunk - 1) / kWgradChunk;
+    k_mlp_wgrad<<<dim3(n_chunks, 4), 128, 65536, s>>>(w, B, n_chunks, err);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_mlp_gsum<<<n_chunks, 256, 0, s>>>(w, B, n_chunks);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_mlp_adam<<<(kMlpParams + 255) / 256, 256, 0, s>>>(w, n_chunks, P, m1, m2, lr, bc1, bc2, grad,
+                                                         W1b, W2b, W3b, W2Tb, W3Tb);
+    return cudaGetLastError();
+}
+
+}  // namespace fc

@@ -26,10 +26,14 @@ FC_MAX_MATERIALS, FC_MAX_BINS = 8, 256
 ENTRY_POINTS = ("fc_create", "fc_destroy", "fc_last_error", "fc_set_geometry", "fc_set_phantom",
                 "fc_set_spectrum_detector", "fc_project", "fc_reconstruct", "fc_set_water_roi",
                 "fc_poisson", "fc_project_lengths", "fc_profile_enable", "fc_profile_read",
-                "fc_detector_blur_static")
+                "fc_detector_blur_static", "fc_surrogate_init", "fc_surrogate_train",
+                "fc_surrogate_grad", "fc_surrogate_get", "fc_surrogate_set", "fc_surrogate_eval",
+                "fc_energy_sum_lengths")
 FC_STATIC_SCRATCH_FLOATS = 8 << 20
+FC_SURROGATE_PARAMS = 34305
+FC_SURROGATE_STATE = 34305 + 24 + 2 * 34305 + 1
 FC_K_NAMES = ("project", "blur_rows", "blur_cols", "fdk_filter", "backproject", "hu", "lengths",
-              "noise")
+              "noise", "surrogate_eval", "surrogate_train", "energy_sum")
 
 
 class FastcatError(RuntimeError):
@@ -85,6 +89,14 @@ def load():
         "fc_profile_read": (I, [P, P, P]),
         "fc_detector_blur_static": (I, [P, P, I, I, I, ctypes.c_double, ctypes.c_double,
                                         ctypes.c_double, ctypes.c_double, P]),
+        "fc_surrogate_init": (I, [P, ctypes.c_uint64]),
+        "fc_surrogate_train": (I, [P, P, P, ctypes.c_int64, I, I, ctypes.c_float, ctypes.c_uint64,
+                                   P, P]),
+        "fc_surrogate_grad": (I, [P, P, P, ctypes.c_int64, P, P, P]),
+        "fc_surrogate_get": (I, [P, P]),
+        "fc_surrogate_set": (I, [P, P]),
+        "fc_surrogate_eval": (I, [P, P, ctypes.c_int64, P, P, P]),
+        "fc_energy_sum_lengths": (I, [P, P, ctypes.c_int64, P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -218,6 +230,62 @@ def fc_detector_blur_static(T, I, n_img, n_v, n_u, psf_sigma_px, scatter_sigma_p
         raise ValueError("fc_detector_blur_static takes device tensors")
     return _check(load().fc_detector_blur_static(tp, ip, n_img, n_v, n_u, psf_sigma_px,
                                                  scatter_sigma_px, spr, n0, _stream(stream)))
+
+
+def _dev(x, name):
+    p, w = _ptr(x)
+    if w != FC_DEVICE:
+        raise ValueError("%s must be a device tensor" % name)
+    return p
+
+
+def fc_surrogate_init(h, seed=0):
+    return _check(load().fc_surrogate_init(h, seed))
+
+
+def fc_surrogate_train(h, L, lnT, steps, batch, lr, seed=0, stream=None):
+    """Train on device tensors L [n][n_mat], lnT [n]; returns the per-step MSE."""
+    n = lnT.numel()
+    hist = np.zeros(max(steps, 1), np.float32)
+    _check(load().fc_surrogate_train(h, _dev(L, "L"), _dev(lnT, "lnT"), n, steps, batch, lr, seed,
+                                     hist.ctypes.data, _stream(stream)))
+    return hist[:steps]
+
+
+def fc_surrogate_grad(h, L, lnT, n=None, stream=None):
+    """(gradient [FC_SURROGATE_PARAMS], loss) over the first n samples."""
+    n = lnT.numel() if n is None else n
+    g = np.zeros(FC_SURROGATE_PARAMS, np.float32)
+    loss = np.zeros(1, np.float32)
+    _check(load().fc_surrogate_grad(h, _dev(L, "L"), _dev(lnT, "lnT"), n, g.ctypes.data,
+                                    loss.ctypes.data, _stream(stream)))
+    return g, float(loss[0])
+
+
+def fc_surrogate_get(h):
+    st = np.zeros(FC_SURROGATE_STATE, np.float32)
+    _check(load().fc_surrogate_get(h, st.ctypes.data))
+    return st
+
+
+def fc_surrogate_set(h, state):
+    st = np.ascontiguousarray(state, np.float32)
+    if st.size != FC_SURROGATE_STATE:
+        raise ValueError("state must hold FC_SURROGATE_STATE floats")
+    return _check(load().fc_surrogate_set(h, st.ctypes.data))
+
+
+def fc_surrogate_eval(h, L, lnT, stream=None, count_fallback=True):
+    """ln T by the surrogate into device tensor lnT; returns the fallback count."""
+    c = ctypes.c_int64(0)
+    _check(load().fc_surrogate_eval(h, _dev(L, "L"), lnT.numel(), _dev(lnT, "lnT"),
+                                    ctypes.byref(c) if count_fallback else None, _stream(stream)))
+    return c.value
+
+
+def fc_energy_sum_lengths(h, L, lnT, stream=None):
+    return _check(load().fc_energy_sum_lengths(h, _dev(L, "L"), lnT.numel(), _dev(lnT, "lnT"),
+                                               _stream(stream)))
 
 
 # ---------------------------------------------------------------- convenience

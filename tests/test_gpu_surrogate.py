@@ -1,0 +1,186 @@
+"""GPU tests of the learned energy-integral surrogate (tensor-core MLP) and of
+the exact energy sum from path lengths, against the FP64 oracle."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2011_04736_gb300 import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def fc():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2011_04736_gb300 import build, fastcat
+    build.build()
+    fastcat.load()
+    return fastcat
+
+
+def _head_small():
+    return W.scaled(W.WORKLOADS["head_surrogate"], n_u=64, n_v=64, n_angles=12, nx=64, ny=64,
+                    nz=64, dx=0.25, dy=0.25, dz=0.25, du=0.2, dv=0.2)
+
+
+def _random_state(seed, n_mat):
+    from oracle import mlp
+    rng = np.random.default_rng(seed)
+    st = np.zeros(34305 + 24 + 2 * 34305 + 1, np.float32)
+    P = st[:mlp.N_PACKED]
+    for name, fan in (("W1", 8), ("W2", 128), ("W3", 128), ("w4", 128)):
+        a, b = mlp.OFF[name]
+        P[a:b] = rng.uniform(-1, 1, b - a) * math.sqrt(3.0 / fan)
+    for name in ("b1", "b2", "b3", "b4"):
+        a, b = mlp.OFF[name]
+        P[a:b] = rng.normal(0, 0.1, b - a)
+    a, b = mlp.OFF["scale"]
+    P[a:b] = 0.1
+    a, b = mlp.OFF["mubar"]
+    P[a:b] = rng.uniform(0.1, 0.4, 8)
+    a, b = mlp.OFF["box"]
+    P[a:b] = 30.0
+    return st
+
+
+def _oracle_rays(orc, wl, lab, n, seed):
+    g = wl.geom
+    rng = np.random.default_rng(seed)
+    rays = np.stack([rng.integers(0, g.n_angles, n), rng.integers(0, g.n_v, n),
+                     rng.integers(0, g.n_u, n)], 1)
+    w, d = wl.spectrum()
+    L, T = orc.rays(g, lab, w, d, wl.mu(), rays)
+    return L, T
+
+
+def test_energy_sum_lengths_matches_oracle(fc, orc):
+    wl = _head_small()
+    lab = wl.make_phantom()
+    L, T = _oracle_rays(orc, wl, lab, 4096, 3)
+    sc = fc.Scanner(wl, labels=lab)
+    try:
+        dL = torch.from_numpy(L.astype(np.float32)).cuda()
+        out = torch.empty(len(T), device="cuda")
+        fc.fc_energy_sum_lengths(sc.h, dL, out)
+        torch.cuda.synchronize()
+    finally:
+        sc.close()
+    got = np.exp(out.cpu().numpy().astype(np.float64))
+    assert np.max(np.abs(got - T) / T) <= 1e-4
+
+
+def test_surrogate_eval_matches_oracle(fc, orc):
+    from oracle import mlp
+    wl = _head_small()
+    lab = wl.make_phantom()
+    L, _ = _oracle_rays(orc, wl, lab, 2000, 4)
+    st = _random_state(11, L.shape[1])
+    sc = fc.Scanner(wl, labels=lab)
+    try:
+        fc.fc_surrogate_set(sc.h, st)
+        dL = torch.from_numpy(L.astype(np.float32)).cuda()
+        out = torch.empty(len(L), device="cuda")
+        nfb = fc.fc_surrogate_eval(sc.h, dL, out)
+        torch.cuda.synchronize()
+    finally:
+        sc.close()
+    assert nfb == 0
+    ref, cache = mlp.forward(st[:mlp.N_PACKED].astype(np.float64), L.astype(np.float32))
+    got = out.cpu().numpy()
+    # bf16 activations (relative 2^-9) feeding 128-term sums, tanh-based sigma
+    scale = np.max(np.abs(cache["h3"] @ mlp.unpack(st[:mlp.N_PACKED])["w4"])) + 1.0
+    assert np.max(np.abs(got - ref)) <= 2e-2 * scale, np.max(np.abs(got - ref))
+
+
+def test_surrogate_gradient_matches_oracle(fc, orc):
+    from oracle import mlp
+    wl = _head_small()
+    lab = wl.make_phantom()
+    L, T = _oracle_rays(orc, wl, lab, 1024, 5)
+    y = np.log(T)
+    st = _random_state(12, L.shape[1])
+    sc = fc.Scanner(wl, labels=lab)
+    try:
+        fc.fc_surrogate_set(sc.h, st)
+        dL = torch.from_numpy(L.astype(np.float32)).cuda()
+        dy = torch.from_numpy(y.astype(np.float32)).cuda()
+        g, loss = fc.fc_surrogate_grad(sc.h, dL, dy)
+    finally:
+        sc.close()
+    lref, gref = mlp.loss_and_grad(st[:mlp.N_PACKED].astype(np.float64), L.astype(np.float32),
+                                   y.astype(np.float32))
+    assert loss == pytest.approx(lref, rel=2e-2)
+    for name in ("W1", "b1", "W2", "b2", "W3", "b3", "w4", "b4"):
+        a, b = mlp.OFF[name]
+        ga, gr = g[a:b].astype(np.float64), gref[a:b]
+        rel = np.linalg.norm(ga - gr) / max(np.linalg.norm(gr), 1e-30)
+        cos = ga @ gr / max(np.linalg.norm(ga) * np.linalg.norm(gr), 1e-30)
+        assert rel <= 5e-2 and cos >= 0.998, (name, rel, cos)
+
+
+@pytest.fixture(scope="module")
+def trained(fc):
+    """Surrogate trained on every ray of a small head-like scan (GPU data)."""
+    wl = _head_small()
+    lab = wl.make_phantom()
+    g = wl.geom
+    sc = fc.Scanner(wl, labels=lab)
+    L = torch.empty((g.n_rays, len(wl.labels)), device="cuda")
+    fc.fc_project_lengths(sc.h, 0, g.n_angles, L)
+    y = torch.empty(g.n_rays, device="cuda")
+    fc.fc_energy_sum_lengths(sc.h, L, y)
+    fc.fc_surrogate_init(sc.h, 3)
+    hist = fc.fc_surrogate_train(sc.h, L, y, steps=3000, batch=4096, lr=2e-3, seed=3)
+    torch.cuda.synchronize()
+    yield wl, sc, L, y, hist
+    sc.close()
+
+
+def test_surrogate_training_gains_over_linear_model(fc, trained):
+    wl, sc, L, y, hist = trained
+    assert hist[-50:].mean() < 1e-2 * hist[:10].mean()
+    out = torch.empty_like(y)
+    fc.fc_surrogate_eval(sc.h, L, out)
+    torch.cuda.synchronize()
+    st = fc.fc_surrogate_get(sc.h)
+    mubar = st[34305 + 8:34305 + 16][:L.shape[1]]
+    Lh, yh, oh = L.cpu().numpy(), y.cpu().numpy(), out.cpu().numpy()
+    err_mlp = np.abs(oh - yh)
+    err_lin = np.abs(-(Lh @ mubar) - yh)
+    print("surrogate |d lnT|: max %.3e p99 %.3e; first-order model max %.3e"
+          % (err_mlp.max(), np.quantile(err_mlp, 0.99), err_lin.max()))
+    assert err_mlp.max() < 0.1 * err_lin.max()
+    assert np.quantile(err_mlp, 0.99) < 5e-3
+
+
+def test_surrogate_fallback_outside_box(fc, trained):
+    wl, sc, L, y, _ = trained
+    far = L[:256].clone()
+    far[:, 1] += 1000.0            # far outside the training box
+    exact = torch.empty(256, device="cuda")
+    fc.fc_energy_sum_lengths(sc.h, far, exact)
+    out = torch.empty(256, device="cuda")
+    nfb = fc.fc_surrogate_eval(sc.h, far, out)
+    torch.cuda.synchronize()
+    assert nfb == 256
+    assert torch.equal(out, exact)
+
+
+def test_surrogate_checkpoint_roundtrip(fc, trained):
+    wl, sc, L, y, _ = trained
+    st = fc.fc_surrogate_get(sc.h)
+    a = torch.empty_like(y)
+    fc.fc_surrogate_eval(sc.h, L, a)
+    sc2 = fc.Scanner(wl, labels=wl.make_phantom())
+    try:
+        fc.fc_surrogate_set(sc2.h, st)
+        b = torch.empty_like(y)
+        fc.fc_surrogate_eval(sc2.h, L, b)
+        torch.cuda.synchronize()
+        assert torch.equal(a, b)
+        assert np.array_equal(fc.fc_surrogate_get(sc2.h), st)
+    finally:
+        sc2.close()

@@ -385,3 +385,59 @@ def test_hu_and_cnr_definitions(orc):
     a, b = img[mask], img[roi]
     assert orc.cnr(img, mask, roi) == pytest.approx(
         abs(a.mean() - b.mean()) / math.sqrt(a.var() + b.var()))
+
+
+# ------------------------------------------------------------------ surrogate oracle
+def _mlp_params(seed, gain=1.0):
+    from oracle import mlp
+    rng = np.random.default_rng(seed)
+    P = np.zeros(mlp.N_PACKED)
+    for name, fan in (("W1", 8), ("W2", 128), ("W3", 128), ("w4", 128)):
+        a, b = mlp.OFF[name]
+        P[a:b] = rng.uniform(-1, 1, b - a) * gain * math.sqrt(3.0 / fan)
+    for name in ("b1", "b2", "b3", "b4"):
+        a, b = mlp.OFF[name]
+        P[a:b] = rng.normal(0, 0.1, b - a)
+    a, b = mlp.OFF["scale"]
+    P[a:b] = rng.uniform(0.05, 0.2, 8)
+    a, b = mlp.OFF["mubar"]
+    P[a:b] = rng.uniform(0.0, 0.5, 8)
+    a, b = mlp.OFF["box"]
+    P[a:b] = 100.0
+    return P
+
+
+def test_mlp_oracle_gradient_matches_finite_differences():
+    from oracle import mlp
+    rng = np.random.default_rng(7)
+    P = _mlp_params(1, gain=2.0)
+    L = rng.uniform(0, 10, (64, 8))
+    y = rng.normal(-2, 1, 64)
+    loss, g = mlp.loss_and_grad(P, L, y, round_weights=False)
+    idx = np.concatenate([rng.choice(np.arange(a, b), 6, replace=False) for (a, b) in
+                          [mlp.OFF[k] for k in ("W1", "b1", "W2", "b2", "W3", "b3", "w4")]] +
+                         [np.array([mlp.OFF["b4"][0]])])
+    for i in idx:
+        h = 1e-6 * max(1.0, abs(P[i]))
+        Pp, Pm = P.copy(), P.copy()
+        Pp[i] += h
+        Pm[i] -= h
+        fd = (mlp.loss(Pp, L, y, False) - mlp.loss(Pm, L, y, False)) / (2 * h)
+        assert abs(fd - g[i]) <= 1e-5 * abs(g[i]) + 1e-8, (i, fd, g[i])
+
+
+def test_mlp_oracle_linear_part_and_bf16():
+    from oracle import mlp
+    torch = pytest.importorskip("torch")
+    P = np.zeros(mlp.N_PACKED)
+    a, b = mlp.OFF["mubar"]
+    P[a:b] = np.linspace(0.1, 0.8, 8)
+    a, b = mlp.OFF["scale"]
+    P[a:b] = 0.1
+    L = np.random.default_rng(0).uniform(0, 5, (10, 7))
+    yh, _ = mlp.forward(P, L)
+    assert np.allclose(yh, -(L @ np.linspace(0.1, 0.8, 8)[:7]), rtol=0, atol=1e-13)
+    x = np.random.default_rng(1).normal(0, 10, 1000).astype(np.float32)
+    x[:4] = [1.00390625, 1.01171875, -3.0e-5, 65504.5]
+    ref = torch.from_numpy(x).to(torch.bfloat16).to(torch.float64).numpy()
+    assert np.array_equal(mlp.bf16(x), ref)
