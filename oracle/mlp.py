@@ -4,7 +4,7 @@ Only the tests may import this module.  The surrogate approximates ln T, the
 logarithm of the energy-weighted transmission of a ray (Sec. II.F, I_f
 equation), from the per-material path lengths L:
 
-    x      = bf16(L * scale)                       (8 input features)
+    x      = L * scale                             (8 input features)
     z1     = W1 x + b1,   h1 = SiLU(z1)            (128)
     z2     = W2 h1 + b2,  h2 = SiLU(z2)            (128)
     z3     = W3 h2 + b3,  h3 = SiLU(z3)            (128)
@@ -13,9 +13,10 @@ equation), from the per-material path lengths L:
 
 Parameters arrive as the packed vector of the C ABI (W1 [128][8], b1,
 W2 [128][128], b2, W3, b3, w4 [128], b4, scale [8], mubar [8], box [8]).
-With ``round_weights`` the three weight matrices and x are rounded to bf16,
-as the tensor cores see them; everything else is float64, with the exact
-SiLU.  The backward pass is the chain rule written out layer by layer
+With ``round_weights`` the three weight matrices are rounded to bf16, the
+operands the tensor cores multiply (the CUDA path carries inputs and
+activations as bf16 hi + lo pairs, i.e. to ~16 bits, which this reference
+does not round); everything else is float64, with the exact SiLU.  The backward pass is the chain rule written out layer by layer
 (pinned against central finite differences of ``loss`` in the tests).
 """
 from __future__ import annotations
@@ -72,7 +73,6 @@ def forward(P, L, round_weights=True):
     x = Lp * p["scale"][None, :]
     W1, W2, W3 = p["W1"], p["W2"], p["W3"]
     if round_weights:
-        x = bf16(x)
         W1, W2, W3 = bf16(W1), bf16(W2), bf16(W3)
     z1 = x @ W1.T + p["b1"]
     h1 = _silu(z1)

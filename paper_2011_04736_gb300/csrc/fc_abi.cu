@@ -687,7 +687,7 @@ static int sur_upload(fc_handle *h, const float *packed)
         w2t((size_t)H * H), w3t((size_t)H * H);
     for (int o = 0; o < H; ++o)
         for (int i = 0; i < 16; ++i)
-            w1[(size_t)o * 16 + i] = __float2bfloat16(i < fc::kMlpIn ? packed[fc::kOffW1 + o * fc::kMlpIn + i] : 0.0f);
+            w1[(size_t)o * 16 + i] = __float2bfloat16(packed[fc::kOffW1 + o * fc::kMlpIn + i % fc::kMlpIn]);
     for (int o = 0; o < H; ++o)
         for (int i = 0; i < H; ++i) {
             w2[(size_t)o * H + i] = w2t[(size_t)i * H + o] = __float2bfloat16(packed[fc::kOffW2 + o * H + i]);

@@ -92,7 +92,7 @@ constexpr int kMlpPacked = kOffBox + kMaxMat;
 constexpr int kWgradChunk = 1024;   // batch columns per split-K weight-gradient CTA
 
 struct SurrogateParams {
-    const __nv_bfloat16 *W1b;   // [128][16] (inputs 8..15 zero)
+    const __nv_bfloat16 *W1b;   // [128][16] (columns 8..15 repeat 0..7: lo parts of the inputs)
     const __nv_bfloat16 *W2b, *W3b;    // [out][in]
     const __nv_bfloat16 *W2Tb, *W3Tb;  // [in][out]
     const float *P;             // packed fp32 parameters

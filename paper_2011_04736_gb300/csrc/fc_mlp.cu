@@ -9,7 +9,11 @@
 // The three 128-wide layers run on the 5th-generation tensor cores
 // (tcgen05.mma kind::f16, bf16 operands in shared memory, f32 accumulators
 // in tensor memory); biases, SiLU and the 128 -> 1 output layer run in the
-// epilogues.  One CTA handles tiles of 128 rays; thread r of the 128 owns
+// epilogues.  Activations are carried as two bf16 parts, hi = bf16(h) and
+// lo = bf16(h - hi), and each layer multiplies both (W hi + W lo), so the
+// activations keep ~16 significant bits while every product is a bf16
+// tensor-core product; the 8 inputs use the same split, with the lo part in
+// the padded K columns 8..15 and W1 duplicated there.  One CTA handles tiles of 128 rays; thread r of the 128 owns
 // ray r of the tile (TMEM lane r).
 //
 // Training: a fused forward + backward kernel per 128-sample tile keeps the
@@ -124,25 +128,26 @@ __device__ __forceinline__ uint32_t trow(uint32_t tbase, int col)
     return tbase + ((uint32_t)(threadIdx.x & ~31) << 16) + (uint32_t)col;
 }
 
-// Epilogue: h = SiLU(acc + bias) of this thread's row -> bf16 row r of a
-// K-major operand (and, if ht != nullptr, feature-major global copy
-// ht[j * ldh + col]).
+// Epilogue: h = SiLU(acc + bias) of this thread's row -> row r of the
+// K-major operands dst (bf16(h)) and dlo (bf16(h - bf16(h))), and, if
+// ht != nullptr, the feature-major global copy ht[j * ldh + col] of bf16(h).
 __device__ __forceinline__ void epi_silu(uint32_t tacc, const float *bias, unsigned char *dst,
-                                         bf16 *ht, size_t ldh, size_t col)
+                                         unsigned char *dlo, bf16 *ht, size_t ldh, size_t col)
 {
     const int r = threadIdx.x;
 #pragma unroll 1
     for (int c0 = 0; c0 < kH; c0 += 16) {
         float v[16];
         tc::tmem_ld16(tacc + c0, v);
-        uint32_t p[8];
+        uint32_t p[8], q[8];
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
             const float a = silu(v[2 * i] + bias[c0 + 2 * i]);
             const float b = silu(v[2 * i + 1] + bias[c0 + 2 * i + 1]);
             p[i] = pack2(a, b);
+            const __nv_bfloat162 hb = *reinterpret_cast<const __nv_bfloat162 *>(&p[i]);
+            q[i] = pack2(a - __low2float(hb), b - __high2float(hb));
             if (ht) {
-                const __nv_bfloat162 hb = *reinterpret_cast<const __nv_bfloat162 *>(&p[i]);
                 ht[(size_t)(c0 + 2 * i) * ldh + col] = hb.x;
                 ht[(size_t)(c0 + 2 * i + 1) * ldh + col] = hb.y;
             }
@@ -151,7 +156,56 @@ __device__ __forceinline__ void epi_silu(uint32_t tacc, const float *bias, unsig
             make_uint4(p[0], p[1], p[2], p[3]);
         *reinterpret_cast<uint4 *>(dst + tc::kmajor_off(r, c0 + 8, kKgs128)) =
             make_uint4(p[4], p[5], p[6], p[7]);
+        *reinterpret_cast<uint4 *>(dlo + tc::kmajor_off(r, c0, kKgs128)) =
+            make_uint4(q[0], q[1], q[2], q[3]);
+        *reinterpret_cast<uint4 *>(dlo + tc::kmajor_off(r, c0 + 8, kKgs128)) =
+            make_uint4(q[4], q[5], q[6], q[7]);
     }
+}
+
+// Stage this thread's inputs x = L * scale as hi (K columns 0..7) and lo
+// (columns 8..15) parts into row r of the 128 x 16 operand; optionally the
+// feature-major copy xt[k * ldx + col].
+__device__ __forceinline__ void stage_x(unsigned char *sX, const float (&Lr)[kMaxMat],
+                                        const float *scale, bf16 *xt, size_t ldx, size_t col)
+{
+    uint32_t q[8];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const float a = Lr[2 * k] * scale[2 * k], b = Lr[2 * k + 1] * scale[2 * k + 1];
+        q[k] = pack2(a, b);
+        const __nv_bfloat162 hb = *reinterpret_cast<const __nv_bfloat162 *>(&q[k]);
+        q[k + 4] = pack2(a - __low2float(hb), b - __high2float(hb));
+    }
+    const int r = threadIdx.x;
+    *reinterpret_cast<uint4 *>(sX + tc::kmajor_off(r, 0, kKgs128)) = make_uint4(q[0], q[1], q[2], q[3]);
+    *reinterpret_cast<uint4 *>(sX + tc::kmajor_off(r, 8, kKgs128)) = make_uint4(q[4], q[5], q[6], q[7]);
+    if (xt) {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const __nv_bfloat162 hb = *reinterpret_cast<const __nv_bfloat162 *>(&q[k]);
+            xt[(size_t)(2 * k) * ldx + col] = hb.x;
+            xt[(size_t)(2 * k + 1) * ldx + col] = hb.y;
+        }
+    }
+}
+
+// Thread 0 issues D = A_hi B^T + A_lo B^T (K = 128) and commits; everyone
+// waits.  Returns false (and records the timeout) if the wait bound expires.
+__device__ __forceinline__ bool run_gemm_split(uint32_t d, const unsigned char *ahi,
+                                               const unsigned char *alo, const unsigned char *b,
+                                               uint64_t *mbar, uint32_t &phase, int *err)
+{
+    if (threadIdx.x == 0) {
+        issue_gemm(d, ahi, kKgs128, b, kKgs128, kH, kH, false);
+        issue_gemm(d, alo, kKgs128, b, kKgs128, kH, kH, true);
+        tc::mma_commit(mbar);
+    }
+    const bool ok = tc::mbar_wait(mbar, phase, kPolls);
+    phase ^= 1u;
+    tc::fence_after_sync();
+    if (!ok && threadIdx.x == 0) atomicExch(err, FC_ETIMEOUT);
+    return __syncthreads_and(ok);
 }
 
 // Exact ln T from path lengths: the projector's energy-integral epilogue.
@@ -174,7 +228,7 @@ __device__ __forceinline__ float exact_lnT(const float (&L)[kMaxMat], const floa
 
 // shared-memory map of the inference kernel (bytes)
 constexpr int kInfW1 = 0, kInfW2 = 4096, kInfW3 = 4096 + 32768, kInfX = 4096 + 2 * 32768,
-              kInfH = kInfX + 4096, kInfF = kInfH + 32768;
+              kInfH = kInfX + 4096, kInfHlo = kInfH + 32768, kInfF = kInfHlo + 32768;
 constexpr int kInfSmem = kInfF + (4 * kH + 3 * kMaxMat + 8) * 4;
 
 }  // namespace
@@ -188,7 +242,7 @@ k_mlp_eval(const __grid_constant__ SurrogateParams p, const float *__restrict__ 
     __shared__ uint64_t mbar;
     __shared__ uint32_t tbase_s;
     unsigned char *sW1 = smem + kInfW1, *sW2 = smem + kInfW2, *sW3 = smem + kInfW3;
-    unsigned char *sX = smem + kInfX, *sH = smem + kInfH;
+    unsigned char *sX = smem + kInfX, *sH = smem + kInfH, *sHlo = smem + kInfHlo;
     float *fb = reinterpret_cast<float *>(smem + kInfF);
     float *b1 = fb, *b2 = fb + kH, *b3 = fb + 2 * kH, *w4 = fb + 3 * kH;
     float *scale = fb + 4 * kH, *mubar = scale + kMaxMat, *box = mubar + kMaxMat;
@@ -228,23 +282,15 @@ k_mlp_eval(const __grid_constant__ SurrogateParams p, const float *__restrict__ 
             ylin = fmaf(-mubar[m], Lr[m], ylin);
             outside = outside || Lr[m] > box[m];
         }
-        {
-            uint32_t q[8];
-#pragma unroll
-            for (int k = 0; k < 4; ++k) q[k] = pack2(Lr[2 * k] * scale[2 * k], Lr[2 * k + 1] * scale[2 * k + 1]);
-#pragma unroll
-            for (int k = 4; k < 8; ++k) q[k] = 0u;
-            *reinterpret_cast<uint4 *>(sX + tc::kmajor_off(r, 0, kKgs128)) = make_uint4(q[0], q[1], q[2], q[3]);
-            *reinterpret_cast<uint4 *>(sX + tc::kmajor_off(r, 8, kKgs128)) = make_uint4(q[4], q[5], q[6], q[7]);
-        }
+        stage_x(sX, Lr, scale, nullptr, 0, 0);
         sync_for_mma();
         if (!run_gemm(tb, sX, kKgs128, sW1, kKgs128, kInP, kH, &mbar, phase, err)) break;
-        epi_silu(trow(tb, 0), b1, sH, nullptr, 0, 0);
+        epi_silu(trow(tb, 0), b1, sH, sHlo, nullptr, 0, 0);
         sync_for_mma();
-        if (!run_gemm(tb, sH, kKgs128, sW2, kKgs128, kH, kH, &mbar, phase, err)) break;
-        epi_silu(trow(tb, 0), b2, sH, nullptr, 0, 0);
+        if (!run_gemm_split(tb, sH, sHlo, sW2, &mbar, phase, err)) break;
+        epi_silu(trow(tb, 0), b2, sH, sHlo, nullptr, 0, 0);
         sync_for_mma();
-        if (!run_gemm(tb, sH, kKgs128, sW3, kKgs128, kH, kH, &mbar, phase, err)) break;
+        if (!run_gemm_split(tb, sH, sHlo, sW3, &mbar, phase, err)) break;
         float res = b4;
 #pragma unroll 1
         for (int c0 = 0; c0 < kH; c0 += 16) {
@@ -360,32 +406,17 @@ k_mlp_train(const __grid_constant__ SurrogateParams p, const float *__restrict__
             ylin = fmaf(-mubar[m], Lr[m], ylin);
         }
         const float yt = valid ? y[idx] : 0.0f;
-        {
-            uint32_t q[8];
-#pragma unroll
-            for (int k = 0; k < 4; ++k) q[k] = pack2(Lr[2 * k] * scale[2 * k], Lr[2 * k + 1] * scale[2 * k + 1]);
-#pragma unroll
-            for (int k = 4; k < 8; ++k) q[k] = 0u;
-            *reinterpret_cast<uint4 *>(sX + tc::kmajor_off(r, 0, kKgs128)) = make_uint4(q[0], q[1], q[2], q[3]);
-            *reinterpret_cast<uint4 *>(sX + tc::kmajor_off(r, 8, kKgs128)) = make_uint4(q[4], q[5], q[6], q[7]);
-            if (valid) {
-#pragma unroll
-                for (int k = 0; k < 8; ++k) {
-                    const __nv_bfloat162 hb = *reinterpret_cast<const __nv_bfloat162 *>(&q[k]);
-                    w.xt[(size_t)(2 * k) * B + col] = hb.x;
-                    w.xt[(size_t)(2 * k + 1) * B + col] = hb.y;
-                }
-            }
-        }
+        stage_x(sX, Lr, scale, valid ? w.xt : nullptr, B, col);
         sync_for_mma();
-        // forward: Z1, Z2, Z3 stay in TMEM columns [0,128), [128,256), [256,384)
+        // forward: Z1, Z2, Z3 stay in TMEM columns [0,128), [128,256), [256,384);
+        // sD holds the lo parts of the activations until the backward pass
         if (!run_gemm(tb, sX, kKgs128, sW1, kKgs128, kInP, kH, &mbar, phase, err)) break;
-        epi_silu(tZ1, b1, sH, valid ? w.h1t : nullptr, B, col);
+        epi_silu(tZ1, b1, sH, sD, valid ? w.h1t : nullptr, B, col);
         sync_for_mma();
-        if (!run_gemm(tb + 128, sH, kKgs128, sW2, kKgs128, kH, kH, &mbar, phase, err)) break;
-        epi_silu(tZ2, b2, sH, valid ? w.h2t : nullptr, B, col);
+        if (!run_gemm_split(tb + 128, sH, sD, sW2, &mbar, phase, err)) break;
+        epi_silu(tZ2, b2, sH, sD, valid ? w.h2t : nullptr, B, col);
         sync_for_mma();
-        if (!run_gemm(tb + 256, sH, kKgs128, sW3, kKgs128, kH, kH, &mbar, phase, err)) break;
+        if (!run_gemm_split(tb + 256, sH, sD, sW3, &mbar, phase, err)) break;
         float res = b4;
 #pragma unroll 1
         for (int c0 = 0; c0 < kH; c0 += 16) {
@@ -570,8 +601,8 @@ __global__ void k_mlp_adam(MlpWork w, int n_chunks, float *P, float *m1, float *
         for (int c = 0; c < n_chunks; ++c) s += w.rsum[((size_t)job * n_chunks + c) * kH + row];
         return s;
     };
-    if (i < kOffB1) {                       // W1 [128][8]
-        g = part(2, i / kMlpIn, i % kMlpIn, 16);
+    if (i < kOffB1) {                       // W1 [128][8], shared by the hi and lo inputs
+        g = part(2, i / kMlpIn, i % kMlpIn, 16) + part(2, i / kMlpIn, kMlpIn + i % kMlpIn, 16);
     } else if (i < kOffW2) {
         g = rsum(2, i - kOffB1);
     } else if (i < kOffB2) {
@@ -604,6 +635,7 @@ __global__ void k_mlp_adam(MlpWork w, int n_chunks, float *P, float *m1, float *
     if (i < kOffB1) {
         const int o = i / kMlpIn, in = i % kMlpIn;
         W1b[o * kInP + in] = pb;
+        W1b[o * kInP + kMlpIn + in] = pb;
     } else if (i >= kOffW2 && i < kOffB2) {
         const int j = i - kOffW2, o = j / kH, in = j % kH;
         W2b[o * kH + in] = pb;
@@ -657,7 +689,7 @@ cudaError_t launch_mlp_eval(const SurrogateParams &p, const float *L, long long 
                                          kInfSmem);
     if (e != cudaSuccess) return e;
     const long long ntiles = (n + 127) / 128;
-    const int grid = (int)(ntiles < 152 * 2 ? ntiles : 152 * 2);
+    const int grid = (int)(ntiles < 152 ? ntiles : 152);   // one CTA per SM (141 KB smem)
     k_mlp_eval<<<grid, 128, kInfSmem, s>>>(p, L, n, lnT, n_fallback, err);
     return cudaGetLastError();
 }
