@@ -196,24 +196,27 @@ int fc_profile_read(fc_handle *h, double *ms, int64_t *launches);
  * The projector's energy loop evaluates, per ray, the I_f equation of
  * Sec. II.F: T = sum_E (w D)_E exp(-sum_m mu_m(E) L_m) / sum_E (w D)_E.  The
  * surrogate approximates ln T from the per-material path lengths L with
- *   ln T ~ -sum_m mubar_m L_m + MLP(L * scale),
- *   mubar_m = sum_E (w D)_E mu_m(E) / sum_E (w D)_E,
- *   MLP 8 -> 128 -> 128 -> 128 -> 1, SiLU (sigma via tanh), bf16 weights and
- *   activations on the tensor cores with f32 accumulation.
+ *   ln T ~ ln sum_k a_k exp(-sum_m mu_km L_m) + MLP(L * scale),
+ *   the baseline being the same integral with the spectrum lumped into four
+ *   groups of equal weight (a_k group weight, mu_km weight-averaged mu_m(E);
+ *   one group would give the first-order term -mubar . L), and
+ *   MLP 8 -> 128 -> 128 -> 128 -> 1, SiLU (sigma via tanh), bf16 weights,
+ *   activations as bf16 hi + lo pairs, tensor cores with f32 accumulation.
  * Path lengths are float [n][n_mat] and ln T float [n], in device memory.
  * The handle's spectrum (fc_set_spectrum_detector) must be set first.
  *
  * Parameter state (fc_surrogate_get/set), FC_SURROGATE_STATE floats:
  *   [0, 34305): W1[128][8], b1[128], W2[128][128], b2, W3[128][128], b3,
  *               w4[128], b4 (fp32 master copies; W[out][in]);
- *   then scale[8], mubar[8], box[8] (inputs are L * scale; rays with any
- *   L_m > box_m are evaluated exactly); then Adam first and second moments
- *   (34305 each) and the Adam step count. */
+ *   then scale[8] (inputs are L * scale), a[4], mu[4][8] (baseline) and
+ *   box[8] (rays with any L_m > box_m are evaluated exactly); then Adam
+ *   first and second moments (34305 each) and the Adam step count. */
 #define FC_SURROGATE_PARAMS 34305
-#define FC_SURROGATE_STATE  (34305 + 24 + 2 * 34305 + 1)
+#define FC_SURROGATE_STATE  (34305 + 52 + 2 * 34305 + 1)
 
 /* Initialise the surrogate with seeded random weights (uniform, scaled by
- * fan-in), mubar from the current spectrum, unit scale and an unbounded box.
+ * fan-in), the baseline groups from the current spectrum, unit scale and an
+ * unbounded box.
  * Errors: FC_ESTATE (no spectrum), FC_ENOMEM, FC_ECUDA. */
 int fc_surrogate_init(fc_handle *h, uint64_t seed);
 

@@ -8,11 +8,13 @@ equation), from the per-material path lengths L:
     z1     = W1 x + b1,   h1 = SiLU(z1)            (128)
     z2     = W2 h1 + b2,  h2 = SiLU(z2)            (128)
     z3     = W3 h2 + b3,  h3 = SiLU(z3)            (128)
-    y_hat  = -mubar . L + w4 . h3 + b4
+    y_hat  = ln sum_k a_k exp(-mu_k . L) + w4 . h3 + b4   (k = 1..4 groups)
     loss   = mean_b (y_hat - y)^2,    SiLU(z) = z / (1 + exp(-z))
 
 Parameters arrive as the packed vector of the C ABI (W1 [128][8], b1,
-W2 [128][128], b2, W3, b3, w4 [128], b4, scale [8], mubar [8], box [8]).
+W2 [128][128], b2, W3, b3, w4 [128], b4, scale [8], a [4], mu [4][8],
+box [8]); (a, mu) is the energy integral with the spectrum lumped into four
+groups (its one-group form is the first-order term -mubar . L).
 With ``round_weights`` the three weight matrices are rounded to bf16, the
 operands the tensor cores multiply (the CUDA path carries inputs and
 activations as bf16 hi + lo pairs, i.e. to ~16 bits, which this reference
@@ -32,9 +34,10 @@ for _name, _size in (("W1", H * NIN), ("b1", H), ("W2", H * H), ("b2", H), ("W3"
     _o += _size
 N_PARAMS = _o
 OFF["scale"] = (_o, _o + 8)
-OFF["mubar"] = (_o + 8, _o + 16)
-OFF["box"] = (_o + 16, _o + 24)
-N_PACKED = _o + 24
+OFF["ga"] = (_o + 8, _o + 12)
+OFF["gmu"] = (_o + 12, _o + 44)
+OFF["box"] = (_o + 44, _o + 52)
+N_PACKED = _o + 52
 
 
 def bf16(a):
@@ -80,7 +83,8 @@ def forward(P, L, round_weights=True):
     h2 = _silu(z2)
     z3 = h2 @ W3.T + p["b3"]
     h3 = _silu(z3)
-    y = -(Lp @ p["mubar"]) + h3 @ p["w4"] + p["b4"][0]
+    base = np.log(np.exp(-(Lp @ p["gmu"].reshape(4, NIN).T)) @ p["ga"])
+    y = base + h3 @ p["w4"] + p["b4"][0]
     return y, dict(x=x, z1=z1, h1=h1, z2=z2, h2=h2, z3=z3, h3=h3, W2=W2, W3=W3)
 
 

@@ -746,12 +746,30 @@ int fc_surrogate_init(fc_handle *h, uint64_t seed)
     for (int i = 0; i < H * H; ++i) P[fc::kOffW2 + i] = unif(sqrt(3.0 / H));
     for (int i = 0; i < H * H; ++i) P[fc::kOffW3 + i] = unif(sqrt(3.0 / H));
     for (int i = 0; i < H; ++i) P[fc::kOffW4 + i] = unif(0.1 * sqrt(3.0 / H));
+    // Spectral groups: consecutive energy bins split where the cumulative
+    // weight w D crosses 1/4, 1/2, 3/4; each group keeps its total weight and
+    // its weight-averaged attenuation.
     const double log2e = 1.4426950408889634;
+    double tot = 0.0;
+    for (int e = 0; e < h->n_e; ++e) tot += h->wd[e];
+    double ga[fc::kMlpGroups] = {0}, gm[fc::kMlpGroups][fc::kMaxMat] = {{0}};
+    double cum = 0.0;
+    for (int e = 0; e < h->n_e; ++e) {
+        const double mid = (cum + 0.5 * h->wd[e]) / tot;
+        cum += h->wd[e];
+        int k = (int)(mid * fc::kMlpGroups);
+        k = k < 0 ? 0 : (k >= fc::kMlpGroups ? fc::kMlpGroups - 1 : k);
+        ga[k] += h->wd[e];
+        for (int m = 0; m < fc::kMaxMat; ++m)
+            gm[k][m] += (double)h->wd[e] * h->mu2[(size_t)e * fc::kMaxMat + m] / log2e;
+    }
+    for (int k = 0; k < fc::kMlpGroups; ++k) {
+        P[fc::kOffGa + k] = (float)(ga[k] / tot);
+        for (int m = 0; m < fc::kMaxMat; ++m)
+            P[fc::kOffGmu + k * fc::kMaxMat + m] = ga[k] > 0.0 ? (float)(gm[k][m] / ga[k]) : 0.0f;
+    }
     for (int m = 0; m < fc::kMaxMat; ++m) {
-        double mb = 0.0;
-        for (int e = 0; e < h->n_e; ++e) mb += (double)h->wd[e] * h->mu2[(size_t)e * fc::kMaxMat + m] / log2e;
         P[fc::kOffScale + m] = 1.0f;
-        P[fc::kOffMubar + m] = (float)mb;
         P[fc::kOffBox + m] = INFINITY;
     }
     rc = sur_upload(h, P.data());

@@ -75,7 +75,8 @@ void set_last_error(const char *msg);
 constexpr int kMlpHidden = 128;
 constexpr int kMlpIn = 8;
 // packed fp32 parameter vector: W1 [128][8], b1, W2 [128][128], b2, W3, b3,
-// w4 [128], b4, then input scale [8], mubar [8] and the training box [8]
+// w4 [128], b4, then input scale [8], the spectral-group baseline (weights
+// a[4], attenuation mu[4][8]) and the training box [8]
 constexpr int kOffW1 = 0;
 constexpr int kOffB1 = kOffW1 + kMlpHidden * kMlpIn;
 constexpr int kOffW2 = kOffB1 + kMlpHidden;
@@ -85,9 +86,11 @@ constexpr int kOffB3 = kOffW3 + kMlpHidden * kMlpHidden;
 constexpr int kOffW4 = kOffB3 + kMlpHidden;
 constexpr int kOffB4 = kOffW4 + kMlpHidden;
 constexpr int kMlpParams = kOffB4 + 1;
+constexpr int kMlpGroups = 4;
 constexpr int kOffScale = kMlpParams;
-constexpr int kOffMubar = kOffScale + kMaxMat;
-constexpr int kOffBox = kOffMubar + kMaxMat;
+constexpr int kOffGa = kOffScale + kMaxMat;
+constexpr int kOffGmu = kOffGa + kMlpGroups;
+constexpr int kOffBox = kOffGmu + kMlpGroups * kMaxMat;
 constexpr int kMlpPacked = kOffBox + kMaxMat;
 constexpr int kWgradChunk = 1024;   // batch columns per split-K weight-gradient CTA
 

@@ -2,9 +2,12 @@
 // path lengths L of a ray (the quantity the projector's energy loop
 // computes, paper Sec. II.F, I_f equation), replacing the N_E-bin sum.
 //
-//   ln T ~ -sum_m mubar_m L_m + MLP(L * scale)
-//   MLP: 8 -> 128 -> 128 -> 128 -> 1, SiLU activations,
-//   mubar = sum_E (w D)_E mu_m(E) / sum_E (w D)_E  (first-order term)
+//   ln T ~ ln sum_k a_k exp(-sum_m mu_km L_m) + MLP(L * scale)
+//   MLP: 8 -> 128 -> 128 -> 128 -> 1, SiLU activations.
+// The baseline is the energy integral with the spectrum lumped into four
+// groups of equal weight (a_k = group weight, mu_km = group-mean
+// attenuation); with one group it is the first-order term -mubar . L.  The
+// network learns the residual of this baseline.
 //
 // The three 128-wide layers run on the 5th-generation tensor cores
 // (tcgen05.mma kind::f16, bf16 operands in shared memory, f32 accumulators
@@ -226,10 +229,25 @@ __device__ __forceinline__ float exact_lnT(const float (&L)[kMaxMat], const floa
     return logf(sum);
 }
 
+// Spectral-group baseline ln sum_k a_k exp(-sum_m mu_km L_m); g holds a[4]
+// then mu[4][8] (mu in 1/cm).
+__device__ __forceinline__ float group_base(const float (&L)[kMaxMat], const float *g)
+{
+    float s = 0.0f;
+#pragma unroll
+    for (int k = 0; k < kMlpGroups; ++k) {
+        float a = 0.0f;
+#pragma unroll
+        for (int m = 0; m < kMaxMat; ++m) a = fmaf(g[kMlpGroups + k * kMaxMat + m], L[m], a);
+        s = fmaf(g[k], __expf(-a), s);
+    }
+    return __logf(s);
+}
+
 // shared-memory map of the inference kernel (bytes)
 constexpr int kInfW1 = 0, kInfW2 = 4096, kInfW3 = 4096 + 32768, kInfX = 4096 + 2 * 32768,
               kInfH = kInfX + 4096, kInfHlo = kInfH + 32768, kInfF = kInfHlo + 32768;
-constexpr int kInfSmem = kInfF + (4 * kH + 3 * kMaxMat + 8) * 4;
+constexpr int kInfSmem = kInfF + (4 * kH + 2 * kMaxMat + kMlpGroups * (kMaxMat + 1) + 8) * 4;
 
 }  // namespace
 
@@ -245,7 +263,7 @@ k_mlp_eval(const __grid_constant__ SurrogateParams p, const float *__restrict__ 
     unsigned char *sX = smem + kInfX, *sH = smem + kInfH, *sHlo = smem + kInfHlo;
     float *fb = reinterpret_cast<float *>(smem + kInfF);
     float *b1 = fb, *b2 = fb + kH, *b3 = fb + 2 * kH, *w4 = fb + 3 * kH;
-    float *scale = fb + 4 * kH, *mubar = scale + kMaxMat, *box = mubar + kMaxMat;
+    float *scale = fb + 4 * kH, *box = scale + kMaxMat, *grp = box + kMaxMat;
     const int r = threadIdx.x;
     if (r < 32) tc::tmem_alloc(&tbase_s, 128);
     if (r == 0) tc::mbar_init(&mbar, 1);
@@ -261,9 +279,9 @@ k_mlp_eval(const __grid_constant__ SurrogateParams p, const float *__restrict__ 
     }
     if (r < kMaxMat) {
         scale[r] = P[kOffScale + r];
-        mubar[r] = P[kOffMubar + r];
         box[r] = P[kOffBox + r];
     }
+    if (r < kMlpGroups * (kMaxMat + 1)) grp[r] = P[kOffGa + r];
     const float b4 = P[kOffB4];
     sync_for_mma();
     const uint32_t tb = tbase_s;
@@ -274,14 +292,13 @@ k_mlp_eval(const __grid_constant__ SurrogateParams p, const float *__restrict__ 
         const long long i = tile * 128 + r;
         const bool valid = i < n;
         float Lr[kMaxMat];
-        float ylin = 0.0f;
         bool outside = false;
 #pragma unroll
         for (int m = 0; m < kMaxMat; ++m) {
             Lr[m] = (valid && m < p.n_mat) ? L[i * p.n_mat + m] : 0.0f;
-            ylin = fmaf(-mubar[m], Lr[m], ylin);
             outside = outside || Lr[m] > box[m];
         }
+        const float ylin = group_base(Lr, grp);
         stage_x(sX, Lr, scale, nullptr, 0, 0);
         sync_for_mma();
         if (!run_gemm(tb, sX, kKgs128, sW1, kKgs128, kInP, kH, &mbar, phase, err)) break;
@@ -337,7 +354,7 @@ namespace {
 constexpr int kTrW1 = 0, kTrW2 = 4096, kTrW3 = kTrW2 + 32768, kTrW2T = kTrW3 + 32768,
               kTrW3T = kTrW2T + 32768, kTrX = kTrW3T + 32768, kTrH = kTrX + 4096,
               kTrD = kTrH + 32768, kTrF = kTrD + 32768;
-constexpr int kTrSmem = kTrF + (4 * kH + 2 * kMaxMat + 8) * 4;
+constexpr int kTrSmem = kTrF + (4 * kH + kMaxMat + kMlpGroups * (kMaxMat + 1) + 8) * 4;
 
 __device__ __forceinline__ unsigned long long mix64(unsigned long long z)
 {
@@ -366,7 +383,7 @@ k_mlp_train(const __grid_constant__ SurrogateParams p, const float *__restrict__
     unsigned char *sX = smem + kTrX, *sH = smem + kTrH, *sD = smem + kTrD;
     float *fb = reinterpret_cast<float *>(smem + kTrF);
     float *b1 = fb, *b2 = fb + kH, *b3 = fb + 2 * kH, *w4 = fb + 3 * kH;
-    float *scale = fb + 4 * kH, *mubar = scale + kMaxMat;
+    float *scale = fb + 4 * kH, *grp = scale + kMaxMat;
     const int r = threadIdx.x;
     if (r < 32) tc::tmem_alloc(&tbase_s, 512);
     if (r == 0) tc::mbar_init(&mbar, 1);
@@ -382,10 +399,8 @@ k_mlp_train(const __grid_constant__ SurrogateParams p, const float *__restrict__
         b3[i] = P[kOffB3 + i];
         w4[i] = P[kOffW4 + i];
     }
-    if (r < kMaxMat) {
-        scale[r] = P[kOffScale + r];
-        mubar[r] = P[kOffMubar + r];
-    }
+    if (r < kMaxMat) scale[r] = P[kOffScale + r];
+    if (r < kMlpGroups * (kMaxMat + 1)) grp[r] = P[kOffGa + r];
     const float b4 = P[kOffB4];
     sync_for_mma();
     const uint32_t tb = tbase_s;
@@ -399,12 +414,10 @@ k_mlp_train(const __grid_constant__ SurrogateParams p, const float *__restrict__
         const bool valid = col < B;
         long long idx = col;
         if (sample) idx = (long long)(mix64(seed ^ mix64(((unsigned long long)step << 32) | (unsigned)col)) % (unsigned long long)n);
-        float Lr[kMaxMat], ylin = 0.0f;
+        float Lr[kMaxMat];
 #pragma unroll
-        for (int m = 0; m < kMaxMat; ++m) {
-            Lr[m] = (valid && m < p.n_mat) ? L[idx * p.n_mat + m] : 0.0f;
-            ylin = fmaf(-mubar[m], Lr[m], ylin);
-        }
+        for (int m = 0; m < kMaxMat; ++m) Lr[m] = (valid && m < p.n_mat) ? L[idx * p.n_mat + m] : 0.0f;
+        const float ylin = group_base(Lr, grp);
         const float yt = valid ? y[idx] : 0.0f;
         stage_x(sX, Lr, scale, valid ? w.xt : nullptr, B, col);
         sync_for_mma();

@@ -31,7 +31,7 @@ ENTRY_POINTS = ("fc_create", "fc_destroy", "fc_last_error", "fc_set_geometry", "
                 "fc_energy_sum_lengths")
 FC_STATIC_SCRATCH_FLOATS = 8 << 20
 FC_SURROGATE_PARAMS = 34305
-FC_SURROGATE_STATE = 34305 + 24 + 2 * 34305 + 1
+FC_SURROGATE_STATE = 34305 + 52 + 2 * 34305 + 1
 FC_K_NAMES = ("project", "blur_rows", "blur_cols", "fdk_filter", "backproject", "hu", "lengths",
               "noise", "surrogate_eval", "surrogate_train", "energy_sum")
 

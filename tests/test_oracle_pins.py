@@ -400,8 +400,10 @@ def _mlp_params(seed, gain=1.0):
         P[a:b] = rng.normal(0, 0.1, b - a)
     a, b = mlp.OFF["scale"]
     P[a:b] = rng.uniform(0.05, 0.2, 8)
-    a, b = mlp.OFF["mubar"]
-    P[a:b] = rng.uniform(0.0, 0.5, 8)
+    a, b = mlp.OFF["ga"]
+    P[a:b] = rng.dirichlet(np.ones(4))
+    a, b = mlp.OFF["gmu"]
+    P[a:b] = rng.uniform(0.0, 0.5, 32)
     a, b = mlp.OFF["box"]
     P[a:b] = 100.0
     return P
@@ -426,17 +428,33 @@ def test_mlp_oracle_gradient_matches_finite_differences():
         assert abs(fd - g[i]) <= 1e-5 * abs(g[i]) + 1e-8, (i, fd, g[i])
 
 
-def test_mlp_oracle_linear_part_and_bf16():
+def test_mlp_oracle_baseline_and_bf16(orc):
+    """With zero network weights the surrogate is its spectral-group
+    baseline: one group gives Beer-Lambert with the mean attenuation, and
+    groups equal to the energy bins give the exact energy sum."""
     from oracle import mlp
     torch = pytest.importorskip("torch")
     P = np.zeros(mlp.N_PACKED)
-    a, b = mlp.OFF["mubar"]
-    P[a:b] = np.linspace(0.1, 0.8, 8)
+    a, b = mlp.OFF["ga"]
+    P[a:b] = [1.0, 0, 0, 0]
+    a, b = mlp.OFF["gmu"]
+    P[a:a + 8] = np.linspace(0.1, 0.8, 8)
     a, b = mlp.OFF["scale"]
     P[a:b] = 0.1
     L = np.random.default_rng(0).uniform(0, 5, (10, 7))
     yh, _ = mlp.forward(P, L)
-    assert np.allclose(yh, -(L @ np.linspace(0.1, 0.8, 8)[:7]), rtol=0, atol=1e-13)
+    assert np.allclose(yh, -(L @ np.linspace(0.1, 0.8, 8)[:7]), rtol=0, atol=1e-12)
+    # four "groups" that are exactly four energy bins reproduce the energy sum
+    w, d = np.array([0.1, 0.4, 0.3, 0.2]), np.array([0.9, 0.8, 0.7, 0.5])
+    mu = np.random.default_rng(2).uniform(0.05, 0.6, (4, 7))
+    P2 = np.zeros(mlp.N_PACKED)
+    a, b = mlp.OFF["ga"]
+    P2[a:b] = w * d / np.sum(w * d)
+    a, b = mlp.OFF["gmu"]
+    P2[a:b] = np.pad(mu, ((0, 0), (0, 1))).ravel()
+    yh2, _ = mlp.forward(P2, L)
+    ref = [math.log(orc.energy_sum(w, d, mu, Lr)) for Lr in L]
+    assert np.allclose(yh2, ref, rtol=0, atol=1e-12)
     x = np.random.default_rng(1).normal(0, 10, 1000).astype(np.float32)
     x[:4] = [1.00390625, 1.01171875, -3.0e-5, 65504.5]
     ref = torch.from_numpy(x).to(torch.bfloat16).to(torch.float64).numpy()
