@@ -255,6 +255,33 @@ int fc_surrogate_eval(fc_handle *h, const float *L, int64_t n, float *lnT, int64
  * FC_ECUDA. */
 int fc_energy_sum_lengths(fc_handle *h, const float *L, int64_t n, float *lnT, void *stream);
 
+/* ---- Gradient of an image-quality objective (adjoint) ----
+ * J = sum_r CNR_r over the insert ROIs, CNR_r = |HU_w - HU_r| /
+ * sqrt(s_w^2 + s_r^2) (Sec. II.G, CNR equation; HU normalised on the water
+ * region of fc_set_water_roi), for the FDK image of the simulated scan with
+ *   spectrum w = softmax(logits) and detector response D (Sec. II.F, I_f
+ *   equation; the handle's attenuation table mu_m(E) at nominal densities),
+ *   voxel densities rho: each voxel of label m attenuates as
+ *   mu_m(E) rho_v / rho_nominal[m],
+ *   detector blur and scatter of the handle (Sec. II.E, II.G),
+ *   Poisson noise in its Gaussian form K = I + sqrt(I) z with a fixed
+ *   standard-normal field z [n_angles][n_v][n_u] (device; NULL: K = I),
+ *   FDK as in fc_reconstruct.
+ * ROI r: voxel centres within radius_cm of (cx_cm, cy_cm), on the slices of
+ * the water region.  Writes J (host) and, where non-NULL, dJ/dlogits and
+ * dJ/dD (host, [n_e]) and dJ/drho (device, [nz][ny][nx] float), computed by
+ * the adjoint of every step (projector recomputing each ray's path lengths).
+ * rho is float [nz][ny][nx] in device memory; rho_nominal is [n_mat] host.
+ * Uses the handle's projection and volume buffers (overwriting them).
+ * Errors: FC_ESTATE, FC_EINVAL, FC_ENOMEM, FC_ECUDA. */
+typedef struct fc_cnr_roi {
+    double cx_cm, cy_cm, radius_cm;
+} fc_cnr_roi;
+
+int fc_cnr_grad(fc_handle *h, const double *logits, const double *D, const double *rho_nominal,
+                const float *rho, const float *z, int n_roi, const fc_cnr_roi *rois, double *J,
+                double *g_logits, double *g_D, float *g_rho, void *stream);
+
 /* Allocation-free detector blur.  The paper has no counterpart: this entry
  * point exists for callers that cannot allocate device memory while they
  * run -- their device memory is owned by another allocator (for example a

@@ -99,6 +99,10 @@ struct fc_handle {
     std::vector<cudaEvent_t> pool;
     double prof_ms[FC_K_COUNT] = {0};
     int64_t prof_n[FC_K_COUNT] = {0};
+    // adjoint of the CNR objective
+    float *d_I = nullptr, *d_gI = nullptr, *d_gT = nullptr, *d_gtmp = nullptr, *d_gf = nullptr;
+    float *d_gmu = nullptr;
+    double *d_gwd = nullptr;
     // learned surrogate of the energy integral
     bool has_sur = false, sur_fitted = false;
     int sur_step = 0;
@@ -134,6 +138,13 @@ struct fc_handle {
         pending.clear();
         for (auto e : pool) cudaEventDestroy(e);
         pool.clear();
+        dfree(d_I);
+        dfree(d_gI);
+        dfree(d_gT);
+        dfree(d_gtmp);
+        dfree(d_gf);
+        dfree(d_gmu);
+        dfree(d_gwd);
         dfree(d_P);
         dfree(d_m1);
         dfree(d_m2);
@@ -314,6 +325,12 @@ int fc_set_geometry(fc_handle *h, const fc_geometry *g)
         h->has_counts = false;
     }
     dfree(h->d_filt);  // its size follows the reachable detector rows
+    dfree(h->d_I);
+    dfree(h->d_gI);
+    dfree(h->d_gT);
+    dfree(h->d_gtmp);
+    dfree(h->d_gf);
+    dfree(h->d_gmu);
     if (vox != h->vol_elems) {
         dfree(h->d_vol);
         dfree(h->d_hu);
@@ -998,6 +1015,132 @@ int fc_energy_sum_lengths(fc_handle *h, const float *L, int64_t n, float *lnT, v
     Trace t(h, FC_K_ENERGY_SUM, 1, s);
     FC_CK(fc::launch_energy_sum_lengths(p, L, n, lnT, s));
     t.end();
+    return FC_OK;
+}
+
+int fc_cnr_grad(fc_handle *h, const double *logits, const double *D, const double *rho_nominal,
+                const float *rho, const float *z, int n_roi, const fc_cnr_roi *rois, double *J,
+                double *g_logits, double *g_D, float *g_rho, void *stream)
+{
+    if (!h || !logits || !D || !rho_nominal || !rho || !J || (n_roi > 0 && !rois))
+        return fail(FC_EINVAL, "fc_cnr_grad: null argument");
+    if (!h->has_geom || !h->has_phantom || !h->has_spec)
+        return fail(FC_ESTATE, "fc_cnr_grad: geometry, phantom and spectrum must be set");
+    if (n_roi < 1 || n_roi > fc::kMaxRoi) return fail(FC_EINVAL, "fc_cnr_grad: n_roi outside [1, %d]", fc::kMaxRoi);
+    for (int m = 0; m < h->n_mat; ++m)
+        if (!(rho_nominal[m] > 0.0)) return fail(FC_EINVAL, "fc_cnr_grad: nominal densities must be > 0");
+    DeviceGuard dgd(h->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    int rc = ensure_proj_buffers(h);
+    if (rc) return rc;
+    rc = ensure_recon_buffers(h, s);
+    if (rc) return rc;
+    const size_t np = h->proj_elems, nv = h->vol_elems;
+    if (!h->d_I) FC_CK(cudaMalloc((void **)&h->d_I, np * sizeof(float)));
+    if (!h->d_gI) FC_CK(cudaMalloc((void **)&h->d_gI, np * sizeof(float)));
+    if (!h->d_gT) FC_CK(cudaMalloc((void **)&h->d_gT, np * sizeof(float)));
+    if (!h->d_gtmp) FC_CK(cudaMalloc((void **)&h->d_gtmp, np * sizeof(float)));
+    if (!h->d_gf) FC_CK(cudaMalloc((void **)&h->d_gf, h->filt_elems * sizeof(float)));
+    if (!h->d_gmu) FC_CK(cudaMalloc((void **)&h->d_gmu, nv * sizeof(float)));
+    if (!h->d_gwd) FC_CK(cudaMalloc((void **)&h->d_gwd, (fc::kMaxBins + 1) * sizeof(double)));
+    // spectrum: w = softmax(logits), c = w D, wd = c / sum c
+    const int ne = h->n_e;
+    std::vector<double> w(ne), c(ne);
+    double mx = logits[0];
+    for (int e = 1; e < ne; ++e) mx = logits[e] > mx ? logits[e] : mx;
+    double zs = 0.0;
+    for (int e = 0; e < ne; ++e) zs += (w[e] = exp(logits[e] - mx));
+    double csum = 0.0;
+    for (int e = 0; e < ne; ++e) {
+        w[e] /= zs;
+        c[e] = w[e] * D[e];
+        csum += c[e];
+    }
+    if (!(csum > 0.0)) return fail(FC_EINVAL, "fc_cnr_grad: sum_E w D must be > 0");
+    fc::AdjParams p;
+    memset(&p, 0, sizeof(p));
+    p.g = h->dg;
+    p.trig = h->d_trig;
+    p.labels = h->d_labels;
+    p.n_e = ne;
+    p.inv_csum = (float)(1.0 / csum);
+    const double log2e = 1.4426950408889634;
+    for (int m = 0; m < fc::kMaxMat; ++m) p.irho0[m] = m < h->n_mat ? (float)(1.0 / rho_nominal[m]) : 0.0f;
+    for (int e = 0; e < ne; ++e) {
+        p.wd[e] = (float)(c[e] / csum);
+        for (int m = 0; m < fc::kMaxMat; ++m) p.mu[e][m] = (float)(h->mu2[(size_t)e * fc::kMaxMat + m] / log2e);
+    }
+    fc::BlurParams b;
+    memset(&b, 0, sizeof(b));
+    b.n_u = h->g.n_u;
+    b.n_v = h->g.n_v;
+    rc = gauss_taps(h->psf, b.gp, &b.rp);
+    if (rc) return rc;
+    rc = gauss_taps(h->sc, b.gs, &b.rs);
+    if (rc) return rc;
+    b.n0 = (float)h->n0;
+    b.spr = (float)h->spr;
+    fc::FdkParams pf;
+    pf.g = h->dg;
+    pf.trig = h->d_trig;
+    pf.log_flood = (float)log(h->n0 * (1.0 + h->spr));
+    pf.tau = (float)(h->g.du_cm * h->g.sad_cm / h->g.sdd_cm);
+    pf.mag = (float)(h->g.sad_cm / h->g.sdd_cm);
+    pf.scale = h->g.arc_rad / (2.0 * h->g.n_angles);
+    fc::fdk_row_range(h->dg, &pf.v_lo, &pf.v_hi);
+    pf.pw = h->g.n_u + 3;
+    pf.ph = pf.v_hi - pf.v_lo + 1 + 3;
+    fc::CnrParams cp;
+    memset(&cp, 0, sizeof(cp));
+    cp.g = h->dg;
+    cp.water_r = h->water_r;
+    const int zcut = (int)floor(h->g.nz * h->zmargin);
+    cp.zcut = (h->g.nz > 2 * zcut) ? zcut : 0;
+    cp.n_roi = n_roi;
+    for (int r = 0; r < n_roi; ++r) {
+        cp.cx[r] = rois[r].cx_cm;
+        cp.cy[r] = rois[r].cy_cm;
+        cp.rad[r] = rois[r].radius_cm;
+    }
+    const int na = h->g.n_angles;
+    // forward
+    FC_CK(fc::launch_project_density(p, rho, h->d_T, s));
+    FC_CK(fc::launch_blur_rows(b, h->d_T, h->d_tp, h->d_ts, na, s));
+    FC_CK(fc::launch_blur_cols(b, h->d_tp, h->d_ts, h->d_I, na, s));
+    FC_CK(fc::launch_noise_gauss(h->d_I, z, h->d_counts, np, s));
+    FC_CK(fc::launch_fdk_filter(pf, h->d_counts, h->d_filt, s));
+    FC_CK(fc::launch_backproject(pf, h->d_filt, h->d_vol, s));
+    FC_CK(fc::launch_cnr(cp, h->d_vol, h->d_gmu, h->d_gwd + fc::kMaxBins, s));
+    const bool grads = g_logits || g_D || g_rho;
+    if (grads) {
+        FC_CK(cudaMemsetAsync(h->d_gf, 0, h->filt_elems * sizeof(float), s));
+        FC_CK(fc::launch_backproject_adjoint(pf, h->d_gmu, h->d_gf, s));
+        FC_CK(cudaMemsetAsync(h->d_gI, 0, np * sizeof(float), s));
+        FC_CK(fc::launch_filter_adjoint(pf, h->d_gf, h->d_I, h->d_counts, z, h->d_gI, s));
+        FC_CK(fc::launch_blur_adjoint(b, na, h->d_gI, h->d_gtmp, h->d_gT, b.n0, b.spr, s));
+        FC_CK(cudaMemsetAsync(h->d_gwd, 0, fc::kMaxBins * sizeof(double), s));
+        float *grho = g_rho ? g_rho : h->d_gtmp;   // scratch when only spectral grads are wanted
+        FC_CK(cudaMemsetAsync(grho, 0, nv * sizeof(float), s));
+        FC_CK(fc::launch_project_density_adjoint(p, rho, h->d_gT, grho, h->d_gwd, s));
+    }
+    std::vector<double> host(fc::kMaxBins + 1);
+    FC_CK(cudaMemcpyAsync(host.data(), h->d_gwd, (fc::kMaxBins + 1) * sizeof(double),
+                          cudaMemcpyDeviceToHost, s));
+    FC_CK(cudaStreamSynchronize(s));
+    *J = host[fc::kMaxBins];
+    if (grads) {
+        // c_E = w_E D_E: dJ/dw_E = gc_E D_E, dJ/dD_E = gc_E w_E; softmax Jacobian
+        double dot = 0.0;
+        std::vector<double> gw(ne);
+        for (int e = 0; e < ne; ++e) {
+            gw[e] = host[e] * D[e];
+            dot += w[e] * gw[e];
+        }
+        for (int e = 0; e < ne; ++e) {
+            if (g_D) g_D[e] = host[e] * w[e];
+            if (g_logits) g_logits[e] = w[e] * (gw[e] - dot);
+        }
+    }
     return FC_OK;
 }
 

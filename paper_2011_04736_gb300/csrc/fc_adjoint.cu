@@ -1,0 +1,517 @@
+// Reverse-mode (adjoint) gradient of an image-quality objective through the
+// whole simulate-and-reconstruct path:
+//
+//   rho (voxel densities) -> A_im = sum_{v in ray i, label m} l_iv rho_v / rho0_m
+//   T_i = sum_E (w D)_E exp(-sum_m mu_m(E) A_im) / sum_E (w D)_E    (Sec. II.F)
+//   I = N0 (G_psf (x) T + SPR G_sc (x) T)                              (II.E/G)
+//   K = I + sqrt(I) z       (Poisson noise replaced by its Gaussian form with
+//                            fixed standard normals z, so K is smooth)
+//   mu = FDK(ln(I_flood / K))                                          (II.G)
+//   J = sum_R CNR_R(HU(mu)),  CNR = |HU_w - HU_R| / sqrt(s_w^2 + s_R^2)  (II.G)
+//
+// The forward pass reuses the detector-blur and FDK kernels; this file adds
+// the density projector, the Gaussian-noise step, the CNR objective and the
+// transposes of each linear step:
+//   * CNR -> dJ/dmu (FP64, one CTA);
+//   * backprojection^T: each ROI voxel scatters its bilinear weights into the
+//     filtered-projection gradient (atomics);
+//   * Ram-Lak^T = Ram-Lak (symmetric kernel, zero padding), then the
+//     log / cosine-weight / noise chain rule down to dJ/dI;
+//   * clamp-to-edge blur^T: zero-padded correlation plus the clamped mass
+//     folded back onto the first and last pixel, columns then rows;
+//   * projector^T: each ray recomputes its path lengths (first walk), forms
+//     dJ/dA_im and the spectral partials, then walks again scattering
+//     dJ/drho_v = dJ/dA_{i,m(v)} l_iv / rho0_m(v) (atomics).
+#include <math.h>
+
+#include "fc_internal.cuh"
+
+namespace fc {
+
+namespace {
+
+__device__ __forceinline__ int clampi_(int v, int lo, int hi)
+{
+    return v < lo ? lo : (v > hi ? hi : v);
+}
+
+// Per-ray set-up shared by both walks: anchor A, direction d, entry/exit.
+struct Ray {
+    float A[3], d[3], inv[3];
+    float t_in, t_out;
+    bool hit;
+};
+
+__device__ __forceinline__ Ray make_ray(const DevGeom &g, float c, float s, int iu, int iv)
+{
+    Ray r;
+    const float u = ((float)iu - g.cu) * g.du;
+    const float v = ((float)iv - g.cv) * g.dv;
+    const float uv2 = u * u + v * v;
+    const float n2 = g.sdd * g.sdd + uv2;
+    const float len = sqrtf(n2);
+    const float il = __frcp_rn(len), in2 = __frcp_rn(n2);
+    const float gx = -g.sdd * il, gy = u * il, gz = v * il;
+    const float sA = g.sad * g.sdd * in2;
+    const float agx = g.sad * uv2 * in2, agy = sA * u, agz = sA * v;
+    r.A[0] = agx * c - agy * s;
+    r.A[1] = agx * s + agy * c;
+    r.A[2] = agz;
+    r.d[0] = gx * c - gy * s;
+    r.d[1] = gx * s + gy * c;
+    r.d[2] = gz;
+    const float lo[3] = {g.lox, g.loy, g.loz};
+    r.t_in = -sA * len;
+    r.t_out = (1.0f - sA) * len;
+    r.hit = true;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        r.inv[a] = __frcp_rn(r.d[a]);
+        if (r.d[a] != 0.0f) {
+            const float t0 = (lo[a] - r.A[a]) * r.inv[a], t1 = (-lo[a] - r.A[a]) * r.inv[a];
+            r.t_in = fmaxf(r.t_in, fminf(t0, t1));
+            r.t_out = fminf(r.t_out, fmaxf(t0, t1));
+        } else if (r.A[a] < lo[a] || r.A[a] >= -lo[a]) {
+            r.hit = false;
+        }
+    }
+    r.hit = r.hit && r.t_in < r.t_out;
+    return r;
+}
+
+// Voxel walk along a ray: calls f(voxel index, segment length) for every
+// voxel crossed.  Crossings t(i) = fma(i, pitch / d, (lo - A) / d); each
+// step advances one index monotonically and stops at the grid edge, so at
+// most nx + ny + nz steps occur and every index stays in the grid.
+template <class F>
+__device__ __forceinline__ void walk(const DevGeom &g, const Ray &r, F f)
+{
+    const int N[3] = {g.nx, g.ny, g.nz};
+    const float lo[3] = {g.lox, g.loy, g.loz}, vox[3] = {g.dx, g.dy, g.dz};
+    const float ivx[3] = {g.idx, g.idy, g.idz};
+    int i[3], sg[3], ux[3];
+    float vs[3], bs[3], tn[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const float p = fmaf(r.t_in, r.d[a], r.A[a]);
+        i[a] = clampi_((int)floorf((p - lo[a]) * ivx[a]), 0, N[a] - 1);
+        sg[a] = r.d[a] > 0.0f ? 1 : (r.d[a] < 0.0f ? -1 : 0);
+        ux[a] = sg[a] > 0;
+        vs[a] = vox[a] * r.inv[a];
+        bs[a] = (lo[a] - r.A[a]) * r.inv[a];
+        tn[a] = sg[a] ? fmaf((float)(i[a] + ux[a]), vs[a], bs[a]) : INFINITY;
+    }
+    float t = r.t_in;
+    for (int budget = g.nx + g.ny + g.nz + 3; budget > 0; --budget) {
+        const float tm = fminf(tn[0], fminf(tn[1], tn[2]));
+        const float te = fminf(fmaxf(tm, t), r.t_out);
+        f((i[2] * g.ny + i[1]) * g.nx + i[0], te - t);
+        t = te;
+        if (tm >= r.t_out) break;
+        const int a = tn[0] == tm ? 0 : (tn[1] == tm ? 1 : 2);
+        i[a] += sg[a];
+        if (i[a] < 0 || i[a] >= N[a]) break;
+        tn[a] = fmaf((float)(i[a] + ux[a]), vs[a], bs[a]);
+    }
+}
+
+}  // namespace
+
+// Forward density projector: T_i (flood-normalised) for all rays.
+__global__ void __launch_bounds__(256)
+k_project_density(const __grid_constant__ AdjParams p, const float *__restrict__ rho,
+                  float *__restrict__ T)
+{
+    const DevGeom &g = p.g;
+    const int iu = blockIdx.x * 32 + threadIdx.x, iv = blockIdx.y * 8 + threadIdx.y, k = blockIdx.z;
+    if (iu >= g.n_u || iv >= g.n_v) return;
+    const float2 cs = p.trig[k];
+    const Ray r = make_ray(g, cs.x, cs.y, iu, iv);
+    float A[kMaxMat];
+#pragma unroll
+    for (int m = 0; m < kMaxMat; ++m) A[m] = 0.0f;
+    if (r.hit) {
+        walk(g, r, [&](int v, float len) {
+            const int m = p.labels[v];
+            const float x = len * rho[v] * p.irho0[m];
+#pragma unroll
+            for (int j = 0; j < kMaxMat; ++j) A[j] += (m == j) ? x : 0.0f;
+        });
+    }
+    float sum = 0.0f;
+    for (int e = 0; e < p.n_e; ++e) {
+        float a = 0.0f;
+#pragma unroll
+        for (int m = 0; m < kMaxMat; ++m) a = fmaf(p.mu[e][m], A[m], a);
+        sum += p.wd[e] * __expf(-a);
+    }
+    T[((size_t)k * g.n_v + iv) * g.n_u + iu] = sum;
+}
+
+// Adjoint projector.  gT = dJ/dT per ray; accumulates dJ/d(wD)_E (before
+// normalisation) into gwd[n_e] (FP64) and dJ/drho into grho.
+__global__ void __launch_bounds__(256)
+k_project_density_adjoint(const __grid_constant__ AdjParams p, const float *__restrict__ rho,
+                          const float *__restrict__ gT, float *__restrict__ grho,
+                          double *__restrict__ gwd)
+{
+    __shared__ float sg[kMaxBins];
+    const DevGeom &g = p.g;
+    const int tid = threadIdx.y * 32 + threadIdx.x;
+    for (int e = tid; e < p.n_e; e += 256) sg[e] = 0.0f;
+    __syncthreads();
+    const int iu = blockIdx.x * 32 + threadIdx.x, iv = blockIdx.y * 8 + threadIdx.y, k = blockIdx.z;
+    const bool in = iu < g.n_u && iv < g.n_v;
+    float gt = 0.0f;
+    Ray r;
+    r.hit = false;
+    if (in) {
+        gt = gT[((size_t)k * g.n_v + iv) * g.n_u + iu];
+        const float2 cs = p.trig[k];
+        r = make_ray(g, cs.x, cs.y, iu, iv);
+    }
+    float A[kMaxMat];
+#pragma unroll
+    for (int m = 0; m < kMaxMat; ++m) A[m] = 0.0f;
+    if (in && r.hit && gt != 0.0f) {
+        walk(g, r, [&](int v, float len) {
+            const int m = p.labels[v];
+            const float x = len * rho[v] * p.irho0[m];
+#pragma unroll
+            for (int j = 0; j < kMaxMat; ++j) A[j] += (m == j) ? x : 0.0f;
+        });
+    }
+    // T = sum_E wd_E e_E with wd normalised (sum 1); for the unnormalised
+    // weights c_E: dT/dc_E = (e_E - T) / sum c.  Here wd = c / sum c, so the
+    // partial w.r.t. c_E is (e_E - T) * p.inv_csum.
+    float gA[kMaxMat];
+#pragma unroll
+    for (int m = 0; m < kMaxMat; ++m) gA[m] = 0.0f;
+    if (in && gt != 0.0f) {
+        float T = 0.0f;
+        for (int e = 0; e < p.n_e; ++e) {
+            float a = 0.0f;
+#pragma unroll
+            for (int m = 0; m < kMaxMat; ++m) a = fmaf(p.mu[e][m], A[m], a);
+            T += p.wd[e] * __expf(-a);
+        }
+        for (int e = 0; e < p.n_e; ++e) {
+            float a = 0.0f;
+#pragma unroll
+            for (int m = 0; m < kMaxMat; ++m) a = fmaf(p.mu[e][m], A[m], a);
+            const float ee = __expf(-a);
+            atomicAdd(&sg[e], gt * (ee - T) * p.inv_csum);
+            const float c = -gt * p.wd[e] * ee;
+#pragma unroll
+            for (int m = 0; m < kMaxMat; ++m) gA[m] = fmaf(c, p.mu[e][m], gA[m]);
+        }
+        if (r.hit) {
+            walk(g, r, [&](int v, float len) {
+                const int m = p.labels[v];
+                float s = 0.0f;
+#pragma unroll
+                for (int j = 0; j < kMaxMat; ++j) s = (m == j) ? gA[j] : s;
+                atomicAdd(grho + v, s * len * p.irho0[m]);
+            });
+        }
+    }
+    __syncthreads();
+    for (int e = tid; e < p.n_e; e += 256)
+        if (sg[e] != 0.0f) atomicAdd(gwd + e, (double)sg[e]);
+}
+
+// K = I + sqrt(I) z (forward) with z a fixed standard-normal field.
+__global__ void k_noise_gauss(const float *__restrict__ I, const float *__restrict__ z,
+                              float *__restrict__ K, size_t n)
+{
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
+         i += (size_t)gridDim.x * blockDim.x) {
+        const float v = I[i];
+        K[i] = z ? v + sqrtf(fmaxf(v, 0.0f)) * z[i] : v;
+    }
+}
+
+// CNR objective and dJ/dmu (FP64, one CTA of 1024 threads).
+// ROI masks: water = centres within water_r of the axis; insert r = centres
+// within rois[r].radius of its centre; both on slices [zcut, nz - zcut).
+__global__ void __launch_bounds__(1024)
+k_cnr(const __grid_constant__ CnrParams c, const double *__restrict__ mu, float *__restrict__ gmu,
+      double *__restrict__ out)
+{
+    __shared__ double red[1024];
+    __shared__ double stat[3 * (kMaxRoi + 1)];   // count, sum, sum of squares (HU)
+    __shared__ double gm[2 * (kMaxRoi + 1)];     // per-ROI gradient coefficients
+    __shared__ double mu_w_s, gsum_s;
+    const DevGeom &g = c.g;
+    const int tid = threadIdx.x;
+    const size_t n = (size_t)g.nx * g.ny * g.nz;
+    auto roi_of = [&](size_t i) -> int {
+        const int ix = (int)(i % g.nx), iy = (int)((i / g.nx) % g.ny), iz = (int)(i / ((size_t)g.nx * g.ny));
+        if (iz < c.zcut || iz >= g.nz - c.zcut) return -1;
+        const double x = (ix - 0.5 * (g.nx - 1)) * (double)g.dx, y = (iy - 0.5 * (g.ny - 1)) * (double)g.dy;
+        if (x * x + y * y <= c.water_r * c.water_r) return 0;
+        for (int r = 0; r < c.n_roi; ++r) {
+            const double dx = x - c.cx[r], dy = y - c.cy[r];
+            if (dx * dx + dy * dy <= c.rad[r] * c.rad[r]) return r + 1;
+        }
+        return -1;
+    };
+    auto block_sum = [&](double v) -> double {
+        red[tid] = v;
+        __syncthreads();
+        for (int s = 512; s > 0; s >>= 1) {
+            if (tid < s) red[tid] += red[tid + s];
+            __syncthreads();
+        }
+        const double r = red[0];
+        __syncthreads();
+        return r;
+    };
+    // mu_w
+    double s = 0.0, cnt = 0.0;
+    for (size_t i = tid; i < n; i += blockDim.x)
+        if (roi_of(i) == 0) { s += mu[i]; cnt += 1.0; }
+    s = block_sum(s);
+    cnt = block_sum(cnt);
+    if (tid == 0) mu_w_s = s / cnt;
+    __syncthreads();
+    const double mu_w = mu_w_s;
+    // per-ROI HU statistics
+    for (int r = 0; r <= c.n_roi; ++r) {
+        double a = 0.0, b = 0.0, q = 0.0;
+        for (size_t i = tid; i < n; i += blockDim.x)
+            if (roi_of(i) == r) {
+                const double hu = 1000.0 * (mu[i] - mu_w) / mu_w;
+                a += 1.0;
+                b += hu;
+                q += hu * hu;
+            }
+        a = block_sum(a);
+        b = block_sum(b);
+        q = block_sum(q);
+        if (tid == 0) {
+            stat[3 * r] = a;
+            stat[3 * r + 1] = b / a;
+            stat[3 * r + 2] = q / a - (b / a) * (b / a);   // population variance
+        }
+        __syncthreads();
+    }
+    if (tid == 0) {
+        double J = 0.0, cw_mean = 0.0, cw_dev = 0.0;
+        const double nw = stat[0], mw = stat[1], vw = stat[2];
+        for (int r = 1; r <= c.n_roi; ++r) {
+            const double nr = stat[3 * r], mr = stat[3 * r + 1], vr = stat[3 * r + 2];
+            const double a = mw - mr, sd = sqrt(vw + vr), sgn = a >= 0.0 ? 1.0 : -1.0;
+            J += fabs(a) / sd;
+            // dCNR/dHU_v: water v: sgn/(nw sd) - |a|/sd^3 (HU_v - mw)/nw
+            //             roi v:  -sgn/(nr sd) - |a|/sd^3 (HU_v - mr)/nr
+            cw_mean += sgn / (nw * sd);
+            cw_dev += -fabs(a) / (sd * sd * sd) / nw;
+            gm[2 * r] = -sgn / (nr * sd);
+            gm[2 * r + 1] = -fabs(a) / (sd * sd * sd) / nr;
+        }
+        gm[0] = cw_mean;
+        gm[1] = cw_dev;
+        out[0] = J;
+    }
+    __syncthreads();
+    // dJ/dHU_v, then through HU = 1000 (mu / mu_w - 1) with mu_w = mean_W mu
+    double gsum = 0.0;   // sum_u dJ/dHU_u mu_u
+    for (size_t i = tid; i < n; i += blockDim.x) {
+        const int r = roi_of(i);
+        if (r < 0) continue;
+        const double hu = 1000.0 * (mu[i] - mu_w) / mu_w;
+        const double gh = gm[2 * r] + gm[2 * r + 1] * (hu - stat[3 * r + 1]);
+        gsum += gh * mu[i];
+    }
+    gsum = block_sum(gsum);
+    if (tid == 0) gsum_s = gsum;
+    __syncthreads();
+    const double corr = 1000.0 / (mu_w * mu_w) * gsum_s / stat[0];
+    for (size_t i = tid; i < n; i += blockDim.x) {
+        const int r = roi_of(i);
+        double v = 0.0;
+        if (r >= 0) {
+            const double hu = 1000.0 * (mu[i] - mu_w) / mu_w;
+            const double gh = gm[2 * r] + gm[2 * r + 1] * (hu - stat[3 * r + 1]);
+            v = 1000.0 / mu_w * gh - (r == 0 ? corr : 0.0);
+        }
+        gmu[i] = (float)v;
+    }
+}
+
+// Backprojection transpose: gf (padded filtered layout) += B^T gmu.
+__global__ void __launch_bounds__(256)
+k_backproject_adjoint(const __grid_constant__ FdkParams p, const float *__restrict__ gmu,
+                      float *__restrict__ gf)
+{
+    const DevGeom &g = p.g;
+    const size_t n = (size_t)g.nx * g.ny * g.nz;
+    const size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float gv = gmu[i];
+    if (gv == 0.0f) return;
+    const int ix = (int)(i % g.nx), iy = (int)((i / g.nx) % g.ny), iz = (int)(i / ((size_t)g.nx * g.ny));
+    const float x = ((float)ix - 0.5f * (float)(g.nx - 1)) * g.dx;
+    const float y = ((float)iy - 0.5f * (float)(g.ny - 1)) * g.dy;
+    const float zz = ((float)iz - 0.5f * (float)(g.nz - 1)) * g.dz;
+    const float cu1 = g.cu + 1.0f, cv1 = g.cv - (float)p.v_lo + 1.0f;
+    const float umax = (float)(p.pw - 2), vmaxp = (float)(p.ph - 2);
+    const float sdd_du = g.sdd / g.du, sdd_dv = g.sdd / g.dv;
+    const size_t plane = (size_t)p.ph * p.pw;
+    const float scale = (float)p.scale;
+    for (int k = 0; k < g.n_angles; ++k) {
+        const float2 cs = p.trig[k];
+        const float U = g.sad - (x * cs.x + y * cs.y);
+        const float ru = y * cs.x - x * cs.y;
+        const float iU = __frcp_rn(U);
+        const float fu = fminf(fmaxf(fmaf(ru * iU, sdd_du, cu1), 0.0f), umax);
+        const float fv = fminf(fmaxf(fmaf(zz * iU, sdd_dv, cv1), 0.0f), vmaxp);
+        const float w = (g.sad * iU) * (g.sad * iU) * scale * gv;
+        const float fu0 = floorf(fu), fv0 = floorf(fv);
+        const float au = fu - fu0, av = fv - fv0;
+        float *b = gf + (size_t)k * plane + (size_t)fv0 * p.pw + (int)fu0;
+        atomicAdd(b, w * (1.0f - au) * (1.0f - av));
+        atomicAdd(b + 1, w * au * (1.0f - av));
+        atomicAdd(b + p.pw, w * (1.0f - au) * av);
+        atomicAdd(b + p.pw + 1, w * au * av);
+    }
+}
+
+// Ram-Lak transpose (the kernel is symmetric) and the chain rule down to
+// dJ/dI:  q = ln(I_flood / max(K, 1)) cosw,  K = I + sqrt(I) z.
+// One thread per detector pixel of the reachable rows; gI elsewhere is zero.
+__global__ void __launch_bounds__(256)
+k_filter_adjoint(const __grid_constant__ FdkParams p, const float *__restrict__ gf,
+                 const float *__restrict__ I, const float *__restrict__ K,
+                 const float *__restrict__ z, float *__restrict__ gI)
+{
+    const DevGeom &g = p.g;
+    const int iu = blockIdx.x * blockDim.x + threadIdx.x;
+    const int r = blockIdx.y, k = blockIdx.z;
+    if (iu >= g.n_u) return;
+    const int iv = p.v_lo + r;
+    const float *row = gf + ((size_t)k * p.ph + (r + 1)) * p.pw + 1;
+    // gq[iu] = (1 / tau) sum_j h'[j] gf[iu + j],  h'[0] = 1/4, h'[odd j] = -1/(pi j)^2
+    float acc = 0.25f * row[iu];
+    for (int j = 1; j < g.n_u; j += 2) {
+        const float h = -1.0f / (9.8696044f * (float)j * (float)j);
+        if (iu - j >= 0) acc = fmaf(h, row[iu - j], acc);
+        if (iu + j < g.n_u) acc = fmaf(h, row[iu + j], acc);
+    }
+    const float gq = acc / p.tau;
+    const float ui = ((float)iu - g.cu) * g.du * p.mag;
+    const float vi = ((float)iv - g.cv) * g.dv * p.mag;
+    const float cosw = g.sad * rsqrtf(g.sad * g.sad + ui * ui + vi * vi);
+    const size_t idx = ((size_t)k * g.n_v + iv) * g.n_u + iu;
+    const float Kv = K[idx];
+    const float gK = Kv > 1.0f ? -gq * cosw / Kv : 0.0f;
+    float dKdI = 1.0f;
+    if (z) {
+        const float Iv = I[idx];
+        dKdI = Iv > 0.0f ? 1.0f + 0.5f * z[idx] * rsqrtf(Iv) : 1.0f;
+    }
+    gI[idx] = gK * dKdI;
+}
+
+// Transpose of one clamp-to-edge 1D Gaussian pass along u (rows) or v
+// (columns): out[t] = sum_j g[j] in[t + j] (zero outside) plus, at t = 0 and
+// t = n - 1, the mass of every tap that the forward pass clamped there.
+template <bool ALONG_V>
+__global__ void __launch_bounds__(256)
+k_blur_adjoint_pass(const __grid_constant__ BlurParams b, int which, const float *__restrict__ in,
+                    float *__restrict__ out, float gain, int accumulate)
+{
+    const int n_u = b.n_u, n_v = b.n_v;
+    const int iu = blockIdx.x * blockDim.x + threadIdx.x;
+    const int iv = blockIdx.y, k = blockIdx.z;
+    if (iu >= n_u) return;
+    const float *taps = which ? b.gs : b.gp;
+    const int R = which ? b.rs : b.rp;
+    const int n = ALONG_V ? n_v : n_u;
+    const int t = ALONG_V ? iv : iu;
+    const size_t plane = (size_t)n_u * n_v;
+    const float *src = in + (size_t)k * plane;
+    auto at = [&](int s) -> float {
+        return ALONG_V ? src[(size_t)s * n_u + iu] : src[(size_t)iv * n_u + s];
+    };
+    float acc = 0.0f;
+    for (int j = -R; j <= R; ++j) {
+        const int s = t - j;   // forward output s read input t with tap j (symmetric kernel)
+        if (s >= 0 && s < n) acc = fmaf(taps[j + R], at(s), acc);
+    }
+    if (t == 0) {
+        for (int s = 0; s < n && s < R; ++s) {
+            float m = 0.0f;
+            for (int j = -R; j < -s; ++j) m += taps[j + R];   // s + j < 0 clamps to 0
+            acc = fmaf(m, at(s), acc);
+        }
+    }
+    if (t == n - 1) {
+        for (int s = n - 1; s >= 0 && s > n - 1 - R; --s) {
+            float m = 0.0f;
+            for (int j = n - s; j <= R; ++j) m += taps[j + R];  // s + j > n - 1 clamps
+            acc = fmaf(m, at(s), acc);
+        }
+    }
+    const size_t o = (size_t)k * plane + (size_t)iv * n_u + iu;
+    out[o] = accumulate ? fmaf(gain, acc, out[o]) : gain * acc;
+}
+
+// ---------------------------------------------------------------- launchers
+cudaError_t launch_project_density(const AdjParams &p, const float *rho, float *T, cudaStream_t s)
+{
+    dim3 block(32, 8), grid((p.g.n_u + 31) / 32, (p.g.n_v + 7) / 8, p.g.n_angles);
+    k_project_density<<<grid, block, 0, s>>>(p, rho, T);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_project_density_adjoint(const AdjParams &p, const float *rho, const float *gT,
+                                           float *grho, double *gwd, cudaStream_t s)
+{
+    dim3 block(32, 8), grid((p.g.n_u + 31) / 32, (p.g.n_v + 7) / 8, p.g.n_angles);
+    k_project_density_adjoint<<<grid, block, 0, s>>>(p, rho, gT, grho, gwd);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_noise_gauss(const float *I, const float *z, float *K, size_t n, cudaStream_t s)
+{
+    k_noise_gauss<<<152 * 8, 256, 0, s>>>(I, z, K, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cnr(const CnrParams &c, const double *mu, float *gmu, double *out, cudaStream_t s)
+{
+    k_cnr<<<1, 1024, 0, s>>>(c, mu, gmu, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_backproject_adjoint(const FdkParams &p, const float *gmu, float *gf, cudaStream_t s)
+{
+    const size_t n = (size_t)p.g.nx * p.g.ny * p.g.nz;
+    k_backproject_adjoint<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(p, gmu, gf);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_filter_adjoint(const FdkParams &p, const float *gf, const float *I, const float *K,
+                                  const float *z, float *gI, cudaStream_t s)
+{
+    dim3 grid((p.g.n_u + 255) / 256, p.v_hi - p.v_lo + 1, p.g.n_angles);
+    k_filter_adjoint<<<grid, 256, 0, s>>>(p, gf, I, K, z, gI);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_blur_adjoint(const BlurParams &b, int n_img, const float *gI, float *tmp,
+                                float *gT, float n0, float spr, cudaStream_t s)
+{
+    // G = C o R per kernel (R rows, C columns); G^T = R^T o C^T.
+    // gT = n0 (Gp^T gI + spr Gs^T gI).
+    dim3 grid((b.n_u + 255) / 256, b.n_v, n_img);
+    k_blur_adjoint_pass<true><<<grid, 256, 0, s>>>(b, 0, gI, tmp, 1.0f, 0);
+    k_blur_adjoint_pass<false><<<grid, 256, 0, s>>>(b, 0, tmp, gT, n0, 0);
+    k_blur_adjoint_pass<true><<<grid, 256, 0, s>>>(b, 1, gI, tmp, 1.0f, 0);
+    k_blur_adjoint_pass<false><<<grid, 256, 0, s>>>(b, 1, tmp, gT, n0 * spr, 1);
+    return cudaGetLastError();
+}
+
+}  // namespace fc

@@ -127,6 +127,40 @@ cudaError_t launch_mlp_step(const SurrogateParams &p, const float *L, const floa
                             __nv_bfloat16 *W2b, __nv_bfloat16 *W3b, __nv_bfloat16 *W2Tb,
                             __nv_bfloat16 *W3Tb, cudaStream_t s);
 
+// ---- adjoint of the CNR objective (fc_adjoint.cu) ----
+constexpr int kMaxRoi = 8;
+
+struct AdjParams {
+    DevGeom g;
+    const float2 *trig;
+    const uint8_t *labels;      // [nz][ny][nx]
+    int n_e;
+    float inv_csum;             // 1 / sum_E (w D)_E before normalisation
+    float irho0[kMaxMat];       // 1 / nominal density of each material
+    float wd[kMaxBins];         // (w D)_E / sum (w D)
+    float mu[kMaxBins][kMaxMat];  // attenuation at nominal density, 1/cm
+};
+
+struct CnrParams {
+    DevGeom g;
+    double water_r;
+    int zcut, n_roi;
+    double cx[kMaxRoi], cy[kMaxRoi], rad[kMaxRoi];
+};
+
+cudaError_t launch_project_density(const AdjParams &p, const float *rho, float *T, cudaStream_t s);
+cudaError_t launch_project_density_adjoint(const AdjParams &p, const float *rho, const float *gT,
+                                           float *grho, double *gwd, cudaStream_t s);
+cudaError_t launch_noise_gauss(const float *I, const float *z, float *K, size_t n, cudaStream_t s);
+cudaError_t launch_cnr(const CnrParams &c, const double *mu, float *gmu, double *out,
+                       cudaStream_t s);
+cudaError_t launch_backproject_adjoint(const FdkParams &p, const float *gmu, float *gf,
+                                       cudaStream_t s);
+cudaError_t launch_filter_adjoint(const FdkParams &p, const float *gf, const float *I,
+                                  const float *K, const float *z, float *gI, cudaStream_t s);
+cudaError_t launch_blur_adjoint(const BlurParams &b, int n_img, const float *gI, float *tmp,
+                                float *gT, float n0, float spr, cudaStream_t s);
+
 // launchers (return cudaError_t of the launch)
 cudaError_t launch_project(const ProjParams &p, float *T, float *L_out, cudaStream_t s);
 cudaError_t launch_blur_rows(const BlurParams &p, const float *T, float *tp, float *ts,
