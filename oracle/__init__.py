@@ -89,6 +89,7 @@ def lib():
                                                      ctypes.c_uint32, ctypes.c_uint32,
                                                      ctypes.c_uint64]),
                 "orc_poisson": (None, [_P, _I, _I, _I, _I, ctypes.c_uint64, _P]),
+                "orc_path_matrix": (ctypes.c_int64, [gp, _I, _I, _P, _P, _P]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(L, name)
@@ -162,6 +163,19 @@ def rays(g, labels, w, D, mu, ray_idx):
                    _ptr(_c(w, np.float64)), _ptr(_c(D, np.float64)), _ptr(mu),
                    len(r), _ptr(r), _ptr(L), _ptr(T))
     return L, T
+
+
+def path_matrix(g, a0=0, na=None):
+    """CSR (rowptr, col, val) of the ray x voxel path lengths (cm) of angles
+    a0 .. a0+na-1; rows in [k][iv][iu] order, columns flat [z][y][x]."""
+    na = g.n_angles - a0 if na is None else na
+    nrays = na * g.n_v * g.n_u
+    cap = g.nx + g.ny + g.nz + 2
+    rowptr = np.zeros(nrays + 1, np.int64)
+    col = np.zeros(nrays * cap, np.int64)
+    val = np.zeros(nrays * cap)
+    nnz = lib().orc_path_matrix(ctypes.byref(_geom(g)), a0, na, _ptr(rowptr), _ptr(col), _ptr(val))
+    return rowptr, col[:nnz].copy(), val[:nnz].copy()
 
 
 # ---------------------------------------------------------------- detector

@@ -128,6 +128,101 @@ double orc_siddon(const orc_geom *g, const uint8_t *lab, int n_mat,
     return total;
 }
 
+/* Voxels crossed by the segment S->P and their path lengths (Siddon, as in
+ * orc_siddon).  Writes up to cap (index, length) pairs; returns the count. */
+static int siddon_voxels(const orc_geom *g, const double S[3], const double P[3], int cap,
+                         int64_t *vidx, double *vlen, double *al)
+{
+    const int N[3] = {g->nx, g->ny, g->nz};
+    const double d[3] = {g->dx, g->dy, g->dz};
+    double lo[3], D[3];
+    double amin = 0.0, amax = 1.0;
+    for (int a = 0; a < 3; ++a) {
+        lo[a] = -0.5 * N[a] * d[a];
+        D[a] = P[a] - S[a];
+        if (D[a] != 0.0) {
+            double a0 = (lo[a] - S[a]) / D[a];
+            double a1 = (lo[a] + N[a] * d[a] - S[a]) / D[a];
+            double lo_a = a0 < a1 ? a0 : a1, hi_a = a0 < a1 ? a1 : a0;
+            if (lo_a > amin) amin = lo_a;
+            if (hi_a < amax) amax = hi_a;
+        } else if (S[a] < lo[a] || S[a] >= lo[a] + N[a] * d[a]) {
+            return 0;
+        }
+    }
+    if (amin >= amax) return 0;
+    const double len = sqrt(D[0] * D[0] + D[1] * D[1] + D[2] * D[2]);
+    int n = 0;
+    al[n++] = amin;
+    al[n++] = amax;
+    for (int a = 0; a < 3; ++a) {
+        if (D[a] == 0.0) continue;
+        for (int i = 0; i <= N[a]; ++i) {
+            double av = (lo[a] + i * d[a] - S[a]) / D[a];
+            if (av > amin && av < amax) al[n++] = av;
+        }
+    }
+    qsort(al, (size_t)n, sizeof(double), cmp_double);
+    int out = 0;
+    for (int j = 0; j + 1 < n && out < cap; ++j) {
+        double a0 = al[j], a1 = al[j + 1];
+        if (a1 <= a0) continue;
+        double am = 0.5 * (a0 + a1);
+        int idx[3];
+        for (int a = 0; a < 3; ++a) {
+            double x = S[a] + am * D[a];
+            int i = (int)floor((x - lo[a]) / d[a]);
+            if (i < 0) i = 0;
+            if (i > N[a] - 1) i = N[a] - 1;
+            idx[a] = i;
+        }
+        vidx[out] = ((int64_t)idx[2] * N[1] + idx[1]) * N[0] + idx[0];
+        vlen[out] = (a1 - a0) * len;
+        ++out;
+    }
+    return out;
+}
+
+/* Sparse ray x voxel path-length matrix of all pixel rays of angles
+ * [a0, a0 + na), row r = ((k - a0) n_v + iv) n_u + iu, in CSR form: row r
+ * holds entries rowptr[r] .. rowptr[r + 1].  Each row has room for
+ * nx + ny + nz + 2 entries (cap of a ray); the arrays must hold
+ * nrays * cap entries.  Returns the total number of entries. */
+int64_t orc_path_matrix(const orc_geom *g, int a0, int na, int64_t *rowptr, int64_t *col,
+                        double *val)
+{
+    const long nrays = (long)na * g->n_v * g->n_u;
+    const int cap = g->nx + g->ny + g->nz + 2;
+    int *cnt = (int *)malloc(sizeof(int) * (size_t)nrays);
+#pragma omp parallel
+    {
+        double *al = (double *)malloc(sizeof(double) * (size_t)(cap + 8));
+#pragma omp for schedule(dynamic, 64)
+        for (long r = 0; r < nrays; ++r) {
+            int iu = (int)(r % g->n_u);
+            int iv = (int)((r / g->n_u) % g->n_v);
+            int k = a0 + (int)(r / ((long)g->n_u * g->n_v));
+            double S[3], P[3];
+            ray_endpoints(g, k, iv, iu, S, P);
+            cnt[r] = siddon_voxels(g, S, P, cap, col + r * cap, val + r * cap, al);
+        }
+        free(al);
+    }
+    /* compact the fixed-stride rows into CSR */
+    int64_t pos = 0;
+    for (long r = 0; r < nrays; ++r) {
+        rowptr[r] = pos;
+        for (int j = 0; j < cnt[r]; ++j) {
+            col[pos] = col[r * cap + j];
+            val[pos] = val[r * cap + j];
+            ++pos;
+        }
+    }
+    rowptr[nrays] = pos;
+    free(cnt);
+    return pos;
+}
+
 /* Path lengths of pixel ray (k, iv, iu). */
 double orc_ray_lengths(const orc_geom *g, const uint8_t *lab, int n_mat,
                        int k, int iv, int iu, double *L)

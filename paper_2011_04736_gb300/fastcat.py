@@ -28,7 +28,7 @@ ENTRY_POINTS = ("fc_create", "fc_destroy", "fc_last_error", "fc_set_geometry", "
                 "fc_poisson", "fc_project_lengths", "fc_profile_enable", "fc_profile_read",
                 "fc_detector_blur_static", "fc_surrogate_init", "fc_surrogate_train",
                 "fc_surrogate_grad", "fc_surrogate_get", "fc_surrogate_set", "fc_surrogate_eval",
-                "fc_energy_sum_lengths")
+                "fc_energy_sum_lengths", "fc_cnr_grad")
 FC_STATIC_SCRATCH_FLOATS = 8 << 20
 FC_SURROGATE_PARAMS = 34305
 FC_SURROGATE_STATE = 34305 + 52 + 2 * 34305 + 1
@@ -50,6 +50,11 @@ class fc_geometry(ctypes.Structure):
                 ("theta0_rad", ctypes.c_double), ("arc_rad", ctypes.c_double),
                 ("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32),
                 ("dx_cm", ctypes.c_double), ("dy_cm", ctypes.c_double), ("dz_cm", ctypes.c_double)]
+
+
+class fc_cnr_roi(ctypes.Structure):
+    _fields_ = [("cx_cm", ctypes.c_double), ("cy_cm", ctypes.c_double),
+                ("radius_cm", ctypes.c_double)]
 
 
 class fc_spectrum_detector(ctypes.Structure):
@@ -97,6 +102,7 @@ def load():
         "fc_surrogate_set": (I, [P, P]),
         "fc_surrogate_eval": (I, [P, P, ctypes.c_int64, P, P, P]),
         "fc_energy_sum_lengths": (I, [P, P, ctypes.c_int64, P, P]),
+        "fc_cnr_grad": (I, [P, P, P, P, P, P, I, P, P, P, P, P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -286,6 +292,55 @@ def fc_surrogate_eval(h, L, lnT, stream=None, count_fallback=True):
 def fc_energy_sum_lengths(h, L, lnT, stream=None):
     return _check(load().fc_energy_sum_lengths(h, _dev(L, "L"), lnT.numel(), _dev(lnT, "lnT"),
                                                _stream(stream)))
+
+
+def fc_cnr_grad(h, logits, D, rho0, rho, z, rois, grads=True, stream=None):
+    """CNR objective J and its gradients.
+
+    logits, D, rho0: host arrays; rho: device float tensor [nz][ny][nx];
+    z: device float tensor [n_angles][n_v][n_u] or None; rois: (cx, cy, r)
+    tuples in cm.  Returns (J, dJ/dlogits, dJ/dD, dJ/drho) (the last a device
+    tensor), or (J, None, None, None) when grads is False."""
+    lg = np.ascontiguousarray(logits, np.float64)
+    dd = np.ascontiguousarray(D, np.float64)
+    r0 = np.ascontiguousarray(rho0, np.float64)
+    roi = (fc_cnr_roi * len(rois))(*[fc_cnr_roi(*r) for r in rois])
+    J = ctypes.c_double(0.0)
+    gl = np.zeros_like(lg) if grads else None
+    gd = np.zeros_like(dd) if grads else None
+    gr = None
+    if grads:
+        import torch
+        gr = torch.empty_like(rho)
+    zp = _dev(z, "z") if z is not None else None
+    _check(load().fc_cnr_grad(h, lg.ctypes.data, dd.ctypes.data, r0.ctypes.data, _dev(rho, "rho"),
+                              zp, len(rois), roi, ctypes.byref(J),
+                              gl.ctypes.data if grads else None, gd.ctypes.data if grads else None,
+                              _dev(gr, "g_rho") if grads else None, _stream(stream)))
+    return J.value, gl, gd, gr
+
+
+def cnr_objective(h, rho0, z, rois):
+    """torch.autograd.Function-backed J(logits, D, rho) for a configured
+    handle: J = apply(logits (cpu f64), D (cpu f64), rho (cuda f32)).  The
+    forward call runs the library's adjoint as well and keeps the gradients."""
+    import torch
+
+    class _Cnr(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, logits, D, rho):
+            J, gl, gd, gr = fc_cnr_grad(h, logits.detach().cpu().numpy(),
+                                        D.detach().cpu().numpy(), rho0, rho.detach().contiguous(),
+                                        z, rois)
+            ctx.save_for_backward(torch.from_numpy(gl), torch.from_numpy(gd), gr)
+            return torch.tensor(J, dtype=torch.float64)
+
+        @staticmethod
+        def backward(ctx, gJ):
+            gl, gd, gr = ctx.saved_tensors
+            return gJ * gl.to(gJ.device), gJ * gd.to(gJ.device), (gJ.to(gr.device) * gr).to(gr.dtype)
+
+    return _Cnr.apply
 
 
 # ---------------------------------------------------------------- convenience

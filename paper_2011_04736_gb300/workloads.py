@@ -339,3 +339,28 @@ def water_roi_mask(g: Geometry, radius_cm=1.0, z_margin=0.1):
         m[:cut] = False
         m[g.nz - cut:] = False
     return m
+
+
+def adjoint_inputs(w: Workload, seed=4):
+    """Inputs of the CNR-gradient case: spectrum logits (seeded normals),
+    detector response D, nominal densities per label, voxel densities (the
+    nominal ones), a fixed standard-normal noise field z [angle][v][u] and
+    the bone and lung insert ROIs (centre, radius = 0.7 insert radius, at
+    least reaching the nearest voxel centre)."""
+    rng = np.random.default_rng(seed)
+    g = w.geom
+    logits = rng.normal(0.0, 0.5, w.n_e)
+    _, D = w.spectrum()
+    rho0 = np.array([MATERIALS[n][0] for n in w.labels])
+    lab = w.make_phantom()
+    rho = rho0[lab].astype(np.float32)
+    z = rng.standard_normal((g.n_angles, g.n_v, g.n_u)).astype(np.float32)
+    x = _centres(g.nx, g.dx)
+    y = _centres(g.ny, g.dy)
+    rois = []
+    for lab_id, cx, cy, r in catphan_inserts():
+        if lab_id not in (2, 3) or r < 0.2:
+            continue   # the 5 mm bone and lung rods
+        dmin = np.min(np.hypot(x[None, :] - cx, y[:, None] - cy))
+        rois.append((cx, cy, max(0.7 * r, dmin + 1e-6)))
+    return dict(logits=logits, D=D, rho0=rho0, rho=rho, z=z, rois=rois, labels=lab)

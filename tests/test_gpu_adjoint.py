@@ -1,0 +1,82 @@
+"""GPU adjoint of the CNR objective against the FP64 oracle gradient
+(PyTorch float64 reverse mode, itself pinned by finite differences):
+relative error <= 1e-3."""
+import numpy as np
+import pytest
+
+from paper_2011_04736_gb300 import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+REL = 1e-3
+
+
+@pytest.fixture(scope="module")
+def fc():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2011_04736_gb300 import build, fastcat
+    build.build()
+    fastcat.load()
+    return fastcat
+
+
+def _small():
+    return W.scaled(W.WORKLOADS["adjoint_kv"], n_u=96, n_v=24, du=0.24, dv=0.24, n_angles=48,
+                    nx=64, ny=64, nz=8, dx=0.25, dy=0.25, dz=0.25)
+
+
+def _gpu(fc, wl, inp, grads=True):
+    sc = fc.Scanner(wl, labels=inp["labels"], noise=False)
+    try:
+        rho = torch.from_numpy(inp["rho"]).cuda()
+        z = torch.from_numpy(inp["z"]).cuda()
+        J, gl, gd, gr = fc.fc_cnr_grad(sc.h, inp["logits"], inp["D"], inp["rho0"], rho, z,
+                                       inp["rois"], grads=grads)
+        torch.cuda.synchronize()
+        return J, gl, gd, (gr.cpu().numpy().ravel() if gr is not None else None)
+    finally:
+        sc.close()
+
+
+def _rel(a, b):
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+def test_cnr_gradient_matches_oracle(fc, orc):
+    from oracle import adjoint
+    wl = _small()
+    inp = W.adjoint_inputs(wl)
+    obj = adjoint.Objective(wl, inp["labels"], inp["rho0"], inp["z"], inp["rois"])
+    Jr, glr, gdr, grr = obj.value_and_grad(inp["logits"], inp["D"], inp["rho"])
+    J, gl, gd, gr = _gpu(fc, wl, inp)
+    print("J gpu %.8f oracle %.8f; rel err logits %.2e D %.2e rho %.2e"
+          % (J, Jr, _rel(gl, glr), _rel(gd, gdr), _rel(gr, grr)))
+    assert abs(J - Jr) <= REL * abs(Jr)
+    assert _rel(gl, glr) <= REL
+    assert _rel(gd, gdr) <= REL
+    assert _rel(gr, grr) <= REL
+
+
+def test_cnr_autograd_function(fc):
+    wl = _small()
+    inp = W.adjoint_inputs(wl)
+    sc = fc.Scanner(wl, labels=inp["labels"], noise=False)
+    try:
+        rho = torch.from_numpy(inp["rho"]).cuda().requires_grad_(True)
+        lg = torch.tensor(inp["logits"], requires_grad=True)
+        dd = torch.tensor(inp["D"], requires_grad=True)
+        z = torch.from_numpy(inp["z"]).cuda()
+        f = fc.cnr_objective(sc.h, inp["rho0"], z, inp["rois"])
+        J = f(lg, dd, rho)
+        (2.0 * J).backward()
+        J2, gl, gd, gr = fc.fc_cnr_grad(sc.h, inp["logits"], inp["D"], inp["rho0"], rho.detach(),
+                                        z, inp["rois"])
+        torch.cuda.synchronize()
+        assert float(J) == pytest.approx(J2)
+        assert np.allclose(lg.grad.numpy(), 2.0 * gl)
+        assert np.allclose(dd.grad.numpy(), 2.0 * gd)
+        assert torch.allclose(rho.grad, 2.0 * gr)
+    finally:
+        sc.close()
