@@ -265,6 +265,97 @@ def run_reference(args):
     return 0
 
 
+def _extra_adjoint(fc, torch):
+    """Forward + adjoint of the CNR objective on the adjoint design case
+    (128 x 128 x 32 voxels, 180 projections of 512 x 384, 30 bins)."""
+    wl = W.WORKLOADS["adjoint_kv"]
+    inp = W.adjoint_inputs(wl)
+    sc = fc.Scanner(wl, labels=inp["labels"], noise=False)
+    try:
+        rho = torch.from_numpy(inp["rho"]).cuda()
+        z = torch.from_numpy(inp["z"]).cuda()
+        args = (sc.h, inp["logits"], inp["D"], inp["rho0"], rho, z, inp["rois"])
+        fc.fc_cnr_grad(*args)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        reps = 3
+        for _ in range(reps):
+            J, gl, gd, gr = fc.fc_cnr_grad(*args)
+        torch.cuda.synchronize()
+        ms = (time.perf_counter() - t0) / reps * 1e3
+        fc.fc_cnr_grad(*args, grads=False)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            fc.fc_cnr_grad(*args, grads=False)
+        torch.cuda.synchronize()
+        ms_fwd = (time.perf_counter() - t0) / reps * 1e3
+        g = wl.geom
+        return {"workload": "adjoint_kv: %dx%dx%d voxels, %d projections of %dx%d, %d bins"
+                            % (g.nx, g.ny, g.nz, g.n_angles, g.n_u, g.n_v, wl.n_e),
+                "J": J, "ms_forward": ms_fwd, "ms_forward_and_gradient": ms,
+                "grad_norms": {"logits": float(np.linalg.norm(gl)), "D": float(np.linalg.norm(gd)),
+                               "rho": float(torch.linalg.vector_norm(gr))}}
+    finally:
+        sc.close()
+
+
+def _extra_paper_scale(fc, torch):
+    """One simulate + reconstruct step of the paper-scale MV case (1024^2 x 10
+    voxels, 720 projections of 1024 x 768, 60 bins) -- context for the
+    paper's whole-pipeline wall times (different GPU, 18 energies, 180
+    projections)."""
+    wl = W.WORKLOADS["paper_mv"]
+    g = wl.geom
+    sc = fc.Scanner(wl, noise=False)
+    try:
+        vol = torch.empty((g.nz, g.ny, g.nx), dtype=torch.float64, device="cuda")
+        fc.fc_project(sc.h, 0, g.n_angles, fc.FC_OUT_NONE, None)
+        fc.fc_reconstruct(sc.h, None, vol_mu=vol)
+        torch.cuda.synchronize()
+        fc.fc_profile_enable(sc.h, True)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        fc.fc_project(sc.h, 0, g.n_angles, fc.FC_OUT_NONE, None)
+        fc.fc_reconstruct(sc.h, None, vol_mu=vol)
+        b.record()
+        torch.cuda.synchronize()
+        kern = fc.fc_profile_read(sc.h)
+        ms = a.elapsed_time(b)
+        return {"workload": "paper_mv: %dx%dx%d voxels, %d projections of %dx%d, %d MV bins"
+                            % (g.nx, g.ny, g.nz, g.n_angles, g.n_u, g.n_v, wl.n_e),
+                "ms_per_step": ms, "rays_bins_per_s": g.n_rays * wl.n_e / (ms / 1e3),
+                "fdk_voxel_updates_per_s": g.n_voxels * g.n_angles / (ms / 1e3),
+                "kernels_ms": {k: v[0] for k, v in kern.items() if v[1]},
+                "paper_context_s": 61.0}
+    finally:
+        sc.close()
+
+
+def _extras(args, fc, torch):
+    out = {}
+    jobs = [("adjoint", lambda: _extra_adjoint(fc, torch)),
+            ("paper_scale", lambda: _extra_paper_scale(fc, torch))]
+    if not args.no_surrogate:
+        from paper_2011_04736_gb300 import surrogate_study
+
+        def sur():
+            r = surrogate_study.run(steps=args.surrogate_steps, verbose=False)
+            return {"workload": "head_surrogate: 256^3 voxels, 360 projections of 512x512, "
+                                "120 bins, %d rays" % r["rays"],
+                    "train": r["train"], "accuracy": r["accuracy"], "speed_ms": r["speed_ms"],
+                    "crossover_bins": r["crossover_bins"]}
+        jobs.append(("surrogate", sur))
+    for name, job in jobs:
+        try:
+            out[name] = job()
+        except Exception as e:  # an extra never costs the main line
+            out[name] = {"error": "%s: %s" % (type(e).__name__, str(e)[:300])}
+        torch.cuda.synchronize()
+    return out
+
+
 def run_ours(args):
     rank, world, dist = _dist()
     import torch
@@ -398,6 +489,8 @@ def run_ours(args):
     sc.close()
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(wl, args.cpu_angles)
+    if rank == 0 and world == 1 and not args.no_extras:
+        line["extras"] = _extras(args, fc, torch)
     if rank == 0:
         print(json.dumps(line))
     if dist is not None:
@@ -417,6 +510,10 @@ def main(argv=None):
     ap.add_argument("--ref-angles", type=int, default=8,
                     help="projections per reference-arm step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the adjoint, paper-scale and surrogate measurements")
+    ap.add_argument("--no-surrogate", action="store_true")
+    ap.add_argument("--surrogate-steps", type=int, default=20000)
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

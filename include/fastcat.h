@@ -250,6 +250,15 @@ int fc_surrogate_set(fc_handle *h, const float *state);
 int fc_surrogate_eval(fc_handle *h, const float *L, int64_t n, float *lnT, int64_t *n_fallback,
                       void *stream);
 
+/* Projection with the surrogate in place of the energy loop: the
+ * projector's path lengths for projections angle_begin .. + angle_count - 1
+ * are fed to the surrogate and T = exp(ln T) of every ray is written to out
+ * ([angle_count][n_v][n_u] float, host or device per out_where).  Uses a
+ * handle-owned scratch buffer of angle_count * n_v * n_u * (n_mat + 1)
+ * floats.  Errors: FC_ESTATE, FC_EINVAL, FC_ENOMEM, FC_ECUDA. */
+int fc_surrogate_project(fc_handle *h, int angle_begin, int angle_count, float *out,
+                         int out_where, void *stream);
+
 /* ln T of n rays from their path lengths by the exact energy sum (the
  * projector's epilogue as a separate pass).  Errors: FC_ESTATE, FC_EINVAL,
  * FC_ECUDA. */

@@ -116,6 +116,8 @@ struct fc_handle {
     unsigned int *d_cnt = nullptr;
     float *d_loss = nullptr;
     int loss_cap = 0;
+    float *d_sL = nullptr, *d_slnT = nullptr;   // fc_surrogate_project scratch
+    size_t sL_rays = 0;
 
     void free_all()
     {
@@ -159,6 +161,8 @@ struct fc_handle {
         dfree(d_err);
         dfree(d_cnt);
         dfree(d_loss);
+        dfree(d_sL);
+        dfree(d_slnT);
     }
 };
 
@@ -1002,6 +1006,47 @@ int fc_surrogate_eval(fc_handle *h, const float *L, int64_t n, float *lnT, int64
         return sur_read_err(h, s, "fc_surrogate_eval");
     }
     return FC_OK;
+}
+
+int fc_surrogate_project(fc_handle *h, int angle_begin, int angle_count, float *out, int out_where,
+                         void *stream)
+{
+    if (!h || !out) return fail(FC_EINVAL, "fc_surrogate_project: null argument");
+    if (out_where != FC_HOST && out_where != FC_DEVICE)
+        return fail(FC_EINVAL, "fc_surrogate_project: bad out_where");
+    if (!h->has_sur) return fail(FC_ESTATE, "fc_surrogate_project: no surrogate");
+    fc::ProjParams p;
+    int rc = fill_proj_params(h, angle_begin, angle_count, &p);
+    if (rc) return rc;
+    DeviceGuard dgd(h->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t n = (size_t)angle_count * h->g.n_v * h->g.n_u;
+    if (n == 0) return FC_OK;
+    if (n > h->sL_rays) {
+        dfree(h->d_sL);
+        dfree(h->d_slnT);
+        FC_CK(cudaMalloc((void **)&h->d_sL, n * h->n_mat * sizeof(float)));
+        FC_CK(cudaMalloc((void **)&h->d_slnT, n * sizeof(float)));
+        h->sL_rays = n;
+    }
+    {
+        Trace t(h, FC_K_LENGTHS, 1, s);
+        FC_CK(fc::launch_project(p, nullptr, h->d_sL, s));
+        t.end();
+    }
+    fc::SurrogateParams sp;
+    fill_sur_params(h, &sp);
+    {
+        Trace t(h, FC_K_SURROGATE_EVAL, 1, s);
+        FC_CK(fc::launch_mlp_eval(sp, h->d_sL, (long long)n, h->d_slnT, h->d_cnt, h->d_err, s));
+        t.end();
+    }
+    if (out_where == FC_DEVICE) {
+        FC_CK(fc::launch_exp(h->d_slnT, out, (long long)n, s));
+        return FC_OK;
+    }
+    FC_CK(fc::launch_exp(h->d_slnT, h->d_slnT, (long long)n, s));
+    return copy_out(out, FC_HOST, h->d_slnT, n * sizeof(float), s);
 }
 
 int fc_energy_sum_lengths(fc_handle *h, const float *L, int64_t n, float *lnT, void *stream)

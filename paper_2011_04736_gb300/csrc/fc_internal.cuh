@@ -118,6 +118,7 @@ cudaError_t launch_mlp_eval(const SurrogateParams &p, const float *L, long long 
                             unsigned int *n_fallback, int *err, cudaStream_t s);
 cudaError_t launch_energy_sum_lengths(const SurrogateParams &p, const float *L, long long n,
                                       float *lnT, cudaStream_t s);
+cudaError_t launch_exp(const float *x, float *y, long long n, cudaStream_t s);
 cudaError_t launch_mlp_lmax(const float *L, long long n, int n_mat, unsigned int *mx,
                             cudaStream_t s);
 cudaError_t launch_mlp_step(const SurrogateParams &p, const float *L, const float *y, long long n,

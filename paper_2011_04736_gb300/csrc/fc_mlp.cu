@@ -707,6 +707,22 @@ cudaError_t launch_mlp_eval(const SurrogateParams &p, const float *L, long long 
     return cudaGetLastError();
 }
 
+__global__ void k_exp(const float *__restrict__ x, float *__restrict__ y, long long n)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+        y[i] = expf(x[i]);
+}
+
+cudaError_t launch_exp(const float *x, float *y, long long n, cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    long long blocks = (n + 255) / 256;
+    if (blocks > 152 * 8) blocks = 152 * 8;
+    k_exp<<<(int)blocks, 256, 0, s>>>(x, y, n);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_energy_sum_lengths(const SurrogateParams &p, const float *L, long long n,
                                       float *lnT, cudaStream_t s)
 {

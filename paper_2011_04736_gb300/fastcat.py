@@ -28,7 +28,7 @@ ENTRY_POINTS = ("fc_create", "fc_destroy", "fc_last_error", "fc_set_geometry", "
                 "fc_poisson", "fc_project_lengths", "fc_profile_enable", "fc_profile_read",
                 "fc_detector_blur_static", "fc_surrogate_init", "fc_surrogate_train",
                 "fc_surrogate_grad", "fc_surrogate_get", "fc_surrogate_set", "fc_surrogate_eval",
-                "fc_energy_sum_lengths", "fc_cnr_grad")
+                "fc_energy_sum_lengths", "fc_cnr_grad", "fc_surrogate_project")
 FC_STATIC_SCRATCH_FLOATS = 8 << 20
 FC_SURROGATE_PARAMS = 34305
 FC_SURROGATE_STATE = 34305 + 52 + 2 * 34305 + 1
@@ -103,6 +103,7 @@ def load():
         "fc_surrogate_eval": (I, [P, P, ctypes.c_int64, P, P, P]),
         "fc_energy_sum_lengths": (I, [P, P, ctypes.c_int64, P, P]),
         "fc_cnr_grad": (I, [P, P, P, P, P, P, I, P, P, P, P, P, P]),
+        "fc_surrogate_project": (I, [P, I, I, P, I, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -287,6 +288,14 @@ def fc_surrogate_eval(h, L, lnT, stream=None, count_fallback=True):
     _check(load().fc_surrogate_eval(h, _dev(L, "L"), lnT.numel(), _dev(lnT, "lnT"),
                                     ctypes.byref(c) if count_fallback else None, _stream(stream)))
     return c.value
+
+
+def fc_surrogate_project(h, angle_begin, angle_count, out, stream=None):
+    """T of every ray by projector path lengths + surrogate (instead of the
+    energy loop) into out (host array or device tensor)."""
+    p, where = _ptr(out)
+    return _check(load().fc_surrogate_project(h, angle_begin, angle_count, p, where,
+                                              _stream(stream)))
 
 
 def fc_energy_sum_lengths(h, L, lnT, stream=None):

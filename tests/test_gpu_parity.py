@@ -327,3 +327,31 @@ def test_full_catphan_reconstruct(fc, orc, catphan_full):
     huref, mu_w = orc.hu(vref, mask)
     assert np.max(np.abs(vol - vref)) <= 5e-4 * mu_w
     assert np.max(np.abs(hu - huref)) <= HU_TOL
+
+
+def test_full_paper_mv_sampled(fc, orc):
+    """Paper-scale MV case (1024^2 x 10 voxels of 0.015625 cm, 1024 x 768
+    detector, 60 MV bins): primary signal at sampled rays of six projections
+    and the intensity of one whole projection against the oracle."""
+    wl = W.WORKLOADS["paper_mv"]
+    g = wl.geom
+    lab = wl.make_phantom()
+    sc = _scanner(fc, wl, lab, noise=False)
+    ks = [0, 97, 211, 360, 531, 719]
+    try:
+        T = np.stack([_project(fc, sc, fc.FC_OUT_PRIMARY, k, 1)[0] for k in ks])
+        I = _project(fc, sc, fc.FC_OUT_INTENSITY, 531, 1)
+    finally:
+        sc.close()
+    rng = np.random.default_rng(2)
+    n = 3000
+    kk = rng.integers(0, len(ks), n)
+    rows = rng.integers(g.n_v // 2 - 16, g.n_v // 2 + 16, n)
+    cols = rng.integers(0, g.n_u, n)
+    rays = np.stack([np.array(ks)[kk], rows, cols], 1)
+    w, d = wl.spectrum()
+    _, Tr = orc.rays(g, lab, w, d, wl.mu(), rays)
+    assert np.max(np.abs(T[kk, rows, cols] - Tr) / Tr) <= REL_T
+    Tp = orc.project_T(g, lab, w, d, wl.mu(), a0=531, na=1)
+    Ir = orc.intensity(Tp, wl.psf_sigma_px, wl.scatter_sigma_px, wl.spr, wl.n0)
+    assert np.max(np.abs(I - Ir) / Ir) <= REL_T

@@ -195,3 +195,20 @@ def test_surrogate_checkpoint_roundtrip(fc, trained):
         assert np.array_equal(fc.fc_surrogate_get(sc2.h), st)
     finally:
         sc2.close()
+
+
+def test_surrogate_project_matches_exact_projection(fc, trained):
+    """Projection with the surrogate in place of the energy loop against the
+    exact projector on the same scan (the trained network's tolerance)."""
+    wl, sc, L, y, _ = trained
+    g = wl.geom
+    Ts = torch.empty((g.n_angles, g.n_v, g.n_u), device="cuda")
+    fc.fc_surrogate_project(sc.h, 0, g.n_angles, Ts)
+    Te = torch.empty_like(Ts)
+    fc.fc_project(sc.h, 0, g.n_angles, fc.FC_OUT_PRIMARY, Te)
+    host = np.empty((2, g.n_v, g.n_u), np.float32)
+    fc.fc_surrogate_project(sc.h, 3, 2, host)
+    torch.cuda.synchronize()
+    d = (torch.log(Ts) - torch.log(Te)).abs()
+    assert float(d.max()) < 1e-2 and float(torch.quantile(d.ravel()[:1 << 20], 0.99)) < 2e-3
+    assert np.array_equal(host, Ts[3:5].cpu().numpy())
