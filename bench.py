@@ -333,9 +333,85 @@ def _extra_paper_scale(fc, torch):
         sc.close()
 
 
+def _extra_dose(fc, torch):
+    """Dose estimate per particle (D0(E), Dp) on the Catphan kV case: one
+    projection, and every projection of the scan; plus the flood height that
+    a 7 mGy scan of 360 projections implies."""
+    wl = W.WORKLOADS["catphan_kv"]
+    g = wl.geom
+    sc = fc.Scanner(wl, noise=False)
+    try:
+        out = {"workload": "catphan_kv: %dx%dx%d voxels, projections of %dx%d, %d bins"
+                           % (g.nx, g.ny, g.nz, g.n_u, g.n_v, wl.n_e)}
+        e, m, r = wl.energies(), wl.muen_water(), wl.densities()
+        for name, na in (("one_projection", 1), ("all_projections", g.n_angles)):
+            fc.fc_dose_estimate(sc.h, 0, na, e, m, r)
+            fc.fc_profile_enable(sc.h, True)
+            reps = 5
+            for _ in range(reps):
+                d0, dp = fc.fc_dose_estimate(sc.h, 0, na, e, m, r)
+            kern = fc.fc_profile_read(sc.h)
+            fc.fc_profile_enable(sc.h, False)
+            ms = kern["dose"][0] / reps
+            out[name] = {"projections": na, "Dp_gy_per_particle": float(dp[0]),
+                         "kernels_ms": ms, "rays_bins_per_s": na * g.n_u * g.n_v * wl.n_e / (ms / 1e3)}
+        out["n0_for_7mGy_over_360"] = fc.fc_fluence_for_dose(
+            sc.h, 7e-3 / 360, out["all_projections"]["Dp_gy_per_particle"])
+        return out
+    finally:
+        sc.close()
+
+
+def _extra_paper_timing(fc, torch):
+    """The paper's timing scan (180 projections, 6 MV, 18 energies, noise
+    before the optical spread) reconstructed to 512^2 x 10 and 1024^2 x 10:
+    device time of simulate + reconstruct + HU, and wall time end to end
+    through the C ABI from a host phantom to a host HU volume (phantom
+    upload, brick map, all kernels, volume download; host-side phantom
+    generation excluded).  The paper's 40 s / 61 s are context (another GPU,
+    TIGRE, whole program)."""
+    out = {}
+    for name, paper_s in (("timing_mv_512", 40.0), ("timing_mv_1024", 61.0)):
+        wl = W.WORKLOADS[name]
+        g = wl.geom
+        lab = wl.make_phantom()
+        hu = np.empty((g.nz, g.ny, g.nx), np.float32)
+        walls = []
+        for rep in range(3):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            sc = fc.Scanner(wl, labels=lab, noise=True)
+            try:
+                fc.fc_set_noise_order(sc.h, fc.FC_NOISE_BEFORE_PSF)
+                fc.fc_project(sc.h, 0, g.n_angles, fc.FC_OUT_NONE, None)
+                fc.fc_reconstruct(sc.h, None, vol_hu=hu)
+                walls.append(time.perf_counter() - t0)
+                if rep == 2:
+                    a = torch.cuda.Event(enable_timing=True)
+                    b = torch.cuda.Event(enable_timing=True)
+                    fc.fc_profile_enable(sc.h, True)
+                    a.record()
+                    fc.fc_project(sc.h, 0, g.n_angles, fc.FC_OUT_NONE, None)
+                    fc.fc_reconstruct(sc.h, None, vol_hu=hu)
+                    b.record()
+                    torch.cuda.synchronize()
+                    kern = fc.fc_profile_read(sc.h)
+                    ms = a.elapsed_time(b)
+            finally:
+                sc.close()
+        out[name] = {"workload": "%dx%dx%d voxels, %d projections of %dx%d, %d bins to %g keV"
+                                 % (g.nx, g.ny, g.nz, g.n_angles, g.n_u, g.n_v, wl.n_e, wl.e_max),
+                     "ms_device": ms, "s_wall_end_to_end": min(walls),
+                     "kernels_ms": {k: v[0] for k, v in kern.items() if v[1]},
+                     "paper_context_s": paper_s}
+    return out
+
+
 def _extras(args, fc, torch):
     out = {}
     jobs = [("adjoint", lambda: _extra_adjoint(fc, torch)),
+            ("dose", lambda: _extra_dose(fc, torch)),
+            ("paper_timing", lambda: _extra_paper_timing(fc, torch)),
             ("paper_scale", lambda: _extra_paper_scale(fc, torch))]
     if not args.no_surrogate:
         from paper_2011_04736_gb300 import surrogate_study

@@ -135,6 +135,20 @@ int fc_set_spectrum_detector(fc_handle *h, const fc_spectrum_detector *s);
 int fc_project(fc_handle *h, int angle_begin, int angle_count, int out_kind,
                float *out, int out_where, void *stream);
 
+/* Order of noise and optical spread in fc_project.
+ *   FC_NOISE_AFTER_BLUR (default): I = N0 (G_psf (x) T + SPR G_sc (x) T),
+ *     K = Poisson(I): noise on the detected signal.
+ *   FC_NOISE_BEFORE_PSF (the order of Sec. II.G: Poisson scaling of the
+ *     counts incident on the detector, then the OSF convolution):
+ *     lambda = N0 (T + SPR G_sc (x) T), K = G_psf (x) Poisson(lambda).
+ *     FC_OUT_INTENSITY then returns lambda; FC_OUT_COUNTS returns K (with
+ *     noise off, G_psf (x) lambda).
+ * The flood stays N0 (1 + SPR) in both orders (the kernels sum to one).
+ * Errors: FC_EINVAL. */
+#define FC_NOISE_AFTER_BLUR 0
+#define FC_NOISE_BEFORE_PSF 1
+int fc_set_noise_order(fc_handle *h, int order);
+
 /* FDK reconstruction (Sec. II.G): p = ln(I_flood / max(K, 1)),
  * I_flood = N0 (1 + SPR); cosine weight SAD / sqrt(SAD^2 + u^2 + v^2) at the
  * isocentre; Ram-Lak row filter; voxel-driven bilinear backprojection with
@@ -167,6 +181,34 @@ int fc_poisson(const float *lam, float *counts, int n_angles, int n_v, int n_u,
 int fc_project_lengths(fc_handle *h, int angle_begin, int angle_count, float *L,
                        void *stream);
 
+/* Dose estimate per particle (Sec. II.H, the D_0(E) and D_p equations):
+ *   D0(E) = E (mu_en/mu)_w(E) sum_i (1 - exp(-sum_m mu_m(E) L_im)) / (N_i M),
+ *   Dp    = sum_E phi(E) D0(E),   phi = w / sum w (the fluence spectrum),
+ * over the N_i = angle_count * n_v * n_u rays of projections angle_begin ..
+ * angle_begin + angle_count - 1 (each ray's attenuation is the projector's
+ * multi-material sum, L from the same traversal), with the phantom mass
+ * M = dx dy dz sum_v rho(label_v).  Units: keV, grams, Gy per particle
+ * (1 keV / g = 1.602176634e-13 Gy).  The paper's empirical linear fit to
+ * Monte Carlo doses is not part of this estimate.
+ *   e_kev        [n_e] host: bin energies, > 0;
+ *   muen_over_mu [n_e] host: energy-absorption over attenuation coefficient
+ *                of water, in [0, 1];
+ *   rho          [n_mat] host: material mass densities, g/cm^3, > 0;
+ *   d0 [n_e], dp [1]: results, host or device memory per `out_where` (with
+ *                FC_DEVICE the copies are queued on `stream`).
+ * Partial sums run in a fixed order: repeated calls give identical bits.
+ * Errors: FC_ESTATE (geometry, phantom or spectrum missing), FC_EINVAL
+ * (range, angle_count < 1, values), FC_ECUDA. */
+int fc_dose_estimate(fc_handle *h, int angle_begin, int angle_count, const double *e_kev,
+                     const double *muen_over_mu, const double *rho, double *d0, double *dp,
+                     int out_where, void *stream);
+
+/* Flood height for a requested mean phantom dose per projection (Sec. II.H,
+ * the H equation): N_gamma = dose_gy / dp_gy particles over a beam of
+ * A / A_p = n_u n_v detector pixels, so *n0 = dose_gy / (dp_gy n_u n_v).
+ * Host arithmetic only.  Errors: FC_EINVAL, FC_ESTATE (no geometry). */
+int fc_fluence_for_dose(const fc_handle *h, double dose_gy, double dp_gy, double *n0);
+
 /* Kernel-time tracing.  While enabled, every kernel the handle launches is
  * bracketed by CUDA events recorded on the launching stream.  Kernel ids: */
 #define FC_K_PROJECT     0  /* projector + energy integral */
@@ -180,7 +222,8 @@ int fc_project_lengths(fc_handle *h, int angle_begin, int angle_count, float *L,
 #define FC_K_SURROGATE_EVAL  8  /* surrogate inference (fc_surrogate_eval) */
 #define FC_K_SURROGATE_TRAIN 9  /* surrogate training steps (4 kernels per step) */
 #define FC_K_ENERGY_SUM     10  /* exact energy sum from path lengths */
-#define FC_K_COUNT          11
+#define FC_K_DOSE           11  /* dose estimate (three kernels) */
+#define FC_K_COUNT          12
 
 /* Enable (1) or disable (0) tracing; enabling discards pending records.
  * Errors: FC_EINVAL. */

@@ -200,6 +200,16 @@ def intensity(T, sig_psf, sig_sc, spr, n0):
     return out.reshape(shp)
 
 
+def counts_noise_before_psf(T, sig_psf, sig_sc, spr, n0, seed=None, k0=0):
+    """Sec. II.G order: rate lambda = N0 (T + SPR G_sc (x) T) incident on the
+    detector, Poisson counts drawn from it (binary32 rates; skipped when
+    seed is None), then the optical spread: K = G_psf (x) counts.
+    Returns (lambda, K)."""
+    lam = intensity(T, 0.0, sig_sc, spr, n0)
+    k = lam if seed is None else poisson(lam, seed, k0).astype(np.float64)
+    return lam, gauss_blur(k, sig_psf)
+
+
 def i_flood(n0, spr):
     """Flood intensity: T = 1 everywhere, both kernels sum to one."""
     return n0 * (1.0 + spr)

@@ -73,10 +73,12 @@ struct fc_handle {
     // spectrum / detector
     int n_e = 0, n_mat = 0;
     std::vector<float> wd;     // [n_e]
+    std::vector<double> phi;   // [n_e] fluence spectrum w / sum w
     std::vector<float> mu2;    // [n_e][kMaxMat]
     double psf = 0.0, sc = 0.0, spr = 0.0, n0 = 1.0;
     uint64_t seed = 0;
     int noise = 0;
+    int noise_order = FC_NOISE_AFTER_BLUR;
     double water_r = 1.0, zmargin = 0.1;
     // device buffers
     float2 *d_trig = nullptr;
@@ -118,6 +120,7 @@ struct fc_handle {
     int loss_cap = 0;
     float *d_sL = nullptr, *d_slnT = nullptr;   // fc_surrogate_project scratch
     size_t sL_rays = 0;
+    double *d_dose = nullptr;   // dose estimate: partial sums, result, label counts
 
     void free_all()
     {
@@ -133,6 +136,7 @@ struct fc_handle {
         dfree(d_hu);
         dfree(d_part);
         dfree(d_flag);
+        dfree(d_dose);
         for (auto &r : pending) {
             cudaEventDestroy(r.a);
             cudaEventDestroy(r.b);
@@ -440,6 +444,10 @@ int fc_set_spectrum_detector(fc_handle *h, const fc_spectrum_detector *s)
     h->n_e = s->n_e;
     h->n_mat = s->n_mat;
     h->wd.assign(s->n_e, 0.0f);
+    h->phi.assign(s->n_e, 0.0);
+    double wsum = 0.0;
+    for (int e = 0; e < s->n_e; ++e) wsum += s->w[e];
+    for (int e = 0; e < s->n_e; ++e) h->phi[e] = s->w[e] / wsum;
     h->mu2.assign((size_t)s->n_e * fc::kMaxMat, 0.0f);
     const double log2e = 1.4426950408889634;
     for (int e = 0; e < s->n_e; ++e) {
@@ -505,6 +513,39 @@ static int fill_proj_params(fc_handle *h, int a0, int na, fc::ProjParams *p)
     return FC_OK;
 }
 
+// out = n0 (G_psf (x) in + spr G_sc (x) in) over `n` images starting at
+// element `off` of the projection buffers (two passes through the handle's
+// row intermediates; `in` and `out` may alias).
+static int run_blur(fc_handle *h, const float *in, float *out, size_t off, int n, double psf,
+                    double sc, double n0, double spr, cudaStream_t s)
+{
+    fc::BlurParams b;
+    memset(&b, 0, sizeof(b));
+    b.n_u = h->g.n_u;
+    b.n_v = h->g.n_v;
+    int rc = gauss_taps(psf, b.gp, &b.rp);
+    if (rc) return rc;
+    rc = gauss_taps(sc, b.gs, &b.rs);
+    if (rc) return rc;
+    b.n0 = (float)n0;
+    b.spr = (float)spr;
+    {
+        Trace t(h, FC_K_BLUR_ROWS, 1, s);
+        FC_CK(fc::launch_blur_rows(b, in, h->d_tp + off, h->d_ts + off, n, s));
+        t.end();
+    }
+    cudaError_t e;
+    {
+        Trace t(h, FC_K_BLUR_COLS, 1, s);
+        e = fc::launch_blur_cols(b, h->d_tp + off, h->d_ts + off, out, n, s);
+        if (e == cudaSuccess) t.end();
+    }
+    if (e == cudaErrorInvalidValue)
+        return fail(FC_EINVAL, "fc_project: detector too tall for the column blur (n_v %d)", h->g.n_v);
+    FC_CK(e);
+    return FC_OK;
+}
+
 int fc_project(fc_handle *h, int angle_begin, int angle_count, int out_kind, float *out,
                int out_where, void *stream)
 {
@@ -529,40 +570,46 @@ int fc_project(fc_handle *h, int angle_begin, int angle_count, int out_kind, flo
         t.end();
     }
     if (out_kind == FC_OUT_PRIMARY) return angle_count ? copy_out(out, out_where, h->d_T + off, bytes, s) : FC_OK;
-    fc::BlurParams b;
-    memset(&b, 0, sizeof(b));
-    b.n_u = h->g.n_u;
-    b.n_v = h->g.n_v;
-    rc = gauss_taps(h->psf, b.gp, &b.rp);
-    if (rc) return rc;
-    rc = gauss_taps(h->sc, b.gs, &b.rs);
-    if (rc) return rc;
-    b.n0 = (float)h->n0;
-    b.spr = (float)h->spr;
     const bool noise = (out_kind != FC_OUT_INTENSITY) && h->noise;
-    {
-        Trace t(h, FC_K_BLUR_ROWS, 1, s);
-        FC_CK(fc::launch_blur_rows(b, h->d_T + off, h->d_tp + off, h->d_ts + off, angle_count, s));
-        t.end();
-    }
-    cudaError_t e;
-    {
-        Trace t(h, FC_K_BLUR_COLS, 1, s);
-        e = fc::launch_blur_cols(b, h->d_tp + off, h->d_ts + off, h->d_counts + off, angle_count, s);
-        if (e == cudaSuccess) t.end();
-    }
-    if (e == cudaErrorInvalidValue)
-        return fail(FC_EINVAL, "fc_project: detector too tall for the column blur (n_v %d)", h->g.n_v);
-    FC_CK(e);
-    if (noise) {
-        Trace t(h, FC_K_NOISE, 1, s);
-        FC_CK(fc::launch_poisson(h->d_counts + off, h->d_counts + off, angle_count, h->g.n_v,
-                                 h->g.n_u, angle_begin, h->seed, s));
-        t.end();
+    if (h->noise_order == FC_NOISE_BEFORE_PSF) {
+        // Sec. II.G order: counts drawn from the scatter-added rate, then the
+        // optical spread applied to the counts
+        rc = run_blur(h, h->d_T + off, h->d_counts + off, off, angle_count, 0.0, h->sc, h->n0, h->spr, s);
+        if (rc) return rc;
+        if (out_kind == FC_OUT_INTENSITY) {
+            h->has_counts = true;
+            return angle_count ? copy_out(out, out_where, h->d_counts + off, bytes, s) : FC_OK;
+        }
+        if (noise) {
+            Trace t(h, FC_K_NOISE, 1, s);
+            FC_CK(fc::launch_poisson(h->d_counts + off, h->d_counts + off, angle_count, h->g.n_v,
+                                     h->g.n_u, angle_begin, h->seed, s));
+            t.end();
+        }
+        rc = run_blur(h, h->d_counts + off, h->d_counts + off, off, angle_count, h->psf, 0.0, 1.0, 0.0, s);
+        if (rc) return rc;
+    } else {
+        rc = run_blur(h, h->d_T + off, h->d_counts + off, off, angle_count, h->psf, h->sc, h->n0, h->spr, s);
+        if (rc) return rc;
+        if (noise) {
+            Trace t(h, FC_K_NOISE, 1, s);
+            FC_CK(fc::launch_poisson(h->d_counts + off, h->d_counts + off, angle_count, h->g.n_v,
+                                     h->g.n_u, angle_begin, h->seed, s));
+            t.end();
+        }
     }
     h->has_counts = true;
     if (out_kind == FC_OUT_NONE || angle_count == 0) return FC_OK;
     return copy_out(out, out_where, h->d_counts + off, bytes, s);
+}
+
+int fc_set_noise_order(fc_handle *h, int order)
+{
+    if (!h) return fail(FC_EINVAL, "fc_set_noise_order: null handle");
+    if (order != FC_NOISE_AFTER_BLUR && order != FC_NOISE_BEFORE_PSF)
+        return fail(FC_EINVAL, "fc_set_noise_order: unknown order %d", order);
+    h->noise_order = order;
+    return FC_OK;
 }
 
 int fc_project_lengths(fc_handle *h, int angle_begin, int angle_count, float *L, void *stream)
@@ -575,6 +622,73 @@ int fc_project_lengths(fc_handle *h, int angle_begin, int angle_count, float *L,
     Trace t(h, FC_K_LENGTHS, 1, (cudaStream_t)stream);
     FC_CK(fc::launch_project(p, nullptr, L, (cudaStream_t)stream));
     t.end();
+    return FC_OK;
+}
+
+int fc_dose_estimate(fc_handle *h, int angle_begin, int angle_count, const double *e_kev,
+                     const double *muen_over_mu, const double *rho, double *d0, double *dp,
+                     int out_where, void *stream)
+{
+    if (!h || !e_kev || !muen_over_mu || !rho || !d0 || !dp)
+        return fail(FC_EINVAL, "fc_dose_estimate: null argument");
+    if (out_where != FC_HOST && out_where != FC_DEVICE)
+        return fail(FC_EINVAL, "fc_dose_estimate: bad out_where");
+    fc::ProjParams p;
+    int rc = fill_proj_params(h, angle_begin, angle_count, &p);
+    if (rc) return rc;
+    if (angle_count < 1) return fail(FC_EINVAL, "fc_dose_estimate: need at least one projection");
+    fc::DoseParams d;
+    memset(&d, 0, sizeof(d));
+    d.n_e = h->n_e;
+    d.n_mat = h->n_mat;
+    for (int e = 0; e < h->n_e; ++e) {
+        if (!(e_kev[e] > 0) || !isfinite(e_kev[e]))
+            return fail(FC_EINVAL, "fc_dose_estimate: bin energy %d must be > 0", e);
+        if (!(muen_over_mu[e] >= 0) || !(muen_over_mu[e] <= 1))
+            return fail(FC_EINVAL, "fc_dose_estimate: mu_en/mu at bin %d outside [0, 1]", e);
+        d.e_kev[e] = e_kev[e];
+        d.muen[e] = muen_over_mu[e];
+        d.phi[e] = h->phi[e];
+    }
+    for (int m = 0; m < h->n_mat; ++m) {
+        if (!(rho[m] > 0) || !isfinite(rho[m]))
+            return fail(FC_EINVAL, "fc_dose_estimate: density of material %d must be > 0", m);
+        d.rho[m] = rho[m];
+    }
+    DeviceGuard dgd(h->device);
+    d.n_part = fc::dose_blocks(p);
+    d.n_rays = (double)angle_count * h->g.n_u * h->g.n_v;
+    d.voxel_cm3 = h->g.dx_cm * h->g.dy_cm * h->g.dz_cm;
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t n_part = (size_t)fc::kDoseBlocks * fc::kMaxBins, n_out = fc::kMaxBins + 1;
+    if (!h->d_dose)
+        FC_CK(cudaMalloc(&h->d_dose, (n_part + n_out + fc::kMaxMat) * sizeof(double)));
+    double *part = h->d_dose, *res = h->d_dose + n_part;
+    auto *count = reinterpret_cast<unsigned long long *>(res + n_out);
+    {
+        Trace t(h, FC_K_DOSE, 3, s);
+        FC_CK(fc::launch_dose(p, d, part, count, res, s));
+        t.end();
+    }
+    if (out_where == FC_DEVICE) {
+        FC_CK(cudaMemcpyAsync(d0, res, h->n_e * sizeof(double), cudaMemcpyDeviceToDevice, s));
+        FC_CK(cudaMemcpyAsync(dp, res + h->n_e, sizeof(double), cudaMemcpyDeviceToDevice, s));
+        return FC_OK;
+    }
+    FC_CK(cudaMemcpyAsync(d0, res, h->n_e * sizeof(double), cudaMemcpyDeviceToHost, s));
+    FC_CK(cudaMemcpyAsync(dp, res + h->n_e, sizeof(double), cudaMemcpyDeviceToHost, s));
+    FC_CK(cudaStreamSynchronize(s));
+    return FC_OK;
+}
+
+int fc_fluence_for_dose(const fc_handle *h, double dose_gy, double dp_gy, double *n0)
+{
+    if (!h || !n0) return fail(FC_EINVAL, "fc_fluence_for_dose: null argument");
+    if (!h->has_geom) return fail(FC_ESTATE, "fc_fluence_for_dose: geometry not set");
+    if (!(dose_gy >= 0) || !(dp_gy > 0) || !isfinite(dose_gy) || !isfinite(dp_gy))
+        return fail(FC_EINVAL, "fc_fluence_for_dose: need dose >= 0 and dose per particle > 0");
+    // N_gamma = dose / Dp particles spread over the A / A_p = n_u n_v pixels
+    *n0 = dose_gy / dp_gy / ((double)h->g.n_u * h->g.n_v);
     return FC_OK;
 }
 

@@ -43,6 +43,20 @@ struct ProjParams {
     float mu2[kMaxBins][kMaxMat];   // mu * log2(e), zero padded
 };
 
+// Final reduction of the dose estimate (Sec. II.H).
+constexpr int kDoseBlocks = 2048;            // most blocks of the per-bin partial sums
+constexpr double kGyGramPerKev = 1.602176634e-13;  // 1 keV per gram, in Gy
+
+struct DoseParams {
+    int n_e, n_mat, n_part;
+    double n_rays;                 // N_i: rays the sums run over
+    double voxel_cm3;              // dx dy dz
+    double e_kev[kMaxBins];        // bin energies
+    double muen[kMaxBins];         // (mu_en / mu) of water
+    double phi[kMaxBins];          // fluence spectrum, sum 1
+    double rho[kMaxMat];           // material densities, g/cm^3
+};
+
 struct BlurParams {
     int n_u, n_v;
     int rp, rs;             // tap radii of the PSF and scatter kernels
@@ -176,6 +190,9 @@ cudaError_t launch_backproject(const FdkParams &p, const float *filt, double *vo
                                cudaStream_t s);
 cudaError_t launch_hu(const DevGeom &g, const double *vol, float *hu, double *partials,
                       float radius, int zcut, cudaStream_t s);
+cudaError_t launch_dose(const ProjParams &p, const DoseParams &d, double *part,
+                        unsigned long long *count, double *out, cudaStream_t s);
+int dose_blocks(const ProjParams &p);
 cudaError_t launch_brick_map(const uint8_t *labels, uint8_t *bricks, int nx, int ny, int nz,
                              int n_mat, unsigned int *bad, cudaStream_t s);
 

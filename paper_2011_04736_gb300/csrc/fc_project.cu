@@ -47,18 +47,12 @@ __device__ __forceinline__ int clampi(int v, int lo, int hi)
 
 }  // namespace
 
-template <bool EMIT_L>
-__global__ void __launch_bounds__(256)
-k_project(const __grid_constant__ ProjParams p, float *__restrict__ T, float *__restrict__ Lout)
+// Per-material path lengths L of pixel ray (iu, iv) of projection k; returns
+// whether the ray meets the voxel box.
+__device__ __forceinline__ bool trace_ray(const ProjParams &p, int iu, int iv, int k,
+                                          float (&L)[kMaxMat])
 {
     const DevGeom &g = p.g;
-    const int iu = blockIdx.x * 32 + threadIdx.x;
-    const int iv = blockIdx.y * blockDim.y + threadIdx.y;
-    const int kl = blockIdx.z;
-    if (iu >= g.n_u || iv >= g.n_v) return;
-    const int k = p.angle0 + kl;
-
-    float L[kMaxMat];
 #pragma unroll
     for (int m = 0; m < kMaxMat; ++m) L[m] = 0.0f;
 
@@ -207,6 +201,21 @@ k_project(const __grid_constant__ ProjParams p, float *__restrict__ T, float *__
         }
     }
 
+    return hit;
+}
+
+template <bool EMIT_L>
+__global__ void __launch_bounds__(256)
+k_project(const __grid_constant__ ProjParams p, float *__restrict__ T, float *__restrict__ Lout)
+{
+    const DevGeom &g = p.g;
+    const int iu = blockIdx.x * 32 + threadIdx.x;
+    const int iv = blockIdx.y * blockDim.y + threadIdx.y;
+    const int kl = blockIdx.z;
+    if (iu >= g.n_u || iv >= g.n_v) return;
+    const int k = p.angle0 + kl;
+    float L[kMaxMat];
+    const bool hit = trace_ray(p, iu, iv, k, L);
     const size_t ray = ((size_t)kl * g.n_v + iv) * g.n_u + iu;
     if (EMIT_L) {
 #pragma unroll
@@ -241,6 +250,175 @@ cudaError_t launch_project(const ProjParams &p, float *T, float *L_out, cudaStre
         k_project<true><<<grid, block, 0, s>>>(p, T, L_out);
     else
         k_project<false><<<grid, block, 0, s>>>(p, T, L_out);
+    return cudaGetLastError();
+}
+
+// Dose estimate, Sec. II.H: for every energy bin E, the sum over the rays of
+// the fraction a ray loses in the phantom, 1 - exp(-sum_m mu_m(E) L_m).
+// Blocks walk 32 x 8 pixel tiles in a fixed order; each warp traces its row
+// of 32 rays, stages their path lengths in its own shared slice and then sums
+// bins lane, lane + 32, ... over those 32 rays (warp-synchronous: no block
+// barrier inside the loop, so a warp with long rays holds up no other).  The
+// warps' per-bin sums are folded in a fixed order at the end: the partials
+// are reproducible.
+static_assert(kMaxMat == 8 && kMaxBins <= 256, "dose kernel: two float4 per ray, 8 bins per lane");
+
+template <int NQ>
+__global__ void __launch_bounds__(256)
+k_dose_partial(const __grid_constant__ ProjParams p, double *__restrict__ part)
+{
+    __shared__ float4 sL[8][32][2];
+    __shared__ double red[8][kMaxBins];
+    const DevGeom &g = p.g;
+    const int lane = threadIdx.x, w = threadIdx.y;
+    const int tu = (g.n_u + 31) / 32, tv = (g.n_v + 7) / 8;
+    const long long n_tiles = (long long)tu * tv * p.n_angles_launch;
+    double acc[NQ];
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) acc[q] = 0.0;
+    for (long long t = blockIdx.x; t < n_tiles; t += gridDim.x) {
+        const int bu = (int)(t % tu), bv = (int)((t / tu) % tv);
+        const int kl = (int)(t / ((long long)tu * tv));
+        const int iu = bu * 32 + lane, iv = bv * 8 + w;
+        float L[kMaxMat];
+        if (iu < g.n_u && iv < g.n_v) {
+            trace_ray(p, iu, iv, p.angle0 + kl, L);
+        } else {
+#pragma unroll
+            for (int m = 0; m < kMaxMat; ++m) L[m] = 0.0f;
+        }
+        sL[w][lane][0] = make_float4(L[0], L[1], L[2], L[3]);
+        sL[w][lane][1] = make_float4(L[4], L[5], L[6], L[7]);
+        __syncwarp();
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+            const int e = lane + 32 * q;
+            if (e < p.n_e) {
+                float mu[kMaxMat];
+#pragma unroll
+                for (int m = 0; m < kMaxMat; ++m) mu[m] = p.mu2[e][m];
+                float sum = 0.0f, comp = 0.0f;
+#pragma unroll 4
+                for (int r = 0; r < 32; ++r) {
+                    const float4 a0 = sL[w][r][0], a1 = sL[w][r][1];
+                    float a = mu[0] * a0.x;
+                    a = fmaf(mu[1], a0.y, a);
+                    a = fmaf(mu[2], a0.z, a);
+                    a = fmaf(mu[3], a0.w, a);
+                    a = fmaf(mu[4], a1.x, a);
+                    a = fmaf(mu[5], a1.y, a);
+                    a = fmaf(mu[6], a1.z, a);
+                    a = fmaf(mu[7], a1.w, a);
+                    const float y = (1.0f - exp2f(-a)) - comp;
+                    const float s2 = sum + y;
+                    comp = (s2 - sum) - y;
+                    sum = s2;
+                }
+                acc[q] += (double)sum;
+            }
+        }
+        __syncwarp();
+    }
+#pragma unroll
+    for (int q = 0; q < NQ; ++q)
+        if (lane + 32 * q < p.n_e) red[w][lane + 32 * q] = acc[q];
+    __syncthreads();
+    const int tid = w * 32 + lane;
+    if (tid < p.n_e) {
+        double a = 0.0;
+        for (int ww = 0; ww < 8; ++ww) a += red[ww][tid];
+        part[(size_t)blockIdx.x * p.n_e + tid] = a;
+    }
+}
+
+// Voxels per label (for the phantom mass): one ballot per label and warp.
+__global__ void __launch_bounds__(256)
+k_label_count(const uint8_t *__restrict__ lab, size_t n, int n_mat, unsigned long long *count)
+{
+    __shared__ unsigned int c[kMaxMat];
+    if (threadIdx.x < kMaxMat) c[threadIdx.x] = 0;
+    __syncthreads();
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    const size_t n_pad = (n + 31) / 32 * 32;   // every lane of a warp takes each ballot
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i - threadIdx.x % 32 < n_pad;
+         i += stride) {
+        const int v = i < n ? lab[i] : -1;
+        for (int m = 0; m < n_mat; ++m) {
+            const unsigned int b = __ballot_sync(0xffffffffu, v == m);
+            if (threadIdx.x % 32 == 0 && b) atomicAdd(&c[m], (unsigned int)__popc(b));
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < n_mat && c[threadIdx.x])
+        atomicAdd(&count[threadIdx.x], (unsigned long long)c[threadIdx.x]);
+}
+
+// D0(E) = E (mu_en/mu)_w(E) sum_i (1 - exp(-mu_i(E) x_i)) / (N_i M) and
+// Dp = sum_E phi(E) D0(E) (Sec. II.H); out = [D0(E_0) .. D0(E_{n-1}), Dp].
+__global__ void __launch_bounds__(256)
+k_dose_final(const __grid_constant__ DoseParams d, const double *__restrict__ part,
+             const unsigned long long *__restrict__ count, double *__restrict__ out)
+{
+    __shared__ double s[kMaxBins];
+    const int e = threadIdx.x;
+    double mass = 0.0;
+    for (int m = 0; m < d.n_mat; ++m) mass += (double)count[m] * d.rho[m];
+    mass *= d.voxel_cm3;
+    if (e < d.n_e) {
+        double a = 0.0;
+        for (int b = 0; b < d.n_part; ++b) a += part[(size_t)b * d.n_e + e];
+        const double d0 = kGyGramPerKev * d.e_kev[e] * d.muen[e] * a / (d.n_rays * mass);
+        out[e] = d0;
+        s[e] = d.phi[e] * d0;
+    }
+    __syncthreads();
+    if (e == 0) {
+        double dp = 0.0;
+        for (int i = 0; i < d.n_e; ++i) dp += s[i];
+        out[d.n_e] = dp;
+    }
+}
+
+template <int NQ>
+static int dose_grid(long long tiles)
+{
+    int dev = 0, sms = 0, per_sm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_dose_partial<NQ>, 256, 0) !=
+            cudaSuccess || per_sm < 1)
+        per_sm = 1, sms = sms > 0 ? sms : 1;
+    long long n = (long long)sms * per_sm;
+    n = n < kDoseBlocks ? n : kDoseBlocks;
+    return (int)(tiles < n ? tiles : n);
+}
+
+int dose_blocks(const ProjParams &p)
+{
+    const long long tiles = (long long)((p.g.n_u + 31) / 32) * ((p.g.n_v + 7) / 8) * p.n_angles_launch;
+    if (p.n_e <= 32) return dose_grid<1>(tiles);
+    if (p.n_e <= 64) return dose_grid<2>(tiles);
+    if (p.n_e <= 128) return dose_grid<4>(tiles);
+    return dose_grid<8>(tiles);
+}
+
+cudaError_t launch_dose(const ProjParams &p, const DoseParams &d, double *part,
+                        unsigned long long *count, double *out, cudaStream_t s)
+{
+    const size_t nvox = (size_t)p.g.nx * p.g.ny * p.g.nz;
+    cudaError_t e = cudaMemsetAsync(count, 0, kMaxMat * sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return e;
+    k_label_count<<<152 * 4, 256, 0, s>>>(p.labels, nvox, d.n_mat, count);
+    const dim3 blk(32, 8);
+    if (d.n_e <= 32)
+        k_dose_partial<1><<<d.n_part, blk, 0, s>>>(p, part);
+    else if (d.n_e <= 64)
+        k_dose_partial<2><<<d.n_part, blk, 0, s>>>(p, part);
+    else if (d.n_e <= 128)
+        k_dose_partial<4><<<d.n_part, blk, 0, s>>>(p, part);
+    else
+        k_dose_partial<8><<<d.n_part, blk, 0, s>>>(p, part);
+    k_dose_final<<<1, 256, 0, s>>>(d, part, count, out);
     return cudaGetLastError();
 }
 

@@ -20,6 +20,7 @@ LIB_PATH = os.path.join(_HERE, "lib", "libfastcat.so")
 FC_OK, FC_EINVAL, FC_ENOMEM, FC_ECUDA, FC_ESTATE, FC_ETIMEOUT = 0, -1, -2, -3, -4, -5
 FC_HOST, FC_DEVICE = 0, 1
 FC_OUT_NONE, FC_OUT_PRIMARY, FC_OUT_INTENSITY, FC_OUT_COUNTS = 0, 1, 2, 3
+FC_NOISE_AFTER_BLUR, FC_NOISE_BEFORE_PSF = 0, 1
 FC_MAX_MATERIALS, FC_MAX_BINS = 8, 256
 
 # every entry point declared in include/fastcat.h
@@ -28,12 +29,13 @@ ENTRY_POINTS = ("fc_create", "fc_destroy", "fc_last_error", "fc_set_geometry", "
                 "fc_poisson", "fc_project_lengths", "fc_profile_enable", "fc_profile_read",
                 "fc_detector_blur_static", "fc_surrogate_init", "fc_surrogate_train",
                 "fc_surrogate_grad", "fc_surrogate_get", "fc_surrogate_set", "fc_surrogate_eval",
-                "fc_energy_sum_lengths", "fc_cnr_grad", "fc_surrogate_project")
+                "fc_energy_sum_lengths", "fc_cnr_grad", "fc_surrogate_project",
+                "fc_dose_estimate", "fc_fluence_for_dose", "fc_set_noise_order")
 FC_STATIC_SCRATCH_FLOATS = 8 << 20
 FC_SURROGATE_PARAMS = 34305
 FC_SURROGATE_STATE = 34305 + 52 + 2 * 34305 + 1
 FC_K_NAMES = ("project", "blur_rows", "blur_cols", "fdk_filter", "backproject", "hu", "lengths",
-              "noise", "surrogate_eval", "surrogate_train", "energy_sum")
+              "noise", "surrogate_eval", "surrogate_train", "energy_sum", "dose")
 
 
 class FastcatError(RuntimeError):
@@ -104,6 +106,9 @@ def load():
         "fc_energy_sum_lengths": (I, [P, P, ctypes.c_int64, P, P]),
         "fc_cnr_grad": (I, [P, P, P, P, P, P, I, P, P, P, P, P, P]),
         "fc_surrogate_project": (I, [P, I, I, P, I, P]),
+        "fc_dose_estimate": (I, [P, I, I, P, P, P, P, P, I, P]),
+        "fc_fluence_for_dose": (I, [P, ctypes.c_double, ctypes.c_double, P]),
+        "fc_set_noise_order": (I, [P, I]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -214,6 +219,37 @@ def fc_project_lengths(h, angle_begin, angle_count, L, stream=None):
     if where != FC_DEVICE:
         raise ValueError("fc_project_lengths writes a device tensor")
     return _check(load().fc_project_lengths(h, angle_begin, angle_count, p, _stream(stream)))
+
+
+def fc_dose_estimate(h, angle_begin, angle_count, e_kev, muen_over_mu, rho, d0=None, dp=None,
+                     stream=None):
+    """D0(E) and Dp (Gy per particle).  With d0/dp omitted, returns host
+    arrays; device tensors d0 [n_e] / dp [1] (float64) receive the results on
+    `stream` instead."""
+    e = np.ascontiguousarray(e_kev, np.float64)
+    m = np.ascontiguousarray(muen_over_mu, np.float64)
+    r = np.ascontiguousarray(rho, np.float64)
+    if d0 is None:
+        d0 = np.zeros(len(e), np.float64)
+    if dp is None:
+        dp = np.zeros(1, np.float64)
+    p0, w0 = _ptr(d0)
+    p1, w1 = _ptr(dp)
+    if w0 != w1:
+        raise ValueError("d0 and dp must both be host or both be device buffers")
+    _check(load().fc_dose_estimate(h, angle_begin, angle_count, e.ctypes.data, m.ctypes.data,
+                                   r.ctypes.data, p0, p1, w0, _stream(stream)))
+    return d0, dp
+
+
+def fc_set_noise_order(h, order):
+    return _check(load().fc_set_noise_order(h, order))
+
+
+def fc_fluence_for_dose(h, dose_gy, dp_gy):
+    n0 = ctypes.c_double()
+    _check(load().fc_fluence_for_dose(h, dose_gy, dp_gy, ctypes.byref(n0)))
+    return n0.value
 
 
 def fc_profile_enable(h, enable=True):
@@ -368,6 +404,12 @@ class Scanner:
         fc_set_spectrum_detector(self.h, w, d, workload.mu(), workload.psf_sigma_px,
                                  workload.scatter_sigma_px, workload.spr, workload.n0,
                                  workload.seed, workload.noise if noise is None else noise)
+
+    def dose(self, angle_begin=0, angle_count=1):
+        """(D0(E) [n_e], Dp) in Gy per particle for the workload's materials."""
+        d0, dp = fc_dose_estimate(self.h, angle_begin, angle_count, self.w.energies(),
+                                  self.w.muen_water(), self.w.densities())
+        return d0, float(dp[0])
 
     def close(self):
         if self.h is not None:

@@ -203,6 +203,14 @@ class Workload:
     def mu(self):
         return mu_table(self.labels, self.energies())
 
+    def densities(self):
+        """Mass density of each label's material, g/cm^3."""
+        return np.array([MATERIALS[m][0] for m in self.labels], dtype=np.float64)
+
+    def muen_water(self):
+        """(mu_en / mu) of water at the bin energies."""
+        return muen_over_mu("water", self.energies())
+
     def make_phantom(self):
         g = self.geom
         if self.phantom == "catphan":
@@ -314,6 +322,21 @@ WORKLOADS = {
         Geometry(SAD_CM, SDD_CM, 512, 512, 0.05, 0.05, 360, 256, 256, 256, 0.0625, 0.0625, 0.0625),
         "head", HEAD_LABELS, 20.0, 140.0, 120, "kv", 140.0,
         0.8, 20.0, 0.2, 1e5, 3, False),
+    # the paper's timing scan: 180 projections of a 6 MV beam in 18 energy
+    # bins, reconstructed to 1024^2 x 10 and to 512^2 x 10 (noise drawn
+    # before the optical spread, as the paper orders it)
+    "timing_mv_1024": Workload(
+        "timing_mv_1024",
+        Geometry(SAD_CM, SDD_CM, 1024, 768, 0.0392, 0.0392, 180, 1024, 1024, 10,
+                 0.015625, 0.015625, 0.015625),
+        "catphan", CATPHAN_LABELS, 100.0, 6000.0, 18, "mv", 6000.0,
+        1.2, 20.0, 0.2, 1e5, 5, True),
+    "timing_mv_512": Workload(
+        "timing_mv_512",
+        Geometry(SAD_CM, SDD_CM, 1024, 768, 0.0392, 0.0392, 180, 512, 512, 10,
+                 0.03125, 0.03125, 0.03125),
+        "catphan", CATPHAN_LABELS, 100.0, 6000.0, 18, "mv", 6000.0,
+        1.2, 20.0, 0.2, 1e5, 5, True),
     # adjoint design case
     "adjoint_kv": Workload(
         "adjoint_kv",
@@ -364,3 +387,27 @@ def adjoint_inputs(w: Workload, seed=4):
         dmin = np.min(np.hypot(x[None, :] - cx, y[:, None] - cy))
         rois.append((cx, cy, max(0.7 * r, dmin + 1e-6)))
     return dict(logits=logits, D=D, rho0=rho0, rho=rho, z=z, rois=rois, labels=lab)
+
+
+def klein_nishina_scatter_ratio(e_kev):
+    """sigma_s / sigma_Thomson: the part of the Klein-Nishina cross-section
+    carried off by the scattered photon's energy (Evans' closed form)."""
+    k = np.asarray(e_kev, dtype=np.float64) / ELECTRON_REST_KEV
+    l2k = np.log1p(2.0 * k)
+    t = (l2k / k**3 + 2.0 * (1.0 + k) * (2.0 * k * k - 2.0 * k - 1.0) / (k * k * (1.0 + 2.0 * k) ** 2)
+         + 8.0 * k * k / (3.0 * (1.0 + 2.0 * k) ** 3))
+    return 0.375 * t
+
+
+def muen_over_mu(name, e_kev):
+    """Energy-absorption to attenuation ratio of material ``name``: the
+    photo-electric part deposits all its energy, incoherent scattering the
+    Klein-Nishina energy-transfer fraction (no fluorescence or radiative
+    losses)."""
+    rho, zoa, a = MATERIALS[name]
+    e = np.asarray(e_kev, dtype=np.float64)
+    tau = a * e**-3
+    kn = klein_nishina_ratio(e)
+    sig = THOMSON_MASS * zoa * kn
+    ftr = 1.0 - klein_nishina_scatter_ratio(e) / kn
+    return (tau + sig * ftr) / (tau + sig)

@@ -75,8 +75,10 @@ def test_cnr_autograd_function(fc):
                                         z, inp["rois"])
         torch.cuda.synchronize()
         assert float(J) == pytest.approx(J2)
-        assert np.allclose(lg.grad.numpy(), 2.0 * gl)
-        assert np.allclose(dd.grad.numpy(), 2.0 * gd)
-        assert torch.allclose(rho.grad, 2.0 * gr)
+        # the density and spectrum gradients are accumulated with atomics, so
+        # two evaluations agree to rounding, not bit for bit
+        assert _rel(lg.grad.numpy(), 2.0 * gl) <= 1e-5
+        assert _rel(dd.grad.numpy(), 2.0 * gd) <= 1e-5
+        assert _rel(rho.grad.cpu().numpy(), 2.0 * gr.cpu().numpy()) <= 1e-5
     finally:
         sc.close()

@@ -459,3 +459,34 @@ def test_mlp_oracle_baseline_and_bf16(orc):
     x[:4] = [1.00390625, 1.01171875, -3.0e-5, 65504.5]
     ref = torch.from_numpy(x).to(torch.bfloat16).to(torch.float64).numpy()
     assert np.array_equal(mlp.bf16(x), ref)
+
+
+def test_noise_before_psf_order(orc):
+    # Sec. II.G order: Poisson counts first, optical spread after.
+    rng = np.random.default_rng(8)
+    T = rng.uniform(0.2, 1.0, size=(2, 24, 30))
+    # without scatter and noise both orders give N0 G_psf (x) T
+    lam, K = orc.counts_noise_before_psf(T, 1.3, 6.0, 0.0, 1e4)
+    np.testing.assert_allclose(lam, 1e4 * T, rtol=1e-15)
+    np.testing.assert_allclose(K, orc.intensity(T, 1.3, 6.0, 0.0, 1e4), rtol=1e-13)
+    # the rate carries unblurred primary plus blurred scatter
+    lam, _ = orc.counts_noise_before_psf(T, 1.3, 6.0, 0.25, 1e4)
+    np.testing.assert_allclose(lam, 1e4 * (T + 0.25 * orc.gauss_blur(T, 6.0)), rtol=1e-13)
+
+
+def test_noise_before_psf_flood_statistics(orc):
+    # flood at rate lam: the blurred counts keep mean lam, and the spread
+    # averages the noise down to var = lam * (sum_j g_j^2)^2 (separable 2-D
+    # kernel, interior pixels); noise after the blur would keep var = lam
+    lam0, sig = 400.0, 1.0
+    T = np.ones((16, 64, 64))
+    lam, K = orc.counts_noise_before_psf(T, sig, 5.0, 0.0, lam0, seed=11)
+    R = int(math.ceil(4 * sig))
+    g = np.exp(-np.arange(-R, R + 1) ** 2 / (2 * sig * sig))
+    g /= g.sum()
+    inner = K[:, R:-R, R:-R]
+    n = inner.size
+    assert abs(inner.mean() - lam0) < 5 * math.sqrt(lam0 / n) * 4
+    want = lam0 * (g * g).sum() ** 2
+    assert inner.var() == pytest.approx(want, rel=0.1)
+    assert inner.var() < 0.2 * lam0
