@@ -212,7 +212,7 @@ int fc_fluence_for_dose(const fc_handle *h, double dose_gy, double dp_gy, double
 /* Kernel-time tracing.  While enabled, every kernel the handle launches is
  * bracketed by CUDA events recorded on the launching stream.  Kernel ids: */
 #define FC_K_PROJECT     0  /* projector + energy integral */
-#define FC_K_BLUR_ROWS   1  /* detector blur, row pass */
+#define FC_K_BLUR_ROWS   1  /* detector blur, band matrices + row pass */
 #define FC_K_BLUR_COLS   2  /* detector blur, column pass */
 #define FC_K_FDK_FILTER  3  /* log, cosine weight, Ram-Lak filter */
 #define FC_K_BACKPROJECT 4  /* FDK backprojection */

@@ -121,6 +121,8 @@ struct fc_handle {
     float *d_sL = nullptr, *d_slnT = nullptr;   // fc_surrogate_project scratch
     size_t sL_rays = 0;
     double *d_dose = nullptr;   // dose estimate: partial sums, result, label counts
+    uint16_t *d_hankel = nullptr;   // tensor-core blur band matrices
+    unsigned int *d_blur_err = nullptr;
 
     void free_all()
     {
@@ -137,6 +139,8 @@ struct fc_handle {
         dfree(d_part);
         dfree(d_flag);
         dfree(d_dose);
+        dfree(d_hankel);
+        dfree(d_blur_err);
         for (auto &r : pending) {
             cudaEventDestroy(r.a);
             cudaEventDestroy(r.b);
@@ -180,7 +184,22 @@ int ensure_proj_buffers(fc_handle *h)
     FC_CK(cudaMalloc((void **)&h->d_tp, b));
     FC_CK(cudaMalloc((void **)&h->d_ts, b));
     FC_CK(cudaMalloc((void **)&h->d_counts, b));
+    FC_CK(cudaMalloc((void **)&h->d_hankel, fc::kBlurTcHankelMax * sizeof(uint16_t)));
+    FC_CK(cudaMalloc((void **)&h->d_blur_err, sizeof(unsigned int)));
+    FC_CK(cudaMemset(h->d_blur_err, 0, sizeof(unsigned int)));
     return FC_OK;
+}
+
+// Read and clear the tensor-core blur's timeout word (synchronises `s`).
+int check_blur_err(fc_handle *h, cudaStream_t s, const char *fn)
+{
+    if (!h->d_blur_err) return FC_OK;
+    unsigned int e = 0;
+    FC_CK(cudaMemcpyAsync(&e, h->d_blur_err, sizeof(e), cudaMemcpyDeviceToHost, s));
+    FC_CK(cudaStreamSynchronize(s));
+    if (!e) return FC_OK;
+    FC_CK(cudaMemsetAsync(h->d_blur_err, 0, sizeof(unsigned int), s));
+    return fail(FC_ETIMEOUT, "%s: a detector-blur kernel timed out waiting for its copies or MMAs", fn);
 }
 
 int ensure_recon_buffers(fc_handle *h, cudaStream_t s)
@@ -514,8 +533,8 @@ static int fill_proj_params(fc_handle *h, int a0, int na, fc::ProjParams *p)
 }
 
 // out = n0 (G_psf (x) in + spr G_sc (x) in) over `n` images starting at
-// element `off` of the projection buffers (two passes through the handle's
-// row intermediates; `in` and `out` may alias).
+// element `off` of the projection buffers: tensor-core row and column
+// passes through the handle's intermediates (`in` and `out` may alias).
 static int run_blur(fc_handle *h, const float *in, float *out, size_t off, int n, double psf,
                     double sc, double n0, double spr, cudaStream_t s)
 {
@@ -530,19 +549,17 @@ static int run_blur(fc_handle *h, const float *in, float *out, size_t off, int n
     b.n0 = (float)n0;
     b.spr = (float)spr;
     {
-        Trace t(h, FC_K_BLUR_ROWS, 1, s);
-        FC_CK(fc::launch_blur_rows(b, in, h->d_tp + off, h->d_ts + off, n, s));
+        Trace t(h, FC_K_BLUR_ROWS, 2, s);
+        FC_CK(fc::launch_blur_tc_rows(b, in, h->d_tp + off, h->d_ts + off, h->d_hankel,
+                                      h->d_blur_err, n, s));
         t.end();
     }
-    cudaError_t e;
     {
         Trace t(h, FC_K_BLUR_COLS, 1, s);
-        e = fc::launch_blur_cols(b, h->d_tp + off, h->d_ts + off, out, n, s);
-        if (e == cudaSuccess) t.end();
+        FC_CK(fc::launch_blur_tc_cols(b, h->d_tp + off, h->d_ts + off, out, h->d_hankel,
+                                      h->d_blur_err, n, s));
+        t.end();
     }
-    if (e == cudaErrorInvalidValue)
-        return fail(FC_EINVAL, "fc_project: detector too tall for the column blur (n_v %d)", h->g.n_v);
-    FC_CK(e);
     return FC_OK;
 }
 
@@ -578,7 +595,10 @@ int fc_project(fc_handle *h, int angle_begin, int angle_count, int out_kind, flo
         if (rc) return rc;
         if (out_kind == FC_OUT_INTENSITY) {
             h->has_counts = true;
-            return angle_count ? copy_out(out, out_where, h->d_counts + off, bytes, s) : FC_OK;
+            if (!angle_count) return FC_OK;
+            rc = copy_out(out, out_where, h->d_counts + off, bytes, s);
+            if (rc || out_where != FC_HOST) return rc;
+            return check_blur_err(h, s, "fc_project");
         }
         if (noise) {
             Trace t(h, FC_K_NOISE, 1, s);
@@ -600,7 +620,9 @@ int fc_project(fc_handle *h, int angle_begin, int angle_count, int out_kind, flo
     }
     h->has_counts = true;
     if (out_kind == FC_OUT_NONE || angle_count == 0) return FC_OK;
-    return copy_out(out, out_where, h->d_counts + off, bytes, s);
+    rc = copy_out(out, out_where, h->d_counts + off, bytes, s);
+    if (rc || out_where != FC_HOST) return rc;
+    return check_blur_err(h, s, "fc_project");
 }
 
 int fc_set_noise_order(fc_handle *h, int order)

@@ -65,6 +65,28 @@ struct BlurParams {
     float gs[kMaxTaps];     // scatter taps, index j + rs
 };
 
+// Tensor-core blur (fc_blur_tc.cu): one band = one sampled-Gaussian kernel
+// applied along the pass's axis as a banded Toeplitz product.
+struct TcBand {
+    const float *src;   // [img][n_v][n_u]
+    uint32_t h_off;     // bf16 offset of the band's Hankel hi array (lo follows)
+    int pad;            // P = 8 ceil(R / 8)
+    int kw;             // window 128 + 2 P
+    int ncore;          // Hankel cores 15 + kw / 8
+};
+
+struct TcBlurParams {
+    TcBand band[2];
+    int n_band;
+    const uint16_t *H;  // Hankel arrays, bf16 bits
+    float *out0, *out1;
+    int n_u, n_v, n_img;
+    float n0, spr;
+    unsigned int *err;  // set on a bounded-wait timeout
+};
+
+constexpr size_t kBlurTcHankelMax = 2 * 2 * 64 * (15 + (128 + 2 * 256) / 8);  // bf16 elements
+
 // Filtered projections are stored only for the detector rows the
 // backprojector can reach, [v_lo, v_hi], in a zero-padded layout
 // [angle][1 + (v_hi - v_lo + 1) + 2][1 + n_u + 2]: one zero row / column
@@ -190,6 +212,10 @@ cudaError_t launch_backproject(const FdkParams &p, const float *filt, double *vo
                                cudaStream_t s);
 cudaError_t launch_hu(const DevGeom &g, const double *vol, float *hu, double *partials,
                       float radius, int zcut, cudaStream_t s);
+cudaError_t launch_blur_tc_rows(const BlurParams &bp, const float *in, float *tp, float *ts,
+                                uint16_t *hankel, unsigned int *err, int n_img, cudaStream_t s);
+cudaError_t launch_blur_tc_cols(const BlurParams &bp, const float *tp, const float *ts, float *out,
+                                const uint16_t *hankel, unsigned int *err, int n_img, cudaStream_t s);
 cudaError_t launch_dose(const ProjParams &p, const DoseParams &d, double *part,
                         unsigned long long *count, double *out, cudaStream_t s);
 int dose_blocks(const ProjParams &p);
