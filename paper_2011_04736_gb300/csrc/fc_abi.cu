@@ -533,8 +533,9 @@ static int fill_proj_params(fc_handle *h, int a0, int na, fc::ProjParams *p)
 }
 
 // out = n0 (G_psf (x) in + spr G_sc (x) in) over `n` images starting at
-// element `off` of the projection buffers: tensor-core row and column
-// passes through the handle's intermediates (`in` and `out` may alias).
+// element `off` of the projection buffers: tensor-core row and column passes
+// through the handle's intermediates (direct f32 passes for radii beyond the
+// tensor-core path); `in` and `out` may alias.
 static int run_blur(fc_handle *h, const float *in, float *out, size_t off, int n, double psf,
                     double sc, double n0, double spr, cudaStream_t s)
 {
@@ -548,6 +549,24 @@ static int run_blur(fc_handle *h, const float *in, float *out, size_t off, int n
     if (rc) return rc;
     b.n0 = (float)n0;
     b.spr = (float)spr;
+    if (!fc::blur_tc_supported(b)) {
+        // radii beyond the tensor-core path: direct f32 passes
+        {
+            Trace t(h, FC_K_BLUR_ROWS, 1, s);
+            FC_CK(fc::launch_blur_rows(b, in, h->d_tp + off, h->d_ts + off, n, s));
+            t.end();
+        }
+        cudaError_t e;
+        {
+            Trace t(h, FC_K_BLUR_COLS, 1, s);
+            e = fc::launch_blur_cols(b, h->d_tp + off, h->d_ts + off, out, n, s);
+            if (e == cudaSuccess) t.end();
+        }
+        if (e == cudaErrorInvalidValue)
+            return fail(FC_EINVAL, "fc_project: detector too tall for the column blur (n_v %d)", h->g.n_v);
+        FC_CK(e);
+        return FC_OK;
+    }
     {
         Trace t(h, FC_K_BLUR_ROWS, 2, s);
         FC_CK(fc::launch_blur_tc_rows(b, in, h->d_tp + off, h->d_ts + off, h->d_hankel,

@@ -5,30 +5,43 @@
 //   rows pass:    tp = G_psf (x)_u T,   ts = G_sc (x)_u T
 //   columns pass: I  = n0 (G_psf (x)_v tp + spr G_sc (x)_v ts)
 //
-// Each pass convolves along one detector axis ("conv", length Lc) with up to
-// two clamp-to-edge sampled-Gaussian kernels ("bands").  A CTA owns 128
-// outputs along the conv axis (one MMA M tile) for kN = 32 lines across it.
-// For band b with radius R_b and pad P_b = 8 ceil(R_b / 8) the input window
-// of 128 + 2 P_b samples per line, read at clamped indices (so the clamp
-// lives in the operand and the matrix is a pure Toeplitz band), is the MMA B
-// operand (kN x K, K-major).  The A operand is the 128 x (128 + 2 P_b) band
-// matrix with its rows in reverse output order, m' = 127 - i.  Then element
-// (r, k) of core matrix (g, c) equals g_b[8 (g + c) + r + k - P_b - 127]: it
-// depends on g + c only, so every core matrix (g, c) is core g + c of a short
-// "Hankel" array and one descriptor whose k-group and row-group byte offsets
-// are both 128 walks the whole band.  That array (15 + (128 + 2 P_b) / 8
-// cores of 128 bytes) is built once per call and copied into each CTA with a
-// bulk asynchronous copy.
+// A pass convolves along one detector axis ("conv") with clamp-to-edge
+// sampled Gaussians ("bands").  A tile is 128 outputs along the conv axis
+// (the MMA M) for kN = 64 detector lines across it (the MMA N).  For band b
+// with radius R_b and pad P_b = 8 ceil(R_b / 8), output i of line n is
+//   sum_k A_b[i][k] W[n][k],   W[n][k] = src(line n, m0 - P_b + k) (clamped)
+// with k over the 128 + 2 P_b window: the clamp lives in the window, so A_b is
+// a pure Toeplitz band.  W is the MMA B operand (kN x K, K-major core
+// matrices).  With the rows of A_b in reverse output order, m' = 127 - i,
+// element (r, k) of core matrix (g, c) is g_b[8 (g + c) + r + k - P_b - 127]:
+// it depends on g + c only, so the whole band matrix is a "Hankel" array of
+// 15 + (128 + 2 P_b) / 8 cores of 128 bytes walked by one descriptor whose
+// k-group and row-group byte offsets are both 128.
 //
-// Precision: samples and taps are split into bf16 hi + lo and every K step
-// issues hi*hi + hi*lo + lo*hi (the dropped lo*lo term is ~2^-18 relative),
-// accumulating in f32 in TMEM: ~1e-5 relative to the f32 direct sum.
+//   rows pass:    both bands on the tensor cores; they share one window (the
+//                 wider band's; the narrower one starts (P_w - P_b) / 8
+//                 k-groups in), A from the Hankel arrays in shared memory.
+//   columns pass: the scatter band on the tensor cores with its full band
+//                 matrix resident in TMEM (written once per CTA), so only W
+//                 streams from shared memory; the optical spread (a few taps)
+//                 on the CUDA cores in the epilogue, from a staged tile of tp.
 //
-// Waits are bounded: a CTA whose copies or MMAs do not complete sets the
-// error word, waits once more (bounded) for its own operations, frees its
-// TMEM and skips its stores.
+// Each pass is a persistent, warp-specialised kernel (one CTA per SM):
+//   warps 0-7   producers: load the tile's inputs (f32), split them into
+//               bf16 hi + lo, store the W stage, arrive on full[stage];
+//   warp 12     MMA issuer (lane 0): 3 MMAs per K step (hi*hi, hi*lo,
+//               lo*hi; the dropped lo*lo term is ~2^-18 relative) into
+//               accumulator buffer j mod 2, commits to empty[stage] and
+//               acc_full[buf];
+//   warps 8-11  epilogue: TMEM lane quarter q = warp - 8, stores, arrive on
+//               acc_empty[buf] (and, in the columns pass, on empty[stage]).
+// Accumulation is f32 in TMEM: ~1e-5 relative to the f32 direct sum.  Every
+// wait is bounded and gives up early once another role has aborted; an
+// aborting CTA sets the error word, waits (bounded) for its own MMAs and
+// copies, frees its TMEM and returns.
 #include <cuda_bf16.h>
 #include <stdint.h>
+#include <string.h>
 
 #include "fc_internal.cuh"
 #include "fc_tc.cuh"
@@ -37,16 +50,18 @@ namespace fc {
 
 namespace {
 
-constexpr int kN = 32;                 // lines across the conv axis per tile
-constexpr int kProdWarps = 8;          // warps 0-7 fill the B stages
+constexpr int kN = 64;                 // detector lines per tile (MMA N)
+constexpr int kProdWarps = 8;          // warps 0-7 fill the stages
 constexpr int kEpiWarps = 4;           // warps 8-11 drain TMEM
 constexpr int kMmaWarp = kProdWarps + kEpiWarps;   // warp 12 issues the MMAs
 constexpr int kThreads = (kMmaWarp + 1) * 32;
+constexpr int kProd = kProdWarps * 32;
 constexpr int kBatch = 8;              // window items a producer thread loads at once
-constexpr uint32_t kLbo = kN / 8 * 128;   // k-group stride of a B operand
-constexpr uint32_t kTmemCols = 128;    // two accumulator buffers x two bands x kN
+constexpr uint32_t kLbo = kN / 8 * 128;   // k-group stride of a W operand
 constexpr uint32_t kPolls = 1u << 24;  // bounded mbarrier polls
 constexpr uint32_t kHdr = 128;         // mbarriers, TMEM slot, abort flag
+constexpr int kTpPitch = kN + 1;       // staged tp tile row (padded: conflict-free columns)
+constexpr size_t kSmemLimit = 227 * 1024;
 
 __device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes)
 {
@@ -72,11 +87,11 @@ __device__ __forceinline__ void split8(const float (&v)[8], uint4 &hi, uint4 &lo
     uint32_t h[4], l[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-        const __nv_bfloat16 a = __float2bfloat16_rn(v[2 * q]);
-        const __nv_bfloat16 b = __float2bfloat16_rn(v[2 * q + 1]);
-        h[q] = (uint32_t)__bfloat16_as_ushort(a) | ((uint32_t)__bfloat16_as_ushort(b) << 16);
-        l[q] = bf16_bits(v[2 * q] - __bfloat162float(a)) |
-               (bf16_bits(v[2 * q + 1] - __bfloat162float(b)) << 16);
+        const __nv_bfloat162 hb = __floats2bfloat162_rn(v[2 * q], v[2 * q + 1]);
+        const float2 hf = __bfloat1622float2(hb);
+        const __nv_bfloat162 lb = __floats2bfloat162_rn(v[2 * q] - hf.x, v[2 * q + 1] - hf.y);
+        h[q] = *reinterpret_cast<const uint32_t *>(&hb);
+        l[q] = *reinterpret_cast<const uint32_t *>(&lb);
     }
     hi = make_uint4(h[0], h[1], h[2], h[3]);
     lo = make_uint4(l[0], l[1], l[2], l[3]);
@@ -97,6 +112,39 @@ __device__ __forceinline__ bool wait_bar(uint64_t *bar, uint32_t parity, volatil
         if ((i & 63u) == 63u && *abort_flag) return false;
     }
     return false;
+}
+
+// Lane 0 waits, the warp follows (keeps .sync.aligned TMEM accesses converged).
+__device__ __forceinline__ bool warp_wait(uint64_t *bar, uint32_t parity, volatile int *abort_flag)
+{
+    int ok = (threadIdx.x & 31) == 0 ? (int)wait_bar(bar, parity, abort_flag) : 0;
+    return __shfl_sync(0xffffffffu, ok, 0) != 0;
+}
+
+// Tile t -> (conv start m0, line start x0, image offset).
+struct Tile {
+    int m0, x0;
+    size_t img;
+};
+
+__device__ __forceinline__ Tile tile_of(long long t, int n_m, int n_x, size_t plane)
+{
+    Tile r;
+    r.m0 = (int)(t % n_m) * 128;
+    r.x0 = (int)((t / n_m) % n_x) * kN;
+    r.img = (size_t)(t / ((long long)n_m * n_x)) * plane;
+    return r;
+}
+
+// Split window item (line n, k-group cg) of a W stage into its hi and lo blocks.
+__device__ __forceinline__ void store_item(uint8_t *whi, uint32_t lo_off, int n, int cg,
+                                           const float (&v)[8])
+{
+    uint4 hi, lo;
+    split8(v, hi, lo);
+    const uint32_t o = (uint32_t)cg * kLbo + (uint32_t)(n >> 3) * 128u + (uint32_t)(n & 7) * 16u;
+    *reinterpret_cast<uint4 *>(whi + o) = hi;
+    *reinterpret_cast<uint4 *>(whi + lo_off + o) = lo;
 }
 
 }  // namespace
@@ -121,55 +169,40 @@ __global__ void k_blur_hankel(const __grid_constant__ BlurParams bp, TcBlurParam
     }
 }
 
-// Persistent, warp-specialised pass.  One CTA per SM walks tiles
-// t = blockIdx.x, blockIdx.x + gridDim.x, ... (128 conv positions x kN
-// lines of one image each):
-//   warps 0-7   producers: fill B stage (j mod n_stage) with the tile's
-//               windows (bf16 hi/lo, both bands), arrive on full[stage];
-//   warp 12     MMA issuer (lane 0): waits full[stage] and acc_empty[buf],
-//               issues 3 MMAs per K step and band into accumulator buffer
-//               j mod 2, commits to empty[stage] and acc_full[buf];
-//   warps 8-11  epilogue: wait acc_full[buf], read TMEM lanes 32 q .. 32 q + 31
-//               (q = warp - 8), store, arrive on acc_empty[buf].
-// Every wait is bounded and gives up early once another role has aborted.
-template <bool ROWS>
+// Rows pass (conv = u, lines = detector rows v).  W is the wider band's
+// window of T; band b's MMAs start (P_w - P_b) / 8 k-groups into it.  A comes
+// from the Hankel arrays in shared memory; TMEM holds two accumulator buffers
+// x two bands x kN columns.
 __global__ void __launch_bounds__(kThreads, 1)
-k_blur_tc(const __grid_constant__ TcBlurParams p, int n_stage)
+k_blur_rows_tc(const __grid_constant__ TcBlurParams p, int n_stage)
 {
+    constexpr uint32_t kCols = 4 * kN;
     extern __shared__ __align__(1024) uint8_t smem[];
-    uint64_t *full = reinterpret_cast<uint64_t *>(smem);         // [2]
-    uint64_t *empty = full + 2;                                   // [2]
-    uint64_t *accf = full + 4;                                    // [2]
-    uint64_t *acce = full + 6;                                    // [2]
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem);   // [2]
+    uint64_t *empty = full + 2;                             // [2]
+    uint64_t *accf = full + 4;                              // [2]
+    uint64_t *acce = full + 6;                              // [2]
     uint64_t *bar_h = full + 8;
     uint64_t *bar_fin = full + 9;
     uint32_t *slot = reinterpret_cast<uint32_t *>(smem + 80);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(smem + 84);
 
-    uint32_t hoff[2] = {0, 0}, boff[2] = {0, 0};
-    uint32_t stage_bytes = 0;
-    {
-        uint32_t o = kHdr;
-        for (int b = 0; b < p.n_band; ++b) {
-            hoff[b] = o;
-            o += 2u * p.band[b].ncore * 128u;
-        }
-        for (int b = 0; b < p.n_band; ++b) {
-            boff[b] = o + stage_bytes;
-            stage_bytes += 4u * kN * p.band[b].kw;
-        }
-    }
+    const int wb = p.n_band > 1 && p.band[1].kw > p.band[0].kw ? 1 : 0;
+    const int kw = p.band[wb].kw, pad = p.band[wb].pad;
+    const uint32_t h_bytes =
+        2u * 128u * (uint32_t)(p.band[0].ncore + (p.n_band > 1 ? p.band[1].ncore : 0));
+    const uint32_t w0 = kHdr + h_bytes;                   // stage 0 of W
+    const uint32_t wlo = 2u * kN * (uint32_t)kw;          // hi -> lo block
+    const uint32_t stage_bytes = 2u * wlo;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int conv_len = ROWS ? p.n_u : p.n_v;
-    const int cross_len = ROWS ? p.n_v : p.n_u;
-    const int n_m = (conv_len + 127) / 128, n_x = (cross_len + kN - 1) / kN;
+    const int n_m = (p.n_u + 127) / 128, n_x = (p.n_v + kN - 1) / kN;
     const long long total = (long long)n_m * n_x * p.n_img;
     const size_t plane = (size_t)p.n_u * p.n_v;
 
-    if (warp == kMmaWarp) tc::tmem_alloc(slot, kTmemCols);
+    if (warp == kMmaWarp) tc::tmem_alloc(slot, kCols);
     if (tid == 0) {
         for (int i = 0; i < 2; ++i) {
-            tc::mbar_init(&full[i], kProdWarps * 32);
+            tc::mbar_init(&full[i], kProd);
             tc::mbar_init(&empty[i], 1);
             tc::mbar_init(&accf[i], 1);
             tc::mbar_init(&acce[i], kEpiWarps * 32);
@@ -185,10 +218,12 @@ k_blur_tc(const __grid_constant__ TcBlurParams p, int n_stage)
     const uint32_t tbase = *slot;
 
     if (warp < kProdWarps) {
-        // ---------------- producers
-        const int ptid = tid;
-        const int ni0 = kN * (p.band[0].kw >> 3);
-        const int ntot = ni0 + (p.n_band > 1 ? kN * (p.band[1].kw >> 3) : 0);
+        // items (line n, k-group cg): each run of 32 is 8 lines x 4 k-groups,
+        // so a warp's loads cover 8 row segments of 128 bytes and its shared
+        // stores 4 contiguous 128-byte core rows
+        const int ngrp = kw >> 3, ng4 = (ngrp + 3) & ~3;
+        const int nitems = kN * ng4;
+        const float *src = p.band[0].src;
         for (long long j = 0;; ++j) {
             const long long t = blockIdx.x + j * gridDim.x;
             if (t >= total) break;
@@ -198,70 +233,57 @@ k_blur_tc(const __grid_constant__ TcBlurParams p, int n_stage)
                 *abort_flag = 1;
                 break;
             }
-            const int m0 = (int)(t % n_m) * 128;
-            const int x0 = (int)((t / n_m) % n_x) * kN;
-            const size_t img = (size_t)(t / ((long long)n_m * n_x)) * plane;
-            for (int base = ptid; base < ntot; base += kProdWarps * 32 * kBatch) {
+            const Tile tl = tile_of(t, n_m, n_x, plane);
+            uint8_t *whi = smem + w0 + (uint32_t)st * stage_bytes;
+            for (int base = tid; base < nitems; base += kProd * kBatch) {
                 float v[kBatch][8];
 #pragma unroll
                 for (int q = 0; q < kBatch; ++q) {
-                    const int i = base + q * kProdWarps * 32;
-                    if (i < ntot) {
-                        const int b = i < ni0 ? 0 : 1;
-                        const int ii = b ? i - ni0 : i;
-                        const int n = ii % kN, cg = ii / kN;
-                        const TcBand &bd = p.band[b];
-                        const float *src = bd.src + img;
-                        const int x = clampi(x0 + n, cross_len);
-                        const int c0 = m0 - bd.pad + 8 * cg;
-                        if (ROWS) {
-                            const float *row = src + (size_t)x * p.n_u;
-                            if (c0 >= 0 && c0 + 8 <= conv_len && (p.n_u & 3) == 0) {
-                                const float4 a = __ldg(reinterpret_cast<const float4 *>(row + c0));
-                                const float4 c = __ldg(reinterpret_cast<const float4 *>(row + c0 + 4));
-                                v[q][0] = a.x; v[q][1] = a.y; v[q][2] = a.z; v[q][3] = a.w;
-                                v[q][4] = c.x; v[q][5] = c.y; v[q][6] = c.z; v[q][7] = c.w;
-                            } else {
+                    const int i = base + q * kProd;
+                    const int blk = i >> 5;
+                    const int n = (i & 7) + 8 * (blk % (kN / 8));
+                    const int cg = ((i >> 3) & 3) + 4 * (blk / (kN / 8));
+                    if (i >= nitems || cg >= ngrp) continue;
+                    const float *row = src + tl.img + (size_t)clampi(tl.x0 + n, p.n_v) * p.n_u;
+                    const int c0 = tl.m0 - pad + 8 * cg;
+                    if (c0 >= 0 && c0 + 8 <= p.n_u && (p.n_u & 3) == 0) {
+                        const float4 a = __ldg(reinterpret_cast<const float4 *>(row + c0));
+                        const float4 c = __ldg(reinterpret_cast<const float4 *>(row + c0 + 4));
+                        v[q][0] = a.x; v[q][1] = a.y; v[q][2] = a.z; v[q][3] = a.w;
+                        v[q][4] = c.x; v[q][5] = c.y; v[q][6] = c.z; v[q][7] = c.w;
+                    } else {
 #pragma unroll
-                                for (int tt = 0; tt < 8; ++tt)
-                                    v[q][tt] = __ldg(row + clampi(c0 + tt, conv_len));
-                            }
-                        } else {
-#pragma unroll
-                            for (int tt = 0; tt < 8; ++tt)
-                                v[q][tt] = __ldg(src + (size_t)clampi(c0 + tt, conv_len) * p.n_u + x);
-                        }
+                        for (int e = 0; e < 8; ++e) v[q][e] = __ldg(row + clampi(c0 + e, p.n_u));
                     }
                 }
 #pragma unroll
                 for (int q = 0; q < kBatch; ++q) {
-                    const int i = base + q * kProdWarps * 32;
-                    if (i < ntot) {
-                        const int b = i < ni0 ? 0 : 1;
-                        const int ii = b ? i - ni0 : i;
-                        const int n = ii % kN, cg = ii / kN;
-                        uint8_t *bhi = smem + boff[b] + (uint32_t)st * stage_bytes;
-                        uint8_t *blo = bhi + 2 * kN * p.band[b].kw;
-                        uint4 hi, lo;
-                        split8(v[q], hi, lo);
-                        const uint32_t o = (uint32_t)cg * kLbo + (uint32_t)(n >> 3) * 128u +
-                                           (uint32_t)(n & 7) * 16u;
-                        *reinterpret_cast<uint4 *>(bhi + o) = hi;
-                        *reinterpret_cast<uint4 *>(blo + o) = lo;
-                    }
+                    const int i = base + q * kProd;
+                    const int blk = i >> 5;
+                    const int n = (i & 7) + 8 * (blk % (kN / 8));
+                    const int cg = ((i >> 3) & 3) + 4 * (blk / (kN / 8));
+                    if (i >= nitems || cg >= ngrp) continue;
+                    store_item(whi, wlo, n, cg, v[q]);
                 }
             }
             tc::fence_async_smem();
             mbar_arrive(&full[st]);
         }
     } else if (warp == kMmaWarp) {
-        // ---------------- MMA issuer
         if (lane == 0) {
-            uint32_t bytes = 0;
-            for (int b = 0; b < p.n_band; ++b) bytes += 2u * p.band[b].ncore * 128u;
-            mbar_expect_tx(bar_h, bytes);
-            for (int b = 0; b < p.n_band; ++b)
-                bulk_g2s(smem + hoff[b], p.H + p.band[b].h_off, 2u * p.band[b].ncore * 128u, bar_h);
+            mbar_expect_tx(bar_h, h_bytes);
+            bulk_g2s(smem + kHdr, p.H, h_bytes, bar_h);
+            uint64_t da[2] = {0, 0}, dal[2] = {0, 0}, dw[2] = {0, 0};
+            uint32_t ha = kHdr;
+#pragma unroll
+            for (int b = 0; b < 2; ++b) {
+                if (b >= p.n_band) break;
+                da[b] = tc::sdesc(tc::smem_u32(smem + ha), 128, 128);
+                dal[b] = (uint64_t)((p.band[b].ncore * 128u) >> 4);
+                ha += 2u * p.band[b].ncore * 128u;
+                const uint32_t koff = (uint32_t)((pad - p.band[b].pad) >> 3) * kLbo;
+                dw[b] = tc::sdesc(tc::smem_u32(smem + w0 + koff), kLbo, 128);
+            }
             bool ok = wait_bar(bar_h, 0, abort_flag);
             constexpr uint32_t idesc = tc::idesc_bf16(128, kN);
             for (long long j = 0; ok; ++j) {
@@ -276,36 +298,39 @@ k_blur_tc(const __grid_constant__ TcBlurParams p, int n_stage)
                     break;
                 }
                 tc::fence_after_sync();
-                for (int b = 0; b < p.n_band; ++b) {
-                    const TcBand &bd = p.band[b];
-                    const uint32_t ah = tc::smem_u32(smem + hoff[b]);
-                    const uint32_t al = ah + (uint32_t)bd.ncore * 128u;
-                    const uint32_t bh = tc::smem_u32(smem + boff[b] + (uint32_t)st * stage_bytes);
-                    const uint32_t bl = bh + 2u * kN * bd.kw;
+#pragma unroll
+                for (int b = 0; b < 2; ++b) {
+                    if (b >= p.n_band) break;
+                    // descriptors advance by whole K steps: the start-address
+                    // field (bits 0-13, bytes / 16) grows by 256 / 16 for A and
+                    // 2 kLbo / 16 for W; shared memory < 256 KB keeps it in range
+                    uint64_t ah = da[b], al = da[b] + dal[b];
+                    uint64_t wh = dw[b] + (uint64_t)(((uint32_t)st * stage_bytes) >> 4);
+                    uint64_t wl = wh + (uint64_t)(wlo >> 4);
                     const uint32_t d = tbase + (uint32_t)(buf * 2 * kN + b * kN);
-                    for (int s = 0; s < (bd.kw >> 4); ++s) {
-                        const uint64_t dah = tc::sdesc(ah + 256u * s, 128, 128);
-                        const uint64_t dal = tc::sdesc(al + 256u * s, 128, 128);
-                        const uint64_t dbh = tc::sdesc(bh + 2u * kLbo * s, kLbo, 128);
-                        const uint64_t dbl = tc::sdesc(bl + 2u * kLbo * s, kLbo, 128);
-                        tc::mma_bf16(d, dah, dbh, idesc, s > 0 ? 1u : 0u);
-                        tc::mma_bf16(d, dah, dbl, idesc, 1u);
-                        tc::mma_bf16(d, dal, dbh, idesc, 1u);
+                    const int ns = p.band[b].kw >> 4;
+                    for (int s = 0; s < ns; ++s) {
+                        tc::mma_bf16(d, ah, wh, idesc, s > 0 ? 1u : 0u);
+                        tc::mma_bf16(d, ah, wl, idesc, 1u);
+                        tc::mma_bf16(d, al, wh, idesc, 1u);
+                        ah += 16u;
+                        al += 16u;
+                        wh += 2u * kLbo / 16u;
+                        wl += 2u * kLbo / 16u;
                     }
                 }
                 tc::mma_commit(&empty[st]);
                 tc::mma_commit(&accf[buf]);
             }
             if (!ok) *abort_flag = 1;
-            // every MMA issued so far has completed before TMEM is freed, and
-            // the table copy has landed before the CTA exits
+            // every MMA issued so far completes before TMEM is freed, and the
+            // table copy lands before the CTA exits
             tc::mma_commit(bar_fin);
             tc::mbar_wait(bar_fin, 0, kPolls);
             tc::mbar_wait(bar_h, 0, kPolls);
         }
         __syncwarp();
     } else {
-        // ---------------- epilogue (warps 8-11: TMEM lane quarter q)
         const int q = warp - kProdWarps;
         const uint32_t lane_base = tbase + ((uint32_t)(32 * q) << 16);
         const int mr = 32 * q + lane;
@@ -314,60 +339,27 @@ k_blur_tc(const __grid_constant__ TcBlurParams p, int n_stage)
             if (t >= total) break;
             const int buf = (int)(j & 1);
             const uint32_t bph = (uint32_t)((j >> 1) & 1);
-            int ok = lane == 0 ? (int)wait_bar(&accf[buf], bph, abort_flag) : 0;
-            ok = __shfl_sync(0xffffffffu, ok, 0);
-            if (!ok) {
+            if (!warp_wait(&accf[buf], bph, abort_flag)) {
                 *abort_flag = 1;
                 break;
             }
             tc::fence_after_sync();
-            const int m0 = (int)(t % n_m) * 128;
-            const int x0 = (int)((t / n_m) % n_x) * kN;
-            const size_t img = (size_t)(t / ((long long)n_m * n_x)) * plane;
-            const int c = m0 + 127 - mr;
+            const Tile tl = tile_of(t, n_m, n_x, plane);
+            const int c = tl.m0 + 127 - mr;
             const uint32_t acc = lane_base + (uint32_t)(buf * 2 * kN);
-            if (ROWS) {
-                for (int b = 0; b < p.n_band; ++b) {
-                    float *out = b == 0 ? p.out0 : p.out1;
 #pragma unroll
-                    for (int j0 = 0; j0 < kN; j0 += 16) {
-                        float v[16];
-                        tc::tmem_ld16(acc + (uint32_t)(b * kN + j0), v);
-                        if (c < conv_len) {
-#pragma unroll
-                            for (int i = 0; i < 16; ++i) {
-                                const int x = x0 + j0 + i;
-                                if (x < cross_len) out[img + (size_t)x * p.n_u + c] = v[i];
-                            }
-                        }
-                    }
-                }
-            } else {
+            for (int b = 0; b < 2; ++b) {
+                if (b >= p.n_band) break;
+                float *out = b == 0 ? p.out0 : p.out1;
 #pragma unroll
                 for (int j0 = 0; j0 < kN; j0 += 16) {
-                    float vp[16], vs[16];
-                    tc::tmem_ld16(acc + (uint32_t)j0, vp);
-                    if (p.n_band > 1) {
-                        tc::tmem_ld16(acc + (uint32_t)(kN + j0), vs);
-                    } else {
+                    float v[16];
+                    tc::tmem_ld16(acc + (uint32_t)(b * kN + j0), v);
+                    if (c < p.n_u) {
 #pragma unroll
-                        for (int i = 0; i < 16; ++i) vs[i] = 0.0f;
-                    }
-                    if (c < conv_len) {
-                        float r[16];
-#pragma unroll
-                        for (int i = 0; i < 16; ++i) r[i] = p.n0 * (vp[i] + p.spr * vs[i]);
-                        const int xs = x0 + j0;
-                        float *dst = p.out0 + img + (size_t)c * p.n_u + xs;
-                        if (xs + 16 <= cross_len && (p.n_u & 3) == 0) {
-#pragma unroll
-                            for (int i = 0; i < 16; i += 4)
-                                *reinterpret_cast<float4 *>(dst + i) =
-                                    make_float4(r[i], r[i + 1], r[i + 2], r[i + 3]);
-                        } else {
-#pragma unroll
-                            for (int i = 0; i < 16; ++i)
-                                if (xs + i < cross_len) dst[i] = r[i];
+                        for (int i = 0; i < 16; ++i) {
+                            const int x = tl.x0 + j0 + i;
+                            if (x < p.n_v) out[tl.img + (size_t)x * p.n_u + c] = v[i];
                         }
                     }
                 }
@@ -381,7 +373,251 @@ k_blur_tc(const __grid_constant__ TcBlurParams p, int n_stage)
     if (tid == 0 && *abort_flag) atomicOr(p.err, 1u);
     if (warp == kMmaWarp) {
         tc::fence_after_sync();
-        tc::tmem_dealloc(tbase, kTmemCols);
+        tc::tmem_dealloc(tbase, kCols);
+    }
+}
+
+// Columns pass (conv = v, lines = detector columns u).  W is the scatter
+// band's window of ts; its full 128 x kw band matrix (hi, then lo; two bf16
+// per column) sits in TMEM columns [2 kN, 2 kN + kw) beside two accumulator
+// buffers of kN columns, so only W streams from shared memory.  The producers
+// also stage tp rows m0 - R_p .. m0 + 127 + R_p of the tile's columns (f32,
+// padded rows); the epilogue forms the optical spread from them on the CUDA
+// cores.  A stage is released once both its MMAs and its epilogue are done:
+// empty[stage] counts one commit and the 128 epilogue threads.
+__global__ void __launch_bounds__(kThreads, 1)
+k_blur_cols_tc(const __grid_constant__ TcBlurParams p, int n_stage)
+{
+    constexpr uint32_t kCols = 512;
+    extern __shared__ __align__(1024) uint8_t smem[];
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem);   // [2]
+    uint64_t *empty = full + 2;                             // [2]
+    uint64_t *accf = full + 4;                              // [2]
+    uint64_t *acce = full + 6;                              // [2]
+    uint64_t *bar_fin = full + 9;
+    uint32_t *slot = reinterpret_cast<uint32_t *>(smem + 80);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(smem + 84);
+
+    const TcBand &bs = p.band[1];
+    const int kw = bs.kw, pad = bs.pad;
+    const int rp = p.rp, trows = 128 + 2 * rp;
+    const uint32_t wlo = 2u * kN * (uint32_t)kw;
+    const uint32_t tp_bytes = ((uint32_t)(trows * kTpPitch) * 4u + 127u) & ~127u;
+    const uint32_t stage_bytes = 2u * wlo + tp_bytes;
+    const uint32_t acol = 2 * kN;                          // TMEM column of A (hi)
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int n_m = (p.n_v + 127) / 128, n_x = (p.n_u + kN - 1) / kN;
+    const long long total = (long long)n_m * n_x * p.n_img;
+    const size_t plane = (size_t)p.n_u * p.n_v;
+
+    if (warp == kMmaWarp) tc::tmem_alloc(slot, kCols);
+    if (tid == 0) {
+        for (int i = 0; i < 2; ++i) {
+            tc::mbar_init(&full[i], kProd);
+            tc::mbar_init(&empty[i], 1 + kEpiWarps * 32);
+            tc::mbar_init(&accf[i], 1);
+            tc::mbar_init(&acce[i], kEpiWarps * 32);
+        }
+        tc::mbar_init(bar_fin, 1);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tbase = *slot;
+    if (warp >= kProdWarps && warp < kMmaWarp) {
+        // row m' of the band matrix, A'[m'][k] = g_s[k + m' - P - 127], read
+        // from the Hankel table (core d, in-core r + k = s - 8 d, r <= 7)
+        const int q = warp - kProdWarps, mr = 32 * q + lane;
+        const uint32_t lane_base = tbase + ((uint32_t)(32 * q) << 16);
+        const uint16_t *hh = p.H + bs.h_off, *hl = hh + bs.ncore * 64;
+        const int nw = kw >> 1;
+        for (int c0 = 0; c0 < nw; c0 += 8) {
+            uint32_t wh[8], wl[8];
+#pragma unroll
+            for (int w = 0; w < 8; ++w) {
+                uint32_t eh[2], el[2];
+#pragma unroll
+                for (int e = 0; e < 2; ++e) {
+                    const int sidx = 2 * (c0 + w) + e + mr;
+                    const int d = min(sidx >> 3, bs.ncore - 1);
+                    const int rem = sidx - 8 * d, r = min(rem, 7);
+                    const int idx = d * 64 + r * 8 + (rem - r);
+                    eh[e] = __ldg(hh + idx);
+                    el[e] = __ldg(hl + idx);
+                }
+                wh[w] = eh[0] | (eh[1] << 16);
+                wl[w] = el[0] | (el[1] << 16);
+            }
+            tc::tmem_st8(lane_base + acol + (uint32_t)c0, wh);
+            tc::tmem_st8(lane_base + acol + (uint32_t)(nw + c0), wl);
+        }
+        tc::tmem_st_wait();
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+
+    if (warp < kProdWarps) {
+        const int ngrp = kw >> 3, nitems = kN * ngrp;
+        const float *ts = bs.src;
+        for (long long j = 0;; ++j) {
+            const long long t = blockIdx.x + j * gridDim.x;
+            if (t >= total) break;
+            const int st = (int)(j % n_stage);
+            const uint32_t ph = (uint32_t)((j / n_stage) & 1);
+            if (!wait_bar(&empty[st], ph ^ 1u, abort_flag)) {
+                *abort_flag = 1;
+                break;
+            }
+            const Tile tl = tile_of(t, n_m, n_x, plane);
+            uint8_t *whi = smem + kHdr + (uint32_t)st * stage_bytes;
+            // W items (line n = column u, k-group cg): a warp's loads are
+            // eight rows of 32 consecutive columns
+            for (int base = tid; base < nitems; base += kProd * kBatch) {
+                float v[kBatch][8];
+#pragma unroll
+                for (int q = 0; q < kBatch; ++q) {
+                    const int i = base + q * kProd;
+                    if (i >= nitems) continue;
+                    const int n = i % kN, cg = i / kN;
+                    const float *col = ts + tl.img + clampi(tl.x0 + n, p.n_u);
+                    const int c0 = tl.m0 - pad + 8 * cg;
+#pragma unroll
+                    for (int e = 0; e < 8; ++e)
+                        v[q][e] = __ldg(col + (size_t)clampi(c0 + e, p.n_v) * p.n_u);
+                }
+#pragma unroll
+                for (int q = 0; q < kBatch; ++q) {
+                    const int i = base + q * kProd;
+                    if (i >= nitems) continue;
+                    store_item(whi, wlo, i % kN, i / kN, v[q]);
+                }
+            }
+            // tp tile: rows m0 - R_p + r (clamped), columns x0 + n (clamped)
+            float *tpt = reinterpret_cast<float *>(whi + 2u * wlo);
+            const int ntp = trows * kN;
+            for (int base = tid; base < ntp; base += kProd * kBatch) {
+                float v[kBatch];
+#pragma unroll
+                for (int q = 0; q < kBatch; ++q) {
+                    const int e = base + q * kProd;
+                    if (e >= ntp) continue;
+                    const int r = e / kN, n = e % kN;
+                    v[q] = __ldg(p.tp + tl.img + (size_t)clampi(tl.m0 - rp + r, p.n_v) * p.n_u +
+                                 clampi(tl.x0 + n, p.n_u));
+                }
+#pragma unroll
+                for (int q = 0; q < kBatch; ++q) {
+                    const int e = base + q * kProd;
+                    if (e >= ntp) continue;
+                    tpt[(e / kN) * kTpPitch + e % kN] = v[q];
+                }
+            }
+            tc::fence_async_smem();
+            mbar_arrive(&full[st]);
+        }
+    } else if (warp == kMmaWarp) {
+        if (lane == 0) {
+            const uint64_t dw = tc::sdesc(tc::smem_u32(smem + kHdr), kLbo, 128);
+            constexpr uint32_t idesc = tc::idesc_bf16(128, kN);
+            const int ns = kw >> 4;
+            const uint32_t tl_off = (uint32_t)(kw >> 1);
+            bool ok = true;
+            for (long long j = 0;; ++j) {
+                const long long t = blockIdx.x + j * gridDim.x;
+                if (t >= total) break;
+                const int st = (int)(j % n_stage);
+                const uint32_t ph = (uint32_t)((j / n_stage) & 1);
+                const int buf = (int)(j & 1);
+                const uint32_t bph = (uint32_t)((j >> 1) & 1);
+                if (!wait_bar(&full[st], ph, abort_flag) || !wait_bar(&acce[buf], bph ^ 1u, abort_flag)) {
+                    ok = false;
+                    break;
+                }
+                tc::fence_after_sync();
+                uint64_t wh = dw + (uint64_t)(((uint32_t)st * stage_bytes) >> 4);
+                uint64_t wl = wh + (uint64_t)(wlo >> 4);
+                uint32_t ah = tbase + acol;
+                const uint32_t d = tbase + (uint32_t)(buf * kN);
+                for (int s = 0; s < ns; ++s) {
+                    tc::mma_bf16_ta(d, ah, wh, idesc, s > 0 ? 1u : 0u);
+                    tc::mma_bf16_ta(d, ah, wl, idesc, 1u);
+                    tc::mma_bf16_ta(d, ah + tl_off, wh, idesc, 1u);
+                    ah += 8u;
+                    wh += 2u * kLbo / 16u;
+                    wl += 2u * kLbo / 16u;
+                }
+                tc::mma_commit(&empty[st]);
+                tc::mma_commit(&accf[buf]);
+            }
+            if (!ok) *abort_flag = 1;
+            tc::mma_commit(bar_fin);
+            tc::mbar_wait(bar_fin, 0, kPolls);
+        }
+        __syncwarp();
+    } else {
+        const int q = warp - kProdWarps;
+        const uint32_t lane_base = tbase + ((uint32_t)(32 * q) << 16);
+        const int mr = 32 * q + lane;
+        for (long long j = 0;; ++j) {
+            const long long t = blockIdx.x + j * gridDim.x;
+            if (t >= total) break;
+            const int st = (int)(j % n_stage);
+            const int buf = (int)(j & 1);
+            const uint32_t bph = (uint32_t)((j >> 1) & 1);
+            if (!warp_wait(&accf[buf], bph, abort_flag)) {
+                *abort_flag = 1;
+                break;
+            }
+            tc::fence_after_sync();
+            const Tile tl = tile_of(t, n_m, n_x, plane);
+            const int c = tl.m0 + 127 - mr;              // detector row of this lane
+            // tile row of output row c's first optical-spread tap
+            const float *tpt = reinterpret_cast<const float *>(smem + kHdr + (uint32_t)st * stage_bytes +
+                                                               2u * wlo) + (127 - mr) * kTpPitch;
+#pragma unroll
+            for (int j0 = 0; j0 < kN; j0 += 16) {
+                float v[16];
+                tc::tmem_ld16(lane_base + (uint32_t)(buf * kN + j0), v);
+                float r[16];
+#pragma unroll
+                for (int i = 0; i < 16; ++i) r[i] = 0.0f;
+                for (int jj = 0; jj <= 2 * rp; ++jj) {
+                    const float g = p.gp[jj];
+                    const float *row = tpt + jj * kTpPitch + j0;
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) r[i] = fmaf(g, row[i], r[i]);
+                }
+#pragma unroll
+                for (int i = 0; i < 16; ++i) r[i] = p.n0 * (r[i] + p.spr * v[i]);
+                if (c < p.n_v) {
+                    const int xs = tl.x0 + j0;
+                    float *dst = p.out0 + tl.img + (size_t)c * p.n_u + xs;
+                    if (xs + 16 <= p.n_u && (p.n_u & 3) == 0) {
+#pragma unroll
+                        for (int i = 0; i < 16; i += 4)
+                            *reinterpret_cast<float4 *>(dst + i) =
+                                make_float4(r[i], r[i + 1], r[i + 2], r[i + 3]);
+                    } else {
+#pragma unroll
+                        for (int i = 0; i < 16; ++i)
+                            if (xs + i < p.n_u) dst[i] = r[i];
+                    }
+                }
+            }
+            tc::fence_before_sync();
+            mbar_arrive(&acce[buf]);
+            mbar_arrive(&empty[st]);
+        }
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (tid == 0 && *abort_flag) atomicOr(p.err, 1u);
+    if (warp == kMmaWarp) {
+        tc::fence_after_sync();
+        tc::tmem_dealloc(tbase, kCols);
     }
 }
 
@@ -397,74 +633,93 @@ static TcBand make_band(const float *src, int R, uint32_t h_off)
     return b;
 }
 
-static size_t tc_smem(const TcBlurParams &p, int n_stage)
+bool blur_tc_supported(const BlurParams &bp)
 {
-    size_t o = kHdr;
-    for (int b = 0; b < p.n_band; ++b)
-        o += 2u * p.band[b].ncore * 128u + (size_t)n_stage * 4u * kN * p.band[b].kw;
-    return o;
+    return bp.rp >= 0 && bp.rp <= kTcMaxPsfR && bp.rs >= 0 && bp.rs <= kTcMaxScR;
 }
 
-template <bool ROWS>
-static cudaError_t launch_tc(TcBlurParams p, int n_img, cudaStream_t s)
-{
-    const size_t limit = 227 * 1024;
-    const int n_stage = tc_smem(p, 2) <= limit ? 2 : 1;
-    const size_t bytes = tc_smem(p, n_stage);
-    if (bytes > limit) return cudaErrorInvalidValue;
-    cudaError_t e = cudaFuncSetAttribute(k_blur_tc<ROWS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)bytes);
-    if (e != cudaSuccess) return e;
-    int dev = 0, sms = 0;
-    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
-    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-    const int conv = ROWS ? p.n_u : p.n_v, cross = ROWS ? p.n_v : p.n_u;
-    const long long tiles = (long long)((conv + 127) / 128) * ((cross + kN - 1) / kN) * n_img;
-    p.n_img = n_img;
-    const int grid = (int)(tiles < sms ? tiles : sms);
-    k_blur_tc<ROWS><<<grid, kThreads, bytes, s>>>(p, n_stage);
-    return cudaGetLastError();
-}
-
-static TcBlurParams tc_params(const BlurParams &bp, const uint16_t *hankel, unsigned int *err)
+static TcBlurParams tc_params(const BlurParams &bp, const uint16_t *hankel, unsigned int *err,
+                              int n_img)
 {
     TcBlurParams p;
+    memset(&p, 0, sizeof(p));
     p.n_band = 2;
     p.H = hankel;
     p.n_u = bp.n_u;
     p.n_v = bp.n_v;
+    p.n_img = n_img;
     p.n0 = bp.n0;
     p.spr = bp.spr;
     p.err = err;
     p.band[0] = make_band(nullptr, bp.rp, 0);
     p.band[1] = make_band(nullptr, bp.rs, (uint32_t)(2 * 64 * p.band[0].ncore));
-    p.out0 = p.out1 = nullptr;
-    p.n_img = 0;
+    p.rp = bp.rp;
+    for (int j = 0; j <= 2 * bp.rp && j < 2 * kTcMaxPsfR + 1; ++j) p.gp[j] = bp.gp[j];
     return p;
+}
+
+static cudaError_t persistent_grid(long long tiles, int *grid)
+{
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    *grid = (int)(tiles < sms ? tiles : sms);
+    return cudaSuccess;
 }
 
 cudaError_t launch_blur_tc_rows(const BlurParams &bp, const float *in, float *tp, float *ts,
                                 uint16_t *hankel, unsigned int *err, int n_img, cudaStream_t s)
 {
     if (n_img <= 0) return cudaSuccess;
-    TcBlurParams p = tc_params(bp, hankel, err);
+    if (!blur_tc_supported(bp)) return cudaErrorInvalidValue;
+    TcBlurParams p = tc_params(bp, hankel, err, n_img);
     k_blur_hankel<<<16, 256, 0, s>>>(bp, p, hankel);
     p.band[0].src = in;
     p.band[1].src = in;
     p.out0 = tp;
     p.out1 = ts;
-    return launch_tc<true>(p, n_img, s);
+    const int kw = p.band[0].kw > p.band[1].kw ? p.band[0].kw : p.band[1].kw;
+    const size_t fixed = kHdr + 2u * 128u * (size_t)(p.band[0].ncore + p.band[1].ncore);
+    const size_t stage = 4u * kN * (size_t)kw;
+    const int n_stage = fixed + 2 * stage <= kSmemLimit ? 2 : 1;
+    const size_t bytes = fixed + n_stage * stage;
+    if (bytes > kSmemLimit) return cudaErrorInvalidValue;
+    cudaError_t e = cudaFuncSetAttribute(k_blur_rows_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)bytes);
+    if (e != cudaSuccess) return e;
+    const long long tiles = (long long)((bp.n_u + 127) / 128) * ((bp.n_v + kN - 1) / kN) * n_img;
+    int grid = 0;
+    if ((e = persistent_grid(tiles, &grid)) != cudaSuccess) return e;
+    k_blur_rows_tc<<<grid, kThreads, bytes, s>>>(p, n_stage);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_blur_tc_cols(const BlurParams &bp, const float *tp, const float *ts, float *out,
                                 const uint16_t *hankel, unsigned int *err, int n_img, cudaStream_t s)
 {
     if (n_img <= 0) return cudaSuccess;
-    TcBlurParams p = tc_params(bp, hankel, err);
-    p.band[0].src = tp;
+    if (!blur_tc_supported(bp)) return cudaErrorInvalidValue;
+    TcBlurParams p = tc_params(bp, hankel, err, n_img);
     p.band[1].src = ts;
+    p.tp = tp;
     p.out0 = out;
-    return launch_tc<false>(p, n_img, s);
+    const size_t tp_bytes = ((size_t)(128 + 2 * bp.rp) * kTpPitch * 4u + 127u) & ~(size_t)127u;
+    const size_t stage = 4u * kN * (size_t)p.band[1].kw + tp_bytes;
+    const int n_stage = kHdr + 2 * stage <= kSmemLimit ? 2 : 1;
+    size_t bytes = kHdr + n_stage * stage;
+    if (bytes > kSmemLimit || 2 * kN + p.band[1].kw > 512) return cudaErrorInvalidValue;
+    // the kernel takes all 512 TMEM columns: reserve enough shared memory that
+    // a second CTA never shares the SM (its allocation would wait for ours)
+    if (bytes < kSmemLimit / 2 + 1024) bytes = kSmemLimit / 2 + 1024;
+    cudaError_t e = cudaFuncSetAttribute(k_blur_cols_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)bytes);
+    if (e != cudaSuccess) return e;
+    const long long tiles = (long long)((bp.n_v + 127) / 128) * ((bp.n_u + kN - 1) / kN) * n_img;
+    int grid = 0;
+    if ((e = persistent_grid(tiles, &grid)) != cudaSuccess) return e;
+    k_blur_cols_tc<<<grid, kThreads, bytes, s>>>(p, n_stage);
+    return cudaGetLastError();
 }
 
 }  // namespace fc

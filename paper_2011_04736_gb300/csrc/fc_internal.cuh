@@ -75,13 +75,23 @@ struct TcBand {
     int ncore;          // Hankel cores 15 + kw / 8
 };
 
+// Radii the tensor-core blur takes: the optical spread of the column pass
+// runs on the CUDA cores from a staged tile of 128 + 2 R rows, and the scatter
+// band matrix of the column pass lives in TMEM beside two accumulators
+// (128 + 2 P <= 384 columns).  Larger radii use the direct f32 kernels.
+constexpr int kTcMaxPsfR = 16;
+constexpr int kTcMaxScR = 128;
+
 struct TcBlurParams {
     TcBand band[2];
     int n_band;
     const uint16_t *H;  // Hankel arrays, bf16 bits
     float *out0, *out1;
+    const float *tp;    // column pass: row-blurred optical-spread input
     int n_u, n_v, n_img;
     float n0, spr;
+    int rp;                          // column pass: optical-spread radius
+    float gp[2 * kTcMaxPsfR + 1];    // and taps
     unsigned int *err;  // set on a bounded-wait timeout
 };
 
@@ -212,6 +222,7 @@ cudaError_t launch_backproject(const FdkParams &p, const float *filt, double *vo
                                cudaStream_t s);
 cudaError_t launch_hu(const DevGeom &g, const double *vol, float *hu, double *partials,
                       float radius, int zcut, cudaStream_t s);
+bool blur_tc_supported(const BlurParams &bp);
 cudaError_t launch_blur_tc_rows(const BlurParams &bp, const float *in, float *tp, float *ts,
                                 uint16_t *hankel, unsigned int *err, int n_img, cudaStream_t s);
 cudaError_t launch_blur_tc_cols(const BlurParams &bp, const float *tp, const float *ts, float *out,
