@@ -60,7 +60,7 @@ constexpr int kBatch = 8;              // window items a producer thread loads a
 constexpr uint32_t kLbo = kN / 8 * 128;   // k-group stride of a W operand
 constexpr uint32_t kPolls = 1u << 24;  // bounded mbarrier polls
 constexpr uint32_t kHdr = 128;         // mbarriers, TMEM slot, abort flag
-constexpr int kTpPitch = kN + 1;       // staged tp tile row (padded: conflict-free columns)
+constexpr int kTpPitch = kN + 4;       // staged tp tile row: 16-byte rows, 17 16-byte groups apart
 constexpr size_t kSmemLimit = 227 * 1024;
 
 __device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes)
@@ -112,6 +112,24 @@ __device__ __forceinline__ bool wait_bar(uint64_t *bar, uint32_t parity, volatil
         if ((i & 63u) == 63u && *abort_flag) return false;
     }
     return false;
+}
+
+// 16-byte global -> shared copy that bypasses the registers (both addresses
+// 16-byte aligned), and waiting for this thread's copies.
+__device__ __forceinline__ void cp_async16(void *dst, const void *src)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;"
+                 :: "r"(tc::smem_u32(dst)), "l"(src) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_commit()
+{
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
+__device__ __forceinline__ void cp_async_wait_all()
+{
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
 }
 
 // Lane 0 waits, the warp follows (keeps .sync.aligned TMEM accesses converged).
@@ -473,6 +491,25 @@ k_blur_cols_tc(const __grid_constant__ TcBlurParams p, int n_stage)
             }
             const Tile tl = tile_of(t, n_m, n_x, plane);
             uint8_t *whi = smem + kHdr + (uint32_t)st * stage_bytes;
+            {
+                // tp tile: rows m0 - R_p + r, columns x0 + n (both clamped),
+                // copied asynchronously while the W items are processed
+                float *tpt = reinterpret_cast<float *>(whi + 2u * wlo);
+                const bool vec = tl.x0 + kN <= p.n_u && (p.n_u & 3) == 0;
+                const int nq = trows * (kN / 4);
+                for (int e = tid; e < nq; e += kProd) {
+                    const int r = e / (kN / 4), n = 4 * (e % (kN / 4));
+                    const float *row = p.tp + tl.img + (size_t)clampi(tl.m0 - rp + r, p.n_v) * p.n_u;
+                    float *d = tpt + r * kTpPitch + n;
+                    if (vec) {
+                        cp_async16(d, row + tl.x0 + n);
+                    } else {
+#pragma unroll
+                        for (int c = 0; c < 4; ++c) d[c] = __ldg(row + clampi(tl.x0 + n + c, p.n_u));
+                    }
+                }
+                cp_async_commit();
+            }
             // W items (line n = column u, k-group cg): a warp's loads are
             // eight rows of 32 consecutive columns
             for (int base = tid; base < nitems; base += kProd * kBatch) {
@@ -495,26 +532,7 @@ k_blur_cols_tc(const __grid_constant__ TcBlurParams p, int n_stage)
                     store_item(whi, wlo, i % kN, i / kN, v[q]);
                 }
             }
-            // tp tile: rows m0 - R_p + r (clamped), columns x0 + n (clamped)
-            float *tpt = reinterpret_cast<float *>(whi + 2u * wlo);
-            const int ntp = trows * kN;
-            for (int base = tid; base < ntp; base += kProd * kBatch) {
-                float v[kBatch];
-#pragma unroll
-                for (int q = 0; q < kBatch; ++q) {
-                    const int e = base + q * kProd;
-                    if (e >= ntp) continue;
-                    const int r = e / kN, n = e % kN;
-                    v[q] = __ldg(p.tp + tl.img + (size_t)clampi(tl.m0 - rp + r, p.n_v) * p.n_u +
-                                 clampi(tl.x0 + n, p.n_u));
-                }
-#pragma unroll
-                for (int q = 0; q < kBatch; ++q) {
-                    const int e = base + q * kProd;
-                    if (e >= ntp) continue;
-                    tpt[(e / kN) * kTpPitch + e % kN] = v[q];
-                }
-            }
+            cp_async_wait_all();
             tc::fence_async_smem();
             mbar_arrive(&full[st]);
         }
@@ -567,7 +585,10 @@ k_blur_cols_tc(const __grid_constant__ TcBlurParams p, int n_stage)
             const int st = (int)(j % n_stage);
             const int buf = (int)(j & 1);
             const uint32_t bph = (uint32_t)((j >> 1) & 1);
-            if (!warp_wait(&accf[buf], bph, abort_flag)) {
+            // acc_full follows full[st] through the MMA commit; waiting on
+            // full[st] too makes the producers' tp tile visible here directly
+            if (!warp_wait(&accf[buf], bph, abort_flag) ||
+                !warp_wait(&full[st], (uint32_t)((j / n_stage) & 1), abort_flag)) {
                 *abort_flag = 1;
                 break;
             }
@@ -586,9 +607,15 @@ k_blur_cols_tc(const __grid_constant__ TcBlurParams p, int n_stage)
                 for (int i = 0; i < 16; ++i) r[i] = 0.0f;
                 for (int jj = 0; jj <= 2 * rp; ++jj) {
                     const float g = p.gp[jj];
-                    const float *row = tpt + jj * kTpPitch + j0;
+                    const float4 *row = reinterpret_cast<const float4 *>(tpt + jj * kTpPitch + j0);
 #pragma unroll
-                    for (int i = 0; i < 16; ++i) r[i] = fmaf(g, row[i], r[i]);
+                    for (int i = 0; i < 4; ++i) {
+                        const float4 x = row[i];
+                        r[4 * i] = fmaf(g, x.x, r[4 * i]);
+                        r[4 * i + 1] = fmaf(g, x.y, r[4 * i + 1]);
+                        r[4 * i + 2] = fmaf(g, x.z, r[4 * i + 2]);
+                        r[4 * i + 3] = fmaf(g, x.w, r[4 * i + 3]);
+                    }
                 }
 #pragma unroll
                 for (int i = 0; i < 16; ++i) r[i] = p.n0 * (r[i] + p.spr * v[i]);
