@@ -148,10 +148,12 @@ def _kernel_models(wl):
     return {
         # labels once + T written once
         "project": {"bytes": g.n_voxels + 4 * px, "flops": None, "bound": "hbm"},
-        # T read, two intermediates written; 2 flops per tap per output
-        "blur_rows": {"bytes": 12 * px, "flops": 2 * taps * px, "bound": "alu"},
+        # T read, two intermediates written (2 flops per tap per output of
+        # direct convolution; on the tensor cores the MMA work is small next
+        # to the traffic, so HBM is the roofline)
+        "blur_rows": {"bytes": 12 * px, "flops": 2 * taps * px, "bound": "hbm"},
         # two intermediates read, counts written
-        "blur_cols": {"bytes": 12 * px, "flops": 2 * taps * px, "bound": "alu"},
+        "blur_cols": {"bytes": 12 * px, "flops": 2 * taps * px, "bound": "hbm"},
         # reachable rows: counts read, filtered written; odd taps + centre
         "fdk_filter": {"bytes": 8 * fpx, "flops": 2 * (odd + 1) * fpx, "bound": "alu"},
         # filtered reachable rows read once, FP64 volume written once
