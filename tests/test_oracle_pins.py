@@ -490,3 +490,55 @@ def test_noise_before_psf_flood_statistics(orc):
     want = lam0 * (g * g).sum() ** 2
     assert inner.var() == pytest.approx(want, rel=0.1)
     assert inner.var() < 0.2 * lam0
+
+
+def test_scatter_fit_form():
+    # Sec. II.E fit: y(0) = 1, y(a) = 2^(-b/2), (a/|x|)^b far out, b = 0 flat
+    from oracle import groups as OG
+    a, b = 12.0, 1.7
+    assert OG.scatter_fit(0.0, a, b) == 1.0
+    assert OG.scatter_fit(a, a, b) == pytest.approx(2.0 ** (-b / 2), rel=1e-14)
+    assert OG.scatter_fit(1e5, a, b) == pytest.approx((a / 1e5) ** b, rel=1e-7)
+    assert np.all(OG.scatter_fit(np.linspace(-30, 30, 61), a, 0.0) == 1.0)
+    y = OG.scatter_fit(np.linspace(0, 30, 31), a, b)
+    assert np.all(np.diff(y) < 0)
+
+
+def _group_case():
+    wl = W.scaled(W.WORKLOADS["small_kv"], n_u=40, n_v=24, nx=16, ny=16, nz=8, dx=1.0,
+                  dy=1.0, dz=1.0, n_angles=3, du=0.5, dv=0.5)
+    return wl, wl.make_phantom()
+
+
+def test_group_primaries_partition_the_energy_sum(orc):
+    # sum over groups of the group primaries is the projector's T
+    from oracle import groups as OG
+    wl, lab = _group_case()
+    w, d = wl.spectrum()
+    P = OG.group_primaries(wl.geom, lab, w, d, wl.mu(), [0, 3, 9, 14, wl.n_e])
+    T = orc.project_T(wl.geom, lab, w, d, wl.mu())
+    np.testing.assert_allclose(P.sum(axis=0), T, rtol=1e-12)
+    assert np.all(P >= 0)
+
+
+def test_group_intensity_reduces_to_single_kernel(orc):
+    # one group without scatter: N0 G_sigma (x) T, the default model with SPR 0;
+    # a scatter profile alone is blurred only across u (it is flat along v)
+    from oracle import groups as OG
+    wl, lab = _group_case()
+    g = wl.geom
+    w, d = wl.spectrum()
+    T = orc.project_T(g, lab, w, d, wl.mu())
+    I = OG.intensity_groups(g, T[None], [1.4], [0.0], [10.0], [1.0], 1e4)
+    np.testing.assert_allclose(I, orc.intensity(T, 1.4, 5.0, 0.0, 1e4), rtol=1e-13)
+    P0 = np.zeros((2,) + T.shape)
+    I0 = OG.intensity_groups(g, P0, [0.8, 2.0], [0.1, 0.3], [8.0, 15.0], [1.2, 2.0], 1.0)
+    assert np.allclose(I0, I0[:, :1, :], rtol=0, atol=1e-15)
+    x = OG.off_axis_cm(g)
+    want = (orc.gauss_blur(np.broadcast_to(0.1 * OG.scatter_fit(x, 8.0, 1.2), (1, 1, g.n_u)), 0.8)
+            + orc.gauss_blur(np.broadcast_to(0.3 * OG.scatter_fit(x, 15.0, 2.0), (1, 1, g.n_u)), 2.0))
+    np.testing.assert_allclose(I0[0, 0], want[0, 0], rtol=1e-13)
+    # flood without a phantom: groups sum to N0 everywhere when amp = 0
+    Pf = np.stack([np.full(T.shape, 0.25), np.full(T.shape, 0.75)])
+    If = OG.intensity_groups(g, Pf, [0.8, 3.0], [0.0, 0.0], [8.0, 8.0], [1.0, 1.0], 2.5e4)
+    np.testing.assert_allclose(If, 2.5e4, rtol=1e-13)
