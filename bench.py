@@ -409,10 +409,43 @@ def _extra_paper_timing(fc, torch):
     return out
 
 
+def _extra_groups(fc, torch):
+    """One simulate + reconstruct step of the catphan_kv scan with the
+    four-group detector model (per-group optical spread, fitted scatter
+    profiles; W.energy_groups)."""
+    wl = W.WORKLOADS["catphan_kv"]
+    g = wl.geom
+    sc = fc.Scanner(wl, noise=True)
+    try:
+        grp = W.energy_groups(wl, 4)
+        fc.fc_set_energy_groups(sc.h, **grp)
+        vol = torch.empty((g.nz, g.ny, g.nx), dtype=torch.float64, device="cuda")
+        for _ in range(2):
+            fc.fc_project(sc.h, 0, g.n_angles, fc.FC_OUT_NONE, None)
+            fc.fc_reconstruct(sc.h, None, vol_mu=vol)
+        torch.cuda.synchronize()
+        fc.fc_profile_enable(sc.h, True)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        fc.fc_project(sc.h, 0, g.n_angles, fc.FC_OUT_NONE, None)
+        fc.fc_reconstruct(sc.h, None, vol_mu=vol)
+        b.record()
+        torch.cuda.synchronize()
+        kern = fc.fc_profile_read(sc.h)
+        ms = a.elapsed_time(b)
+        return {"workload": "catphan_kv with 4 energy groups", "ms_per_step": ms,
+                "rays_bins_per_s": g.n_rays * wl.n_e / (ms / 1e3),
+                "kernels_ms": {k: v[0] for k, v in kern.items() if v[1]}}
+    finally:
+        sc.close()
+
+
 def _extras(args, fc, torch):
     out = {}
     jobs = [("adjoint", lambda: _extra_adjoint(fc, torch)),
             ("dose", lambda: _extra_dose(fc, torch)),
+            ("groups", lambda: _extra_groups(fc, torch)),
             ("paper_timing", lambda: _extra_paper_timing(fc, torch)),
             ("paper_scale", lambda: _extra_paper_scale(fc, torch))]
     if not args.no_surrogate:

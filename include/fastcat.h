@@ -149,6 +149,38 @@ int fc_project(fc_handle *h, int angle_begin, int angle_count, int out_kind,
 #define FC_NOISE_BEFORE_PSF 1
 int fc_set_noise_order(fc_handle *h, int order);
 
+/* Energy-group detector model (Sec. II.E scatter fit, Sec. II.F I_f
+ * equation, Sec. II.G optical spread "at each energy and summed"), with the
+ * spectrum's bins lumped into contiguous groups g = [bin_end[g-1], bin_end[g]):
+ *   P_g = sum_{E in g} w D exp(-sum_m mu_m(E) L_m) / sum_E w D  (sum_g P_g = T)
+ *   I   = N0 sum_g G_g (x) (P_g + A_g y_g(x)),
+ *   y_g(x) = (a_g / sqrt(x^2 + a_g^2))^b_g, x = off-axis distance of the
+ *   detector column, cm; G_g a sampled Gaussian (clamp-to-edge) of sigma_g px;
+ *   K   = Poisson(I) when noise is on.
+ * It replaces the single-kernel model of fc_set_spectrum_detector (psf,
+ * scatter sigma and spr) for FC_OUT_INTENSITY, FC_OUT_COUNTS and FC_OUT_NONE;
+ * FC_OUT_PRIMARY still returns T.  The flood used by fc_reconstruct is then
+ * N0 (no phantom, no scatter).  Noise before the optical spread is not
+ * defined for this model (fc_project returns FC_EINVAL with that order).
+ *   n_groups     0 turns the model off; else 1 .. FC_MAX_GROUPS;
+ *   bin_end      [n_groups] strictly increasing, last = n_e of the spectrum;
+ *   psf_sigma_px [n_groups] in [0, FC_MAX_GROUP_SIGMA_PX];
+ *   scatter_amp  [n_groups] A_g >= 0, relative to the flood;
+ *   scatter_a_cm [n_groups] a_g > 0;  scatter_b [n_groups] b_g >= 0.
+ * Arrays are host memory, copied.  Call after fc_set_spectrum_detector
+ * (which clears the groups).  Errors: FC_ESTATE (no spectrum), FC_EINVAL. */
+#define FC_MAX_GROUPS 8
+#define FC_MAX_GROUP_SIGMA_PX 4.0
+typedef struct fc_energy_groups {
+    int32_t n_groups;
+    const int32_t *bin_end;
+    const double *psf_sigma_px;
+    const double *scatter_amp;
+    const double *scatter_a_cm;
+    const double *scatter_b;
+} fc_energy_groups;
+int fc_set_energy_groups(fc_handle *h, const fc_energy_groups *g);
+
 /* FDK reconstruction (Sec. II.G): p = ln(I_flood / max(K, 1)),
  * I_flood = N0 (1 + SPR); cosine weight SAD / sqrt(SAD^2 + u^2 + v^2) at the
  * isocentre; Ram-Lak row filter; voxel-driven bilinear backprojection with
@@ -223,7 +255,8 @@ int fc_fluence_for_dose(const fc_handle *h, double dose_gy, double dp_gy, double
 #define FC_K_SURROGATE_TRAIN 9  /* surrogate training steps (4 kernels per step) */
 #define FC_K_ENERGY_SUM     10  /* exact energy sum from path lengths */
 #define FC_K_DOSE           11  /* dose estimate (three kernels) */
-#define FC_K_COUNT          12
+#define FC_K_GROUP_BLUR     12  /* energy-group model: scatter profile + per-group blur (2 kernels) */
+#define FC_K_COUNT          13
 
 /* Enable (1) or disable (0) tracing; enabling discards pending records.
  * Errors: FC_EINVAL. */

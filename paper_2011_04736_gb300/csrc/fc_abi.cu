@@ -79,6 +79,13 @@ struct fc_handle {
     uint64_t seed = 0;
     int noise = 0;
     int noise_order = FC_NOISE_AFTER_BLUR;
+    // energy-group detector model (off when n_groups == 0)
+    int n_groups = 0;
+    int grp_end[FC_MAX_GROUPS] = {0};
+    double grp_psf[FC_MAX_GROUPS] = {0}, grp_amp[FC_MAX_GROUPS] = {0};
+    double grp_a[FC_MAX_GROUPS] = {0}, grp_b[FC_MAX_GROUPS] = {0};
+    float *d_grp = nullptr, *d_prof = nullptr;   // group primaries, scatter profile
+    int grp_alloc = 0;
     double water_r = 1.0, zmargin = 0.1;
     // device buffers
     float2 *d_trig = nullptr;
@@ -139,6 +146,8 @@ struct fc_handle {
         dfree(d_part);
         dfree(d_flag);
         dfree(d_dose);
+        dfree(d_grp);
+        dfree(d_prof);
         dfree(d_hankel);
         dfree(d_blur_err);
         for (auto &r : pending) {
@@ -461,6 +470,7 @@ int fc_set_spectrum_detector(fc_handle *h, const fc_spectrum_detector *s)
     rc = gauss_taps(s->scatter_sigma_px, tmp, &r);
     if (rc) return rc;
     h->n_e = s->n_e;
+    h->n_groups = 0;   // energy groups refer to the previous spectrum's bins
     h->n_mat = s->n_mat;
     h->wd.assign(s->n_e, 0.0f);
     h->phi.assign(s->n_e, 0.0);
@@ -582,6 +592,86 @@ static int run_blur(fc_handle *h, const float *in, float *out, size_t off, int n
     return FC_OK;
 }
 
+// Energy-group model: group primaries (projector), then the scatter profile
+// and the per-group blur into the counts buffer.
+static int run_groups(fc_handle *h, int a0, int na, cudaStream_t s)
+{
+    fc::ProjParams p;
+    int rc = fill_proj_params(h, a0, na, &p);
+    if (rc) return rc;
+    const size_t plane_all = h->proj_elems;
+    if (!h->d_grp || h->grp_alloc < h->n_groups) {
+        dfree(h->d_grp);
+        FC_CK(cudaMalloc((void **)&h->d_grp, (size_t)h->n_groups * plane_all * sizeof(float)));
+        h->grp_alloc = h->n_groups;
+    }
+    if (!h->d_prof) FC_CK(cudaMalloc((void **)&h->d_prof, (size_t)h->g.n_u * sizeof(float)));
+    p.n_groups = h->n_groups;
+    for (int i = 0; i < h->n_groups; ++i) p.grp_end[i] = h->grp_end[i];
+    p.grp_stride = plane_all;
+    {
+        Trace t(h, FC_K_PROJECT, 1, s);
+        FC_CK(fc::launch_project_groups(p, h->d_grp, s));
+        t.end();
+    }
+    fc::GroupParams gp;
+    memset(&gp, 0, sizeof(gp));
+    gp.n_u = h->g.n_u;
+    gp.n_v = h->g.n_v;
+    gp.n_groups = h->n_groups;
+    gp.grp_stride = plane_all;
+    for (int i = 0; i < h->n_groups; ++i) {
+        rc = gauss_taps(h->grp_psf[i], gp.taps[i], &gp.r[i]);
+        if (rc) return rc;
+        gp.amp[i] = (float)h->grp_amp[i];
+        gp.a_cm[i] = (float)h->grp_a[i];
+        gp.b[i] = (float)h->grp_b[i];
+    }
+    gp.du = (float)h->g.du_cm;
+    gp.cu = 0.5f * (float)(h->g.n_u - 1);
+    gp.n0 = (float)h->n0;
+    Trace t(h, FC_K_GROUP_BLUR, 2, s);
+    FC_CK(fc::launch_group_blur(gp, h->d_grp, h->d_prof, h->d_counts, a0, na, s));
+    t.end();
+    return FC_OK;
+}
+
+int fc_set_energy_groups(fc_handle *h, const fc_energy_groups *g)
+{
+    if (!h || !g) return fail(FC_EINVAL, "fc_set_energy_groups: null argument");
+    if (g->n_groups == 0) {
+        h->n_groups = 0;
+        return FC_OK;
+    }
+    if (!h->has_spec) return fail(FC_ESTATE, "fc_set_energy_groups: set the spectrum first");
+    if (g->n_groups < 0 || g->n_groups > FC_MAX_GROUPS)
+        return fail(FC_EINVAL, "fc_set_energy_groups: n_groups %d outside [0, %d]", g->n_groups, FC_MAX_GROUPS);
+    if (!g->bin_end || !g->psf_sigma_px || !g->scatter_amp || !g->scatter_a_cm || !g->scatter_b)
+        return fail(FC_EINVAL, "fc_set_energy_groups: null array");
+    int prev = 0;
+    for (int i = 0; i < g->n_groups; ++i) {
+        if (g->bin_end[i] <= prev || g->bin_end[i] > h->n_e)
+            return fail(FC_EINVAL, "fc_set_energy_groups: bin_end must increase within (0, n_e]");
+        prev = g->bin_end[i];
+        if (!(g->psf_sigma_px[i] >= 0) || g->psf_sigma_px[i] > FC_MAX_GROUP_SIGMA_PX)
+            return fail(FC_EINVAL, "fc_set_energy_groups: group %d sigma outside [0, %g]", i,
+                        (double)FC_MAX_GROUP_SIGMA_PX);
+        if (!(g->scatter_amp[i] >= 0) || !isfinite(g->scatter_amp[i]) || !(g->scatter_a_cm[i] > 0) ||
+            !isfinite(g->scatter_a_cm[i]) || !(g->scatter_b[i] >= 0) || !isfinite(g->scatter_b[i]))
+            return fail(FC_EINVAL, "fc_set_energy_groups: bad scatter parameters for group %d", i);
+    }
+    if (prev != h->n_e) return fail(FC_EINVAL, "fc_set_energy_groups: last bin_end must equal n_e");
+    for (int i = 0; i < g->n_groups; ++i) {
+        h->grp_end[i] = g->bin_end[i];
+        h->grp_psf[i] = g->psf_sigma_px[i];
+        h->grp_amp[i] = g->scatter_amp[i];
+        h->grp_a[i] = g->scatter_a_cm[i];
+        h->grp_b[i] = g->scatter_b[i];
+    }
+    h->n_groups = g->n_groups;
+    return FC_OK;
+}
+
 int fc_project(fc_handle *h, int angle_begin, int angle_count, int out_kind, float *out,
                int out_where, void *stream)
 {
@@ -600,13 +690,29 @@ int fc_project(fc_handle *h, int angle_begin, int angle_count, int out_kind, flo
     const size_t plane = (size_t)h->g.n_v * h->g.n_u;
     const size_t off = (size_t)angle_begin * plane;
     const size_t bytes = (size_t)angle_count * plane * sizeof(float);
-    {
+    if (h->n_groups && out_kind != FC_OUT_PRIMARY) {
+        if (h->noise_order == FC_NOISE_BEFORE_PSF)
+            return fail(FC_EINVAL, "fc_project: noise before the optical spread is not defined for energy groups");
+    } else {
         Trace t(h, FC_K_PROJECT, 1, s);
         FC_CK(fc::launch_project(p, h->d_T, nullptr, s));
         t.end();
     }
     if (out_kind == FC_OUT_PRIMARY) return angle_count ? copy_out(out, out_where, h->d_T + off, bytes, s) : FC_OK;
     const bool noise = (out_kind != FC_OUT_INTENSITY) && h->noise;
+    if (h->n_groups) {
+        rc = run_groups(h, angle_begin, angle_count, s);
+        if (rc) return rc;
+        if (noise) {
+            Trace t(h, FC_K_NOISE, 1, s);
+            FC_CK(fc::launch_poisson(h->d_counts + off, h->d_counts + off, angle_count, h->g.n_v,
+                                     h->g.n_u, angle_begin, h->seed, s));
+            t.end();
+        }
+        h->has_counts = true;
+        if (out_kind == FC_OUT_NONE || angle_count == 0) return FC_OK;
+        return copy_out(out, out_where, h->d_counts + off, bytes, s);
+    }
     if (h->noise_order == FC_NOISE_BEFORE_PSF) {
         // Sec. II.G order: counts drawn from the scatter-added rate, then the
         // optical spread applied to the counts
@@ -759,7 +865,9 @@ int fc_reconstruct(fc_handle *h, const float *counts, int counts_where, double *
     fc::FdkParams p;
     p.g = h->dg;
     p.trig = h->d_trig;
-    p.log_flood = (float)log(h->n0 * (1.0 + h->spr));
+    // flood: T = 1 through the detector model (single kernel: N0 (1 + SPR);
+    // energy groups: N0, the scatter profile needing a phantom)
+    p.log_flood = (float)log(h->n_groups ? h->n0 : h->n0 * (1.0 + h->spr));
     p.tau = (float)(h->g.du_cm * h->g.sad_cm / h->g.sdd_cm);
     p.mag = (float)(h->g.sad_cm / h->g.sdd_cm);
     p.scale = h->g.arc_rad / (2.0 * h->g.n_angles);

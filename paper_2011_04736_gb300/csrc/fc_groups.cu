@@ -1,0 +1,109 @@
+// Energy-group detector model: the scatter profile of Sec. II.E added to each
+// group's primary and the optical spread of Sec. II.G applied per group
+// ("convolved with the OSF at each energy and summed"):
+//
+//   I = N0 sum_g G_g (x) (P_g + A_g y_g(x)),   y_g(x) = (a_g / sqrt(x^2 + a_g^2))^b_g
+//
+// The scatter term depends on the detector column only, and a clamp-to-edge
+// blur leaves a row-constant image constant along v, so it reduces to one
+// profile prof[u] = N0 sum_g A_g (g_g (x)_u y_g)(u) (k_group_profile).  The
+// primaries go through k_group_blur: one CTA per 64 x 32 output tile, each
+// group's tile (with a clamped halo of its radius) staged in shared memory,
+// separable row then column passes, the groups accumulated in registers.
+#include <math.h>
+
+#include "fc_internal.cuh"
+
+namespace fc {
+
+namespace {
+
+constexpr int kTu = 64, kTv = 32;                 // output tile (columns x rows)
+constexpr int kThreads = 256;                     // 64 columns x 4 row groups of 8
+constexpr int kInH = kTv + 2 * kMaxGroupR;
+constexpr int kInW = kTu + 2 * kMaxGroupR;
+
+__device__ __forceinline__ int clampi(int i, int n) { return i < 0 ? 0 : (i > n - 1 ? n - 1 : i); }
+
+}  // namespace
+
+__global__ void k_group_profile(const __grid_constant__ GroupParams p, float *__restrict__ prof)
+{
+    const int u = blockIdx.x * blockDim.x + threadIdx.x;
+    if (u >= p.n_u) return;
+    float acc = 0.0f;
+    for (int gi = 0; gi < p.n_groups; ++gi) {
+        if (!(p.amp[gi] > 0.0f)) continue;
+        const int R = p.r[gi];
+        const float a = p.a_cm[gi];
+        float s = 0.0f;
+        for (int j = -R; j <= R; ++j) {
+            const float x = ((float)clampi(u + j, p.n_u) - p.cu) * p.du;
+            s = fmaf(p.taps[gi][j + R], powf(a / sqrtf(fmaf(x, x, a * a)), p.b[gi]), s);
+        }
+        acc = fmaf(p.amp[gi], s, acc);
+    }
+    prof[u] = p.n0 * acc;
+}
+
+__global__ void __launch_bounds__(kThreads)
+k_group_blur(const __grid_constant__ GroupParams p, const float *__restrict__ P,
+             const float *__restrict__ prof, float *__restrict__ out)
+{
+    __shared__ float sin_[kInH][kInW + 1];
+    __shared__ float smid[kInH][kTu + 1];
+    const int tid = threadIdx.x, tx = tid % kTu, ty = tid / kTu;
+    const int u0 = blockIdx.x * kTu, v0 = blockIdx.y * kTv;
+    const size_t img = (size_t)blockIdx.z * p.n_u * p.n_v;
+    float acc[8];
+#pragma unroll
+    for (int o = 0; o < 8; ++o) acc[o] = 0.0f;
+    for (int gi = 0; gi < p.n_groups; ++gi) {
+        const int R = p.r[gi], H = kTv + 2 * R, Wd = kTu + 2 * R, nt = 2 * R + 1;
+        const float *src = P + (size_t)gi * p.grp_stride + img;
+        const float *tap = p.taps[gi];
+        __syncthreads();
+        for (int i = tid; i < H * Wd; i += kThreads) {
+            const int r = i / Wd, c = i % Wd;
+            sin_[r][c] = __ldg(src + (size_t)clampi(v0 - R + r, p.n_v) * p.n_u + clampi(u0 - R + c, p.n_u));
+        }
+        __syncthreads();
+        for (int i = tid; i < H * kTu; i += kThreads) {
+            const int r = i / kTu, c = i % kTu;
+            float s = 0.0f;
+            for (int j = 0; j < nt; ++j) s = fmaf(tap[j], sin_[r][c + j], s);
+            smid[r][c] = s;
+        }
+        __syncthreads();
+        for (int j = 0; j < nt; ++j) {
+            const float t = tap[j];
+#pragma unroll
+            for (int o = 0; o < 8; ++o) acc[o] = fmaf(t, smid[ty * 8 + o + j][tx], acc[o]);
+        }
+    }
+    const int u = u0 + tx;
+    if (u >= p.n_u) return;
+    const float pu = prof[u];
+#pragma unroll
+    for (int o = 0; o < 8; ++o) {
+        const int v = v0 + ty * 8 + o;
+        if (v < p.n_v) out[img + (size_t)v * p.n_u + u] = fmaf(p.n0, acc[o], pu);
+    }
+}
+
+cudaError_t launch_group_blur(const GroupParams &g, const float *P, float *prof, float *out,
+                              int angle0, int n_img, cudaStream_t s)
+{
+    if (n_img <= 0) return cudaSuccess;
+    k_group_profile<<<(g.n_u + 127) / 128, 128, 0, s>>>(g, prof);
+    const size_t plane = (size_t)g.n_u * g.n_v;
+    for (int i0 = 0; i0 < n_img; i0 += 65535) {   // grid z limit
+        const int n = n_img - i0 < 65535 ? n_img - i0 : 65535;
+        const size_t off = (size_t)(angle0 + i0) * plane;
+        dim3 grid((g.n_u + kTu - 1) / kTu, (g.n_v + kTv - 1) / kTv, n);
+        k_group_blur<<<grid, kThreads, 0, s>>>(g, P + off, prof, out + off);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace fc

@@ -39,8 +39,23 @@ struct ProjParams {
     int n_angles_launch;
     int v_hit_lo, v_hit_hi; // detector rows whose rays can meet the voxel slab
     int n_mat, n_e;
+    int n_groups;                   // energy-group output (k_project<kModeGroups>)
+    int grp_end[FC_MAX_GROUPS];     // exclusive end bin of each group
+    size_t grp_stride;              // elements between group planes of the output
     float wd[kMaxBins];             // w D / sum(w D)
     float mu2[kMaxBins][kMaxMat];   // mu * log2(e), zero padded
+};
+
+// Energy-group detector model: per-group optical spread and scatter profile.
+constexpr int kMaxGroupR = 16;      // ceil(4 * FC_MAX_GROUP_SIGMA_PX)
+struct GroupParams {
+    int n_u, n_v, n_groups;
+    size_t grp_stride;              // elements between group planes of P
+    int r[FC_MAX_GROUPS];
+    float taps[FC_MAX_GROUPS][2 * kMaxGroupR + 1];
+    float amp[FC_MAX_GROUPS], a_cm[FC_MAX_GROUPS], b[FC_MAX_GROUPS];
+    float du, cu;                   // detector pitch (cm) and centre column
+    float n0;
 };
 
 // Final reduction of the dose estimate (Sec. II.H).
@@ -210,6 +225,9 @@ cudaError_t launch_blur_adjoint(const BlurParams &b, int n_img, const float *gI,
 
 // launchers (return cudaError_t of the launch)
 cudaError_t launch_project(const ProjParams &p, float *T, float *L_out, cudaStream_t s);
+cudaError_t launch_project_groups(const ProjParams &p, float *P, cudaStream_t s);
+cudaError_t launch_group_blur(const GroupParams &g, const float *P, float *prof, float *out,
+                              int angle0, int n_img, cudaStream_t s);
 cudaError_t launch_blur_rows(const BlurParams &p, const float *T, float *tp, float *ts,
                              int n_img, cudaStream_t s);
 cudaError_t launch_blur_cols(const BlurParams &p, const float *tp, const float *ts, float *out,

@@ -253,6 +253,50 @@ cudaError_t launch_project(const ProjParams &p, float *T, float *L_out, cudaStre
     return cudaGetLastError();
 }
 
+// Energy-group primaries (the I_f equation of Sec. II.F split over groups of
+// contiguous bins): P_g = sum_{E in g} w D exp(-sum_m mu_m L_m) / sum_E w D,
+// a compensated sum per group, written to P + g * grp_stride at the ray's
+// absolute position.  Rays that miss the volume give P_g = sum_{E in g} wD.
+__global__ void __launch_bounds__(256)
+k_project_groups(const __grid_constant__ ProjParams p, float *__restrict__ P)
+{
+    const DevGeom &g = p.g;
+    const int iu = blockIdx.x * 32 + threadIdx.x;
+    const int iv = blockIdx.y * blockDim.y + threadIdx.y;
+    if (iu >= g.n_u || iv >= g.n_v) return;
+    const int k = p.angle0 + blockIdx.z;
+    float L[kMaxMat];
+    const bool hit = trace_ray(p, iu, iv, k, L);
+    const size_t ray = ((size_t)k * g.n_v + iv) * g.n_u + iu;
+    int e = 0;
+    for (int gi = 0; gi < p.n_groups; ++gi) {
+        float sum = 0.0f, comp = 0.0f;
+        for (const int e1 = p.grp_end[gi]; e < e1; ++e) {
+            float term = p.wd[e];
+            if (hit) {
+                float a = 0.0f;
+#pragma unroll
+                for (int m = 0; m < kMaxMat; ++m) a = fmaf(p.mu2[e][m], L[m], a);
+                term *= exp2f(-a);
+            }
+            const float y = term - comp;
+            const float t = sum + y;
+            comp = (t - sum) - y;
+            sum = t;
+        }
+        P[(size_t)gi * p.grp_stride + ray] = sum;
+    }
+}
+
+cudaError_t launch_project_groups(const ProjParams &p, float *P, cudaStream_t s)
+{
+    if (p.n_angles_launch <= 0) return cudaSuccess;
+    dim3 block(32, 8);
+    dim3 grid((p.g.n_u + 31) / 32, (p.g.n_v + 7) / 8, p.n_angles_launch);
+    k_project_groups<<<grid, block, 0, s>>>(p, P);
+    return cudaGetLastError();
+}
+
 // Dose estimate, Sec. II.H: for every energy bin E, the sum over the rays of
 // the fraction a ray loses in the phantom, 1 - exp(-sum_m mu_m(E) L_m).
 // Blocks walk 32 x 8 pixel tiles in a fixed order; each warp traces its row

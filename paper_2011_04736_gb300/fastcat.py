@@ -30,12 +30,13 @@ ENTRY_POINTS = ("fc_create", "fc_destroy", "fc_last_error", "fc_set_geometry", "
                 "fc_detector_blur_static", "fc_surrogate_init", "fc_surrogate_train",
                 "fc_surrogate_grad", "fc_surrogate_get", "fc_surrogate_set", "fc_surrogate_eval",
                 "fc_energy_sum_lengths", "fc_cnr_grad", "fc_surrogate_project",
-                "fc_dose_estimate", "fc_fluence_for_dose", "fc_set_noise_order")
+                "fc_dose_estimate", "fc_fluence_for_dose", "fc_set_noise_order",
+                "fc_set_energy_groups")
 FC_STATIC_SCRATCH_FLOATS = 8 << 20
 FC_SURROGATE_PARAMS = 34305
 FC_SURROGATE_STATE = 34305 + 52 + 2 * 34305 + 1
 FC_K_NAMES = ("project", "blur_rows", "blur_cols", "fdk_filter", "backproject", "hu", "lengths",
-              "noise", "surrogate_eval", "surrogate_train", "energy_sum", "dose")
+              "noise", "surrogate_eval", "surrogate_train", "energy_sum", "dose", "group_blur")
 
 
 class FastcatError(RuntimeError):
@@ -65,6 +66,12 @@ class fc_spectrum_detector(ctypes.Structure):
                 ("psf_sigma_px", ctypes.c_double), ("scatter_sigma_px", ctypes.c_double),
                 ("spr", ctypes.c_double), ("n0", ctypes.c_double),
                 ("seed", ctypes.c_uint64), ("noise", ctypes.c_int32)]
+
+
+class fc_energy_groups(ctypes.Structure):
+    _fields_ = [("n_groups", ctypes.c_int32), ("bin_end", ctypes.c_void_p),
+                ("psf_sigma_px", ctypes.c_void_p), ("scatter_amp", ctypes.c_void_p),
+                ("scatter_a_cm", ctypes.c_void_p), ("scatter_b", ctypes.c_void_p)]
 
 
 _lib = None
@@ -109,6 +116,7 @@ def load():
         "fc_dose_estimate": (I, [P, I, I, P, P, P, P, P, I, P]),
         "fc_fluence_for_dose": (I, [P, ctypes.c_double, ctypes.c_double, P]),
         "fc_set_noise_order": (I, [P, I]),
+        "fc_set_energy_groups": (I, [P, ctypes.POINTER(fc_energy_groups)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -240,6 +248,19 @@ def fc_dose_estimate(h, angle_begin, angle_count, e_kev, muen_over_mu, rho, d0=N
     _check(load().fc_dose_estimate(h, angle_begin, angle_count, e.ctypes.data, m.ctypes.data,
                                    r.ctypes.data, p0, p1, w0, _stream(stream)))
     return d0, dp
+
+
+def fc_set_energy_groups(h, bin_end=(), psf_sigma_px=(), scatter_amp=(), scatter_a_cm=(),
+                         scatter_b=()):
+    """Energy-group detector model; no groups turns it off."""
+    be = np.ascontiguousarray(bin_end, np.int32)
+    arr = [np.ascontiguousarray(x, np.float64) for x in
+           (psf_sigma_px, scatter_amp, scatter_a_cm, scatter_b)]
+    n = len(be)
+    if any(len(a) != n for a in arr):
+        raise ValueError("all group arrays need n_groups entries")
+    gs = fc_energy_groups(n, be.ctypes.data, *[a.ctypes.data for a in arr])
+    return _check(load().fc_set_energy_groups(h, ctypes.byref(gs)))
 
 
 def fc_set_noise_order(h, order):
