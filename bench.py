@@ -441,11 +441,37 @@ def _extra_groups(fc, torch):
         sc.close()
 
 
+def _extra_deconv(fc, torch):
+    """Richardson-Lucy deconvolution of the catphan_kv counts (10 iterations
+    with the workload's PSF), per-iteration device time and the HBM rate of
+    its algorithmic bytes (u and d read, u written: 12 B per pixel)."""
+    wl = W.WORKLOADS["catphan_kv"]
+    g = wl.geom
+    sc = fc.Scanner(wl, noise=True)
+    try:
+        fc.fc_project(sc.h, 0, g.n_angles, fc.FC_OUT_NONE, None)
+        fc.fc_deconvolve_rl(sc.h, 0, g.n_angles, wl.psf_sigma_px, 2)
+        torch.cuda.synchronize()
+        fc.fc_profile_enable(sc.h, True)
+        n_iter = 10
+        fc.fc_deconvolve_rl(sc.h, 0, g.n_angles, wl.psf_sigma_px, n_iter)
+        kern = fc.fc_profile_read(sc.h)
+        ms = kern["deconv"][0]
+        per = ms / n_iter
+        px = g.n_angles * g.n_v * g.n_u
+        return {"workload": "catphan_kv counts, 360 x 512 x 384, PSF sigma %.1f px" % wl.psf_sigma_px,
+                "iterations": n_iter, "ms_total": ms, "ms_per_iteration": per,
+                "hbm_gbs_per_iteration": 12 * px / (per / 1e3) / 1e9}
+    finally:
+        sc.close()
+
+
 def _extras(args, fc, torch):
     out = {}
     jobs = [("adjoint", lambda: _extra_adjoint(fc, torch)),
             ("dose", lambda: _extra_dose(fc, torch)),
             ("groups", lambda: _extra_groups(fc, torch)),
+            ("deconv", lambda: _extra_deconv(fc, torch)),
             ("paper_timing", lambda: _extra_paper_timing(fc, torch)),
             ("paper_scale", lambda: _extra_paper_scale(fc, torch))]
     if not args.no_surrogate:

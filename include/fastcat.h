@@ -169,6 +169,20 @@ int fc_set_noise_order(fc_handle *h, int order);
  *   scatter_a_cm [n_groups] a_g > 0;  scatter_b [n_groups] b_g >= 0.
  * Arrays are host memory, copied.  Call after fc_set_spectrum_detector
  * (which clears the groups).  Errors: FC_ESTATE (no spectrum), FC_EINVAL. */
+/* Richardson-Lucy deconvolution of the handle's counts for projections
+ * angle_begin .. angle_begin + angle_count - 1 (the discussion of the paper,
+ * Sec. IV: projections deconvolved with the detector PSF before
+ * reconstruction), in place, as the EM update for Poisson data
+ *   u_{k+1} = u_k H^T(d / max(H u_k, 1e-12)) / H^T 1,   u_0 = d (the counts),
+ * H the clamp-to-edge separable sampled Gaussian of psf_sigma_px
+ * (0 .. FC_MAX_GROUP_SIGMA_PX) and H^T its exact adjoint; n_iter >= 0 steps.
+ * The result replaces the counts that fc_reconstruct(counts = NULL) uses and
+ * is also copied to `out` ([angle_count][n_v][n_u] float, host or device per
+ * `out_where`) when out is not NULL.
+ * Errors: FC_ESTATE (no counts), FC_EINVAL, FC_ECUDA. */
+int fc_deconvolve_rl(fc_handle *h, int angle_begin, int angle_count, double psf_sigma_px,
+                     int n_iter, float *out, int out_where, void *stream);
+
 #define FC_MAX_GROUPS 8
 #define FC_MAX_GROUP_SIGMA_PX 4.0
 typedef struct fc_energy_groups {
@@ -256,7 +270,8 @@ int fc_fluence_for_dose(const fc_handle *h, double dose_gy, double dp_gy, double
 #define FC_K_ENERGY_SUM     10  /* exact energy sum from path lengths */
 #define FC_K_DOSE           11  /* dose estimate (three kernels) */
 #define FC_K_GROUP_BLUR     12  /* energy-group model: scatter profile + per-group blur (2 kernels) */
-#define FC_K_COUNT          13
+#define FC_K_DECONV         13  /* Richardson-Lucy deconvolution (1 + n_iter kernels) */
+#define FC_K_COUNT          14
 
 /* Enable (1) or disable (0) tracing; enabling discards pending records.
  * Errors: FC_EINVAL. */

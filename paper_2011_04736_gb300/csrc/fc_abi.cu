@@ -85,6 +85,7 @@ struct fc_handle {
     double grp_psf[FC_MAX_GROUPS] = {0}, grp_amp[FC_MAX_GROUPS] = {0};
     double grp_a[FC_MAX_GROUPS] = {0}, grp_b[FC_MAX_GROUPS] = {0};
     float *d_grp = nullptr, *d_prof = nullptr;   // group primaries, scatter profile
+    float *d_rlnorm = nullptr;                   // deconvolution: H^T 1 per axis
     int grp_alloc = 0;
     double water_r = 1.0, zmargin = 0.1;
     // device buffers
@@ -148,6 +149,7 @@ struct fc_handle {
         dfree(d_dose);
         dfree(d_grp);
         dfree(d_prof);
+        dfree(d_rlnorm);
         dfree(d_hankel);
         dfree(d_blur_err);
         for (auto &r : pending) {
@@ -634,6 +636,53 @@ static int run_groups(fc_handle *h, int a0, int na, cudaStream_t s)
     FC_CK(fc::launch_group_blur(gp, h->d_grp, h->d_prof, h->d_counts, a0, na, s));
     t.end();
     return FC_OK;
+}
+
+int fc_deconvolve_rl(fc_handle *h, int angle_begin, int angle_count, double psf_sigma_px,
+                     int n_iter, float *out, int out_where, void *stream)
+{
+    if (!h) return fail(FC_EINVAL, "fc_deconvolve_rl: null handle");
+    if (!h->has_geom || !h->has_counts || !h->d_counts)
+        return fail(FC_ESTATE, "fc_deconvolve_rl: no counts in the handle (run fc_project first)");
+    if (angle_begin < 0 || angle_count < 0 || angle_begin + angle_count > h->g.n_angles)
+        return fail(FC_EINVAL, "fc_deconvolve_rl: angles [%d, %d) outside [0, %d)", angle_begin,
+                    angle_begin + angle_count, h->g.n_angles);
+    if (!(psf_sigma_px >= 0) || psf_sigma_px > FC_MAX_GROUP_SIGMA_PX)
+        return fail(FC_EINVAL, "fc_deconvolve_rl: sigma outside [0, %g]", (double)FC_MAX_GROUP_SIGMA_PX);
+    if (n_iter < 0) return fail(FC_EINVAL, "fc_deconvolve_rl: negative iteration count");
+    if (out && out_where != FC_HOST && out_where != FC_DEVICE)
+        return fail(FC_EINVAL, "fc_deconvolve_rl: bad out_where");
+    DeviceGuard dgd(h->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    int rc = ensure_proj_buffers(h);
+    if (rc) return rc;
+    fc::RlParams p;
+    memset(&p, 0, sizeof(p));
+    p.n_u = h->g.n_u;
+    p.n_v = h->g.n_v;
+    rc = gauss_taps(psf_sigma_px, p.taps, &p.R);
+    if (rc) return rc;
+    for (int k = 0; k <= p.R; ++k) {
+        double c = 0.0;
+        for (int j = 0; j < p.R - k; ++j) c += p.taps[j];   // taps j - R < -k
+        p.cl[k] = (float)c;
+    }
+    p.floor_ = 1e-12f;
+    if (!h->d_rlnorm)
+        FC_CK(cudaMalloc((void **)&h->d_rlnorm, (size_t)(h->g.n_u + h->g.n_v) * sizeof(float)));
+    const size_t plane = (size_t)h->g.n_v * h->g.n_u;
+    const size_t off = (size_t)angle_begin * plane;
+    const size_t bytes = (size_t)angle_count * plane * sizeof(float);
+    float *res = nullptr;
+    {
+        Trace t(h, FC_K_DECONV, n_iter + 1, s);
+        FC_CK(fc::launch_rl(p, h->d_counts + off, h->d_tp + off, h->d_ts + off, h->d_rlnorm,
+                            angle_count, n_iter, &res, s));
+        t.end();
+    }
+    if (res) FC_CK(cudaMemcpyAsync(h->d_counts + off, res, bytes, cudaMemcpyDeviceToDevice, s));
+    if (!out || angle_count == 0) return FC_OK;
+    return copy_out(out, out_where, h->d_counts + off, bytes, s);
 }
 
 int fc_set_energy_groups(fc_handle *h, const fc_energy_groups *g)

@@ -58,6 +58,14 @@ struct GroupParams {
     float n0;
 };
 
+// Richardson-Lucy deconvolution (fc_deconvolve.cu): blur radius <= 16.
+struct RlParams {
+    int n_u, n_v, R;
+    float taps[2 * kMaxGroupR + 1];
+    float cl[kMaxGroupR + 1];       // cl[k] = sum of taps j < -k (mass clamped onto index 0)
+    float floor_;                   // lower bound of H u before the division
+};
+
 // Final reduction of the dose estimate (Sec. II.H).
 constexpr int kDoseBlocks = 2048;            // most blocks of the per-bin partial sums
 constexpr double kGyGramPerKev = 1.602176634e-13;  // 1 keV per gram, in Gy
@@ -245,6 +253,8 @@ cudaError_t launch_blur_tc_rows(const BlurParams &bp, const float *in, float *tp
                                 uint16_t *hankel, unsigned int *err, int n_img, cudaStream_t s);
 cudaError_t launch_blur_tc_cols(const BlurParams &bp, const float *tp, const float *ts, float *out,
                                 const uint16_t *hankel, unsigned int *err, int n_img, cudaStream_t s);
+cudaError_t launch_rl(const RlParams &p, const float *d, float *ua, float *ub, float *norm,
+                      int n_img, int n_iter, float **result, cudaStream_t s);
 cudaError_t launch_dose(const ProjParams &p, const DoseParams &d, double *part,
                         unsigned long long *count, double *out, cudaStream_t s);
 int dose_blocks(const ProjParams &p);

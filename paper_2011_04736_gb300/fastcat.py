@@ -31,12 +31,13 @@ ENTRY_POINTS = ("fc_create", "fc_destroy", "fc_last_error", "fc_set_geometry", "
                 "fc_surrogate_grad", "fc_surrogate_get", "fc_surrogate_set", "fc_surrogate_eval",
                 "fc_energy_sum_lengths", "fc_cnr_grad", "fc_surrogate_project",
                 "fc_dose_estimate", "fc_fluence_for_dose", "fc_set_noise_order",
-                "fc_set_energy_groups")
+                "fc_set_energy_groups", "fc_deconvolve_rl")
 FC_STATIC_SCRATCH_FLOATS = 8 << 20
 FC_SURROGATE_PARAMS = 34305
 FC_SURROGATE_STATE = 34305 + 52 + 2 * 34305 + 1
 FC_K_NAMES = ("project", "blur_rows", "blur_cols", "fdk_filter", "backproject", "hu", "lengths",
-              "noise", "surrogate_eval", "surrogate_train", "energy_sum", "dose", "group_blur")
+              "noise", "surrogate_eval", "surrogate_train", "energy_sum", "dose", "group_blur",
+              "deconv")
 
 
 class FastcatError(RuntimeError):
@@ -117,6 +118,7 @@ def load():
         "fc_fluence_for_dose": (I, [P, ctypes.c_double, ctypes.c_double, P]),
         "fc_set_noise_order": (I, [P, I]),
         "fc_set_energy_groups": (I, [P, ctypes.POINTER(fc_energy_groups)]),
+        "fc_deconvolve_rl": (I, [P, I, I, ctypes.c_double, I, P, I, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -261,6 +263,13 @@ def fc_set_energy_groups(h, bin_end=(), psf_sigma_px=(), scatter_amp=(), scatter
         raise ValueError("all group arrays need n_groups entries")
     gs = fc_energy_groups(n, be.ctypes.data, *[a.ctypes.data for a in arr])
     return _check(load().fc_set_energy_groups(h, ctypes.byref(gs)))
+
+
+def fc_deconvolve_rl(h, angle_begin, angle_count, psf_sigma_px, n_iter, out=None, stream=None):
+    """Richardson-Lucy deconvolution of the handle's counts, in place."""
+    p, where = _ptr(out)
+    return _check(load().fc_deconvolve_rl(h, angle_begin, angle_count, float(psf_sigma_px),
+                                          int(n_iter), p, where, _stream(stream)))
 
 
 def fc_set_noise_order(h, order):
