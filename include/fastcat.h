@@ -183,6 +183,22 @@ int fc_set_noise_order(fc_handle *h, int order);
 int fc_deconvolve_rl(fc_handle *h, int angle_begin, int angle_count, double psf_sigma_px,
                      int n_iter, float *out, int out_where, void *stream);
 
+/* Detector MTF by the slanted-slit method (Sec. II.C): the detector PSF of
+ * the current model (the single optical-spread kernel, or each energy
+ * group's kernel weighted by the group's share of the flood, sum_E w D) is
+ * applied, clamp-to-edge, to a 192 x 192-pixel image of an ideal slit
+ * slit_width_mm wide tilted by slit_angle_deg (|angle| < 45) on the u-pitch
+ * grid; pixel values are the area fractions inside the slit.  The line spread
+ * function is presampled from rows 48 .. 143 on bins du / oversample wide
+ * over +-16 pixels (mean per bin); the MTF is its normalised Fourier
+ * magnitude at f = k / (32 du), k = 0 .. 16 oversample, written with the
+ * frequencies (1/mm) to host arrays of n_cap >= 16 oversample + 1 entries;
+ * *n_out receives the count.  Binary64, synchronous (default stream).
+ * Optical-spread sigmas above FC_MAX_GROUP_SIGMA_PX are refused.
+ * Errors: FC_ESTATE, FC_EINVAL, FC_ENOMEM, FC_ECUDA. */
+int fc_detector_mtf(fc_handle *h, double slit_width_mm, double slit_angle_deg, int oversample,
+                    double *freq_per_mm, double *mtf, int n_cap, int *n_out);
+
 #define FC_MAX_GROUPS 8
 #define FC_MAX_GROUP_SIGMA_PX 4.0
 typedef struct fc_energy_groups {

@@ -685,6 +685,68 @@ int fc_deconvolve_rl(fc_handle *h, int angle_begin, int angle_count, double psf_
     return copy_out(out, out_where, h->d_counts + off, bytes, s);
 }
 
+int fc_detector_mtf(fc_handle *h, double slit_width_mm, double slit_angle_deg, int oversample,
+                    double *freq_per_mm, double *mtf, int n_cap, int *n_out)
+{
+    if (!h || !freq_per_mm || !mtf || !n_out) return fail(FC_EINVAL, "fc_detector_mtf: null argument");
+    if (!h->has_geom || !h->has_spec) return fail(FC_ESTATE, "fc_detector_mtf: geometry and spectrum must be set");
+    if (!(slit_width_mm > 0) || !isfinite(slit_width_mm) || !(fabs(slit_angle_deg) < 45.0))
+        return fail(FC_EINVAL, "fc_detector_mtf: need slit width > 0 and |angle| < 45 degrees");
+    if (oversample < 1 || oversample > 16) return fail(FC_EINVAL, "fc_detector_mtf: oversample outside [1, 16]");
+    const int nb = 32 * oversample, nf = nb / 2 + 1;
+    if (n_cap < nf) return fail(FC_EINVAL, "fc_detector_mtf: need room for %d frequencies", nf);
+    fc::MtfParams p;
+    memset(&p, 0, sizeof(p));
+    p.n = 192;
+    p.pitch = h->g.du_cm;
+    p.width = slit_width_mm / 10.0;
+    p.ca = cos(slit_angle_deg * M_PI / 180.0);
+    p.sa = sin(slit_angle_deg * M_PI / 180.0);
+    p.nb = nb;
+    p.delta = p.pitch / oversample;
+    p.row0 = p.n / 4;
+    p.row1 = 3 * p.n / 4;
+    // PSF: each group's optical spread weighted by its share of the flood,
+    // or the single optical-spread kernel
+    const int ng = h->n_groups ? h->n_groups : 1;
+    double tot = 0.0;
+    int e0 = 0;
+    for (int g = 0; g < ng; ++g) {
+        const double sigma = h->n_groups ? h->grp_psf[g] : h->psf;
+        if (sigma > FC_MAX_GROUP_SIGMA_PX)
+            return fail(FC_EINVAL, "fc_detector_mtf: optical spread sigma %g above %g px", sigma,
+                        (double)FC_MAX_GROUP_SIGMA_PX);
+        const int e1 = h->n_groups ? h->grp_end[g] : h->n_e;
+        double c = 0.0;
+        for (int e = e0; e < e1; ++e) c += h->wd[e];
+        e0 = e1;
+        p.wgt[g] = c;
+        tot += c;
+        const int R = sigma > 0.0 ? (int)ceil(4.0 * sigma) : 0;
+        double sum = 0.0;
+        for (int j = -R; j <= R; ++j) {
+            p.taps[g][j + R] = R == 0 ? 1.0 : exp(-(double)j * j / (2.0 * sigma * sigma));
+            sum += p.taps[g][j + R];
+        }
+        for (int j = 0; j <= 2 * R; ++j) p.taps[g][j] /= sum;
+        p.r[g] = R;
+    }
+    for (int g = 0; g < ng; ++g) p.wgt[g] /= tot;
+    p.n_groups = ng;
+    DeviceGuard dgd(h->device);
+    double *work = nullptr;
+    const size_t nwork = 2 * (size_t)p.n * p.n + nb + 2 * (size_t)nf;
+    FC_CK(cudaMalloc((void **)&work, nwork * sizeof(double)));
+    double *fr = work + 2 * (size_t)p.n * p.n + nb, *mt = fr + nf;
+    cudaError_t e = fc::launch_mtf(p, work, fr, mt, 0);
+    if (e == cudaSuccess) e = cudaMemcpy(freq_per_mm, fr, nf * sizeof(double), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(mtf, mt, nf * sizeof(double), cudaMemcpyDeviceToHost);
+    cudaFree(work);
+    FC_CK(e);
+    *n_out = nf;
+    return FC_OK;
+}
+
 int fc_set_energy_groups(fc_handle *h, const fc_energy_groups *g)
 {
     if (!h || !g) return fail(FC_EINVAL, "fc_set_energy_groups: null argument");

@@ -66,6 +66,18 @@ struct RlParams {
     float floor_;                   // lower bound of H u before the division
 };
 
+// Slanted-slit detector MTF (fc_mtf.cu), binary64 throughout.
+struct MtfParams {
+    int n;                          // image size (pixels per side)
+    double pitch, width, ca, sa;    // cm, cm, slit normal (cos, sin)
+    int n_groups;
+    double wgt[FC_MAX_GROUPS];      // share of the flood per group, sum 1
+    int r[FC_MAX_GROUPS];
+    double taps[FC_MAX_GROUPS][2 * kMaxGroupR + 1];
+    int nb, row0, row1;             // presampling bins, rows used
+    double delta;                   // bin width, cm
+};
+
 // Final reduction of the dose estimate (Sec. II.H).
 constexpr int kDoseBlocks = 2048;            // most blocks of the per-bin partial sums
 constexpr double kGyGramPerKev = 1.602176634e-13;  // 1 keV per gram, in Gy
@@ -255,6 +267,7 @@ cudaError_t launch_blur_tc_cols(const BlurParams &bp, const float *tp, const flo
                                 const uint16_t *hankel, unsigned int *err, int n_img, cudaStream_t s);
 cudaError_t launch_rl(const RlParams &p, const float *d, float *ua, float *ub, float *norm,
                       int n_img, int n_iter, float **result, cudaStream_t s);
+cudaError_t launch_mtf(const MtfParams &p, double *work, double *freq, double *mtf, cudaStream_t s);
 cudaError_t launch_dose(const ProjParams &p, const DoseParams &d, double *part,
                         unsigned long long *count, double *out, cudaStream_t s);
 int dose_blocks(const ProjParams &p);

@@ -1,0 +1,124 @@
+// Detector MTF by the slanted-slit method (Sec. II.C): the detector PSF
+// (each energy group's optical spread weighted by the group's share of the
+// flood, or the single optical-spread kernel) is applied to an ideal slit
+// tilted across the pixel grid, the line spread function is presampled on a
+// grid d / os fine, and the MTF is its Fourier magnitude.  The problem is
+// small (a 192 x 192 image, 32 os bins), so every kernel works in binary64
+// and in a fixed order (results reproducible bit for bit).
+//   k_mtf_slit  area fraction of each pixel inside |n . (x - c)| <= w / 2
+//               (the pixel's distribution of n . x is the convolution of two
+//               uniforms of widths d |cos a| and d |sin a|: a trapezoid);
+//   k_mtf_blur  I = sum_g c_g G_g (x) S, clamp-to-edge sampled Gaussians;
+//   k_mtf_lsf   one thread per bin: mean of I over the pixels of rows
+//               [N/4, 3N/4) whose signed distance falls in the bin;
+//   k_mtf_dft   one thread per frequency k / (32 d), k = 0 .. 16 os.
+#include <math.h>
+
+#include "fc_internal.cuh"
+
+namespace fc {
+
+namespace {
+
+__device__ __forceinline__ int clampi(int i, int n) { return i < 0 ? 0 : (i > n - 1 ? n - 1 : i); }
+
+// CDF at t of the sum of two centred uniforms of widths a >= b >= 0.
+__device__ double trap_cdf(double t, double a, double b)
+{
+    if (b == 0.0) return fmin(fmax(__ddiv_rn(__dadd_rn(t, 0.5 * a), a), 0.0), 1.0);
+    double x = __dadd_rn(t, 0.5 * (a + b));
+    x = fmin(fmax(x, 0.0), a + b);
+    if (x <= b) return __ddiv_rn(__dmul_rn(x, x), 2.0 * a * b);
+    if (x <= a) return __ddiv_rn(__dsub_rn(x, 0.5 * b), a);
+    const double y = __dsub_rn(a + b, x);
+    return __dsub_rn(1.0, __ddiv_rn(__dmul_rn(y, y), 2.0 * a * b));
+}
+
+// signed distance of pixel (row i, column j) from the slit's centre line
+__device__ __forceinline__ double dist(const MtfParams &p, int i, int j)
+{
+    const double x = __dmul_rn((double)j - 0.5 * (p.n - 1), p.pitch);
+    const double y = __dmul_rn((double)i - 0.5 * (p.n - 1), p.pitch);
+    return __dadd_rn(__dmul_rn(x, p.ca), __dmul_rn(y, p.sa));
+}
+
+}  // namespace
+
+__global__ void k_mtf_slit(const __grid_constant__ MtfParams p, double *S)
+{
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= p.n * p.n) return;
+    const double s = dist(p, e / p.n, e % p.n);
+    const double a = p.pitch * fmax(fabs(p.ca), fabs(p.sa));
+    const double b = p.pitch * fmin(fabs(p.ca), fabs(p.sa));
+    S[e] = trap_cdf(__dadd_rn(-s, 0.5 * p.width), a, b) - trap_cdf(__dsub_rn(-s, 0.5 * p.width), a, b);
+}
+
+__global__ void k_mtf_blur(const __grid_constant__ MtfParams p, const double *S, double *I)
+{
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= p.n * p.n) return;
+    const int i = e / p.n, j = e % p.n;
+    double acc = 0.0;
+    for (int g = 0; g < p.n_groups; ++g) {
+        const int R = p.r[g];
+        double sg = 0.0;
+        for (int jv = -R; jv <= R; ++jv) {
+            const double *row = S + (size_t)clampi(i + jv, p.n) * p.n;
+            double sr = 0.0;
+            for (int ju = -R; ju <= R; ++ju) sr = fma(p.taps[g][ju + R], row[clampi(j + ju, p.n)], sr);
+            sg = fma(p.taps[g][jv + R], sr, sg);
+        }
+        acc = fma(p.wgt[g], sg, acc);
+    }
+    I[e] = acc;
+}
+
+__global__ void k_mtf_lsf(const __grid_constant__ MtfParams p, const double *I, double *lsf)
+{
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= p.nb) return;
+    double tot = 0.0;
+    int cnt = 0;
+    for (int i = p.row0; i < p.row1; ++i)
+        for (int j = 0; j < p.n; ++j) {
+            const double q = floor(__dadd_rn(__ddiv_rn(dist(p, i, j), p.delta), 0.5 * p.nb));
+            if (q == (double)b) {
+                tot += I[(size_t)i * p.n + j];
+                ++cnt;
+            }
+        }
+    lsf[b] = cnt ? tot / cnt : 0.0;
+}
+
+__global__ void k_mtf_dft(const __grid_constant__ MtfParams p, const double *lsf, double *freq,
+                          double *mtf)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k > p.nb / 2) return;
+    const double f = k / (p.nb * p.delta);           // 1/cm
+    double re = 0.0, im = 0.0, sum = 0.0;
+    for (int b = 0; b < p.nb; ++b) {
+        const double sb = (b - 0.5 * p.nb + 0.5) * p.delta;
+        double sn, cs;
+        sincospi(2.0 * f * sb, &sn, &cs);
+        re = fma(lsf[b], cs, re);
+        im = fma(-lsf[b], sn, im);
+        sum += lsf[b];
+    }
+    freq[k] = f / 10.0;
+    mtf[k] = sqrt(re * re + im * im) / fabs(sum);
+}
+
+cudaError_t launch_mtf(const MtfParams &p, double *work, double *freq, double *mtf, cudaStream_t s)
+{
+    const int np = p.n * p.n;
+    double *S = work, *I = work + np, *lsf = work + 2 * (size_t)np;
+    k_mtf_slit<<<(np + 255) / 256, 256, 0, s>>>(p, S);
+    k_mtf_blur<<<(np + 255) / 256, 256, 0, s>>>(p, S, I);
+    k_mtf_lsf<<<(p.nb + 63) / 64, 64, 0, s>>>(p, I, lsf);
+    k_mtf_dft<<<(p.nb / 2 + 1 + 63) / 64, 64, 0, s>>>(p, lsf, freq, mtf);
+    return cudaGetLastError();
+}
+
+}  // namespace fc

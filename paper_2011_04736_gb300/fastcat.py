@@ -31,7 +31,7 @@ ENTRY_POINTS = ("fc_create", "fc_destroy", "fc_last_error", "fc_set_geometry", "
                 "fc_surrogate_grad", "fc_surrogate_get", "fc_surrogate_set", "fc_surrogate_eval",
                 "fc_energy_sum_lengths", "fc_cnr_grad", "fc_surrogate_project",
                 "fc_dose_estimate", "fc_fluence_for_dose", "fc_set_noise_order",
-                "fc_set_energy_groups", "fc_deconvolve_rl")
+                "fc_set_energy_groups", "fc_deconvolve_rl", "fc_detector_mtf")
 FC_STATIC_SCRATCH_FLOATS = 8 << 20
 FC_SURROGATE_PARAMS = 34305
 FC_SURROGATE_STATE = 34305 + 52 + 2 * 34305 + 1
@@ -119,6 +119,7 @@ def load():
         "fc_set_noise_order": (I, [P, I]),
         "fc_set_energy_groups": (I, [P, ctypes.POINTER(fc_energy_groups)]),
         "fc_deconvolve_rl": (I, [P, I, I, ctypes.c_double, I, P, I, P]),
+        "fc_detector_mtf": (I, [P, ctypes.c_double, ctypes.c_double, I, P, P, I, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -270,6 +271,17 @@ def fc_deconvolve_rl(h, angle_begin, angle_count, psf_sigma_px, n_iter, out=None
     p, where = _ptr(out)
     return _check(load().fc_deconvolve_rl(h, angle_begin, angle_count, float(psf_sigma_px),
                                           int(n_iter), p, where, _stream(stream)))
+
+
+def fc_detector_mtf(h, slit_width_mm=0.3, slit_angle_deg=2.5, oversample=4):
+    """(frequencies in 1/mm, MTF) of the handle's detector model."""
+    cap = 16 * oversample + 1
+    f = np.zeros(cap)
+    m = np.zeros(cap)
+    n = ctypes.c_int()
+    _check(load().fc_detector_mtf(h, slit_width_mm, slit_angle_deg, oversample, f.ctypes.data,
+                                  m.ctypes.data, cap, ctypes.byref(n)))
+    return f[:n.value], m[:n.value]
 
 
 def fc_set_noise_order(h, order):
