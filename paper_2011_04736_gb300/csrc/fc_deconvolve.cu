@@ -55,12 +55,13 @@ __global__ void k_rl_norm(const __grid_constant__ RlParams p, float *norm)
     norm[i] = s;
 }
 
+template <int R>
 __global__ void __launch_bounds__(kThreads)
 k_rl_step(const __grid_constant__ RlParams p, const float *__restrict__ d,
           const float *__restrict__ uin, float *__restrict__ uout, const float *__restrict__ norm)
 {
     extern __shared__ float sm[];
-    const int R = p.R, nt = 2 * R + 1;
+    constexpr int nt = 2 * R + 1;
     const int WA = kTu + 4 * R, HA = kTv + 4 * R;   // su
     const int WB = kTu + 2 * R;                      // eu (HA rows), later t (kTv rows)
     const int HC = kTv + 2 * R, WC = kTu + 2 * R;    // e, then r
@@ -84,6 +85,7 @@ k_rl_step(const __grid_constant__ RlParams p, const float *__restrict__ d,
         const int r = i / WB, c = i % WB;
         const float *x = su + r * WA + c;
         float s = 0.0f;
+#pragma unroll
         for (int j = 0; j < nt; ++j) s = fmaf(g[j], x[j], s);
         sb[i] = s;
     }
@@ -94,6 +96,7 @@ k_rl_step(const __grid_constant__ RlParams p, const float *__restrict__ d,
         const int r = i / WC, c = i % WC;
         const float *x = sb + r * WB + c;
         float e = 0.0f;
+#pragma unroll
         for (int j = 0; j < nt; ++j) e = fmaf(g[j], x[j * WB], e);
         const int v = v0 - R + r, u = u0 - R + c;
         float ratio = 0.0f;
@@ -107,6 +110,7 @@ k_rl_step(const __grid_constant__ RlParams p, const float *__restrict__ d,
         const int q = i / WC, c = i % WC;
         const int vq = v0 + q;
         float s = 0.0f;
+#pragma unroll
         for (int j = 0; j < nt; ++j) s = fmaf(g[j], sc[(q + 2 * R - j) * WC + c], s);
         if (vq == 0)
             for (int k = 0; k < R; ++k) s = fmaf(p.cl[k], sc[(k + R) * WC + c], s);
@@ -122,6 +126,7 @@ k_rl_step(const __grid_constant__ RlParams p, const float *__restrict__ d,
         if (vq >= p.n_v || uq >= p.n_u) continue;
         const float *t = sb + q * WC;
         float s = 0.0f;
+#pragma unroll
         for (int j = 0; j < nt; ++j) s = fmaf(g[j], t[c + 2 * R - j], s);
         if (uq == 0)
             for (int k = 0; k < R; ++k) s = fmaf(p.cl[k], t[k + R], s);
@@ -139,8 +144,16 @@ cudaError_t launch_rl(const RlParams &p, const float *d, float *ua, float *ub, f
     if (n_img <= 0 || n_iter <= 0) return cudaSuccess;
     k_rl_norm<<<(p.n_u + p.n_v + 127) / 128, 128, 0, s>>>(p, norm);
     const size_t bytes = rl_smem_floats(p.R) * sizeof(float);
-    cudaError_t e = cudaFuncSetAttribute(k_rl_step, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)bytes);
+    void (*kern)(RlParams, const float *, const float *, float *, const float *) = nullptr;
+    switch (p.R) {
+#define FC_RL_CASE(r) case r: kern = k_rl_step<r>; break;
+        FC_RL_CASE(0) FC_RL_CASE(1) FC_RL_CASE(2) FC_RL_CASE(3) FC_RL_CASE(4) FC_RL_CASE(5)
+        FC_RL_CASE(6) FC_RL_CASE(7) FC_RL_CASE(8) FC_RL_CASE(9) FC_RL_CASE(10) FC_RL_CASE(11)
+        FC_RL_CASE(12) FC_RL_CASE(13) FC_RL_CASE(14) FC_RL_CASE(15) FC_RL_CASE(16)
+#undef FC_RL_CASE
+    default: return cudaErrorInvalidValue;
+    }
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     if (e != cudaSuccess) return e;
     const size_t plane = (size_t)p.n_u * p.n_v;
     const float *src = d;
@@ -149,8 +162,8 @@ cudaError_t launch_rl(const RlParams &p, const float *d, float *ua, float *ub, f
         for (int i0 = 0; i0 < n_img; i0 += 65535) {   // grid z limit
             const int n = n_img - i0 < 65535 ? n_img - i0 : 65535;
             dim3 grid((p.n_u + kTu - 1) / kTu, (p.n_v + kTv - 1) / kTv, n);
-            k_rl_step<<<grid, kThreads, bytes, s>>>(p, d + i0 * plane, src + i0 * plane,
-                                                    dst + i0 * plane, norm);
+            kern<<<grid, kThreads, bytes, s>>>(p, d + i0 * plane, src + i0 * plane,
+                                               dst + i0 * plane, norm);
         }
         src = dst;
         dst = dst == ua ? ub : ua;

@@ -11,6 +11,7 @@
 // group's tile (with a clamped halo of its radius) staged in shared memory,
 // separable row then column passes, the groups accumulated in registers.
 #include <math.h>
+#include <string.h>
 
 #include "fc_internal.cuh"
 
@@ -20,8 +21,6 @@ namespace {
 
 constexpr int kTu = 64, kTv = 32;                 // output tile (columns x rows)
 constexpr int kThreads = 256;                     // 64 columns x 4 row groups of 8
-constexpr int kInH = kTv + 2 * kMaxGroupR;
-constexpr int kInW = kTu + 2 * kMaxGroupR;
 
 __device__ __forceinline__ int clampi(int i, int n) { return i < 0 ? 0 : (i > n - 1 ? n - 1 : i); }
 
@@ -46,12 +45,16 @@ __global__ void k_group_profile(const __grid_constant__ GroupParams p, float *__
     prof[u] = p.n0 * acc;
 }
 
+// RM: the largest radius of the groups; every group's taps are read zero
+// padded to RM (p.tpad[g][j + RM]), so the tap loops unroll at compile time.
+template <int RM>
 __global__ void __launch_bounds__(kThreads)
 k_group_blur(const __grid_constant__ GroupParams p, const float *__restrict__ P,
              const float *__restrict__ prof, float *__restrict__ out)
 {
-    __shared__ float sin_[kInH][kInW + 1];
-    __shared__ float smid[kInH][kTu + 1];
+    constexpr int H = kTv + 2 * RM, Wd = kTu + 2 * RM, nt = 2 * RM + 1;
+    __shared__ float sin_[H][Wd + 1];
+    __shared__ float smid[H][kTu + 1];
     const int tid = threadIdx.x, tx = tid % kTu, ty = tid / kTu;
     const int u0 = blockIdx.x * kTu, v0 = blockIdx.y * kTv;
     const size_t img = (size_t)blockIdx.z * p.n_u * p.n_v;
@@ -59,22 +62,23 @@ k_group_blur(const __grid_constant__ GroupParams p, const float *__restrict__ P,
 #pragma unroll
     for (int o = 0; o < 8; ++o) acc[o] = 0.0f;
     for (int gi = 0; gi < p.n_groups; ++gi) {
-        const int R = p.r[gi], H = kTv + 2 * R, Wd = kTu + 2 * R, nt = 2 * R + 1;
         const float *src = P + (size_t)gi * p.grp_stride + img;
-        const float *tap = p.taps[gi];
+        const float *tap = p.tpad[gi];
         __syncthreads();
         for (int i = tid; i < H * Wd; i += kThreads) {
             const int r = i / Wd, c = i % Wd;
-            sin_[r][c] = __ldg(src + (size_t)clampi(v0 - R + r, p.n_v) * p.n_u + clampi(u0 - R + c, p.n_u));
+            sin_[r][c] = __ldg(src + (size_t)clampi(v0 - RM + r, p.n_v) * p.n_u + clampi(u0 - RM + c, p.n_u));
         }
         __syncthreads();
         for (int i = tid; i < H * kTu; i += kThreads) {
             const int r = i / kTu, c = i % kTu;
             float s = 0.0f;
+#pragma unroll
             for (int j = 0; j < nt; ++j) s = fmaf(tap[j], sin_[r][c + j], s);
             smid[r][c] = s;
         }
         __syncthreads();
+#pragma unroll
         for (int j = 0; j < nt; ++j) {
             const float t = tap[j];
 #pragma unroll
@@ -96,12 +100,27 @@ cudaError_t launch_group_blur(const GroupParams &g, const float *P, float *prof,
 {
     if (n_img <= 0) return cudaSuccess;
     k_group_profile<<<(g.n_u + 127) / 128, 128, 0, s>>>(g, prof);
+    int rm = 0;
+    for (int i = 0; i < g.n_groups; ++i) rm = g.r[i] > rm ? g.r[i] : rm;
+    GroupParams q = g;
+    memset(q.tpad, 0, sizeof(q.tpad));
+    for (int i = 0; i < g.n_groups; ++i)
+        for (int j = -g.r[i]; j <= g.r[i]; ++j) q.tpad[i][j + rm] = g.taps[i][j + g.r[i]];
+    void (*kern)(GroupParams, const float *, const float *, float *) = nullptr;
+    switch (rm) {
+#define FC_GB_CASE(r) case r: kern = k_group_blur<r>; break;
+        FC_GB_CASE(0) FC_GB_CASE(1) FC_GB_CASE(2) FC_GB_CASE(3) FC_GB_CASE(4) FC_GB_CASE(5)
+        FC_GB_CASE(6) FC_GB_CASE(7) FC_GB_CASE(8) FC_GB_CASE(9) FC_GB_CASE(10) FC_GB_CASE(11)
+        FC_GB_CASE(12) FC_GB_CASE(13) FC_GB_CASE(14) FC_GB_CASE(15) FC_GB_CASE(16)
+#undef FC_GB_CASE
+    default: return cudaErrorInvalidValue;
+    }
     const size_t plane = (size_t)g.n_u * g.n_v;
     for (int i0 = 0; i0 < n_img; i0 += 65535) {   // grid z limit
         const int n = n_img - i0 < 65535 ? n_img - i0 : 65535;
         const size_t off = (size_t)(angle0 + i0) * plane;
         dim3 grid((g.n_u + kTu - 1) / kTu, (g.n_v + kTv - 1) / kTv, n);
-        k_group_blur<<<grid, kThreads, 0, s>>>(g, P + off, prof, out + off);
+        kern<<<grid, kThreads, 0, s>>>(q, P + off, prof, out + off);
     }
     return cudaGetLastError();
 }

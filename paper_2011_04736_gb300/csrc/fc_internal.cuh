@@ -52,7 +52,8 @@ struct GroupParams {
     int n_u, n_v, n_groups;
     size_t grp_stride;              // elements between group planes of P
     int r[FC_MAX_GROUPS];
-    float taps[FC_MAX_GROUPS][2 * kMaxGroupR + 1];
+    float taps[FC_MAX_GROUPS][2 * kMaxGroupR + 1];   // index j + r[g]
+    float tpad[FC_MAX_GROUPS][2 * kMaxGroupR + 1];   // index j + max r (zero padded)
     float amp[FC_MAX_GROUPS], a_cm[FC_MAX_GROUPS], b[FC_MAX_GROUPS];
     float du, cu;                   // detector pitch (cm) and centre column
     float n0;
