@@ -53,6 +53,10 @@ struct DeviceGuard {
     }
 };
 
+// Padded filtered-projection row: one zero column before the detector row,
+// at least two after, rounded up to 16 bytes (tensor-map row stride).
+int fdk_row_pitch(int n_u) { return (n_u + 3 + 3) & ~3; }
+
 template <class T>
 void dfree(T *&p)
 {
@@ -218,7 +222,7 @@ int ensure_recon_buffers(fc_handle *h, cudaStream_t s)
     if (!h->d_filt) {
         int lo, hi;
         fc::fdk_row_range(h->dg, &lo, &hi);
-        h->filt_elems = (size_t)h->g.n_angles * (hi - lo + 1 + 3) * (h->g.n_u + 3);
+        h->filt_elems = (size_t)h->g.n_angles * (hi - lo + 1 + 3) * fdk_row_pitch(h->g.n_u);
         FC_CK(cudaMalloc((void **)&h->d_filt, h->filt_elems * sizeof(float)));
         FC_CK(cudaMemsetAsync(h->d_filt, 0, h->filt_elems * sizeof(float), s));
     }
@@ -983,7 +987,7 @@ int fc_reconstruct(fc_handle *h, const float *counts, int counts_where, double *
     p.mag = (float)(h->g.sad_cm / h->g.sdd_cm);
     p.scale = h->g.arc_rad / (2.0 * h->g.n_angles);
     fc::fdk_row_range(h->dg, &p.v_lo, &p.v_hi);
-    p.pw = h->g.n_u + 3;
+    p.pw = fdk_row_pitch(h->g.n_u);
     p.ph = p.v_hi - p.v_lo + 1 + 3;
     {
         Trace t(h, FC_K_FDK_FILTER, 1, s);
@@ -1010,6 +1014,7 @@ int fc_reconstruct(fc_handle *h, const float *counts, int counts_where, double *
         rc = copy_out(vol_hu, out_where, h->d_hu, h->vol_elems * sizeof(float), s);
         if (rc) return rc;
     }
+    if ((vol_mu || vol_hu) && out_where == FC_HOST) return check_blur_err(h, s, "fc_reconstruct");
     return FC_OK;
 }
 
@@ -1507,7 +1512,7 @@ int fc_cnr_grad(fc_handle *h, const double *logits, const double *D, const doubl
     pf.mag = (float)(h->g.sad_cm / h->g.sdd_cm);
     pf.scale = h->g.arc_rad / (2.0 * h->g.n_angles);
     fc::fdk_row_range(h->dg, &pf.v_lo, &pf.v_hi);
-    pf.pw = h->g.n_u + 3;
+    pf.pw = fdk_row_pitch(h->g.n_u);
     pf.ph = pf.v_hi - pf.v_lo + 1 + 3;
     fc::CnrParams cp;
     memset(&cp, 0, sizeof(cp));

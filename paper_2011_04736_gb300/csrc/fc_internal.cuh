@@ -145,7 +145,7 @@ struct FdkParams {
     float mag;              // SAD / SDD
     double scale;           // arc / (2 n_angles)
     int v_lo, v_hi;         // reachable detector rows
-    int pw, ph;             // padded row length n_u + 3, padded rows (v_hi - v_lo + 1) + 3
+    int pw, ph;             // padded row length (n_u + 3 rounded up to 4), padded rows (v_hi - v_lo + 1) + 3
 };
 
 void fdk_row_range(const DevGeom &g, int *v_lo, int *v_hi);
