@@ -15,7 +15,8 @@
 //   columns: one CTA per (projection, tile of TW columns); both row-pass
 //            results are staged with replicated halos, each thread produces
 //            8 adjacent outputs of one column, and the epilogue forms I.
-// Poisson counts are drawn by k_poisson, one thread per pixel.
+// Poisson counts are drawn by k_poisson (a round phase of first attempts and
+// a per-warp queue of the undecided draws).
 #include <math.h>
 
 #include "fc_internal.cuh"
@@ -235,47 +236,116 @@ cudaError_t launch_blur_cols(const BlurParams &p, const float *tp, const float *
     return cudaErrorInvalidValue;
 }
 
-// Each thread draws kPer pixels of one detector row (u = base + 32 s).  A
-// rejection draw takes a variable number of attempts, so instead of
-// finishing one pixel before the next (where every warp waits for its
-// slowest lane at each pixel), a lane that finishes a pixel starts its next
-// one in the same loop pass; a warp then runs about kPer * E[attempts] passes
-// plus the spread of the per-lane totals.  The draws themselves are exactly
-// those of noise::poisson.  lam and out may alias.
+// Each warp draws 32 * kPer pixels of one detector row (lane l: pixels
+// base + l + 32 s).  Most draws are decided by their first PTRS attempt's
+// squeeze; the final acceptance test (log P(k; lam)) is long and needed by
+// ~14% of attempts, so a warp that ran it whenever any lane needed it would
+// run it almost every pass with most lanes idle.  Instead:
+//   round phase  every lane takes its next pixel: the early exits (rate <= 0,
+//                > 1e7, < 10) or the first attempt's squeeze; undecided draws
+//                (final test pending, or rejected) go to a per-warp queue in
+//                shared memory with their state;
+//   drain phase  the warp takes the queue 32 items at a time, one per lane,
+//                and completes each draw (final test, further attempts).
+// Each draw performs exactly the operations of noise::poisson in the same
+// order, so the counts are those of the serial sampler.  A full queue (rare)
+// makes the lane complete its draw on the spot.  lam and out may alias.
 namespace {
 constexpr int kPer = 8;
-}
+constexpr int kQueue = 96;          // queued draws per warp
+constexpr int kWarps = 8;
 
-__global__ void __launch_bounds__(256)
+struct DrawQueue {
+    int iu[kQueue];
+    float lam[kQueue], b[kQueue], a[kQueue], vr[kQueue];
+    float kf[kQueue], us[kQueue], V[kQueue];
+    uint32_t jh[kQueue];            // attempt block j << 1 | word pair h; bit 31: final pending
+    uint32_t wz[kQueue], ww[kQueue];
+};
+}  // namespace
+
+__global__ void __launch_bounds__(32 * kWarps, 5)
 k_poisson(const float *lam, float *out, int n_v, int n_u, int angle0, uint64_t seed)
 {
+    __shared__ DrawQueue q_all[kWarps];
+    DrawQueue &q = q_all[threadIdx.y];
+    const int lane = threadIdx.x;
     const int iv = blockIdx.y * blockDim.y + threadIdx.y;
-    if (iv >= n_v) return;
+    if (iv >= n_v) return;                      // whole warps leave together
     const int k = blockIdx.z;
     const size_t row = ((size_t)k * n_v + iv) * n_u;
-    const int u_base = blockIdx.x * (32 * kPer) + threadIdx.x;
+    const int u_base = blockIdx.x * (32 * kPer) + lane;
     const uint32_t kabs = (uint32_t)(angle0 + k);
-    noise::Ptrs st;
-    int s = 0, cur = -1;
-    for (;;) {
-        while (cur < 0 && s < kPer) {
-            const int iu = u_base + 32 * s;
-            if (iu >= n_u) { s = kPer; break; }
+    const unsigned lt = (1u << lane) - 1u;
+    int count = 0;                              // warp-uniform
+    for (int sidx = 0; sidx < kPer; ++sidx) {
+        const int iu = u_base + 32 * sidx;
+        bool enq = false;
+        noise::Ptrs st;
+        float kf = 0.0f, us = 0.0f, V = 0.0f;
+        bool pending = false;
+        if (iu < n_u) {
             float r;
             if (noise::poisson_begin(lam[row + iu], (uint32_t)iu, (uint32_t)iv, kabs, seed, st, r)) {
                 out[row + iu] = r;
-                ++s;
             } else {
-                cur = iu;
+                const int o = noise::ptrs_quick(st, r, kf, us, V);
+                if (o == noise::kDone) {
+                    out[row + iu] = r;
+                } else {
+                    enq = true;
+                    pending = o == noise::kPending;
+                }
             }
         }
-        if (cur < 0) break;
-        float r;
-        if (noise::ptrs_attempt(st, r)) {
-            out[row + cur] = r;
-            cur = -1;
-            ++s;
+        const unsigned m = __ballot_sync(0xffffffffu, enq);
+        if (enq) {
+            const int pos = count + __popc(m & lt);
+            if (pos < kQueue) {
+                q.iu[pos] = iu;
+                q.lam[pos] = st.lam;
+                q.b[pos] = st.b;
+                q.a[pos] = st.a;
+                q.vr[pos] = st.vr;
+                q.kf[pos] = kf;
+                q.us[pos] = us;
+                q.V[pos] = V;
+                q.jh[pos] = (st.j << 1) | (uint32_t)st.h | (pending ? 0x80000000u : 0u);
+                q.wz[pos] = st.w.z;
+                q.ww[pos] = st.w.w;
+            } else {
+                // queue full: finish this draw here
+                float r;
+                bool done = pending ? noise::ptrs_final(st, kf, us, V, r) : false;
+                while (!done) done = noise::ptrs_attempt(st, r);
+                out[row + iu] = r;
+            }
         }
+        count = min(count + __popc(m), kQueue);
+    }
+    __syncwarp();
+    const uint2 key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
+    for (int i = lane; i < count; i += 32) {
+        noise::Ptrs st;
+        st.lam = q.lam[i];
+        st.b = q.b[i];
+        st.a = q.a[i];
+        st.vr = q.vr[i];
+        st.loglam = 0.0f;
+        st.invalpha = 0.0f;
+        st.have_slow = false;
+        st.iu = (uint32_t)q.iu[i];
+        st.iv = (uint32_t)iv;
+        st.k = kabs;
+        const uint32_t jh = q.jh[i];
+        st.j = (jh & 0x7fffffffu) >> 1;
+        st.h = (int)(jh & 1u);
+        st.key = key;
+        st.w = make_uint4(0u, 0u, q.wz[i], q.ww[i]);
+        float r;
+        bool done = (jh & 0x80000000u) ? noise::ptrs_final(st, q.kf[i], q.us[i], q.V[i], r) : false;
+        while (!done) done = noise::ptrs_attempt(st, r);
+        out[row + q.iu[i]] = r;
     }
 }
 
@@ -283,9 +353,9 @@ cudaError_t launch_poisson(const float *lam, float *out, int n_img, int n_v, int
                            uint64_t seed, cudaStream_t s)
 {
     if ((size_t)n_img * n_v * n_u == 0) return cudaSuccess;
-    if ((n_v + 7) / 8 > 65535 || n_img > 65535) return cudaErrorInvalidValue;
-    dim3 block(32, 8);
-    dim3 grid((n_u + 32 * kPer - 1) / (32 * kPer), (n_v + 7) / 8, n_img);
+    if ((n_v + kWarps - 1) / kWarps > 65535 || n_img > 65535) return cudaErrorInvalidValue;
+    dim3 block(32, kWarps);
+    dim3 grid((n_u + 32 * kPer - 1) / (32 * kPer), (n_v + kWarps - 1) / kWarps, n_img);
     k_poisson<<<grid, block, 0, s>>>(lam, out, n_v, n_u, angle0, seed);
     return cudaGetLastError();
 }
