@@ -613,7 +613,18 @@ static int run_groups(fc_handle *h, int a0, int na, cudaStream_t s)
     }
     if (!h->d_prof) FC_CK(cudaMalloc((void **)&h->d_prof, (size_t)h->g.n_u * sizeof(float)));
     p.n_groups = h->n_groups;
-    for (int i = 0; i < h->n_groups; ++i) p.grp_end[i] = h->grp_end[i];
+    for (int i = 0, e = 0; i < h->n_groups; ++i) {
+        p.grp_end[i] = h->grp_end[i];
+        // the binary32 compensated sum the kernel forms for an unattenuated ray
+        float sum = 0.0f, comp = 0.0f;
+        for (; e < h->grp_end[i]; ++e) {
+            const volatile float y = h->wd[e] - comp;
+            const volatile float t = sum + y;
+            comp = (t - sum) - y;
+            sum = t;
+        }
+        p.grp_flood[i] = sum;
+    }
     p.grp_stride = plane_all;
     {
         Trace t(h, FC_K_PROJECT, 1, s);

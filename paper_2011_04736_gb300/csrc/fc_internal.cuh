@@ -41,6 +41,7 @@ struct ProjParams {
     int n_mat, n_e;
     int n_groups;                   // energy-group output (k_project<kModeGroups>)
     int grp_end[FC_MAX_GROUPS];     // exclusive end bin of each group
+    float grp_flood[FC_MAX_GROUPS]; // compensated sum of wd over each group (rays that miss)
     size_t grp_stride;              // elements between group planes of the output
     float wd[kMaxBins];             // w D / sum(w D)
     float mu2[kMaxBins][kMaxMat];   // mu * log2(e), zero padded

@@ -268,17 +268,19 @@ k_project_groups(const __grid_constant__ ProjParams p, float *__restrict__ P)
     float L[kMaxMat];
     const bool hit = trace_ray(p, iu, iv, k, L);
     const size_t ray = ((size_t)k * g.n_v + iv) * g.n_u + iu;
+    if (!hit) {
+        // no attenuation: each group's share of the flood
+        for (int gi = 0; gi < p.n_groups; ++gi) P[(size_t)gi * p.grp_stride + ray] = p.grp_flood[gi];
+        return;
+    }
     int e = 0;
     for (int gi = 0; gi < p.n_groups; ++gi) {
         float sum = 0.0f, comp = 0.0f;
         for (const int e1 = p.grp_end[gi]; e < e1; ++e) {
-            float term = p.wd[e];
-            if (hit) {
-                float a = 0.0f;
+            float a = 0.0f;
 #pragma unroll
-                for (int m = 0; m < kMaxMat; ++m) a = fmaf(p.mu2[e][m], L[m], a);
-                term *= exp2f(-a);
-            }
+            for (int m = 0; m < kMaxMat; ++m) a = fmaf(p.mu2[e][m], L[m], a);
+            const float term = p.wd[e] * exp2f(-a);
             const float y = term - comp;
             const float t = sum + y;
             comp = (t - sum) - y;
