@@ -466,15 +466,37 @@ def _extra_deconv(fc, torch):
         sc.close()
 
 
+def _extra_mtf(fc, torch):
+    """Detector MTF by the slanted-slit method for the catphan_kv detector
+    (single kernel) and its four-group model."""
+    wl = W.WORKLOADS["catphan_kv"]
+    sc = fc.Scanner(wl, noise=False)
+    try:
+        out = {}
+        for name, grp in (("single_kernel", None), ("four_groups", W.energy_groups(wl, 4))):
+            if grp is not None:
+                fc.fc_set_energy_groups(sc.h, **grp)
+            fc.fc_detector_mtf(sc.h)
+            t0 = time.perf_counter()
+            f, m = fc.fc_detector_mtf(sc.h)
+            ms = (time.perf_counter() - t0) * 1e3
+            f50 = float(np.interp(0.5, m[::-1], f[::-1]))
+            out[name] = {"ms": ms, "f50_per_mm": f50, "mtf_at_1_per_mm": float(np.interp(1.0, f, m))}
+        return out
+    finally:
+        sc.close()
+
+
 def _extras(args, fc, torch):
     out = {}
     jobs = [("adjoint", lambda: _extra_adjoint(fc, torch)),
             ("dose", lambda: _extra_dose(fc, torch)),
             ("groups", lambda: _extra_groups(fc, torch)),
             ("deconv", lambda: _extra_deconv(fc, torch)),
+            ("mtf", lambda: _extra_mtf(fc, torch)),
             ("paper_timing", lambda: _extra_paper_timing(fc, torch)),
             ("paper_scale", lambda: _extra_paper_scale(fc, torch))]
-    if not args.no_surrogate:
+    if not args.no_surrogate and (not args.extra or "surrogate" in args.extra):
         from paper_2011_04736_gb300 import surrogate_study
 
         def sur():
@@ -484,6 +506,8 @@ def _extras(args, fc, torch):
                     "train": r["train"], "accuracy": r["accuracy"], "speed_ms": r["speed_ms"],
                     "crossover_bins": r["crossover_bins"]}
         jobs.append(("surrogate", sur))
+    if args.extra:
+        jobs = [j for j in jobs if j[0] in args.extra]
     for name, job in jobs:
         try:
             out[name] = job()
@@ -650,6 +674,9 @@ def main(argv=None):
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the adjoint, paper-scale and surrogate measurements")
     ap.add_argument("--no-surrogate", action="store_true")
+    ap.add_argument("--extra", action="append", default=[],
+                    help="run only these extras (repeatable): adjoint, dose, groups, deconv, mtf, "
+                         "paper_timing, paper_scale, surrogate")
     ap.add_argument("--surrogate-steps", type=int, default=20000)
     args = ap.parse_args(argv)
     if args.warmup < 3:

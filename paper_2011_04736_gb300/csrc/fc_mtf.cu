@@ -9,8 +9,8 @@
 //               (the pixel's distribution of n . x is the convolution of two
 //               uniforms of widths d |cos a| and d |sin a|: a trapezoid);
 //   k_mtf_blur  I = sum_g c_g G_g (x) S, clamp-to-edge sampled Gaussians;
-//   k_mtf_lsf   one thread per bin: mean of I over the pixels of rows
-//               [N/4, 3N/4) whose signed distance falls in the bin;
+//   k_mtf_bins  the presampling bin of every pixel of rows [N/4, 3N/4);
+//   k_mtf_lsf   one thread per bin: mean of I over that bin's pixels;
 //   k_mtf_dft   one thread per frequency k / (32 d), k = 0 .. 16 os.
 #include <math.h>
 
@@ -74,19 +74,30 @@ __global__ void k_mtf_blur(const __grid_constant__ MtfParams p, const double *S,
     I[e] = acc;
 }
 
-__global__ void k_mtf_lsf(const __grid_constant__ MtfParams p, const double *I, double *lsf)
+// bin of every pixel of rows [row0, row1) (-1 outside the bins)
+__global__ void k_mtf_bins(const __grid_constant__ MtfParams p, int *bins)
+{
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    const int nr = p.row1 - p.row0;
+    if (e >= nr * p.n) return;
+    const int i = p.row0 + e / p.n, j = e % p.n;
+    const double q = floor(__dadd_rn(__ddiv_rn(dist(p, i, j), p.delta), 0.5 * p.nb));
+    bins[e] = (q >= 0.0 && q < (double)p.nb) ? (int)q : -1;
+}
+
+// mean of I over each bin, pixels taken in row-major order
+__global__ void k_mtf_lsf(const __grid_constant__ MtfParams p, const double *I, const int *bins,
+                          double *lsf)
 {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= p.nb) return;
+    const int nr = p.row1 - p.row0;
     double tot = 0.0;
     int cnt = 0;
-    for (int i = p.row0; i < p.row1; ++i)
-        for (int j = 0; j < p.n; ++j) {
-            const double q = floor(__dadd_rn(__ddiv_rn(dist(p, i, j), p.delta), 0.5 * p.nb));
-            if (q == (double)b) {
-                tot += I[(size_t)i * p.n + j];
-                ++cnt;
-            }
+    for (int e = 0; e < nr * p.n; ++e)
+        if (bins[e] == b) {
+            tot += I[(size_t)(p.row0 + e / p.n) * p.n + e % p.n];
+            ++cnt;
         }
     lsf[b] = cnt ? tot / cnt : 0.0;
 }
@@ -114,9 +125,12 @@ cudaError_t launch_mtf(const MtfParams &p, double *work, double *freq, double *m
 {
     const int np = p.n * p.n;
     double *S = work, *I = work + np, *lsf = work + 2 * (size_t)np;
+    int *bins = reinterpret_cast<int *>(S);       // S is no longer needed after the blur
+    const int nb_px = (p.row1 - p.row0) * p.n;
     k_mtf_slit<<<(np + 255) / 256, 256, 0, s>>>(p, S);
     k_mtf_blur<<<(np + 255) / 256, 256, 0, s>>>(p, S, I);
-    k_mtf_lsf<<<(p.nb + 63) / 64, 64, 0, s>>>(p, I, lsf);
+    k_mtf_bins<<<(nb_px + 255) / 256, 256, 0, s>>>(p, bins);
+    k_mtf_lsf<<<(p.nb + 63) / 64, 64, 0, s>>>(p, I, bins, lsf);
     k_mtf_dft<<<(p.nb / 2 + 1 + 63) / 64, 64, 0, s>>>(p, lsf, freq, mtf);
     return cudaGetLastError();
 }
