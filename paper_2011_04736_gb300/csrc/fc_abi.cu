@@ -117,6 +117,7 @@ struct fc_handle {
     float *d_I = nullptr, *d_gI = nullptr, *d_gT = nullptr, *d_gtmp = nullptr, *d_gf = nullptr;
     float *d_gmu = nullptr;
     double *d_gwd = nullptr;
+    double *d_cnr_work = nullptr;   // CNR stage partials
     // learned surrogate of the energy integral
     bool has_sur = false, sur_fitted = false;
     int sur_step = 0;
@@ -151,6 +152,7 @@ struct fc_handle {
         dfree(d_part);
         dfree(d_flag);
         dfree(d_dose);
+        dfree(d_cnr_work);
         dfree(d_grp);
         dfree(d_prof);
         dfree(d_rlnorm);
@@ -1545,7 +1547,8 @@ int fc_cnr_grad(fc_handle *h, const double *logits, const double *D, const doubl
     FC_CK(fc::launch_noise_gauss(h->d_I, z, h->d_counts, np, s));
     FC_CK(fc::launch_fdk_filter(pf, h->d_counts, h->d_filt, s));
     FC_CK(fc::launch_backproject(pf, h->d_filt, h->d_vol, s));
-    FC_CK(fc::launch_cnr(cp, h->d_vol, h->d_gmu, h->d_gwd + fc::kMaxBins, s));
+    if (!h->d_cnr_work) FC_CK(cudaMalloc((void **)&h->d_cnr_work, fc::cnr_work_doubles() * sizeof(double)));
+    FC_CK(fc::launch_cnr(cp, h->d_vol, h->d_gmu, h->d_gwd + fc::kMaxBins, h->d_cnr_work, s));
     const bool grads = g_logits || g_D || g_rho;
     if (grads) {
         FC_CK(cudaMemsetAsync(h->d_gf, 0, h->filt_elems * sizeof(float), s));

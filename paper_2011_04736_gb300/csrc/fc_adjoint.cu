@@ -231,110 +231,202 @@ __global__ void k_noise_gauss(const float *__restrict__ I, const float *__restri
     }
 }
 
-// CNR objective and dJ/dmu (FP64, one CTA of 1024 threads).
-// ROI masks: water = centres within water_r of the axis; insert r = centres
-// within rois[r].radius of its centre; both on slices [zcut, nz - zcut).
-__global__ void __launch_bounds__(1024)
-k_cnr(const __grid_constant__ CnrParams c, const double *__restrict__ mu, float *__restrict__ gmu,
-      double *__restrict__ out)
+// CNR objective and dJ/dmu (FP64).  ROI masks: water = centres within
+// water_r of the axis; insert r = centres within rois[r].radius of its centre
+// (first match, water first); both on slices [zcut, nz - zcut).
+// Four grid-wide stages, each reduced per CTA into partials that every CTA
+// of the next stage folds in the same fixed order (reproducible bits):
+//   s1  count and sum of mu per region          -> mu_w, mean HU per region
+//   s2  sum of (HU - mean HU)^2 per region      -> variances, J, dJ/dHU terms
+//   s3  sum over regions of dJ/dHU_u mu_u        -> the mu_w correction
+//   s4  dJ/dmu per voxel; CTA 0 writes J
+namespace {
+constexpr int kCnrBlocks = 304;
+constexpr int kCnrThreads = 256;
+constexpr int kReg = kMaxRoi + 1;
+
+__device__ int cnr_region(const CnrParams &c, size_t i)
 {
-    __shared__ double red[1024];
-    __shared__ double stat[3 * (kMaxRoi + 1)];   // count, sum, sum of squares (HU)
-    __shared__ double gm[2 * (kMaxRoi + 1)];     // per-ROI gradient coefficients
-    __shared__ double mu_w_s, gsum_s;
     const DevGeom &g = c.g;
-    const int tid = threadIdx.x;
-    const size_t n = (size_t)g.nx * g.ny * g.nz;
-    auto roi_of = [&](size_t i) -> int {
-        const int ix = (int)(i % g.nx), iy = (int)((i / g.nx) % g.ny), iz = (int)(i / ((size_t)g.nx * g.ny));
-        if (iz < c.zcut || iz >= g.nz - c.zcut) return -1;
-        const double x = (ix - 0.5 * (g.nx - 1)) * (double)g.dx, y = (iy - 0.5 * (g.ny - 1)) * (double)g.dy;
-        if (x * x + y * y <= c.water_r * c.water_r) return 0;
-        for (int r = 0; r < c.n_roi; ++r) {
-            const double dx = x - c.cx[r], dy = y - c.cy[r];
-            if (dx * dx + dy * dy <= c.rad[r] * c.rad[r]) return r + 1;
-        }
-        return -1;
-    };
-    auto block_sum = [&](double v) -> double {
-        red[tid] = v;
-        __syncthreads();
-        for (int s = 512; s > 0; s >>= 1) {
-            if (tid < s) red[tid] += red[tid + s];
-            __syncthreads();
-        }
-        const double r = red[0];
-        __syncthreads();
-        return r;
-    };
-    // mu_w
-    double s = 0.0, cnt = 0.0;
-    for (size_t i = tid; i < n; i += blockDim.x)
-        if (roi_of(i) == 0) { s += mu[i]; cnt += 1.0; }
-    s = block_sum(s);
-    cnt = block_sum(cnt);
-    if (tid == 0) mu_w_s = s / cnt;
+    const int ix = (int)(i % g.nx), iy = (int)((i / g.nx) % g.ny), iz = (int)(i / ((size_t)g.nx * g.ny));
+    if (iz < c.zcut || iz >= g.nz - c.zcut) return -1;
+    const double x = (ix - 0.5 * (g.nx - 1)) * (double)g.dx, y = (iy - 0.5 * (g.ny - 1)) * (double)g.dy;
+    if (x * x + y * y <= c.water_r * c.water_r) return 0;
+    for (int r = 0; r < c.n_roi; ++r) {
+        const double dx = x - c.cx[r], dy = y - c.cy[r];
+        if (dx * dx + dy * dy <= c.rad[r] * c.rad[r]) return r + 1;
+    }
+    return -1;
+}
+
+// fixed-order block sum (tree over kCnrThreads)
+__device__ double cnr_block_sum(double v, double *red)
+{
+    red[threadIdx.x] = v;
     __syncthreads();
-    const double mu_w = mu_w_s;
-    // per-ROI HU statistics
-    for (int r = 0; r <= c.n_roi; ++r) {
-        double a = 0.0, b = 0.0, q = 0.0;
-        for (size_t i = tid; i < n; i += blockDim.x)
-            if (roi_of(i) == r) {
-                const double hu = 1000.0 * (mu[i] - mu_w) / mu_w;
-                a += 1.0;
-                b += hu;
-                q += hu * hu;
-            }
-        a = block_sum(a);
-        b = block_sum(b);
-        q = block_sum(q);
-        if (tid == 0) {
-            stat[3 * r] = a;
-            stat[3 * r + 1] = b / a;
-            stat[3 * r + 2] = q / a - (b / a) * (b / a);   // population variance
-        }
+    for (int s = kCnrThreads / 2; s > 0; s >>= 1) {
+        if ((int)threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
         __syncthreads();
     }
-    if (tid == 0) {
+    const double r = red[0];
+    __syncthreads();
+    return r;
+}
+
+struct CnrStats {
+    double cnt[kReg], mean_mu[kReg], mean_hu[kReg], var[kReg];
+    double mu_w;
+    double gm0[kReg], gm1[kReg];   // dJ/dHU_v = gm0[r] + gm1[r] (HU_v - mean_hu[r])
+    double J;
+};
+
+// totals of stage 1 (and 2 when part2 != nullptr), folded by the whole CTA in
+// a fixed order (thread t takes partials t, t + kCnrThreads, ...; then the
+// block tree), so every CTA obtains the same bits.  All threads call it.
+__device__ void cnr_fold(const CnrParams &c, const double *part1, const double *part2, CnrStats &t,
+                         double *red)
+{
+    const int nr = c.n_roi + 1;
+    for (int r = 0; r < nr; ++r) {
+        double n = 0.0, sm = 0.0;
+        for (int b = threadIdx.x; b < kCnrBlocks; b += kCnrThreads) {
+            n += part1[(size_t)b * 2 * kReg + r];
+            sm += part1[(size_t)b * 2 * kReg + kReg + r];
+        }
+        n = cnr_block_sum(n, red);
+        sm = cnr_block_sum(sm, red);
+        if (threadIdx.x == 0) {
+            t.cnt[r] = n;
+            t.mean_mu[r] = sm / n;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        t.mu_w = t.mean_mu[0];
+        for (int r = 0; r < nr; ++r) t.mean_hu[r] = 1000.0 * (t.mean_mu[r] - t.mu_w) / t.mu_w;
+    }
+    __syncthreads();
+    if (!part2) return;
+    for (int r = 0; r < nr; ++r) {
+        double q = 0.0;
+        for (int b = threadIdx.x; b < kCnrBlocks; b += kCnrThreads) q += part2[(size_t)b * kReg + r];
+        q = cnr_block_sum(q, red);
+        if (threadIdx.x == 0) t.var[r] = q / t.cnt[r];   // population variance
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
         double J = 0.0, cw_mean = 0.0, cw_dev = 0.0;
-        const double nw = stat[0], mw = stat[1], vw = stat[2];
-        for (int r = 1; r <= c.n_roi; ++r) {
-            const double nr = stat[3 * r], mr = stat[3 * r + 1], vr = stat[3 * r + 2];
+        const double nw = t.cnt[0], mw = t.mean_hu[0], vw = t.var[0];
+        // dCNR/dHU_v: water v: sgn/(nw sd) - |a|/sd^3 (HU_v - mw)/nw
+        //             insert v: -sgn/(nr sd) - |a|/sd^3 (HU_v - mr)/nr
+        for (int r = 1; r < nr; ++r) {
+            const double nrr = t.cnt[r], mr = t.mean_hu[r], vr = t.var[r];
             const double a = mw - mr, sd = sqrt(vw + vr), sgn = a >= 0.0 ? 1.0 : -1.0;
             J += fabs(a) / sd;
-            // dCNR/dHU_v: water v: sgn/(nw sd) - |a|/sd^3 (HU_v - mw)/nw
-            //             roi v:  -sgn/(nr sd) - |a|/sd^3 (HU_v - mr)/nr
             cw_mean += sgn / (nw * sd);
             cw_dev += -fabs(a) / (sd * sd * sd) / nw;
-            gm[2 * r] = -sgn / (nr * sd);
-            gm[2 * r + 1] = -fabs(a) / (sd * sd * sd) / nr;
+            t.gm0[r] = -sgn / (nrr * sd);
+            t.gm1[r] = -fabs(a) / (sd * sd * sd) / nrr;
         }
-        gm[0] = cw_mean;
-        gm[1] = cw_dev;
-        out[0] = J;
+        t.gm0[0] = cw_mean;
+        t.gm1[0] = cw_dev;
+        t.J = J;
     }
     __syncthreads();
-    // dJ/dHU_v, then through HU = 1000 (mu / mu_w - 1) with mu_w = mean_W mu
-    double gsum = 0.0;   // sum_u dJ/dHU_u mu_u
-    for (size_t i = tid; i < n; i += blockDim.x) {
-        const int r = roi_of(i);
+}
+}  // namespace
+
+__global__ void __launch_bounds__(kCnrThreads)
+k_cnr_s1(const __grid_constant__ CnrParams c, const double *__restrict__ mu, double *part1)
+{
+    __shared__ double red[kCnrThreads];
+    const size_t n = (size_t)c.g.nx * c.g.ny * c.g.nz;
+    double cnt[kReg], sm[kReg];
+#pragma unroll
+    for (int r = 0; r < kReg; ++r) cnt[r] = sm[r] = 0.0;
+    for (size_t i = (size_t)blockIdx.x * kCnrThreads + threadIdx.x; i < n; i += (size_t)kCnrBlocks * kCnrThreads) {
+        const int r = cnr_region(c, i);
+#pragma unroll
+        for (int rr = 0; rr < kReg; ++rr)
+            if (r == rr) { cnt[rr] += 1.0; sm[rr] += mu[i]; }
+    }
+    for (int r = 0; r < kReg; ++r) {
+        const double a = cnr_block_sum(cnt[r], red), b = cnr_block_sum(sm[r], red);
+        if (threadIdx.x == 0) {
+            part1[(size_t)blockIdx.x * 2 * kReg + r] = a;
+            part1[(size_t)blockIdx.x * 2 * kReg + kReg + r] = b;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kCnrThreads)
+k_cnr_s2(const __grid_constant__ CnrParams c, const double *__restrict__ mu, const double *part1,
+         double *part2)
+{
+    __shared__ double red[kCnrThreads];
+    __shared__ CnrStats t;
+    cnr_fold(c, part1, nullptr, t, red);
+    const size_t n = (size_t)c.g.nx * c.g.ny * c.g.nz;
+    double q[kReg];
+#pragma unroll
+    for (int r = 0; r < kReg; ++r) q[r] = 0.0;
+    for (size_t i = (size_t)blockIdx.x * kCnrThreads + threadIdx.x; i < n; i += (size_t)kCnrBlocks * kCnrThreads) {
+        const int r = cnr_region(c, i);
         if (r < 0) continue;
-        const double hu = 1000.0 * (mu[i] - mu_w) / mu_w;
-        const double gh = gm[2 * r] + gm[2 * r + 1] * (hu - stat[3 * r + 1]);
-        gsum += gh * mu[i];
+        const double hu = 1000.0 * (mu[i] - t.mu_w) / t.mu_w;
+#pragma unroll
+        for (int rr = 0; rr < kReg; ++rr)
+            if (r == rr) {
+                const double dv = hu - t.mean_hu[rr];
+                q[rr] += dv * dv;
+            }
     }
-    gsum = block_sum(gsum);
-    if (tid == 0) gsum_s = gsum;
-    __syncthreads();
-    const double corr = 1000.0 / (mu_w * mu_w) * gsum_s / stat[0];
-    for (size_t i = tid; i < n; i += blockDim.x) {
-        const int r = roi_of(i);
+    for (int r = 0; r < kReg; ++r) {
+        const double a = cnr_block_sum(q[r], red);
+        if (threadIdx.x == 0) part2[(size_t)blockIdx.x * kReg + r] = a;
+    }
+}
+
+__global__ void __launch_bounds__(kCnrThreads)
+k_cnr_s3(const __grid_constant__ CnrParams c, const double *__restrict__ mu, const double *part1,
+         const double *part2, double *part3)
+{
+    __shared__ double red[kCnrThreads];
+    __shared__ CnrStats t;
+    cnr_fold(c, part1, part2, t, red);
+    const size_t n = (size_t)c.g.nx * c.g.ny * c.g.nz;
+    double gs = 0.0;   // sum_u dJ/dHU_u mu_u
+    for (size_t i = (size_t)blockIdx.x * kCnrThreads + threadIdx.x; i < n; i += (size_t)kCnrBlocks * kCnrThreads) {
+        const int r = cnr_region(c, i);
+        if (r < 0) continue;
+        const double hu = 1000.0 * (mu[i] - t.mu_w) / t.mu_w;
+        gs += (t.gm0[r] + t.gm1[r] * (hu - t.mean_hu[r])) * mu[i];
+    }
+    gs = cnr_block_sum(gs, red);
+    if (threadIdx.x == 0) part3[blockIdx.x] = gs;
+}
+
+// dJ/dmu through HU = 1000 (mu / mu_w - 1), mu_w = mean over the water region
+__global__ void __launch_bounds__(kCnrThreads)
+k_cnr_s4(const __grid_constant__ CnrParams c, const double *__restrict__ mu, const double *part1,
+         const double *part2, const double *part3, float *__restrict__ gmu, double *out)
+{
+    __shared__ double red[kCnrThreads];
+    __shared__ CnrStats t;
+    cnr_fold(c, part1, part2, t, red);
+    double gs = 0.0;
+    for (int b = threadIdx.x; b < kCnrBlocks; b += kCnrThreads) gs += part3[b];
+    gs = cnr_block_sum(gs, red);
+    const double corr = 1000.0 / (t.mu_w * t.mu_w) * gs / t.cnt[0];
+    if (blockIdx.x == 0 && threadIdx.x == 0) out[0] = t.J;
+    const size_t n = (size_t)c.g.nx * c.g.ny * c.g.nz;
+    for (size_t i = (size_t)blockIdx.x * kCnrThreads + threadIdx.x; i < n; i += (size_t)kCnrBlocks * kCnrThreads) {
+        const int r = cnr_region(c, i);
         double v = 0.0;
         if (r >= 0) {
-            const double hu = 1000.0 * (mu[i] - mu_w) / mu_w;
-            const double gh = gm[2 * r] + gm[2 * r + 1] * (hu - stat[3 * r + 1]);
-            v = 1000.0 / mu_w * gh - (r == 0 ? corr : 0.0);
+            const double hu = 1000.0 * (mu[i] - t.mu_w) / t.mu_w;
+            const double gh = t.gm0[r] + t.gm1[r] * (hu - t.mean_hu[r]);
+            v = 1000.0 / t.mu_w * gh - (r == 0 ? corr : 0.0);
         }
         gmu[i] = (float)v;
     }
@@ -480,9 +572,16 @@ cudaError_t launch_noise_gauss(const float *I, const float *z, float *K, size_t 
     return cudaGetLastError();
 }
 
-cudaError_t launch_cnr(const CnrParams &c, const double *mu, float *gmu, double *out, cudaStream_t s)
+size_t cnr_work_doubles() { return (size_t)kCnrBlocks * (3 * kReg + 1); }
+
+cudaError_t launch_cnr(const CnrParams &c, const double *mu, float *gmu, double *out, double *work,
+                       cudaStream_t s)
 {
-    k_cnr<<<1, 1024, 0, s>>>(c, mu, gmu, out);
+    double *p1 = work, *p2 = p1 + (size_t)kCnrBlocks * 2 * kReg, *p3 = p2 + (size_t)kCnrBlocks * kReg;
+    k_cnr_s1<<<kCnrBlocks, kCnrThreads, 0, s>>>(c, mu, p1);
+    k_cnr_s2<<<kCnrBlocks, kCnrThreads, 0, s>>>(c, mu, p1, p2);
+    k_cnr_s3<<<kCnrBlocks, kCnrThreads, 0, s>>>(c, mu, p1, p2, p3);
+    k_cnr_s4<<<kCnrBlocks, kCnrThreads, 0, s>>>(c, mu, p1, p2, p3, gmu, out);
     return cudaGetLastError();
 }
 

@@ -236,8 +236,9 @@ cudaError_t launch_project_density(const AdjParams &p, const float *rho, float *
 cudaError_t launch_project_density_adjoint(const AdjParams &p, const float *rho, const float *gT,
                                            float *grho, double *gwd, cudaStream_t s);
 cudaError_t launch_noise_gauss(const float *I, const float *z, float *K, size_t n, cudaStream_t s);
-cudaError_t launch_cnr(const CnrParams &c, const double *mu, float *gmu, double *out,
+cudaError_t launch_cnr(const CnrParams &c, const double *mu, float *gmu, double *out, double *work,
                        cudaStream_t s);
+size_t cnr_work_doubles();
 cudaError_t launch_backproject_adjoint(const FdkParams &p, const float *gmu, float *gf,
                                        cudaStream_t s);
 cudaError_t launch_filter_adjoint(const FdkParams &p, const float *gf, const float *I,
