@@ -822,7 +822,7 @@ int fc_project(fc_handle *h, int angle_begin, int angle_count, int out_kind, flo
         if (h->noise_order == FC_NOISE_BEFORE_PSF)
             return fail(FC_EINVAL, "fc_project: noise before the optical spread is not defined for energy groups");
     } else {
-        Trace t(h, FC_K_PROJECT, 1, s);
+        Trace t(h, FC_K_PROJECT, fc::project_launches(p), s);
         FC_CK(fc::launch_project(p, h->d_T, nullptr, s));
         t.end();
     }

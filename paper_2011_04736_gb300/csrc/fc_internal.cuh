@@ -248,6 +248,7 @@ cudaError_t launch_blur_adjoint(const BlurParams &b, int n_img, const float *gI,
 
 // launchers (return cudaError_t of the launch)
 cudaError_t launch_project(const ProjParams &p, float *T, float *L_out, cudaStream_t s);
+int project_launches(const ProjParams &p);
 cudaError_t launch_project_groups(const ProjParams &p, float *P, cudaStream_t s);
 cudaError_t launch_group_blur(const GroupParams &g, const float *P, float *prof, float *out,
                               int angle0, int n_img, cudaStream_t s);

@@ -206,11 +206,11 @@ __device__ __forceinline__ bool trace_ray(const ProjParams &p, int iu, int iv, i
 
 template <bool EMIT_L>
 __global__ void __launch_bounds__(256)
-k_project(const __grid_constant__ ProjParams p, float *__restrict__ T, float *__restrict__ Lout)
+k_project(const __grid_constant__ ProjParams p, float *__restrict__ T, float *__restrict__ Lout, int row0)
 {
     const DevGeom &g = p.g;
     const int iu = blockIdx.x * 32 + threadIdx.x;
-    const int iv = blockIdx.y * blockDim.y + threadIdx.y;
+    const int iv = row0 + blockIdx.y * blockDim.y + threadIdx.y;
     const int kl = blockIdx.z;
     if (iu >= g.n_u || iv >= g.n_v) return;
     const int k = p.angle0 + kl;
@@ -241,15 +241,78 @@ k_project(const __grid_constant__ ProjParams p, float *__restrict__ T, float *__
     T[((size_t)k * g.n_v + iv) * g.n_u + iu] = Tv;
 }
 
+// T = 1 on the rows outside [r0, r1) of projection angle0 + blockIdx.y (VEC:
+// four floats per store): rays of those rows cannot meet the voxel slab.
+// Per projection the filled elements are [0, r0 n_u) and [r1 n_u, n_v n_u).
+template <bool VEC>
+__global__ void __launch_bounds__(256)
+k_fill_miss_rows(float *__restrict__ T, int n_u, int n_v, int angle0, int r0, int r1)
+{
+    const int w = VEC ? 4 : 1;
+    const size_t lo = (size_t)r0 * n_u / w, hs = (size_t)r1 * n_u / w, end = (size_t)n_v * n_u / w;
+    const size_t n_fill = lo + (end - hs);
+    const size_t base = (size_t)(angle0 + blockIdx.y) * n_v * n_u / w;
+    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n_fill;
+         e += (size_t)gridDim.x * blockDim.x) {
+        const size_t i = base + (e < lo ? e : hs + (e - lo));
+        if (VEC)
+            reinterpret_cast<float4 *>(T)[i] = make_float4(1.0f, 1.0f, 1.0f, 1.0f);
+        else
+            T[i] = 1.0f;
+    }
+}
+
+// Traced band [r0, r1) of 8-row blocks holding the rows in [v_hit_lo, v_hit_hi]
+// (r0 = r1 = 0 when no row can meet the slab).
+static void project_band(const ProjParams &p, int &r0, int &r1)
+{
+    const int n_v = p.g.n_v;
+    const int lo = max(p.v_hit_lo, 0), hi = min(p.v_hit_hi, n_v - 1);
+    r0 = r1 = 0;
+    if (lo <= hi) {
+        r0 = lo / 8 * 8;
+        r1 = min((hi / 8 + 1) * 8, n_v);
+    }
+}
+
+// Kernels launch_project starts for a T output: the traced band and the fill.
+int project_launches(const ProjParams &p)
+{
+    if (p.n_angles_launch <= 0) return 0;
+    int r0, r1;
+    project_band(p, r0, r1);
+    return (r1 > r0) + (r1 - r0 < p.g.n_v);
+}
+
 cudaError_t launch_project(const ProjParams &p, float *T, float *L_out, cudaStream_t s)
 {
     if (p.n_angles_launch <= 0) return cudaSuccess;
     dim3 block(32, 8);
-    dim3 grid((p.g.n_u + 31) / 32, (p.g.n_v + 7) / 8, p.n_angles_launch);
-    if (L_out)
-        k_project<true><<<grid, block, 0, s>>>(p, T, L_out);
-    else
-        k_project<false><<<grid, block, 0, s>>>(p, T, L_out);
+    if (L_out) {
+        dim3 grid((p.g.n_u + 31) / 32, (p.g.n_v + 7) / 8, p.n_angles_launch);
+        k_project<true><<<grid, block, 0, s>>>(p, T, L_out, 0);
+        return cudaGetLastError();
+    }
+    // Only the 8-row blocks that hold rows in [v_hit_lo, v_hit_hi] are traced;
+    // the other rows are filled with T = 1 by a store-only kernel.
+    const int n_v = p.g.n_v, n_u = p.g.n_u;
+    int r0, r1;
+    project_band(p, r0, r1);
+    if (r1 > r0) {
+        dim3 grid((n_u + 31) / 32, (r1 - r0 + 7) / 8, p.n_angles_launch);
+        k_project<false><<<grid, block, 0, s>>>(p, T, nullptr, r0);
+    }
+    const size_t n_fill = (size_t)(n_v - (r1 - r0)) * n_u;
+    if (n_fill) {
+        const bool vec = n_u % 4 == 0 && reinterpret_cast<uintptr_t>(T) % 16 == 0;
+        const size_t per = vec ? n_fill / 4 : n_fill;
+        const size_t want = (per + 256 * 8 - 1) / (256 * 8);
+        dim3 grid((unsigned)(want < 1024 ? want : 1024), p.n_angles_launch);
+        if (vec)
+            k_fill_miss_rows<true><<<grid, 256, 0, s>>>(T, n_u, n_v, p.angle0, r0, r1);
+        else
+            k_fill_miss_rows<false><<<grid, 256, 0, s>>>(T, n_u, n_v, p.angle0, r0, r1);
+    }
     return cudaGetLastError();
 }
 
