@@ -629,7 +629,7 @@ static int run_groups(fc_handle *h, int a0, int na, cudaStream_t s)
     }
     p.grp_stride = plane_all;
     {
-        Trace t(h, FC_K_PROJECT, 1, s);
+        Trace t(h, FC_K_PROJECT, fc::project_launches(p), s);
         FC_CK(fc::launch_project_groups(p, h->d_grp, s));
         t.end();
     }

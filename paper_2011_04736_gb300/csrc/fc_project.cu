@@ -241,25 +241,53 @@ k_project(const __grid_constant__ ProjParams p, float *__restrict__ T, float *__
     T[((size_t)k * g.n_v + iv) * g.n_u + iu] = Tv;
 }
 
-// T = 1 on the rows outside [r0, r1) of projection angle0 + blockIdx.y (VEC:
-// four floats per store): rays of those rows cannot meet the voxel slab.
-// Per projection the filled elements are [0, r0 n_u) and [r1 n_u, n_v n_u).
+// Value planes of the rows outside the traced band: plane z starts at
+// z * stride elements and is filled with v[z].
+struct FillPlanes {
+    float v[FC_MAX_GROUPS];
+    size_t stride;
+};
+
+// Rows outside [r0, r1) of projection angle0 + blockIdx.y in plane blockIdx.z
+// (VEC: four floats per store) get the value of a ray that misses the voxel
+// slab.  Per projection the filled elements are [0, r0 n_u) and
+// [r1 n_u, n_v n_u).
 template <bool VEC>
 __global__ void __launch_bounds__(256)
-k_fill_miss_rows(float *__restrict__ T, int n_u, int n_v, int angle0, int r0, int r1)
+k_fill_miss_rows(float *__restrict__ T, int n_u, int n_v, int angle0, int r0, int r1,
+                 const __grid_constant__ FillPlanes f)
 {
     const int w = VEC ? 4 : 1;
     const size_t lo = (size_t)r0 * n_u / w, hs = (size_t)r1 * n_u / w, end = (size_t)n_v * n_u / w;
     const size_t n_fill = lo + (end - hs);
-    const size_t base = (size_t)(angle0 + blockIdx.y) * n_v * n_u / w;
+    const size_t base = (blockIdx.z * f.stride + (size_t)(angle0 + blockIdx.y) * n_v * n_u) / w;
+    const float v = f.v[blockIdx.z];
     for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n_fill;
          e += (size_t)gridDim.x * blockDim.x) {
         const size_t i = base + (e < lo ? e : hs + (e - lo));
         if (VEC)
-            reinterpret_cast<float4 *>(T)[i] = make_float4(1.0f, 1.0f, 1.0f, 1.0f);
+            reinterpret_cast<float4 *>(T)[i] = make_float4(v, v, v, v);
         else
-            T[i] = 1.0f;
+            T[i] = v;
     }
+}
+
+static cudaError_t launch_fill(const ProjParams &p, float *T, int r0, int r1, const FillPlanes &f,
+                               int n_planes, cudaStream_t s)
+{
+    const int n_v = p.g.n_v, n_u = p.g.n_u;
+    const size_t n_fill = (size_t)(n_v - (r1 - r0)) * n_u;
+    if (!n_fill || n_planes <= 0) return cudaSuccess;
+    const bool vec = n_u % 4 == 0 && reinterpret_cast<uintptr_t>(T) % 16 == 0 &&
+                     (n_planes == 1 || f.stride % 4 == 0);
+    const size_t per = vec ? n_fill / 4 : n_fill;
+    const size_t want = (per + 256 * 8 - 1) / (256 * 8);
+    dim3 grid((unsigned)(want < 1024 ? want : 1024), p.n_angles_launch, n_planes);
+    if (vec)
+        k_fill_miss_rows<true><<<grid, 256, 0, s>>>(T, n_u, n_v, p.angle0, r0, r1, f);
+    else
+        k_fill_miss_rows<false><<<grid, 256, 0, s>>>(T, n_u, n_v, p.angle0, r0, r1, f);
+    return cudaGetLastError();
 }
 
 // Traced band [r0, r1) of 8-row blocks holding the rows in [v_hit_lo, v_hit_hi]
@@ -275,7 +303,8 @@ static void project_band(const ProjParams &p, int &r0, int &r1)
     }
 }
 
-// Kernels launch_project starts for a T output: the traced band and the fill.
+// Kernels launch_project (T output) or launch_project_groups starts: the
+// traced band and the fill.
 int project_launches(const ProjParams &p)
 {
     if (p.n_angles_launch <= 0) return 0;
@@ -295,25 +324,16 @@ cudaError_t launch_project(const ProjParams &p, float *T, float *L_out, cudaStre
     }
     // Only the 8-row blocks that hold rows in [v_hit_lo, v_hit_hi] are traced;
     // the other rows are filled with T = 1 by a store-only kernel.
-    const int n_v = p.g.n_v, n_u = p.g.n_u;
     int r0, r1;
     project_band(p, r0, r1);
     if (r1 > r0) {
-        dim3 grid((n_u + 31) / 32, (r1 - r0 + 7) / 8, p.n_angles_launch);
+        dim3 grid((p.g.n_u + 31) / 32, (r1 - r0 + 7) / 8, p.n_angles_launch);
         k_project<false><<<grid, block, 0, s>>>(p, T, nullptr, r0);
     }
-    const size_t n_fill = (size_t)(n_v - (r1 - r0)) * n_u;
-    if (n_fill) {
-        const bool vec = n_u % 4 == 0 && reinterpret_cast<uintptr_t>(T) % 16 == 0;
-        const size_t per = vec ? n_fill / 4 : n_fill;
-        const size_t want = (per + 256 * 8 - 1) / (256 * 8);
-        dim3 grid((unsigned)(want < 1024 ? want : 1024), p.n_angles_launch);
-        if (vec)
-            k_fill_miss_rows<true><<<grid, 256, 0, s>>>(T, n_u, n_v, p.angle0, r0, r1);
-        else
-            k_fill_miss_rows<false><<<grid, 256, 0, s>>>(T, n_u, n_v, p.angle0, r0, r1);
-    }
-    return cudaGetLastError();
+    FillPlanes f{};
+    f.v[0] = 1.0f;
+    f.stride = 0;
+    return launch_fill(p, T, r0, r1, f, 1, s);
 }
 
 // Energy-group primaries (the I_f equation of Sec. II.F split over groups of
@@ -321,11 +341,11 @@ cudaError_t launch_project(const ProjParams &p, float *T, float *L_out, cudaStre
 // a compensated sum per group, written to P + g * grp_stride at the ray's
 // absolute position.  Rays that miss the volume give P_g = sum_{E in g} wD.
 __global__ void __launch_bounds__(256)
-k_project_groups(const __grid_constant__ ProjParams p, float *__restrict__ P)
+k_project_groups(const __grid_constant__ ProjParams p, float *__restrict__ P, int row0)
 {
     const DevGeom &g = p.g;
     const int iu = blockIdx.x * 32 + threadIdx.x;
-    const int iv = blockIdx.y * blockDim.y + threadIdx.y;
+    const int iv = row0 + blockIdx.y * blockDim.y + threadIdx.y;
     if (iu >= g.n_u || iv >= g.n_v) return;
     const int k = p.angle0 + blockIdx.z;
     float L[kMaxMat];
@@ -357,14 +377,22 @@ cudaError_t launch_project_groups(const ProjParams &p, float *P, cudaStream_t s)
 {
     if (p.n_angles_launch <= 0) return cudaSuccess;
     dim3 block(32, 8);
-    dim3 grid((p.g.n_u + 31) / 32, (p.g.n_v + 7) / 8, p.n_angles_launch);
-    k_project_groups<<<grid, block, 0, s>>>(p, P);
-    return cudaGetLastError();
+    int r0, r1;
+    project_band(p, r0, r1);
+    if (r1 > r0) {
+        dim3 grid((p.g.n_u + 31) / 32, (r1 - r0 + 7) / 8, p.n_angles_launch);
+        k_project_groups<<<grid, block, 0, s>>>(p, P, r0);
+    }
+    FillPlanes f{};
+    for (int gi = 0; gi < p.n_groups; ++gi) f.v[gi] = p.grp_flood[gi];
+    f.stride = p.grp_stride;
+    return launch_fill(p, P, r0, r1, f, p.n_groups, s);
 }
 
 // Dose estimate, Sec. II.H: for every energy bin E, the sum over the rays of
 // the fraction a ray loses in the phantom, 1 - exp(-sum_m mu_m(E) L_m).
-// Blocks walk 32 x 8 pixel tiles in a fixed order; each warp traces its row
+// Rays outside the rows [r0, r1) cannot meet the voxel slab and lose nothing,
+// so only that band is visited.  Blocks walk 32 x 8 pixel tiles in a fixed order; each warp traces its row
 // of 32 rays, stages their path lengths in its own shared slice and then sums
 // bins lane, lane + 32, ... over those 32 rays (warp-synchronous: no block
 // barrier inside the loop, so a warp with long rays holds up no other).  The
@@ -374,13 +402,13 @@ static_assert(kMaxMat == 8 && kMaxBins <= 256, "dose kernel: two float4 per ray,
 
 template <int NQ>
 __global__ void __launch_bounds__(256)
-k_dose_partial(const __grid_constant__ ProjParams p, double *__restrict__ part)
+k_dose_partial(const __grid_constant__ ProjParams p, double *__restrict__ part, int r0, int r1)
 {
     __shared__ float4 sL[8][32][2];
     __shared__ double red[8][kMaxBins];
     const DevGeom &g = p.g;
     const int lane = threadIdx.x, w = threadIdx.y;
-    const int tu = (g.n_u + 31) / 32, tv = (g.n_v + 7) / 8;
+    const int tu = (g.n_u + 31) / 32, tv = (r1 - r0 + 7) / 8;
     const long long n_tiles = (long long)tu * tv * p.n_angles_launch;
     double acc[NQ];
 #pragma unroll
@@ -388,9 +416,9 @@ k_dose_partial(const __grid_constant__ ProjParams p, double *__restrict__ part)
     for (long long t = blockIdx.x; t < n_tiles; t += gridDim.x) {
         const int bu = (int)(t % tu), bv = (int)((t / tu) % tv);
         const int kl = (int)(t / ((long long)tu * tv));
-        const int iu = bu * 32 + lane, iv = bv * 8 + w;
+        const int iu = bu * 32 + lane, iv = r0 + bv * 8 + w;
         float L[kMaxMat];
-        if (iu < g.n_u && iv < g.n_v) {
+        if (iu < g.n_u && iv < r1) {
             trace_ray(p, iu, iv, p.angle0 + kl, L);
         } else {
 #pragma unroll
@@ -504,7 +532,10 @@ static int dose_grid(long long tiles)
 
 int dose_blocks(const ProjParams &p)
 {
-    const long long tiles = (long long)((p.g.n_u + 31) / 32) * ((p.g.n_v + 7) / 8) * p.n_angles_launch;
+    int r0, r1;
+    project_band(p, r0, r1);
+    long long tiles = (long long)((p.g.n_u + 31) / 32) * ((r1 - r0 + 7) / 8) * p.n_angles_launch;
+    tiles = tiles > 0 ? tiles : 1;   // one block writes zero partials
     if (p.n_e <= 32) return dose_grid<1>(tiles);
     if (p.n_e <= 64) return dose_grid<2>(tiles);
     if (p.n_e <= 128) return dose_grid<4>(tiles);
@@ -519,14 +550,16 @@ cudaError_t launch_dose(const ProjParams &p, const DoseParams &d, double *part,
     if (e != cudaSuccess) return e;
     k_label_count<<<152 * 4, 256, 0, s>>>(p.labels, nvox, d.n_mat, count);
     const dim3 blk(32, 8);
+    int r0, r1;
+    project_band(p, r0, r1);
     if (d.n_e <= 32)
-        k_dose_partial<1><<<d.n_part, blk, 0, s>>>(p, part);
+        k_dose_partial<1><<<d.n_part, blk, 0, s>>>(p, part, r0, r1);
     else if (d.n_e <= 64)
-        k_dose_partial<2><<<d.n_part, blk, 0, s>>>(p, part);
+        k_dose_partial<2><<<d.n_part, blk, 0, s>>>(p, part, r0, r1);
     else if (d.n_e <= 128)
-        k_dose_partial<4><<<d.n_part, blk, 0, s>>>(p, part);
+        k_dose_partial<4><<<d.n_part, blk, 0, s>>>(p, part, r0, r1);
     else
-        k_dose_partial<8><<<d.n_part, blk, 0, s>>>(p, part);
+        k_dose_partial<8><<<d.n_part, blk, 0, s>>>(p, part, r0, r1);
     k_dose_final<<<1, 256, 0, s>>>(d, part, count, out);
     return cudaGetLastError();
 }
