@@ -12,15 +12,16 @@
 // The forward pass reuses the detector-blur and FDK kernels; this file adds
 // the density projector, the Gaussian-noise step, the CNR objective and the
 // transposes of each linear step:
-//   * CNR -> dJ/dmu (FP64, one CTA);
+//   * CNR -> dJ/dmu (FP64, four grid-wide stages with fixed-order folds);
 //   * backprojection^T: each ROI voxel scatters its bilinear weights into the
 //     filtered-projection gradient (atomics);
 //   * Ram-Lak^T = Ram-Lak (symmetric kernel, zero padding), then the
 //     log / cosine-weight / noise chain rule down to dJ/dI;
 //   * clamp-to-edge blur^T: zero-padded correlation plus the clamped mass
 //     folded back onto the first and last pixel, columns then rows;
-//   * projector^T: each ray recomputes its path lengths (first walk), forms
-//     dJ/dA_im and the spectral partials, then walks again scattering
+//   * projector^T: each ray that meets the voxels recomputes its path
+//     lengths (first walk), forms dJ/dA_im and the spectral partials (summed
+//     over each warp's rays by shuffles), then walks again scattering
 //     dJ/drho_v = dJ/dA_{i,m(v)} l_iv / rho0_m(v) (atomics).
 #include <math.h>
 
@@ -86,36 +87,76 @@ __device__ __forceinline__ Ray make_ray(const DevGeom &g, float c, float s, int 
 template <class F>
 __device__ __forceinline__ void walk(const DevGeom &g, const Ray &r, F f)
 {
-    const int N[3] = {g.nx, g.ny, g.nz};
-    const float lo[3] = {g.lox, g.loy, g.loz}, vox[3] = {g.dx, g.dy, g.dz};
-    const float ivx[3] = {g.idx, g.idy, g.idz};
-    int i[3], sg[3], ux[3];
-    float vs[3], bs[3], tn[3];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        const float p = fmaf(r.t_in, r.d[a], r.A[a]);
-        i[a] = clampi_((int)floorf((p - lo[a]) * ivx[a]), 0, N[a] - 1);
-        sg[a] = r.d[a] > 0.0f ? 1 : (r.d[a] < 0.0f ? -1 : 0);
-        ux[a] = sg[a] > 0;
-        vs[a] = vox[a] * r.inv[a];
-        bs[a] = (lo[a] - r.A[a]) * r.inv[a];
-        tn[a] = sg[a] ? fmaf((float)(i[a] + ux[a]), vs[a], bs[a]) : INFINITY;
-    }
+    // per-axis state in scalars (a runtime axis index would put it in local memory)
+    const float px = fmaf(r.t_in, r.d[0], r.A[0]), py = fmaf(r.t_in, r.d[1], r.A[1]);
+    const float pz = fmaf(r.t_in, r.d[2], r.A[2]);
+    int ix = clampi_((int)floorf((px - g.lox) * g.idx), 0, g.nx - 1);
+    int iy = clampi_((int)floorf((py - g.loy) * g.idy), 0, g.ny - 1);
+    int iz = clampi_((int)floorf((pz - g.loz) * g.idz), 0, g.nz - 1);
+    const int sx = r.d[0] > 0.0f ? 1 : (r.d[0] < 0.0f ? -1 : 0);
+    const int sy = r.d[1] > 0.0f ? 1 : (r.d[1] < 0.0f ? -1 : 0);
+    const int sz = r.d[2] > 0.0f ? 1 : (r.d[2] < 0.0f ? -1 : 0);
+    const int ux = sx > 0, uy = sy > 0, uz = sz > 0;
+    const float vx = g.dx * r.inv[0], vy = g.dy * r.inv[1], vz = g.dz * r.inv[2];
+    const float bx = (g.lox - r.A[0]) * r.inv[0], by = (g.loy - r.A[1]) * r.inv[1];
+    const float bz = (g.loz - r.A[2]) * r.inv[2];
+    float tx = sx ? fmaf((float)(ix + ux), vx, bx) : INFINITY;
+    float ty = sy ? fmaf((float)(iy + uy), vy, by) : INFINITY;
+    float tz = sz ? fmaf((float)(iz + uz), vz, bz) : INFINITY;
+    const int nxy = g.nx * g.ny;
+    int id = iz * nxy + iy * g.nx + ix;
     float t = r.t_in;
     for (int budget = g.nx + g.ny + g.nz + 3; budget > 0; --budget) {
-        const float tm = fminf(tn[0], fminf(tn[1], tn[2]));
+        const float tm = fminf(tx, fminf(ty, tz));
         const float te = fminf(fmaxf(tm, t), r.t_out);
-        f((i[2] * g.ny + i[1]) * g.nx + i[0], te - t);
+        f(id, te - t);
         t = te;
         if (tm >= r.t_out) break;
-        const int a = tn[0] == tm ? 0 : (tn[1] == tm ? 1 : 2);
-        i[a] += sg[a];
-        if (i[a] < 0 || i[a] >= N[a]) break;
-        tn[a] = fmaf((float)(i[a] + ux[a]), vs[a], bs[a]);
+        if (tx == tm) {
+            ix += sx;
+            if (ix < 0 || ix >= g.nx) break;
+            id += sx;
+            tx = fmaf((float)(ix + ux), vx, bx);
+        } else if (ty == tm) {
+            iy += sy;
+            if (iy < 0 || iy >= g.ny) break;
+            id += sy * g.nx;
+            ty = fmaf((float)(iy + uy), vy, by);
+        } else {
+            iz += sz;
+            if (iz < 0 || iz >= g.nz) break;
+            id += sz * nxy;
+            tz = fmaf((float)(iz + uz), vz, bz);
+        }
     }
 }
 
 }  // namespace
+
+// Density-weighted path lengths A_m = sum_{v, label m} l_v rho_v / rho0_m of
+// one ray (zero when r.hit is false): l_v rho_v is summed over each run of
+// one label and the run is scaled by 1 / rho0_m when the label changes.
+__device__ __forceinline__ void density_lengths(const AdjParams &p, const float *__restrict__ rho,
+                                                const Ray &r, float (&A)[kMaxMat])
+{
+#pragma unroll
+    for (int m = 0; m < kMaxMat; ++m) A[m] = 0.0f;
+    if (!r.hit) return;
+    int cur = -1;
+    float run = 0.0f;
+    walk(p.g, r, [&](int v, float len) {
+        const int m = p.labels[v];
+        if (m != cur) {
+#pragma unroll
+            for (int j = 0; j < kMaxMat; ++j) A[j] += (cur == j) ? run * p.irho0[j] : 0.0f;
+            cur = m;
+            run = 0.0f;
+        }
+        run = fmaf(len, rho[v], run);
+    });
+#pragma unroll
+    for (int j = 0; j < kMaxMat; ++j) A[j] += (cur == j) ? run * p.irho0[j] : 0.0f;
+}
 
 // Forward density projector: T_i (flood-normalised) for all rays.
 __global__ void __launch_bounds__(256)
@@ -128,16 +169,7 @@ k_project_density(const __grid_constant__ AdjParams p, const float *__restrict__
     const float2 cs = p.trig[k];
     const Ray r = make_ray(g, cs.x, cs.y, iu, iv);
     float A[kMaxMat];
-#pragma unroll
-    for (int m = 0; m < kMaxMat; ++m) A[m] = 0.0f;
-    if (r.hit) {
-        walk(g, r, [&](int v, float len) {
-            const int m = p.labels[v];
-            const float x = len * rho[v] * p.irho0[m];
-#pragma unroll
-            for (int j = 0; j < kMaxMat; ++j) A[j] += (m == j) ? x : 0.0f;
-        });
-    }
+    density_lengths(p, rho, r, A);
     float sum = 0.0f;
     for (int e = 0; e < p.n_e; ++e) {
         float a = 0.0f;
@@ -155,12 +187,11 @@ k_project_density_adjoint(const __grid_constant__ AdjParams p, const float *__re
                           const float *__restrict__ gT, float *__restrict__ grho,
                           double *__restrict__ gwd)
 {
-    __shared__ float sg[kMaxBins];
+    __shared__ float sgw[8][kMaxBins];   // per-warp sums of dJ/dc_E over its rays
     const DevGeom &g = p.g;
-    const int tid = threadIdx.y * 32 + threadIdx.x;
-    for (int e = tid; e < p.n_e; e += 256) sg[e] = 0.0f;
-    __syncthreads();
-    const int iu = blockIdx.x * 32 + threadIdx.x, iv = blockIdx.y * 8 + threadIdx.y, k = blockIdx.z;
+    const int lane = threadIdx.x, w = threadIdx.y;
+    const int tid = w * 32 + lane;
+    const int iu = blockIdx.x * 32 + lane, iv = blockIdx.y * 8 + w, k = blockIdx.z;
     const bool in = iu < g.n_u && iv < g.n_v;
     float gt = 0.0f;
     Ray r;
@@ -170,54 +201,71 @@ k_project_density_adjoint(const __grid_constant__ AdjParams p, const float *__re
         const float2 cs = p.trig[k];
         r = make_ray(g, cs.x, cs.y, iu, iv);
     }
+    // A ray that misses the voxels has A = 0, T = 1 and e_E - T = 0: it adds
+    // nothing to either gradient.
+    const bool act = in && r.hit && gt != 0.0f;
+    Ray rr = r;
+    rr.hit = act;
     float A[kMaxMat];
-#pragma unroll
-    for (int m = 0; m < kMaxMat; ++m) A[m] = 0.0f;
-    if (in && r.hit && gt != 0.0f) {
-        walk(g, r, [&](int v, float len) {
-            const int m = p.labels[v];
-            const float x = len * rho[v] * p.irho0[m];
-#pragma unroll
-            for (int j = 0; j < kMaxMat; ++j) A[j] += (m == j) ? x : 0.0f;
-        });
-    }
+    density_lengths(p, rho, rr, A);
     // T = sum_E wd_E e_E with wd normalised (sum 1); for the unnormalised
     // weights c_E: dT/dc_E = (e_E - T) / sum c.  Here wd = c / sum c, so the
-    // partial w.r.t. c_E is (e_E - T) * p.inv_csum.
+    // partial w.r.t. c_E is (e_E - T) * p.inv_csum.  Each bin's partial is
+    // summed over the warp's 32 rays by a butterfly (fixed order).
     float gA[kMaxMat];
 #pragma unroll
     for (int m = 0; m < kMaxMat; ++m) gA[m] = 0.0f;
-    if (in && gt != 0.0f) {
+    if (__any_sync(0xffffffffu, act)) {
         float T = 0.0f;
-        for (int e = 0; e < p.n_e; ++e) {
-            float a = 0.0f;
+        if (act) {
+            for (int e = 0; e < p.n_e; ++e) {
+                float a = 0.0f;
 #pragma unroll
-            for (int m = 0; m < kMaxMat; ++m) a = fmaf(p.mu[e][m], A[m], a);
-            T += p.wd[e] * __expf(-a);
+                for (int m = 0; m < kMaxMat; ++m) a = fmaf(p.mu[e][m], A[m], a);
+                T += p.wd[e] * __expf(-a);
+            }
         }
         for (int e = 0; e < p.n_e; ++e) {
-            float a = 0.0f;
+            float v = 0.0f;
+            if (act) {
+                float a = 0.0f;
 #pragma unroll
-            for (int m = 0; m < kMaxMat; ++m) a = fmaf(p.mu[e][m], A[m], a);
-            const float ee = __expf(-a);
-            atomicAdd(&sg[e], gt * (ee - T) * p.inv_csum);
-            const float c = -gt * p.wd[e] * ee;
+                for (int m = 0; m < kMaxMat; ++m) a = fmaf(p.mu[e][m], A[m], a);
+                const float ee = __expf(-a);
+                v = gt * (ee - T) * p.inv_csum;
+                const float c = -gt * p.wd[e] * ee;
 #pragma unroll
-            for (int m = 0; m < kMaxMat; ++m) gA[m] = fmaf(c, p.mu[e][m], gA[m]);
+                for (int m = 0; m < kMaxMat; ++m) gA[m] = fmaf(c, p.mu[e][m], gA[m]);
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if (lane == 0) sgw[w][e] = v;
         }
-        if (r.hit) {
-            walk(g, r, [&](int v, float len) {
-                const int m = p.labels[v];
-                float s = 0.0f;
+    } else if (lane == 0) {
+        for (int e = 0; e < p.n_e; ++e) sgw[w][e] = 0.0f;
+    }
+    if (act) {
+        // dJ/drho_v = gA_m(v) l_v / rho0_m(v): the coefficient changes only
+        // with the label.
+        int mc = -1;
+        float cc = 0.0f;
+        walk(g, r, [&](int v, float len) {
+            const int m = p.labels[v];
+            if (m != mc) {
+                mc = m;
+                cc = 0.0f;
 #pragma unroll
-                for (int j = 0; j < kMaxMat; ++j) s = (m == j) ? gA[j] : s;
-                atomicAdd(grho + v, s * len * p.irho0[m]);
-            });
-        }
+                for (int j2 = 0; j2 < kMaxMat; ++j2) cc = (m == j2) ? gA[j2] * p.irho0[j2] : cc;
+            }
+            atomicAdd(grho + v, cc * len);
+        });
     }
     __syncthreads();
-    for (int e = tid; e < p.n_e; e += 256)
-        if (sg[e] != 0.0f) atomicAdd(gwd + e, (double)sg[e]);
+    for (int e = tid; e < p.n_e; e += 256) {
+        float sum = 0.0f;
+        for (int ww = 0; ww < 8; ++ww) sum += sgw[ww][e];
+        if (sum != 0.0f) atomicAdd(gwd + e, (double)sum);
+    }
 }
 
 // K = I + sqrt(I) z (forward) with z a fixed standard-normal field.
