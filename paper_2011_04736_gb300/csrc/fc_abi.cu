@@ -1555,7 +1555,8 @@ int fc_cnr_grad(fc_handle *h, const double *logits, const double *D, const doubl
         FC_CK(fc::launch_backproject_adjoint(pf, h->d_gmu, h->d_gf, s));
         FC_CK(cudaMemsetAsync(h->d_gI, 0, np * sizeof(float), s));
         FC_CK(fc::launch_filter_adjoint(pf, h->d_gf, h->d_I, h->d_counts, z, h->d_gI, s));
-        FC_CK(fc::launch_blur_adjoint(b, na, h->d_gI, h->d_gtmp, h->d_gT, b.n0, b.spr, s));
+        // d_tp / d_ts are free once the forward blur has run
+        FC_CK(fc::launch_blur_transpose(b, h->d_gI, h->d_tp, h->d_ts, h->d_gT, na, s));
         FC_CK(cudaMemsetAsync(h->d_gwd, 0, fc::kMaxBins * sizeof(double), s));
         float *grho = g_rho ? g_rho : h->d_gtmp;   // scratch when only spectral grads are wanted
         FC_CK(cudaMemsetAsync(grho, 0, nv * sizeof(float), s));

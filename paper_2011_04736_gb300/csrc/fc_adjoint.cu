@@ -15,10 +15,12 @@
 //   * CNR -> dJ/dmu (FP64, four grid-wide stages with fixed-order folds);
 //   * backprojection^T: each ROI voxel scatters its bilinear weights into the
 //     filtered-projection gradient (atomics);
-//   * Ram-Lak^T = Ram-Lak (symmetric kernel, zero padding), then the
-//     log / cosine-weight / noise chain rule down to dJ/dI;
+//   * Ram-Lak^T = Ram-Lak (symmetric kernel, zero padding: the forward row
+//     filter of fc_fdk.cu), then the log / cosine-weight / noise chain rule
+//     down to dJ/dI;
 //   * clamp-to-edge blur^T: zero-padded correlation plus the clamped mass
-//     folded back onto the first and last pixel, columns then rows;
+//     folded back onto the first and last pixel (the transposed mode of the
+//     direct blur kernels, fc_detector.cu);
 //   * projector^T: each ray that meets the voxels recomputes its path
 //     lengths (first walk), forms dJ/dA_im and the spectral partials (summed
 //     over each warp's rays by shuffles), then walks again scattering
@@ -518,86 +520,6 @@ k_backproject_adjoint(const __grid_constant__ FdkParams p, const float *__restri
     }
 }
 
-// Ram-Lak transpose (the kernel is symmetric) and the chain rule down to
-// dJ/dI:  q = ln(I_flood / max(K, 1)) cosw,  K = I + sqrt(I) z.
-// One thread per detector pixel of the reachable rows; gI elsewhere is zero.
-__global__ void __launch_bounds__(256)
-k_filter_adjoint(const __grid_constant__ FdkParams p, const float *__restrict__ gf,
-                 const float *__restrict__ I, const float *__restrict__ K,
-                 const float *__restrict__ z, float *__restrict__ gI)
-{
-    const DevGeom &g = p.g;
-    const int iu = blockIdx.x * blockDim.x + threadIdx.x;
-    const int r = blockIdx.y, k = blockIdx.z;
-    if (iu >= g.n_u) return;
-    const int iv = p.v_lo + r;
-    const float *row = gf + ((size_t)k * p.ph + (r + 1)) * p.pw + 1;
-    // gq[iu] = (1 / tau) sum_j h'[j] gf[iu + j],  h'[0] = 1/4, h'[odd j] = -1/(pi j)^2
-    float acc = 0.25f * row[iu];
-    for (int j = 1; j < g.n_u; j += 2) {
-        const float h = -1.0f / (9.8696044f * (float)j * (float)j);
-        if (iu - j >= 0) acc = fmaf(h, row[iu - j], acc);
-        if (iu + j < g.n_u) acc = fmaf(h, row[iu + j], acc);
-    }
-    const float gq = acc / p.tau;
-    const float ui = ((float)iu - g.cu) * g.du * p.mag;
-    const float vi = ((float)iv - g.cv) * g.dv * p.mag;
-    const float cosw = g.sad * rsqrtf(g.sad * g.sad + ui * ui + vi * vi);
-    const size_t idx = ((size_t)k * g.n_v + iv) * g.n_u + iu;
-    const float Kv = K[idx];
-    const float gK = Kv > 1.0f ? -gq * cosw / Kv : 0.0f;
-    float dKdI = 1.0f;
-    if (z) {
-        const float Iv = I[idx];
-        dKdI = Iv > 0.0f ? 1.0f + 0.5f * z[idx] * rsqrtf(Iv) : 1.0f;
-    }
-    gI[idx] = gK * dKdI;
-}
-
-// Transpose of one clamp-to-edge 1D Gaussian pass along u (rows) or v
-// (columns): out[t] = sum_j g[j] in[t + j] (zero outside) plus, at t = 0 and
-// t = n - 1, the mass of every tap that the forward pass clamped there.
-template <bool ALONG_V>
-__global__ void __launch_bounds__(256)
-k_blur_adjoint_pass(const __grid_constant__ BlurParams b, int which, const float *__restrict__ in,
-                    float *__restrict__ out, float gain, int accumulate)
-{
-    const int n_u = b.n_u, n_v = b.n_v;
-    const int iu = blockIdx.x * blockDim.x + threadIdx.x;
-    const int iv = blockIdx.y, k = blockIdx.z;
-    if (iu >= n_u) return;
-    const float *taps = which ? b.gs : b.gp;
-    const int R = which ? b.rs : b.rp;
-    const int n = ALONG_V ? n_v : n_u;
-    const int t = ALONG_V ? iv : iu;
-    const size_t plane = (size_t)n_u * n_v;
-    const float *src = in + (size_t)k * plane;
-    auto at = [&](int s) -> float {
-        return ALONG_V ? src[(size_t)s * n_u + iu] : src[(size_t)iv * n_u + s];
-    };
-    float acc = 0.0f;
-    for (int j = -R; j <= R; ++j) {
-        const int s = t - j;   // forward output s read input t with tap j (symmetric kernel)
-        if (s >= 0 && s < n) acc = fmaf(taps[j + R], at(s), acc);
-    }
-    if (t == 0) {
-        for (int s = 0; s < n && s < R; ++s) {
-            float m = 0.0f;
-            for (int j = -R; j < -s; ++j) m += taps[j + R];   // s + j < 0 clamps to 0
-            acc = fmaf(m, at(s), acc);
-        }
-    }
-    if (t == n - 1) {
-        for (int s = n - 1; s >= 0 && s > n - 1 - R; --s) {
-            float m = 0.0f;
-            for (int j = n - s; j <= R; ++j) m += taps[j + R];  // s + j > n - 1 clamps
-            acc = fmaf(m, at(s), acc);
-        }
-    }
-    const size_t o = (size_t)k * plane + (size_t)iv * n_u + iu;
-    out[o] = accumulate ? fmaf(gain, acc, out[o]) : gain * acc;
-}
-
 // ---------------------------------------------------------------- launchers
 cudaError_t launch_project_density(const AdjParams &p, const float *rho, float *T, cudaStream_t s)
 {
@@ -637,27 +559,6 @@ cudaError_t launch_backproject_adjoint(const FdkParams &p, const float *gmu, flo
 {
     const size_t n = (size_t)p.g.nx * p.g.ny * p.g.nz;
     k_backproject_adjoint<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(p, gmu, gf);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_filter_adjoint(const FdkParams &p, const float *gf, const float *I, const float *K,
-                                  const float *z, float *gI, cudaStream_t s)
-{
-    dim3 grid((p.g.n_u + 255) / 256, p.v_hi - p.v_lo + 1, p.g.n_angles);
-    k_filter_adjoint<<<grid, 256, 0, s>>>(p, gf, I, K, z, gI);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_blur_adjoint(const BlurParams &b, int n_img, const float *gI, float *tmp,
-                                float *gT, float n0, float spr, cudaStream_t s)
-{
-    // G = C o R per kernel (R rows, C columns); G^T = R^T o C^T.
-    // gT = n0 (Gp^T gI + spr Gs^T gI).
-    dim3 grid((b.n_u + 255) / 256, b.n_v, n_img);
-    k_blur_adjoint_pass<true><<<grid, 256, 0, s>>>(b, 0, gI, tmp, 1.0f, 0);
-    k_blur_adjoint_pass<false><<<grid, 256, 0, s>>>(b, 0, tmp, gT, n0, 0);
-    k_blur_adjoint_pass<true><<<grid, 256, 0, s>>>(b, 1, gI, tmp, 1.0f, 0);
-    k_blur_adjoint_pass<false><<<grid, 256, 0, s>>>(b, 1, tmp, gT, n0 * spr, 1);
     return cudaGetLastError();
 }
 

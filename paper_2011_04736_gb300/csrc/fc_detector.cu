@@ -59,8 +59,39 @@ __device__ __forceinline__ void row_conv(const float *__restrict__ srow, int bas
     }
 }
 
+// Transposed clamp-to-edge pass, edge terms.  The forward pass read input 0
+// for every tap j of output s with s + j < 0, so the transpose adds to output
+// 0 the sum over s < r of x[s] times the mass of those taps,
+//     sum_s x[s] sum_{i <= r - 1 - s} g[i] = sum_s g[r - 1 - s] P[s],
+// P[s] = x[0] + ... + x[s]; the last output takes the mirror image.  x(s)
+// returns the zero-padded staged input at s.
+template <class X>
+__device__ __forceinline__ float fold_lo(X x, const float *g, int r)
+{
+    float P = 0.0f, f = 0.0f;
+    for (int s = 0; s < r; ++s) {
+        P += x(s);
+        f = fmaf(g[r - 1 - s], P, f);
+    }
+    return f;
+}
+
+template <class X>
+__device__ __forceinline__ float fold_hi(X x, const float *g, int r, int n)
+{
+    float Q = 0.0f, f = 0.0f;
+    for (int d = 0; d < r; ++d) {
+        Q += x(n - 1 - d);
+        f = fmaf(g[r + 1 + d], Q, f);
+    }
+    return f;
+}
+
 }  // namespace
 
+// ADJ: the transposed pass (zero padding instead of clamped indices, plus the
+// clamped taps' mass folded onto the first and last output).
+template <bool ADJ>
 __global__ void __launch_bounds__(kRowThreads)
 k_blur_rows(const __grid_constant__ BlurParams p, const float *__restrict__ T,
             float *__restrict__ tp, float *__restrict__ ts)
@@ -73,8 +104,12 @@ k_blur_rows(const __grid_constant__ BlurParams p, const float *__restrict__ T,
     const int span = n + 2 * R + 2 * kOut;
     for (int i = threadIdx.x; i < span; i += blockDim.x) {
         int uu = i - R;
-        uu = uu < 0 ? 0 : (uu > n - 1 ? n - 1 : uu);
-        srow[skew(i)] = src[uu];
+        if (ADJ) {
+            srow[skew(i)] = uu >= 0 && uu < n ? src[uu] : 0.0f;
+        } else {
+            uu = uu < 0 ? 0 : (uu > n - 1 ? n - 1 : uu);
+            srow[skew(i)] = src[uu];
+        }
     }
     __syncthreads();
     for (int u0 = threadIdx.x * kOut; u0 < n; u0 += blockDim.x * kOut) {
@@ -83,6 +118,19 @@ k_blur_rows(const __grid_constant__ BlurParams p, const float *__restrict__ T,
         for (int o = 0; o < kOut; ++o) { ap[o] = 0.0f; as[o] = 0.0f; }
         row_conv(srow, u0 + R - p.rp, p.gp, 2 * p.rp + 1, ap);
         row_conv(srow, u0 + R - p.rs, p.gs, 2 * p.rs + 1, as);
+        if (ADJ) {
+            auto x = [&](int q) { return srow[skew(R + q)]; };
+            if (u0 == 0) {
+                ap[0] += fold_lo(x, p.gp, p.rp);
+                as[0] += fold_lo(x, p.gs, p.rs);
+            }
+            if (n - 1 >= u0 && n - 1 < u0 + kOut) {
+                const float fp = fold_hi(x, p.gp, p.rp, n), fs = fold_hi(x, p.gs, p.rs, n);
+#pragma unroll
+                for (int o = 0; o < kOut; ++o)
+                    if (u0 + o == n - 1) { ap[o] += fp; as[o] += fs; }
+            }
+        }
 #pragma unroll
         for (int o = 0; o < kOut; ++o) {
             if (u0 + o < n) {
@@ -97,7 +145,7 @@ k_blur_rows(const __grid_constant__ BlurParams p, const float *__restrict__ T,
 // row stride ST floats.  The 32 / TW column groups of a warp work on rows
 // 8 apart; ST is chosen so those rows start 32 / (32 / TW) banks apart
 // (ST = 32, 18, 9 for TW = 32, 16, 8), which keeps shared reads conflict-free.
-template <int TW, int ST>
+template <int TW, int ST, bool ADJ>
 __global__ void __launch_bounds__(kColThreads)
 k_blur_cols(const __grid_constant__ BlurParams p, const float *__restrict__ tp,
             const float *__restrict__ ts, float *__restrict__ out)
@@ -119,13 +167,21 @@ k_blur_cols(const __grid_constant__ BlurParams p, const float *__restrict__ tp,
     const int uc = u < nu ? u : nu - 1;
     for (int r = grp; r < hp; r += ngrp) {
         int vv = r - p.rp;
-        vv = vv < 0 ? 0 : (vv > nv - 1 ? nv - 1 : vv);
-        sp[r * ST + col] = gp_src[(size_t)vv * nu + uc];
+        if (ADJ) {
+            sp[r * ST + col] = vv >= 0 && vv < nv ? gp_src[(size_t)vv * nu + uc] : 0.0f;
+        } else {
+            vv = vv < 0 ? 0 : (vv > nv - 1 ? nv - 1 : vv);
+            sp[r * ST + col] = gp_src[(size_t)vv * nu + uc];
+        }
     }
     for (int r = grp; r < hs; r += ngrp) {
         int vv = r - p.rs;
-        vv = vv < 0 ? 0 : (vv > nv - 1 ? nv - 1 : vv);
-        ss[r * ST + col] = gs_src[(size_t)vv * nu + uc];
+        if (ADJ) {
+            ss[r * ST + col] = vv >= 0 && vv < nv ? gs_src[(size_t)vv * nu + uc] : 0.0f;
+        } else {
+            vv = vv < 0 ? 0 : (vv > nv - 1 ? nv - 1 : vv);
+            ss[r * ST + col] = gs_src[(size_t)vv * nu + uc];
+        }
     }
     __syncthreads();
     for (int v0 = grp * kOut; v0 < nv; v0 += ngrp * kOut) {
@@ -175,6 +231,20 @@ k_blur_cols(const __grid_constant__ BlurParams p, const float *__restrict__ tp,
                 for (int o = 0; o < kOut; ++o) as[o] = fmaf(gj, ss[(v0 + j + q + o) * ST + col], as[o]);
             }
         }
+        if (ADJ) {
+            auto xp = [&](int q) { return sp[(q + p.rp) * ST + col]; };
+            auto xs = [&](int q) { return ss[(q + p.rs) * ST + col]; };
+            if (v0 == 0) {
+                ap[0] += fold_lo(xp, p.gp, p.rp);
+                as[0] += fold_lo(xs, p.gs, p.rs);
+            }
+            if (nv - 1 >= v0 && nv - 1 < v0 + kOut) {
+                const float fp = fold_hi(xp, p.gp, p.rp, nv), fs = fold_hi(xs, p.gs, p.rs, nv);
+#pragma unroll
+                for (int o = 0; o < kOut; ++o)
+                    if (v0 + o == nv - 1) { ap[o] += fp; as[o] += fs; }
+            }
+        }
         if (u < nu) {
 #pragma unroll
             for (int o = 0; o < kOut; ++o) {
@@ -192,20 +262,21 @@ static size_t col_smem_bytes(const BlurParams &p, int st)
     return (size_t)(2 * p.n_v + 2 * p.rp + 2 * p.rs + 2 * kOut) * st * sizeof(float);
 }
 
-template <int TW, int ST>
+template <int TW, int ST, bool ADJ>
 static cudaError_t launch_cols_tw(const BlurParams &p, const float *tp, const float *ts, float *out,
                                   int n_img, cudaStream_t s)
 {
     const size_t b = col_smem_bytes(p, ST);
-    cudaError_t e = cudaFuncSetAttribute(k_blur_cols<TW, ST>,
+    cudaError_t e = cudaFuncSetAttribute(k_blur_cols<TW, ST, ADJ>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b);
     if (e != cudaSuccess) return e;
     dim3 grid((p.n_u + TW - 1) / TW, n_img);
-    k_blur_cols<TW, ST><<<grid, kColThreads, b, s>>>(p, tp, ts, out);
+    k_blur_cols<TW, ST, ADJ><<<grid, kColThreads, b, s>>>(p, tp, ts, out);
     return cudaGetLastError();
 }
 
-cudaError_t launch_blur_rows(const BlurParams &p, const float *T, float *tp, float *ts, int n_img,
+template <bool ADJ>
+static cudaError_t rows_pass(const BlurParams &p, const float *T, float *tp, float *ts, int n_img,
                              cudaStream_t s)
 {
     if (n_img <= 0) return cudaSuccess;
@@ -214,26 +285,52 @@ cudaError_t launch_blur_rows(const BlurParams &p, const float *T, float *tp, flo
     const size_t row_smem = (size_t)(span + span / 32 + 2) * sizeof(float);
     cudaError_t e;
     if (row_smem > 48 * 1024) {
-        e = cudaFuncSetAttribute(k_blur_rows, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        e = cudaFuncSetAttribute(k_blur_rows<ADJ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)row_smem);
         if (e != cudaSuccess) return e;
     }
     int threads = ((p.n_u + kOut - 1) / kOut + 31) / 32 * 32;
     threads = threads < 32 ? 32 : (threads > kRowThreads ? kRowThreads : threads);
-    k_blur_rows<<<(unsigned)((size_t)n_img * p.n_v), threads, row_smem, s>>>(p, T, tp, ts);
+    k_blur_rows<ADJ><<<(unsigned)((size_t)n_img * p.n_v), threads, row_smem, s>>>(p, T, tp, ts);
     return cudaGetLastError();
 }
 
-cudaError_t launch_blur_cols(const BlurParams &p, const float *tp, const float *ts, float *out,
+template <bool ADJ>
+static cudaError_t cols_pass(const BlurParams &p, const float *tp, const float *ts, float *out,
                              int n_img, cudaStream_t s)
 {
     if (n_img <= 0) return cudaSuccess;
     // Prefer 16-column tiles (about 3 CTAs per SM for a 384-row detector);
     // fall back to narrower tiles for tall detectors.
     const size_t limit = 220 * 1024;
-    if (col_smem_bytes(p, 18) <= limit / 2) return launch_cols_tw<16, 18>(p, tp, ts, out, n_img, s);
-    if (col_smem_bytes(p, 9) <= limit) return launch_cols_tw<8, 9>(p, tp, ts, out, n_img, s);
+    if (col_smem_bytes(p, 18) <= limit / 2) return launch_cols_tw<16, 18, ADJ>(p, tp, ts, out, n_img, s);
+    if (col_smem_bytes(p, 9) <= limit) return launch_cols_tw<8, 9, ADJ>(p, tp, ts, out, n_img, s);
     return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_blur_rows(const BlurParams &p, const float *T, float *tp, float *ts, int n_img,
+                             cudaStream_t s)
+{
+    return rows_pass<false>(p, T, tp, ts, n_img, s);
+}
+
+cudaError_t launch_blur_cols(const BlurParams &p, const float *tp, const float *ts, float *out,
+                             int n_img, cudaStream_t s)
+{
+    return cols_pass<false>(p, tp, ts, out, n_img, s);
+}
+
+// Transpose of out = n0 (C_p R_p + spr C_s R_s) in (clamp-to-edge passes):
+// the row and column passes act on different axes and commute, so the
+// transpose is n0 (C_p^T R_p^T + spr C_s^T R_s^T) gin: the transposed row pass
+// (one input, both kernels) into tp and ts, then the transposed column pass
+// combining them.
+cudaError_t launch_blur_transpose(const BlurParams &p, const float *gin, float *tp, float *ts,
+                                  float *gout, int n_img, cudaStream_t s)
+{
+    cudaError_t e = rows_pass<true>(p, gin, tp, ts, n_img, s);
+    if (e != cudaSuccess) return e;
+    return cols_pass<true>(p, tp, ts, gout, n_img, s);
 }
 
 // Each warp draws 32 * kPer pixels of one detector row (lane l: pixels

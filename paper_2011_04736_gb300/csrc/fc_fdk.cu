@@ -46,39 +46,15 @@ cudaError_t upload_ramp_taps()
     return e;
 }
 
-// rows [v_lo, v_hi] of every projection; blockIdx.x = projection * nrows + r
-__global__ void __launch_bounds__(kFiltThreads)
-k_fdk_filter(const __grid_constant__ FdkParams p, const float *__restrict__ counts,
-             float *__restrict__ filt)
+// Ram-Lak filtered row from the staged zero-padded row sx (index n + j holds
+// sample j, zeros around it): calls out(i, v) for i in [0, n) with
+// v = (x[i] / 4 + sum over odd j of -x[i + j] / (pi j)^2) / tau.
+template <class Out>
+__device__ __forceinline__ void ramp_row(const float *sx, int n, float inv_tau, Out out)
 {
-    extern __shared__ float sx[];
-    const DevGeom &g = p.g;
-    const int n = g.n_u;
-    const int nrows = p.v_hi - p.v_lo + 1;
-    const int k = blockIdx.x / nrows;
-    const int r = (int)(blockIdx.x % nrows);
-    const int iv = p.v_lo + r;
-    const size_t row = ((size_t)k * g.n_v + iv) * n;
-    float *dst = filt + ((size_t)k * p.ph + (r + 1)) * p.pw + 1;
-    // padded row: index n + j holds q[j], zeros in [0, n) and [2n, 3n + pad)
-    const float vi = ((float)iv - g.cv) * g.dv * p.mag;
-    const float sad2v = g.sad * g.sad + vi * vi;
-    const int span = 3 * n + kFiltOut + 2;
-    for (int i = threadIdx.x; i < span; i += blockDim.x) {
-        float val = 0.0f;
-        const int j = i - n;
-        if (j >= 0 && j < n) {
-            const float ui = ((float)j - g.cu) * g.du * p.mag;
-            const float K = fmaxf(counts[row + j], 1.0f);
-            val = (p.log_flood - logf(K)) * (g.sad * rsqrtf(sad2v + ui * ui));
-        }
-        sx[skew(i)] = val;
-    }
-    __syncthreads();
     // odd offsets j in [-jm, jm], jm = largest odd <= n - 1
     const int jm = ((n - 1) & 1) ? n - 1 : n - 2;
     const int ntap = jm >= 1 ? (jm + 1) : 0;   // number of odd offsets (both signs)
-    const float inv_tau = 1.0f / p.tau;
     for (int i0 = threadIdx.x * kFiltOut; i0 < n; i0 += blockDim.x * kFiltOut) {
         float acc[kFiltOut];
 #pragma unroll
@@ -115,8 +91,40 @@ k_fdk_filter(const __grid_constant__ FdkParams p, const float *__restrict__ coun
         }
 #pragma unroll
         for (int o = 0; o < kFiltOut; ++o)
-            if (i0 + o < n) dst[i0 + o] = acc[o] * inv_tau;
+            if (i0 + o < n) out(i0 + o, acc[o] * inv_tau);
     }
+}
+
+// rows [v_lo, v_hi] of every projection; blockIdx.x = projection * nrows + r
+__global__ void __launch_bounds__(kFiltThreads)
+k_fdk_filter(const __grid_constant__ FdkParams p, const float *__restrict__ counts,
+             float *__restrict__ filt)
+{
+    extern __shared__ float sx[];
+    const DevGeom &g = p.g;
+    const int n = g.n_u;
+    const int nrows = p.v_hi - p.v_lo + 1;
+    const int k = blockIdx.x / nrows;
+    const int r = (int)(blockIdx.x % nrows);
+    const int iv = p.v_lo + r;
+    const size_t row = ((size_t)k * g.n_v + iv) * n;
+    float *dst = filt + ((size_t)k * p.ph + (r + 1)) * p.pw + 1;
+    // padded row: index n + j holds q[j], zeros in [0, n) and [2n, 3n + pad)
+    const float vi = ((float)iv - g.cv) * g.dv * p.mag;
+    const float sad2v = g.sad * g.sad + vi * vi;
+    const int span = 3 * n + kFiltOut + 2;
+    for (int i = threadIdx.x; i < span; i += blockDim.x) {
+        float val = 0.0f;
+        const int j = i - n;
+        if (j >= 0 && j < n) {
+            const float ui = ((float)j - g.cu) * g.du * p.mag;
+            const float K = fmaxf(counts[row + j], 1.0f);
+            val = (p.log_flood - logf(K)) * (g.sad * rsqrtf(sad2v + ui * ui));
+        }
+        sx[skew(i)] = val;
+    }
+    __syncthreads();
+    ramp_row(sx, n, 1.0f / p.tau, [&](int i, float v) { dst[i] = v; });
 }
 
 cudaError_t launch_fdk_filter(const FdkParams &p, const float *counts, float *filt, cudaStream_t s)
@@ -135,6 +143,66 @@ cudaError_t launch_fdk_filter(const FdkParams &p, const float *counts, float *fi
     }
     const size_t blocks = (size_t)p.g.n_angles * nrows;
     k_fdk_filter<<<(unsigned)blocks, kFiltThreads, smem, s>>>(p, counts, filt);
+    return cudaGetLastError();
+}
+
+// Ram-Lak transpose (the kernel is symmetric, so it is the same row filter)
+// and the chain rule down to dJ/dI:  q = ln(I_flood / max(K, 1)) cosw,
+// K = I + sqrt(I) z.  One CTA per reachable detector row of a projection
+// (gf in the padded layout of the filtered rows); gI elsewhere is left as is.
+__global__ void __launch_bounds__(kFiltThreads)
+k_filter_adjoint(const __grid_constant__ FdkParams p, const float *__restrict__ gf,
+                 const float *__restrict__ I, const float *__restrict__ K,
+                 const float *__restrict__ z, float *__restrict__ gI)
+{
+    extern __shared__ float sx[];
+    const DevGeom &g = p.g;
+    const int n = g.n_u;
+    const int nrows = p.v_hi - p.v_lo + 1;
+    const int k = blockIdx.x / nrows;
+    const int r = (int)(blockIdx.x % nrows);
+    const int iv = p.v_lo + r;
+    const float *src = gf + ((size_t)k * p.ph + (r + 1)) * p.pw + 1;
+    const int span = 3 * n + kFiltOut + 2;
+    for (int i = threadIdx.x; i < span; i += blockDim.x) {
+        const int j = i - n;
+        sx[skew(i)] = j >= 0 && j < n ? src[j] : 0.0f;
+    }
+    __syncthreads();
+    const float vi = ((float)iv - g.cv) * g.dv * p.mag;
+    const size_t row = ((size_t)k * g.n_v + iv) * n;
+    ramp_row(sx, n, 1.0f / p.tau, [&](int iu, float gq) {
+        const float ui = ((float)iu - g.cu) * g.du * p.mag;
+        const float cosw = g.sad * rsqrtf(g.sad * g.sad + ui * ui + vi * vi);
+        const size_t idx = row + iu;
+        const float Kv = K[idx];
+        const float gK = Kv > 1.0f ? -gq * cosw / Kv : 0.0f;
+        float dKdI = 1.0f;
+        if (z) {
+            const float Iv = I[idx];
+            dKdI = Iv > 0.0f ? 1.0f + 0.5f * z[idx] * rsqrtf(Iv) : 1.0f;
+        }
+        gI[idx] = gK * dKdI;
+    });
+}
+
+cudaError_t launch_filter_adjoint(const FdkParams &p, const float *gf, const float *I, const float *K,
+                                  const float *z, float *gI, cudaStream_t s)
+{
+    const int nrows = p.v_hi - p.v_lo + 1;
+    if (nrows <= 0 || p.g.n_angles <= 0) return cudaSuccess;
+    if (p.g.n_u > kMaxFiltTaps) return cudaErrorInvalidValue;
+    cudaError_t e = upload_ramp_taps();
+    if (e != cudaSuccess) return e;
+    const int span = 3 * p.g.n_u + kFiltOut + 2;
+    const size_t smem = (size_t)(span + span / 32 + 2) * sizeof(float);
+    if (smem > 48 * 1024) {
+        e = cudaFuncSetAttribute(k_filter_adjoint, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    const size_t blocks = (size_t)p.g.n_angles * nrows;
+    k_filter_adjoint<<<(unsigned)blocks, kFiltThreads, smem, s>>>(p, gf, I, K, z, gI);
     return cudaGetLastError();
 }
 

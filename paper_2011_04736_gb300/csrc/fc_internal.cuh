@@ -243,9 +243,6 @@ cudaError_t launch_backproject_adjoint(const FdkParams &p, const float *gmu, flo
                                        cudaStream_t s);
 cudaError_t launch_filter_adjoint(const FdkParams &p, const float *gf, const float *I,
                                   const float *K, const float *z, float *gI, cudaStream_t s);
-cudaError_t launch_blur_adjoint(const BlurParams &b, int n_img, const float *gI, float *tmp,
-                                float *gT, float n0, float spr, cudaStream_t s);
-
 // launchers (return cudaError_t of the launch)
 cudaError_t launch_project(const ProjParams &p, float *T, float *L_out, cudaStream_t s);
 int project_launches(const ProjParams &p);
@@ -256,6 +253,9 @@ cudaError_t launch_blur_rows(const BlurParams &p, const float *T, float *tp, flo
                              int n_img, cudaStream_t s);
 cudaError_t launch_blur_cols(const BlurParams &p, const float *tp, const float *ts, float *out,
                              int n_img, cudaStream_t s);
+// transposed blur: gout = n0 (G_psf^T + spr G_scatter^T) gin (tp, ts scratch)
+cudaError_t launch_blur_transpose(const BlurParams &p, const float *gin, float *tp, float *ts,
+                                  float *gout, int n_img, cudaStream_t s);
 cudaError_t launch_poisson(const float *lam, float *out, int n_img, int n_v, int n_u,
                            int angle0, uint64_t seed, cudaStream_t s);
 cudaError_t launch_fdk_filter(const FdkParams &p, const float *counts, float *filt,
