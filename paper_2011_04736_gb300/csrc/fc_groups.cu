@@ -9,6 +9,7 @@
 // profile prof[u] = N0 sum_g A_g (g_g (x)_u y_g)(u) (k_group_profile).  The
 // primaries go through k_group_blur: one CTA per 64 x 32 output tile, each
 // group's tile (with a clamped halo of its radius) staged in shared memory,
+// the next group's copy in flight while the current one is filtered,
 // separable row then column passes, the groups accumulated in registers.
 #include <math.h>
 #include <string.h>
@@ -23,6 +24,23 @@ constexpr int kTu = 64, kTv = 32;                 // output tile (columns x rows
 constexpr int kThreads = 256;                     // 64 columns x 4 row groups of 8
 
 __device__ __forceinline__ int clampi(int i, int n) { return i < 0 ? 0 : (i > n - 1 ? n - 1 : i); }
+
+__device__ __forceinline__ void cp_async4(float *dst, const float *src)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;"
+                 :: "r"((unsigned)__cvta_generic_to_shared(dst)), "l"(src) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" :: "n"(N) : "memory"); }
+
+// shared bytes of k_group_blur<RM>: two input tiles and the row-pass tile
+constexpr size_t group_blur_smem(int rm)
+{
+    return sizeof(float) * (2 * (size_t)(kTv + 2 * rm) * (kTu + 2 * rm + 1) + (size_t)(kTv + 2 * rm) * (kTu + 1));
+}
 
 }  // namespace
 
@@ -47,42 +65,74 @@ __global__ void k_group_profile(const __grid_constant__ GroupParams p, float *__
 
 // RM: the largest radius of the groups; every group's taps are read zero
 // padded to RM (p.tpad[g][j + RM]), so the tap loops unroll at compile time.
+// The next group's tile is copied (cp.async) into the second input buffer
+// while the current one is filtered.
 template <int RM>
 __global__ void __launch_bounds__(kThreads)
 k_group_blur(const __grid_constant__ GroupParams p, const float *__restrict__ P,
              const float *__restrict__ prof, float *__restrict__ out)
 {
     constexpr int H = kTv + 2 * RM, Wd = kTu + 2 * RM, nt = 2 * RM + 1;
-    __shared__ float sin_[H][Wd + 1];
-    __shared__ float smid[H][kTu + 1];
+    extern __shared__ float smem[];
+    float (*sin_)[H][Wd + 1] = reinterpret_cast<float (*)[H][Wd + 1]>(smem);
+    float (*smid)[kTu + 1] = reinterpret_cast<float (*)[kTu + 1]>(smem + 2 * H * (Wd + 1));
     const int tid = threadIdx.x, tx = tid % kTu, ty = tid / kTu;
     const int u0 = blockIdx.x * kTu, v0 = blockIdx.y * kTv;
     const size_t img = (size_t)blockIdx.z * p.n_u * p.n_v;
+    const int lane = tid % 32, warp = tid / 32;
+    auto stage = [&](int gi, int b) {
+        const float *src = P + (size_t)gi * p.grp_stride + img;
+        for (int r = warp; r < H; r += kThreads / 32) {
+            const float *row = src + (size_t)clampi(v0 - RM + r, p.n_v) * p.n_u;
+            for (int c = lane; c < Wd; c += 32) cp_async4(&sin_[b][r][c], row + clampi(u0 - RM + c, p.n_u));
+        }
+        cp_async_commit();
+    };
     float acc[8];
 #pragma unroll
     for (int o = 0; o < 8; ++o) acc[o] = 0.0f;
+    if (p.n_groups > 0) stage(0, 0);
     for (int gi = 0; gi < p.n_groups; ++gi) {
-        const float *src = P + (size_t)gi * p.grp_stride + img;
+        const int b = gi & 1;
         const float *tap = p.tpad[gi];
-        __syncthreads();
-        for (int i = tid; i < H * Wd; i += kThreads) {
-            const int r = i / Wd, c = i % Wd;
-            sin_[r][c] = __ldg(src + (size_t)clampi(v0 - RM + r, p.n_v) * p.n_u + clampi(u0 - RM + c, p.n_u));
+        if (gi + 1 < p.n_groups) {
+            stage(gi + 1, b ^ 1);     // its buffer was last read before the previous barrier
+            cp_async_wait<1>();
+        } else {
+            cp_async_wait<0>();
         }
         __syncthreads();
-        for (int i = tid; i < H * kTu; i += kThreads) {
-            const int r = i / kTu, c = i % kTu;
-            float s = 0.0f;
+        // row pass: 8 adjacent outputs per item from a register window of
+        // 8 + 2 RM inputs; the lanes of a warp take different rows (row
+        // pitches Wd + 1 and kTu + 1 keep them on different banks)
+        for (int it = tid; it < H * (kTu / 8); it += kThreads) {
+            const int r = it % H, c0 = (it / H) * 8;
+            float w[8 + 2 * RM], o8[8];
 #pragma unroll
-            for (int j = 0; j < nt; ++j) s = fmaf(tap[j], sin_[r][c + j], s);
-            smid[r][c] = s;
+            for (int k = 0; k < 8 + 2 * RM; ++k) w[k] = sin_[b][r][c0 + k];
+#pragma unroll
+            for (int o = 0; o < 8; ++o) o8[o] = 0.0f;
+#pragma unroll
+            for (int j = 0; j < nt; ++j) {
+                const float t = tap[j];
+#pragma unroll
+                for (int o = 0; o < 8; ++o) o8[o] = fmaf(t, w[o + j], o8[o]);
+            }
+#pragma unroll
+            for (int o = 0; o < 8; ++o) smid[r][c0 + o] = o8[o];
         }
         __syncthreads();
+        // column pass: 8 outputs of column tx from a window of 8 + 2 RM rows
+        {
+            float w[8 + 2 * RM];
 #pragma unroll
-        for (int j = 0; j < nt; ++j) {
-            const float t = tap[j];
+            for (int k = 0; k < 8 + 2 * RM; ++k) w[k] = smid[ty * 8 + k][tx];
 #pragma unroll
-            for (int o = 0; o < 8; ++o) acc[o] = fmaf(t, smid[ty * 8 + o + j][tx], acc[o]);
+            for (int j = 0; j < nt; ++j) {
+                const float t = tap[j];
+#pragma unroll
+                for (int o = 0; o < 8; ++o) acc[o] = fmaf(t, w[o + j], acc[o]);
+            }
         }
     }
     const int u = u0 + tx;
@@ -115,12 +165,15 @@ cudaError_t launch_group_blur(const GroupParams &g, const float *P, float *prof,
 #undef FC_GB_CASE
     default: return cudaErrorInvalidValue;
     }
+    const size_t smem = group_blur_smem(rm);
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
     const size_t plane = (size_t)g.n_u * g.n_v;
     for (int i0 = 0; i0 < n_img; i0 += 65535) {   // grid z limit
         const int n = n_img - i0 < 65535 ? n_img - i0 : 65535;
         const size_t off = (size_t)(angle0 + i0) * plane;
         dim3 grid((g.n_u + kTu - 1) / kTu, (g.n_v + kTv - 1) / kTv, n);
-        kern<<<grid, kThreads, 0, s>>>(q, P + off, prof, out + off);
+        kern<<<grid, kThreads, smem, s>>>(q, P + off, prof, out + off);
     }
     return cudaGetLastError();
 }
