@@ -330,27 +330,23 @@ namespace {
 constexpr int kRoiBlocks = 256;
 }
 
-__device__ __forceinline__ bool in_roi(const DevGeom &g, int ix, int iy, int iz, float r2, int zcut)
-{
-    if (iz < zcut || iz >= g.nz - zcut) return false;
-    const float x = ((float)ix - 0.5f * (float)(g.nx - 1)) * g.dx;
-    const float y = ((float)iy - 0.5f * (float)(g.ny - 1)) * g.dy;
-    return x * x + y * y <= r2;
-}
-
 __global__ void k_roi_partial(DevGeom g, const double *__restrict__ vol, double *partials,
                               float r2, int zcut)
 {
     __shared__ double ssum[256];
     __shared__ double scnt[256];
-    const size_t n = (size_t)g.nx * g.ny * g.nz;
+    // one (x, y) column per thread and pass, its z range in an inner loop
+    // (32-bit index arithmetic: nx ny < 2^31)
+    const int nxy = g.nx * g.ny;
     double s = 0.0, c = 0.0;
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
-         i += (size_t)gridDim.x * blockDim.x) {
-        const int ix = (int)(i % g.nx);
-        const int iy = (int)((i / g.nx) % g.ny);
-        const int iz = (int)(i / ((size_t)g.nx * g.ny));
-        if (in_roi(g, ix, iy, iz, r2, zcut)) { s += vol[i]; c += 1.0; }
+    for (int col = blockIdx.x * blockDim.x + threadIdx.x; col < nxy; col += gridDim.x * blockDim.x) {
+        const float x = ((float)(col % g.nx) - 0.5f * (float)(g.nx - 1)) * g.dx;
+        const float y = ((float)(col / g.nx) - 0.5f * (float)(g.ny - 1)) * g.dy;
+        if (x * x + y * y > r2) continue;
+        for (int iz = zcut; iz < g.nz - zcut; ++iz) {
+            s += vol[(size_t)iz * nxy + col];
+            c += 1.0;
+        }
     }
     ssum[threadIdx.x] = s;
     scnt[threadIdx.x] = c;
@@ -371,18 +367,26 @@ __global__ void k_roi_partial(DevGeom g, const double *__restrict__ vol, double 
 __global__ void k_hu(DevGeom g, const double *__restrict__ vol, const double *__restrict__ partials,
                      float *__restrict__ hu)
 {
-    __shared__ double mu_w;
-    if (threadIdx.x == 0) {
-        double s = 0.0, c = 0.0;
-        for (int b = 0; b < kRoiBlocks; ++b) { s += partials[2 * b]; c += partials[2 * b + 1]; }
-        mu_w = c > 0.0 ? s / c : 0.0;
-    }
+    // every CTA folds the partials the same way (thread b takes block b's,
+    // then a fixed tree), so all obtain the same mu_w
+    __shared__ double ssum[kRoiBlocks], scnt[kRoiBlocks];
+    static_assert(kRoiBlocks == 256, "one partial per thread");
+    ssum[threadIdx.x] = partials[2 * threadIdx.x];
+    scnt[threadIdx.x] = partials[2 * threadIdx.x + 1];
     __syncthreads();
-    const double m = mu_w;
+    for (int st = kRoiBlocks / 2; st > 0; st >>= 1) {
+        if ((int)threadIdx.x < st) {
+            ssum[threadIdx.x] += ssum[threadIdx.x + st];
+            scnt[threadIdx.x] += scnt[threadIdx.x + st];
+        }
+        __syncthreads();
+    }
+    const double m = scnt[0] > 0.0 ? ssum[0] / scnt[0] : 0.0;
+    const double k = m != 0.0 ? 1000.0 / m : 0.0;    // HU = 1000 (mu - mu_w) / mu_w
     const size_t n = (size_t)g.nx * g.ny * g.nz;
     for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
          i += (size_t)gridDim.x * blockDim.x)
-        hu[i] = m != 0.0 ? (float)(1000.0 * (vol[i] - m) / m) : 0.0f;
+        hu[i] = (float)((vol[i] - m) * k);
 }
 
 cudaError_t launch_hu(const DevGeom &g, const double *vol, float *hu, double *partials, float radius,
