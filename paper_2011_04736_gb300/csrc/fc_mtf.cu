@@ -4,14 +4,14 @@
 // tilted across the pixel grid, the line spread function is presampled on a
 // grid d / os fine, and the MTF is its Fourier magnitude.  The problem is
 // small (a 192 x 192 image, 32 os bins), so every kernel works in binary64
-// and in a fixed order (results reproducible bit for bit).
+// and in fixed orders (results reproducible bit for bit).
 //   k_mtf_slit  area fraction of each pixel inside |n . (x - c)| <= w / 2
 //               (the pixel's distribution of n . x is the convolution of two
 //               uniforms of widths d |cos a| and d |sin a|: a trapezoid);
 //   k_mtf_blur  I = sum_g c_g G_g (x) S, clamp-to-edge sampled Gaussians;
 //   k_mtf_bins  the presampling bin of every pixel of rows [N/4, 3N/4);
-//   k_mtf_lsf   one thread per bin: mean of I over that bin's pixels;
-//   k_mtf_dft   one thread per frequency k / (32 d), k = 0 .. 16 os.
+//   k_mtf_lsf   one CTA per bin: mean of I over that bin's pixels;
+//   k_mtf_dft   one CTA per frequency k / (32 d), k = 0 .. 16 os.
 #include <math.h>
 
 #include "fc_internal.cuh"
@@ -85,31 +85,47 @@ __global__ void k_mtf_bins(const __grid_constant__ MtfParams p, int *bins)
     bins[e] = (q >= 0.0 && q < (double)p.nb) ? (int)q : -1;
 }
 
-// mean of I over each bin, pixels taken in row-major order
-__global__ void k_mtf_lsf(const __grid_constant__ MtfParams p, const double *I, const int *bins,
-                          double *lsf)
+// mean of I over each bin: one CTA per bin; thread t sums the bin's pixels
+// t, t + 256, ... (row-major), then a fixed tree (reproducible bits)
+constexpr int kLsfThreads = 256;
+__global__ void __launch_bounds__(kLsfThreads)
+k_mtf_lsf(const __grid_constant__ MtfParams p, const double *I, const int *bins, double *lsf)
 {
-    const int b = blockIdx.x * blockDim.x + threadIdx.x;
-    if (b >= p.nb) return;
+    __shared__ double st[kLsfThreads];
+    __shared__ int sc[kLsfThreads];
+    const int b = blockIdx.x;
     const int nr = p.row1 - p.row0;
     double tot = 0.0;
     int cnt = 0;
-    for (int e = 0; e < nr * p.n; ++e)
+    for (int e = threadIdx.x; e < nr * p.n; e += kLsfThreads)
         if (bins[e] == b) {
             tot += I[(size_t)(p.row0 + e / p.n) * p.n + e % p.n];
             ++cnt;
         }
-    lsf[b] = cnt ? tot / cnt : 0.0;
+    st[threadIdx.x] = tot;
+    sc[threadIdx.x] = cnt;
+    __syncthreads();
+    for (int h = kLsfThreads / 2; h > 0; h >>= 1) {
+        if ((int)threadIdx.x < h) {
+            st[threadIdx.x] += st[threadIdx.x + h];
+            sc[threadIdx.x] += sc[threadIdx.x + h];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) lsf[b] = sc[0] ? st[0] / sc[0] : 0.0;
 }
 
-__global__ void k_mtf_dft(const __grid_constant__ MtfParams p, const double *lsf, double *freq,
-                          double *mtf)
+// one CTA per frequency: thread t takes bins t, t + 128, ..., then a fixed
+// tree of the real part, the imaginary part and the LSF sum
+constexpr int kDftThreads = 128;
+__global__ void __launch_bounds__(kDftThreads)
+k_mtf_dft(const __grid_constant__ MtfParams p, const double *lsf, double *freq, double *mtf)
 {
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k > p.nb / 2) return;
+    __shared__ double sre[kDftThreads], sim[kDftThreads], ssum[kDftThreads];
+    const int k = blockIdx.x;
     const double f = k / (p.nb * p.delta);           // 1/cm
     double re = 0.0, im = 0.0, sum = 0.0;
-    for (int b = 0; b < p.nb; ++b) {
+    for (int b = threadIdx.x; b < p.nb; b += kDftThreads) {
         const double sb = (b - 0.5 * p.nb + 0.5) * p.delta;
         double sn, cs;
         sincospi(2.0 * f * sb, &sn, &cs);
@@ -117,8 +133,22 @@ __global__ void k_mtf_dft(const __grid_constant__ MtfParams p, const double *lsf
         im = fma(-lsf[b], sn, im);
         sum += lsf[b];
     }
-    freq[k] = f / 10.0;
-    mtf[k] = sqrt(re * re + im * im) / fabs(sum);
+    sre[threadIdx.x] = re;
+    sim[threadIdx.x] = im;
+    ssum[threadIdx.x] = sum;
+    __syncthreads();
+    for (int h = kDftThreads / 2; h > 0; h >>= 1) {
+        if ((int)threadIdx.x < h) {
+            sre[threadIdx.x] += sre[threadIdx.x + h];
+            sim[threadIdx.x] += sim[threadIdx.x + h];
+            ssum[threadIdx.x] += ssum[threadIdx.x + h];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        freq[k] = f / 10.0;
+        mtf[k] = sqrt(sre[0] * sre[0] + sim[0] * sim[0]) / fabs(ssum[0]);
+    }
 }
 
 cudaError_t launch_mtf(const MtfParams &p, double *work, double *freq, double *mtf, cudaStream_t s)
@@ -130,8 +160,8 @@ cudaError_t launch_mtf(const MtfParams &p, double *work, double *freq, double *m
     k_mtf_slit<<<(np + 255) / 256, 256, 0, s>>>(p, S);
     k_mtf_blur<<<(np + 255) / 256, 256, 0, s>>>(p, S, I);
     k_mtf_bins<<<(nb_px + 255) / 256, 256, 0, s>>>(p, bins);
-    k_mtf_lsf<<<(p.nb + 63) / 64, 64, 0, s>>>(p, I, bins, lsf);
-    k_mtf_dft<<<(p.nb / 2 + 1 + 63) / 64, 64, 0, s>>>(p, lsf, freq, mtf);
+    k_mtf_lsf<<<p.nb, kLsfThreads, 0, s>>>(p, I, bins, lsf);
+    k_mtf_dft<<<p.nb / 2 + 1, kDftThreads, 0, s>>>(p, lsf, freq, mtf);
     return cudaGetLastError();
 }
 
