@@ -150,9 +150,12 @@ __device__ __forceinline__ bool trace_ray(const ProjParams &p, int iu, int iv, i
                                     min((by + 1) * kBrick, ny) - 1);
                     int jz = clampi((int)floorf((qz - g.loz) * g.idz), bz * kBrick,
                                     min((bz + 1) * kBrick, nz) - 1);
-                    float tfx = plane_t(jx + ux, vx, bx_, sx);
-                    float tfy = plane_t(jy + uy, vy, by_, sy);
-                    float tfz = plane_t(jz + uz, vz, bz_, sz);
+                    // next plane index per axis; an axis that is stepped
+                    // has a nonzero direction, so its crossing is a plain fma
+                    int fx = jx + ux, fy = jy + uy, fz = jz + uz;
+                    float tfx = plane_t(fx, vx, bx_, sx);
+                    float tfy = plane_t(fy, vy, by_, sy);
+                    float tfz = plane_t(fz, vz, bz_, sz);
                     int id = jz * nxy + jy * nx + jx;
                     int lab = __ldg(p.labels + id);
                     if (lab != cur) {
@@ -164,11 +167,11 @@ __device__ __forceinline__ bool trace_ray(const ProjParams &p, int iu, int iv, i
                         const float tn = fminf(tfx, fminf(tfy, tfz));
                         if (tn >= t_exit) break;
                         if (tfx == tn) {
-                            jx += sx; id += sx; tfx = plane_t(jx + ux, vx, bx_, sx);
+                            fx += sx; id += sx; tfx = fmaf((float)fx, vx, bx_);
                         } else if (tfy == tn) {
-                            jy += sy; id += sy * nx; tfy = plane_t(jy + uy, vy, by_, sy);
+                            fy += sy; id += sy * nx; tfy = fmaf((float)fy, vy, by_);
                         } else {
-                            jz += sz; id += sz * nxy; tfz = plane_t(jz + uz, vz, bz_, sz);
+                            fz += sz; id += sz * nxy; tfz = fmaf((float)fz, vz, bz_);
                         }
                         lab = __ldg(p.labels + id);
                         if (lab != cur) {
@@ -185,15 +188,15 @@ __device__ __forceinline__ bool trace_ray(const ProjParams &p, int iu, int iv, i
                 if (tcx == tmin) {
                     bx += sx;
                     inside = bx >= 0 && bx < nbx;
-                    tcx = plane_t(ux ? min((bx + 1) * kBrick, nx) : bx * kBrick, vx, bx_, sx);
+                    tcx = fmaf((float)(ux ? min((bx + 1) * kBrick, nx) : bx * kBrick), vx, bx_);
                 } else if (tcy == tmin) {
                     by += sy;
                     inside = by >= 0 && by < nby;
-                    tcy = plane_t(uy ? min((by + 1) * kBrick, ny) : by * kBrick, vy, by_, sy);
+                    tcy = fmaf((float)(uy ? min((by + 1) * kBrick, ny) : by * kBrick), vy, by_);
                 } else {
                     bz += sz;
                     inside = bz >= 0 && bz < nbz;
-                    tcz = plane_t(uz ? min((bz + 1) * kBrick, nz) : bz * kBrick, vz, bz_, sz);
+                    tcz = fmaf((float)(uz ? min((bz + 1) * kBrick, nz) : bz * kBrick), vz, bz_);
                 }
                 if (!inside) break;
             }
