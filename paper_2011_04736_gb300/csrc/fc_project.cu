@@ -113,10 +113,15 @@ __device__ __forceinline__ bool trace_ray(const ProjParams &p, int iu, int iv, i
             const int nbx = (nx + kBrick - 1) / kBrick, nby = (ny + kBrick - 1) / kBrick;
             const int nbz = (nz + kBrick - 1) / kBrick;
             int bx = ix0 / kBrick, by = iy0 / kBrick, bz = iz0 / kBrick;
+            int bi = (bz * nby + by) * nbx + bx;       // brick index, kept incrementally
             // coarse crossing: far face of the current brick along the ray
-            float tcx = plane_t(ux ? min((bx + 1) * kBrick, nx) : bx * kBrick, vx, bx_, sx);
-            float tcy = plane_t(uy ? min((by + 1) * kBrick, ny) : by * kBrick, vy, by_, sy);
-            float tcz = plane_t(uz ? min((bz + 1) * kBrick, nz) : bz * kBrick, vz, bz_, sz);
+            // (plane index cp*, kept incrementally)
+            int cpx = ux ? min((bx + 1) * kBrick, nx) : bx * kBrick;
+            int cpy = uy ? min((by + 1) * kBrick, ny) : by * kBrick;
+            int cpz = uz ? min((bz + 1) * kBrick, nz) : bz * kBrick;
+            float tcx = plane_t(cpx, vx, bx_, sx);
+            float tcy = plane_t(cpy, vy, by_, sy);
+            float tcz = plane_t(cpz, vz, bz_, sz);
             int cur = __ldg(p.labels + (iz0 * ny + iy0) * nx + ix0);
             float t_run = t_in, t_cur = t_in;
             // Coarse passes: each advances one brick index by one step along
@@ -128,7 +133,7 @@ __device__ __forceinline__ bool trace_ray(const ProjParams &p, int iu, int iv, i
             for (int cb = nbx + nby + nbz + 3; cb > 0; --cb) {
                 const float tmin = fminf(tcx, fminf(tcy, tcz));
                 const float t_exit = fmaxf(tmin, t_cur);
-                const int bl = __ldg(p.bricks + (bz * nby + by) * nbx + bx);
+                const int bl = __ldg(p.bricks + bi);
                 if (bl != kMixed) {
                     if (bl != cur) {
                         add_run(L, cur, t_cur - t_run);
@@ -185,18 +190,26 @@ __device__ __forceinline__ bool trace_ray(const ProjParams &p, int iu, int iv, i
                 // step to the next brick along the axis of the nearest face
                 t_cur = t_exit;
                 bool inside;
+                // (a stepped axis has a nonzero direction; leaving the last
+                // brick ends the walk, so the clip to n only matters going up)
                 if (tcx == tmin) {
                     bx += sx;
+                    bi += sx;
                     inside = bx >= 0 && bx < nbx;
-                    tcx = fmaf((float)(ux ? min((bx + 1) * kBrick, nx) : bx * kBrick), vx, bx_);
+                    cpx = ux ? min(cpx + kBrick, nx) : cpx - kBrick;
+                    tcx = fmaf((float)cpx, vx, bx_);
                 } else if (tcy == tmin) {
                     by += sy;
+                    bi += sy * nbx;
                     inside = by >= 0 && by < nby;
-                    tcy = fmaf((float)(uy ? min((by + 1) * kBrick, ny) : by * kBrick), vy, by_);
+                    cpy = uy ? min(cpy + kBrick, ny) : cpy - kBrick;
+                    tcy = fmaf((float)cpy, vy, by_);
                 } else {
                     bz += sz;
+                    bi += sz * nbx * nby;
                     inside = bz >= 0 && bz < nbz;
-                    tcz = fmaf((float)(uz ? min((bz + 1) * kBrick, nz) : bz * kBrick), vz, bz_);
+                    cpz = uz ? min(cpz + kBrick, nz) : cpz - kBrick;
+                    tcz = fmaf((float)cpz, vz, bz_);
                 }
                 if (!inside) break;
             }
