@@ -195,20 +195,20 @@ __device__ __forceinline__ bool trace_ray(const ProjParams &p, int iu, int iv, i
                 if (tcx == tmin) {
                     bx += sx;
                     bi += sx;
-                    inside = bx >= 0 && bx < nbx;
-                    cpx = ux ? min(cpx + kBrick, nx) : cpx - kBrick;
+                    inside = (unsigned)bx < (unsigned)nbx;
+                    cpx = min(cpx + kBrick * sx, nx);
                     tcx = fmaf((float)cpx, vx, bx_);
                 } else if (tcy == tmin) {
                     by += sy;
                     bi += sy * nbx;
-                    inside = by >= 0 && by < nby;
-                    cpy = uy ? min(cpy + kBrick, ny) : cpy - kBrick;
+                    inside = (unsigned)by < (unsigned)nby;
+                    cpy = min(cpy + kBrick * sy, ny);
                     tcy = fmaf((float)cpy, vy, by_);
                 } else {
                     bz += sz;
                     bi += sz * nbx * nby;
-                    inside = bz >= 0 && bz < nbz;
-                    cpz = uz ? min(cpz + kBrick, nz) : cpz - kBrick;
+                    inside = (unsigned)bz < (unsigned)nbz;
+                    cpz = min(cpz + kBrick * sz, nz);
                     tcz = fmaf((float)cpz, vz, bz_);
                 }
                 if (!inside) break;
