@@ -86,6 +86,31 @@ def test_primary_ragged_random_labels(fc, orc):
     assert rel.max() <= REL_T, rel.max()
 
 
+def test_primary_thin_slab_band_edges(fc, orc):
+    """A 3-slice slab seen by a 45-row detector: only a band of rows can meet
+    the voxels, so the projector traces 8-row blocks around it and a store
+    kernel writes the other rows.  Every ray is checked against the oracle,
+    and rays that miss the voxels must give exactly T = 1."""
+    wl = W.scaled(W.WORKLOADS["small_kv"], n_u=70, n_v=45, n_angles=9, nx=24, ny=20, nz=3,
+                  dx=0.25, dy=0.25, dz=0.1, du=0.12, dv=0.05)
+    g = wl.geom
+    rng = np.random.default_rng(22)
+    lab = rng.integers(0, 7, size=(g.nz, g.ny, g.nx)).astype(np.uint8)
+    sc = _scanner(fc, wl, lab)
+    try:
+        T = _project(fc, sc, fc.FC_OUT_PRIMARY)
+    finally:
+        sc.close()
+    w, d = wl.spectrum()
+    Tr = orc.project_T(g, lab, w, d, wl.mu())
+    rel = np.abs(T - Tr) / Tr
+    assert rel.max() <= REL_T, rel.max()
+    miss = Tr == 1.0
+    rows_hit = np.where((~miss).any(axis=(0, 2)))[0]
+    assert 0 < len(rows_hit) < g.n_v // 2          # a band, not the whole detector
+    assert np.all(T[miss] == 1.0)
+
+
 @pytest.fixture(scope="module")
 def small_kv_ref(orc):
     wl = W.WORKLOADS["small_kv"]
