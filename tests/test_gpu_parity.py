@@ -111,6 +111,35 @@ def test_primary_thin_slab_band_edges(fc, orc):
     assert np.all(T[miss] == 1.0)
 
 
+def test_tiny_geometry_and_empty_angle_range(fc, orc):
+    """A volume smaller than one 8-voxel brick on every axis (5 x 3 x 2, random
+    labels) seen by a 3 x 4 detector: every ray's T and the reconstruction
+    (a 3-column ramp filter) against the oracle; an empty angle range
+    leaves the output untouched."""
+    wl = W.scaled(W.WORKLOADS["small_kv"], n_u=3, n_v=4, n_angles=5, nx=5, ny=3, nz=2,
+                  dx=0.5, dy=0.5, dz=0.5, du=0.3, dv=0.3)
+    g = wl.geom
+    lab = np.random.default_rng(23).integers(0, 7, size=(g.nz, g.ny, g.nx)).astype(np.uint8)
+    sc = _scanner(fc, wl, lab)
+    try:
+        T = _project(fc, sc, fc.FC_OUT_PRIMARY)
+        out = torch.full((1, g.n_v, g.n_u), -7.0, dtype=torch.float32, device="cuda")
+        fc.fc_project(sc.h, 2, 0, fc.FC_OUT_PRIMARY, out)
+        torch.cuda.synchronize()
+        assert bool(torch.all(out == -7.0))
+    finally:
+        sc.close()
+    w, d = wl.spectrum()
+    Tr = orc.project_T(g, lab, w, d, wl.mu())
+    assert (Tr < 1.0).all()                       # every ray crosses the voxels
+    rel = np.abs(T - Tr) / Tr
+    assert rel.max() <= REL_T, rel.max()
+    counts = orc.intensity(Tr, wl.psf_sigma_px, wl.scatter_sigma_px, wl.spr, wl.n0).astype(np.float32)
+    vol, _ = _recon_gpu(fc, wl, counts, lab)
+    vref = orc.fdk(g, counts.astype(np.float64), orc.i_flood(wl.n0, wl.spr))
+    assert np.max(np.abs(vol - vref)) <= 5e-4 * np.max(np.abs(vref)), np.max(np.abs(vol - vref))
+
+
 @pytest.fixture(scope="module")
 def small_kv_ref(orc):
     wl = W.WORKLOADS["small_kv"]
