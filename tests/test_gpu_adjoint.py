@@ -82,3 +82,37 @@ def test_cnr_autograd_function(fc):
         assert _rel(rho.grad.cpu().numpy(), 2.0 * gr.cpu().numpy()) <= 1e-5
     finally:
         sc.close()
+
+
+def test_cnr_gradient_full_size_directional(fc):
+    """At the benchmarked size (128^2 x 32 voxels, 180 projections of 512 x
+    384, 30 bins) the FP64 oracle is too slow, so a property that holds at
+    any size is checked instead: central differences of J along the density
+    gradient and along the logit gradient match the directional derivatives
+    the adjoint gives (the density step is applied in binary32, so the
+    expectation uses the densities actually applied)."""
+    wl = W.WORKLOADS["adjoint_kv"]
+    inp = W.adjoint_inputs(wl)
+    sc = fc.Scanner(wl, labels=inp["labels"], noise=False)
+    try:
+        rho = torch.from_numpy(inp["rho"]).cuda()
+        z = torch.from_numpy(inp["z"]).cuda()
+
+        def J_of(logits, r):
+            return fc.fc_cnr_grad(sc.h, logits, inp["D"], inp["rho0"], r, z, inp["rois"], grads=False)[0]
+
+        J, gl, _, gr = fc.fc_cnr_grad(sc.h, inp["logits"], inp["D"], inp["rho0"], rho, z, inp["rois"])
+        g = gr.double()
+        step = 0.01 * g / torch.linalg.norm(g)
+        rp, rm = (rho.double() + step).float(), (rho.double() - step).float()
+        expect = float(torch.sum(g * (rp.double() - rm.double()))) / 2.0
+        got = (J_of(inp["logits"], rp) - J_of(inp["logits"], rm)) / 2.0
+        assert abs(got - expect) <= 1e-3 * abs(expect), (got, expect)
+
+        gl = np.asarray(gl, dtype=np.float64)
+        dl = 0.01 * gl / np.linalg.norm(gl)
+        expect = float(gl @ dl)
+        got = (J_of(inp["logits"] + dl, rho) - J_of(inp["logits"] - dl, rho)) / 2.0
+        assert abs(got - expect) <= 1e-3 * abs(expect), (got, expect)
+    finally:
+        sc.close()
