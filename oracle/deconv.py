@@ -39,13 +39,13 @@ def clamp_blur_matrix(n, sigma):
 
 
 def forward(X, Bv, Bu):
-    """H X for a stack X [..., n_v, n_u]."""
-    return np.einsum("vw,...wu,xu->...vx", Bv, X, Bu)
+    """H X = B_v X B_u^T for a stack X [..., n_v, n_u] (two matrix products)."""
+    return np.matmul(np.matmul(Bv, X), Bu.T)
 
 
 def adjoint(Y, Bv, Bu):
-    """H^T Y for a stack Y [..., n_v, n_u]."""
-    return np.einsum("wv,...wu,ux->...vx", Bv, Y, Bu)
+    """H^T Y = B_v^T Y B_u for a stack Y [..., n_v, n_u] (two matrix products)."""
+    return np.matmul(np.matmul(Bv.T, Y), Bu)
 
 
 def richardson_lucy(d, sigma, n_iter, floor=1e-12):
