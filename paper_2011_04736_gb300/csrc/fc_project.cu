@@ -580,7 +580,8 @@ cudaError_t launch_dose(const ProjParams &p, const DoseParams &d, double *part,
     return cudaGetLastError();
 }
 
-// One thread per 8x8x8 brick: its single label, or kMixed; flags any label
+// One warp per 8x8x8 brick (lane l takes voxels l, l + 32, ... of the
+// brick, clipped to the grid): its single label, or kMixed; flags any label
 // >= n_mat.
 __global__ void k_brick_map(const uint8_t *__restrict__ lab, uint8_t *__restrict__ bricks, int nx,
                             int ny, int nz, int n_mat, unsigned int *bad)
@@ -588,21 +589,27 @@ __global__ void k_brick_map(const uint8_t *__restrict__ lab, uint8_t *__restrict
     const int nbx = (nx + kBrick - 1) / kBrick, nby = (ny + kBrick - 1) / kBrick;
     const int nbz = (nz + kBrick - 1) / kBrick;
     const int nb = nbx * nby * nbz;
-    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nb; b += gridDim.x * blockDim.x) {
+    const int lane = threadIdx.x & 31;
+    const int warps = (gridDim.x * blockDim.x) >> 5;
+    for (int b = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; b < nb; b += warps) {
         const int bx = b % nbx, by = (b / nbx) % nby, bz = b / (nbx * nby);
-        const int x1 = min((bx + 1) * kBrick, nx), y1 = min((by + 1) * kBrick, ny);
-        const int z1 = min((bz + 1) * kBrick, nz);
-        const int first = lab[((size_t)(bz * kBrick) * ny + by * kBrick) * nx + bx * kBrick];
+        const int x0 = bx * kBrick, y0 = by * kBrick, z0 = bz * kBrick;
+        const int first = lab[((size_t)z0 * ny + y0) * nx + x0];
         bool uniform = true, badlab = false;
-        for (int z = bz * kBrick; z < z1; ++z)
-            for (int y = by * kBrick; y < y1; ++y)
-                for (int x = bx * kBrick; x < x1; ++x) {
-                    const int v = lab[((size_t)z * ny + y) * nx + x];
-                    uniform = uniform && v == first;
-                    badlab = badlab || v >= n_mat;
-                }
-        if (badlab) atomicOr(bad, 1u);
-        bricks[b] = uniform ? (uint8_t)first : (uint8_t)kMixed;
+        for (int v = lane; v < kBrick * kBrick * kBrick; v += 32) {
+            const int x = x0 + v % kBrick, y = y0 + (v / kBrick) % kBrick, z = z0 + v / (kBrick * kBrick);
+            if (x < nx && y < ny && z < nz) {
+                const int l = lab[((size_t)z * ny + y) * nx + x];
+                uniform = uniform && l == first;
+                badlab = badlab || l >= n_mat;
+            }
+        }
+        uniform = __all_sync(0xffffffffu, uniform);
+        badlab = __any_sync(0xffffffffu, badlab);
+        if (lane == 0) {
+            if (badlab) atomicOr(bad, 1u);
+            bricks[b] = uniform ? (uint8_t)first : (uint8_t)kMixed;
+        }
     }
 }
 
@@ -611,7 +618,7 @@ cudaError_t launch_brick_map(const uint8_t *labels, uint8_t *bricks, int nx, int
 {
     const int nb = ((nx + kBrick - 1) / kBrick) * ((ny + kBrick - 1) / kBrick) *
                    ((nz + kBrick - 1) / kBrick);
-    const int blocks = (nb + 127) / 128 < 152 * 8 ? (nb + 127) / 128 : 152 * 8;
+    const int blocks = (nb + 3) / 4 < 152 * 16 ? (nb + 3) / 4 : 152 * 16;   // 4 warps per block
     k_brick_map<<<blocks, 128, 0, s>>>(labels, bricks, nx, ny, nz, n_mat, bad);
     return cudaGetLastError();
 }
