@@ -941,7 +941,7 @@ int fc_dose_estimate(fc_handle *h, int angle_begin, int angle_count, const doubl
     double *part = h->d_dose, *res = h->d_dose + n_part;
     auto *count = reinterpret_cast<unsigned long long *>(res + n_out);
     {
-        Trace t(h, FC_K_DOSE, 3, s);
+        Trace t(h, FC_K_DOSE, 4, s);   // label count, partials, fold, final
         FC_CK(fc::launch_dose(p, d, part, count, res, s));
         t.end();
     }

@@ -506,11 +506,30 @@ k_label_count(const uint8_t *__restrict__ lab, size_t n, int n_mat, unsigned lon
         atomicAdd(&count[threadIdx.x], (unsigned long long)c[threadIdx.x]);
 }
 
-// D0(E) = E (mu_en/mu)_w(E) sum_i (1 - exp(-mu_i(E) x_i)) / (N_i M) and
-// Dp = sum_E phi(E) D0(E) (Sec. II.H); out = [D0(E_0) .. D0(E_{n-1}), Dp].
+// Sum over the partial rows for bin blockIdx.x: thread t takes rows t,
+// t + 256, ..., then a fixed tree (reproducible); the sum goes to out[e].
 __global__ void __launch_bounds__(256)
-k_dose_final(const __grid_constant__ DoseParams d, const double *__restrict__ part,
-             const unsigned long long *__restrict__ count, double *__restrict__ out)
+k_dose_fold(const __grid_constant__ DoseParams d, const double *__restrict__ part, double *__restrict__ out)
+{
+    __shared__ double s[256];
+    const int e = blockIdx.x;
+    double a = 0.0;
+    for (int b = threadIdx.x; b < d.n_part; b += 256) a += part[(size_t)b * d.n_e + e];
+    s[threadIdx.x] = a;
+    __syncthreads();
+    for (int h = 128; h > 0; h >>= 1) {
+        if ((int)threadIdx.x < h) s[threadIdx.x] += s[threadIdx.x + h];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[e] = s[0];
+}
+
+// D0(E) = E (mu_en/mu)_w(E) sum_i (1 - exp(-mu_i(E) x_i)) / (N_i M) and
+// Dp = sum_E phi(E) D0(E) (Sec. II.H); out = [D0(E_0) .. D0(E_{n-1}), Dp],
+// the sums over rays already in out[0 .. n_e).
+__global__ void __launch_bounds__(256)
+k_dose_final(const __grid_constant__ DoseParams d, const unsigned long long *__restrict__ count,
+             double *__restrict__ out)
 {
     __shared__ double s[kMaxBins];
     const int e = threadIdx.x;
@@ -518,9 +537,7 @@ k_dose_final(const __grid_constant__ DoseParams d, const double *__restrict__ pa
     for (int m = 0; m < d.n_mat; ++m) mass += (double)count[m] * d.rho[m];
     mass *= d.voxel_cm3;
     if (e < d.n_e) {
-        double a = 0.0;
-        for (int b = 0; b < d.n_part; ++b) a += part[(size_t)b * d.n_e + e];
-        const double d0 = kGyGramPerKev * d.e_kev[e] * d.muen[e] * a / (d.n_rays * mass);
+        const double d0 = kGyGramPerKev * d.e_kev[e] * d.muen[e] * out[e] / (d.n_rays * mass);
         out[e] = d0;
         s[e] = d.phi[e] * d0;
     }
@@ -576,7 +593,8 @@ cudaError_t launch_dose(const ProjParams &p, const DoseParams &d, double *part,
         k_dose_partial<4><<<d.n_part, blk, 0, s>>>(p, part, r0, r1);
     else
         k_dose_partial<8><<<d.n_part, blk, 0, s>>>(p, part, r0, r1);
-    k_dose_final<<<1, 256, 0, s>>>(d, part, count, out);
+    k_dose_fold<<<d.n_e, 256, 0, s>>>(d, part, out);
+    k_dose_final<<<1, 256, 0, s>>>(d, count, out);
     return cudaGetLastError();
 }
 
