@@ -93,13 +93,16 @@ typedef struct fc_spectrum_detector {
 } fc_spectrum_detector;
 
 /* Create a handle bound to CUDA device `device`.  *out receives it.
+ * (Library set-up: the paper has no counterpart.)
  * Errors: FC_EINVAL (null out, bad device), FC_ECUDA. */
 int fc_create(fc_handle **out, int device);
 
-/* Release the handle and every device buffer it owns.  NULL is accepted. */
+/* Release the handle and every device buffer it owns.  NULL is accepted.
+ * (Library set-up: the paper has no counterpart.) */
 int fc_destroy(fc_handle *h);
 
-/* Message describing the last failure on this thread ("" if none). */
+/* Message describing the last failure on this thread ("" if none).
+ * (Error reporting: the paper has no counterpart.) */
 const char *fc_last_error(void);
 
 /* Scan geometry (Sec. II.F raytracing set-up; Sec. II.G FDK).  Copies *g.
@@ -125,9 +128,12 @@ int fc_set_spectrum_detector(fc_handle *h, const fc_spectrum_detector *s);
 
 /* Simulate projections angle_begin .. angle_begin + angle_count - 1:
  *   T = sum_E w D exp(-sum_m mu_m(E) L_m) / sum_E w D  (projector with the
- *       energy integral fused; L_m = path length in material m, Siddon),
- *   I = N0 (G_psf (x) T + SPR G_scatter (x) T)  (separable, clamp-to-edge),
- *   K = Poisson(I) (Philox4x32-10 counters (iu, iv, k, j), if noise is on).
+ *       energy integral fused; L_m = path length in material m, Siddon:
+ *       Sec. II.F raytracing and the I_f equation),
+ *   I = N0 (G_psf (x) T + SPR G_scatter (x) T)  (separable, clamp-to-edge:
+ *       Sec. II.B/G optical spread, Sec. II.E scatter),
+ *   K = Poisson(I) (Philox4x32-10 counters (iu, iv, k, j), if noise is on:
+ *       Sec. II.G-H).
  * Results stay in the handle for fc_reconstruct; `out_kind` selects which
  * one (if any) is also copied to `out` ([angle_count][n_v][n_u] float, in
  * host or device memory per `out_where`).
@@ -237,7 +243,7 @@ int fc_poisson(const float *lam, float *counts, int n_angles, int n_v, int n_u,
 
 /* Per-material path lengths of the rays of projections angle_begin ..
  * angle_begin + angle_count - 1 (the traversal of fc_project without the
- * energy integral), written to the device buffer L
+ * energy integral; Sec. II.F raytracing), written to the device buffer L
  * ([angle_count][n_v][n_u][n_mat] float, cm).  Errors: FC_ESTATE, FC_EINVAL,
  * FC_ECUDA. */
 int fc_project_lengths(fc_handle *h, int angle_begin, int angle_count, float *L,
@@ -271,9 +277,10 @@ int fc_dose_estimate(fc_handle *h, int angle_begin, int angle_count, const doubl
  * Host arithmetic only.  Errors: FC_EINVAL, FC_ESTATE (no geometry). */
 int fc_fluence_for_dose(const fc_handle *h, double dose_gy, double dp_gy, double *n0);
 
-/* Kernel-time tracing.  While enabled, every kernel the handle launches is
- * bracketed by CUDA events recorded on the launching stream.  Kernel ids: */
-#define FC_K_PROJECT     0  /* projector + energy integral */
+/* Kernel-time tracing (instrumentation: the paper has no counterpart).
+ * While enabled, every kernel the handle launches is bracketed by CUDA
+ * events recorded on the launching stream.  Kernel ids: */
+#define FC_K_PROJECT     0  /* projector + energy integral (traced rows + T = 1 fill) */
 #define FC_K_BLUR_ROWS   1  /* detector blur, band matrices + row pass */
 #define FC_K_BLUR_COLS   2  /* detector blur, column pass */
 #define FC_K_FDK_FILTER  3  /* log, cosine weight, Ram-Lak filter */
@@ -284,7 +291,7 @@ int fc_fluence_for_dose(const fc_handle *h, double dose_gy, double dp_gy, double
 #define FC_K_SURROGATE_EVAL  8  /* surrogate inference (fc_surrogate_eval) */
 #define FC_K_SURROGATE_TRAIN 9  /* surrogate training steps (4 kernels per step) */
 #define FC_K_ENERGY_SUM     10  /* exact energy sum from path lengths */
-#define FC_K_DOSE           11  /* dose estimate (three kernels) */
+#define FC_K_DOSE           11  /* dose estimate (four kernels) */
 #define FC_K_GROUP_BLUR     12  /* energy-group model: scatter profile + per-group blur (2 kernels) */
 #define FC_K_DECONV         13  /* Richardson-Lucy deconvolution (1 + n_iter kernels) */
 #define FC_K_COUNT          14
@@ -366,8 +373,8 @@ int fc_surrogate_eval(fc_handle *h, const float *L, int64_t n, float *lnT, int64
 int fc_surrogate_project(fc_handle *h, int angle_begin, int angle_count, float *out,
                          int out_where, void *stream);
 
-/* ln T of n rays from their path lengths by the exact energy sum (the
- * projector's epilogue as a separate pass).  Errors: FC_ESTATE, FC_EINVAL,
+/* ln T of n rays from their path lengths by the exact energy sum (the I_f
+ * equation of Sec. II.F; the projector's epilogue as a separate pass).  Errors: FC_ESTATE, FC_EINVAL,
  * FC_ECUDA. */
 int fc_energy_sum_lengths(fc_handle *h, const float *L, int64_t n, float *lnT, void *stream);
 
