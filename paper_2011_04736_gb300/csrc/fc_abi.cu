@@ -554,8 +554,11 @@ static int fill_proj_params(fc_handle *h, int a0, int na, fc::ProjParams *p)
 // element `off` of the projection buffers: tensor-core row and column passes
 // through the handle's intermediates (direct f32 passes for radii beyond the
 // tensor-core path); `in` and `out` may alias.
+// one_lo, one_hi: when one_hi >= 0, every row of `in` outside [one_lo,
+// one_hi) is all ones (the projector's primary on rows that cannot meet the
+// voxels); the tensor-core row pass then skips those rows' tiles.
 static int run_blur(fc_handle *h, const float *in, float *out, size_t off, int n, double psf,
-                    double sc, double n0, double spr, cudaStream_t s)
+                    double sc, double n0, double spr, cudaStream_t s, int one_lo = 0, int one_hi = -1)
 {
     fc::BlurParams b;
     memset(&b, 0, sizeof(b));
@@ -586,9 +589,9 @@ static int run_blur(fc_handle *h, const float *in, float *out, size_t off, int n
         return FC_OK;
     }
     {
-        Trace t(h, FC_K_BLUR_ROWS, 2, s);
+        Trace t(h, FC_K_BLUR_ROWS, fc::blur_tc_rows_launches(b, one_lo, one_hi), s);
         FC_CK(fc::launch_blur_tc_rows(b, in, h->d_tp + off, h->d_ts + off, h->d_hankel,
-                                      h->d_blur_err, n, s));
+                                      h->d_blur_err, n, s, one_lo, one_hi));
         t.end();
     }
     {
@@ -827,6 +830,10 @@ int fc_project(fc_handle *h, int angle_begin, int angle_count, int out_kind, flo
         t.end();
     }
     if (out_kind == FC_OUT_PRIMARY) return angle_count ? copy_out(out, out_where, h->d_T + off, bytes, s) : FC_OK;
+    // rows outside [v_hit_lo, v_hit_hi] hold T = 1 exactly (their rays cannot
+    // meet the voxels)
+    const int one_lo = p.v_hit_lo > 0 ? p.v_hit_lo : 0;
+    const int one_hi = (p.v_hit_hi < h->g.n_v - 1 ? p.v_hit_hi : h->g.n_v - 1) + 1;
     const bool noise = (out_kind != FC_OUT_INTENSITY) && h->noise;
     if (h->n_groups) {
         rc = run_groups(h, angle_begin, angle_count, s);
@@ -844,7 +851,8 @@ int fc_project(fc_handle *h, int angle_begin, int angle_count, int out_kind, flo
     if (h->noise_order == FC_NOISE_BEFORE_PSF) {
         // Sec. II.G order: counts drawn from the scatter-added rate, then the
         // optical spread applied to the counts
-        rc = run_blur(h, h->d_T + off, h->d_counts + off, off, angle_count, 0.0, h->sc, h->n0, h->spr, s);
+        rc = run_blur(h, h->d_T + off, h->d_counts + off, off, angle_count, 0.0, h->sc, h->n0, h->spr, s,
+                      one_lo, one_hi);
         if (rc) return rc;
         if (out_kind == FC_OUT_INTENSITY) {
             h->has_counts = true;
@@ -862,7 +870,8 @@ int fc_project(fc_handle *h, int angle_begin, int angle_count, int out_kind, flo
         rc = run_blur(h, h->d_counts + off, h->d_counts + off, off, angle_count, h->psf, 0.0, 1.0, 0.0, s);
         if (rc) return rc;
     } else {
-        rc = run_blur(h, h->d_T + off, h->d_counts + off, off, angle_count, h->psf, h->sc, h->n0, h->spr, s);
+        rc = run_blur(h, h->d_T + off, h->d_counts + off, off, angle_count, h->psf, h->sc, h->n0, h->spr, s,
+                      one_lo, one_hi);
         if (rc) return rc;
         if (noise) {
             Trace t(h, FC_K_NOISE, 1, s);

@@ -145,11 +145,11 @@ struct Tile {
     size_t img;
 };
 
-__device__ __forceinline__ Tile tile_of(long long t, int n_m, int n_x, size_t plane)
+__device__ __forceinline__ Tile tile_of(long long t, int n_m, int n_x, size_t plane, int x_off = 0)
 {
     Tile r;
     r.m0 = (int)(t % n_m) * 128;
-    r.x0 = (int)((t / n_m) % n_x) * kN;
+    r.x0 = ((int)((t / n_m) % n_x) + x_off) * kN;
     r.img = (size_t)(t / ((long long)n_m * n_x)) * plane;
     return r;
 }
@@ -213,7 +213,7 @@ k_blur_rows_tc(const __grid_constant__ TcBlurParams p, int n_stage)
     const uint32_t wlo = 2u * kN * (uint32_t)kw;          // hi -> lo block
     const uint32_t stage_bytes = 2u * wlo;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int n_m = (p.n_u + 127) / 128, n_x = (p.n_v + kN - 1) / kN;
+    const int n_m = (p.n_u + 127) / 128, n_x = p.x_cnt;   // line tiles [x_off, x_off + x_cnt)
     const long long total = (long long)n_m * n_x * p.n_img;
     const size_t plane = (size_t)p.n_u * p.n_v;
 
@@ -251,7 +251,7 @@ k_blur_rows_tc(const __grid_constant__ TcBlurParams p, int n_stage)
                 *abort_flag = 1;
                 break;
             }
-            const Tile tl = tile_of(t, n_m, n_x, plane);
+            const Tile tl = tile_of(t, n_m, n_x, plane, p.x_off);
             uint8_t *whi = smem + w0 + (uint32_t)st * stage_bytes;
             for (int base = tid; base < nitems; base += kProd * kBatch) {
                 float v[kBatch][8];
@@ -362,7 +362,7 @@ k_blur_rows_tc(const __grid_constant__ TcBlurParams p, int n_stage)
                 break;
             }
             tc::fence_after_sync();
-            const Tile tl = tile_of(t, n_m, n_x, plane);
+            const Tile tl = tile_of(t, n_m, n_x, plane, p.x_off);
             const int c = tl.m0 + 127 - mr;
             const uint32_t acc = lane_base + (uint32_t)(buf * 2 * kN);
 #pragma unroll
@@ -682,6 +682,8 @@ static TcBlurParams tc_params(const BlurParams &bp, const uint16_t *hankel, unsi
     p.band[1] = make_band(nullptr, bp.rs, (uint32_t)(2 * 64 * p.band[0].ncore));
     p.rp = bp.rp;
     for (int j = 0; j <= 2 * bp.rp && j < 2 * kTcMaxPsfR + 1; ++j) p.gp[j] = bp.gp[j];
+    p.x_off = 0;
+    p.x_cnt = (bp.n_v + kN - 1) / kN;
     return p;
 }
 
@@ -695,8 +697,31 @@ static cudaError_t persistent_grid(long long tiles, int *grid)
     return cudaSuccess;
 }
 
+// Rows [0, r_lo) and [r_hi, n_v) of image blockIdx.y get the row-pass values
+// of an input row that is all ones: vp in tp, vs in ts.
+__global__ void __launch_bounds__(256)
+k_fill_const_rows(float *__restrict__ tp, float *__restrict__ ts, float vp, float vs, int n_u, int n_v,
+                  int r_lo, int r_hi)
+{
+    const size_t lo = (size_t)r_lo * n_u, hs = (size_t)r_hi * n_u, end = (size_t)n_v * n_u;
+    const size_t n_fill = lo + (end - hs);
+    const size_t base = (size_t)blockIdx.y * end;
+    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n_fill;
+         e += (size_t)gridDim.x * blockDim.x) {
+        const size_t i = base + (e < lo ? e : hs + (e - lo));
+        tp[i] = vp;
+        ts[i] = vs;
+    }
+}
+
+// one_lo, one_hi: when one_hi >= 0, every row of `in` outside [one_lo,
+// one_hi) is known to be all ones (the primary of rays that cannot meet the
+// voxels).  Only the 64-line tiles that hold rows of [one_lo, one_hi) are
+// computed; the other rows get the row pass of an all-ones row, the sum of
+// each kernel's taps, from a store-only kernel.
 cudaError_t launch_blur_tc_rows(const BlurParams &bp, const float *in, float *tp, float *ts,
-                                uint16_t *hankel, unsigned int *err, int n_img, cudaStream_t s)
+                                uint16_t *hankel, unsigned int *err, int n_img, cudaStream_t s,
+                                int one_lo, int one_hi)
 {
     if (n_img <= 0) return cudaSuccess;
     if (!blur_tc_supported(bp)) return cudaErrorInvalidValue;
@@ -715,11 +740,49 @@ cudaError_t launch_blur_tc_rows(const BlurParams &bp, const float *in, float *tp
     cudaError_t e = cudaFuncSetAttribute(k_blur_rows_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)bytes);
     if (e != cudaSuccess) return e;
-    const long long tiles = (long long)((bp.n_u + 127) / 128) * ((bp.n_v + kN - 1) / kN) * n_img;
-    int grid = 0;
-    if ((e = persistent_grid(tiles, &grid)) != cudaSuccess) return e;
-    k_blur_rows_tc<<<grid, kThreads, bytes, s>>>(p, n_stage);
+    int r_lo = 0, r_hi = bp.n_v;                 // rows the tensor-core pass computes
+    if (one_hi >= 0) {
+        const int lo = one_lo > 0 ? one_lo : 0, hi = one_hi < bp.n_v ? one_hi : bp.n_v;
+        if (lo < hi) {
+            p.x_off = lo / kN;
+            p.x_cnt = (hi - 1) / kN - p.x_off + 1;
+            r_lo = p.x_off * kN;
+            r_hi = (p.x_off + p.x_cnt) * kN < bp.n_v ? (p.x_off + p.x_cnt) * kN : bp.n_v;
+        } else {
+            p.x_cnt = 0;
+            r_lo = r_hi = 0;
+        }
+    }
+    if (p.x_cnt > 0) {
+        const long long tiles = (long long)((bp.n_u + 127) / 128) * p.x_cnt * n_img;
+        int grid = 0;
+        if ((e = persistent_grid(tiles, &grid)) != cudaSuccess) return e;
+        k_blur_rows_tc<<<grid, kThreads, bytes, s>>>(p, n_stage);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    if (r_hi - r_lo < bp.n_v) {
+        float vp = 0.0f, vs = 0.0f;                // row pass of an all-ones row
+        for (int j = 0; j <= 2 * bp.rp; ++j) vp += bp.gp[j];
+        for (int j = 0; j <= 2 * bp.rs; ++j) vs += bp.gs[j];
+        const size_t per = (size_t)(bp.n_v - (r_hi - r_lo)) * bp.n_u;
+        const size_t want = (per + 256 * 8 - 1) / (256 * 8);
+        if (n_img > 65535) return cudaErrorInvalidValue;
+        dim3 fgrid((unsigned)(want < 1024 ? want : 1024), n_img);
+        k_fill_const_rows<<<fgrid, 256, 0, s>>>(tp, ts, vp, vs, bp.n_u, bp.n_v, r_lo, r_hi);
+    }
     return cudaGetLastError();
+}
+
+// Kernels launch_blur_tc_rows starts: band matrices, the tensor-core pass
+// (unless no tile is computed) and the constant-row fill (when rows are skipped).
+int blur_tc_rows_launches(const BlurParams &bp, int one_lo, int one_hi)
+{
+    if (one_hi < 0) return 2;
+    const int lo = one_lo > 0 ? one_lo : 0, hi = one_hi < bp.n_v ? one_hi : bp.n_v;
+    if (lo >= hi) return 2;
+    const int first = lo / kN, last = (hi - 1) / kN;
+    const int r_hi = (last + 1) * kN < bp.n_v ? (last + 1) * kN : bp.n_v;
+    return 2 + (first * kN > 0 || r_hi < bp.n_v);
 }
 
 cudaError_t launch_blur_tc_cols(const BlurParams &bp, const float *tp, const float *ts, float *out,

@@ -130,6 +130,7 @@ struct TcBlurParams {
     int rp;                          // column pass: optical-spread radius
     float gp[2 * kTcMaxPsfR + 1];    // and taps
     unsigned int *err;  // set on a bounded-wait timeout
+    int x_off, x_cnt;   // rows pass: the 64-line tiles [x_off, x_off + x_cnt) are computed
 };
 
 constexpr size_t kBlurTcHankelMax = 2 * 2 * 64 * (15 + (128 + 2 * 256) / 8);  // bf16 elements
@@ -266,7 +267,9 @@ cudaError_t launch_hu(const DevGeom &g, const double *vol, float *hu, double *pa
                       float radius, int zcut, cudaStream_t s);
 bool blur_tc_supported(const BlurParams &bp);
 cudaError_t launch_blur_tc_rows(const BlurParams &bp, const float *in, float *tp, float *ts,
-                                uint16_t *hankel, unsigned int *err, int n_img, cudaStream_t s);
+                                uint16_t *hankel, unsigned int *err, int n_img, cudaStream_t s,
+                                int one_lo = 0, int one_hi = -1);
+int blur_tc_rows_launches(const BlurParams &bp, int one_lo, int one_hi);
 cudaError_t launch_blur_tc_cols(const BlurParams &bp, const float *tp, const float *ts, float *out,
                                 const uint16_t *hankel, unsigned int *err, int n_img, cudaStream_t s);
 cudaError_t launch_rl(const RlParams &p, const float *d, float *ua, float *ub, float *norm,
