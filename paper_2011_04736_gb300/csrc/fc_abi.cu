@@ -597,7 +597,7 @@ static int run_blur(fc_handle *h, const float *in, float *out, size_t off, int n
     {
         Trace t(h, FC_K_BLUR_COLS, 1, s);
         FC_CK(fc::launch_blur_tc_cols(b, h->d_tp + off, h->d_ts + off, out, h->d_hankel,
-                                      h->d_blur_err, n, s));
+                                      h->d_blur_err, n, s, one_lo, one_hi));
         t.end();
     }
     return FC_OK;

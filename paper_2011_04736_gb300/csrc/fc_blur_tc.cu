@@ -521,9 +521,18 @@ k_blur_cols_tc(const __grid_constant__ TcBlurParams p, int n_stage)
                     const int n = i % kN, cg = i / kN;
                     const float *col = ts + tl.img + clampi(tl.x0 + n, p.n_u);
                     const int c0 = tl.m0 - pad + 8 * cg;
+                    // an item's 8 rows start on a multiple of 8 and the rows
+                    // the row pass computed are whole 64-row tiles, so the
+                    // item lies wholly inside them or holds the constant
+                    const int rc = clampi(c0, p.n_v);
+                    if (rc >= p.ts_lo && rc < p.ts_hi) {
 #pragma unroll
-                    for (int e = 0; e < 8; ++e)
-                        v[q][e] = __ldg(col + (size_t)clampi(c0 + e, p.n_v) * p.n_u);
+                        for (int e = 0; e < 8; ++e)
+                            v[q][e] = __ldg(col + (size_t)clampi(c0 + e, p.n_v) * p.n_u);
+                    } else {
+#pragma unroll
+                        for (int e = 0; e < 8; ++e) v[q][e] = p.ts_const;
+                    }
                 }
 #pragma unroll
                 for (int q = 0; q < kBatch; ++q) {
@@ -684,6 +693,9 @@ static TcBlurParams tc_params(const BlurParams &bp, const uint16_t *hankel, unsi
     for (int j = 0; j <= 2 * bp.rp && j < 2 * kTcMaxPsfR + 1; ++j) p.gp[j] = bp.gp[j];
     p.x_off = 0;
     p.x_cnt = (bp.n_v + kN - 1) / kN;
+    p.ts_lo = 0;
+    p.ts_hi = bp.n_v;
+    p.ts_const = 0.0f;
     return p;
 }
 
@@ -697,21 +709,51 @@ static cudaError_t persistent_grid(long long tiles, int *grid)
     return cudaSuccess;
 }
 
-// Rows [0, r_lo) and [r_hi, n_v) of image blockIdx.y get the row-pass values
-// of an input row that is all ones: vp in tp, vs in ts.
+// Rows the tensor-core row pass computes when the rows of its input outside
+// [one_lo, one_hi) are all ones (one_hi < 0: no such knowledge, every row):
+// the 64-line tiles holding rows of [one_lo, one_hi), as tiles [x_off, x_off
+// + x_cnt) and rows [r_lo, r_hi).
+static void rows_computed(const BlurParams &bp, int one_lo, int one_hi, int &x_off, int &x_cnt, int &r_lo,
+                          int &r_hi)
+{
+    x_off = 0;
+    x_cnt = (bp.n_v + kN - 1) / kN;
+    r_lo = 0;
+    r_hi = bp.n_v;
+    if (one_hi < 0) return;
+    const int lo = one_lo > 0 ? one_lo : 0, hi = one_hi < bp.n_v ? one_hi : bp.n_v;
+    if (lo >= hi) {
+        x_cnt = 0;
+        r_lo = r_hi = 0;
+        return;
+    }
+    x_off = lo / kN;
+    x_cnt = (hi - 1) / kN - x_off + 1;
+    r_lo = x_off * kN;
+    r_hi = (x_off + x_cnt) * kN < bp.n_v ? (x_off + x_cnt) * kN : bp.n_v;
+}
+
+// the row pass of an all-ones row: the sums of the taps
+static void ones_row_pass(const BlurParams &bp, float &vp, float &vs)
+{
+    vp = 0.0f;
+    vs = 0.0f;
+    for (int j = 0; j <= 2 * bp.rp; ++j) vp += bp.gp[j];
+    for (int j = 0; j <= 2 * bp.rs; ++j) vs += bp.gs[j];
+}
+
+// Rows [0, r_lo) and [r_hi, n_v) of image blockIdx.y of tp get vp, the
+// optical-spread row pass of an all-ones row.  (The scatter plane needs no
+// store: the column pass takes the same constant for those rows.)
 __global__ void __launch_bounds__(256)
-k_fill_const_rows(float *__restrict__ tp, float *__restrict__ ts, float vp, float vs, int n_u, int n_v,
-                  int r_lo, int r_hi)
+k_fill_const_rows(float *__restrict__ tp, float vp, int n_u, int n_v, int r_lo, int r_hi)
 {
     const size_t lo = (size_t)r_lo * n_u, hs = (size_t)r_hi * n_u, end = (size_t)n_v * n_u;
     const size_t n_fill = lo + (end - hs);
     const size_t base = (size_t)blockIdx.y * end;
     for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n_fill;
-         e += (size_t)gridDim.x * blockDim.x) {
-        const size_t i = base + (e < lo ? e : hs + (e - lo));
-        tp[i] = vp;
-        ts[i] = vs;
-    }
+         e += (size_t)gridDim.x * blockDim.x)
+        tp[base + (e < lo ? e : hs + (e - lo))] = vp;
 }
 
 // one_lo, one_hi: when one_hi >= 0, every row of `in` outside [one_lo,
@@ -740,19 +782,8 @@ cudaError_t launch_blur_tc_rows(const BlurParams &bp, const float *in, float *tp
     cudaError_t e = cudaFuncSetAttribute(k_blur_rows_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)bytes);
     if (e != cudaSuccess) return e;
-    int r_lo = 0, r_hi = bp.n_v;                 // rows the tensor-core pass computes
-    if (one_hi >= 0) {
-        const int lo = one_lo > 0 ? one_lo : 0, hi = one_hi < bp.n_v ? one_hi : bp.n_v;
-        if (lo < hi) {
-            p.x_off = lo / kN;
-            p.x_cnt = (hi - 1) / kN - p.x_off + 1;
-            r_lo = p.x_off * kN;
-            r_hi = (p.x_off + p.x_cnt) * kN < bp.n_v ? (p.x_off + p.x_cnt) * kN : bp.n_v;
-        } else {
-            p.x_cnt = 0;
-            r_lo = r_hi = 0;
-        }
-    }
+    int r_lo, r_hi;                                // rows the tensor-core pass computes
+    rows_computed(bp, one_lo, one_hi, p.x_off, p.x_cnt, r_lo, r_hi);
     if (p.x_cnt > 0) {
         const long long tiles = (long long)((bp.n_u + 127) / 128) * p.x_cnt * n_img;
         int grid = 0;
@@ -761,14 +792,13 @@ cudaError_t launch_blur_tc_rows(const BlurParams &bp, const float *in, float *tp
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     if (r_hi - r_lo < bp.n_v) {
-        float vp = 0.0f, vs = 0.0f;                // row pass of an all-ones row
-        for (int j = 0; j <= 2 * bp.rp; ++j) vp += bp.gp[j];
-        for (int j = 0; j <= 2 * bp.rs; ++j) vs += bp.gs[j];
+        float vp, vs;
+        ones_row_pass(bp, vp, vs);
         const size_t per = (size_t)(bp.n_v - (r_hi - r_lo)) * bp.n_u;
         const size_t want = (per + 256 * 8 - 1) / (256 * 8);
         if (n_img > 65535) return cudaErrorInvalidValue;
         dim3 fgrid((unsigned)(want < 1024 ? want : 1024), n_img);
-        k_fill_const_rows<<<fgrid, 256, 0, s>>>(tp, ts, vp, vs, bp.n_u, bp.n_v, r_lo, r_hi);
+        k_fill_const_rows<<<fgrid, 256, 0, s>>>(tp, vp, bp.n_u, bp.n_v, r_lo, r_hi);
     }
     return cudaGetLastError();
 }
@@ -777,20 +807,26 @@ cudaError_t launch_blur_tc_rows(const BlurParams &bp, const float *in, float *tp
 // (unless no tile is computed) and the constant-row fill (when rows are skipped).
 int blur_tc_rows_launches(const BlurParams &bp, int one_lo, int one_hi)
 {
-    if (one_hi < 0) return 2;
-    const int lo = one_lo > 0 ? one_lo : 0, hi = one_hi < bp.n_v ? one_hi : bp.n_v;
-    if (lo >= hi) return 2;
-    const int first = lo / kN, last = (hi - 1) / kN;
-    const int r_hi = (last + 1) * kN < bp.n_v ? (last + 1) * kN : bp.n_v;
-    return 2 + (first * kN > 0 || r_hi < bp.n_v);
+    int x_off, x_cnt, r_lo, r_hi;
+    rows_computed(bp, one_lo, one_hi, x_off, x_cnt, r_lo, r_hi);
+    return 1 + (x_cnt > 0) + (r_hi - r_lo < bp.n_v);
 }
 
+// one_lo, one_hi: as for launch_blur_tc_rows with the same values; the rows
+// of ts that pass did not compute are taken as the constant it stands for.
 cudaError_t launch_blur_tc_cols(const BlurParams &bp, const float *tp, const float *ts, float *out,
-                                const uint16_t *hankel, unsigned int *err, int n_img, cudaStream_t s)
+                                const uint16_t *hankel, unsigned int *err, int n_img, cudaStream_t s,
+                                int one_lo, int one_hi)
 {
     if (n_img <= 0) return cudaSuccess;
     if (!blur_tc_supported(bp)) return cudaErrorInvalidValue;
     TcBlurParams p = tc_params(bp, hankel, err, n_img);
+    {
+        int x_off, x_cnt;
+        rows_computed(bp, one_lo, one_hi, x_off, x_cnt, p.ts_lo, p.ts_hi);
+        float vp;
+        ones_row_pass(bp, vp, p.ts_const);
+    }
     p.band[1].src = ts;
     p.tp = tp;
     p.out0 = out;

@@ -131,6 +131,8 @@ struct TcBlurParams {
     float gp[2 * kTcMaxPsfR + 1];    // and taps
     unsigned int *err;  // set on a bounded-wait timeout
     int x_off, x_cnt;   // rows pass: the 64-line tiles [x_off, x_off + x_cnt) are computed
+    int ts_lo, ts_hi;   // columns pass: rows of ts outside [ts_lo, ts_hi) equal ts_const
+    float ts_const;
 };
 
 constexpr size_t kBlurTcHankelMax = 2 * 2 * 64 * (15 + (128 + 2 * 256) / 8);  // bf16 elements
@@ -271,7 +273,8 @@ cudaError_t launch_blur_tc_rows(const BlurParams &bp, const float *in, float *tp
                                 int one_lo = 0, int one_hi = -1);
 int blur_tc_rows_launches(const BlurParams &bp, int one_lo, int one_hi);
 cudaError_t launch_blur_tc_cols(const BlurParams &bp, const float *tp, const float *ts, float *out,
-                                const uint16_t *hankel, unsigned int *err, int n_img, cudaStream_t s);
+                                const uint16_t *hankel, unsigned int *err, int n_img, cudaStream_t s,
+                                int one_lo = 0, int one_hi = -1);
 cudaError_t launch_rl(const RlParams &p, const float *d, float *ua, float *ub, float *norm,
                       int n_img, int n_iter, float **result, cudaStream_t s);
 cudaError_t launch_mtf(const MtfParams &p, double *work, double *freq, double *mtf, cudaStream_t s);
