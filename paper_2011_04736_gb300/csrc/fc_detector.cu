@@ -362,7 +362,8 @@ struct DrawQueue {
 }  // namespace
 
 __global__ void __launch_bounds__(32 * kWarps, 5)
-k_poisson(const float *lam, float *out, int n_v, int n_u, int angle0, uint64_t seed)
+k_poisson(const float *lam, float *out, int n_v, int n_u, int angle0,
+          const __grid_constant__ noise::PhiloxKeys seed)
 {
     __shared__ DrawQueue q_all[kWarps];
     DrawQueue &q = q_all[threadIdx.y];
@@ -421,7 +422,6 @@ k_poisson(const float *lam, float *out, int n_v, int n_u, int angle0, uint64_t s
         count = min(count + __popc(m), kQueue);
     }
     __syncwarp();
-    const uint2 key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
     for (int i = lane; i < count; i += 32) {
         noise::Ptrs st;
         st.lam = q.lam[i];
@@ -437,7 +437,7 @@ k_poisson(const float *lam, float *out, int n_v, int n_u, int angle0, uint64_t s
         const uint32_t jh = q.jh[i];
         st.j = (jh & 0x7fffffffu) >> 1;
         st.h = (int)(jh & 1u);
-        st.key = key;
+        st.key = &seed;
         st.w = make_uint4(0u, 0u, q.wz[i], q.ww[i]);
         float r;
         bool done = (jh & 0x80000000u) ? noise::ptrs_final(st, q.kf[i], q.us[i], q.V[i], r) : false;
@@ -453,7 +453,7 @@ cudaError_t launch_poisson(const float *lam, float *out, int n_img, int n_v, int
     if ((n_v + kWarps - 1) / kWarps > 65535 || n_img > 65535) return cudaErrorInvalidValue;
     dim3 block(32, kWarps);
     dim3 grid((n_u + 32 * kPer - 1) / (32 * kPer), (n_v + kWarps - 1) / kWarps, n_img);
-    k_poisson<<<grid, block, 0, s>>>(lam, out, n_v, n_u, angle0, seed);
+    k_poisson<<<grid, block, 0, s>>>(lam, out, n_v, n_u, angle0, noise::philox_keys(seed));
     return cudaGetLastError();
 }
 

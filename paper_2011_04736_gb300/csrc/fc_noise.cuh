@@ -26,22 +26,44 @@ namespace noise {
 #define FMUL __fmul_rn
 #define FDIV __fdiv_rn
 
-__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k)
+// The ten round keys of Philox4x32-10 for one seed (the key bumped by the
+// Weyl constants after every round), built on the host and passed as a kernel
+// parameter so that each round's xor takes its key from the constant bank.
+struct PhiloxKeys {
+    uint32_t x[10], y[10];
+};
+
+inline PhiloxKeys philox_keys(uint64_t seed)
+{
+    PhiloxKeys k;
+    uint32_t kx = (uint32_t)seed, ky = (uint32_t)(seed >> 32);
+    for (int r = 0; r < 10; ++r) {
+        k.x[r] = kx;
+        k.y[r] = ky;
+        kx += 0x9E3779B9u;
+        ky += 0xBB67AE85u;
+    }
+    return k;
+}
+
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, const PhiloxKeys &k)
 {
 #pragma unroll
     for (int r = 0; r < 10; ++r) {
         const uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
         const uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
-        c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
-        k.x += 0x9E3779B9u;
-        k.y += 0xBB67AE85u;
+        c = make_uint4(hi1 ^ c.y ^ k.x[r], lo1, hi0 ^ c.w ^ k.y[r], lo0);
     }
     return c;
 }
 
+// (2 (w >> 9) + 1) 2^-24 without an integer-to-float conversion: the bits of
+// 1 + m 2^-23 (m = w >> 9), minus 1 (exact), plus 2^-24 (exact: the sum has at
+// most 24 significant bits), so the value is the one the formula defines.
 __device__ __forceinline__ float unif(uint32_t w)
 {
-    return FMUL(__uint2float_rn(((w >> 9) << 1) | 1u), 5.9604644775390625e-08f);
+    const float f = __uint_as_float(0x3f800000u | (w >> 9));
+    return FADD(FSUB(f, 1.0f), 5.9604644775390625e-08f);
 }
 
 // natural log of a positive normal binary32 value
@@ -154,7 +176,7 @@ struct Ptrs {
     float lam, b, a, vr, loglam, invalpha;
     uint4 w;            // Philox block j
     uint32_t iu, iv, k, j;
-    uint2 key;
+    const PhiloxKeys *key;   // round keys of the seed (kernel parameter)
     int h;              // 0: attempt uses words (x, y) of block j, 1: words (z, w)
     bool have_slow;     // loglam and invalpha evaluated
 };
@@ -163,9 +185,8 @@ struct Ptrs {
 // without rejection sampling (rate <= 0 or NaN, rate > 1e7, rate < 10);
 // otherwise prepares s for ptrs_attempt.
 __device__ __forceinline__ bool poisson_begin(float lam, uint32_t iu, uint32_t iv, uint32_t k,
-                                              uint64_t seed, Ptrs &s, float &r)
+                                              const PhiloxKeys &key, Ptrs &s, float &r)
 {
-    const uint2 key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
     if (!(lam > 0.0f)) { r = 0.0f; return true; }
     if (lam > 1.0e7f) { r = floorf(FADD(lam, 0.5f)); return true; }
     if (lam < 10.0f) {
@@ -196,7 +217,7 @@ __device__ __forceinline__ bool poisson_begin(float lam, uint32_t iu, uint32_t i
     vr = FSUB(0.9277f, vr);
     s.lam = lam; s.b = b; s.a = a; s.vr = vr;
     s.loglam = 0.0f; s.invalpha = 0.0f; s.have_slow = false;
-    s.iu = iu; s.iv = iv; s.k = k; s.j = 0; s.h = 0; s.key = key;
+    s.iu = iu; s.iv = iv; s.k = k; s.j = 0; s.h = 0; s.key = &key;
     return false;
 }
 
@@ -222,7 +243,7 @@ enum { kDone = 0, kReject = 1, kPending = 2 };
 __device__ __forceinline__ int ptrs_quick(Ptrs &s, float &r, float &kf_out, float &us_out,
                                           float &V_out)
 {
-    if (s.h == 0) s.w = philox4x32_10(make_uint4(s.iu, s.iv, s.k, s.j), s.key);
+    if (s.h == 0) s.w = philox4x32_10(make_uint4(s.iu, s.iv, s.k, s.j), *s.key);
     const float U = FSUB(unif(s.h ? s.w.z : s.w.x), 0.5f);
     const float V = unif(s.h ? s.w.w : s.w.y);
     const float us = FSUB(0.5f, fabsf(U));
@@ -274,7 +295,7 @@ __device__ __forceinline__ bool ptrs_attempt(Ptrs &s, float &r)
 
 // Complete draw for pixel (iu, iv) of projection k.
 __device__ __forceinline__ float poisson(float lam, uint32_t iu, uint32_t iv, uint32_t k,
-                                         uint64_t seed)
+                                         const PhiloxKeys &seed)
 {
     Ptrs s;
     float r;
