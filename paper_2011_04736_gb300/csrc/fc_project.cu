@@ -47,6 +47,19 @@ __device__ __forceinline__ int clampi(int v, int lo, int hi)
 
 }  // namespace
 
+// Ray tiles: a CTA of 32 x 8 threads traces kTileU columns x kTileV rows of
+// one projection; warp w takes columns 2w and 2w + 1 of the tile, all 16 rows
+// (lane l: column 2w + (l & 1), row l >> 1).  Rays of one detector column
+// cross the phantom above one another, a slice apart or less, so where labels
+// vary slowly along z they meet the same bricks and voxel runs and the warp's
+// lanes step together; 32 rays along a row fan out in-plane and meet mixed
+// bricks at different steps.  (The warp's rays, hence every result, are the
+// same for any tile shape; only the grouping into warps changes.)
+constexpr int kTileU = 16, kTileV = 16;
+
+__device__ __forceinline__ int tile_du() { return (int)threadIdx.y * 2 + ((int)threadIdx.x & 1); }
+__device__ __forceinline__ int tile_dv() { return (int)threadIdx.x >> 1; }
+
 // Per-material path lengths L of pixel ray (iu, iv) of projection k; returns
 // whether the ray meets the voxel box.
 __device__ __forceinline__ bool trace_ray(const ProjParams &p, int iu, int iv, int k,
@@ -225,8 +238,8 @@ __global__ void __launch_bounds__(256)
 k_project(const __grid_constant__ ProjParams p, float *__restrict__ T, float *__restrict__ Lout, int row0)
 {
     const DevGeom &g = p.g;
-    const int iu = blockIdx.x * 32 + threadIdx.x;
-    const int iv = row0 + blockIdx.y * blockDim.y + threadIdx.y;
+    const int iu = blockIdx.x * kTileU + tile_du();
+    const int iv = row0 + blockIdx.y * kTileV + tile_dv();
     const int kl = blockIdx.z;
     if (iu >= g.n_u || iv >= g.n_v) return;
     const int k = p.angle0 + kl;
@@ -306,16 +319,16 @@ static cudaError_t launch_fill(const ProjParams &p, float *T, int r0, int r1, co
     return cudaGetLastError();
 }
 
-// Traced band [r0, r1) of 8-row blocks holding the rows in [v_hit_lo, v_hit_hi]
-// (r0 = r1 = 0 when no row can meet the slab).
+// Traced band [r0, r1) of kTileV-row tiles holding the rows in
+// [v_hit_lo, v_hit_hi] (r0 = r1 = 0 when no row can meet the slab).
 static void project_band(const ProjParams &p, int &r0, int &r1)
 {
     const int n_v = p.g.n_v;
     const int lo = max(p.v_hit_lo, 0), hi = min(p.v_hit_hi, n_v - 1);
     r0 = r1 = 0;
     if (lo <= hi) {
-        r0 = lo / 8 * 8;
-        r1 = min((hi / 8 + 1) * 8, n_v);
+        r0 = lo / kTileV * kTileV;
+        r1 = min((hi / kTileV + 1) * kTileV, n_v);
     }
 }
 
@@ -334,16 +347,16 @@ cudaError_t launch_project(const ProjParams &p, float *T, float *L_out, cudaStre
     if (p.n_angles_launch <= 0) return cudaSuccess;
     dim3 block(32, 8);
     if (L_out) {
-        dim3 grid((p.g.n_u + 31) / 32, (p.g.n_v + 7) / 8, p.n_angles_launch);
+        dim3 grid((p.g.n_u + kTileU - 1) / kTileU, (p.g.n_v + kTileV - 1) / kTileV, p.n_angles_launch);
         k_project<true><<<grid, block, 0, s>>>(p, T, L_out, 0);
         return cudaGetLastError();
     }
-    // Only the 8-row blocks that hold rows in [v_hit_lo, v_hit_hi] are traced;
+    // Only the row tiles that hold rows in [v_hit_lo, v_hit_hi] are traced;
     // the other rows are filled with T = 1 by a store-only kernel.
     int r0, r1;
     project_band(p, r0, r1);
     if (r1 > r0) {
-        dim3 grid((p.g.n_u + 31) / 32, (r1 - r0 + 7) / 8, p.n_angles_launch);
+        dim3 grid((p.g.n_u + kTileU - 1) / kTileU, (r1 - r0 + kTileV - 1) / kTileV, p.n_angles_launch);
         k_project<false><<<grid, block, 0, s>>>(p, T, nullptr, r0);
     }
     FillPlanes f{};
@@ -360,8 +373,8 @@ __global__ void __launch_bounds__(256)
 k_project_groups(const __grid_constant__ ProjParams p, float *__restrict__ P, int row0)
 {
     const DevGeom &g = p.g;
-    const int iu = blockIdx.x * 32 + threadIdx.x;
-    const int iv = row0 + blockIdx.y * blockDim.y + threadIdx.y;
+    const int iu = blockIdx.x * kTileU + tile_du();
+    const int iv = row0 + blockIdx.y * kTileV + tile_dv();
     if (iu >= g.n_u || iv >= g.n_v) return;
     const int k = p.angle0 + blockIdx.z;
     float L[kMaxMat];
@@ -396,7 +409,7 @@ cudaError_t launch_project_groups(const ProjParams &p, float *P, cudaStream_t s)
     int r0, r1;
     project_band(p, r0, r1);
     if (r1 > r0) {
-        dim3 grid((p.g.n_u + 31) / 32, (r1 - r0 + 7) / 8, p.n_angles_launch);
+        dim3 grid((p.g.n_u + kTileU - 1) / kTileU, (r1 - r0 + kTileV - 1) / kTileV, p.n_angles_launch);
         k_project_groups<<<grid, block, 0, s>>>(p, P, r0);
     }
     FillPlanes f{};
@@ -408,8 +421,9 @@ cudaError_t launch_project_groups(const ProjParams &p, float *P, cudaStream_t s)
 // Dose estimate, Sec. II.H: for every energy bin E, the sum over the rays of
 // the fraction a ray loses in the phantom, 1 - exp(-sum_m mu_m(E) L_m).
 // Rays outside the rows [r0, r1) cannot meet the voxel slab and lose nothing,
-// so only that band is visited.  Blocks walk 32 x 8 pixel tiles in a fixed order; each warp traces its row
-// of 32 rays, stages their path lengths in its own shared slice and then sums
+// so only that band is visited.  Blocks walk the projector's ray tiles in a
+// fixed order; each warp traces its 32 rays (two columns of 16 rows), stages
+// their path lengths in its own shared slice and then sums
 // bins lane, lane + 32, ... over those 32 rays (warp-synchronous: no block
 // barrier inside the loop, so a warp with long rays holds up no other).  The
 // warps' per-bin sums are folded in a fixed order at the end: the partials
@@ -424,7 +438,7 @@ k_dose_partial(const __grid_constant__ ProjParams p, double *__restrict__ part, 
     __shared__ double red[8][kMaxBins];
     const DevGeom &g = p.g;
     const int lane = threadIdx.x, w = threadIdx.y;
-    const int tu = (g.n_u + 31) / 32, tv = (r1 - r0 + 7) / 8;
+    const int tu = (g.n_u + kTileU - 1) / kTileU, tv = (r1 - r0 + kTileV - 1) / kTileV;
     const long long n_tiles = (long long)tu * tv * p.n_angles_launch;
     double acc[NQ];
 #pragma unroll
@@ -432,7 +446,7 @@ k_dose_partial(const __grid_constant__ ProjParams p, double *__restrict__ part, 
     for (long long t = blockIdx.x; t < n_tiles; t += gridDim.x) {
         const int bu = (int)(t % tu), bv = (int)((t / tu) % tv);
         const int kl = (int)(t / ((long long)tu * tv));
-        const int iu = bu * 32 + lane, iv = r0 + bv * 8 + w;
+        const int iu = bu * kTileU + tile_du(), iv = r0 + bv * kTileV + tile_dv();
         float L[kMaxMat];
         if (iu < g.n_u && iv < r1) {
             trace_ray(p, iu, iv, p.angle0 + kl, L);
@@ -567,7 +581,8 @@ int dose_blocks(const ProjParams &p)
 {
     int r0, r1;
     project_band(p, r0, r1);
-    long long tiles = (long long)((p.g.n_u + 31) / 32) * ((r1 - r0 + 7) / 8) * p.n_angles_launch;
+    long long tiles = (long long)((p.g.n_u + kTileU - 1) / kTileU) * ((r1 - r0 + kTileV - 1) / kTileV) *
+                      p.n_angles_launch;
     tiles = tiles > 0 ? tiles : 1;   // one block writes zero partials
     if (p.n_e <= 32) return dose_grid<1>(tiles);
     if (p.n_e <= 64) return dose_grid<2>(tiles);
