@@ -166,7 +166,10 @@ k_project_density(const __grid_constant__ AdjParams p, const float *__restrict__
                   float *__restrict__ T)
 {
     const DevGeom &g = p.g;
-    const int iu = blockIdx.x * 32 + threadIdx.x, iv = blockIdx.y * 8 + threadIdx.y, k = blockIdx.z;
+    // warp w of the CTA's 16 x 16 ray tile: columns 2w, 2w + 1, all 16 rows
+    // (rays of one column cross the phantom close together and walk alike)
+    const int iu = blockIdx.x * 16 + threadIdx.y * 2 + (threadIdx.x & 1);
+    const int iv = blockIdx.y * 16 + (threadIdx.x >> 1), k = blockIdx.z;
     if (iu >= g.n_u || iv >= g.n_v) return;
     const float2 cs = p.trig[k];
     const Ray r = make_ray(g, cs.x, cs.y, iu, iv);
@@ -183,7 +186,10 @@ k_project_density(const __grid_constant__ AdjParams p, const float *__restrict__
 }
 
 // Adjoint projector.  gT = dJ/dT per ray; accumulates dJ/d(wD)_E (before
-// normalisation) into gwd[n_e] (FP64) and dJ/drho into grho.
+// normalisation) into gwd[n_e] (FP64) and dJ/drho into grho.  A warp takes
+// 32 rays of one row: rays of one column, as the forward kernel groups them,
+// would add into the same voxels at the same steps and serialise the atomics
+// (forward + gradient 20.8 ms against 19.2).
 __global__ void __launch_bounds__(256)
 k_project_density_adjoint(const __grid_constant__ AdjParams p, const float *__restrict__ rho,
                           const float *__restrict__ gT, float *__restrict__ grho,
@@ -523,7 +529,7 @@ k_backproject_adjoint(const __grid_constant__ FdkParams p, const float *__restri
 // ---------------------------------------------------------------- launchers
 cudaError_t launch_project_density(const AdjParams &p, const float *rho, float *T, cudaStream_t s)
 {
-    dim3 block(32, 8), grid((p.g.n_u + 31) / 32, (p.g.n_v + 7) / 8, p.g.n_angles);
+    dim3 block(32, 8), grid((p.g.n_u + 15) / 16, (p.g.n_v + 15) / 16, p.g.n_angles);
     k_project_density<<<grid, block, 0, s>>>(p, rho, T);
     return cudaGetLastError();
 }
