@@ -230,9 +230,11 @@ namespace {
 constexpr int kFold = 64;        // angles per binary32 partial sum
 }
 
-// kZc z values per thread (the launcher balances the z chunks).
-template <int kZc>
-__global__ void __launch_bounds__(256)
+// kZc z values per thread (the launcher balances the z chunks).  kMinCtas:
+// CTAs per SM the register budget must allow (8 caps it at 32 registers, a
+// few bytes of the binary64 sums spilled; 6 at 40 registers, no spill).
+template <int kZc, int kMinCtas>
+__global__ void __launch_bounds__(256, kMinCtas)
 k_backproject(const __grid_constant__ FdkParams p, const float *__restrict__ f,
               double *__restrict__ vol)
 {
@@ -312,16 +314,30 @@ cudaError_t launch_backproject(const FdkParams &p, const float *filt, double *vo
         zc = (p.g.nz + nchunk - 1) / nchunk;
     }
     dim3 grid((p.g.nx + 31) / 32, (p.g.ny + 7) / 8, (p.g.nz + zc - 1) / zc);
+    // A grid of two or more waves at 6 CTAs per SM runs faster with 8
+    // resident CTAs (more warps to hide the tap latency; paper-scale MV case
+    // 10.26 -> 9.21 ms); a grid of about one wave (catphan_kv: 1024 CTAs)
+    // runs faster with the unspilled 40-register kernel.
+    const bool dense = (long)grid.x * grid.y * grid.z >= 2L * 152 * 6;
+#define FC_BP(Z)                                                                  \
+    case Z:                                                                       \
+        if (dense)                                                                \
+            k_backproject<Z, 8><<<grid, block, 0, s>>>(p, filt, vol);             \
+        else                                                                      \
+            k_backproject<Z, 6><<<grid, block, 0, s>>>(p, filt, vol);             \
+        break;
     switch (zc) {
-    case 1: k_backproject<1><<<grid, block, 0, s>>>(p, filt, vol); break;
-    case 2: k_backproject<2><<<grid, block, 0, s>>>(p, filt, vol); break;
-    case 3: k_backproject<3><<<grid, block, 0, s>>>(p, filt, vol); break;
-    case 4: k_backproject<4><<<grid, block, 0, s>>>(p, filt, vol); break;
-    case 5: k_backproject<5><<<grid, block, 0, s>>>(p, filt, vol); break;
-    case 6: k_backproject<6><<<grid, block, 0, s>>>(p, filt, vol); break;
-    case 7: k_backproject<7><<<grid, block, 0, s>>>(p, filt, vol); break;
-    default: k_backproject<8><<<grid, block, 0, s>>>(p, filt, vol); break;
+    FC_BP(1)
+    FC_BP(2)
+    FC_BP(3)
+    FC_BP(4)
+    FC_BP(5)
+    FC_BP(6)
+    FC_BP(7)
+    default:
+    FC_BP(8)
     }
+#undef FC_BP
     return cudaGetLastError();
 }
 

@@ -47,18 +47,26 @@ __device__ __forceinline__ int clampi(int v, int lo, int hi)
 
 }  // namespace
 
-// Ray tiles: a CTA of 32 x 8 threads traces kTileU columns x kTileV rows of
-// one projection; warp w takes columns 2w and 2w + 1 of the tile, all 16 rows
-// (lane l: column 2w + (l & 1), row l >> 1).  Rays of one detector column
-// cross the phantom above one another, a slice apart or less, so where labels
-// vary slowly along z they meet the same bricks and voxel runs and the warp's
-// lanes step together; 32 rays along a row fan out in-plane and meet mixed
-// bricks at different steps.  (The warp's rays, hence every result, are the
-// same for any tile shape; only the grouping into warps changes.)
-constexpr int kTileU = 16, kTileV = 16;
+// Ray order inside the traced band [r0, r0 + R) of one projection: ray t is
+// row r0 + t % R of column t / R, so a warp's 32 consecutive rays run down
+// the columns of the band (CTAs of 256 rays).  Rays of one detector column
+// cross the phantom above one another, a slice apart or less, so where
+// labels vary slowly along z they meet the same bricks and voxel runs and the
+// warp's lanes step together; 32 rays along a row fan out in-plane and meet
+// mixed bricks at different steps.  The band is not padded, so however thin
+// it is no lane holds a ray outside it.  (Every ray's result is the same in
+// any order; only the grouping into warps changes.)
+constexpr int kBandCta = 256;
 
-__device__ __forceinline__ int tile_du() { return (int)threadIdx.y * 2 + ((int)threadIdx.x & 1); }
-__device__ __forceinline__ int tile_dv() { return (int)threadIdx.x >> 1; }
+__device__ __forceinline__ bool band_ray(int t, int r0, int R, int n_u, int &iu, int &iv)
+{
+    if (t >= R * n_u) return false;
+    iu = t / R;
+    iv = r0 + (t - iu * R);
+    return true;
+}
+
+__device__ __forceinline__ int band_t() { return (int)blockIdx.x * kBandCta + (int)threadIdx.y * 32 + (int)threadIdx.x; }
 
 // Per-material path lengths L of pixel ray (iu, iv) of projection k; returns
 // whether the ray meets the voxel box.
@@ -235,13 +243,13 @@ __device__ __forceinline__ bool trace_ray(const ProjParams &p, int iu, int iv, i
 
 template <bool EMIT_L>
 __global__ void __launch_bounds__(256)
-k_project(const __grid_constant__ ProjParams p, float *__restrict__ T, float *__restrict__ Lout, int row0)
+k_project(const __grid_constant__ ProjParams p, float *__restrict__ T, float *__restrict__ Lout, int r0,
+          int R)
 {
     const DevGeom &g = p.g;
-    const int iu = blockIdx.x * kTileU + tile_du();
-    const int iv = row0 + blockIdx.y * kTileV + tile_dv();
+    int iu, iv;
+    if (!band_ray(band_t(), r0, R, g.n_u, iu, iv)) return;
     const int kl = blockIdx.z;
-    if (iu >= g.n_u || iv >= g.n_v) return;
     const int k = p.angle0 + kl;
     float L[kMaxMat];
     const bool hit = trace_ray(p, iu, iv, k, L);
@@ -319,16 +327,22 @@ static cudaError_t launch_fill(const ProjParams &p, float *T, int r0, int r1, co
     return cudaGetLastError();
 }
 
-// Traced band [r0, r1) of kTileV-row tiles holding the rows in
-// [v_hit_lo, v_hit_hi] (r0 = r1 = 0 when no row can meet the slab).
+// Traced band [r0, r1): the rows in [v_hit_lo, v_hit_hi] clipped to the
+// detector (r0 = r1 = 0 when no row can meet the slab).
+// CTAs of kBandCta rays covering R rows x n_u columns of one projection.
+static unsigned band_ctas(int R, int n_u)
+{
+    return (unsigned)(((long long)R * n_u + kBandCta - 1) / kBandCta);
+}
+
 static void project_band(const ProjParams &p, int &r0, int &r1)
 {
     const int n_v = p.g.n_v;
     const int lo = max(p.v_hit_lo, 0), hi = min(p.v_hit_hi, n_v - 1);
     r0 = r1 = 0;
     if (lo <= hi) {
-        r0 = lo / kTileV * kTileV;
-        r1 = min((hi / kTileV + 1) * kTileV, n_v);
+        r0 = lo;
+        r1 = hi + 1;
     }
 }
 
@@ -347,8 +361,8 @@ cudaError_t launch_project(const ProjParams &p, float *T, float *L_out, cudaStre
     if (p.n_angles_launch <= 0) return cudaSuccess;
     dim3 block(32, 8);
     if (L_out) {
-        dim3 grid((p.g.n_u + kTileU - 1) / kTileU, (p.g.n_v + kTileV - 1) / kTileV, p.n_angles_launch);
-        k_project<true><<<grid, block, 0, s>>>(p, T, L_out, 0);
+        dim3 grid(band_ctas(p.g.n_v, p.g.n_u), 1, p.n_angles_launch);
+        k_project<true><<<grid, block, 0, s>>>(p, T, L_out, 0, p.g.n_v);
         return cudaGetLastError();
     }
     // Only the row tiles that hold rows in [v_hit_lo, v_hit_hi] are traced;
@@ -356,8 +370,8 @@ cudaError_t launch_project(const ProjParams &p, float *T, float *L_out, cudaStre
     int r0, r1;
     project_band(p, r0, r1);
     if (r1 > r0) {
-        dim3 grid((p.g.n_u + kTileU - 1) / kTileU, (r1 - r0 + kTileV - 1) / kTileV, p.n_angles_launch);
-        k_project<false><<<grid, block, 0, s>>>(p, T, nullptr, r0);
+        dim3 grid(band_ctas(r1 - r0, p.g.n_u), 1, p.n_angles_launch);
+        k_project<false><<<grid, block, 0, s>>>(p, T, nullptr, r0, r1 - r0);
     }
     FillPlanes f{};
     f.v[0] = 1.0f;
@@ -370,12 +384,11 @@ cudaError_t launch_project(const ProjParams &p, float *T, float *L_out, cudaStre
 // a compensated sum per group, written to P + g * grp_stride at the ray's
 // absolute position.  Rays that miss the volume give P_g = sum_{E in g} wD.
 __global__ void __launch_bounds__(256)
-k_project_groups(const __grid_constant__ ProjParams p, float *__restrict__ P, int row0)
+k_project_groups(const __grid_constant__ ProjParams p, float *__restrict__ P, int r0, int R)
 {
     const DevGeom &g = p.g;
-    const int iu = blockIdx.x * kTileU + tile_du();
-    const int iv = row0 + blockIdx.y * kTileV + tile_dv();
-    if (iu >= g.n_u || iv >= g.n_v) return;
+    int iu, iv;
+    if (!band_ray(band_t(), r0, R, g.n_u, iu, iv)) return;
     const int k = p.angle0 + blockIdx.z;
     float L[kMaxMat];
     const bool hit = trace_ray(p, iu, iv, k, L);
@@ -409,8 +422,8 @@ cudaError_t launch_project_groups(const ProjParams &p, float *P, cudaStream_t s)
     int r0, r1;
     project_band(p, r0, r1);
     if (r1 > r0) {
-        dim3 grid((p.g.n_u + kTileU - 1) / kTileU, (r1 - r0 + kTileV - 1) / kTileV, p.n_angles_launch);
-        k_project_groups<<<grid, block, 0, s>>>(p, P, r0);
+        dim3 grid(band_ctas(r1 - r0, p.g.n_u), 1, p.n_angles_launch);
+        k_project_groups<<<grid, block, 0, s>>>(p, P, r0, r1 - r0);
     }
     FillPlanes f{};
     for (int gi = 0; gi < p.n_groups; ++gi) f.v[gi] = p.grp_flood[gi];
@@ -421,9 +434,9 @@ cudaError_t launch_project_groups(const ProjParams &p, float *P, cudaStream_t s)
 // Dose estimate, Sec. II.H: for every energy bin E, the sum over the rays of
 // the fraction a ray loses in the phantom, 1 - exp(-sum_m mu_m(E) L_m).
 // Rays outside the rows [r0, r1) cannot meet the voxel slab and lose nothing,
-// so only that band is visited.  Blocks walk the projector's ray tiles in a
-// fixed order; each warp traces its 32 rays (two columns of 16 rows), stages
-// their path lengths in its own shared slice and then sums
+// so only that band is visited.  Blocks walk tiles of 256 rays of the
+// projector's band order in a fixed order; each warp traces its 32 rays,
+// stages their path lengths in its own shared slice and then sums
 // bins lane, lane + 32, ... over those 32 rays (warp-synchronous: no block
 // barrier inside the loop, so a warp with long rays holds up no other).  The
 // warps' per-bin sums are folded in a fixed order at the end: the partials
@@ -438,17 +451,18 @@ k_dose_partial(const __grid_constant__ ProjParams p, double *__restrict__ part, 
     __shared__ double red[8][kMaxBins];
     const DevGeom &g = p.g;
     const int lane = threadIdx.x, w = threadIdx.y;
-    const int tu = (g.n_u + kTileU - 1) / kTileU, tv = (r1 - r0 + kTileV - 1) / kTileV;
-    const long long n_tiles = (long long)tu * tv * p.n_angles_launch;
+    const int R = r1 - r0;
+    const int tpa = (R * g.n_u + kBandCta - 1) / kBandCta;   // tiles per projection
+    const long long n_tiles = (long long)tpa * p.n_angles_launch;
     double acc[NQ];
 #pragma unroll
     for (int q = 0; q < NQ; ++q) acc[q] = 0.0;
     for (long long t = blockIdx.x; t < n_tiles; t += gridDim.x) {
-        const int bu = (int)(t % tu), bv = (int)((t / tu) % tv);
-        const int kl = (int)(t / ((long long)tu * tv));
-        const int iu = bu * kTileU + tile_du(), iv = r0 + bv * kTileV + tile_dv();
+        const int kl = (int)(t / tpa);
+        const int tr = (int)(t % tpa) * kBandCta + w * 32 + lane;
+        int iu, iv;
         float L[kMaxMat];
-        if (iu < g.n_u && iv < r1) {
+        if (band_ray(tr, r0, R, g.n_u, iu, iv)) {
             trace_ray(p, iu, iv, p.angle0 + kl, L);
         } else {
 #pragma unroll
@@ -581,8 +595,7 @@ int dose_blocks(const ProjParams &p)
 {
     int r0, r1;
     project_band(p, r0, r1);
-    long long tiles = (long long)((p.g.n_u + kTileU - 1) / kTileU) * ((r1 - r0 + kTileV - 1) / kTileV) *
-                      p.n_angles_launch;
+    long long tiles = (long long)band_ctas(r1 - r0, p.g.n_u) * p.n_angles_launch;
     tiles = tiles > 0 ? tiles : 1;   // one block writes zero partials
     if (p.n_e <= 32) return dose_grid<1>(tiles);
     if (p.n_e <= 64) return dose_grid<2>(tiles);
