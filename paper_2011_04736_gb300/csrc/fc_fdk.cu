@@ -230,13 +230,10 @@ namespace {
 constexpr int kFold = 64;        // angles per binary32 partial sum
 }
 
-// kZc z values per thread (the launcher balances the z chunks).  kMinCtas:
-// CTAs per SM the register budget must allow (8 caps it at 32 registers, a
-// few bytes of the binary64 sums spilled; 6 at 40 registers, no spill).
-template <int kZc, int kMinCtas>
-__global__ void __launch_bounds__(256, kMinCtas)
-k_backproject(const __grid_constant__ FdkParams p, const float *__restrict__ f,
-              double *__restrict__ vol)
+// kZc z values per thread (the launcher balances the z chunks).
+template <int kZc>
+__device__ __forceinline__ void backproject_body(const FdkParams &p, const float *__restrict__ f,
+                                                 double *__restrict__ vol)
 {
     const DevGeom &g = p.g;
     const int ix = blockIdx.x * 32 + threadIdx.x;
@@ -300,6 +297,25 @@ k_backproject(const __grid_constant__ FdkParams p, const float *__restrict__ f,
         if (z < nzc) vol[((size_t)(iz0 + z) * g.ny + iy) * g.nx + ix] = accd[z] * p.scale;
 }
 
+// The body as compiled with the default register budget (40 registers, 6
+// CTAs per SM, no spill) and capped for 8 CTAs per SM (32 registers, a few
+// bytes of the binary64 sums spilled).
+template <int kZc>
+__global__ void __launch_bounds__(256) k_backproject(const __grid_constant__ FdkParams p,
+                                                     const float *__restrict__ f,
+                                                     double *__restrict__ vol)
+{
+    backproject_body<kZc>(p, f, vol);
+}
+
+template <int kZc>
+__global__ void __launch_bounds__(256, 8) k_backproject_dense(const __grid_constant__ FdkParams p,
+                                                              const float *__restrict__ f,
+                                                              double *__restrict__ vol)
+{
+    backproject_body<kZc>(p, f, vol);
+}
+
 cudaError_t launch_backproject(const FdkParams &p, const float *filt, double *vol, cudaStream_t s)
 {
     dim3 block(32, 8);
@@ -322,9 +338,9 @@ cudaError_t launch_backproject(const FdkParams &p, const float *filt, double *vo
 #define FC_BP(Z)                                                                  \
     case Z:                                                                       \
         if (dense)                                                                \
-            k_backproject<Z, 8><<<grid, block, 0, s>>>(p, filt, vol);             \
+            k_backproject_dense<Z><<<grid, block, 0, s>>>(p, filt, vol);          \
         else                                                                      \
-            k_backproject<Z, 6><<<grid, block, 0, s>>>(p, filt, vol);             \
+            k_backproject<Z><<<grid, block, 0, s>>>(p, filt, vol);                \
         break;
     switch (zc) {
     FC_BP(1)
