@@ -744,16 +744,25 @@ static void ones_row_pass(const BlurParams &bp, float &vp, float &vs)
 
 // Rows [0, r_lo) and [r_hi, n_v) of image blockIdx.y of tp get vp, the
 // optical-spread row pass of an all-ones row.  (The scatter plane needs no
-// store: the column pass takes the same constant for those rows.)
+// store: the column pass takes the same constant for those rows.)  VEC: four
+// floats per store (n_u a multiple of 4 and tp 16-byte aligned, so no store
+// straddles the gap between the two row ranges).
+template <bool VEC>
 __global__ void __launch_bounds__(256)
 k_fill_const_rows(float *__restrict__ tp, float vp, int n_u, int n_v, int r_lo, int r_hi)
 {
-    const size_t lo = (size_t)r_lo * n_u, hs = (size_t)r_hi * n_u, end = (size_t)n_v * n_u;
+    constexpr int w = VEC ? 4 : 1;
+    const size_t lo = (size_t)r_lo * n_u / w, hs = (size_t)r_hi * n_u / w, end = (size_t)n_v * n_u / w;
     const size_t n_fill = lo + (end - hs);
     const size_t base = (size_t)blockIdx.y * end;
     for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n_fill;
-         e += (size_t)gridDim.x * blockDim.x)
-        tp[base + (e < lo ? e : hs + (e - lo))] = vp;
+         e += (size_t)gridDim.x * blockDim.x) {
+        const size_t i = base + (e < lo ? e : hs + (e - lo));
+        if (VEC)
+            reinterpret_cast<float4 *>(tp)[i] = make_float4(vp, vp, vp, vp);
+        else
+            tp[i] = vp;
+    }
 }
 
 // one_lo, one_hi: when one_hi >= 0, every row of `in` outside [one_lo,
@@ -794,11 +803,15 @@ cudaError_t launch_blur_tc_rows(const BlurParams &bp, const float *in, float *tp
     if (r_hi - r_lo < bp.n_v) {
         float vp, vs;
         ones_row_pass(bp, vp, vs);
-        const size_t per = (size_t)(bp.n_v - (r_hi - r_lo)) * bp.n_u;
+        const bool vec = bp.n_u % 4 == 0 && reinterpret_cast<uintptr_t>(tp) % 16 == 0;
+        const size_t per = (size_t)(bp.n_v - (r_hi - r_lo)) * bp.n_u / (vec ? 4 : 1);
         const size_t want = (per + 256 * 8 - 1) / (256 * 8);
         if (n_img > 65535) return cudaErrorInvalidValue;
         dim3 fgrid((unsigned)(want < 1024 ? want : 1024), n_img);
-        k_fill_const_rows<<<fgrid, 256, 0, s>>>(tp, vp, bp.n_u, bp.n_v, r_lo, r_hi);
+        if (vec)
+            k_fill_const_rows<true><<<fgrid, 256, 0, s>>>(tp, vp, bp.n_u, bp.n_v, r_lo, r_hi);
+        else
+            k_fill_const_rows<false><<<fgrid, 256, 0, s>>>(tp, vp, bp.n_u, bp.n_v, r_lo, r_hi);
     }
     return cudaGetLastError();
 }

@@ -352,12 +352,14 @@ constexpr int kPer = 8;
 constexpr int kQueue = 96;          // queued draws per warp
 constexpr int kWarps = 8;
 
+// One queued draw in three 16-byte words (one shared store or load each):
+// p = (lam, b, a, vr); t = bits of (kf, us, V) and jh = attempt block j << 1
+// | word pair h, bit 31 set while the final test is pending; w = (iu, words
+// z and w of block j, unused).
 struct DrawQueue {
-    int iu[kQueue];
-    float lam[kQueue], b[kQueue], a[kQueue], vr[kQueue];
-    float kf[kQueue], us[kQueue], V[kQueue];
-    uint32_t jh[kQueue];            // attempt block j << 1 | word pair h; bit 31: final pending
-    uint32_t wz[kQueue], ww[kQueue];
+    float4 p[kQueue];
+    uint4 t[kQueue];
+    uint4 w[kQueue];
 };
 }  // namespace
 
@@ -400,17 +402,10 @@ k_poisson(const float *lam, float *out, int n_v, int n_u, int angle0,
         if (enq) {
             const int pos = count + __popc(m & lt);
             if (pos < kQueue) {
-                q.iu[pos] = iu;
-                q.lam[pos] = st.lam;
-                q.b[pos] = st.b;
-                q.a[pos] = st.a;
-                q.vr[pos] = st.vr;
-                q.kf[pos] = kf;
-                q.us[pos] = us;
-                q.V[pos] = V;
-                q.jh[pos] = (st.j << 1) | (uint32_t)st.h | (pending ? 0x80000000u : 0u);
-                q.wz[pos] = st.w.z;
-                q.ww[pos] = st.w.w;
+                q.p[pos] = make_float4(st.lam, st.b, st.a, st.vr);
+                q.t[pos] = make_uint4(__float_as_uint(kf), __float_as_uint(us), __float_as_uint(V),
+                                      (st.j << 1) | (uint32_t)st.h | (pending ? 0x80000000u : 0u));
+                q.w[pos] = make_uint4((uint32_t)iu, st.w.z, st.w.w, 0u);
             } else {
                 // queue full: finish this draw here
                 float r;
@@ -423,26 +418,31 @@ k_poisson(const float *lam, float *out, int n_v, int n_u, int angle0,
     }
     __syncwarp();
     for (int i = lane; i < count; i += 32) {
+        const float4 qp = q.p[i];
+        const uint4 qt = q.t[i], qw = q.w[i];
         noise::Ptrs st;
-        st.lam = q.lam[i];
-        st.b = q.b[i];
-        st.a = q.a[i];
-        st.vr = q.vr[i];
+        st.lam = qp.x;
+        st.b = qp.y;
+        st.a = qp.z;
+        st.vr = qp.w;
         st.loglam = 0.0f;
         st.invalpha = 0.0f;
         st.have_slow = false;
-        st.iu = (uint32_t)q.iu[i];
+        st.iu = qw.x;
         st.iv = (uint32_t)iv;
         st.k = kabs;
-        const uint32_t jh = q.jh[i];
+        const uint32_t jh = qt.w;
         st.j = (jh & 0x7fffffffu) >> 1;
         st.h = (int)(jh & 1u);
         st.key = &seed;
-        st.w = make_uint4(0u, 0u, q.wz[i], q.ww[i]);
+        st.w = make_uint4(0u, 0u, qw.y, qw.z);
         float r;
-        bool done = (jh & 0x80000000u) ? noise::ptrs_final(st, q.kf[i], q.us[i], q.V[i], r) : false;
+        bool done = (jh & 0x80000000u)
+                        ? noise::ptrs_final(st, __uint_as_float(qt.x), __uint_as_float(qt.y),
+                                            __uint_as_float(qt.z), r)
+                        : false;
         while (!done) done = noise::ptrs_attempt(st, r);
-        out[row + q.iu[i]] = r;
+        out[row + qw.x] = r;
     }
 }
 
