@@ -95,7 +95,7 @@ struct fc_handle {
     // device buffers
     float2 *d_trig = nullptr;
     uint8_t *d_labels = nullptr;   // caller layout [nz][ny][nx]
-    uint8_t *d_bricks = nullptr;   // 8x8x8 brick map: uniform label or mixed
+    uint8_t *d_bricks = nullptr;   // 8x8x16 brick map: uniform label or mixed
     float *d_T = nullptr, *d_tp = nullptr, *d_ts = nullptr, *d_counts = nullptr, *d_filt = nullptr;
     double *d_vol = nullptr;
     float *d_hu = nullptr;
@@ -433,7 +433,9 @@ int fc_set_phantom(fc_handle *h, const uint8_t *labels, int n_mat, int where, vo
     if (!h->d_labels) FC_CK(cudaMalloc((void **)&h->d_labels, h->vol_elems));
     if (!h->d_bricks)
         FC_CK(cudaMalloc((void **)&h->d_bricks,
-                         (size_t)((h->g.nx + 7) / 8) * ((h->g.ny + 7) / 8) * ((h->g.nz + 7) / 8)));
+                         (size_t)((h->g.nx + fc::kBrick - 1) / fc::kBrick) *
+                             ((h->g.ny + fc::kBrick - 1) / fc::kBrick) *
+                             ((h->g.nz + fc::kBrickZ - 1) / fc::kBrickZ)));
     FC_CK(cudaMemcpyAsync(h->d_labels, labels, h->vol_elems,
                           where == FC_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, s));
     FC_CK(cudaMemsetAsync(h->d_flag, 0, sizeof(unsigned int), s));

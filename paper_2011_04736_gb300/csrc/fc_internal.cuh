@@ -12,7 +12,8 @@ namespace fc {
 constexpr int kMaxMat = FC_MAX_MATERIALS;
 constexpr int kMaxBins = FC_MAX_BINS;
 constexpr int kMaxTaps = 2 * 256 + 1;  // 2 * ceil(4 * FC_MAX_SIGMA_PX) + 1
-constexpr int kBrick = 8;              // edge of the label bricks the projector skips
+constexpr int kBrick = 8;              // x and y edge of the label bricks the projector skips
+constexpr int kBrickZ = 16;            // their depth along z (the rotation axis)
 constexpr int kMixed = 255;            // brick-map value of a brick with several labels
 
 // Geometry in the precision the kernels use (binary32), derived on the host

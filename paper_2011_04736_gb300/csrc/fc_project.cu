@@ -2,8 +2,11 @@
 // energy-weighting equation I_f = sum_E phi(E) eta(E) I(E)).
 //
 // One thread per detector pixel ray.  The ray is traversed in voxel order
-// (Siddon / Amanatides-Woo) on two levels: 8x8x8 bricks whose voxels all
-// carry one label are crossed in a single step, mixed bricks voxel by voxel.
+// (Siddon / Amanatides-Woo) on two levels: bricks of 8 x 8 voxels in-plane
+// and 16 along the rotation axis whose voxels all carry one label are crossed
+// in a single step, mixed bricks voxel by voxel.  (Rays of one detector
+// column, which share a warp, differ mostly in z; deep bricks keep their brick
+// sequences in step through thin slabs.)
 // Every plane crossing, coarse or fine, is t(i) = fma(i, pitch / d, (lo - A) / d)
 // for the plane's index i, so both levels agree bit for bit on brick faces.
 // The path length inside each material is accumulated run by run: a length
@@ -132,14 +135,14 @@ __device__ __forceinline__ bool trace_ray(const ProjParams &p, int iu, int iv, i
             const float vx = g.dx * ix_, vy = g.dy * iy_, vz = g.dz * iz_;
             const float bx_ = (g.lox - Ax) * ix_, by_ = (g.loy - Ay) * iy_, bz_ = (g.loz - Az) * iz_;
             const int nbx = (nx + kBrick - 1) / kBrick, nby = (ny + kBrick - 1) / kBrick;
-            const int nbz = (nz + kBrick - 1) / kBrick;
-            int bx = ix0 / kBrick, by = iy0 / kBrick, bz = iz0 / kBrick;
+            const int nbz = (nz + kBrickZ - 1) / kBrickZ;
+            int bx = ix0 / kBrick, by = iy0 / kBrick, bz = iz0 / kBrickZ;
             int bi = (bz * nby + by) * nbx + bx;       // brick index, kept incrementally
             // coarse crossing: far face of the current brick along the ray
             // (plane index cp*, kept incrementally)
             int cpx = ux ? min((bx + 1) * kBrick, nx) : bx * kBrick;
             int cpy = uy ? min((by + 1) * kBrick, ny) : by * kBrick;
-            int cpz = uz ? min((bz + 1) * kBrick, nz) : bz * kBrick;
+            int cpz = uz ? min((bz + 1) * kBrickZ, nz) : bz * kBrickZ;
             float tcx = plane_t(cpx, vx, bx_, sx);
             float tcy = plane_t(cpy, vy, by_, sy);
             float tcz = plane_t(cpz, vz, bz_, sz);
@@ -149,7 +152,8 @@ __device__ __forceinline__ bool trace_ray(const ProjParams &p, int iu, int iv, i
             // the ray, so at most nbx + nby + nbz passes occur before an index
             // leaves the grid.  Fine passes inside a brick: each advances one
             // voxel index inside the brick (a step that would cross the brick
-            // face has t >= t_exit and ends the fine walk), at most 3 kBrick.
+            // face has t >= t_exit and ends the fine walk), at most
+            // 2 kBrick + kBrickZ.
             // The budgets only guard against non-finite geometry.
             for (int cb = nbx + nby + nbz + 3; cb > 0; --cb) {
                 const float tmin = fminf(tcx, fminf(tcy, tcz));
@@ -174,8 +178,8 @@ __device__ __forceinline__ bool trace_ray(const ProjParams &p, int iu, int iv, i
                                     min((bx + 1) * kBrick, nx) - 1);
                     int jy = clampi((int)floorf((qy - g.loy) * g.idy), by * kBrick,
                                     min((by + 1) * kBrick, ny) - 1);
-                    int jz = clampi((int)floorf((qz - g.loz) * g.idz), bz * kBrick,
-                                    min((bz + 1) * kBrick, nz) - 1);
+                    int jz = clampi((int)floorf((qz - g.loz) * g.idz), bz * kBrickZ,
+                                    min((bz + 1) * kBrickZ, nz) - 1);
                     // next plane index per axis; an axis that is stepped
                     // has a nonzero direction, so its crossing is a plain fma
                     int fx = jx + ux, fy = jy + uy, fz = jz + uz;
@@ -189,7 +193,7 @@ __device__ __forceinline__ bool trace_ray(const ProjParams &p, int iu, int iv, i
                         t_run = t_cur;
                         cur = lab;
                     }
-                    for (int fb = 3 * kBrick + 3; fb > 0; --fb) {
+                    for (int fb = 2 * kBrick + kBrickZ + 3; fb > 0; --fb) {
                         const float tn = fminf(tfx, fminf(tfy, tfz));
                         if (tn >= t_exit) break;
                         if (tfx == tn) {
@@ -229,7 +233,7 @@ __device__ __forceinline__ bool trace_ray(const ProjParams &p, int iu, int iv, i
                     bz += sz;
                     bi += sz * nbx * nby;
                     inside = (unsigned)bz < (unsigned)nbz;
-                    cpz = min(cpz + kBrick * sz, nz);
+                    cpz = min(cpz + kBrickZ * sz, nz);
                     tcz = fmaf((float)cpz, vz, bz_);
                 }
                 if (!inside) break;
@@ -626,23 +630,23 @@ cudaError_t launch_dose(const ProjParams &p, const DoseParams &d, double *part,
     return cudaGetLastError();
 }
 
-// One warp per 8x8x8 brick (lane l takes voxels l, l + 32, ... of the
+// One warp per 8x8x16 brick (lane l takes voxels l, l + 32, ... of the
 // brick, clipped to the grid): its single label, or kMixed; flags any label
 // >= n_mat.
 __global__ void k_brick_map(const uint8_t *__restrict__ lab, uint8_t *__restrict__ bricks, int nx,
                             int ny, int nz, int n_mat, unsigned int *bad)
 {
     const int nbx = (nx + kBrick - 1) / kBrick, nby = (ny + kBrick - 1) / kBrick;
-    const int nbz = (nz + kBrick - 1) / kBrick;
+    const int nbz = (nz + kBrickZ - 1) / kBrickZ;
     const int nb = nbx * nby * nbz;
     const int lane = threadIdx.x & 31;
     const int warps = (gridDim.x * blockDim.x) >> 5;
     for (int b = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; b < nb; b += warps) {
         const int bx = b % nbx, by = (b / nbx) % nby, bz = b / (nbx * nby);
-        const int x0 = bx * kBrick, y0 = by * kBrick, z0 = bz * kBrick;
+        const int x0 = bx * kBrick, y0 = by * kBrick, z0 = bz * kBrickZ;
         const int first = lab[((size_t)z0 * ny + y0) * nx + x0];
         bool uniform = true, badlab = false;
-        for (int v = lane; v < kBrick * kBrick * kBrick; v += 32) {
+        for (int v = lane; v < kBrick * kBrick * kBrickZ; v += 32) {
             const int x = x0 + v % kBrick, y = y0 + (v / kBrick) % kBrick, z = z0 + v / (kBrick * kBrick);
             if (x < nx && y < ny && z < nz) {
                 const int l = lab[((size_t)z * ny + y) * nx + x];
@@ -663,7 +667,7 @@ cudaError_t launch_brick_map(const uint8_t *labels, uint8_t *bricks, int nx, int
                              int n_mat, unsigned int *bad, cudaStream_t s)
 {
     const int nb = ((nx + kBrick - 1) / kBrick) * ((ny + kBrick - 1) / kBrick) *
-                   ((nz + kBrick - 1) / kBrick);
+                   ((nz + kBrickZ - 1) / kBrickZ);
     const int blocks = (nb + 3) / 4 < 152 * 16 ? (nb + 3) / 4 : 152 * 16;   // 4 warps per block
     k_brick_map<<<blocks, 128, 0, s>>>(labels, bricks, nx, ny, nz, n_mat, bad);
     return cudaGetLastError();
