@@ -229,6 +229,32 @@ int fc_set_energy_groups(fc_handle *h, const fc_energy_groups *g);
 int fc_reconstruct(fc_handle *h, const float *counts, int counts_where,
                    double *vol_mu, float *vol_hu, int out_where, void *stream);
 
+/* FDK backprojector variant (instrumentation and testing: the paper has no
+ * counterpart; every variant computes the same backprojection of
+ * fc_reconstruct, Sec. II.G, the sums differing only in rounding).
+ *   FC_BP_AUTO          (default) the fastest applicable for the geometry:
+ *                       FC_BP_SLAB where it applies, else FC_BP_CHUNKED_DENSE
+ *                       for grids of two or more waves, else FC_BP_CHUNKED;
+ *   FC_BP_CHUNKED       one thread per (x, y) column and chunk of z slices,
+ *                       four bilinear taps per voxel update;
+ *   FC_BP_CHUNKED_DENSE the same body capped at 32 registers (8 CTAs per SM);
+ *   FC_BP_SLAB          one thread per column and every slice; each slice
+ *                       reuses the previous slice's detector row.  Applies
+ *                       when nz <= 16 and the z pitch projects to at most 0.98
+ *                       detector rows at every voxel (dz SDD / (SAD - r_max)
+ *                       <= 0.98 dv, r_max the half-diagonal of the volume).
+ * fc_reconstruct and fc_cnr_grad fail with FC_EINVAL when the requested
+ * variant does not apply.  fc_backprojector_in_use writes the variant the
+ * current request resolves to for the handle's geometry.
+ * Errors: FC_EINVAL (unknown variant, null pointers, not applicable),
+ * FC_ESTATE (no geometry). */
+#define FC_BP_AUTO          0
+#define FC_BP_CHUNKED       1
+#define FC_BP_CHUNKED_DENSE 2
+#define FC_BP_SLAB          3
+int fc_set_backprojector(fc_handle *h, int variant);
+int fc_backprojector_in_use(fc_handle *h, int *variant);
+
 /* Water region used for HU (Sec. II.G): voxels whose centre lies within
  * radius_cm of the rotation axis, excluding floor(z_margin * nz) slices at
  * each end.  Default 1.0 cm and 0.1.  Errors: FC_EINVAL. */
@@ -409,9 +435,12 @@ int fc_cnr_grad(fc_handle *h, const double *logits, const double *D, const doubl
  * point exists for callers that cannot allocate device memory while they
  * run -- their device memory is owned by another allocator (for example a
  * pool that reserved the whole GPU at start-up) or fixed by a budget that
- * forbids allocation after initialisation.  It computes the same
- * I = n0 (G_psf (x) T + spr G_scatter (x) T) as fc_project's FC_OUT_INTENSITY
- * (same kernels), for T and I of n_img x n_v x n_u floats in device memory
+ * forbids allocation after initialisation.  It computes the operator of
+ * fc_project's FC_OUT_INTENSITY, I = n0 (G_psf (x) T + spr G_scatter (x) T),
+ * with fc_project's direct f32 blur passes (the ones fc_project falls back
+ * to for radii beyond its tensor-core passes), so it agrees with
+ * FC_OUT_INTENSITY within 1e-4 relative, not bit for bit, and is slower.
+ * T and I are n_img x n_v x n_u floats in device memory
  * provided by the caller, without a handle, and calls no cudaMalloc,
  * cudaFree or other allocating routine.  The two row-pass intermediates live
  * in a file-scope device array of FC_STATIC_SCRATCH_FLOATS floats (32 MiB)
@@ -420,9 +449,12 @@ int fc_cnr_grad(fc_handle *h, const double *logits, const double *D, const doubl
  * The first call on a device looks up the array's device address (once per
  * device, with that device current); make that first call before any stream
  * capture.  Every call shares the array: calls whose kernels overlap on the
- * GPU race on it, so order them (one stream, or events).  Runs on the current
- * device and `stream`.  Errors: FC_EINVAL (null pointers, sizes, sigmas,
- * spr < 0, n0 <= 0), FC_ECUDA. */
+ * GPU race on it, so order them (one stream, or events).  The looked-up
+ * address is kept for the life of the process: a device reset while the
+ * library is loaded is not supported.  Runs on the current device and
+ * `stream`.  Errors: FC_EINVAL (null pointers, sizes, sigmas, spr < 0,
+ * n0 <= 0, a detector too wide for the row pass or too tall for the column
+ * pass's shared-memory staging), FC_ECUDA. */
 #define FC_STATIC_SCRATCH_FLOATS (8u << 20)
 int fc_detector_blur_static(const float *T, float *I, int n_img, int n_v, int n_u,
                             double psf_sigma_px, double scatter_sigma_px, double spr, double n0,

@@ -11,6 +11,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <atomic>
 #include <string>
 #include <vector>
 
@@ -68,6 +69,22 @@ void dfree(T *&p)
 
 void fc::set_last_error(const char *msg) { g_err = msg; }
 
+int fc::sm_count()
+{
+    constexpr int kMaxDev = 64;
+    static std::atomic<int> cache[kMaxDev];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 1;
+    if (dev >= 0 && dev < kMaxDev) {
+        const int c = cache[dev].load(std::memory_order_relaxed);
+        if (c > 0) return c;
+    }
+    int n = 0;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1) return 1;
+    if (dev >= 0 && dev < kMaxDev) cache[dev].store(n, std::memory_order_relaxed);
+    return n;
+}
+
 struct fc_handle {
     int device = 0;
     bool has_geom = false, has_phantom = false, has_spec = false, has_counts = false;
@@ -83,6 +100,7 @@ struct fc_handle {
     uint64_t seed = 0;
     int noise = 0;
     int noise_order = FC_NOISE_AFTER_BLUR;
+    int bp_request = FC_BP_AUTO;   // FDK backprojector variant (fc_set_backprojector)
     // energy-group detector model (off when n_groups == 0)
     int n_groups = 0;
     int grp_end[FC_MAX_GROUPS] = {0};
@@ -574,20 +592,20 @@ static int run_blur(fc_handle *h, const float *in, float *out, size_t off, int n
     b.spr = (float)spr;
     if (!fc::blur_tc_supported(b)) {
         // radii beyond the tensor-core path: direct f32 passes
+        if (!fc::blur_rows_fit(b))
+            return fail(FC_EINVAL, "fc_project: detector too wide for the row blur (n_u %d)", h->g.n_u);
+        if (!fc::blur_cols_fit(b))
+            return fail(FC_EINVAL, "fc_project: detector too tall for the column blur (n_v %d)", h->g.n_v);
         {
             Trace t(h, FC_K_BLUR_ROWS, 1, s);
             FC_CK(fc::launch_blur_rows(b, in, h->d_tp + off, h->d_ts + off, n, s));
             t.end();
         }
-        cudaError_t e;
         {
             Trace t(h, FC_K_BLUR_COLS, 1, s);
-            e = fc::launch_blur_cols(b, h->d_tp + off, h->d_ts + off, out, n, s);
-            if (e == cudaSuccess) t.end();
+            FC_CK(fc::launch_blur_cols(b, h->d_tp + off, h->d_ts + off, out, n, s));
+            t.end();
         }
-        if (e == cudaErrorInvalidValue)
-            return fail(FC_EINVAL, "fc_project: detector too tall for the column blur (n_v %d)", h->g.n_v);
-        FC_CK(e);
         return FC_OK;
     }
     {
@@ -898,6 +916,44 @@ int fc_set_noise_order(fc_handle *h, int order)
     return FC_OK;
 }
 
+int fc_set_backprojector(fc_handle *h, int variant)
+{
+    if (!h) return fail(FC_EINVAL, "fc_set_backprojector: null handle");
+    if (variant < FC_BP_AUTO || variant > FC_BP_SLAB)
+        return fail(FC_EINVAL, "fc_set_backprojector: unknown variant %d", variant);
+    h->bp_request = variant;
+    return FC_OK;
+}
+
+// FdkParams of the handle's geometry (no buffers touched).
+static void fill_fdk_params(const fc_handle *h, fc::FdkParams *p)
+{
+    memset(p, 0, sizeof(*p));
+    p->g = h->dg;
+    p->trig = h->d_trig;
+    p->log_flood = (float)log(h->n_groups ? h->n0 : h->n0 * (1.0 + h->spr));
+    p->tau = (float)(h->g.du_cm * h->g.sad_cm / h->g.sdd_cm);
+    p->mag = (float)(h->g.sad_cm / h->g.sdd_cm);
+    p->scale = h->g.arc_rad / (2.0 * h->g.n_angles);
+    fc::fdk_row_range(h->dg, &p->v_lo, &p->v_hi);
+    p->pw = fdk_row_pitch(h->g.n_u);
+    p->ph = p->v_hi - p->v_lo + 1 + 3;
+}
+
+int fc_backprojector_in_use(fc_handle *h, int *variant)
+{
+    if (!h || !variant) return fail(FC_EINVAL, "fc_backprojector_in_use: null argument");
+    if (!h->has_geom) return fail(FC_ESTATE, "fc_backprojector_in_use: geometry not set");
+    DeviceGuard dgd(h->device);
+    fc::FdkParams p;
+    fill_fdk_params(h, &p);
+    *variant = fc::backproject_variant(p, h->bp_request);
+    if (*variant < 0)
+        return fail(FC_EINVAL, "fc_backprojector_in_use: variant %d does not apply to this geometry",
+                    h->bp_request);
+    return FC_OK;
+}
+
 int fc_project_lengths(fc_handle *h, int angle_begin, int angle_count, float *L, void *stream)
 {
     if (!h || !L) return fail(FC_EINVAL, "fc_project_lengths: null argument");
@@ -1002,25 +1058,21 @@ int fc_reconstruct(fc_handle *h, const float *counts, int counts_where, double *
         h->has_counts = true;
     }
     fc::FdkParams p;
-    p.g = h->dg;
-    p.trig = h->d_trig;
     // flood: T = 1 through the detector model (single kernel: N0 (1 + SPR);
     // energy groups: N0, the scatter profile needing a phantom)
-    p.log_flood = (float)log(h->n_groups ? h->n0 : h->n0 * (1.0 + h->spr));
-    p.tau = (float)(h->g.du_cm * h->g.sad_cm / h->g.sdd_cm);
-    p.mag = (float)(h->g.sad_cm / h->g.sdd_cm);
-    p.scale = h->g.arc_rad / (2.0 * h->g.n_angles);
-    fc::fdk_row_range(h->dg, &p.v_lo, &p.v_hi);
-    p.pw = fdk_row_pitch(h->g.n_u);
-    p.ph = p.v_hi - p.v_lo + 1 + 3;
+    fill_fdk_params(h, &p);
     {
         Trace t(h, FC_K_FDK_FILTER, 1, s);
         FC_CK(fc::launch_fdk_filter(p, src, h->d_filt, s));
         t.end();
     }
     {
+        const int bpv = fc::backproject_variant(p, h->bp_request);
+        if (bpv < 0)
+            return fail(FC_EINVAL, "fc_reconstruct: backprojector variant %d does not apply to this geometry",
+                        h->bp_request);
         Trace t(h, FC_K_BACKPROJECT, 1, s);
-        FC_CK(fc::launch_backproject(p, h->d_filt, h->d_vol, s));
+        FC_CK(fc::launch_backproject(p, h->d_filt, h->d_vol, bpv, s));
         t.end();
     }
     if (vol_hu) {
@@ -1557,7 +1609,12 @@ int fc_cnr_grad(fc_handle *h, const double *logits, const double *D, const doubl
     FC_CK(fc::launch_blur_cols(b, h->d_tp, h->d_ts, h->d_I, na, s));
     FC_CK(fc::launch_noise_gauss(h->d_I, z, h->d_counts, np, s));
     FC_CK(fc::launch_fdk_filter(pf, h->d_counts, h->d_filt, s));
-    FC_CK(fc::launch_backproject(pf, h->d_filt, h->d_vol, s));
+    {
+        const int bpv = fc::backproject_variant(pf, h->bp_request);
+        if (bpv < 0) return fail(FC_EINVAL, "fc_cnr_grad: backprojector variant %d does not apply to this geometry",
+                                 h->bp_request);
+        FC_CK(fc::launch_backproject(pf, h->d_filt, h->d_vol, bpv, s));
+    }
     if (!h->d_cnr_work) FC_CK(cudaMalloc((void **)&h->d_cnr_work, fc::cnr_work_doubles() * sizeof(double)));
     FC_CK(fc::launch_cnr(cp, h->d_vol, h->d_gmu, h->d_gwd + fc::kMaxBins, h->d_cnr_work, s));
     const bool grads = g_logits || g_D || g_rho;

@@ -544,7 +544,7 @@ cudaError_t launch_project_density_adjoint(const AdjParams &p, const float *rho,
 
 cudaError_t launch_noise_gauss(const float *I, const float *z, float *K, size_t n, cudaStream_t s)
 {
-    k_noise_gauss<<<152 * 8, 256, 0, s>>>(I, z, K, n);
+    k_noise_gauss<<<sm_count() * 8, 256, 0, s>>>(I, z, K, n);
     return cudaGetLastError();
 }
 

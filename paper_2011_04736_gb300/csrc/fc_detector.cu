@@ -275,14 +275,28 @@ static cudaError_t launch_cols_tw(const BlurParams &p, const float *tp, const fl
     return cudaGetLastError();
 }
 
+static size_t row_smem_bytes(const BlurParams &p)
+{
+    const int R = p.rs > p.rp ? p.rs : p.rp;
+    const int span = p.n_u + 2 * R + 2 * kOut;
+    return (size_t)(span + span / 32 + 2) * sizeof(float);
+}
+
+namespace {
+constexpr size_t kDirectSmemLimit = 220 * 1024;   // dynamic shared memory the direct passes ask for
+}
+
+bool blur_rows_fit(const BlurParams &p) { return row_smem_bytes(p) <= kDirectSmemLimit; }
+
+bool blur_cols_fit(const BlurParams &p) { return col_smem_bytes(p, 9) <= kDirectSmemLimit; }
+
 template <bool ADJ>
 static cudaError_t rows_pass(const BlurParams &p, const float *T, float *tp, float *ts, int n_img,
                              cudaStream_t s)
 {
     if (n_img <= 0) return cudaSuccess;
-    const int R = p.rs > p.rp ? p.rs : p.rp;
-    const int span = p.n_u + 2 * R + 2 * kOut;
-    const size_t row_smem = (size_t)(span + span / 32 + 2) * sizeof(float);
+    if (!blur_rows_fit(p)) return cudaErrorInvalidValue;
+    const size_t row_smem = row_smem_bytes(p);
     cudaError_t e;
     if (row_smem > 48 * 1024) {
         e = cudaFuncSetAttribute(k_blur_rows<ADJ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -302,7 +316,7 @@ static cudaError_t cols_pass(const BlurParams &p, const float *tp, const float *
     if (n_img <= 0) return cudaSuccess;
     // Prefer 16-column tiles (about 3 CTAs per SM for a 384-row detector);
     // fall back to narrower tiles for tall detectors.
-    const size_t limit = 220 * 1024;
+    const size_t limit = kDirectSmemLimit;
     if (col_smem_bytes(p, 18) <= limit / 2) return launch_cols_tw<16, 18, ADJ>(p, tp, ts, out, n_img, s);
     if (col_smem_bytes(p, 9) <= limit) return launch_cols_tw<8, 9, ADJ>(p, tp, ts, out, n_img, s);
     return cudaErrorInvalidValue;

@@ -228,7 +228,26 @@ void fdk_row_range(const DevGeom &g, int *v_lo, int *v_hi)
 
 namespace {
 constexpr int kFold = 64;        // angles per binary32 partial sum
+constexpr int kSlabMaxNz = 16;   // slices the thin-slab kernel keeps per thread
+// largest projected z pitch (detector rows) the thin-slab kernel takes: the
+// row index may then advance by at most one per slice, rounding included
+constexpr double kSlabMaxStep = 0.98;
+
+// Chunked kernel: z values per thread as many as possible (the per-angle
+// column set-up is shared by them) while keeping about 48 resident warps
+// per SM; the chunks are balanced.
+void chunked_launch_shape(const FdkParams &p, int *zc_out, dim3 *grid)
+{
+    const long cols = (long)p.g.nx * p.g.ny;
+    const long want = (long)sm_count() * 1536;
+    int zc = 8;
+    while (zc > 1 && cols * ((p.g.nz + zc - 1) / zc) < want) --zc;
+    const int nchunk = (p.g.nz + zc - 1) / zc;
+    zc = (p.g.nz + nchunk - 1) / nchunk;
+    *zc_out = zc;
+    *grid = dim3((p.g.nx + 31) / 32, (p.g.ny + 7) / 8, (p.g.nz + zc - 1) / zc);
 }
+}  // namespace
 
 // kZc z values per thread (the launcher balances the z chunks).
 template <int kZc>
@@ -316,25 +335,138 @@ __global__ void __launch_bounds__(256, 8) k_backproject_dense(const __grid_const
     backproject_body<kZc>(p, f, vol);
 }
 
-cudaError_t launch_backproject(const FdkParams &p, const float *filt, double *vol, cudaStream_t s)
+// Thin slabs: the z pitch projects to less than one detector row at every
+// voxel (dz SDD / U < dv), which holds for the paper-scale 10-slice volumes
+// with a fine voxel pitch.  One thread per (x, y) column then walks all NZ
+// slices of its column for each angle.  Slice z samples rows j_z and j_z + 1
+// with j_z - j_{z-1} in {0, 1}, so the u-interpolated value of each row is
+// formed once: slice z loads only row j_z + 1 (two taps) and takes row j_z
+// from the slice before (the same row, or the one it loaded).  Per update
+// that is two tap loads instead of four and one u interpolation instead of
+// two; each slice's arithmetic is otherwise the chunked kernel's, so the
+// sums are the same.  Binary32 partial sums over kFold angles are folded
+// into binary64 sums kept in shared memory.
+template <int NZ>
+__global__ void __launch_bounds__(256)
+k_backproject_slab(const __grid_constant__ FdkParams p, const float *__restrict__ f,
+                   double *__restrict__ vol)
 {
-    dim3 block(32, 8);
-    // z values per thread: as many as possible (the per-angle column set-up
-    // is shared by them) while keeping about 48 resident warps per SM.
-    const long cols = (long)p.g.nx * p.g.ny;
-    const long want = 152L * 1536;
-    int zc = 8;
-    while (zc > 1 && cols * ((p.g.nz + zc - 1) / zc) < want) --zc;
-    {
-        const int nchunk = (p.g.nz + zc - 1) / zc;   // balance the chunks
-        zc = (p.g.nz + nchunk - 1) / nchunk;
+    __shared__ double accd[NZ][256];
+    const DevGeom &g = p.g;
+    const int t = threadIdx.y * 32 + threadIdx.x;
+    const int ix = blockIdx.x * 32 + threadIdx.x;
+    const int iy = blockIdx.y * 8 + threadIdx.y;
+#pragma unroll
+    for (int z = 0; z < NZ; ++z) accd[z][t] = 0.0;
+    if (ix >= g.nx || iy >= g.ny) return;   // no block-wide barrier follows
+    const float x = ((float)ix - 0.5f * (float)(g.nx - 1)) * g.dx;
+    const float y = ((float)iy - 0.5f * (float)(g.ny - 1)) * g.dy;
+    const float z0 = -0.5f * (float)(g.nz - 1) * g.dz;
+    const size_t plane = (size_t)p.ph * p.pw;
+    const int pw = p.pw;
+    const float cu1 = g.cu + 1.0f, cv1 = g.cv - (float)p.v_lo + 1.0f;
+    const float umax = (float)(p.pw - 2), vmaxp = (float)(p.ph - 2);
+    const float sdd_du = g.sdd / g.du, sdd_dv = g.sdd / g.dv;
+    for (int kb = 0; kb < g.n_angles; kb += kFold) {
+        const int ke = min(g.n_angles, kb + kFold);
+        float accf[NZ];
+#pragma unroll
+        for (int z = 0; z < NZ; ++z) accf[z] = 0.0f;
+#pragma unroll 2
+        for (int k = kb; k < ke; ++k) {
+            const float2 cs = p.trig[k];
+            const float U = g.sad - (x * cs.x + y * cs.y);
+            const float ru = y * cs.x - x * cs.y;
+            const float iU = __frcp_rn(U);
+            const float fu = fminf(fmaxf(fmaf(ru * iU, sdd_du, cu1), 0.0f), umax);
+            const float w = (g.sad * iU) * (g.sad * iU);
+            const float fv0 = fmaf(z0 * iU, sdd_dv, cv1);
+            const float dfv = g.dz * iU * sdd_dv;
+            const float fu0 = floorf(fu);
+            const float au = fu - fu0;
+            const float *fk = f + (size_t)k * plane + (int)fu0;
+            float lo = 0.0f, hi = 0.0f;
+            int jp = 0;
+#pragma unroll
+            for (int z = 0; z < NZ; ++z) {
+                const float fv = fminf(fmaxf(fmaf((float)z, dfv, fv0), 0.0f), vmaxp);
+                const float fvf = floorf(fv);
+                const float av = fv - fvf;
+                const int j = (int)fvf;
+                const float *r = fk + (j + 1) * pw;
+                const float b0 = __ldg(r), b1 = __ldg(r + 1);
+                const float nh = fmaf(au, b1 - b0, b0);
+                if (z == 0) {
+                    const float a0 = __ldg(r - pw), a1 = __ldg(r - pw + 1);
+                    lo = fmaf(au, a1 - a0, a0);
+                } else {
+                    lo = j == jp ? lo : hi;
+                }
+                hi = nh;
+                jp = j;
+                accf[z] = fmaf(w, fmaf(av, hi - lo, lo), accf[z]);
+            }
+        }
+#pragma unroll
+        for (int z = 0; z < NZ; ++z) accd[z][t] += (double)accf[z];
     }
-    dim3 grid((p.g.nx + 31) / 32, (p.g.ny + 7) / 8, (p.g.nz + zc - 1) / zc);
+#pragma unroll
+    for (int z = 0; z < NZ; ++z) vol[((size_t)z * g.ny + iy) * g.nx + ix] = accd[z][t] * p.scale;
+}
+
+// Largest projected z pitch, in detector rows, over the voxels of the
+// volume (U >= SAD - r_max); +inf when the volume reaches the source.
+double fdk_slab_row_step(const DevGeom &g)
+{
+    const double hx = 0.5 * g.nx * (double)g.dx, hy = 0.5 * g.ny * (double)g.dy;
+    const double umin = (double)g.sad - sqrt(hx * hx + hy * hy);
+    if (umin <= 0.0) return INFINITY;
+    return (double)g.dz * (double)g.sdd / umin / (double)g.dv;
+}
+
+int backproject_variant(const FdkParams &p, int request)
+{
+    const bool slab_ok = p.g.nz <= kSlabMaxNz && fdk_slab_row_step(p.g) <= kSlabMaxStep;
+    if (request == FC_BP_SLAB) return slab_ok ? FC_BP_SLAB : -1;
+    if (request == FC_BP_CHUNKED || request == FC_BP_CHUNKED_DENSE) return request;
+    if (request != FC_BP_AUTO) return -1;
+    if (slab_ok) return FC_BP_SLAB;
+    int zc;
+    dim3 grid;
+    chunked_launch_shape(p, &zc, &grid);
     // A grid of two or more waves at 6 CTAs per SM runs faster with 8
-    // resident CTAs (more warps to hide the tap latency; paper-scale MV case
-    // 10.26 -> 9.21 ms); a grid of about one wave (catphan_kv: 1024 CTAs)
-    // runs faster with the unspilled 40-register kernel.
-    const bool dense = (long)grid.x * grid.y * grid.z >= 2L * 152 * 6;
+    // resident CTAs (more warps to hide the tap latency; 512^2 x 10 voxels
+    // with 180 projections: 1.087 -> 0.872 ms); a grid of about one wave
+    // (256^2 x 10: 1024 CTAs) runs faster with the unspilled 40-register
+    // kernel.
+    return (long)grid.x * grid.y * grid.z >= 2L * sm_count() * 6 ? FC_BP_CHUNKED_DENSE : FC_BP_CHUNKED;
+}
+
+cudaError_t launch_backproject(const FdkParams &p, const float *filt, double *vol, int variant,
+                               cudaStream_t s)
+{
+    if (variant == FC_BP_SLAB) {
+        dim3 block(32, 8);
+        dim3 grid((p.g.nx + 31) / 32, (p.g.ny + 7) / 8);
+#define FC_BPS(Z)                                                              \
+    case Z:                                                                    \
+        k_backproject_slab<Z><<<grid, block, 0, s>>>(p, filt, vol);            \
+        break;
+        switch (p.g.nz) {
+        FC_BPS(1) FC_BPS(2) FC_BPS(3) FC_BPS(4) FC_BPS(5) FC_BPS(6) FC_BPS(7) FC_BPS(8)
+        FC_BPS(9) FC_BPS(10) FC_BPS(11) FC_BPS(12) FC_BPS(13) FC_BPS(14) FC_BPS(15) FC_BPS(16)
+        default:
+            return cudaErrorInvalidValue;
+        }
+#undef FC_BPS
+        return cudaGetLastError();
+    }
+    if (variant != FC_BP_CHUNKED && variant != FC_BP_CHUNKED_DENSE) return cudaErrorInvalidValue;
+    const bool dense = variant == FC_BP_CHUNKED_DENSE;
+    dim3 block(32, 8);
+    int zc;
+    dim3 grid;
+    chunked_launch_shape(p, &zc, &grid);
 #define FC_BP(Z)                                                                  \
     case Z:                                                                       \
         if (dense)                                                                \
@@ -427,7 +559,7 @@ cudaError_t launch_hu(const DevGeom &g, const double *vol, float *hu, double *pa
     k_roi_partial<<<kRoiBlocks, 256, 0, s>>>(g, vol, partials, radius * radius, zcut);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    k_hu<<<152 * 4, 256, 0, s>>>(g, vol, partials, hu);
+    k_hu<<<sm_count() * 4, 256, 0, s>>>(g, vol, partials, hu);
     return cudaGetLastError();
 }
 

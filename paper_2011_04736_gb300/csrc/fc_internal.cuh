@@ -35,7 +35,7 @@ struct ProjParams {
     DevGeom g;
     const float2 *trig;     // [n_angles] (cos, sin) of each angle
     const uint8_t *labels;  // [nz][ny][nx]
-    const uint8_t *bricks;  // [nz/8][ny/8][nx/8] (rounded up): uniform label or kMixed
+    const uint8_t *bricks;  // [ceil(nz/kBrickZ)][ceil(ny/kBrick)][ceil(nx/kBrick)]: uniform label or kMixed
     int angle0;             // absolute index of the first angle of the launch
     int n_angles_launch;
     int v_hit_lo, v_hit_hi; // detector rows whose rays can meet the voxel slab
@@ -158,6 +158,17 @@ void fdk_row_range(const DevGeom &g, int *v_lo, int *v_hi);
 // Sets the message fc_last_error() returns on this thread.
 void set_last_error(const char *msg);
 
+// Streaming multiprocessors of the current device (queried once per device
+// ordinal; 1 if the query fails).  Launchers size persistent and grid-stride
+// grids from it.
+int sm_count();
+
+// FDK backprojector variants (FC_BP_* in fastcat.h).  backproject_variant
+// resolves a request for the geometry (-1: not applicable);
+// fdk_slab_row_step is the largest projected z pitch in detector rows.
+double fdk_slab_row_step(const DevGeom &g);
+int backproject_variant(const FdkParams &p, int request);
+
 // ---- learned surrogate of the energy integral (fc_mlp.cu) ----
 constexpr int kMlpHidden = 128;
 constexpr int kMlpIn = 8;
@@ -255,6 +266,10 @@ cudaError_t launch_group_blur(const GroupParams &g, const float *P, float *prof,
                               int angle0, int n_img, cudaStream_t s);
 cudaError_t launch_blur_rows(const BlurParams &p, const float *T, float *tp, float *ts,
                              int n_img, cudaStream_t s);
+// whether the direct f32 row / column pass fits its shared-memory staging
+// (a row of n_u + 2R samples; a tile of columns over all n_v rows)
+bool blur_rows_fit(const BlurParams &p);
+bool blur_cols_fit(const BlurParams &p);
 cudaError_t launch_blur_cols(const BlurParams &p, const float *tp, const float *ts, float *out,
                              int n_img, cudaStream_t s);
 // transposed blur: gout = n0 (G_psf^T + spr G_scatter^T) gin (tp, ts scratch)
@@ -264,7 +279,7 @@ cudaError_t launch_poisson(const float *lam, float *out, int n_img, int n_v, int
                            int angle0, uint64_t seed, cudaStream_t s);
 cudaError_t launch_fdk_filter(const FdkParams &p, const float *counts, float *filt,
                               cudaStream_t s);
-cudaError_t launch_backproject(const FdkParams &p, const float *filt, double *vol,
+cudaError_t launch_backproject(const FdkParams &p, const float *filt, double *vol, int variant,
                                cudaStream_t s);
 cudaError_t launch_hu(const DevGeom &g, const double *vol, float *hu, double *partials,
                       float radius, int zcut, cudaStream_t s);

@@ -702,7 +702,8 @@ cudaError_t launch_mlp_eval(const SurrogateParams &p, const float *L, long long 
                                          kInfSmem);
     if (e != cudaSuccess) return e;
     const long long ntiles = (n + 127) / 128;
-    const int grid = (int)(ntiles < 152 ? ntiles : 152);   // one CTA per SM (141 KB smem)
+    const int sms = sm_count();
+    const int grid = (int)(ntiles < sms ? ntiles : sms);   // one CTA per SM (141 KB smem)
     k_mlp_eval<<<grid, 128, kInfSmem, s>>>(p, L, n, lnT, n_fallback, err);
     return cudaGetLastError();
 }
@@ -718,7 +719,7 @@ cudaError_t launch_exp(const float *x, float *y, long long n, cudaStream_t s)
 {
     if (n <= 0) return cudaSuccess;
     long long blocks = (n + 255) / 256;
-    if (blocks > 152 * 8) blocks = 152 * 8;
+    if (blocks > sm_count() * 8) blocks = sm_count() * 8;
     k_exp<<<(int)blocks, 256, 0, s>>>(x, y, n);
     return cudaGetLastError();
 }
@@ -728,7 +729,7 @@ cudaError_t launch_energy_sum_lengths(const SurrogateParams &p, const float *L, 
 {
     if (n <= 0) return cudaSuccess;
     long long blocks = (n + 255) / 256;
-    if (blocks > 152 * 16) blocks = 152 * 16;
+    if (blocks > sm_count() * 16) blocks = sm_count() * 16;
     k_energy_sum_lengths<<<(int)blocks, 256, 0, s>>>(p, L, n, lnT);
     return cudaGetLastError();
 }
@@ -737,7 +738,7 @@ cudaError_t launch_mlp_lmax(const float *L, long long n, int n_mat, unsigned int
 {
     if (n <= 0) return cudaSuccess;
     long long blocks = (n + 255) / 256;
-    if (blocks > 152 * 8) blocks = 152 * 8;
+    if (blocks > sm_count() * 8) blocks = sm_count() * 8;
     k_mlp_lmax<<<(int)blocks, 256, 0, s>>>(L, n, n_mat, mx);
     return cudaGetLastError();
 }
@@ -754,7 +755,8 @@ cudaError_t launch_mlp_step(const SurrogateParams &p, const float *L, const floa
     e = cudaFuncSetAttribute(k_mlp_wgrad, cudaFuncAttributeMaxDynamicSharedMemorySize, 65536);
     if (e != cudaSuccess) return e;
     const int ntiles = (B + 127) / 128;
-    k_mlp_train<<<ntiles < 152 ? ntiles : 152, 128, kTrSmem, s>>>(p, L, y, n, B, sample, seed, step,
+    const int sms = sm_count();
+    k_mlp_train<<<ntiles < sms ? ntiles : sms, 128, kTrSmem, s>>>(p, L, y, n, B, sample, seed, step,
                                                                   w, loss, err);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;

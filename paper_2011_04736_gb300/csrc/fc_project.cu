@@ -613,7 +613,7 @@ cudaError_t launch_dose(const ProjParams &p, const DoseParams &d, double *part,
     const size_t nvox = (size_t)p.g.nx * p.g.ny * p.g.nz;
     cudaError_t e = cudaMemsetAsync(count, 0, kMaxMat * sizeof(unsigned long long), s);
     if (e != cudaSuccess) return e;
-    k_label_count<<<152 * 4, 256, 0, s>>>(p.labels, nvox, d.n_mat, count);
+    k_label_count<<<sm_count() * 4, 256, 0, s>>>(p.labels, nvox, d.n_mat, count);
     const dim3 blk(32, 8);
     int r0, r1;
     project_band(p, r0, r1);
@@ -668,7 +668,7 @@ cudaError_t launch_brick_map(const uint8_t *labels, uint8_t *bricks, int nx, int
 {
     const int nb = ((nx + kBrick - 1) / kBrick) * ((ny + kBrick - 1) / kBrick) *
                    ((nz + kBrickZ - 1) / kBrickZ);
-    const int blocks = (nb + 3) / 4 < 152 * 16 ? (nb + 3) / 4 : 152 * 16;   // 4 warps per block
+    const int blocks = (nb + 3) / 4 < sm_count() * 16 ? (nb + 3) / 4 : sm_count() * 16;   // 4 warps per block
     k_brick_map<<<blocks, 128, 0, s>>>(labels, bricks, nx, ny, nz, n_mat, bad);
     return cudaGetLastError();
 }

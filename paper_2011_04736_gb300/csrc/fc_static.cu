@@ -14,6 +14,10 @@
 // whose kernels overlap on the GPU (different streams, or different host
 // threads without ordering) race on it.  The row pass overwrites every
 // scratch element the column pass then reads, so nothing needs clearing.
+// The array's device address is looked up once per device and kept for the
+// life of the process; a device reset (cudaDeviceReset, or anything else
+// that destroys the primary context) invalidates it and is not supported
+// while this library is loaded.
 #include <math.h>
 #include <string.h>
 
@@ -93,6 +97,14 @@ int fc_detector_blur_static(const float *T, float *I, int n_img, int n_v, int n_
     b.n_v = n_v;
     b.n0 = (float)n0;
     b.spr = (float)spr;
+    // both passes stage their inputs in shared memory: a row of n_u + 2R
+    // samples (row pass), a tile of columns over all n_v rows (column pass)
+    if (!fc::blur_rows_fit(b))
+        return fail(FC_EINVAL, "fc_detector_blur_static: detector too wide for the row blur "
+                               "(n_u + 2 * blur radius)");
+    if (!fc::blur_cols_fit(b))
+        return fail(FC_EINVAL, "fc_detector_blur_static: detector too tall for the column blur "
+                               "(n_v + blur radii)");
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess) return fail(FC_ECUDA, "fc_detector_blur_static: no device");
     float *scratch = nullptr;
@@ -100,9 +112,8 @@ int fc_detector_blur_static(const float *T, float *I, int n_img, int n_v, int n_
     if (e != cudaSuccess) return fail(FC_ECUDA, cudaGetErrorString(e));
     cudaStream_t s = (cudaStream_t)stream;
     e = fc::launch_blur_rows(b, T, scratch, scratch + n, n_img, s);
-    if (e == cudaSuccess) e = fc::launch_blur_cols(b, scratch, scratch + n, I, n_img, s);
-    if (e == cudaErrorInvalidValue)
-        return fail(FC_EINVAL, "fc_detector_blur_static: detector too tall for the column blur");
+    if (e != cudaSuccess) return fail(FC_ECUDA, cudaGetErrorString(e));
+    e = fc::launch_blur_cols(b, scratch, scratch + n, I, n_img, s);
     if (e != cudaSuccess) return fail(FC_ECUDA, cudaGetErrorString(e));
     return FC_OK;
 }

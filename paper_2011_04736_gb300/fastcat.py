@@ -21,6 +21,8 @@ FC_OK, FC_EINVAL, FC_ENOMEM, FC_ECUDA, FC_ESTATE, FC_ETIMEOUT = 0, -1, -2, -3, -
 FC_HOST, FC_DEVICE = 0, 1
 FC_OUT_NONE, FC_OUT_PRIMARY, FC_OUT_INTENSITY, FC_OUT_COUNTS = 0, 1, 2, 3
 FC_NOISE_AFTER_BLUR, FC_NOISE_BEFORE_PSF = 0, 1
+FC_BP_AUTO, FC_BP_CHUNKED, FC_BP_CHUNKED_DENSE, FC_BP_SLAB = 0, 1, 2, 3
+FC_BP_NAMES = {FC_BP_CHUNKED: "chunked", FC_BP_CHUNKED_DENSE: "chunked_dense", FC_BP_SLAB: "slab"}
 FC_MAX_MATERIALS, FC_MAX_BINS = 8, 256
 
 # every entry point declared in include/fastcat.h
@@ -31,7 +33,8 @@ ENTRY_POINTS = ("fc_create", "fc_destroy", "fc_last_error", "fc_set_geometry", "
                 "fc_surrogate_grad", "fc_surrogate_get", "fc_surrogate_set", "fc_surrogate_eval",
                 "fc_energy_sum_lengths", "fc_cnr_grad", "fc_surrogate_project",
                 "fc_dose_estimate", "fc_fluence_for_dose", "fc_set_noise_order",
-                "fc_set_energy_groups", "fc_deconvolve_rl", "fc_detector_mtf")
+                "fc_set_energy_groups", "fc_deconvolve_rl", "fc_detector_mtf",
+                "fc_set_backprojector", "fc_backprojector_in_use")
 FC_STATIC_SCRATCH_FLOATS = 8 << 20
 FC_SURROGATE_PARAMS = 34305
 FC_SURROGATE_STATE = 34305 + 52 + 2 * 34305 + 1
@@ -120,6 +123,8 @@ def load():
         "fc_set_energy_groups": (I, [P, ctypes.POINTER(fc_energy_groups)]),
         "fc_deconvolve_rl": (I, [P, I, I, ctypes.c_double, I, P, I, P]),
         "fc_detector_mtf": (I, [P, ctypes.c_double, ctypes.c_double, I, P, P, I, P]),
+        "fc_set_backprojector": (I, [P, I]),
+        "fc_backprojector_in_use": (I, [P, ctypes.POINTER(I)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -284,6 +289,16 @@ def fc_detector_mtf(h, slit_width_mm=0.3, slit_angle_deg=2.5, oversample=4):
     return f[:n.value], m[:n.value]
 
 
+def fc_set_backprojector(h, variant):
+    return _check(load().fc_set_backprojector(h, variant))
+
+
+def fc_backprojector_in_use(h):
+    v = ctypes.c_int(-1)
+    _check(load().fc_backprojector_in_use(h, ctypes.byref(v)))
+    return v.value
+
+
 def fc_set_noise_order(h, order):
     return _check(load().fc_set_noise_order(h, order))
 
@@ -306,15 +321,39 @@ def fc_profile_read(h):
     return {k: (float(ms[i]), int(n[i])) for i, k in enumerate(FC_K_NAMES)}
 
 
+def check_blur_static_args(T, I, n_img, n_v, n_u):
+    """Argument checks of fc_detector_blur_static, raised before any launch:
+    T and I float32, contiguous, on the same CUDA device, each holding at
+    least n_img * n_v * n_u elements (the kernels read and write that many)."""
+    import torch
+    for name, x in (("T", T), ("I", I)):
+        if not hasattr(x, "data_ptr") or not getattr(x, "is_cuda", False):
+            raise ValueError("fc_detector_blur_static takes device tensors (%s)" % name)
+        if x.dtype != torch.float32:
+            raise ValueError("fc_detector_blur_static: %s must be float32, got %s" % (name, x.dtype))
+        if not x.is_contiguous():
+            raise ValueError("fc_detector_blur_static: %s must be contiguous" % name)
+    if T.device != I.device:
+        raise ValueError("fc_detector_blur_static: T on %s, I on %s" % (T.device, I.device))
+    if min(n_img, n_v, n_u) <= 0:
+        raise ValueError("fc_detector_blur_static: sizes must be positive")
+    n = int(n_img) * int(n_v) * int(n_u)
+    for name, x in (("T", T), ("I", I)):
+        if x.numel() < n:
+            raise ValueError("fc_detector_blur_static: %s holds %d elements, n_img * n_v * n_u = %d"
+                             % (name, x.numel(), n))
+
+
 def fc_detector_blur_static(T, I, n_img, n_v, n_u, psf_sigma_px, scatter_sigma_px, spr, n0,
                             stream=None):
-    """Allocation-free detector blur on caller-provided device tensors."""
-    tp, tw = _ptr(T)
-    ip, iw = _ptr(I)
-    if tw != FC_DEVICE or iw != FC_DEVICE:
-        raise ValueError("fc_detector_blur_static takes device tensors")
-    return _check(load().fc_detector_blur_static(tp, ip, n_img, n_v, n_u, psf_sigma_px,
-                                                 scatter_sigma_px, spr, n0, _stream(stream)))
+    """Allocation-free detector blur on caller-provided device tensors (the
+    library runs on T's device)."""
+    import torch
+    check_blur_static_args(T, I, n_img, n_v, n_u)
+    with torch.cuda.device(T.device):
+        return _check(load().fc_detector_blur_static(T.data_ptr(), I.data_ptr(), n_img, n_v, n_u,
+                                                     psf_sigma_px, scatter_sigma_px, spr, n0,
+                                                     _stream(stream)))
 
 
 def _dev(x, name):

@@ -59,3 +59,44 @@ def test_create_without_gpu_is_an_error(libpath):
     with pytest.raises(fastcat.FastcatError) as ei:
         fastcat.fc_create(0)
     assert ei.value.code in (fastcat.FC_ECUDA, fastcat.FC_EINVAL)
+
+
+class _FakeCudaTensor:
+    """Stand-in with the attributes the argument checks read (no GPU needed)."""
+
+    def __init__(self, n, dtype=None, device="cuda:0", contiguous=True):
+        import torch
+        self.n = n
+        self.dtype = torch.float32 if dtype is None else dtype
+        self.device = torch.device(device)
+        self.is_cuda = True
+        self._c = contiguous
+
+    def numel(self):
+        return self.n
+
+    def is_contiguous(self):
+        return self._c
+
+    def data_ptr(self):
+        raise AssertionError("the checks must not take a pointer")
+
+
+def test_blur_static_argument_checks_on_host():
+    import torch
+    from paper_2011_04736_gb300 import fastcat
+    n_img, n_v, n_u = 3, 10, 20
+    n = n_img * n_v * n_u
+    ok = _FakeCudaTensor(n)
+    fastcat.check_blur_static_args(ok, _FakeCudaTensor(n + 5), n_img, n_v, n_u)
+    bad = [(_FakeCudaTensor(n - 1), ok), (ok, _FakeCudaTensor(n - 1)),
+           (_FakeCudaTensor(n, dtype=torch.bfloat16), ok),
+           (ok, _FakeCudaTensor(n, dtype=torch.float64)),
+           (_FakeCudaTensor(n, contiguous=False), ok),
+           (ok, _FakeCudaTensor(n, device="cuda:1")),
+           (torch.zeros(n), ok)]
+    for T, I in bad:
+        with pytest.raises(ValueError):
+            fastcat.check_blur_static_args(T, I, n_img, n_v, n_u)
+    with pytest.raises(ValueError):
+        fastcat.check_blur_static_args(ok, ok, 0, n_v, n_u)

@@ -1,0 +1,172 @@
+"""GPU parity of the FDK backprojector variants (fc_set_backprojector)
+against the FP64 oracle: the chunked kernel, its 32-register variant and the
+thin-slab kernel, each forced on small ragged cases and on the full
+paper-scale grid (1024^2 x 10 voxels, 720 projections).  Tolerance
+|d mu| <= 5e-4 mu_water (0.5 HU)."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2011_04736_gb300 import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+MU_TOL = 5e-4
+
+
+@pytest.fixture(scope="module")
+def fc():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2011_04736_gb300 import build, fastcat
+    build.build()
+    fastcat.load()
+    return fastcat
+
+
+def _thin_slab(nx=37, ny=29, nz=10, n_angles=24):
+    """A slab whose z pitch projects to about half a detector row (the slab
+    kernel applies), ragged in x and y."""
+    return W.scaled(W.WORKLOADS["small_kv"], n_u=96, n_v=40, n_angles=n_angles, nx=nx, ny=ny,
+                    nz=nz, dx=0.09, dy=0.09, dz=0.03, du=0.06, dv=0.09)
+
+
+def _recon(fc, wl, counts, variant, lab=None):
+    g = wl.geom
+    sc = fc.Scanner(wl, labels=wl.make_phantom() if lab is None else lab, noise=False)
+    try:
+        fc.fc_set_backprojector(sc.h, variant)
+        used = fc.fc_backprojector_in_use(sc.h)
+        vol = torch.empty((g.nz, g.ny, g.nx), dtype=torch.float64, device="cuda")
+        c = counts if isinstance(counts, torch.Tensor) else np.ascontiguousarray(counts, np.float32)
+        fc.fc_reconstruct(sc.h, c, vol_mu=vol)
+        torch.cuda.synchronize()
+        return vol.cpu().numpy(), used
+    finally:
+        sc.close()
+
+
+def _oracle_counts(orc, wl, lab=None):
+    g = wl.geom
+    lab = wl.make_phantom() if lab is None else lab
+    w, d = wl.spectrum()
+    T = orc.project_T(g, lab, w, d, wl.mu())
+    return orc.intensity(T, wl.psf_sigma_px, wl.scatter_sigma_px, wl.spr, wl.n0).astype(np.float32)
+
+
+@pytest.mark.parametrize("nz", [10, 1, 16, 7])
+def test_variants_thin_slab(fc, orc, nz):
+    wl = _thin_slab(nz=nz)
+    g = wl.geom
+    assert fc_step(g) <= 0.98
+    lab = np.random.default_rng(40 + nz).integers(0, 7, size=(g.nz, g.ny, g.nx)).astype(np.uint8)
+    counts = _oracle_counts(orc, wl, lab)
+    vref = orc.fdk(g, counts.astype(np.float64), orc.i_flood(wl.n0, wl.spr))
+    scale = float(np.max(np.abs(vref)))
+    vols = {}
+    for req in (fc.FC_BP_AUTO, fc.FC_BP_SLAB, fc.FC_BP_CHUNKED, fc.FC_BP_CHUNKED_DENSE):
+        vol, used = _recon(fc, wl, counts, req)
+        if req == fc.FC_BP_AUTO:
+            assert used == fc.FC_BP_SLAB
+        else:
+            assert used == req
+        err = np.max(np.abs(vol - vref))
+        assert err <= MU_TOL * scale, (req, err / scale)
+        vols[req] = vol
+    # the slab kernel repeats the chunked kernel's per-slice arithmetic
+    d = np.max(np.abs(vols[fc.FC_BP_SLAB] - vols[fc.FC_BP_CHUNKED]))
+    assert d <= 1e-5 * scale, d / scale
+
+
+def fc_step(g):
+    """Largest projected z pitch in detector rows (host restatement of the
+    condition the slab kernel needs)."""
+    rmax = math.hypot(0.5 * g.nx * g.dx, 0.5 * g.ny * g.dy)
+    return g.dz * g.sdd / (g.sad - rmax) / g.dv
+
+
+def test_chunked_dense_small_kv(fc, orc):
+    """The 32-register chunked kernel (the default for grids of two or more
+    waves) forced on the 64^3 small kV case."""
+    wl = W.WORKLOADS["small_kv"]
+    g = wl.geom
+    counts = _oracle_counts(orc, wl)
+    vref = orc.fdk(g, counts.astype(np.float64), orc.i_flood(wl.n0, wl.spr))
+    mu_w = float(np.mean(vref[W.water_roi_mask(g)]))
+    for req in (fc.FC_BP_CHUNKED_DENSE, fc.FC_BP_CHUNKED):
+        vol, used = _recon(fc, wl, counts, req)
+        assert used == req
+        assert np.max(np.abs(vol - vref)) <= MU_TOL * mu_w, (req, np.max(np.abs(vol - vref)) / mu_w)
+
+
+def test_slab_refused_where_it_does_not_apply(fc):
+    wl = W.WORKLOADS["small_kv"]          # z pitch ~5 detector rows
+    assert fc_step(wl.geom) > 1.0
+    sc = fc.Scanner(wl, noise=False)
+    try:
+        assert fc.fc_backprojector_in_use(sc.h) in (fc.FC_BP_CHUNKED, fc.FC_BP_CHUNKED_DENSE)
+        fc.fc_set_backprojector(sc.h, fc.FC_BP_SLAB)
+        with pytest.raises(fc.FastcatError) as ei:
+            fc.fc_backprojector_in_use(sc.h)
+        assert ei.value.code == fc.FC_EINVAL
+        fc.fc_project(sc.h, 0, wl.geom.n_angles, fc.FC_OUT_NONE)
+        with pytest.raises(fc.FastcatError) as ei:
+            fc.fc_reconstruct(sc.h)
+        assert ei.value.code == fc.FC_EINVAL
+        with pytest.raises(fc.FastcatError):
+            fc.fc_set_backprojector(sc.h, 7)
+        fc.fc_set_backprojector(sc.h, fc.FC_BP_AUTO)
+        fc.fc_reconstruct(sc.h)
+    finally:
+        sc.close()
+
+
+def _synthetic_band_counts(g, rows, flood, seed=7):
+    """Counts on detector rows `rows` of every projection: the flood times
+    exp(-p), p a water cylinder's chord (mu 0.05 / cm, radius 8 cm at the
+    isocentre) plus seeded smooth random modes in u, v and the angle."""
+    rng = np.random.default_rng(seed)
+    u = (np.arange(g.n_u) - (g.n_u - 1) / 2) * g.du * g.sad / g.sdd
+    v = (rows - (g.n_v - 1) / 2) * g.dv * g.sad / g.sdd
+    th = g.theta0 + g.arc * np.arange(g.n_angles) / g.n_angles
+    chord = 2.0 * np.sqrt(np.clip(64.0 - u * u, 0.0, None))
+    p = np.broadcast_to(0.05 * chord, (g.n_angles, len(rows), g.n_u)).copy()
+    for _ in range(6):
+        a, fu, fv, ft, ph = rng.uniform(0.005, 0.02), rng.uniform(0.1, 2.0), rng.uniform(1.0, 20.0), \
+            rng.integers(1, 4), rng.uniform(0, 2 * np.pi)
+        p += a * (np.sin(fu * u[None, None, :] + fv * v[None, :, None] + ft * th[:, None, None] + ph)
+                  * (chord > 0)[None, None, :])
+    return (flood * np.exp(-p)).astype(np.float32)
+
+
+def test_full_paper_mv_reconstruct_variants(fc, orc):
+    """Full paper-scale grid (1024^2 x 10 voxels of 0.015625 cm, 720
+    projections of 1024 x 768): synthetic counts on the rows the volume
+    projects onto, flood elsewhere.  The oracle reconstructs from a
+    32-row detector centred like the full one (the same pixel centres; no
+    voxel projects outside it); every voxel of the slab kernel (the
+    default here) and of the 32-register chunked kernel is compared."""
+    wl = W.WORKLOADS["paper_mv"]
+    g = wl.geom
+    flood = wl.n0 * (1.0 + wl.spr)
+    assert fc_step(g) <= 0.98
+    crop = 32
+    r0 = g.n_v // 2 - crop // 2
+    rows = np.arange(r0, r0 + crop)
+    band = _synthetic_band_counts(g, rows, flood)
+    gc = W.Geometry(g.sad, g.sdd, g.n_u, crop, g.du, g.dv, g.n_angles, g.nx, g.ny, g.nz,
+                    g.dx, g.dy, g.dz, g.theta0, g.arc)
+    assert 2 * r0 == g.n_v - crop           # crop row r has full-detector row r0 + r's centre
+    q = orc.fdk_weight(gc, band.astype(np.float64), flood)
+    f = orc.ramp_filter(q, g.du * g.sad / g.sdd)
+    vref = orc.backproject(gc, f)
+    mu_w = float(np.mean(vref[W.water_roi_mask(g)]))
+    counts = torch.full((g.n_angles, g.n_v, g.n_u), flood, dtype=torch.float32, device="cuda")
+    counts[:, r0:r0 + crop] = torch.from_numpy(band).cuda()
+    for req in (fc.FC_BP_AUTO, fc.FC_BP_CHUNKED_DENSE):
+        vol, used = _recon(fc, wl, counts, req, lab=np.zeros((g.nz, g.ny, g.nx), np.uint8))
+        assert used == (fc.FC_BP_SLAB if req == fc.FC_BP_AUTO else req)
+        err = np.max(np.abs(vol - vref))
+        assert err <= MU_TOL * mu_w, (req, err / mu_w)

@@ -61,8 +61,27 @@ def test_blur_static_matches_handle_path_twice(fc):
 def test_blur_static_rejects_oversize(fc):
     n_v, n_u = 512, 512
     n_img = fc.FC_STATIC_SCRATCH_FLOATS // (2 * n_v * n_u) + 1
-    T = torch.zeros(1, dtype=torch.float32, device="cuda")
+    T = torch.zeros(n_img * n_v * n_u, dtype=torch.float32, device="cuda")
     with pytest.raises(fc.FastcatError) as ei:
         fc.fc_detector_blur_static(T, T, n_img, n_v, n_u, 0.8, 20.0, 0.2, 1e5)
     assert ei.value.code == fc.FC_EINVAL
     assert "FC_STATIC_SCRATCH_FLOATS" in fc.fc_last_error()
+
+
+def test_blur_static_rejects_bad_tensors_before_launch(fc):
+    """Undersized, non-float32 or mixed-device tensors never reach a kernel
+    (the kernels would read and write n_img * n_v * n_u elements)."""
+    n_img, n_v, n_u = 2, 16, 24
+    n = n_img * n_v * n_u
+    good = torch.zeros(n, dtype=torch.float32, device="cuda")
+    short = torch.zeros(n - 1, dtype=torch.float32, device="cuda")
+    half = torch.zeros(n, dtype=torch.float16, device="cuda")
+    for T, I in ((short, good), (good, short), (half, good), (good, half),
+                 (good.cpu(), good)):
+        with pytest.raises(ValueError):
+            fc.fc_detector_blur_static(T, I, n_img, n_v, n_u, 0.8, 20.0, 0.2, 1e5)
+    # a valid call still works after the refusals
+    out = torch.empty_like(good)
+    fc.fc_detector_blur_static(good + 1.0, out, n_img, n_v, n_u, 0.8, 20.0, 0.2, 1e5)
+    torch.cuda.synchronize()
+    assert torch.allclose(out, torch.full_like(out, 1.2e5), rtol=1e-5)
