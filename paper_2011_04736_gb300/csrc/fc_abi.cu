@@ -577,19 +577,26 @@ static int fill_proj_params(fc_handle *h, int a0, int na, fc::ProjParams *p)
 // one_lo, one_hi: when one_hi >= 0, every row of `in` outside [one_lo,
 // one_hi) is all ones (the projector's primary on rows that cannot meet the
 // voxels); the tensor-core row pass then skips those rows' tiles.
+static int blur_params(const fc_handle *h, double psf, double sc, double n0, double spr, fc::BlurParams *b)
+{
+    memset(b, 0, sizeof(*b));
+    b->n_u = h->g.n_u;
+    b->n_v = h->g.n_v;
+    int rc = gauss_taps(psf, b->gp, &b->rp);
+    if (rc) return rc;
+    rc = gauss_taps(sc, b->gs, &b->rs);
+    if (rc) return rc;
+    b->n0 = (float)n0;
+    b->spr = (float)spr;
+    return FC_OK;
+}
+
 static int run_blur(fc_handle *h, const float *in, float *out, size_t off, int n, double psf,
                     double sc, double n0, double spr, cudaStream_t s, int one_lo = 0, int one_hi = -1)
 {
     fc::BlurParams b;
-    memset(&b, 0, sizeof(b));
-    b.n_u = h->g.n_u;
-    b.n_v = h->g.n_v;
-    int rc = gauss_taps(psf, b.gp, &b.rp);
+    int rc = blur_params(h, psf, sc, n0, spr, &b);
     if (rc) return rc;
-    rc = gauss_taps(sc, b.gs, &b.rs);
-    if (rc) return rc;
-    b.n0 = (float)n0;
-    b.spr = (float)spr;
     if (!fc::blur_tc_supported(b)) {
         // radii beyond the tensor-core path: direct f32 passes
         if (!fc::blur_rows_fit(b))
@@ -615,7 +622,7 @@ static int run_blur(fc_handle *h, const float *in, float *out, size_t off, int n
         t.end();
     }
     {
-        Trace t(h, FC_K_BLUR_COLS, 1, s);
+        Trace t(h, FC_K_BLUR_COLS, fc::blur_tc_cols_launches(b, one_lo, one_hi), s);
         FC_CK(fc::launch_blur_tc_cols(b, h->d_tp + off, h->d_ts + off, out, h->d_hankel,
                                       h->d_blur_err, n, s, one_lo, one_hi));
         t.end();
@@ -841,19 +848,28 @@ int fc_project(fc_handle *h, int angle_begin, int angle_count, int out_kind, flo
     const size_t plane = (size_t)h->g.n_v * h->g.n_u;
     const size_t off = (size_t)angle_begin * plane;
     const size_t bytes = (size_t)angle_count * plane * sizeof(float);
-    if (h->n_groups && out_kind != FC_OUT_PRIMARY) {
-        if (h->noise_order == FC_NOISE_BEFORE_PSF)
-            return fail(FC_EINVAL, "fc_project: noise before the optical spread is not defined for energy groups");
-    } else {
-        Trace t(h, FC_K_PROJECT, fc::project_launches(p), s);
-        FC_CK(fc::launch_project(p, h->d_T, nullptr, s));
-        t.end();
-    }
-    if (out_kind == FC_OUT_PRIMARY) return angle_count ? copy_out(out, out_where, h->d_T + off, bytes, s) : FC_OK;
     // rows outside [v_hit_lo, v_hit_hi] hold T = 1 exactly (their rays cannot
     // meet the voxels)
     const int one_lo = p.v_hit_lo > 0 ? p.v_hit_lo : 0;
     const int one_hi = (p.v_hit_hi < h->g.n_v - 1 ? p.v_hit_hi : h->g.n_v - 1) + 1;
+    if (h->n_groups && out_kind != FC_OUT_PRIMARY) {
+        if (h->noise_order == FC_NOISE_BEFORE_PSF)
+            return fail(FC_EINVAL, "fc_project: noise before the optical spread is not defined for energy groups");
+    } else {
+        // T = 1 goes to every row when T is returned; otherwise only to the
+        // rows the tensor-core row pass reads (it takes the others as 1)
+        int f_lo = 0, f_hi = -1;
+        if (out_kind != FC_OUT_PRIMARY) {
+            fc::BlurParams b;
+            rc = blur_params(h, h->noise_order == FC_NOISE_BEFORE_PSF ? 0.0 : h->psf, h->sc, h->n0, h->spr, &b);
+            if (rc) return rc;
+            if (fc::blur_tc_supported(b)) fc::blur_tc_rows_read(b, one_lo, one_hi, &f_lo, &f_hi);
+        }
+        Trace t(h, FC_K_PROJECT, fc::project_launches(p, f_lo, f_hi), s);
+        FC_CK(fc::launch_project(p, h->d_T, nullptr, s, f_lo, f_hi));
+        t.end();
+    }
+    if (out_kind == FC_OUT_PRIMARY) return angle_count ? copy_out(out, out_where, h->d_T + off, bytes, s) : FC_OK;
     const bool noise = (out_kind != FC_OUT_INTENSITY) && h->noise;
     if (h->n_groups) {
         rc = run_groups(h, angle_begin, angle_count, s);

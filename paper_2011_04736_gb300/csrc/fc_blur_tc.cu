@@ -145,10 +145,11 @@ struct Tile {
     size_t img;
 };
 
-__device__ __forceinline__ Tile tile_of(long long t, int n_m, int n_x, size_t plane, int x_off = 0)
+__device__ __forceinline__ Tile tile_of(long long t, int n_m, int n_x, size_t plane, int x_off = 0,
+                                        int m_off = 0)
 {
     Tile r;
-    r.m0 = (int)(t % n_m) * 128;
+    r.m0 = (int)(t % n_m) * 128 + m_off;
     r.x0 = ((int)((t / n_m) % n_x) + x_off) * kN;
     r.img = (size_t)(t / ((long long)n_m * n_x)) * plane;
     return r;
@@ -424,7 +425,7 @@ k_blur_cols_tc(const __grid_constant__ TcBlurParams p, int n_stage)
     const uint32_t stage_bytes = 2u * wlo + tp_bytes;
     const uint32_t acol = 2 * kN;                          // TMEM column of A (hi)
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int n_m = (p.n_v + 127) / 128, n_x = (p.n_u + kN - 1) / kN;
+    const int n_m = p.m_cnt, n_x = (p.n_u + kN - 1) / kN;
     const long long total = (long long)n_m * n_x * p.n_img;
     const size_t plane = (size_t)p.n_u * p.n_v;
 
@@ -489,19 +490,25 @@ k_blur_cols_tc(const __grid_constant__ TcBlurParams p, int n_stage)
                 *abort_flag = 1;
                 break;
             }
-            const Tile tl = tile_of(t, n_m, n_x, plane);
+            const Tile tl = tile_of(t, n_m, n_x, plane, 0, p.m_off);
             uint8_t *whi = smem + kHdr + (uint32_t)st * stage_bytes;
             {
                 // tp tile: rows m0 - R_p + r, columns x0 + n (both clamped),
-                // copied asynchronously while the W items are processed
+                // copied asynchronously while the W items are processed; rows
+                // outside [tp_lo, tp_hi) hold the constant the row pass
+                // stands for there and are not loaded
                 float *tpt = reinterpret_cast<float *>(whi + 2u * wlo);
                 const bool vec = tl.x0 + kN <= p.n_u && (p.n_u & 3) == 0;
                 const int nq = trows * (kN / 4);
                 for (int e = tid; e < nq; e += kProd) {
                     const int r = e / (kN / 4), n = 4 * (e % (kN / 4));
-                    const float *row = p.tp + tl.img + (size_t)clampi(tl.m0 - rp + r, p.n_v) * p.n_u;
+                    const int src_row = clampi(tl.m0 - rp + r, p.n_v);
+                    const float *row = p.tp + tl.img + (size_t)src_row * p.n_u;
                     float *d = tpt + r * kTpPitch + n;
-                    if (vec) {
+                    if (src_row < p.tp_lo || src_row >= p.tp_hi) {
+                        *reinterpret_cast<float4 *>(d) = make_float4(p.tp_const, p.tp_const, p.tp_const,
+                                                                     p.tp_const);
+                    } else if (vec) {
                         cp_async16(d, row + tl.x0 + n);
                     } else {
 #pragma unroll
@@ -602,7 +609,7 @@ k_blur_cols_tc(const __grid_constant__ TcBlurParams p, int n_stage)
                 break;
             }
             tc::fence_after_sync();
-            const Tile tl = tile_of(t, n_m, n_x, plane);
+            const Tile tl = tile_of(t, n_m, n_x, plane, 0, p.m_off);
             const int c = tl.m0 + 127 - mr;              // detector row of this lane
             // tile row of output row c's first optical-spread tap
             const float *tpt = reinterpret_cast<const float *>(smem + kHdr + (uint32_t)st * stage_bytes +
@@ -696,6 +703,11 @@ static TcBlurParams tc_params(const BlurParams &bp, const uint16_t *hankel, unsi
     p.ts_lo = 0;
     p.ts_hi = bp.n_v;
     p.ts_const = 0.0f;
+    p.tp_lo = 0;
+    p.tp_hi = bp.n_v;
+    p.tp_const = 0.0f;
+    p.m_off = 0;
+    p.m_cnt = (bp.n_v + 127) / 128;
     return p;
 }
 
@@ -742,11 +754,10 @@ static void ones_row_pass(const BlurParams &bp, float &vp, float &vs)
     for (int j = 0; j <= 2 * bp.rs; ++j) vs += bp.gs[j];
 }
 
-// Rows [0, r_lo) and [r_hi, n_v) of image blockIdx.y of tp get vp, the
-// optical-spread row pass of an all-ones row.  (The scatter plane needs no
-// store: the column pass takes the same constant for those rows.)  VEC: four
-// floats per store (n_u a multiple of 4 and tp 16-byte aligned, so no store
-// straddles the gap between the two row ranges).
+// Rows [0, r_lo) and [r_hi, n_v) of image blockIdx.y of tp get the constant
+// vp (the column pass's output rows that see only constant inputs).  VEC:
+// four floats per store (n_u a multiple of 4 and tp 16-byte aligned, so no
+// store straddles the gap between the two row ranges).
 template <bool VEC>
 __global__ void __launch_bounds__(256)
 k_fill_const_rows(float *__restrict__ tp, float vp, int n_u, int n_v, int r_lo, int r_hi)
@@ -768,8 +779,9 @@ k_fill_const_rows(float *__restrict__ tp, float vp, int n_u, int n_v, int r_lo, 
 // one_lo, one_hi: when one_hi >= 0, every row of `in` outside [one_lo,
 // one_hi) is known to be all ones (the primary of rays that cannot meet the
 // voxels).  Only the 64-line tiles that hold rows of [one_lo, one_hi) are
-// computed; the other rows get the row pass of an all-ones row, the sum of
-// each kernel's taps, from a store-only kernel.
+// computed; the other rows of tp and ts are left unwritten, and the column
+// pass (given the same one_lo, one_hi) takes for them the row pass of an
+// all-ones row, the sum of each kernel's taps.
 cudaError_t launch_blur_tc_rows(const BlurParams &bp, const float *in, float *tp, float *ts,
                                 uint16_t *hankel, unsigned int *err, int n_img, cudaStream_t s,
                                 int one_lo, int one_hi)
@@ -800,33 +812,66 @@ cudaError_t launch_blur_tc_rows(const BlurParams &bp, const float *in, float *tp
         k_blur_rows_tc<<<grid, kThreads, bytes, s>>>(p, n_stage);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
-    if (r_hi - r_lo < bp.n_v) {
-        float vp, vs;
-        ones_row_pass(bp, vp, vs);
-        const bool vec = bp.n_u % 4 == 0 && reinterpret_cast<uintptr_t>(tp) % 16 == 0;
-        const size_t per = (size_t)(bp.n_v - (r_hi - r_lo)) * bp.n_u / (vec ? 4 : 1);
-        const size_t want = (per + 256 * 8 - 1) / (256 * 8);
-        if (n_img > 65535) return cudaErrorInvalidValue;
-        dim3 fgrid((unsigned)(want < 1024 ? want : 1024), n_img);
-        if (vec)
-            k_fill_const_rows<true><<<fgrid, 256, 0, s>>>(tp, vp, bp.n_u, bp.n_v, r_lo, r_hi);
-        else
-            k_fill_const_rows<false><<<fgrid, 256, 0, s>>>(tp, vp, bp.n_u, bp.n_v, r_lo, r_hi);
-    }
+    (void)r_lo;
+    (void)r_hi;
     return cudaGetLastError();
 }
 
-// Kernels launch_blur_tc_rows starts: band matrices, the tensor-core pass
-// (unless no tile is computed) and the constant-row fill (when rows are skipped).
+void blur_tc_rows_read(const BlurParams &bp, int one_lo, int one_hi, int *lo, int *hi)
+{
+    int x_off, x_cnt;
+    rows_computed(bp, one_lo, one_hi, x_off, x_cnt, *lo, *hi);
+}
+
+// Kernels launch_blur_tc_rows starts: band matrices and the tensor-core pass
+// (unless no tile is computed).  The rows it skips are not written: the
+// column pass takes the constant they stand for.
 int blur_tc_rows_launches(const BlurParams &bp, int one_lo, int one_hi)
 {
     int x_off, x_cnt, r_lo, r_hi;
     rows_computed(bp, one_lo, one_hi, x_off, x_cnt, r_lo, r_hi);
-    return 1 + (x_cnt > 0) + (r_hi - r_lo < bp.n_v);
+    return 1 + (x_cnt > 0);
+}
+
+// Output rows the tensor-core column pass computes when the rows of the
+// primary outside [one_lo, one_hi) are all ones: every row within R (the
+// larger radius) of that band, as 128-row tiles from m_off (a multiple of 8,
+// so a window item of 8 rows never straddles a computed-tile edge of the row
+// pass); the other output rows see only constant inputs.  Without that
+// knowledge (one_hi < 0): every row.
+static void out_rows_computed(const BlurParams &bp, int one_lo, int one_hi, int &m_off, int &m_cnt)
+{
+    m_off = 0;
+    m_cnt = (bp.n_v + 127) / 128;
+    if (one_hi < 0) return;
+    const int R = bp.rs > bp.rp ? bp.rs : bp.rp;
+    const int lo_b = one_lo > 0 ? one_lo : 0, hi_b = one_hi < bp.n_v ? one_hi : bp.n_v;
+    if (lo_b >= hi_b) {
+        m_cnt = 0;
+        return;
+    }
+    const int lo = lo_b - R > 0 ? lo_b - R : 0;
+    const int hi = hi_b + R < bp.n_v ? hi_b + R : bp.n_v;
+    m_off = lo & ~7;
+    m_cnt = (hi - m_off + 127) / 128;
+}
+
+// Kernels launch_blur_tc_cols starts: the tensor-core pass (unless no tile is
+// computed) and the constant fill of the other output rows.
+int blur_tc_cols_launches(const BlurParams &bp, int one_lo, int one_hi)
+{
+    int m_off, m_cnt;
+    out_rows_computed(bp, one_lo, one_hi, m_off, m_cnt);
+    const int hi = m_off + 128 * m_cnt < bp.n_v ? m_off + 128 * m_cnt : bp.n_v;
+    return (m_cnt > 0) + (hi - m_off < bp.n_v);
 }
 
 // one_lo, one_hi: as for launch_blur_tc_rows with the same values; the rows
-// of ts that pass did not compute are taken as the constant it stands for.
+// of tp and ts that pass did not compute are taken as the constants they
+// stand for.  Only the output rows within the larger radius of [one_lo,
+// one_hi) are computed on the tensor cores (whole 128-row tiles); every
+// other output row sees constant inputs only and gets the column pass of
+// those constants from a store-only kernel.
 cudaError_t launch_blur_tc_cols(const BlurParams &bp, const float *tp, const float *ts, float *out,
                                 const uint16_t *hankel, unsigned int *err, int n_img, cudaStream_t s,
                                 int one_lo, int one_hi)
@@ -837,8 +882,10 @@ cudaError_t launch_blur_tc_cols(const BlurParams &bp, const float *tp, const flo
     {
         int x_off, x_cnt;
         rows_computed(bp, one_lo, one_hi, x_off, x_cnt, p.ts_lo, p.ts_hi);
-        float vp;
-        ones_row_pass(bp, vp, p.ts_const);
+        p.tp_lo = p.ts_lo;
+        p.tp_hi = p.ts_hi;
+        ones_row_pass(bp, p.tp_const, p.ts_const);
+        out_rows_computed(bp, one_lo, one_hi, p.m_off, p.m_cnt);
     }
     p.band[1].src = ts;
     p.tp = tp;
@@ -854,10 +901,32 @@ cudaError_t launch_blur_tc_cols(const BlurParams &bp, const float *tp, const flo
     cudaError_t e = cudaFuncSetAttribute(k_blur_cols_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)bytes);
     if (e != cudaSuccess) return e;
-    const long long tiles = (long long)((bp.n_v + 127) / 128) * ((bp.n_u + kN - 1) / kN) * n_img;
-    int grid = 0;
-    if ((e = persistent_grid(tiles, &grid)) != cudaSuccess) return e;
-    k_blur_cols_tc<<<grid, kThreads, bytes, s>>>(p, n_stage);
+    if (p.m_cnt > 0) {
+        const long long tiles = (long long)p.m_cnt * ((bp.n_u + kN - 1) / kN) * n_img;
+        int grid = 0;
+        if ((e = persistent_grid(tiles, &grid)) != cudaSuccess) return e;
+        k_blur_cols_tc<<<grid, kThreads, bytes, s>>>(p, n_stage);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    const int r_lo = p.m_cnt > 0 ? p.m_off : 0;
+    const int r_hi = p.m_cnt > 0 ? (p.m_off + 128 * p.m_cnt < bp.n_v ? p.m_off + 128 * p.m_cnt : bp.n_v) : 0;
+    if (r_hi - r_lo < bp.n_v) {
+        // output rows whose every tap reads constant inputs: the column pass
+        // of the constant rows, n0 (vp sum g_psf + spr vs sum g_scatter)
+        double sp = 0.0, ss = 0.0;
+        for (int j = 0; j <= 2 * bp.rp; ++j) sp += bp.gp[j];
+        for (int j = 0; j <= 2 * bp.rs; ++j) ss += bp.gs[j];
+        const float c = (float)((double)bp.n0 * ((double)p.tp_const * sp + (double)bp.spr * (double)p.ts_const * ss));
+        const bool vec = bp.n_u % 4 == 0 && reinterpret_cast<uintptr_t>(out) % 16 == 0;
+        const size_t per = (size_t)(bp.n_v - (r_hi - r_lo)) * bp.n_u / (vec ? 4 : 1);
+        const size_t want = (per + 256 * 8 - 1) / (256 * 8);
+        if (n_img > 65535) return cudaErrorInvalidValue;
+        dim3 fgrid((unsigned)(want < 1024 ? want : 1024), n_img);
+        if (vec)
+            k_fill_const_rows<true><<<fgrid, 256, 0, s>>>(out, c, bp.n_u, bp.n_v, r_lo, r_hi);
+        else
+            k_fill_const_rows<false><<<fgrid, 256, 0, s>>>(out, c, bp.n_u, bp.n_v, r_lo, r_hi);
+    }
     return cudaGetLastError();
 }
 

@@ -134,6 +134,9 @@ struct TcBlurParams {
     int x_off, x_cnt;   // rows pass: the 64-line tiles [x_off, x_off + x_cnt) are computed
     int ts_lo, ts_hi;   // columns pass: rows of ts outside [ts_lo, ts_hi) equal ts_const
     float ts_const;
+    int tp_lo, tp_hi;   // columns pass: rows of tp outside [tp_lo, tp_hi) equal tp_const
+    float tp_const;
+    int m_off, m_cnt;   // columns pass: output rows [m_off + 128 i, +128), i < m_cnt, are computed
 };
 
 constexpr size_t kBlurTcHankelMax = 2 * 2 * 64 * (15 + (128 + 2 * 256) / 8);  // bf16 elements
@@ -259,8 +262,11 @@ cudaError_t launch_backproject_adjoint(const FdkParams &p, const float *gmu, flo
 cudaError_t launch_filter_adjoint(const FdkParams &p, const float *gf, const float *I,
                                   const float *K, const float *z, float *gI, cudaStream_t s);
 // launchers (return cudaError_t of the launch)
-cudaError_t launch_project(const ProjParams &p, float *T, float *L_out, cudaStream_t s);
-int project_launches(const ProjParams &p);
+// T output: rows [f_lo, f_hi) that no ray of the traced band covers get
+// T = 1 (f_hi < 0: every row); L_out: path lengths of every ray.
+cudaError_t launch_project(const ProjParams &p, float *T, float *L_out, cudaStream_t s, int f_lo = 0,
+                           int f_hi = -1);
+int project_launches(const ProjParams &p, int f_lo = 0, int f_hi = -1);
 cudaError_t launch_project_groups(const ProjParams &p, float *P, cudaStream_t s);
 cudaError_t launch_group_blur(const GroupParams &g, const float *P, float *prof, float *out,
                               int angle0, int n_img, cudaStream_t s);
@@ -288,6 +294,10 @@ cudaError_t launch_blur_tc_rows(const BlurParams &bp, const float *in, float *tp
                                 uint16_t *hankel, unsigned int *err, int n_img, cudaStream_t s,
                                 int one_lo = 0, int one_hi = -1);
 int blur_tc_rows_launches(const BlurParams &bp, int one_lo, int one_hi);
+// rows [lo, hi) of the input that launch_blur_tc_rows reads (with one_hi < 0:
+// every row)
+void blur_tc_rows_read(const BlurParams &bp, int one_lo, int one_hi, int *lo, int *hi);
+int blur_tc_cols_launches(const BlurParams &bp, int one_lo, int one_hi);
 cudaError_t launch_blur_tc_cols(const BlurParams &bp, const float *tp, const float *ts, float *out,
                                 const uint16_t *hankel, unsigned int *err, int n_img, cudaStream_t s,
                                 int one_lo = 0, int one_hi = -1);

@@ -289,23 +289,22 @@ struct FillPlanes {
     size_t stride;
 };
 
-// Rows outside [r0, r1) of projection angle0 + blockIdx.y in plane blockIdx.z
-// (VEC: four floats per store) get the value of a ray that misses the voxel
-// slab.  Per projection the filled elements are [0, r0 n_u) and
-// [r1 n_u, n_v n_u).
+// Rows [a0, a1) and [b0, b1) (a1 <= b0) of projection angle0 + blockIdx.y
+// in plane blockIdx.z (VEC: four floats per store) get the value of a ray
+// that misses the voxel slab.
 template <bool VEC>
 __global__ void __launch_bounds__(256)
-k_fill_miss_rows(float *__restrict__ T, int n_u, int n_v, int angle0, int r0, int r1,
+k_fill_miss_rows(float *__restrict__ T, int n_u, int n_v, int angle0, int a0, int a1, int b0, int b1,
                  const __grid_constant__ FillPlanes f)
 {
     const int w = VEC ? 4 : 1;
-    const size_t lo = (size_t)r0 * n_u / w, hs = (size_t)r1 * n_u / w, end = (size_t)n_v * n_u / w;
-    const size_t n_fill = lo + (end - hs);
+    const size_t s0 = (size_t)a0 * n_u / w, lo = (size_t)(a1 - a0) * n_u / w;
+    const size_t hs = (size_t)b0 * n_u / w, n_fill = lo + (size_t)(b1 - b0) * n_u / w;
     const size_t base = (blockIdx.z * f.stride + (size_t)(angle0 + blockIdx.y) * n_v * n_u) / w;
     const float v = f.v[blockIdx.z];
     for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < n_fill;
          e += (size_t)gridDim.x * blockDim.x) {
-        const size_t i = base + (e < lo ? e : hs + (e - lo));
+        const size_t i = base + (e < lo ? s0 + e : hs + (e - lo));
         if (VEC)
             reinterpret_cast<float4 *>(T)[i] = make_float4(v, v, v, v);
         else
@@ -313,11 +312,23 @@ k_fill_miss_rows(float *__restrict__ T, int n_u, int n_v, int angle0, int r0, in
     }
 }
 
-static cudaError_t launch_fill(const ProjParams &p, float *T, int r0, int r1, const FillPlanes &f,
-                               int n_planes, cudaStream_t s)
+// Rows of [f_lo, f_hi) outside the traced band [r0, r1) (the band lies
+// inside [f_lo, f_hi) or is empty).
+static void fill_ranges(int r0, int r1, int f_lo, int f_hi, int &a0, int &a1, int &b0, int &b1)
+{
+    a0 = f_lo;
+    a1 = r1 > r0 ? max(f_lo, min(r0, f_hi)) : f_lo;
+    b0 = r1 > r0 ? max(a1, min(r1, f_hi)) : f_lo;
+    b1 = f_hi;
+}
+
+static cudaError_t launch_fill(const ProjParams &p, float *T, int r0, int r1, int f_lo, int f_hi,
+                               const FillPlanes &f, int n_planes, cudaStream_t s)
 {
     const int n_v = p.g.n_v, n_u = p.g.n_u;
-    const size_t n_fill = (size_t)(n_v - (r1 - r0)) * n_u;
+    int a0, a1, b0, b1;
+    fill_ranges(r0, r1, f_lo, f_hi, a0, a1, b0, b1);
+    const size_t n_fill = (size_t)((a1 - a0) + (b1 - b0)) * n_u;
     if (!n_fill || n_planes <= 0) return cudaSuccess;
     const bool vec = n_u % 4 == 0 && reinterpret_cast<uintptr_t>(T) % 16 == 0 &&
                      (n_planes == 1 || f.stride % 4 == 0);
@@ -325,9 +336,9 @@ static cudaError_t launch_fill(const ProjParams &p, float *T, int r0, int r1, co
     const size_t want = (per + 256 * 8 - 1) / (256 * 8);
     dim3 grid((unsigned)(want < 1024 ? want : 1024), p.n_angles_launch, n_planes);
     if (vec)
-        k_fill_miss_rows<true><<<grid, 256, 0, s>>>(T, n_u, n_v, p.angle0, r0, r1, f);
+        k_fill_miss_rows<true><<<grid, 256, 0, s>>>(T, n_u, n_v, p.angle0, a0, a1, b0, b1, f);
     else
-        k_fill_miss_rows<false><<<grid, 256, 0, s>>>(T, n_u, n_v, p.angle0, r0, r1, f);
+        k_fill_miss_rows<false><<<grid, 256, 0, s>>>(T, n_u, n_v, p.angle0, a0, a1, b0, b1, f);
     return cudaGetLastError();
 }
 
@@ -350,17 +361,24 @@ static void project_band(const ProjParams &p, int &r0, int &r1)
     }
 }
 
-// Kernels launch_project (T output) or launch_project_groups starts: the
-// traced band and the fill.
-int project_launches(const ProjParams &p)
+// Kernels launch_project (T output, fill rows [f_lo, f_hi); f_hi < 0: every
+// row) or launch_project_groups starts: the traced band and the fill.
+int project_launches(const ProjParams &p, int f_lo, int f_hi)
 {
     if (p.n_angles_launch <= 0) return 0;
     int r0, r1;
     project_band(p, r0, r1);
-    return (r1 > r0) + (r1 - r0 < p.g.n_v);
+    if (f_hi < 0) {
+        f_lo = 0;
+        f_hi = p.g.n_v;
+    }
+    int a0, a1, b0, b1;
+    fill_ranges(r0, r1, f_lo, f_hi, a0, a1, b0, b1);
+    return (r1 > r0) + ((a1 - a0) + (b1 - b0) > 0);
 }
 
-cudaError_t launch_project(const ProjParams &p, float *T, float *L_out, cudaStream_t s)
+cudaError_t launch_project(const ProjParams &p, float *T, float *L_out, cudaStream_t s, int f_lo,
+                           int f_hi)
 {
     if (p.n_angles_launch <= 0) return cudaSuccess;
     dim3 block(32, 8);
@@ -369,8 +387,10 @@ cudaError_t launch_project(const ProjParams &p, float *T, float *L_out, cudaStre
         k_project<true><<<grid, block, 0, s>>>(p, T, L_out, 0, p.g.n_v);
         return cudaGetLastError();
     }
-    // Only the row tiles that hold rows in [v_hit_lo, v_hit_hi] are traced;
-    // the other rows are filled with T = 1 by a store-only kernel.
+    // Only the rows in [v_hit_lo, v_hit_hi] are traced; the other rows of
+    // [f_lo, f_hi) are filled with T = 1 by a store-only kernel (rows outside
+    // it are left as they are: a consumer that takes them as 1 without
+    // reading them narrows the range).
     int r0, r1;
     project_band(p, r0, r1);
     if (r1 > r0) {
@@ -380,7 +400,11 @@ cudaError_t launch_project(const ProjParams &p, float *T, float *L_out, cudaStre
     FillPlanes f{};
     f.v[0] = 1.0f;
     f.stride = 0;
-    return launch_fill(p, T, r0, r1, f, 1, s);
+    if (f_hi < 0) {
+        f_lo = 0;
+        f_hi = p.g.n_v;
+    }
+    return launch_fill(p, T, r0, r1, f_lo, f_hi, f, 1, s);
 }
 
 // Energy-group primaries (the I_f equation of Sec. II.F split over groups of
@@ -432,7 +456,7 @@ cudaError_t launch_project_groups(const ProjParams &p, float *P, cudaStream_t s)
     FillPlanes f{};
     for (int gi = 0; gi < p.n_groups; ++gi) f.v[gi] = p.grp_flood[gi];
     f.stride = p.grp_stride;
-    return launch_fill(p, P, r0, r1, f, p.n_groups, s);
+    return launch_fill(p, P, r0, r1, 0, p.g.n_v, f, p.n_groups, s);
 }
 
 // Dose estimate, Sec. II.H: for every energy bin E, the sum over the rays of

@@ -111,6 +111,35 @@ def test_primary_thin_slab_band_edges(fc, orc):
     assert np.all(T[miss] == 1.0)
 
 
+def test_intensity_thin_band_every_pixel(fc, orc):
+    """A 3-slice slab on a 240-row detector with a 5 px scatter kernel: the
+    projector traces a band of rows, the row pass computes the 64-line tiles
+    holding it, the column pass the 128-row tiles within the larger blur
+    radius of it, and a store kernel writes the rest.  Every pixel of I (and
+    of the rate of the Sec. II.G noise order) against the oracle."""
+    import dataclasses
+    wl = W.scaled(W.WORKLOADS["small_kv"], n_u=70, n_v=240, n_angles=6, nx=24, ny=20, nz=3,
+                  dx=0.25, dy=0.25, dz=0.1, du=0.12, dv=0.05)
+    wl = dataclasses.replace(wl, scatter_sigma_px=5.0, psf_sigma_px=0.8)
+    g = wl.geom
+    lab = np.random.default_rng(24).integers(0, 7, size=(g.nz, g.ny, g.nx)).astype(np.uint8)
+    sc = _scanner(fc, wl, lab, noise=False)
+    try:
+        I = _project(fc, sc, fc.FC_OUT_INTENSITY)
+        fc.fc_set_noise_order(sc.h, fc.FC_NOISE_BEFORE_PSF)
+        lam = _project(fc, sc, fc.FC_OUT_INTENSITY)
+    finally:
+        sc.close()
+    w, d = wl.spectrum()
+    Tr = orc.project_T(g, lab, w, d, wl.mu())
+    hit_rows = np.where((Tr < 1.0).any(axis=(0, 2)))[0]
+    assert 0 < len(hit_rows) < 20          # a narrow band: most rows are filled
+    Ir = orc.intensity(Tr, wl.psf_sigma_px, wl.scatter_sigma_px, wl.spr, wl.n0)
+    assert np.max(np.abs(I - Ir) / Ir) <= REL_T
+    lam_r, _ = orc.counts_noise_before_psf(Tr, wl.psf_sigma_px, wl.scatter_sigma_px, wl.spr, wl.n0)
+    assert np.max(np.abs(lam - lam_r) / lam_r) <= REL_T
+
+
 def test_tiny_geometry_and_empty_angle_range(fc, orc):
     """A volume smaller than one 8-voxel brick on every axis (5 x 3 x 2, random
     labels) seen by a 3 x 4 detector: every ray's T and the reconstruction
