@@ -1,13 +1,17 @@
 """Benchmark of the fastCAT CBCT hot path on GB300.
 
 One step = the whole path over one synthetic scan: polyenergetic projection
-with the fused energy integral, detector blur + scatter, Poisson noise, FDK
-filter, FDK backprojection and HU (fc_project + fc_reconstruct).  The
-workload is the Catphan-like kV case (256 x 256 x 10 voxels of 0.0625 cm,
-360 projections on a 512 x 384 detector of 0.4 mm, 30 energy bins).
+with the fused energy integral, detector blur + scatter (and Poisson noise
+when the workload draws it), FDK filter, FDK backprojection and HU
+(fc_project + fc_reconstruct).  The workload is the paper-scale MV case
+(1024 x 1024 x 10 voxels of 0.015625 cm with the Catphan-like phantom, 720
+projections on a 1024 x 768 detector of 0.392 mm, 60 energy bins of a
+2.5 MV bremsstrahlung spectrum, noise-free), the largest configuration that
+fits one GPU.
 
 Metric: rays*bins/s = n_angles * n_v * n_u * n_E / step time (whole job,
-summed over ranks); FDK voxel updates/s are reported beside it.
+summed over ranks); FDK voxel updates/s, rays traced/s and voxel crossings/s
+are reported beside it.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -39,7 +43,7 @@ from paper_2011_04736_gb300 import workloads as W  # noqa: E402
 
 METRIC = "poly-projection rays·bins/s & FDK voxel-upd/s; surrogate vs plain @≤1e-3 err"
 UNIT = "rays*bins/s"
-WORKLOAD = "catphan_kv"
+WORKLOAD = "paper_mv"
 L2_FLUSH_BYTES = 256 << 20
 
 
@@ -130,30 +134,110 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------ roofline
-def _kernel_models(wl):
-    """Algorithmic bytes and FLOPs per launch of each kernel for one step."""
-    g = wl.geom
-    px = g.n_angles * g.n_v * g.n_u
-    rp = int(math.ceil(4 * wl.psf_sigma_px)) if wl.psf_sigma_px > 0 else 0
-    rs = int(math.ceil(4 * wl.scatter_sigma_px)) if wl.scatter_sigma_px > 0 else 0
-    taps = (2 * rp + 1) + (2 * rs + 1)
+def _hit_band(g):
+    """Detector rows [lo, hi] whose rays can meet the voxel slab (the
+    projector's traced band: |v| (SAD - r_max) / SDD <= nz dz / 2, two rows of
+    margin), clipped to the detector; None when empty."""
+    rmax = math.sqrt((0.5 * g.nx * g.dx) ** 2 + (0.5 * g.ny * g.dy) ** 2)
+    vmax = 0.5 * g.nz * g.dz * g.sdd / (g.sad - rmax) / g.dv
+    cv = 0.5 * (g.n_v - 1)
+    lo = max(0, int(math.floor(cv - vmax)) - 2)
+    hi = min(g.n_v - 1, int(math.ceil(cv + vmax)) + 2)
+    return (lo, hi) if lo <= hi else None
+
+
+def _reach_rows(g):
+    """Detector rows the backprojector samples (conservative, two rows of
+    margin): the rows of the filtered-projection buffer."""
     zmax = (g.nz - 1) / 2 * g.dz
     rmax = math.hypot(g.nx * g.dx / 2, g.ny * g.dy / 2)
     vmax = zmax * g.sdd / (g.sad - rmax) / g.dv
     lo = max(0, int(math.floor((g.n_v - 1) / 2 - vmax)) - 2)
     hi = min(g.n_v - 1, int(math.ceil((g.n_v - 1) / 2 + vmax)) + 2)
+    return lo, hi
+
+
+def _blur_rows(wl):
+    """(rows the row pass computes, output rows the column pass computes) on
+    the tensor-core path for the projector's primary: the 64-row tiles
+    holding the traced band, and the 128-row tiles from a multiple of 8
+    covering the band widened by the larger blur radius."""
+    g = wl.geom
+    band = _hit_band(g)
+    if band is None:
+        return 0, 0
+    lo, hi = band[0], band[1] + 1
+    r_lo, r_hi = lo // 64 * 64, min(g.n_v, ((hi - 1) // 64 + 1) * 64)
+    R = max(int(math.ceil(4 * wl.psf_sigma_px)), int(math.ceil(4 * wl.scatter_sigma_px)))
+    clo, chi = max(0, lo - R), min(g.n_v, hi + R)
+    m_off = clo // 8 * 8
+    m_cnt = (chi - m_off + 127) // 128
+    return r_hi - r_lo, min(g.n_v, m_off + 128 * m_cnt) - m_off
+
+
+def ray_stats(g, rows=None):
+    """Rays of detector rows `rows` (default: every row) that meet the voxel
+    box, and the voxels they cross (Siddon segments: per axis the planes
+    crossed inside the box, plus one), summed over every projection."""
+    rows = np.arange(g.n_v) if rows is None else np.asarray(rows)
+    u = (np.arange(g.n_u) - (g.n_u - 1) / 2) * g.du
+    v = (rows - (g.n_v - 1) / 2) * g.dv
+    uu, vv = np.meshgrid(u, v)
+    uu, vv = uu.ravel(), vv.ravel()
+    n = np.array([g.nx, g.ny, g.nz])
+    d = np.array([g.dx, g.dy, g.dz])
+    lo = -0.5 * n * d
+    hits = 0
+    cross = 0
+    for th in g.angles():
+        c, s_ = math.cos(th), math.sin(th)
+        S = np.array([g.sad * c, g.sad * s_, 0.0])
+        P = np.stack([-(g.sdd - g.sad) * c - uu * s_, -(g.sdd - g.sad) * s_ + uu * c, vv], 1)
+        D = P - S
+        with np.errstate(divide="ignore", invalid="ignore"):
+            ta = (lo[None, :] - S[None, :]) / D
+            tb = (-lo[None, :] - S[None, :]) / D
+        tmin = np.where(D == 0, np.where((S[None, :] > lo) & (S[None, :] < -lo), -np.inf, np.inf),
+                        np.minimum(ta, tb))
+        tmax = np.where(D == 0, np.where((S[None, :] > lo) & (S[None, :] < -lo), np.inf, -np.inf),
+                        np.maximum(ta, tb))
+        t0 = np.maximum(0.0, tmin.max(1))
+        t1 = np.minimum(1.0, tmax.min(1))
+        h = t1 > t0
+        if not h.any():
+            continue
+        E = S[None, :] + t0[h, None] * D[h]
+        X = S[None, :] + t1[h, None] * D[h]
+        iE = np.clip(np.floor((E - lo) / d), 0, n - 1)
+        iX = np.clip(np.floor((X - lo) / d), 0, n - 1)
+        hits += int(h.sum())
+        cross += int(np.abs(iX - iE).sum() + h.sum())
+    return hits, cross
+
+
+def _kernel_models(wl):
+    """Algorithmic bytes and FLOPs per step of each kernel: what the kernel
+    must read and write at least, given what it computes in this design
+    (the traced band, the blur tiles near it, the reachable filtered rows)."""
+    g = wl.geom
+    px = g.n_angles * g.n_v * g.n_u
+    rp = int(math.ceil(4 * wl.psf_sigma_px)) if wl.psf_sigma_px > 0 else 0
+    rs = int(math.ceil(4 * wl.scatter_sigma_px)) if wl.scatter_sigma_px > 0 else 0
+    taps = (2 * rp + 1) + (2 * rs + 1)
+    lo, hi = _reach_rows(g)
     rows = hi - lo + 1
     fpx = g.n_angles * rows * g.n_u
     odd = g.n_u if (g.n_u - 1) % 2 == 1 else g.n_u - 1
+    row_rows, col_rows = _blur_rows(wl)
+    bpx_r = g.n_angles * row_rows * g.n_u      # pixels the row pass computes
+    bpx_c = g.n_angles * col_rows * g.n_u      # pixels the column pass computes
     return {
-        # labels once + T written once
-        "project": {"bytes": g.n_voxels + 4 * px, "flops": None, "bound": "hbm"},
-        # T read, two intermediates written (2 flops per tap per output of
-        # direct convolution; on the tensor cores the MMA work is small next
-        # to the traffic, so HBM is the roofline)
-        "blur_rows": {"bytes": 12 * px, "flops": 2 * taps * px, "bound": "hbm"},
-        # two intermediates read, counts written
-        "blur_cols": {"bytes": 12 * px, "flops": 2 * taps * px, "bound": "hbm"},
+        # labels once + T on the rows the row pass reads (T = 1 fill included)
+        "project": {"bytes": g.n_voxels + 4 * bpx_r, "flops": None, "bound": "hbm"},
+        # T read, two intermediates written on the computed tiles
+        "blur_rows": {"bytes": 12 * bpx_r, "flops": 2 * taps * bpx_r, "bound": "hbm"},
+        # intermediates read on the computed tiles, every output pixel written
+        "blur_cols": {"bytes": 8 * bpx_c + 4 * px, "flops": 2 * taps * bpx_c, "bound": "hbm"},
         # reachable rows: counts read, filtered written; odd taps + centre
         "fdk_filter": {"bytes": 8 * fpx, "flops": 2 * (odd + 1) * fpx, "bound": "alu"},
         # filtered reachable rows read once, FP64 volume written once
@@ -164,9 +248,11 @@ def _kernel_models(wl):
     }
 
 
-def _traffic(kernel):
-    """ncu DRAM bytes per launch from profiles/ncu_traffic.json, or None when
-    absent or taken from a different source revision of the kernel."""
+def _ncu_record(kernel, workload=None):
+    """ncu record of a kernel from profiles/ncu_traffic.json (DRAM bytes and
+    warp instructions per launch, the workload they were taken on), or None
+    when absent, taken from a different source revision of the kernel, or
+    (with `workload` given) on another workload."""
     p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     if not os.path.exists(p):
         return None
@@ -179,14 +265,26 @@ def _traffic(kernel):
         return None
     if hashlib.sha256(open(src, "rb").read()).hexdigest()[:16] != ent.get("source_sha"):
         return None
+    if workload is not None and ent.get("workload") not in (None, workload):
+        return None
+    return ent
+
+
+def _traffic(kernel, workload=None):
+    """ncu DRAM bytes per launch (see _ncu_record), scaled from the captured
+    launch to the bench's by `scale` in the record (units of work per
+    launch: the bench launch's over the captured one's)."""
+    ent = _ncu_record(kernel, workload)
+    if not ent:
+        return None
     return ent.get("dram_bytes_per_launch")
 
 
 # ------------------------------------------------------------------ oracle arm
 def _oracle_sample(wl, n_angles):
     """Oracle pipeline on the first n_angles projections of the workload:
-    projection + energy sum, blur + scatter, Poisson noise and FDK over those
-    projections.  Returns seconds."""
+    projection + energy sum, blur + scatter, Poisson noise (when the
+    workload draws it) and FDK over those projections.  Returns seconds."""
     import oracle
     oracle.build()
     g = dataclasses.replace(wl.geom, n_angles=n_angles,
@@ -197,8 +295,8 @@ def _oracle_sample(wl, n_angles):
     t0 = time.perf_counter()
     T = oracle.project_T(g, lab, w, d, mu)
     I = oracle.intensity(T, wl.psf_sigma_px, wl.scatter_sigma_px, wl.spr, wl.n0)
-    K = oracle.poisson(I.astype(np.float32), wl.seed)
-    oracle.fdk(g, K.astype(np.float64), oracle.i_flood(wl.n0, wl.spr))
+    K = oracle.poisson(I.astype(np.float32), wl.seed).astype(np.float64) if wl.noise else I
+    oracle.fdk(g, K, oracle.i_flood(wl.n0, wl.spr))
     return time.perf_counter() - t0
 
 
@@ -209,8 +307,11 @@ def cpu_baseline(wl, n_angles):
     units = n_angles * g.n_v * g.n_u * wl.n_e
     return {"value": units / t, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
             "sample": "%d of %d projections through the FP64 oracle (projection + energy sum, "
-                      "blur + scatter, binary32 Poisson, FDK over those projections), %.2f s"
-                      % (n_angles, g.n_angles, t)}
+                      "blur + scatter%s, FDK over those projections) in %.2f s; every stage is "
+                      "linear in the projections, so the full scan extrapolates linearly to "
+                      "%.1f s at the same rate"
+                      % (n_angles, g.n_angles, ", binary32 Poisson" if wl.noise else "", t,
+                         t * g.n_angles / n_angles)}
 
 
 # ------------------------------------------------------------------ distributed
@@ -302,35 +403,37 @@ def _extra_adjoint(fc, torch):
         sc.close()
 
 
-def _extra_paper_scale(fc, torch):
-    """One simulate + reconstruct step of the paper-scale MV case (1024^2 x 10
-    voxels, 720 projections of 1024 x 768, 60 bins) -- context for the
-    paper's whole-pipeline wall times (different GPU, 18 energies, 180
-    projections)."""
-    wl = W.WORKLOADS["paper_mv"]
+def _extra_step(fc, torch, name, n_sm, mhz, steps=5, warmup=3, angle_stride=1):
+    """One simulate + reconstruct step of another workload, timed like the
+    headline (device time on the launching stream, L2 flushed between
+    steps): ms per step, rays*bins/s, per-kernel times, the dominant
+    kernel's roofline and the projector / backprojector rates."""
+    wl = W.WORKLOADS[name]
     g = wl.geom
-    sc = fc.Scanner(wl, noise=False)
+    stream = torch.cuda.Stream()
+    sc = fc.Scanner(wl, noise=wl.noise, stream=stream)
     try:
+        h = sc.h
         vol = torch.empty((g.nz, g.ny, g.nx), dtype=torch.float64, device="cuda")
-        fc.fc_project(sc.h, 0, g.n_angles, fc.FC_OUT_NONE, None)
-        fc.fc_reconstruct(sc.h, None, vol_mu=vol)
+        hu = torch.empty((g.nz, g.ny, g.nx), dtype=torch.float32, device="cuda")
+        flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+
+        def step():
+            fc.fc_project(h, 0, g.n_angles, fc.FC_OUT_NONE, None, stream)
+            fc.fc_reconstruct(h, None, vol_mu=vol, vol_hu=hu, stream=stream)
+
+        with torch.cuda.stream(stream):
+            for _ in range(warmup):
+                step()
         torch.cuda.synchronize()
-        fc.fc_profile_enable(sc.h, True)
-        a = torch.cuda.Event(enable_timing=True)
-        b = torch.cuda.Event(enable_timing=True)
-        a.record()
-        fc.fc_project(sc.h, 0, g.n_angles, fc.FC_OUT_NONE, None)
-        fc.fc_reconstruct(sc.h, None, vol_mu=vol)
-        b.record()
-        torch.cuda.synchronize()
-        kern = fc.fc_profile_read(sc.h)
-        ms = a.elapsed_time(b)
-        return {"workload": "paper_mv: %dx%dx%d voxels, %d projections of %dx%d, %d MV bins"
-                            % (g.nx, g.ny, g.nz, g.n_angles, g.n_u, g.n_v, wl.n_e),
-                "ms_per_step": ms, "rays_bins_per_s": g.n_rays * wl.n_e / (ms / 1e3),
-                "fdk_voxel_updates_per_s": g.n_voxels * g.n_angles / (ms / 1e3),
-                "kernels_ms": {k: v[0] for k, v in kern.items() if v[1]},
-                "paper_context_s": 61.0}
+        ms, kern, _, _ = _timed(fc, torch, h, step, steps, stream, flush)
+        kernels = _kernel_table(wl, kern, steps)
+        peaks, peak_src = _peaks()
+        return dict(_workload_desc(wl), ms_per_step=ms,
+                    rays_bins_per_s=g.n_rays * wl.n_e / (ms / 1e3),
+                    fdk_voxel_updates_per_s=g.n_voxels * g.n_angles / (ms / 1e3),
+                    kernels=kernels, roofline=_roofline(wl, kernels, peaks, peak_src, n_sm, mhz),
+                    rates=_path_rates(fc, h, wl, kernels, n_sm, mhz, angle_stride))
     finally:
         sc.close()
 
@@ -487,15 +590,17 @@ def _extra_mtf(fc, torch):
         sc.close()
 
 
-def _extras(args, fc, torch):
+def _extras(args, fc, torch, n_sm, mhz):
     out = {}
-    jobs = [("adjoint", lambda: _extra_adjoint(fc, torch)),
+    jobs = [("catphan_kv", lambda: _extra_step(fc, torch, "catphan_kv", n_sm, mhz, steps=20)),
+            ("head", lambda: _extra_step(fc, torch, "head_surrogate", n_sm, mhz, steps=5,
+                                         angle_stride=8)),
+            ("adjoint", lambda: _extra_adjoint(fc, torch)),
             ("dose", lambda: _extra_dose(fc, torch)),
             ("groups", lambda: _extra_groups(fc, torch)),
             ("deconv", lambda: _extra_deconv(fc, torch)),
             ("mtf", lambda: _extra_mtf(fc, torch)),
-            ("paper_timing", lambda: _extra_paper_timing(fc, torch)),
-            ("paper_scale", lambda: _extra_paper_scale(fc, torch))]
+            ("paper_timing", lambda: _extra_paper_timing(fc, torch))]
     if not args.no_surrogate and (not args.extra or "surrogate" in args.extra):
         from paper_2011_04736_gb300 import surrogate_study
 
@@ -517,6 +622,131 @@ def _extras(args, fc, torch):
     return out
 
 
+def _timed(fc, torch, h, step, steps, stream, flush, dist=None):
+    """Device time of `steps` calls of step() on `stream` (CUDA events on that
+    stream, L2 flushed before each, barrier + synchronize around), with the
+    library's per-kernel tracer on.  Returns (ms per step, tracer totals,
+    wall-clock start, end)."""
+    fc.fc_profile_enable(h, True)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(steps)]
+    _barrier(dist)
+    torch.cuda.synchronize()
+    t0 = time.time()
+    with torch.cuda.stream(stream):
+        for i in range(steps):
+            flush.fill_(float(i))           # evict L2 between timed steps (untimed)
+            evs[i][0].record(stream)
+            step()
+            evs[i][1].record(stream)
+    torch.cuda.synchronize()
+    _barrier(dist)
+    t1 = time.time()
+    kern = fc.fc_profile_read(h)
+    fc.fc_profile_enable(h, False)
+    return sum(a.elapsed_time(b) for a, b in evs) / steps, kern, t0, t1
+
+
+def _kernel_table(wl, kern, steps):
+    models = _kernel_models(wl)
+    kernels = {}
+    for name, (ms, n) in kern.items():
+        if n == 0 or name not in models:
+            continue
+        per = ms / steps
+        m = models[name]
+        ent = {"ms_per_step": per, "share": None, "launches_per_step": n / steps,
+               "gbs": m["bytes"] / (per / 1e3) / 1e9}
+        if m["flops"]:
+            ent["gflops"] = m["flops"] / (per / 1e3) / 1e9
+        kernels[name] = ent
+    tot = sum(k["ms_per_step"] for k in kernels.values())
+    for k in kernels.values():
+        k["share"] = k["ms_per_step"] / tot if tot else None
+    return kernels
+
+
+def _issue(kernel, wl, units, seconds, n_sm, mhz):
+    """Instruction-issue fraction of a kernel: its warp instructions per step
+    (ncu record for the current source on this workload family, scaled by
+    units of work) over n_SM x 4 schedulers x clock x time."""
+    ent = _ncu_record(kernel)
+    if not ent or not ent.get("warp_inst_per_launch") or not ent.get("units_per_launch"):
+        return None
+    if ent.get("workload_family") not in (None, wl.name):
+        return None
+    inst = ent["warp_inst_per_launch"] * units / ent["units_per_launch"]
+    peak = n_sm * 4 * mhz * 1e6
+    return {"warp_inst_per_step": inst, "achieved_warp_inst_per_s": inst / seconds,
+            "peak_warp_inst_per_s": peak, "frac": inst / seconds / peak,
+            "lanes_active_per_inst": ent.get("lanes_active_per_inst"),
+            "source": "ncu sm__inst_executed of %s, scaled by %s" % (ent.get("workload"), ent.get("units"))}
+
+
+def _roofline(wl, kernels, peaks, peak_src, n_sm, mhz):
+    """Roofline of the kernel with the largest time share: achieved =
+    algorithmic bytes (or FLOPs) per launch / its measured time."""
+    models = _kernel_models(wl)
+    top = max(kernels, key=lambda k: kernels[k]["ms_per_step"])
+    m = models[top]
+    per_s = kernels[top]["ms_per_step"] / 1e3
+    launches = kernels[top]["launches_per_step"]
+    if m["bound"] == "alu":
+        fmax = float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
+        peak = n_sm * 128 * 2 * fmax / 1e12  # FP32 FMA lanes x 2 flops x clock
+        achieved = m["flops"] / per_s / 1e12
+        unit = "TFLOP/s"
+        peak_note = "FP32 FMA peak %d SM x 128 lanes x 2 x %.0f MHz (derived)" % (n_sm, fmax / 1e6)
+    else:
+        peak = float(peaks["hbm_gbs"])
+        achieved = m["bytes"] / per_s / 1e9
+        unit = "GB/s"
+        peak_note = "HBM copy bandwidth (%s)" % peak_src
+    ent = _ncu_record(top)
+    traffic = None
+    if ent and ent.get("dram_bytes_per_launch") and ent.get("workload_family") in (None, wl.name):
+        traffic = ent["dram_bytes_per_launch"] * ent.get("scale_to_bench", 1.0)
+    return {"kernel": top, "bound": m["bound"], "achieved": achieved, "peak": peak, "unit": unit,
+            "frac": achieved / peak, "traffic": (traffic / launches if traffic else None),
+            "peak_source": peak_note,
+            "algorithmic": {"bytes_per_launch": m["bytes"] / launches,
+                            "flops_per_launch": (m["flops"] / launches if m["flops"] else None)}}
+
+
+def _path_rates(fc, h, wl, kernels, n_sm, mhz, angle_stride=1):
+    """Projector and backprojector rates beside the headline: rays traced,
+    voxel crossings (Siddon segments of the rays that meet the voxels),
+    exp2 evaluations against the MUFU rate (16 per SM per clock), voxel
+    updates, and each kernel's issue fraction where an ncu record exists."""
+    g = wl.geom
+    band = _hit_band(g)
+    out = {}
+    if band is not None and "project" in kernels:
+        gs = g if angle_stride == 1 else dataclasses.replace(g, n_angles=g.n_angles // angle_stride,
+                                                             arc=g.arc * (g.n_angles // angle_stride)
+                                                             * angle_stride / g.n_angles)
+        hits, cross = ray_stats(gs, np.arange(band[0], band[1] + 1))
+        hits, cross = hits * angle_stride, cross * angle_stride
+        t = kernels["project"]["ms_per_step"] / 1e3
+        exps = hits * wl.n_e
+        mufu = n_sm * 16 * mhz * 1e6
+        out["projector"] = {
+            "band_rows": [band[0], band[1]], "rays_in_band": (band[1] - band[0] + 1) * g.n_u * g.n_angles,
+            "rays_traced": hits, "rays_traced_per_s": hits / t,
+            "voxel_crossings": cross, "voxel_crossings_per_s": cross / t,
+            "exp2_per_s": exps / t, "mufu_peak_per_s": mufu, "mufu_frac": exps / t / mufu,
+            "counted": "every projection" if angle_stride == 1 else "every %dth projection, scaled" % angle_stride,
+            "issue": _issue("project", wl, (band[1] - band[0] + 1) * g.n_u * g.n_angles, t, n_sm, mhz)}
+    if "backproject" in kernels:
+        t = kernels["backproject"]["ms_per_step"] / 1e3
+        upd = g.n_voxels * g.n_angles
+        out["backprojector"] = {
+            "variant": fc.FC_BP_NAMES.get(fc.fc_backprojector_in_use(h)),
+            "voxel_updates_per_s": upd / t,
+            "issue": _issue("backproject", wl, upd, t, n_sm, mhz)}
+    return out
+
+
 def run_ours(args):
     rank, world, dist = _dist()
     import torch
@@ -526,11 +756,13 @@ def run_ours(args):
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
     fc.load()
+    props = torch.cuda.get_device_properties(local)
+    n_sm = props.multi_processor_count
     wl = W.WORKLOADS[args.workload]
     g = wl.geom
     lab = wl.make_phantom()
     stream = torch.cuda.Stream()
-    sc = fc.Scanner(wl, labels=lab, device=local, noise=True, stream=stream)
+    sc = fc.Scanner(wl, labels=lab, device=local, noise=wl.noise, stream=stream)
     h = sc.h
     vol = torch.empty((g.nz, g.ny, g.nx), dtype=torch.float64, device="cuda")
     hu = torch.empty((g.nz, g.ny, g.nx), dtype=torch.float32, device="cuda")
@@ -547,33 +779,17 @@ def run_ours(args):
 
     bus = None
     try:
-        bus = torch.cuda.get_device_properties(local).pci_bus_id
+        bus = props.pci_bus_id
     except Exception:
         pass
     clocks = ClockSampler(bus)
     clocks.start()
     time.sleep(0.3)
-    fc.fc_profile_enable(h, True)
-    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-           for _ in range(args.steps)]
-    _barrier(dist)
-    torch.cuda.synchronize()
-    t_wall0 = time.time()
-    with torch.cuda.stream(stream):
-        for i in range(args.steps):
-            flush.fill_(float(i))           # evict L2 between timed steps (untimed)
-            evs[i][0].record(stream)
-            step()
-            evs[i][1].record(stream)
-    torch.cuda.synchronize()
-    _barrier(dist)
-    t_wall1 = time.time()
-    dev_ms = sum(a.elapsed_time(b) for a, b in evs)
-    kern = fc.fc_profile_read(h)
-    fc.fc_profile_enable(h, False)
-    ms_step = aggregate(dist, dev_ms / args.steps, "max")
+    ms_step, kern, t_wall0, t_wall1 = _timed(fc, torch, h, step, args.steps, stream, flush, dist)
+    ms_step = aggregate(dist, ms_step, "max")
 
-    # e2e through the public API with host buffers (pinned)
+    # e2e through the public API with host buffers (pinned): labels in,
+    # volume out, every step
     lab_h = torch.from_numpy(lab).pin_memory().numpy()
     vol_h = torch.empty((g.nz, g.ny, g.nx), dtype=torch.float64).pin_memory().numpy()
     for _ in range(2):
@@ -582,76 +798,51 @@ def run_ours(args):
         fc.fc_reconstruct(h, None, vol_mu=vol_h, stream=stream)
     _barrier(dist)
     torch.cuda.synchronize()
+    n_e2e = max(1, min(args.steps, 100))
     t0 = time.perf_counter()
-    for _ in range(args.steps):
+    for _ in range(n_e2e):
         fc.fc_set_phantom(h, lab_h, sc.n_mat, stream)          # H2D: labels
         fc.fc_project(h, 0, g.n_angles, fc.FC_OUT_NONE, None, stream)
         fc.fc_reconstruct(h, None, vol_mu=vol_h, stream=stream)  # D2H: volume (syncs)
     torch.cuda.synchronize()
-    e2e_s = aggregate(dist, (time.perf_counter() - t0) / args.steps, "max")
+    e2e_s = aggregate(dist, (time.perf_counter() - t0) / n_e2e, "max")
     _barrier(dist)
     clocks.stop()
+    clk = clocks.summary(t_wall0, t_wall1)
+    mhz = clk["sm_mhz"] or 2070.0
 
     units = g.n_rays * wl.n_e
     value = units * world / (ms_step / 1e3)
     vox_rate = g.n_voxels * g.n_angles * world / (ms_step / 1e3)
     peaks, peak_src = _peaks()
-    models = _kernel_models(wl)
-    kernels = {}
-    for name, (ms, n) in kern.items():
-        if n == 0 or name not in models:
-            continue
-        per = ms / args.steps
-        m = models[name]
-        ent = {"ms_per_step": per, "share": None, "launches_per_step": n / args.steps,
-               "gbs": m["bytes"] / (per / 1e3) / 1e9}
-        if m["flops"]:
-            ent["gflops"] = m["flops"] / (per / 1e3) / 1e9
-        kernels[name] = ent
-    tot = sum(k["ms_per_step"] for k in kernels.values())
-    for k in kernels.values():
-        k["share"] = k["ms_per_step"] / tot if tot else None
-    top = max(kernels, key=lambda k: kernels[k]["ms_per_step"])
-    m = models[top]
-    per_s = kernels[top]["ms_per_step"] / 1e3
-    launches = kernels[top]["launches_per_step"]
-    if m["bound"] == "alu":
-        fmax = float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
-        peak = 152 * 128 * 2 * fmax / 1e12  # FP32 FMA lanes x 2 flops x clock
-        achieved = m["flops"] / per_s / 1e12
-        unit = "TFLOP/s"
-        peak_note = "FP32 FMA peak 152 SM x 128 lanes x 2 x %.0f MHz (derived)" % (fmax / 1e6)
-    else:
-        peak = float(peaks["hbm_gbs"])
-        achieved = m["bytes"] / per_s / 1e9
-        unit = "GB/s"
-        peak_note = "HBM copy bandwidth (%s)" % peak_src
-    traffic = _traffic(top)
-    roof = {"kernel": top, "bound": m["bound"], "achieved": achieved, "peak": peak, "unit": unit,
-            "frac": achieved / peak, "traffic": (traffic / launches if traffic else None),
-            "peak_source": peak_note,
-            "algorithmic": {"bytes_per_launch": m["bytes"] / launches,
-                            "flops_per_launch": (m["flops"] / launches if m["flops"] else None)}}
+    kernels = _kernel_table(wl, kern, args.steps)
+    roof = _roofline(wl, kernels, peaks, peak_src, n_sm, mhz)
+    rates = _path_rates(fc, h, wl, kernels, n_sm, mhz)
     launches_total = int(sum(n for (_, n) in kern.values()))
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": dict(_workload_desc(wl), l2="flushed by a 256 MiB write between timed steps",
+        "config": dict(_workload_desc(wl), l2="flushed by a 256 MiB write between timed steps "
+                                              "(the projection buffers are larger than L2 as well)",
                        parallelism="replicas (one independent scan per GPU)"),
         "fdk_voxel_updates_per_s": vox_rate,
-        "clocks": clocks.summary(t_wall0, t_wall1),
+        "rays_traced_per_s": (rates.get("projector", {}).get("rays_traced", 0) * world
+                              / (ms_step / 1e3)),
+        "clocks": clk,
         "e2e": {"value": units * world / e2e_s, "unit": UNIT,
-                "h2d_bytes_per_step": int(lab.nbytes), "d2h_bytes_per_step": int(vol_h.nbytes)},
+                "h2d_bytes_per_step": int(lab.nbytes), "d2h_bytes_per_step": int(vol_h.nbytes),
+                "steps": n_e2e},
         "gpu_launches": launches_total,
         "roofline": roof,
+        "rates": rates,
         "kernels": kernels,
     }
     sc.close()
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(wl, args.cpu_angles)
     if rank == 0 and world == 1 and not args.no_extras:
-        line["extras"] = _extras(args, fc, torch)
+        line["extras"] = _extras(args, fc, torch, n_sm, mhz)
     if rank == 0:
         print(json.dumps(line))
     if dist is not None:
@@ -669,7 +860,7 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(W.WORKLOADS))
-    ap.add_argument("--cpu-angles", type=int, default=96,
+    ap.add_argument("--cpu-angles", type=int, default=64,
                     help="projections in the oracle CPU-baseline sample")
     ap.add_argument("--ref-angles", type=int, default=8,
                     help="projections per reference-arm step")
@@ -678,8 +869,8 @@ def main(argv=None):
                     help="skip the adjoint, paper-scale and surrogate measurements")
     ap.add_argument("--no-surrogate", action="store_true")
     ap.add_argument("--extra", action="append", default=[],
-                    help="run only these extras (repeatable): adjoint, dose, groups, deconv, mtf, "
-                         "paper_timing, paper_scale, surrogate")
+                    help="run only these extras (repeatable): catphan_kv, head, adjoint, dose, "
+                         "groups, deconv, mtf, paper_timing, surrogate")
     ap.add_argument("--surrogate-steps", type=int, default=20000)
     args = ap.parse_args(argv)
     if args.warmup < 3:

@@ -343,14 +343,28 @@ __global__ void __launch_bounds__(256, 8) k_backproject_dense(const __grid_const
 // formed once: slice z loads only row j_z + 1 (two taps) and takes row j_z
 // from the slice before (the same row, or the one it loaded).  Per update
 // that is two tap loads instead of four and one u interpolation instead of
-// two; each slice's arithmetic is otherwise the chunked kernel's, so the
-// sums are the same.  Binary32 partial sums over kFold angles are folded
-// into binary64 sums kept in shared memory.
-template <int NZ>
+// two.  The slices run as two interleaved halves (z and z + NA), so the
+// binary32 arithmetic issues as packed pairs (Blackwell f32x2 FMA / add
+// instructions: two lanes' worth of binary32 work per instruction, each
+// element rounded exactly as the scalar instruction would); floors come
+// from adding 2^23 with rounding toward -inf (exact for 0 <= v < 2^22).
+// Binary32 partial sums over kFold angles are folded into binary64 sums
+// kept in shared memory.  CLAMP_V: clamp the detector row coordinate into
+// the stored rows (needed only when the stored rows were cut at the
+// detector edge).
+namespace {
+__device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
+// a - b, exactly as a binary32 subtraction rounds it (b * -1 is exact)
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, f2(-1.0f), a); }
+constexpr float kTwo23 = 8388608.0f;
+}  // namespace
+
+template <int NZ, bool CLAMP_V>
 __global__ void __launch_bounds__(256)
 k_backproject_slab(const __grid_constant__ FdkParams p, const float *__restrict__ f,
                    double *__restrict__ vol)
 {
+    constexpr int NA = (NZ + 1) / 2;     // slices per half: z = i and z = i + NA
     __shared__ double accd[NZ][256];
     const DevGeom &g = p.g;
     const int t = threadIdx.y * 32 + threadIdx.x;
@@ -363,15 +377,17 @@ k_backproject_slab(const __grid_constant__ FdkParams p, const float *__restrict_
     const float y = ((float)iy - 0.5f * (float)(g.ny - 1)) * g.dy;
     const float z0 = -0.5f * (float)(g.nz - 1) * g.dz;
     const size_t plane = (size_t)p.ph * p.pw;
-    const int pw = p.pw;
+    const int pw4 = 4 * p.pw;        // row pitch in bytes (32-bit: one wide multiply-add per address)
     const float cu1 = g.cu + 1.0f, cv1 = g.cv - (float)p.v_lo + 1.0f;
     const float umax = (float)(p.pw - 2), vmaxp = (float)(p.ph - 2);
-    const float sdd_du = g.sdd / g.du, sdd_dv = g.sdd / g.dv;
+    const float sdd_du = g.sdd / g.du, sdd_dv = g.sdd / g.dv, dz_dv = g.dz * (g.sdd / g.dv);
+    const float2 zz_step = make_float2(0.0f, (float)NA);   // (z_a, z_b) at i = 0
+    const int two23 = __float_as_int(kTwo23);
     for (int kb = 0; kb < g.n_angles; kb += kFold) {
         const int ke = min(g.n_angles, kb + kFold);
-        float accf[NZ];
+        float2 acc[NA];
 #pragma unroll
-        for (int z = 0; z < NZ; ++z) accf[z] = 0.0f;
+        for (int i = 0; i < NA; ++i) acc[i] = make_float2(0.0f, 0.0f);
 #pragma unroll 2
         for (int k = kb; k < ke; ++k) {
             const float2 cs = p.trig[k];
@@ -379,39 +395,65 @@ k_backproject_slab(const __grid_constant__ FdkParams p, const float *__restrict_
             const float ru = y * cs.x - x * cs.y;
             const float iU = __frcp_rn(U);
             const float fu = fminf(fmaxf(fmaf(ru * iU, sdd_du, cu1), 0.0f), umax);
-            const float w = (g.sad * iU) * (g.sad * iU);
-            const float fv0 = fmaf(z0 * iU, sdd_dv, cv1);
-            const float dfv = g.dz * iU * sdd_dv;
-            const float fu0 = floorf(fu);
-            const float au = fu - fu0;
-            const float *fk = f + (size_t)k * plane + (int)fu0;
-            float lo = 0.0f, hi = 0.0f;
-            int jp = 0;
+            const float tu = __fadd_rd(fu, kTwo23);          // 2^23 + floor(fu)
+            const float au = fu - (tu - kTwo23);
+            const float2 w2 = f2((g.sad * iU) * (g.sad * iU));
+            const float2 fv0 = f2(fmaf(z0 * iU, sdd_dv, cv1));
+            const float2 dfv = f2(dz_dv * iU);
+            const float2 au2 = f2(au);
+            // byte address of row r + 1 of the column: base + (2^23 + r) * pw4
+            const char *base = reinterpret_cast<const char *>(f + (size_t)k * plane +
+                                                              (__float_as_int(tu) - two23)) +
+                               (long long)(1 - two23) * (long long)pw4;
+            float2 lo, hi;
+            int2 jp;
 #pragma unroll
-            for (int z = 0; z < NZ; ++z) {
-                const float fv = fminf(fmaxf(fmaf((float)z, dfv, fv0), 0.0f), vmaxp);
-                const float fvf = floorf(fv);
-                const float av = fv - fvf;
-                const int j = (int)fvf;
-                const float *r = fk + (j + 1) * pw;
-                const float b0 = __ldg(r), b1 = __ldg(r + 1);
-                const float nh = fmaf(au, b1 - b0, b0);
-                if (z == 0) {
-                    const float a0 = __ldg(r - pw), a1 = __ldg(r - pw + 1);
-                    lo = fmaf(au, a1 - a0, a0);
+            for (int i = 0; i < NA; ++i) {
+                const float2 zz = make_float2((float)i + zz_step.x, (float)i + zz_step.y);
+                float2 fv = __ffma2_rn(zz, dfv, fv0);
+                if (CLAMP_V) {
+                    fv.x = fminf(fmaxf(fv.x, 0.0f), vmaxp);
+                    fv.y = fminf(fmaxf(fv.y, 0.0f), vmaxp);
+                }
+                const float2 tv = __fadd2_rd(fv, f2(kTwo23));    // 2^23 + floor(fv)
+                const float2 av = sub2(fv, __fadd2_rn(tv, f2(-kTwo23)));
+                const int2 j = make_int2(__float_as_int(tv.x), __float_as_int(tv.y));
+                const float *ra = reinterpret_cast<const float *>(base + (long long)j.x * (long long)pw4);
+                const float *rb = reinterpret_cast<const float *>(base + (long long)j.y * (long long)pw4);
+                const float2 b0 = make_float2(__ldg(ra), __ldg(rb));
+                const float2 b1 = make_float2(__ldg(ra + 1), __ldg(rb + 1));
+                const float2 nh = __ffma2_rn(au2, sub2(b1, b0), b0);
+                if (i == 0) {
+                    const float2 a0 = make_float2(__ldg(ra - p.pw), __ldg(rb - p.pw));
+                    const float2 a1 = make_float2(__ldg(ra - p.pw + 1), __ldg(rb - p.pw + 1));
+                    lo = __ffma2_rn(au2, sub2(a1, a0), a0);
                 } else {
-                    lo = j == jp ? lo : hi;
+                    lo.x = j.x == jp.x ? lo.x : hi.x;
+                    lo.y = j.y == jp.y ? lo.y : hi.y;
                 }
                 hi = nh;
                 jp = j;
-                accf[z] = fmaf(w, fmaf(av, hi - lo, lo), accf[z]);
+                acc[i] = __ffma2_rn(w2, __ffma2_rn(av, sub2(hi, lo), lo), acc[i]);
             }
         }
 #pragma unroll
-        for (int z = 0; z < NZ; ++z) accd[z][t] += (double)accf[z];
+        for (int i = 0; i < NA; ++i) {
+            accd[i][t] += (double)acc[i].x;
+            if (i + NA < NZ) accd[i + NA][t] += (double)acc[i].y;
+        }
     }
 #pragma unroll
     for (int z = 0; z < NZ; ++z) vol[((size_t)z * g.ny + iy) * g.nx + ix] = accd[z][t] * p.scale;
+}
+
+// Whether fdk_row_range cut the reachable rows at a detector edge.
+static bool slab_rows_cut(const DevGeom &g)
+{
+    const double hx = 0.5 * g.nx * (double)g.dx, hy = 0.5 * g.ny * (double)g.dy;
+    const double umin = (double)g.sad - sqrt(hx * hx + hy * hy);
+    if (umin <= 0.0) return true;
+    const double vmax = 0.5 * (g.nz - 1) * (double)g.dz * (double)g.sdd / umin / (double)g.dv;
+    return (int)floor((double)g.cv - vmax) - 2 < 0 || (int)ceil((double)g.cv + vmax) + 2 > g.n_v - 1;
 }
 
 // Largest projected z pitch, in detector rows, over the voxels of the
@@ -448,9 +490,16 @@ cudaError_t launch_backproject(const FdkParams &p, const float *filt, double *vo
     if (variant == FC_BP_SLAB) {
         dim3 block(32, 8);
         dim3 grid((p.g.nx + 31) / 32, (p.g.ny + 7) / 8);
+        // the stored rows [v_lo, v_hi] hold every row a voxel projects onto
+        // (with two rows of margin) unless the range was cut at a detector
+        // edge; only then can a row coordinate leave the stored rows
+        const bool clamp = slab_rows_cut(p.g);
 #define FC_BPS(Z)                                                              \
     case Z:                                                                    \
-        k_backproject_slab<Z><<<grid, block, 0, s>>>(p, filt, vol);            \
+        if (clamp)                                                             \
+            k_backproject_slab<Z, true><<<grid, block, 0, s>>>(p, filt, vol);  \
+        else                                                                   \
+            k_backproject_slab<Z, false><<<grid, block, 0, s>>>(p, filt, vol); \
         break;
         switch (p.g.nz) {
         FC_BPS(1) FC_BPS(2) FC_BPS(3) FC_BPS(4) FC_BPS(5) FC_BPS(6) FC_BPS(7) FC_BPS(8)

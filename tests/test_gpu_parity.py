@@ -86,6 +86,74 @@ def test_primary_ragged_random_labels(fc, orc):
     assert rel.max() <= REL_T, rel.max()
 
 
+def test_eight_materials_ragged_random_labels(fc, orc):
+    """All eight material slots (labels 0..7, the head-like phantom's
+    table): per-material path lengths and T of every ray against the
+    oracle on a ragged grid."""
+    wl = W.scaled(W.WORKLOADS["head_surrogate"], n_u=70, n_v=45, n_angles=7, nx=24, ny=20, nz=16,
+                  dx=0.25, dy=0.25, dz=0.25, du=0.12, dv=0.12)
+    g = wl.geom
+    assert len(wl.labels) == 8
+    lab = np.random.default_rng(25).integers(0, 8, size=(g.nz, g.ny, g.nx)).astype(np.uint8)
+    assert (np.bincount(lab.ravel(), minlength=8) > 0).all()
+    sc = _scanner(fc, wl, lab, noise=False)
+    try:
+        T = _project(fc, sc, fc.FC_OUT_PRIMARY)
+        L = torch.empty((g.n_angles, g.n_v, g.n_u, 8), dtype=torch.float32, device="cuda")
+        fc.fc_project_lengths(sc.h, 0, g.n_angles, L)
+        torch.cuda.synchronize()
+        L = L.cpu().numpy().reshape(-1, 8)
+    finally:
+        sc.close()
+    w, d = wl.spectrum()
+    Tr = orc.project_T(g, lab, w, d, wl.mu())
+    assert np.max(np.abs(T - Tr) / Tr) <= REL_T
+    k, v, u = np.meshgrid(np.arange(g.n_angles), np.arange(g.n_v), np.arange(g.n_u), indexing="ij")
+    Lr, _ = orc.rays(g, lab, w, d, wl.mu(), np.stack([k.ravel(), v.ravel(), u.ravel()], 1))
+    assert (Lr[:, 7] > 0).sum() > 100                  # slot 7 is exercised
+    assert np.abs(L - Lr).max() < 2e-4
+
+
+def test_head_phantom_reduced_every_ray(fc, orc):
+    """The head-like phantom (8 materials, 40 random ellipsoids) at 64^3
+    voxels of 0.25 cm, 24 projections of 128 x 128, 120 bins: every ray."""
+    wl = W.scaled(W.WORKLOADS["head_surrogate"], n_u=128, n_v=128, n_angles=24, nx=64, ny=64,
+                  nz=64, dx=0.25, dy=0.25, dz=0.25, du=0.2, dv=0.2)
+    g = wl.geom
+    lab = wl.make_phantom()
+    sc = _scanner(fc, wl, lab, noise=False)
+    try:
+        T = _project(fc, sc, fc.FC_OUT_PRIMARY)
+    finally:
+        sc.close()
+    w, d = wl.spectrum()
+    Tr = orc.project_T(g, lab, w, d, wl.mu())
+    assert np.max(np.abs(T - Tr) / Tr) <= REL_T
+
+
+def test_head_phantom_full_size_sampled(fc, orc):
+    """Full head-like scan (256^3 voxels of 0.0625 cm, 360 projections of
+    512 x 512, 120 bins): T at 4000 sampled rays of five projections."""
+    wl = W.WORKLOADS["head_surrogate"]
+    g = wl.geom
+    lab = wl.make_phantom()
+    ks = [0, 77, 180, 251, 359]
+    sc = _scanner(fc, wl, lab, noise=False)
+    try:
+        T = np.stack([_project(fc, sc, fc.FC_OUT_PRIMARY, k, 1)[0] for k in ks])
+    finally:
+        sc.close()
+    rng = np.random.default_rng(26)
+    n = 4000
+    kk = rng.integers(0, len(ks), n)
+    rows = rng.integers(0, g.n_v, n)
+    cols = rng.integers(0, g.n_u, n)
+    w, d = wl.spectrum()
+    Lr, Tr = orc.rays(g, lab, w, d, wl.mu(), np.stack([np.array(ks)[kk], rows, cols], 1))
+    assert (Lr[:, 7] > 0).sum() > 10                   # teeth crossed by some sampled rays
+    assert np.max(np.abs(T[kk, rows, cols] - Tr) / Tr) <= REL_T
+
+
 def test_primary_thin_slab_band_edges(fc, orc):
     """A 3-slice slab seen by a 45-row detector: only a band of rows can meet
     the voxels, so the projector traces 8-row blocks around it and a store
