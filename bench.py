@@ -157,6 +157,18 @@ def _reach_rows(g):
     return lo, hi
 
 
+def _band_blur(wl):
+    """Whether the detector blur of the workload's primary takes the band
+    kernel (a traced band of at most 32 rows touching neither detector edge),
+    and the band height."""
+    g = wl.geom
+    band = _hit_band(g)
+    if band is None:
+        return False, 0
+    hb = band[1] - band[0] + 1
+    return (hb <= 32 and band[0] >= 1 and band[1] + 1 <= g.n_v - 1), hb
+
+
 def _blur_rows(wl):
     """(rows the row pass computes, output rows the column pass computes) on
     the tensor-core path for the projector's primary: the 64-row tiles
@@ -231,9 +243,18 @@ def _kernel_models(wl):
     row_rows, col_rows = _blur_rows(wl)
     bpx_r = g.n_angles * row_rows * g.n_u      # pixels the row pass computes
     bpx_c = g.n_angles * col_rows * g.n_u      # pixels the column pass computes
+    band, hb = _band_blur(wl)
+    bpx_b = g.n_angles * hb * g.n_u            # band pixels
+    R = max(rp, rs)
     return {
-        # labels once + T on the rows the row pass reads (T = 1 fill included)
-        "project": {"bytes": g.n_voxels + 4 * bpx_r, "flops": None, "bound": "hbm"},
+        # labels once + T on the rows the blur reads (T = 1 fill included)
+        "project": {"bytes": g.n_voxels + 4 * (bpx_b if band else bpx_r), "flops": None,
+                    "bound": "hbm"},
+        # band rows of T read, every output pixel written; row passes of the
+        # band rows, column sums over the band rows near it
+        "blur_band": {"bytes": 4 * bpx_b + 4 * px,
+                      "flops": 2 * taps * bpx_b + 2 * 2 * hb * g.n_angles * g.n_u * min(g.n_v, hb + 2 * R),
+                      "bound": "hbm"},
         # T read, two intermediates written on the computed tiles
         "blur_rows": {"bytes": 12 * bpx_r, "flops": 2 * taps * bpx_r, "bound": "hbm"},
         # intermediates read on the computed tiles, every output pixel written

@@ -320,7 +320,8 @@ int fc_fluence_for_dose(const fc_handle *h, double dose_gy, double dp_gy, double
 #define FC_K_DOSE           11  /* dose estimate (four kernels) */
 #define FC_K_GROUP_BLUR     12  /* energy-group model: scatter profile + per-group blur (2 kernels) */
 #define FC_K_DECONV         13  /* Richardson-Lucy deconvolution (1 + n_iter kernels) */
-#define FC_K_COUNT          14
+#define FC_K_BLUR_BAND      14  /* detector blur of a primary that is 1 outside a narrow band of rows */
+#define FC_K_COUNT          15
 
 /* Enable (1) or disable (0) tracing; enabling discards pending records.
  * Errors: FC_EINVAL. */

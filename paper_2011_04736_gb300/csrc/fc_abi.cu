@@ -597,6 +597,13 @@ static int run_blur(fc_handle *h, const float *in, float *out, size_t off, int n
     fc::BlurParams b;
     int rc = blur_params(h, psf, sc, n0, spr, &b);
     if (rc) return rc;
+    if (one_hi >= 0 && in != out && fc::blur_band_supported(b, one_lo, one_hi)) {
+        // the input differs from 1 on a narrow band of rows only
+        Trace t(h, FC_K_BLUR_BAND, 1, s);
+        FC_CK(fc::launch_blur_band(b, in, out, n, one_lo, one_hi, s));
+        t.end();
+        return FC_OK;
+    }
     if (!fc::blur_tc_supported(b)) {
         // radii beyond the tensor-core path: direct f32 passes
         if (!fc::blur_rows_fit(b))
@@ -857,13 +864,19 @@ int fc_project(fc_handle *h, int angle_begin, int angle_count, int out_kind, flo
             return fail(FC_EINVAL, "fc_project: noise before the optical spread is not defined for energy groups");
     } else {
         // T = 1 goes to every row when T is returned; otherwise only to the
-        // rows the tensor-core row pass reads (it takes the others as 1)
+        // rows the blur reads (it takes the others as 1): none for the band
+        // blur, the 64-row tiles around the band for the tensor-core pass
         int f_lo = 0, f_hi = -1;
         if (out_kind != FC_OUT_PRIMARY) {
             fc::BlurParams b;
             rc = blur_params(h, h->noise_order == FC_NOISE_BEFORE_PSF ? 0.0 : h->psf, h->sc, h->n0, h->spr, &b);
             if (rc) return rc;
-            if (fc::blur_tc_supported(b)) fc::blur_tc_rows_read(b, one_lo, one_hi, &f_lo, &f_hi);
+            if (fc::blur_band_supported(b, one_lo, one_hi)) {
+                f_lo = one_lo;
+                f_hi = one_hi;
+            } else if (fc::blur_tc_supported(b)) {
+                fc::blur_tc_rows_read(b, one_lo, one_hi, &f_lo, &f_hi);
+            }
         }
         Trace t(h, FC_K_PROJECT, fc::project_launches(p, f_lo, f_hi), s);
         FC_CK(fc::launch_project(p, h->d_T, nullptr, s, f_lo, f_hi));

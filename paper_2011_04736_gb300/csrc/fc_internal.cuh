@@ -298,6 +298,11 @@ int blur_tc_rows_launches(const BlurParams &bp, int one_lo, int one_hi);
 // every row)
 void blur_tc_rows_read(const BlurParams &bp, int one_lo, int one_hi, int *lo, int *hi);
 int blur_tc_cols_launches(const BlurParams &bp, int one_lo, int one_hi);
+// Blur of an input that is 1 outside the rows [b_lo, b_hi) (fc_blur_band.cu):
+// one kernel reading only those rows and writing every output pixel.
+bool blur_band_supported(const BlurParams &bp, int b_lo, int b_hi);
+cudaError_t launch_blur_band(const BlurParams &bp, const float *T, float *out, int n_img, int b_lo,
+                             int b_hi, cudaStream_t s);
 cudaError_t launch_blur_tc_cols(const BlurParams &bp, const float *tp, const float *ts, float *out,
                                 const uint16_t *hankel, unsigned int *err, int n_img, cudaStream_t s,
                                 int one_lo = 0, int one_hi = -1);

@@ -40,7 +40,7 @@ FC_SURROGATE_PARAMS = 34305
 FC_SURROGATE_STATE = 34305 + 52 + 2 * 34305 + 1
 FC_K_NAMES = ("project", "blur_rows", "blur_cols", "fdk_filter", "backproject", "hu", "lengths",
               "noise", "surrogate_eval", "surrogate_train", "energy_sum", "dose", "group_blur",
-              "deconv")
+              "deconv", "blur_band")
 
 
 class FastcatError(RuntimeError):

@@ -13,14 +13,16 @@ def test_kernel_models_cover_the_step_and_scale_with_the_workload():
     for name in ("catphan_kv", "paper_mv"):
         wl = W.WORKLOADS[name]
         m = bench._kernel_models(wl)
-        assert set(m) == {"project", "blur_rows", "blur_cols", "fdk_filter", "backproject", "hu",
-                          "noise"}
+        assert set(m) == {"project", "blur_rows", "blur_cols", "blur_band", "fdk_filter",
+                          "backproject", "hu", "noise"}
         g = wl.geom
         px = g.n_angles * g.n_v * g.n_u
         rows_r, rows_c = bench._blur_rows(wl)
         assert m["noise"]["bytes"] == 8 * px                  # rates in, counts out
-        # labels once, T on the rows the row pass reads
-        assert m["project"]["bytes"] == g.n_voxels + 4 * g.n_angles * rows_r * g.n_u
+        # labels once, T on the rows the blur reads (the band for both workloads)
+        band, hb = bench._band_blur(wl)
+        assert band
+        assert m["project"]["bytes"] == g.n_voxels + 4 * g.n_angles * hb * g.n_u
         assert m["blur_cols"]["bytes"] >= 4 * px              # every output pixel written
         for k in m.values():
             assert k["bound"] in ("hbm", "alu") and k["bytes"] > 0
