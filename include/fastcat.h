@@ -432,6 +432,25 @@ int fc_cnr_grad(fc_handle *h, const double *logits, const double *D, const doubl
                 const float *rho, const float *z, int n_roi, const fc_cnr_roi *rois, double *J,
                 double *g_logits, double *g_D, float *g_rho, void *stream);
 
+/* Fault injection for failure-handling tests (instrumentation: the paper
+ * has no counterpart).  Process-wide and one-shot; nothing faults the GPU:
+ *   FC_FAULT_NONE          clear every pending injection;
+ *   FC_FAULT_ALLOC         the device allocation after the next `arg` ones
+ *                          (arg >= 0) fails as out of memory: the call that
+ *                          makes it returns FC_ENOMEM, the handle stays
+ *                          usable and a later call allocates again;
+ *   FC_FAULT_BLUR_TIMEOUT  the next tensor-core detector blur gives up its
+ *                          first bounded accumulator wait at once and takes
+ *                          its abort path (its MMAs and copies drained, tensor
+ *                          memory freed, the error word set); the call that
+ *                          reads the error word (a host output) returns
+ *                          FC_ETIMEOUT and later calls run normally.
+ * Errors: FC_EINVAL (unknown kind, negative count). */
+#define FC_FAULT_NONE         0
+#define FC_FAULT_ALLOC        1
+#define FC_FAULT_BLUR_TIMEOUT 2
+int fc_inject_fault(int kind, int64_t arg);
+
 /* Allocation-free detector blur.  The paper has no counterpart: this entry
  * point exists for callers that cannot allocate device memory while they
  * run -- their device memory is owned by another allocator (for example a

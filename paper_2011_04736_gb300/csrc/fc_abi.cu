@@ -54,6 +54,25 @@ struct DeviceGuard {
     }
 };
 
+// Fault injection for tests (fc_inject_fault): device allocations left
+// before one fails (-1: none), and whether the next tensor-core blur gives up
+// its epilogue waits at once.
+std::atomic<long long> g_alloc_fail_in{-1};
+std::atomic<int> g_blur_timeout{0};
+
+// cudaMalloc, or the injected failure.
+cudaError_t dev_malloc(void **p, size_t bytes)
+{
+    long long c = g_alloc_fail_in.load();
+    while (c >= 0 && !g_alloc_fail_in.compare_exchange_weak(c, c - 1)) {
+    }
+    if (c == 0) {
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
+    return cudaMalloc(p, bytes);
+}
+
 // Padded filtered-projection row: one zero column before the detector row,
 // at least two after, rounded up to 16 bytes (tensor-map row stride).
 int fdk_row_pitch(int n_u) { return (n_u + 3 + 3) & ~3; }
@@ -101,6 +120,7 @@ struct fc_handle {
     int noise = 0;
     int noise_order = FC_NOISE_AFTER_BLUR;
     int bp_request = FC_BP_AUTO;   // FDK backprojector variant (fc_set_backprojector)
+    double band_hit_frac = 1.0;    // share of the traced band's rays that meet the voxels
     // energy-group detector model (off when n_groups == 0)
     int n_groups = 0;
     int grp_end[FC_MAX_GROUPS] = {0};
@@ -211,17 +231,24 @@ struct fc_handle {
 
 namespace {
 
+// Each buffer is allocated on its own, so a call that failed part-way (out
+// of memory) leaves the handle consistent and the next call allocates the rest.
 int ensure_proj_buffers(fc_handle *h)
 {
-    if (h->d_T) return FC_OK;
     const size_t b = h->proj_elems * sizeof(float);
-    FC_CK(cudaMalloc((void **)&h->d_T, b));
-    FC_CK(cudaMalloc((void **)&h->d_tp, b));
-    FC_CK(cudaMalloc((void **)&h->d_ts, b));
-    FC_CK(cudaMalloc((void **)&h->d_counts, b));
-    FC_CK(cudaMalloc((void **)&h->d_hankel, fc::kBlurTcHankelMax * sizeof(uint16_t)));
-    FC_CK(cudaMalloc((void **)&h->d_blur_err, sizeof(unsigned int)));
-    FC_CK(cudaMemset(h->d_blur_err, 0, sizeof(unsigned int)));
+    if (!h->d_T) FC_CK(dev_malloc((void **)&h->d_T, b));
+    if (!h->d_tp) FC_CK(dev_malloc((void **)&h->d_tp, b));
+    if (!h->d_ts) FC_CK(dev_malloc((void **)&h->d_ts, b));
+    if (!h->d_counts) FC_CK(dev_malloc((void **)&h->d_counts, b));
+    if (!h->d_hankel) FC_CK(dev_malloc((void **)&h->d_hankel, fc::kBlurTcHankelMax * sizeof(uint16_t)));
+    if (!h->d_blur_err) {
+        FC_CK(dev_malloc((void **)&h->d_blur_err, sizeof(unsigned int)));
+        const cudaError_t e = cudaMemset(h->d_blur_err, 0, sizeof(unsigned int));
+        if (e != cudaSuccess) {
+            dfree(h->d_blur_err);
+            FC_CK(e);
+        }
+    }
     return FC_OK;
 }
 
@@ -243,13 +270,13 @@ int ensure_recon_buffers(fc_handle *h, cudaStream_t s)
         int lo, hi;
         fc::fdk_row_range(h->dg, &lo, &hi);
         h->filt_elems = (size_t)h->g.n_angles * (hi - lo + 1 + 3) * fdk_row_pitch(h->g.n_u);
-        FC_CK(cudaMalloc((void **)&h->d_filt, h->filt_elems * sizeof(float)));
+        FC_CK(dev_malloc((void **)&h->d_filt, h->filt_elems * sizeof(float)));
         FC_CK(cudaMemsetAsync(h->d_filt, 0, h->filt_elems * sizeof(float), s));
     }
-    if (!h->d_counts) FC_CK(cudaMalloc((void **)&h->d_counts, h->proj_elems * sizeof(float)));
-    if (!h->d_vol) FC_CK(cudaMalloc((void **)&h->d_vol, h->vol_elems * sizeof(double)));
-    if (!h->d_hu) FC_CK(cudaMalloc((void **)&h->d_hu, h->vol_elems * sizeof(float)));
-    if (!h->d_part) FC_CK(cudaMalloc((void **)&h->d_part, 2 * 256 * sizeof(double)));
+    if (!h->d_counts) FC_CK(dev_malloc((void **)&h->d_counts, h->proj_elems * sizeof(float)));
+    if (!h->d_vol) FC_CK(dev_malloc((void **)&h->d_vol, h->vol_elems * sizeof(double)));
+    if (!h->d_hu) FC_CK(dev_malloc((void **)&h->d_hu, h->vol_elems * sizeof(float)));
+    if (!h->d_part) FC_CK(dev_malloc((void **)&h->d_part, 2 * 256 * sizeof(double)));
     return FC_OK;
 }
 
@@ -321,11 +348,84 @@ int gauss_taps(double sigma, float *taps, int *radius)
     return FC_OK;
 }
 
+// Detector rows whose rays can meet the voxel slab: a ray through row v lies
+// at height z = v * s along the central direction, s = distance from the
+// source / SDD; inside the voxel box s >= (SAD - r_max) / SDD.  It can meet the
+// slab |z| <= nz dz / 2 only if |v| (SAD - r_max) / SDD <= nz dz / 2.  Two rows
+// of margin.
+static void hit_band(const fc_geometry &G, int *lo, int *hi)
+{
+    const double rmax = sqrt(0.25 * G.nx * G.dx_cm * G.nx * G.dx_cm + 0.25 * G.ny * G.dy_cm * G.ny * G.dy_cm);
+    const double vmax = 0.5 * G.nz * G.dz_cm * G.sdd_cm / (G.sad_cm - rmax) / G.dv_cm;
+    const double cv = 0.5 * (G.n_v - 1);
+    *lo = (int)floor(cv - vmax) - 2;
+    *hi = (int)ceil(cv + vmax) + 2;
+}
+
+// Fraction of the rays of the traced band that meet the voxel box, from a
+// sample (8 projections, every 4th column, up to 64 rows) intersected with
+// the box in binary64.  It only chooses how the projector assigns rays to
+// threads (compacted when most band rays miss); results do not depend on it.
+static double band_hit_fraction(const fc_geometry &G)
+{
+    int lo, hi;
+    hit_band(G, &lo, &hi);
+    lo = lo < 0 ? 0 : lo;
+    hi = hi > G.n_v - 1 ? G.n_v - 1 : hi;
+    if (lo > hi) return 1.0;
+    const double box[3] = {0.5 * G.nx * G.dx_cm, 0.5 * G.ny * G.dy_cm, 0.5 * G.nz * G.dz_cm};
+    const int rstep = (hi - lo + 1 + 63) / 64;
+    long long n = 0, hits = 0;
+    for (int ka = 0; ka < 8; ++ka) {
+        const double th = G.theta0_rad + G.arc_rad * (double)ka / 8.0;
+        const double c = cos(th), sn = sin(th);
+        const double S[3] = {G.sad_cm * c, G.sad_cm * sn, 0.0};
+        for (int iv = lo; iv <= hi; iv += rstep)
+            for (int iu = 0; iu < G.n_u; iu += 4) {
+                const double u = (iu - 0.5 * (G.n_u - 1)) * G.du_cm, v = (iv - 0.5 * (G.n_v - 1)) * G.dv_cm;
+                const double P[3] = {-(G.sdd_cm - G.sad_cm) * c - u * sn, -(G.sdd_cm - G.sad_cm) * sn + u * c, v};
+                double t0 = 0.0, t1 = 1.0;
+                for (int a = 0; a < 3; ++a) {
+                    const double d = P[a] - S[a];
+                    if (d == 0.0) {
+                        if (S[a] < -box[a] || S[a] >= box[a]) t1 = -1.0;
+                        continue;
+                    }
+                    const double ta = (-box[a] - S[a]) / d, tb = (box[a] - S[a]) / d;
+                    t0 = fmax(t0, fmin(ta, tb));
+                    t1 = fmin(t1, fmax(ta, tb));
+                }
+                ++n;
+                hits += t1 > t0;
+            }
+    }
+    return n ? (double)hits / (double)n : 1.0;
+}
+
 }  // namespace
 
 extern "C" {
 
 const char *fc_last_error(void) { return g_err.c_str(); }
+
+int fc_inject_fault(int kind, int64_t arg)
+{
+    switch (kind) {
+    case FC_FAULT_NONE:
+        g_alloc_fail_in.store(-1);
+        g_blur_timeout.store(0);
+        return FC_OK;
+    case FC_FAULT_ALLOC:
+        if (arg < 0) return fail(FC_EINVAL, "fc_inject_fault: allocation count %lld < 0", (long long)arg);
+        g_alloc_fail_in.store(arg);
+        return FC_OK;
+    case FC_FAULT_BLUR_TIMEOUT:
+        g_blur_timeout.store(1);
+        return FC_OK;
+    default:
+        return fail(FC_EINVAL, "fc_inject_fault: unknown kind %d", kind);
+    }
+}
 
 int fc_create(fc_handle **out, int device)
 {
@@ -338,7 +438,7 @@ int fc_create(fc_handle **out, int device)
     if (!dgd.ok) return fail(FC_ECUDA, "fc_create: cannot select device %d", device);
     fc_handle *h = new fc_handle();
     h->device = device;
-    if (cudaMalloc((void **)&h->d_flag, sizeof(unsigned int)) != cudaSuccess) {
+    if (dev_malloc((void **)&h->d_flag, sizeof(unsigned int)) != cudaSuccess) {
         delete h;
         return fail(FC_ENOMEM, "fc_create: allocation failed");
     }
@@ -433,8 +533,9 @@ int fc_set_geometry(fc_handle *h, const fc_geometry *g)
         const double th = g->theta0_rad + g->arc_rad * (double)k / (double)g->n_angles;
         trig[k] = make_float2((float)cos(th), (float)sin(th));
     }
-    FC_CK(cudaMalloc((void **)&h->d_trig, sizeof(float2) * g->n_angles));
+    FC_CK(dev_malloc((void **)&h->d_trig, sizeof(float2) * g->n_angles));
     FC_CK(cudaMemcpy(h->d_trig, trig.data(), sizeof(float2) * g->n_angles, cudaMemcpyHostToDevice));
+    h->band_hit_frac = band_hit_fraction(*g);
     h->has_geom = true;
     return FC_OK;
 }
@@ -448,9 +549,9 @@ int fc_set_phantom(fc_handle *h, const uint8_t *labels, int n_mat, int where, vo
     if (where != FC_HOST && where != FC_DEVICE) return fail(FC_EINVAL, "fc_set_phantom: bad where");
     DeviceGuard dgd(h->device);
     cudaStream_t s = (cudaStream_t)stream;
-    if (!h->d_labels) FC_CK(cudaMalloc((void **)&h->d_labels, h->vol_elems));
+    if (!h->d_labels) FC_CK(dev_malloc((void **)&h->d_labels, h->vol_elems));
     if (!h->d_bricks)
-        FC_CK(cudaMalloc((void **)&h->d_bricks,
+        FC_CK(dev_malloc((void **)&h->d_bricks,
                          (size_t)((h->g.nx + fc::kBrick - 1) / fc::kBrick) *
                              ((h->g.ny + fc::kBrick - 1) / fc::kBrick) *
                              ((h->g.nz + fc::kBrickZ - 1) / fc::kBrickZ)));
@@ -548,19 +649,8 @@ static int fill_proj_params(fc_handle *h, int a0, int na, fc::ProjParams *p)
     p->bricks = h->d_bricks;
     p->angle0 = a0;
     p->n_angles_launch = na;
-    {
-        // A ray through row v lies at height z = v * s along the central
-        // direction, s = distance from the source / SDD; inside the voxel box
-        // s >= (SAD - r_max) / SDD.  It can meet the slab |z| <= nz dz / 2 only
-        // if |v| (SAD - r_max) / SDD <= nz dz / 2.  Two rows of margin.
-        const fc_geometry &G = h->g;
-        const double rmax = sqrt(0.25 * G.nx * G.dx_cm * G.nx * G.dx_cm +
-                                 0.25 * G.ny * G.dy_cm * G.ny * G.dy_cm);
-        const double vmax = 0.5 * G.nz * G.dz_cm * G.sdd_cm / (G.sad_cm - rmax) / G.dv_cm;
-        const double cv = 0.5 * (G.n_v - 1);
-        p->v_hit_lo = (int)floor(cv - vmax) - 2;
-        p->v_hit_hi = (int)ceil(cv + vmax) + 2;
-    }
+    hit_band(h->g, &p->v_hit_lo, &p->v_hit_hi);
+    p->compact = h->band_hit_frac < 0.6;
     p->n_mat = h->n_mat;
     p->n_e = h->n_e;
     for (int e = 0; e < h->n_e; ++e) {
@@ -622,6 +712,7 @@ static int run_blur(fc_handle *h, const float *in, float *out, size_t off, int n
         }
         return FC_OK;
     }
+    b.inject_timeout = g_blur_timeout.exchange(0);
     {
         Trace t(h, FC_K_BLUR_ROWS, fc::blur_tc_rows_launches(b, one_lo, one_hi), s);
         FC_CK(fc::launch_blur_tc_rows(b, in, h->d_tp + off, h->d_ts + off, h->d_hankel,
@@ -647,10 +738,10 @@ static int run_groups(fc_handle *h, int a0, int na, cudaStream_t s)
     const size_t plane_all = h->proj_elems;
     if (!h->d_grp || h->grp_alloc < h->n_groups) {
         dfree(h->d_grp);
-        FC_CK(cudaMalloc((void **)&h->d_grp, (size_t)h->n_groups * plane_all * sizeof(float)));
+        FC_CK(dev_malloc((void **)&h->d_grp, (size_t)h->n_groups * plane_all * sizeof(float)));
         h->grp_alloc = h->n_groups;
     }
-    if (!h->d_prof) FC_CK(cudaMalloc((void **)&h->d_prof, (size_t)h->g.n_u * sizeof(float)));
+    if (!h->d_prof) FC_CK(dev_malloc((void **)&h->d_prof, (size_t)h->g.n_u * sizeof(float)));
     p.n_groups = h->n_groups;
     for (int i = 0, e = 0; i < h->n_groups; ++i) {
         p.grp_end[i] = h->grp_end[i];
@@ -723,7 +814,7 @@ int fc_deconvolve_rl(fc_handle *h, int angle_begin, int angle_count, double psf_
     }
     p.floor_ = 1e-12f;
     if (!h->d_rlnorm)
-        FC_CK(cudaMalloc((void **)&h->d_rlnorm, (size_t)(h->g.n_u + h->g.n_v) * sizeof(float)));
+        FC_CK(dev_malloc((void **)&h->d_rlnorm, (size_t)(h->g.n_u + h->g.n_v) * sizeof(float)));
     const size_t plane = (size_t)h->g.n_v * h->g.n_u;
     const size_t off = (size_t)angle_begin * plane;
     const size_t bytes = (size_t)angle_count * plane * sizeof(float);
@@ -790,7 +881,7 @@ int fc_detector_mtf(fc_handle *h, double slit_width_mm, double slit_angle_deg, i
     DeviceGuard dgd(h->device);
     double *work = nullptr;
     const size_t nwork = 2 * (size_t)p.n * p.n + nb + 2 * (size_t)nf;
-    FC_CK(cudaMalloc((void **)&work, nwork * sizeof(double)));
+    FC_CK(dev_malloc((void **)&work, nwork * sizeof(double)));
     double *fr = work + 2 * (size_t)p.n * p.n + nb, *mt = fr + nf;
     cudaError_t e = fc::launch_mtf(p, work, fr, mt, 0);
     if (e == cudaSuccess) e = cudaMemcpy(freq_per_mm, fr, nf * sizeof(double), cudaMemcpyDeviceToHost);
@@ -1033,7 +1124,7 @@ int fc_dose_estimate(fc_handle *h, int angle_begin, int angle_count, const doubl
     cudaStream_t s = (cudaStream_t)stream;
     const size_t n_part = (size_t)fc::kDoseBlocks * fc::kMaxBins, n_out = fc::kMaxBins + 1;
     if (!h->d_dose)
-        FC_CK(cudaMalloc(&h->d_dose, (n_part + n_out + fc::kMaxMat) * sizeof(double)));
+        FC_CK(dev_malloc((void **)&h->d_dose, (n_part + n_out + fc::kMaxMat) * sizeof(double)));
     double *part = h->d_dose, *res = h->d_dose + n_part;
     auto *count = reinterpret_cast<unsigned long long *>(res + n_out);
     {
@@ -1209,20 +1300,25 @@ static int sur_upload(fc_handle *h, const float *packed)
 
 static int sur_alloc(fc_handle *h)
 {
-    if (h->d_P) return FC_OK;
     const int H = fc::kMlpHidden;
-    FC_CK(cudaMalloc((void **)&h->d_P, sizeof(float) * fc::kMlpPacked));
-    FC_CK(cudaMalloc((void **)&h->d_m1, sizeof(float) * fc::kMlpParams));
-    FC_CK(cudaMalloc((void **)&h->d_m2, sizeof(float) * fc::kMlpParams));
-    FC_CK(cudaMalloc((void **)&h->d_grad, sizeof(float) * fc::kMlpParams));
-    FC_CK(cudaMalloc((void **)&h->d_W1b, 2 * H * 16));
-    FC_CK(cudaMalloc((void **)&h->d_W2b, 2 * H * H));
-    FC_CK(cudaMalloc((void **)&h->d_W3b, 2 * H * H));
-    FC_CK(cudaMalloc((void **)&h->d_W2Tb, 2 * H * H));
-    FC_CK(cudaMalloc((void **)&h->d_W3Tb, 2 * H * H));
-    FC_CK(cudaMalloc((void **)&h->d_err, sizeof(int)));
-    FC_CK(cudaMalloc((void **)&h->d_cnt, sizeof(unsigned int) * 16));
-    FC_CK(cudaMemset(h->d_err, 0, sizeof(int)));
+    if (!h->d_P) FC_CK(dev_malloc((void **)&h->d_P, sizeof(float) * fc::kMlpPacked));
+    if (!h->d_m1) FC_CK(dev_malloc((void **)&h->d_m1, sizeof(float) * fc::kMlpParams));
+    if (!h->d_m2) FC_CK(dev_malloc((void **)&h->d_m2, sizeof(float) * fc::kMlpParams));
+    if (!h->d_grad) FC_CK(dev_malloc((void **)&h->d_grad, sizeof(float) * fc::kMlpParams));
+    if (!h->d_W1b) FC_CK(dev_malloc((void **)&h->d_W1b, 2 * H * 16));
+    if (!h->d_W2b) FC_CK(dev_malloc((void **)&h->d_W2b, 2 * H * H));
+    if (!h->d_W3b) FC_CK(dev_malloc((void **)&h->d_W3b, 2 * H * H));
+    if (!h->d_W2Tb) FC_CK(dev_malloc((void **)&h->d_W2Tb, 2 * H * H));
+    if (!h->d_W3Tb) FC_CK(dev_malloc((void **)&h->d_W3Tb, 2 * H * H));
+    if (!h->d_cnt) FC_CK(dev_malloc((void **)&h->d_cnt, sizeof(unsigned int) * 16));
+    if (!h->d_err) {
+        FC_CK(dev_malloc((void **)&h->d_err, sizeof(int)));
+        const cudaError_t e = cudaMemset(h->d_err, 0, sizeof(int));
+        if (e != cudaSuccess) {
+            dfree(h->d_err);
+            FC_CK(e);
+        }
+    }
     return FC_OK;
 }
 
@@ -1298,7 +1394,7 @@ static int sur_work(fc_handle *h, int B)
     const size_t bytes = 2 * (16 * nb + 6 * (size_t)H * nb + 16 * nb) +
                          4 * (4 * (size_t)n_chunks * H * H + 4 * (size_t)n_chunks * H + n_chunks) +
                          16 * 256;  // each of the 11 pieces is rounded up to 256 bytes
-    FC_CK(cudaMalloc(&h->work_mem, bytes));
+    FC_CK(dev_malloc((void **)&h->work_mem, bytes));
     FC_CK(cudaMemset(h->work_mem, 0, bytes));
     char *q = (char *)h->work_mem;
     auto take = [&](size_t b) { char *r = q; q += (b + 255) / 256 * 256; return r; };
@@ -1380,9 +1476,10 @@ int fc_surrogate_train(fc_handle *h, const float *L, const float *lnT, int64_t n
     if (rc) return rc;
     rc = sur_work(h, batch);
     if (rc) return rc;
-    if (h->loss_cap < steps) {
+    if (h->loss_cap < steps || !h->d_loss) {
         dfree(h->d_loss);
-        FC_CK(cudaMalloc((void **)&h->d_loss, sizeof(float) * (steps > 0 ? steps : 1)));
+        h->loss_cap = 0;
+        FC_CK(dev_malloc((void **)&h->d_loss, sizeof(float) * (steps > 0 ? steps : 1)));
         h->loss_cap = steps;
     }
     if (steps > 0) FC_CK(cudaMemsetAsync(h->d_loss, 0, sizeof(float) * steps, s));
@@ -1419,9 +1516,10 @@ int fc_surrogate_grad(fc_handle *h, const float *L, const float *lnT, int64_t n,
     cudaStream_t s = (cudaStream_t)stream;
     rc = sur_work(h, (int)n);
     if (rc) return rc;
-    if (h->loss_cap < 1) {
+    if (h->loss_cap < 1 || !h->d_loss) {
         dfree(h->d_loss);
-        FC_CK(cudaMalloc((void **)&h->d_loss, sizeof(float)));
+        h->loss_cap = 0;
+        FC_CK(dev_malloc((void **)&h->d_loss, sizeof(float)));
         h->loss_cap = 1;
     }
     FC_CK(cudaMemsetAsync(h->d_loss, 0, sizeof(float), s));
@@ -1506,11 +1604,12 @@ int fc_surrogate_project(fc_handle *h, int angle_begin, int angle_count, float *
     cudaStream_t s = (cudaStream_t)stream;
     const size_t n = (size_t)angle_count * h->g.n_v * h->g.n_u;
     if (n == 0) return FC_OK;
-    if (n > h->sL_rays) {
+    if (n > h->sL_rays || !h->d_sL || !h->d_slnT) {
         dfree(h->d_sL);
         dfree(h->d_slnT);
-        FC_CK(cudaMalloc((void **)&h->d_sL, n * h->n_mat * sizeof(float)));
-        FC_CK(cudaMalloc((void **)&h->d_slnT, n * sizeof(float)));
+        h->sL_rays = 0;
+        FC_CK(dev_malloc((void **)&h->d_sL, n * h->n_mat * sizeof(float)));
+        FC_CK(dev_malloc((void **)&h->d_slnT, n * sizeof(float)));
         h->sL_rays = n;
     }
     {
@@ -1565,13 +1664,13 @@ int fc_cnr_grad(fc_handle *h, const double *logits, const double *D, const doubl
     rc = ensure_recon_buffers(h, s);
     if (rc) return rc;
     const size_t np = h->proj_elems, nv = h->vol_elems;
-    if (!h->d_I) FC_CK(cudaMalloc((void **)&h->d_I, np * sizeof(float)));
-    if (!h->d_gI) FC_CK(cudaMalloc((void **)&h->d_gI, np * sizeof(float)));
-    if (!h->d_gT) FC_CK(cudaMalloc((void **)&h->d_gT, np * sizeof(float)));
-    if (!h->d_gtmp) FC_CK(cudaMalloc((void **)&h->d_gtmp, np * sizeof(float)));
-    if (!h->d_gf) FC_CK(cudaMalloc((void **)&h->d_gf, h->filt_elems * sizeof(float)));
-    if (!h->d_gmu) FC_CK(cudaMalloc((void **)&h->d_gmu, nv * sizeof(float)));
-    if (!h->d_gwd) FC_CK(cudaMalloc((void **)&h->d_gwd, (fc::kMaxBins + 1) * sizeof(double)));
+    if (!h->d_I) FC_CK(dev_malloc((void **)&h->d_I, np * sizeof(float)));
+    if (!h->d_gI) FC_CK(dev_malloc((void **)&h->d_gI, np * sizeof(float)));
+    if (!h->d_gT) FC_CK(dev_malloc((void **)&h->d_gT, np * sizeof(float)));
+    if (!h->d_gtmp) FC_CK(dev_malloc((void **)&h->d_gtmp, np * sizeof(float)));
+    if (!h->d_gf) FC_CK(dev_malloc((void **)&h->d_gf, h->filt_elems * sizeof(float)));
+    if (!h->d_gmu) FC_CK(dev_malloc((void **)&h->d_gmu, nv * sizeof(float)));
+    if (!h->d_gwd) FC_CK(dev_malloc((void **)&h->d_gwd, (fc::kMaxBins + 1) * sizeof(double)));
     // spectrum: w = softmax(logits), c = w D, wd = c / sum c
     const int ne = h->n_e;
     std::vector<double> w(ne), c(ne);
@@ -1644,7 +1743,7 @@ int fc_cnr_grad(fc_handle *h, const double *logits, const double *D, const doubl
                                  h->bp_request);
         FC_CK(fc::launch_backproject(pf, h->d_filt, h->d_vol, bpv, s));
     }
-    if (!h->d_cnr_work) FC_CK(cudaMalloc((void **)&h->d_cnr_work, fc::cnr_work_doubles() * sizeof(double)));
+    if (!h->d_cnr_work) FC_CK(dev_malloc((void **)&h->d_cnr_work, fc::cnr_work_doubles() * sizeof(double)));
     FC_CK(fc::launch_cnr(cp, h->d_vol, h->d_gmu, h->d_gwd + fc::kMaxBins, h->d_cnr_work, s));
     const bool grads = g_logits || g_D || g_rho;
     if (grads) {

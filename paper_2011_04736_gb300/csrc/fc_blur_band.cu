@@ -19,8 +19,7 @@
 // C.  One CTA per (projection, 128-column tile) stages the band rows of D
 // (T - 1, exact for T in [1/2, 1] and within 2^-25 below) with the clamped
 // halo, forms both row passes in shared memory, and writes every output row
-// of its tile: the column sums for rows near the band (each thread keeps its
-// column's band values in registers), C elsewhere.  Binary32 throughout;
+// of its tile: the column sums for rows near the band, C elsewhere.  Binary32 throughout;
 // the whole image is written once and only the band rows of T are read, so
 // the kernel is bound by the output stores.
 #include <math.h>
@@ -31,9 +30,15 @@ namespace fc {
 
 namespace {
 constexpr int kTW = 128;          // output columns per CTA
-constexpr int kThreads = 256;     // two threads per column in the column phase
+constexpr int kThreads = 256;
+constexpr int kRun = 8;           // outputs per thread and task (register tile)
 }  // namespace
 
+// Work split: row passes as tasks of kRun adjacent outputs of one band row
+// (a sliding window of D in registers: one shared load per tap for kRun
+// FMAs); column sums as tasks of kRun adjacent output rows x 2 columns (per
+// band row one pair of A values and one new tap per kernel, 4 kRun FMAs);
+// the constant rows as float4 stores.
 template <int HB>
 __global__ void __launch_bounds__(kThreads)
 k_blur_band(const __grid_constant__ BlurParams bp, const float *__restrict__ T, float *__restrict__ out,
@@ -41,13 +46,13 @@ k_blur_band(const __grid_constant__ BlurParams bp, const float *__restrict__ T, 
 {
     extern __shared__ float sm[];
     const int R = bp.rp > bp.rs ? bp.rp : bp.rs;
-    const int W = kTW + 2 * R;                     // staged columns per band row
-    const int off = R + HB;                        // padded-tap offset
+    const int W = kTW + 2 * R + kRun;              // staged columns per band row
+    const int off = R + HB + kRun;                 // padded-tap offset
     const int ntp = 2 * off + 1;
     float *D = sm;                                 // [hb][W]
-    float *Ap = D + hb * W;                        // [hb][kTW]
-    float *As = Ap + hb * kTW;                     // [hb][kTW]
-    float *Gp = As + hb * kTW;                     // [ntp]: g_psf[q - off], zero beyond rp
+    float *Ap = D + hb * W;                        // [HB][kTW], rows hb.. zero
+    float *As = Ap + HB * kTW;                     // [HB][kTW], rows hb.. zero
+    float *Gp = As + HB * kTW;                     // [ntp]: g_psf[q - off], zero beyond rp
     float *Gs = Gp + ntp;                          // [ntp]
     const int n_u = bp.n_u, n_v = bp.n_v;
     const int x0 = blockIdx.x * kTW;
@@ -64,42 +69,110 @@ k_blur_band(const __grid_constant__ BlurParams bp, const float *__restrict__ T, 
         const int col = min(max(x0 - R + c, 0), n_u - 1);
         D[e] = T[img + (size_t)(b0 + j) * n_u + col] - 1.0f;
     }
-    __syncthreads();
-    // row passes of the band rows: A_b[j][x] = sum_k g_b[k] D[j][x + R + k]
-    for (int e = tid; e < hb * kTW; e += kThreads) {
-        const int j = e / kTW, x = e - j * kTW;
-        const float *d = D + j * W + x + R;
-        float ap = 0.0f, as = 0.0f;
-        for (int k = -bp.rp; k <= bp.rp; ++k) ap = fmaf(bp.gp[k + bp.rp], d[k], ap);
-        for (int k = -bp.rs; k <= bp.rs; ++k) as = fmaf(bp.gs[k + bp.rs], d[k], as);
-        Ap[e] = ap;
-        As[e] = as;
+    for (int e = hb * kTW + tid; e < HB * kTW; e += kThreads) {
+        Ap[e] = 0.0f;
+        As[e] = 0.0f;
     }
     __syncthreads();
-    const int x = tid % kTW, half = tid / kTW;
-    if (x0 + x >= n_u) return;                     // no barrier follows
-    float ap[HB], as[HB];
+    // row passes: A_b[j][x + o] = sum_k g_b[k] D[j][x + o + R + k], o < kRun
+    for (int task = tid; task < hb * (kTW / kRun); task += kThreads) {
+        const int j = task / (kTW / kRun), x = (task - j * (kTW / kRun)) * kRun;
 #pragma unroll
-    for (int j = 0; j < HB; ++j) {
-        ap[j] = j < hb ? Ap[j * kTW + x] : 0.0f;
-        as[j] = j < hb ? As[j * kTW + x] : 0.0f;
-    }
-    const int c_lo = max(b0 - R, 0), c_hi = min(b0 + hb + R, n_v);
-    float *o = out + img + x0 + x;
-    for (int c = half; c < n_v; c += 2) {
-        float v = cst;
-        if (c >= c_lo && c < c_hi) {
-            // band row j meets output row c through tap b0 + j - c
-            const float *gp = Gp + off + b0 - c, *gs = Gs + off + b0 - c;
-            float sp = 0.0f, ss = 0.0f;
+        for (int b = 0; b < 2; ++b) {
+            const int r = b ? bp.rs : bp.rp;
+            const float *g = b ? bp.gs : bp.gp;
+            const float *d = D + j * W + x + R - r;    // window start for tap k = -r
+            float acc[kRun], win[kRun];
 #pragma unroll
-            for (int j = 0; j < HB; ++j) {
-                sp = fmaf(gp[j], ap[j], sp);
-                ss = fmaf(gs[j], as[j], ss);
+            for (int o = 0; o < kRun; ++o) {
+                acc[o] = 0.0f;
+                win[o] = d[o];
             }
-            v = fmaf(bp.n0, fmaf(bp.spr, ss, sp), cst);
+            int k = 0;
+            for (; k + kRun <= 2 * r + 1; k += kRun) {
+#pragma unroll
+                for (int q = 0; q < kRun; ++q) {
+                    const float gk = g[k + q];
+#pragma unroll
+                    for (int o = 0; o < kRun; ++o) acc[o] = fmaf(gk, win[(o + q) % kRun], acc[o]);
+                    win[q] = d[k + q + kRun];
+                }
+            }
+            for (int q = 0; k + q < 2 * r + 1; ++q) {
+                const float gk = g[k + q];
+#pragma unroll
+                for (int o = 0; o < kRun; ++o) acc[o] = fmaf(gk, d[k + q + o], acc[o]);
+            }
+            float *A = (b ? As : Ap) + j * kTW + x;
+#pragma unroll
+            for (int o = 0; o < kRun; ++o) A[o] = acc[o];
         }
-        o[(size_t)c * n_u] = v;
+    }
+    __syncthreads();
+    // output rows near the band: c in [c_lo, c_hi); the rest hold cst
+    const int c_lo = max(b0 - R, 0), c_hi = min(b0 + hb + R, n_v);
+    const int n_runs = (c_hi - c_lo + kRun - 1) / kRun;
+    for (int task = tid; task < n_runs * (kTW / 2); task += kThreads) {
+        const int run = task / (kTW / 2), x = 2 * (task - run * (kTW / 2));
+        const int c0 = c_lo + run * kRun;
+        // band row j meets output row c0 + o through tap b0 + j - c0 - o,
+        // padded index off + b0 + j - c0 - o = gp[j + kRun - 1 - o] below
+        const float *gp = Gp + off + b0 - c0 - (kRun - 1), *gs = Gs + off + b0 - c0 - (kRun - 1);
+        float2 accp[kRun], accs[kRun];
+#pragma unroll
+        for (int o = 0; o < kRun; ++o) accp[o] = accs[o] = make_float2(0.0f, 0.0f);
+#pragma unroll 1
+        for (int jb = 0; jb < HB; jb += kRun) {     // rows hb.. of A are zero
+            // taps of this block of kRun band rows: gp[jb + i], i < 2 kRun - 1
+            float tp[2 * kRun - 1], ts[2 * kRun - 1];
+#pragma unroll
+            for (int i = 0; i < 2 * kRun - 1; ++i) {
+                tp[i] = gp[jb + i];
+                ts[i] = gs[jb + i];
+            }
+#pragma unroll
+            for (int q = 0; q < kRun; ++q) {
+                const float2 ap = *reinterpret_cast<const float2 *>(Ap + (jb + q) * kTW + x);
+                const float2 as = *reinterpret_cast<const float2 *>(As + (jb + q) * kTW + x);
+#pragma unroll
+                for (int o = 0; o < kRun; ++o) {
+                    const float a = tp[q + kRun - 1 - o], b = ts[q + kRun - 1 - o];
+                    accp[o].x = fmaf(a, ap.x, accp[o].x);
+                    accp[o].y = fmaf(a, ap.y, accp[o].y);
+                    accs[o].x = fmaf(b, as.x, accs[o].x);
+                    accs[o].y = fmaf(b, as.y, accs[o].y);
+                }
+            }
+        }
+#pragma unroll
+        for (int o = 0; o < kRun; ++o) {
+            const int c = c0 + o;
+            if (c >= c_hi) break;
+            const float vx = fmaf(bp.n0, fmaf(bp.spr, accs[o].x, accp[o].x), cst);
+            const float vy = fmaf(bp.n0, fmaf(bp.spr, accs[o].y, accp[o].y), cst);
+            float *dst = out + img + (size_t)c * n_u + x0 + x;
+            if (x0 + x + 1 < n_u && (n_u & 1) == 0) {
+                *reinterpret_cast<float2 *>(dst) = make_float2(vx, vy);
+            } else {
+                if (x0 + x < n_u) dst[0] = vx;
+                if (x0 + x + 1 < n_u) dst[1] = vy;
+            }
+        }
+    }
+    // constant rows [0, c_lo) and [c_hi, n_v) of the tile
+    const int n_const = c_lo + (n_v - c_hi);
+    const bool vec = (n_u & 3) == 0;
+    for (int e = tid; e < n_const * (kTW / 4); e += kThreads) {
+        const int rr = e / (kTW / 4), x = 4 * (e - rr * (kTW / 4));
+        const int c = rr < c_lo ? rr : c_hi + (rr - c_lo);
+        float *dst = out + img + (size_t)c * n_u + x0 + x;
+        if (vec && x0 + x + 4 <= n_u) {
+            *reinterpret_cast<float4 *>(dst) = make_float4(cst, cst, cst, cst);
+        } else {
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                if (x0 + x + q < n_u) dst[q] = cst;
+        }
     }
 }
 
@@ -107,8 +180,8 @@ namespace {
 size_t band_smem(const BlurParams &bp, int hb, int HB)
 {
     const int R = bp.rp > bp.rs ? bp.rp : bp.rs;
-    return ((size_t)hb * (kTW + 2 * R) + 2 * (size_t)hb * kTW + 2 * (size_t)(2 * (R + HB) + 1)) *
-           sizeof(float);
+    return ((size_t)hb * (kTW + 2 * R + kRun) + 2 * (size_t)HB * kTW +
+            2 * (size_t)(2 * (R + HB + kRun) + 1)) * sizeof(float);
 }
 constexpr size_t kBandSmemLimit = 200 * 1024;
 }  // namespace

@@ -105,9 +105,10 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *bar)
 }
 
 // Bounded wait for phase `parity` that also gives up once `abort_flag` is set.
-__device__ __forceinline__ bool wait_bar(uint64_t *bar, uint32_t parity, volatile int *abort_flag)
+__device__ __forceinline__ bool wait_bar(uint64_t *bar, uint32_t parity, volatile int *abort_flag,
+                                         uint32_t polls = kPolls)
 {
-    for (uint32_t i = 0; i < kPolls; ++i) {
+    for (uint32_t i = 0; i < polls; ++i) {
         if (tc::mbar_try_wait(bar, parity)) return true;
         if ((i & 63u) == 63u && *abort_flag) return false;
     }
@@ -133,9 +134,10 @@ __device__ __forceinline__ void cp_async_wait_all()
 }
 
 // Lane 0 waits, the warp follows (keeps .sync.aligned TMEM accesses converged).
-__device__ __forceinline__ bool warp_wait(uint64_t *bar, uint32_t parity, volatile int *abort_flag)
+__device__ __forceinline__ bool warp_wait(uint64_t *bar, uint32_t parity, volatile int *abort_flag,
+                                          uint32_t polls = kPolls)
 {
-    int ok = (threadIdx.x & 31) == 0 ? (int)wait_bar(bar, parity, abort_flag) : 0;
+    int ok = (threadIdx.x & 31) == 0 ? (int)wait_bar(bar, parity, abort_flag, polls) : 0;
     return __shfl_sync(0xffffffffu, ok, 0) != 0;
 }
 
@@ -358,7 +360,7 @@ k_blur_rows_tc(const __grid_constant__ TcBlurParams p, int n_stage)
             if (t >= total) break;
             const int buf = (int)(j & 1);
             const uint32_t bph = (uint32_t)((j >> 1) & 1);
-            if (!warp_wait(&accf[buf], bph, abort_flag)) {
+            if (!warp_wait(&accf[buf], bph, abort_flag, p.epi_polls)) {
                 *abort_flag = 1;
                 break;
             }
@@ -603,7 +605,7 @@ k_blur_cols_tc(const __grid_constant__ TcBlurParams p, int n_stage)
             const uint32_t bph = (uint32_t)((j >> 1) & 1);
             // acc_full follows full[st] through the MMA commit; waiting on
             // full[st] too makes the producers' tp tile visible here directly
-            if (!warp_wait(&accf[buf], bph, abort_flag) ||
+            if (!warp_wait(&accf[buf], bph, abort_flag, p.epi_polls) ||
                 !warp_wait(&full[st], (uint32_t)((j / n_stage) & 1), abort_flag)) {
                 *abort_flag = 1;
                 break;
@@ -708,6 +710,9 @@ static TcBlurParams tc_params(const BlurParams &bp, const uint16_t *hankel, unsi
     p.tp_const = 0.0f;
     p.m_off = 0;
     p.m_cnt = (bp.n_v + 127) / 128;
+    // an injected timeout (testing) makes the epilogue give up its first
+    // accumulator wait at once, which exercises the abort path
+    p.epi_polls = bp.inject_timeout ? 0u : kPolls;
     return p;
 }
 

@@ -349,9 +349,11 @@ __global__ void __launch_bounds__(256, 8) k_backproject_dense(const __grid_const
 // element rounded exactly as the scalar instruction would); floors come
 // from adding 2^23 with rounding toward -inf (exact for 0 <= v < 2^22).
 // Binary32 partial sums over kFold angles are folded into binary64 sums
-// kept in shared memory.  CLAMP_V: clamp the detector row coordinate into
-// the stored rows (needed only when the stored rows were cut at the
-// detector edge).
+// kept in shared memory.  CLAMP: clamp the detector coordinates into the
+// stored rows and columns (needed only when a voxel can project outside them:
+// rows cut at a detector edge, or a detector narrower than the volume's
+// shadow).  The reciprocal of U is the hardware approximation refined by one
+// Newton-Raphson step, r' = r (2 - U r), within an ulp or so of 1 / U.
 namespace {
 __device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
 // a - b, exactly as a binary32 subtraction rounds it (b * -1 is exact)
@@ -359,7 +361,7 @@ __device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b
 constexpr float kTwo23 = 8388608.0f;
 }  // namespace
 
-template <int NZ, bool CLAMP_V>
+template <int NZ, bool CLAMP>
 __global__ void __launch_bounds__(256)
 k_backproject_slab(const __grid_constant__ FdkParams p, const float *__restrict__ f,
                    double *__restrict__ vol)
@@ -393,8 +395,11 @@ k_backproject_slab(const __grid_constant__ FdkParams p, const float *__restrict_
             const float2 cs = p.trig[k];
             const float U = g.sad - (x * cs.x + y * cs.y);
             const float ru = y * cs.x - x * cs.y;
-            const float iU = __frcp_rn(U);
-            const float fu = fminf(fmaxf(fmaf(ru * iU, sdd_du, cu1), 0.0f), umax);
+            float iU;
+            asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(iU) : "f"(U));
+            iU = fmaf(iU, fmaf(-U, iU, 1.0f), iU);
+            float fu = fmaf(ru * iU, sdd_du, cu1);
+            if (CLAMP) fu = fminf(fmaxf(fu, 0.0f), umax);
             const float tu = __fadd_rd(fu, kTwo23);          // 2^23 + floor(fu)
             const float au = fu - (tu - kTwo23);
             const float2 w2 = f2((g.sad * iU) * (g.sad * iU));
@@ -411,7 +416,7 @@ k_backproject_slab(const __grid_constant__ FdkParams p, const float *__restrict_
             for (int i = 0; i < NA; ++i) {
                 const float2 zz = make_float2((float)i + zz_step.x, (float)i + zz_step.y);
                 float2 fv = __ffma2_rn(zz, dfv, fv0);
-                if (CLAMP_V) {
+                if (CLAMP) {
                     fv.x = fminf(fmaxf(fv.x, 0.0f), vmaxp);
                     fv.y = fminf(fmaxf(fv.y, 0.0f), vmaxp);
                 }
@@ -446,14 +451,19 @@ k_backproject_slab(const __grid_constant__ FdkParams p, const float *__restrict_
     for (int z = 0; z < NZ; ++z) vol[((size_t)z * g.ny + iy) * g.nx + ix] = accd[z][t] * p.scale;
 }
 
-// Whether fdk_row_range cut the reachable rows at a detector edge.
-static bool slab_rows_cut(const DevGeom &g)
+// Whether a voxel can project outside the stored filtered rows (fdk_row_range
+// cut them at a detector edge) or outside the detector columns with less
+// than two pixels to spare (|u| <= SDD r_max / (SAD - r_max) at the voxels).
+static bool slab_needs_clamp(const DevGeom &g)
 {
     const double hx = 0.5 * g.nx * (double)g.dx, hy = 0.5 * g.ny * (double)g.dy;
-    const double umin = (double)g.sad - sqrt(hx * hx + hy * hy);
+    const double rmax = sqrt(hx * hx + hy * hy);
+    const double umin = (double)g.sad - rmax;
     if (umin <= 0.0) return true;
     const double vmax = 0.5 * (g.nz - 1) * (double)g.dz * (double)g.sdd / umin / (double)g.dv;
-    return (int)floor((double)g.cv - vmax) - 2 < 0 || (int)ceil((double)g.cv + vmax) + 2 > g.n_v - 1;
+    const double uext = (double)g.sdd * rmax / umin / (double)g.du;
+    return (int)floor((double)g.cv - vmax) - 2 < 0 || (int)ceil((double)g.cv + vmax) + 2 > g.n_v - 1 ||
+           uext + 2.0 > (double)g.cu;
 }
 
 // Largest projected z pitch, in detector rows, over the voxels of the
@@ -493,7 +503,7 @@ cudaError_t launch_backproject(const FdkParams &p, const float *filt, double *vo
         // the stored rows [v_lo, v_hi] hold every row a voxel projects onto
         // (with two rows of margin) unless the range was cut at a detector
         // edge; only then can a row coordinate leave the stored rows
-        const bool clamp = slab_rows_cut(p.g);
+        const bool clamp = slab_needs_clamp(p.g);
 #define FC_BPS(Z)                                                              \
     case Z:                                                                    \
         if (clamp)                                                             \

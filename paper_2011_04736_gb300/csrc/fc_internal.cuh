@@ -39,6 +39,7 @@ struct ProjParams {
     int angle0;             // absolute index of the first angle of the launch
     int n_angles_launch;
     int v_hit_lo, v_hit_hi; // detector rows whose rays can meet the voxel slab
+    int compact;            // trace the band with its rays compacted (most miss the voxels)
     int n_mat, n_e;
     int n_groups;                   // energy-group output (k_project<kModeGroups>)
     int grp_end[FC_MAX_GROUPS];     // exclusive end bin of each group
@@ -98,6 +99,7 @@ struct DoseParams {
 struct BlurParams {
     int n_u, n_v;
     int rp, rs;             // tap radii of the PSF and scatter kernels
+    int inject_timeout;     // testing: tensor-core passes give up their first epilogue wait
     float n0, spr;
     float gp[kMaxTaps];     // PSF taps, index j + rp
     float gs[kMaxTaps];     // scatter taps, index j + rs
@@ -137,6 +139,7 @@ struct TcBlurParams {
     int tp_lo, tp_hi;   // columns pass: rows of tp outside [tp_lo, tp_hi) equal tp_const
     float tp_const;
     int m_off, m_cnt;   // columns pass: output rows [m_off + 128 i, +128), i < m_cnt, are computed
+    unsigned int epi_polls;   // bound of the epilogue's accumulator waits
 };
 
 constexpr size_t kBlurTcHankelMax = 2 * 2 * 64 * (15 + (128 + 2 * 256) / 8);  // bf16 elements

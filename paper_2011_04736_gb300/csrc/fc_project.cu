@@ -72,7 +72,9 @@ __device__ __forceinline__ bool band_ray(int t, int r0, int R, int n_u, int &iu,
 __device__ __forceinline__ int band_t() { return (int)blockIdx.x * kBandCta + (int)threadIdx.y * 32 + (int)threadIdx.x; }
 
 // Per-material path lengths L of pixel ray (iu, iv) of projection k; returns
-// whether the ray meets the voxel box.
+// whether the ray meets the voxel box.  TEST_ONLY: return after the box test
+// (L not computed).
+template <bool TEST_ONLY = false>
 __device__ __forceinline__ bool trace_ray(const ProjParams &p, int iu, int iv, int k,
                                           float (&L)[kMaxMat])
 {
@@ -121,6 +123,7 @@ __device__ __forceinline__ bool trace_ray(const ProjParams &p, int iu, int iv, i
             }
         }
         hit = hit && t_in < t_out;
+        if (TEST_ONLY) return hit;
         if (hit) {
             const float px = fmaf(t_in, dx, Ax), py = fmaf(t_in, dy, Ay), pz = fmaf(t_in, dz, Az);
             const int nx = g.nx, ny = g.ny, nz = g.nz, nxy = g.nx * g.ny;
@@ -245,6 +248,86 @@ __device__ __forceinline__ bool trace_ray(const ProjParams &p, int iu, int iv, i
     return hit;
 }
 
+// Energy integral of one ray from its path lengths (compensated sum over the
+// bins; T = 1 for a ray that misses the voxels).
+__device__ __forceinline__ float energy_T(const ProjParams &p, bool hit, const float (&L)[kMaxMat])
+{
+    float Tv = 1.0f;
+    if (hit) {
+        float sum = 0.0f, comp = 0.0f;
+        for (int e = 0; e < p.n_e; ++e) {
+            float a = 0.0f;
+#pragma unroll
+            for (int m = 0; m < kMaxMat; ++m) a = fmaf(p.mu2[e][m], L[m], a);
+            const float term = p.wd[e] * exp2f(-a);
+            const float y = term - comp;
+            const float t = sum + y;
+            comp = (t - sum) - y;
+            sum = t;
+        }
+        Tv = sum;
+    }
+    return Tv;
+}
+
+// The traced band with its rays compacted: in a thin slab most rays of the
+// band pass above or below the voxels (their T is 1), and the rays that do
+// meet them would leave most lanes of a warp idle through the walk.  Each
+// CTA takes kCompact consecutive band rays of one projection (the band
+// order above); phase 1 tests every one against the voxel box with the
+// walk's own set-up (the same binary32 operations, so the decision is the
+// walk's), stores T = 1 for the misses and appends the others, in order, to
+// a queue in shared memory (one aggregated append per warp); phase 2 hands
+// the queue out to the warps 32 rays at a time, so every lane walks a ray
+// that meets the voxels.  T of a ray does not depend on which thread traces
+// it.
+constexpr int kCompact = 2048;
+
+__global__ void __launch_bounds__(256)
+k_project_compact(const __grid_constant__ ProjParams p, float *__restrict__ T, int r0, int R)
+{
+    __shared__ int queue[kCompact];
+    __shared__ int q_len, q_head;
+    const DevGeom &g = p.g;
+    const int tid = threadIdx.y * 32 + threadIdx.x, lane = threadIdx.x;
+    const int kl = blockIdx.z;
+    const int k = p.angle0 + kl;
+    const int base = (int)blockIdx.x * kCompact;
+    if (tid == 0) {
+        q_len = 0;
+        q_head = 0;
+    }
+    __syncthreads();
+    for (int c = tid; c < kCompact; c += 256) {       // a warp takes 32 consecutive rays
+        int iu = 0, iv = 0;
+        const bool valid = band_ray(base + c, r0, R, g.n_u, iu, iv);
+        float L[kMaxMat];
+        const bool hit = valid && trace_ray<true>(p, iu, iv, k, L);
+        if (valid && !hit) T[((size_t)k * g.n_v + iv) * g.n_u + iu] = 1.0f;
+        const unsigned m = __ballot_sync(0xffffffffu, hit);
+        int pos = 0;
+        if (lane == 0 && m) pos = atomicAdd(&q_len, __popc(m));
+        pos = __shfl_sync(0xffffffffu, pos, 0);
+        if (hit) queue[pos + __popc(m & ((1u << lane) - 1u))] = base + c;
+    }
+    __syncthreads();
+    const int n = q_len;
+    for (;;) {
+        int chunk = 0;
+        if (lane == 0) chunk = atomicAdd(&q_head, 32);
+        chunk = __shfl_sync(0xffffffffu, chunk, 0);
+        if (chunk >= n) break;
+        const int i = chunk + lane;
+        if (i < n) {
+            int iu, iv;
+            band_ray(queue[i], r0, R, g.n_u, iu, iv);
+            float L[kMaxMat];
+            const bool hit = trace_ray<false>(p, iu, iv, k, L);
+            T[((size_t)k * g.n_v + iv) * g.n_u + iu] = energy_T(p, hit, L);
+        }
+    }
+}
+
 template <bool EMIT_L>
 __global__ void __launch_bounds__(256)
 k_project(const __grid_constant__ ProjParams p, float *__restrict__ T, float *__restrict__ Lout, int r0,
@@ -264,22 +347,7 @@ k_project(const __grid_constant__ ProjParams p, float *__restrict__ T, float *__
             if (m < p.n_mat) Lout[ray * p.n_mat + m] = L[m];
         return;
     }
-    float Tv = 1.0f;
-    if (hit) {
-        float sum = 0.0f, comp = 0.0f;
-        for (int e = 0; e < p.n_e; ++e) {
-            float a = 0.0f;
-#pragma unroll
-            for (int m = 0; m < kMaxMat; ++m) a = fmaf(p.mu2[e][m], L[m], a);
-            const float term = p.wd[e] * exp2f(-a);
-            const float y = term - comp;
-            const float t = sum + y;
-            comp = (t - sum) - y;
-            sum = t;
-        }
-        Tv = sum;
-    }
-    T[((size_t)k * g.n_v + iv) * g.n_u + iu] = Tv;
+    T[((size_t)k * g.n_v + iv) * g.n_u + iu] = energy_T(p, hit, L);
 }
 
 // Value planes of the rows outside the traced band: plane z starts at
@@ -393,7 +461,11 @@ cudaError_t launch_project(const ProjParams &p, float *T, float *L_out, cudaStre
     // reading them narrows the range).
     int r0, r1;
     project_band(p, r0, r1);
-    if (r1 > r0) {
+    if (r1 > r0 && p.compact) {
+        const long long rays = (long long)(r1 - r0) * p.g.n_u;
+        dim3 grid((unsigned)((rays + kCompact - 1) / kCompact), 1, p.n_angles_launch);
+        k_project_compact<<<grid, block, 0, s>>>(p, T, r0, r1 - r0);
+    } else if (r1 > r0) {
         dim3 grid(band_ctas(r1 - r0, p.g.n_u), 1, p.n_angles_launch);
         k_project<false><<<grid, block, 0, s>>>(p, T, nullptr, r0, r1 - r0);
     }

@@ -22,6 +22,7 @@ FC_HOST, FC_DEVICE = 0, 1
 FC_OUT_NONE, FC_OUT_PRIMARY, FC_OUT_INTENSITY, FC_OUT_COUNTS = 0, 1, 2, 3
 FC_NOISE_AFTER_BLUR, FC_NOISE_BEFORE_PSF = 0, 1
 FC_BP_AUTO, FC_BP_CHUNKED, FC_BP_CHUNKED_DENSE, FC_BP_SLAB = 0, 1, 2, 3
+FC_FAULT_NONE, FC_FAULT_ALLOC, FC_FAULT_BLUR_TIMEOUT = 0, 1, 2
 FC_BP_NAMES = {FC_BP_CHUNKED: "chunked", FC_BP_CHUNKED_DENSE: "chunked_dense", FC_BP_SLAB: "slab"}
 FC_MAX_MATERIALS, FC_MAX_BINS = 8, 256
 
@@ -34,7 +35,7 @@ ENTRY_POINTS = ("fc_create", "fc_destroy", "fc_last_error", "fc_set_geometry", "
                 "fc_energy_sum_lengths", "fc_cnr_grad", "fc_surrogate_project",
                 "fc_dose_estimate", "fc_fluence_for_dose", "fc_set_noise_order",
                 "fc_set_energy_groups", "fc_deconvolve_rl", "fc_detector_mtf",
-                "fc_set_backprojector", "fc_backprojector_in_use")
+                "fc_set_backprojector", "fc_backprojector_in_use", "fc_inject_fault")
 FC_STATIC_SCRATCH_FLOATS = 8 << 20
 FC_SURROGATE_PARAMS = 34305
 FC_SURROGATE_STATE = 34305 + 52 + 2 * 34305 + 1
@@ -125,6 +126,7 @@ def load():
         "fc_detector_mtf": (I, [P, ctypes.c_double, ctypes.c_double, I, P, P, I, P]),
         "fc_set_backprojector": (I, [P, I]),
         "fc_backprojector_in_use": (I, [P, ctypes.POINTER(I)]),
+        "fc_inject_fault": (I, [I, ctypes.c_int64]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -297,6 +299,10 @@ def fc_backprojector_in_use(h):
     v = ctypes.c_int(-1)
     _check(load().fc_backprojector_in_use(h, ctypes.byref(v)))
     return v.value
+
+
+def fc_inject_fault(kind, arg=0):
+    return _check(load().fc_inject_fault(kind, arg))
 
 
 def fc_set_noise_order(h, order):

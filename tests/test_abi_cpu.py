@@ -100,3 +100,13 @@ def test_blur_static_argument_checks_on_host():
             fastcat.check_blur_static_args(T, I, n_img, n_v, n_u)
     with pytest.raises(ValueError):
         fastcat.check_blur_static_args(ok, ok, 0, n_v, n_u)
+
+
+def test_fault_injection_arguments_checked_on_host(libpath):
+    from paper_2011_04736_gb300 import fastcat
+    fastcat.fc_inject_fault(fastcat.FC_FAULT_NONE)
+    for kind, arg in ((7, 0), (fastcat.FC_FAULT_ALLOC, -1)):
+        with pytest.raises(fastcat.FastcatError) as ei:
+            fastcat.fc_inject_fault(kind, arg)
+        assert ei.value.code == fastcat.FC_EINVAL
+    fastcat.fc_inject_fault(fastcat.FC_FAULT_NONE)
