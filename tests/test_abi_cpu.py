@@ -110,3 +110,21 @@ def test_fault_injection_arguments_checked_on_host(libpath):
             fastcat.fc_inject_fault(kind, arg)
         assert ei.value.code == fastcat.FC_EINVAL
     fastcat.fc_inject_fault(fastcat.FC_FAULT_NONE)
+
+
+def test_binding_constants_match_header():
+    """Every FC_* integer constant the binding defines has the header's value."""
+    from paper_2011_04736_gb300 import fastcat
+    txt = open(HEADER).read()
+    defs = {m.group(1): int(m.group(2)) for m in
+            re.finditer(r"^#define\s+(FC_\w+)\s+(-?\d+)\s*(?:/\*.*)?$", txt, flags=re.M)}
+    m = re.search(r"^#define\s+FC_STATIC_SCRATCH_FLOATS\s+\((\d+)u << (\d+)\)", txt, flags=re.M)
+    defs["FC_STATIC_SCRATCH_FLOATS"] = int(m.group(1)) << int(m.group(2))
+    names = [n for n in dir(fastcat) if n.startswith("FC_") and isinstance(getattr(fastcat, n), int)]
+    checked = 0
+    for n in names:
+        if n in defs:
+            assert getattr(fastcat, n) == defs[n], n
+            checked += 1
+    assert checked >= 20
+    assert len(fastcat.FC_K_NAMES) == defs["FC_K_COUNT"]

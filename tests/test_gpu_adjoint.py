@@ -44,7 +44,7 @@ def _rel(a, b):
     return np.linalg.norm(a - b) / np.linalg.norm(b)
 
 
-def test_cnr_gradient_matches_oracle(fc, orc):
+def test_cnr_gradient_matches_oracle(fc, orc, precision):
     from oracle import adjoint
     wl = _small()
     inp = W.adjoint_inputs(wl)
@@ -53,6 +53,11 @@ def test_cnr_gradient_matches_oracle(fc, orc):
     J, gl, gd, gr = _gpu(fc, wl, inp)
     print("J gpu %.8f oracle %.8f; rel err logits %.2e D %.2e rho %.2e"
           % (J, Jr, _rel(gl, glr), _rel(gd, gdr), _rel(gr, grr)))
+    case = "64^2x8 voxels, 48 x 96 x 24"
+    precision("J (CNR objective)", case, abs(J - Jr) / abs(Jr), REL)
+    precision("dJ/dlogits", case, _rel(gl, glr), REL, "relative (norm)")
+    precision("dJ/dD", case, _rel(gd, gdr), REL, "relative (norm)")
+    precision("dJ/drho", case, _rel(gr, grr), REL, "relative (norm)")
     assert abs(J - Jr) <= REL * abs(Jr)
     assert _rel(gl, glr) <= REL
     assert _rel(gd, gdr) <= REL
@@ -84,7 +89,7 @@ def test_cnr_autograd_function(fc):
         sc.close()
 
 
-def test_cnr_gradient_full_size_directional(fc):
+def test_cnr_gradient_full_size_directional(fc, precision):
     """At the benchmarked size (128^2 x 32 voxels, 180 projections of 512 x
     384, 30 bins) the FP64 oracle is too slow, so a property that holds at
     any size is checked instead: central differences of J along the density
@@ -107,12 +112,15 @@ def test_cnr_gradient_full_size_directional(fc):
         rp, rm = (rho.double() + step).float(), (rho.double() - step).float()
         expect = float(torch.sum(g * (rp.double() - rm.double()))) / 2.0
         got = (J_of(inp["logits"], rp) - J_of(inp["logits"], rm)) / 2.0
+        precision("dJ/drho . step", "adjoint_kv 128^2x32, 180x512x384 (central diff.)",
+                  abs(got - expect) / abs(expect), 1e-3)
         assert abs(got - expect) <= 1e-3 * abs(expect), (got, expect)
 
         gl = np.asarray(gl, dtype=np.float64)
         dl = 0.01 * gl / np.linalg.norm(gl)
         expect = float(gl @ dl)
         got = (J_of(inp["logits"] + dl, rho) - J_of(inp["logits"] - dl, rho)) / 2.0
+        precision("dJ/dlogits . step", "adjoint_kv (central diff.)", abs(got - expect) / abs(expect), 1e-3)
         assert abs(got - expect) <= 1e-3 * abs(expect), (got, expect)
     finally:
         sc.close()

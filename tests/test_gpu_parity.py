@@ -131,7 +131,7 @@ def test_head_phantom_reduced_every_ray(fc, orc):
     assert np.max(np.abs(T - Tr) / Tr) <= REL_T
 
 
-def test_head_phantom_full_size_sampled(fc, orc):
+def test_head_phantom_full_size_sampled(fc, orc, precision):
     """Full head-like scan (256^3 voxels of 0.0625 cm, 360 projections of
     512 x 512, 120 bins): T at 4000 sampled rays of five projections."""
     wl = W.WORKLOADS["head_surrogate"]
@@ -151,6 +151,8 @@ def test_head_phantom_full_size_sampled(fc, orc):
     w, d = wl.spectrum()
     Lr, Tr = orc.rays(g, lab, w, d, wl.mu(), np.stack([np.array(ks)[kk], rows, cols], 1))
     assert (Lr[:, 7] > 0).sum() > 10                   # teeth crossed by some sampled rays
+    precision("T (primary)", "head 256^3, 360x512x512, 120 bins, %d rays" % n,
+              np.max(np.abs(T[kk, rows, cols] - Tr) / Tr), REL_T)
     assert np.max(np.abs(T[kk, rows, cols] - Tr) / Tr) <= REL_T
 
 
@@ -270,7 +272,7 @@ def test_intensity_small_kv(fc, small_kv_ref):
     assert rel.max() <= REL_T, rel.max()
 
 
-def test_poisson_bit_identical(fc, orc, small_kv_ref):
+def test_poisson_bit_identical(fc, orc, small_kv_ref, precision):
     wl, _, _, Ir = small_kv_ref
     rng = np.random.default_rng(5)
     lam = (Ir[:20] * rng.uniform(0.0, 1.0, Ir[:20].shape) ** 6).astype(np.float32)
@@ -282,6 +284,8 @@ def test_poisson_bit_identical(fc, orc, small_kv_ref):
     fc.fc_poisson(d_lam, d_out, n, nv, nu, 3, wl.seed)
     torch.cuda.synchronize()
     got = d_out.cpu().numpy()
+    precision("Poisson counts", "%d draws, identical rates" % got.size,
+              np.count_nonzero(got.view(np.uint32) != ref.view(np.uint32)), 0, "mismatched draws")
     assert np.array_equal(got.view(np.uint32), ref.view(np.uint32)), \
         np.count_nonzero(got != ref)
     assert (lam < 10).sum() > 100  # both sampler branches exercised
@@ -426,7 +430,7 @@ def catphan_full(fc):
     return wl, lab, T, I
 
 
-def test_full_catphan_primary_sampled(orc, catphan_full):
+def test_full_catphan_primary_sampled(orc, catphan_full, precision):
     wl, lab, T, _ = catphan_full
     g = wl.geom
     rng = np.random.default_rng(1)
@@ -439,10 +443,12 @@ def test_full_catphan_primary_sampled(orc, catphan_full):
     w, d = wl.spectrum()
     _, Tr = orc.rays(g, lab, w, d, wl.mu(), rays)
     got = T[rays[:, 0], rays[:, 1], rays[:, 2]]
+    precision("T (primary)", "catphan_kv 256^2x10, 360x512x384, %d rays" % len(rays),
+              np.max(np.abs(got - Tr) / Tr), REL_T)
     assert np.max(np.abs(got - Tr) / Tr) <= REL_T
 
 
-def test_full_catphan_intensity_sampled(orc, catphan_full):
+def test_full_catphan_intensity_sampled(orc, catphan_full, precision):
     """I at sampled pixels: the oracle blurs its own T over the projections
     that contain the samples."""
     wl, lab, _, I = catphan_full
@@ -452,10 +458,11 @@ def test_full_catphan_intensity_sampled(orc, catphan_full):
     Tr = np.concatenate([orc.project_T(g, lab, w, d, wl.mu(), a0=k, na=1) for k in ks])
     Ir = orc.intensity(Tr, wl.psf_sigma_px, wl.scatter_sigma_px, wl.spr, wl.n0)
     got = I[ks]
+    precision("I (blur + scatter)", "catphan_kv, 3 full projections", np.max(np.abs(got - Ir) / Ir), REL_T)
     assert np.max(np.abs(got - Ir) / Ir) <= REL_T
 
 
-def test_full_catphan_reconstruct(fc, orc, catphan_full):
+def test_full_catphan_reconstruct(fc, orc, catphan_full, precision):
     """Full-size FDK of oracle-made noise-free counts, every voxel."""
     wl, lab, _, _ = catphan_full
     g = wl.geom
@@ -477,11 +484,13 @@ def test_full_catphan_reconstruct(fc, orc, catphan_full):
     vref = orc.backproject(g, f)
     mask = W.water_roi_mask(g)
     huref, mu_w = orc.hu(vref, mask)
+    precision("mu (FDK)", "catphan_kv, every voxel", np.max(np.abs(vol - vref)) / mu_w, 5e-4, "of mu_water")
+    precision("HU", "catphan_kv, every voxel", np.max(np.abs(hu - huref)), HU_TOL, "HU")
     assert np.max(np.abs(vol - vref)) <= 5e-4 * mu_w
     assert np.max(np.abs(hu - huref)) <= HU_TOL
 
 
-def test_full_paper_mv_sampled(fc, orc):
+def test_full_paper_mv_sampled(fc, orc, precision):
     """Paper-scale MV case (1024^2 x 10 voxels of 0.015625 cm, 1024 x 768
     detector, 60 MV bins): primary signal at sampled rays of six projections
     and the intensity of one whole projection against the oracle."""
@@ -493,6 +502,10 @@ def test_full_paper_mv_sampled(fc, orc):
     try:
         T = np.stack([_project(fc, sc, fc.FC_OUT_PRIMARY, k, 1)[0] for k in ks])
         I = _project(fc, sc, fc.FC_OUT_INTENSITY, 531, 1)
+        L = torch.empty((1, g.n_v, g.n_u, 7), dtype=torch.float32, device="cuda")
+        fc.fc_project_lengths(sc.h, 211, 1, L)
+        torch.cuda.synchronize()
+        L = L.cpu().numpy()[0]
     finally:
         sc.close()
     rng = np.random.default_rng(2)
@@ -502,8 +515,15 @@ def test_full_paper_mv_sampled(fc, orc):
     cols = rng.integers(0, g.n_u, n)
     rays = np.stack([np.array(ks)[kk], rows, cols], 1)
     w, d = wl.spectrum()
-    _, Tr = orc.rays(g, lab, w, d, wl.mu(), rays)
+    Lr, Tr = orc.rays(g, lab, w, d, wl.mu(), rays)
+    precision("T (primary)", "paper_mv 1024^2x10, 720x1024x768, %d rays" % n,
+              np.max(np.abs(T[kk, rows, cols] - Tr) / Tr), REL_T)
     assert np.max(np.abs(T[kk, rows, cols] - Tr) / Tr) <= REL_T
+    sel = np.array(ks)[kk] == 211
+    eL = np.max(np.abs(L[rows[sel], cols[sel]] - Lr[sel]))
+    precision("L (path lengths)", "paper_mv, projection 211, %d rays" % sel.sum(), eL, 2e-4, "cm")
+    assert eL < 2e-4
     Tp = orc.project_T(g, lab, w, d, wl.mu(), a0=531, na=1)
     Ir = orc.intensity(Tp, wl.psf_sigma_px, wl.scatter_sigma_px, wl.spr, wl.n0)
+    precision("I (blur + scatter)", "paper_mv, projection 531 (every pixel)", np.max(np.abs(I - Ir) / Ir), REL_T)
     assert np.max(np.abs(I - Ir) / Ir) <= REL_T
