@@ -247,7 +247,9 @@ int fc_reconstruct(fc_handle *h, const float *counts, int counts_where,
  *                       next angles copied to shared memory ahead of use;
  *                       applies where FC_BP_SLAB does and the window fits.
  * fc_reconstruct and fc_cnr_grad fail with FC_EINVAL when the requested
- * variant does not apply.  fc_backprojector_in_use writes the variant the
+ * variant does not apply (for every variant: when the stored filtered rows,
+ * n_angles x (reachable rows + 3) x (n_u + 3, rounded up to 4), reach 2^31
+ * elements).  fc_backprojector_in_use writes the variant the
  * current request resolves to for the handle's geometry.
  * Errors: FC_EINVAL (unknown variant, null pointers, not applicable),
  * FC_ESTATE (no geometry). */

@@ -228,6 +228,8 @@ void fdk_row_range(const DevGeom &g, int *v_lo, int *v_hi)
 
 namespace {
 constexpr int kFold = 64;        // angles per binary32 partial sum
+// floor(v) of 0 <= v < 2^22 as the low bits of v + 2^23 rounded toward -inf
+constexpr float kTwo23 = 8388608.0f;
 constexpr int kSlabMaxNz = 16;   // slices the thin-slab kernel keeps per thread
 // largest projected z pitch (detector rows) the thin-slab kernel takes: the
 // row index may then advance by at most one per slice, rounding included
@@ -263,7 +265,7 @@ __device__ __forceinline__ void backproject_body(const FdkParams &p, const float
     const float y = ((float)iy - 0.5f * (float)(g.ny - 1)) * g.dy;
     const float z0 = ((float)iz0 - 0.5f * (float)(g.nz - 1)) * g.dz;
     const int nzc = min(kZc, g.nz - iz0);
-    const size_t plane = (size_t)p.ph * p.pw;
+    const unsigned plane = (unsigned)p.ph * (unsigned)p.pw;
     // padded coordinates: column c + 1 holds detector column c, row r + 1
     // holds detector row v_lo + r; clamping to [0, pw - 2] x [0, ph - 2]
     // keeps both taps inside the buffer and only ever lands on zero padding
@@ -272,6 +274,7 @@ __device__ __forceinline__ void backproject_body(const FdkParams &p, const float
     const float cu1 = g.cu + 1.0f, cv1 = g.cv - (float)p.v_lo + 1.0f;
     const float umax = (float)(p.pw - 2), vmaxp = (float)(p.ph - 2);
     const float sdd_du = g.sdd / g.du, sdd_dv = g.sdd / g.dv;
+    const int two23 = __float_as_int(kTwo23);
     double accd[kZc];
 #pragma unroll
     for (int z = 0; z < kZc; ++z) accd[z] = 0.0;
@@ -285,23 +288,28 @@ __device__ __forceinline__ void backproject_body(const FdkParams &p, const float
             const float2 cs = p.trig[k];
             const float U = g.sad - (x * cs.x + y * cs.y);
             const float ru = y * cs.x - x * cs.y;
-            const float iU = __frcp_rn(U);
+            float iU;                                   // hardware reciprocal + one Newton step
+            asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(iU) : "f"(U));
+            iU = fmaf(iU, fmaf(-U, iU, 1.0f), iU);
             const float fu = fminf(fmaxf(fmaf(ru * iU, sdd_du, cu1), 0.0f), umax);
             const float w = (g.sad * iU) * (g.sad * iU);
             const float fv0 = fmaf(z0 * iU, sdd_dv, cv1);
             const float dfv = g.dz * iU * sdd_dv;
-            const float fu0 = floorf(fu);
-            const float au = fu - fu0;
-            const float *fk = f + (size_t)k * plane + (int)fu0;
+            const float tu = __fadd_rd(fu, kTwo23);     // 2^23 + floor(fu)
+            const float au = fu - (tu - kTwo23);
+            // element offset of the column in projection k (the buffer holds
+            // fewer than 2^31 elements: 32-bit offsets from the kernel's pointer)
+            const unsigned cofs = (unsigned)k * (unsigned)plane + (unsigned)(__float_as_int(tu) - two23);
 #pragma unroll
             for (int z = 0; z < kZc; ++z) {
                 if (z < nzc) {
                     const float fv = fminf(fmaxf(fmaf((float)z, dfv, fv0), 0.0f), vmaxp);
-                    const float fvf = floorf(fv);
-                    const float av = fv - fvf;
-                    const float *r = fk + (int)fvf * p.pw;
+                    const float tv = __fadd_rd(fv, kTwo23);
+                    const float av = fv - (tv - kTwo23);
+                    const unsigned o = (unsigned)(__float_as_int(tv) - two23) * (unsigned)p.pw + cofs;
+                    const float *r = f + o, *r2 = f + (o + (unsigned)p.pw);
                     const float a00 = __ldg(r), a01 = __ldg(r + 1);
-                    const float a10 = __ldg(r + p.pw), a11 = __ldg(r + p.pw + 1);
+                    const float a10 = __ldg(r2), a11 = __ldg(r2 + 1);
                     const float top = fmaf(au, a01 - a00, a00);
                     const float bot = fmaf(au, a11 - a10, a10);
                     accf[z] = fmaf(w, fmaf(av, bot - top, top), accf[z]);
@@ -344,10 +352,13 @@ __global__ void __launch_bounds__(256, 8) k_backproject_dense(const __grid_const
 // from the slice before (the same row, or the one it loaded).  Per update
 // that is two tap loads instead of four and one u interpolation instead of
 // two.  The slices run as two interleaved halves (z and z + NA), so the
-// binary32 arithmetic issues as packed pairs (Blackwell f32x2 FMA / add
-// instructions: two lanes' worth of binary32 work per instruction, each
-// element rounded exactly as the scalar instruction would); floors come
-// from adding 2^23 with rounding toward -inf (exact for 0 <= v < 2^22).
+// binary32 arithmetic of the v coordinate, the v interpolation and the sums
+// issues as packed pairs (Blackwell f32x2 FMA / add instructions: two lanes'
+// worth of binary32 work per instruction, each element rounded exactly as the
+// scalar instruction would); the u interpolation of the loaded taps stays
+// scalar (fewer registers); floors come from adding 2^23 with rounding toward
+// -inf (exact for 0 <= v < 2^22); tap addresses are 32-bit element offsets
+// from the kernel's pointer, one multiply-add each.
 // Binary32 partial sums over kFold angles are folded into binary64 sums
 // kept in shared memory.  CLAMP: clamp the detector coordinates into the
 // stored rows and columns (needed only when a voxel can project outside them:
@@ -358,7 +369,6 @@ namespace {
 __device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
 // a - b, exactly as a binary32 subtraction rounds it (b * -1 is exact)
 __device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, f2(-1.0f), a); }
-constexpr float kTwo23 = 8388608.0f;
 }  // namespace
 
 template <int NZ, bool CLAMP>
@@ -378,8 +388,7 @@ k_backproject_slab(const __grid_constant__ FdkParams p, const float *__restrict_
     const float x = ((float)ix - 0.5f * (float)(g.nx - 1)) * g.dx;
     const float y = ((float)iy - 0.5f * (float)(g.ny - 1)) * g.dy;
     const float z0 = -0.5f * (float)(g.nz - 1) * g.dz;
-    const size_t plane = (size_t)p.ph * p.pw;
-    const int pw4 = 4 * p.pw;        // row pitch in bytes (32-bit: one wide multiply-add per address)
+    const unsigned plane = (unsigned)p.ph * (unsigned)p.pw;
     const float cu1 = g.cu + 1.0f, cv1 = g.cv - (float)p.v_lo + 1.0f;
     const float umax = (float)(p.pw - 2), vmaxp = (float)(p.ph - 2);
     const float sdd_du = g.sdd / g.du, sdd_dv = g.sdd / g.dv, dz_dv = g.dz * (g.sdd / g.dv);
@@ -406,10 +415,11 @@ k_backproject_slab(const __grid_constant__ FdkParams p, const float *__restrict_
             const float2 fv0 = f2(fmaf(z0 * iU, sdd_dv, cv1));
             const float2 dfv = f2(dz_dv * iU);
             const float2 au2 = f2(au);
-            // byte address of row r + 1 of the column: base + (2^23 + r) * pw4
-            const char *base = reinterpret_cast<const char *>(f + (size_t)k * plane +
-                                                              (__float_as_int(tu) - two23)) +
-                               (long long)(1 - two23) * (long long)pw4;
+            // element offset of row r + 1 of the column: (2^23 + r) pw + cofs,
+            // in 32-bit modular arithmetic (the true offset is below 2^31), so
+            // each tap address is one multiply-add off the kernel's pointer
+            const unsigned cofs = (unsigned)k * (unsigned)plane + (unsigned)(__float_as_int(tu) - two23) +
+                                  (unsigned)(1 - two23) * (unsigned)p.pw;
             float2 lo, hi;
             int2 jp;
 #pragma unroll
@@ -423,11 +433,10 @@ k_backproject_slab(const __grid_constant__ FdkParams p, const float *__restrict_
                 const float2 tv = __fadd2_rd(fv, f2(kTwo23));    // 2^23 + floor(fv)
                 const float2 av = sub2(fv, __fadd2_rn(tv, f2(-kTwo23)));
                 const int2 j = make_int2(__float_as_int(tv.x), __float_as_int(tv.y));
-                const float *ra = reinterpret_cast<const float *>(base + (long long)j.x * (long long)pw4);
-                const float *rb = reinterpret_cast<const float *>(base + (long long)j.y * (long long)pw4);
-                const float2 b0 = make_float2(__ldg(ra), __ldg(rb));
-                const float2 b1 = make_float2(__ldg(ra + 1), __ldg(rb + 1));
-                const float2 nh = __ffma2_rn(au2, sub2(b1, b0), b0);
+                const float *ra = f + ((unsigned)j.x * (unsigned)p.pw + cofs);
+                const float *rb = f + ((unsigned)j.y * (unsigned)p.pw + cofs);
+                const float b0a = __ldg(ra), b1a = __ldg(ra + 1), b0b = __ldg(rb), b1b = __ldg(rb + 1);
+                const float2 nh = make_float2(fmaf(au2.x, b1a - b0a, b0a), fmaf(au2.x, b1b - b0b, b0b));
                 if (i == 0) {
                     const float2 a0 = make_float2(__ldg(ra - p.pw), __ldg(rb - p.pw));
                     const float2 a1 = make_float2(__ldg(ra - p.pw + 1), __ldg(rb - p.pw + 1));
@@ -661,6 +670,8 @@ static size_t slab_staged_smem(const FdkParams &p)
 
 int backproject_variant(const FdkParams &p, int request)
 {
+    // every kernel addresses the filtered rows with 32-bit element offsets
+    if ((double)p.g.n_angles * p.ph * p.pw >= 2147483648.0) return -1;
     const bool slab_ok = p.g.nz <= kSlabMaxNz && fdk_slab_row_step(p.g) <= kSlabMaxStep;
     if (request == FC_BP_SLAB) return slab_ok ? FC_BP_SLAB : -1;
     if (request == FC_BP_SLAB_STAGED) return slab_ok && slab_staged_smem(p) ? FC_BP_SLAB_STAGED : -1;
