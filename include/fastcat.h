@@ -242,10 +242,7 @@ int fc_reconstruct(fc_handle *h, const float *counts, int counts_where,
  *                       reuses the previous slice's detector row.  Applies
  *                       when nz <= 16 and the z pitch projects to at most 0.98
  *                       detector rows at every voxel (dz SDD / (SAD - r_max)
- *                       <= 0.98 dv, r_max the half-diagonal of the volume);
- *   FC_BP_SLAB_STAGED   FC_BP_SLAB with each CTA's detector window of the
- *                       next angles copied to shared memory ahead of use;
- *                       applies where FC_BP_SLAB does and the window fits.
+ *                       <= 0.98 dv, r_max the half-diagonal of the volume).
  * fc_reconstruct and fc_cnr_grad fail with FC_EINVAL when the requested
  * variant does not apply (for every variant: when the stored filtered rows,
  * n_angles x (reachable rows + 3) x (n_u + 3, rounded up to 4), reach 2^31
@@ -257,7 +254,6 @@ int fc_reconstruct(fc_handle *h, const float *counts, int counts_where,
 #define FC_BP_CHUNKED       1
 #define FC_BP_CHUNKED_DENSE 2
 #define FC_BP_SLAB          3
-#define FC_BP_SLAB_STAGED   4
 int fc_set_backprojector(fc_handle *h, int variant);
 int fc_backprojector_in_use(fc_handle *h, int *variant);
 

@@ -134,7 +134,8 @@ struct fc_handle {
     float2 *d_trig = nullptr;
     uint8_t *d_labels = nullptr;   // caller layout [nz][ny][nx]
     uint8_t *d_bricks = nullptr;   // 8x8x16 brick map: uniform label or mixed
-    float *d_T = nullptr, *d_tp = nullptr, *d_ts = nullptr, *d_counts = nullptr, *d_filt = nullptr;
+    float *d_T = nullptr, *d_tp = nullptr, *d_ts = nullptr, *d_counts = nullptr;
+    float2 *d_filt = nullptr;   // filtered rows as (value, next - value) pairs
     double *d_vol = nullptr;
     float *d_hu = nullptr;
     double *d_part = nullptr;
@@ -270,8 +271,8 @@ int ensure_recon_buffers(fc_handle *h, cudaStream_t s)
         int lo, hi;
         fc::fdk_row_range(h->dg, &lo, &hi);
         h->filt_elems = (size_t)h->g.n_angles * (hi - lo + 1 + 3) * fdk_row_pitch(h->g.n_u);
-        FC_CK(dev_malloc((void **)&h->d_filt, h->filt_elems * sizeof(float)));
-        FC_CK(cudaMemsetAsync(h->d_filt, 0, h->filt_elems * sizeof(float), s));
+        FC_CK(dev_malloc((void **)&h->d_filt, h->filt_elems * sizeof(float2)));
+        FC_CK(cudaMemsetAsync(h->d_filt, 0, h->filt_elems * sizeof(float2), s));
     }
     if (!h->d_counts) FC_CK(dev_malloc((void **)&h->d_counts, h->proj_elems * sizeof(float)));
     if (!h->d_vol) FC_CK(dev_malloc((void **)&h->d_vol, h->vol_elems * sizeof(double)));
@@ -1039,7 +1040,7 @@ int fc_set_noise_order(fc_handle *h, int order)
 int fc_set_backprojector(fc_handle *h, int variant)
 {
     if (!h) return fail(FC_EINVAL, "fc_set_backprojector: null handle");
-    if (variant < FC_BP_AUTO || variant > FC_BP_SLAB_STAGED)
+    if (variant < FC_BP_AUTO || variant > FC_BP_SLAB)
         return fail(FC_EINVAL, "fc_set_backprojector: unknown variant %d", variant);
     h->bp_request = variant;
     return FC_OK;

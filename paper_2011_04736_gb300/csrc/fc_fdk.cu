@@ -95,10 +95,14 @@ __device__ __forceinline__ void ramp_row(const float *sx, int n, float inv_tau, 
     }
 }
 
-// rows [v_lo, v_hi] of every projection; blockIdx.x = projection * nrows + r
+// rows [v_lo, v_hi] of every projection; blockIdx.x = projection * nrows + r.
+// The filtered row goes to shared memory, then out as (value, next value -
+// value) pairs over padded columns 0..n (the zero column before the row and
+// the one after it included), so a bilinear tap pair is one 8-byte load and
+// the u interpolation one FMA.
 __global__ void __launch_bounds__(kFiltThreads)
 k_fdk_filter(const __grid_constant__ FdkParams p, const float *__restrict__ counts,
-             float *__restrict__ filt)
+             float2 *__restrict__ filt)
 {
     extern __shared__ float sx[];
     const DevGeom &g = p.g;
@@ -108,7 +112,7 @@ k_fdk_filter(const __grid_constant__ FdkParams p, const float *__restrict__ coun
     const int r = (int)(blockIdx.x % nrows);
     const int iv = p.v_lo + r;
     const size_t row = ((size_t)k * g.n_v + iv) * n;
-    float *dst = filt + ((size_t)k * p.ph + (r + 1)) * p.pw + 1;
+    float2 *dst = filt + ((size_t)k * p.ph + (r + 1)) * p.pw;
     // padded row: index n + j holds q[j], zeros in [0, n) and [2n, 3n + pad)
     const float vi = ((float)iv - g.cv) * g.dv * p.mag;
     const float sad2v = g.sad * g.sad + vi * vi;
@@ -124,10 +128,17 @@ k_fdk_filter(const __grid_constant__ FdkParams p, const float *__restrict__ coun
         sx[skew(i)] = val;
     }
     __syncthreads();
-    ramp_row(sx, n, 1.0f / p.tau, [&](int i, float v) { dst[i] = v; });
+    float *fo = sx + span + span / 32 + 2;          // filtered row, index i + 1 = padded column
+    ramp_row(sx, n, 1.0f / p.tau, [&](int i, float v) { fo[i + 1] = v; });
+    if (threadIdx.x == 0) {
+        fo[0] = 0.0f;
+        fo[n + 1] = 0.0f;
+    }
+    __syncthreads();
+    for (int c = threadIdx.x; c <= n; c += blockDim.x) dst[c] = make_float2(fo[c], fo[c + 1] - fo[c]);
 }
 
-cudaError_t launch_fdk_filter(const FdkParams &p, const float *counts, float *filt, cudaStream_t s)
+cudaError_t launch_fdk_filter(const FdkParams &p, const float *counts, float2 *filt, cudaStream_t s)
 {
     const int nrows = p.v_hi - p.v_lo + 1;
     if (nrows <= 0 || p.g.n_angles <= 0) return cudaSuccess;
@@ -135,7 +146,7 @@ cudaError_t launch_fdk_filter(const FdkParams &p, const float *counts, float *fi
     cudaError_t e = upload_ramp_taps();
     if (e != cudaSuccess) return e;
     const int span = 3 * p.g.n_u + kFiltOut + 2;
-    const size_t smem = (size_t)(span + span / 32 + 2) * sizeof(float);
+    const size_t smem = (size_t)(span + span / 32 + 2 + p.g.n_u + 2) * sizeof(float);
     if (smem > 48 * 1024) {
         e = cudaFuncSetAttribute(k_fdk_filter, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)smem);
@@ -253,7 +264,7 @@ void chunked_launch_shape(const FdkParams &p, int *zc_out, dim3 *grid)
 
 // kZc z values per thread (the launcher balances the z chunks).
 template <int kZc>
-__device__ __forceinline__ void backproject_body(const FdkParams &p, const float *__restrict__ f,
+__device__ __forceinline__ void backproject_body(const FdkParams &p, const float2 *__restrict__ f,
                                                  double *__restrict__ vol)
 {
     const DevGeom &g = p.g;
@@ -307,11 +318,9 @@ __device__ __forceinline__ void backproject_body(const FdkParams &p, const float
                     const float tv = __fadd_rd(fv, kTwo23);
                     const float av = fv - (tv - kTwo23);
                     const unsigned o = (unsigned)(__float_as_int(tv) - two23) * (unsigned)p.pw + cofs;
-                    const float *r = f + o, *r2 = f + (o + (unsigned)p.pw);
-                    const float a00 = __ldg(r), a01 = __ldg(r + 1);
-                    const float a10 = __ldg(r2), a11 = __ldg(r2 + 1);
-                    const float top = fmaf(au, a01 - a00, a00);
-                    const float bot = fmaf(au, a11 - a10, a10);
+                    const float2 t0 = __ldg(f + o), t1 = __ldg(f + (o + (unsigned)p.pw));
+                    const float top = fmaf(au, t0.y, t0.x);
+                    const float bot = fmaf(au, t1.y, t1.x);
                     accf[z] = fmaf(w, fmaf(av, bot - top, top), accf[z]);
                 }
             }
@@ -329,7 +338,7 @@ __device__ __forceinline__ void backproject_body(const FdkParams &p, const float
 // bytes of the binary64 sums spilled).
 template <int kZc>
 __global__ void __launch_bounds__(256) k_backproject(const __grid_constant__ FdkParams p,
-                                                     const float *__restrict__ f,
+                                                     const float2 *__restrict__ f,
                                                      double *__restrict__ vol)
 {
     backproject_body<kZc>(p, f, vol);
@@ -337,7 +346,7 @@ __global__ void __launch_bounds__(256) k_backproject(const __grid_constant__ Fdk
 
 template <int kZc>
 __global__ void __launch_bounds__(256, 8) k_backproject_dense(const __grid_constant__ FdkParams p,
-                                                              const float *__restrict__ f,
+                                                              const float2 *__restrict__ f,
                                                               double *__restrict__ vol)
 {
     backproject_body<kZc>(p, f, vol);
@@ -373,7 +382,7 @@ __device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b
 
 template <int NZ, bool CLAMP>
 __global__ void __launch_bounds__(256)
-k_backproject_slab(const __grid_constant__ FdkParams p, const float *__restrict__ f,
+k_backproject_slab(const __grid_constant__ FdkParams p, const float2 *__restrict__ f,
                    double *__restrict__ vol)
 {
     constexpr int NA = (NZ + 1) / 2;     // slices per half: z = i and z = i + NA
@@ -433,14 +442,13 @@ k_backproject_slab(const __grid_constant__ FdkParams p, const float *__restrict_
                 const float2 tv = __fadd2_rd(fv, f2(kTwo23));    // 2^23 + floor(fv)
                 const float2 av = sub2(fv, __fadd2_rn(tv, f2(-kTwo23)));
                 const int2 j = make_int2(__float_as_int(tv.x), __float_as_int(tv.y));
-                const float *ra = f + ((unsigned)j.x * (unsigned)p.pw + cofs);
-                const float *rb = f + ((unsigned)j.y * (unsigned)p.pw + cofs);
-                const float b0a = __ldg(ra), b1a = __ldg(ra + 1), b0b = __ldg(rb), b1b = __ldg(rb + 1);
-                const float2 nh = make_float2(fmaf(au2.x, b1a - b0a, b0a), fmaf(au2.x, b1b - b0b, b0b));
+                const float2 *ra = f + ((unsigned)j.x * (unsigned)p.pw + cofs);
+                const float2 *rb = f + ((unsigned)j.y * (unsigned)p.pw + cofs);
+                const float2 qa = __ldg(ra), qb = __ldg(rb);
+                const float2 nh = make_float2(fmaf(au2.x, qa.y, qa.x), fmaf(au2.x, qb.y, qb.x));
                 if (i == 0) {
-                    const float2 a0 = make_float2(__ldg(ra - p.pw), __ldg(rb - p.pw));
-                    const float2 a1 = make_float2(__ldg(ra - p.pw + 1), __ldg(rb - p.pw + 1));
-                    lo = __ffma2_rn(au2, sub2(a1, a0), a0);
+                    const float2 pa = __ldg(ra - p.pw), pb = __ldg(rb - p.pw);
+                    lo = make_float2(fmaf(au2.x, pa.y, pa.x), fmaf(au2.x, pb.y, pb.x));
                 } else {
                     lo.x = j.x == jp.x ? lo.x : hi.x;
                     lo.y = j.y == jp.y ? lo.y : hi.y;
@@ -458,179 +466,6 @@ k_backproject_slab(const __grid_constant__ FdkParams p, const float *__restrict_
     }
 #pragma unroll
     for (int z = 0; z < NZ; ++z) vol[((size_t)z * g.ny + iy) * g.nx + ix] = accd[z][t] * p.scale;
-}
-
-// The thin-slab kernel with each CTA's detector footprint staged in shared
-// memory.  Per angle a CTA (32 x 8 columns) samples a window of at most cw
-// columns (a host bound on the tile's projected width plus margins) of the
-// stored rows; the window of angle k + kStages - 1 is copied with 16-byte
-// cp.async (one per thread, every stored row) while angle k is computed from
-// shared memory, so the taps never wait on L2.  The window's first column
-// comes from the tile's corners (the projected u of a rectangle is extreme at
-// a corner), two columns of margin for rounding, aligned down to 4.  One
-// barrier per angle hands the ring on.  Arithmetic per slice is the
-// thin-slab kernel's.
-namespace {
-constexpr int kStages = 4;
-
-// Padded column, clamped as the consumers clamp it, of tile corner `lane`
-// (0..3) for angle (c, s); other lanes return a large value.
-__device__ __forceinline__ float corner_fu(const DevGeom &g, int lane, int ix0, int iy0, float2 cs,
-                                           float sdd_du, float cu1, float umax, bool clamp)
-{
-    const int ix = min(ix0 + ((lane & 1) ? 31 : 0), g.nx - 1);
-    const int iy = min(iy0 + ((lane & 2) ? 7 : 0), g.ny - 1);
-    const float x = ((float)ix - 0.5f * (float)(g.nx - 1)) * g.dx;
-    const float y = ((float)iy - 0.5f * (float)(g.ny - 1)) * g.dy;
-    const float U = g.sad - (x * cs.x + y * cs.y);
-    const float ru = y * cs.x - x * cs.y;
-    float fu = fmaf(ru / U, sdd_du, cu1);
-    if (clamp) fu = fminf(fmaxf(fu, 0.0f), umax);
-    return lane < 4 ? fu : 3.0e38f;
-}
-
-__device__ __forceinline__ void cp_async16(void *dst, const void *src)
-{
-    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" :: "r"(d), "l"(src) : "memory");
-}
-}  // namespace
-
-template <int NZ, bool CLAMP>
-__global__ void __launch_bounds__(256)
-k_backproject_slab_staged(const __grid_constant__ FdkParams p, const float *__restrict__ f,
-                          double *__restrict__ vol, int cw)
-{
-    constexpr int NA = (NZ + 1) / 2;
-    extern __shared__ __align__(16) float st[];          // [kStages][ph][cw]
-    __shared__ double accd[NZ][256];
-    __shared__ int c_first[kStages];
-    const DevGeom &g = p.g;
-    const int t = threadIdx.y * 32 + threadIdx.x, lane = threadIdx.x;
-    const int ix0 = blockIdx.x * 32, iy0 = blockIdx.y * 8;
-    const int ix = ix0 + threadIdx.x, iy = iy0 + threadIdx.y;
-    const bool live = ix < g.nx && iy < g.ny;
-    const int ph = p.ph, pw = p.pw;
-    const int stage_floats = ph * cw, nchunk = stage_floats / 4, cw4 = cw / 4;
-    const size_t plane = (size_t)ph * pw;
-    const float x = ((float)ix - 0.5f * (float)(g.nx - 1)) * g.dx;
-    const float y = ((float)iy - 0.5f * (float)(g.ny - 1)) * g.dy;
-    const float z0 = -0.5f * (float)(g.nz - 1) * g.dz;
-    const float cu1 = g.cu + 1.0f, cv1 = g.cv - (float)p.v_lo + 1.0f;
-    const float umax = (float)(pw - 2), vmaxp = (float)(ph - 2);
-    const float sdd_du = g.sdd / g.du, sdd_dv = g.sdd / g.dv, dz_dv = g.dz * (g.sdd / g.dv);
-    const int two23 = __float_as_int(kTwo23);
-#pragma unroll
-    for (int z = 0; z < NZ; ++z) accd[z][t] = 0.0;
-
-    // copy the window of angle kn into its stage (every thread, uniform)
-    auto produce = [&](int kn) {
-        if (kn < g.n_angles) {
-            float m = corner_fu(g, lane, ix0, iy0, p.trig[kn], sdd_du, cu1, umax, CLAMP);
-            m = fminf(m, __shfl_xor_sync(0xffffffffu, m, 1));
-            m = fminf(m, __shfl_xor_sync(0xffffffffu, m, 2));
-            m = __shfl_sync(0xffffffffu, m, 0);
-            int c0 = ((int)floorf(m) - 2) & ~3;
-            c0 = max(0, min(c0, pw - cw));
-            if (t == 0) c_first[kn % kStages] = c0;
-            float *dst = st + (kn % kStages) * stage_floats;
-            const float *src = f + (size_t)kn * plane + c0;
-            for (int e = t; e < nchunk; e += 256) {
-                const int r = e / cw4, c4 = e - r * cw4;
-                cp_async16(dst + r * cw + 4 * c4, src + (size_t)r * pw + 4 * c4);
-            }
-        }
-        asm volatile("cp.async.commit_group;" ::: "memory");
-    };
-#pragma unroll 1
-    for (int kn = 0; kn < kStages - 1; ++kn) produce(kn);
-
-    for (int kb = 0; kb < g.n_angles; kb += kFold) {
-        const int ke = min(g.n_angles, kb + kFold);
-        float2 acc[NA];
-#pragma unroll
-        for (int i = 0; i < NA; ++i) acc[i] = make_float2(0.0f, 0.0f);
-#pragma unroll 1
-        for (int k = kb; k < ke; ++k) {
-            asm volatile("cp.async.wait_group %0;" :: "n"(kStages - 2) : "memory");
-            __syncthreads();                      // angle k staged; stage of k - 1 free
-            produce(k + kStages - 1);
-            if (!live) continue;
-            const float *sk = st + (k % kStages) * stage_floats;
-            const int c0 = c_first[k % kStages];
-            const float2 cs = p.trig[k];
-            const float U = g.sad - (x * cs.x + y * cs.y);
-            const float ru = y * cs.x - x * cs.y;
-            float iU;
-            asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(iU) : "f"(U));
-            iU = fmaf(iU, fmaf(-U, iU, 1.0f), iU);
-            float fu = fmaf(ru * iU, sdd_du, cu1);
-            if (CLAMP) fu = fminf(fmaxf(fu, 0.0f), umax);
-            const float tu = __fadd_rd(fu, kTwo23);          // 2^23 + floor(fu)
-            const float au = fu - (tu - kTwo23);
-            const float2 w2 = f2((g.sad * iU) * (g.sad * iU));
-            const float2 fv0 = f2(fmaf(z0 * iU, sdd_dv, cv1));
-            const float2 dfv = f2(dz_dv * iU);
-            const float2 au2 = f2(au);
-            // row r + 1 of the column in the window: base + r * cw
-            const float *base = sk + (__float_as_int(tu) - two23 - c0) + cw;
-            float2 lo, hi;
-            int2 jp;
-#pragma unroll
-            for (int i = 0; i < NA; ++i) {
-                const float2 zz = make_float2((float)i, (float)(i + NA));
-                float2 fv = __ffma2_rn(zz, dfv, fv0);
-                if (CLAMP) {
-                    fv.x = fminf(fmaxf(fv.x, 0.0f), vmaxp);
-                    fv.y = fminf(fmaxf(fv.y, 0.0f), vmaxp);
-                }
-                const float2 tv = __fadd2_rd(fv, f2(kTwo23));
-                const float2 av = sub2(fv, __fadd2_rn(tv, f2(-kTwo23)));
-                const int2 j = make_int2(__float_as_int(tv.x) - two23, __float_as_int(tv.y) - two23);
-                const float *ra = base + j.x * cw, *rb = base + j.y * cw;
-                const float2 b0 = make_float2(ra[0], rb[0]);
-                const float2 b1 = make_float2(ra[1], rb[1]);
-                const float2 nh = __ffma2_rn(au2, sub2(b1, b0), b0);
-                if (i == 0) {
-                    const float2 a0 = make_float2(ra[-cw], rb[-cw]);
-                    const float2 a1 = make_float2(ra[1 - cw], rb[1 - cw]);
-                    lo = __ffma2_rn(au2, sub2(a1, a0), a0);
-                } else {
-                    lo.x = j.x == jp.x ? lo.x : hi.x;
-                    lo.y = j.y == jp.y ? lo.y : hi.y;
-                }
-                hi = nh;
-                jp = j;
-                acc[i] = __ffma2_rn(w2, __ffma2_rn(av, sub2(hi, lo), lo), acc[i]);
-            }
-        }
-        if (live) {
-#pragma unroll
-            for (int i = 0; i < NA; ++i) {
-                accd[i][t] += (double)acc[i].x;
-                if (i + NA < NZ) accd[i + NA][t] += (double)acc[i].y;
-            }
-        }
-    }
-    asm volatile("cp.async.wait_group 0;" ::: "memory");
-    if (!live) return;
-#pragma unroll
-    for (int z = 0; z < NZ; ++z) vol[((size_t)z * g.ny + iy) * g.nx + ix] = accd[z][t] * p.scale;
-}
-
-// Window width (columns, multiple of 4) the staged kernel needs: the
-// projected u extent of a 32 x 8 voxel tile, |du| <= SDD D (1 / U_min +
-// r_max / U_min^2) for its diagonal D, plus 2 + 2 columns of margin and 3 of
-// alignment.
-static int slab_window(const DevGeom &g)
-{
-    const double hx = 0.5 * g.nx * (double)g.dx, hy = 0.5 * g.ny * (double)g.dy;
-    const double rmax = sqrt(hx * hx + hy * hy);
-    const double umin = (double)g.sad - rmax;
-    if (umin <= 0.0) return 1 << 30;
-    const double dg = sqrt(32.0 * g.dx * 32.0 * g.dx + 8.0 * g.dy * 8.0 * g.dy);
-    const double ext = (double)g.sdd * dg * (1.0 / umin + rmax / (umin * umin)) / (double)g.du;
-    return ((int)ceil(ext) + 7 + 3) & ~3;
 }
 
 // Whether a voxel can project outside the stored filtered rows (fdk_row_range
@@ -658,23 +493,12 @@ double fdk_slab_row_step(const DevGeom &g)
     return (double)g.dz * (double)g.sdd / umin / (double)g.dv;
 }
 
-// Dynamic shared memory of the staged thin-slab kernel, or 0 when its window
-// does not fit the stored rows or shared memory.
-static size_t slab_staged_smem(const FdkParams &p)
-{
-    const int cw = slab_window(p.g);
-    if (cw > p.pw) return 0;
-    const size_t bytes = (size_t)kStages * p.ph * cw * sizeof(float);
-    return bytes + (size_t)kSlabMaxNz * 256 * sizeof(double) <= 200 * 1024 ? bytes : 0;
-}
-
 int backproject_variant(const FdkParams &p, int request)
 {
     // every kernel addresses the filtered rows with 32-bit element offsets
     if ((double)p.g.n_angles * p.ph * p.pw >= 2147483648.0) return -1;
     const bool slab_ok = p.g.nz <= kSlabMaxNz && fdk_slab_row_step(p.g) <= kSlabMaxStep;
     if (request == FC_BP_SLAB) return slab_ok ? FC_BP_SLAB : -1;
-    if (request == FC_BP_SLAB_STAGED) return slab_ok && slab_staged_smem(p) ? FC_BP_SLAB_STAGED : -1;
     if (request == FC_BP_CHUNKED || request == FC_BP_CHUNKED_DENSE) return request;
     if (request != FC_BP_AUTO) return -1;
     if (slab_ok) return FC_BP_SLAB;
@@ -689,39 +513,9 @@ int backproject_variant(const FdkParams &p, int request)
     return (long)grid.x * grid.y * grid.z >= 2L * sm_count() * 6 ? FC_BP_CHUNKED_DENSE : FC_BP_CHUNKED;
 }
 
-cudaError_t launch_backproject(const FdkParams &p, const float *filt, double *vol, int variant,
+cudaError_t launch_backproject(const FdkParams &p, const float2 *filt, double *vol, int variant,
                                cudaStream_t s)
 {
-    if (variant == FC_BP_SLAB_STAGED) {
-        dim3 block(32, 8);
-        dim3 grid((p.g.nx + 31) / 32, (p.g.ny + 7) / 8);
-        const size_t smem = slab_staged_smem(p);
-        if (!smem) return cudaErrorInvalidValue;
-        const int cw = slab_window(p.g);
-        const bool clamp = slab_needs_clamp(p.g);
-        cudaError_t e = cudaSuccess;
-#define FC_BPT(Z)                                                                                  \
-    case Z:                                                                                        \
-        if (clamp) {                                                                               \
-            e = cudaFuncSetAttribute(k_backproject_slab_staged<Z, true>,                           \
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);      \
-            if (e == cudaSuccess) k_backproject_slab_staged<Z, true><<<grid, block, smem, s>>>(p, filt, vol, cw); \
-        } else {                                                                                   \
-            e = cudaFuncSetAttribute(k_backproject_slab_staged<Z, false>,                          \
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);      \
-            if (e == cudaSuccess) k_backproject_slab_staged<Z, false><<<grid, block, smem, s>>>(p, filt, vol, cw); \
-        }                                                                                          \
-        break;
-        switch (p.g.nz) {
-        FC_BPT(1) FC_BPT(2) FC_BPT(3) FC_BPT(4) FC_BPT(5) FC_BPT(6) FC_BPT(7) FC_BPT(8)
-        FC_BPT(9) FC_BPT(10) FC_BPT(11) FC_BPT(12) FC_BPT(13) FC_BPT(14) FC_BPT(15) FC_BPT(16)
-        default:
-            return cudaErrorInvalidValue;
-        }
-#undef FC_BPT
-        if (e != cudaSuccess) return e;
-        return cudaGetLastError();
-    }
     if (variant == FC_BP_SLAB) {
         dim3 block(32, 8);
         dim3 grid((p.g.nx + 31) / 32, (p.g.ny + 7) / 8);

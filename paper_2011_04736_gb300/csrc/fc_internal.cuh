@@ -146,8 +146,9 @@ constexpr size_t kBlurTcHankelMax = 2 * 2 * 64 * (15 + (128 + 2 * 256) / 8);  //
 
 // Filtered projections are stored only for the detector rows the
 // backprojector can reach, [v_lo, v_hi], in a zero-padded layout
-// [angle][1 + (v_hi - v_lo + 1) + 2][1 + n_u + 2]: one zero row / column
-// before and two after, so bilinear taps need no bounds tests.
+// [angle][1 + (v_hi - v_lo + 1) + 2][1 + n_u + 2] of (value, next value -
+// value) pairs: one zero row / column before and two after, so bilinear taps
+// need no bounds tests and a tap pair is one 8-byte load.
 struct FdkParams {
     DevGeom g;
     const float2 *trig;
@@ -286,9 +287,9 @@ cudaError_t launch_blur_transpose(const BlurParams &p, const float *gin, float *
                                   float *gout, int n_img, cudaStream_t s);
 cudaError_t launch_poisson(const float *lam, float *out, int n_img, int n_v, int n_u,
                            int angle0, uint64_t seed, cudaStream_t s);
-cudaError_t launch_fdk_filter(const FdkParams &p, const float *counts, float *filt,
+cudaError_t launch_fdk_filter(const FdkParams &p, const float *counts, float2 *filt,
                               cudaStream_t s);
-cudaError_t launch_backproject(const FdkParams &p, const float *filt, double *vol, int variant,
+cudaError_t launch_backproject(const FdkParams &p, const float2 *filt, double *vol, int variant,
                                cudaStream_t s);
 cudaError_t launch_hu(const DevGeom &g, const double *vol, float *hu, double *partials,
                       float radius, int zcut, cudaStream_t s);

@@ -66,21 +66,19 @@ def test_variants_thin_slab(fc, orc, nz):
     vref = orc.fdk(g, counts.astype(np.float64), orc.i_flood(wl.n0, wl.spr))
     scale = float(np.max(np.abs(vref)))
     vols = {}
-    for req in (fc.FC_BP_AUTO, fc.FC_BP_SLAB, fc.FC_BP_SLAB_STAGED, fc.FC_BP_CHUNKED,
-                fc.FC_BP_CHUNKED_DENSE):
+    for req in (fc.FC_BP_AUTO, fc.FC_BP_SLAB, fc.FC_BP_CHUNKED, fc.FC_BP_CHUNKED_DENSE):
         vol, used = _recon(fc, wl, counts, req)
         if req == fc.FC_BP_AUTO:
-            assert used in (fc.FC_BP_SLAB, fc.FC_BP_SLAB_STAGED)
+            assert used == fc.FC_BP_SLAB
         else:
             assert used == req
         err = np.max(np.abs(vol - vref))
         assert err <= MU_TOL * scale, (req, err / scale)
         vols[req] = vol
-    # the slab kernels repeat the chunked kernel's per-slice arithmetic (the
-    # reciprocal of U rounded differently); staging does not change a bit
+    # the slab kernel repeats the chunked kernel's per-slice arithmetic (the
+    # v coordinate of a slice formed from another origin)
     d = np.max(np.abs(vols[fc.FC_BP_SLAB] - vols[fc.FC_BP_CHUNKED]))
     assert d <= 1e-5 * scale, d / scale
-    assert np.array_equal(vols[fc.FC_BP_SLAB], vols[fc.FC_BP_SLAB_STAGED])
 
 
 def fc_step(g):
@@ -168,12 +166,9 @@ def test_full_paper_mv_reconstruct_variants(fc, orc, precision):
     mu_w = float(np.mean(vref[W.water_roi_mask(g)]))
     counts = torch.full((g.n_angles, g.n_v, g.n_u), flood, dtype=torch.float32, device="cuda")
     counts[:, r0:r0 + crop] = torch.from_numpy(band).cuda()
-    for req in (fc.FC_BP_AUTO, fc.FC_BP_SLAB, fc.FC_BP_SLAB_STAGED, fc.FC_BP_CHUNKED_DENSE):
+    for req in (fc.FC_BP_AUTO, fc.FC_BP_CHUNKED_DENSE):
         vol, used = _recon(fc, wl, counts, req, lab=np.zeros((g.nz, g.ny, g.nx), np.uint8))
-        if req == fc.FC_BP_AUTO:
-            assert used in (fc.FC_BP_SLAB, fc.FC_BP_SLAB_STAGED)
-        else:
-            assert used == req
+        assert used == (fc.FC_BP_SLAB if req == fc.FC_BP_AUTO else req)
         err = np.max(np.abs(vol - vref))
         precision("mu (FDK)", "paper_mv every voxel, %s" % fc.FC_BP_NAMES[used], err / mu_w, MU_TOL,
                   "of mu_water")
