@@ -881,6 +881,9 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--workload", default=WORKLOAD, choices=sorted(W.WORKLOADS))
+    ap.add_argument("--angles", type=int, default=None,
+                    help="profile a smaller case: the workload's first N projections (same "
+                         "angular step); the bench line then names the reduced workload")
     ap.add_argument("--cpu-angles", type=int, default=64,
                     help="projections in the oracle CPU-baseline sample")
     ap.add_argument("--ref-angles", type=int, default=8,
@@ -900,6 +903,15 @@ def main(argv=None):
         args.steps = 50 if args.impl == "reference" else 300
     if args.steps < 1:
         ap.error("--steps must be >= 1")
+    if args.angles is not None:
+        base = W.WORKLOADS[args.workload]
+        if not 1 <= args.angles <= base.geom.n_angles:
+            ap.error("--angles must be in [1, %d]" % base.geom.n_angles)
+        name = "%s_%da" % (args.workload, args.angles)
+        W.WORKLOADS[name] = dataclasses.replace(
+            W.scaled(base, n_angles=args.angles, arc=base.geom.arc * args.angles / base.geom.n_angles),
+            name=name)
+        args.workload = name
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

@@ -153,7 +153,11 @@ cudaError_t launch_fdk_filter(const FdkParams &p, const float *counts, float2 *f
         if (e != cudaSuccess) return e;
     }
     const size_t blocks = (size_t)p.g.n_angles * nrows;
-    k_fdk_filter<<<(unsigned)blocks, kFiltThreads, smem, s>>>(p, counts, filt);
+    // one thread per 16 outputs of the row (whole warps, at most kFiltThreads):
+    // short rows leave no idle warps in the CTA
+    int threads = ((p.g.n_u + kFiltOut - 1) / kFiltOut + 31) / 32 * 32;
+    threads = threads > kFiltThreads ? kFiltThreads : threads;
+    k_fdk_filter<<<(unsigned)blocks, threads, smem, s>>>(p, counts, filt);
     return cudaGetLastError();
 }
 
