@@ -269,11 +269,9 @@ def _kernel_models(wl):
     }
 
 
-def _ncu_record(kernel, workload=None):
-    """ncu record of a kernel from profiles/ncu_traffic.json (DRAM bytes and
-    warp instructions per launch, the workload they were taken on), or None
-    when absent, taken from a different source revision of the kernel, or
-    (with `workload` given) on another workload."""
+def _ncu_record(kernel):
+    """ncu record of a kernel from profiles/ncu_traffic.json, or None when
+    absent or taken from a different source revision of the kernel."""
     p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     if not os.path.exists(p):
         return None
@@ -286,19 +284,16 @@ def _ncu_record(kernel, workload=None):
         return None
     if hashlib.sha256(open(src, "rb").read()).hexdigest()[:16] != ent.get("source_sha"):
         return None
-    if workload is not None and ent.get("workload") not in (None, workload):
-        return None
     return ent
 
 
-def _traffic(kernel, workload=None):
-    """ncu DRAM bytes per launch (see _ncu_record), scaled from the captured
-    launch to the bench's by `scale` in the record (units of work per
-    launch: the bench launch's over the captured one's)."""
-    ent = _ncu_record(kernel, workload)
-    if not ent:
+def _traffic(kernel, workload):
+    """ncu DRAM bytes (read + write) of one launch of `kernel` on `workload`,
+    or None when not recorded for this source and workload."""
+    ent = _ncu_record(kernel)
+    if not ent or not ent.get("dram") or ent["dram"].get("workload") != workload:
         return None
-    return ent.get("dram_bytes_per_launch")
+    return ent["dram"].get("bytes_per_launch")
 
 
 # ------------------------------------------------------------------ oracle arm
@@ -629,8 +624,8 @@ def _extras(args, fc, torch, n_sm, mhz):
             r = surrogate_study.run(steps=args.surrogate_steps, verbose=False)
             return {"workload": "head_surrogate: 256^3 voxels, 360 projections of 512x512, "
                                 "120 bins, %d rays" % r["rays"],
-                    "train": r["train"], "accuracy": r["accuracy"], "speed_ms": r["speed_ms"],
-                    "crossover_bins": r["crossover_bins"]}
+                    "train": r["train"], "accuracy": r["accuracy"], "guard": r["guard"],
+                    "speed_ms": r["speed_ms"], "crossover_bins": r["crossover_bins"]}
         jobs.append(("surrogate", sur))
     if args.extra:
         jobs = [j for j in jobs if j[0] in args.extra]
@@ -692,16 +687,18 @@ def _issue(kernel, wl, units, seconds, n_sm, mhz):
     (ncu record for the current source on this workload family, scaled by
     units of work) over n_SM x 4 schedulers x clock x time."""
     ent = _ncu_record(kernel)
-    if not ent or not ent.get("warp_inst_per_launch") or not ent.get("units_per_launch"):
+    rec = ent.get("inst") if ent else None
+    if not rec or not rec.get("warp_inst_per_launch") or not rec.get("units_per_launch"):
         return None
-    if ent.get("workload_family") not in (None, wl.name):
+    if not rec.get("workload", "").startswith(wl.name):
         return None
-    inst = ent["warp_inst_per_launch"] * units / ent["units_per_launch"]
+    inst = rec["warp_inst_per_launch"] * units / rec["units_per_launch"]
     peak = n_sm * 4 * mhz * 1e6
     return {"warp_inst_per_step": inst, "achieved_warp_inst_per_s": inst / seconds,
             "peak_warp_inst_per_s": peak, "frac": inst / seconds / peak,
-            "lanes_active_per_inst": ent.get("lanes_active_per_inst"),
-            "source": "ncu sm__inst_executed of %s, scaled by %s" % (ent.get("workload"), ent.get("units"))}
+            "lanes_active_per_inst": rec.get("lanes_active_per_inst"),
+            "source": "ncu smsp__inst_executed.sum on %s, scaled by %s" % (rec.get("workload"),
+                                                                          rec.get("units"))}
 
 
 def _roofline(wl, kernels, peaks, peak_src, n_sm, mhz):
@@ -723,12 +720,9 @@ def _roofline(wl, kernels, peaks, peak_src, n_sm, mhz):
         achieved = m["bytes"] / per_s / 1e9
         unit = "GB/s"
         peak_note = "HBM copy bandwidth (%s)" % peak_src
-    ent = _ncu_record(top)
-    traffic = None
-    if ent and ent.get("dram_bytes_per_launch") and ent.get("workload_family") in (None, wl.name):
-        traffic = ent["dram_bytes_per_launch"] * ent.get("scale_to_bench", 1.0)
+    traffic = _traffic(top, wl.name)
     return {"kernel": top, "bound": m["bound"], "achieved": achieved, "peak": peak, "unit": unit,
-            "frac": achieved / peak, "traffic": (traffic / launches if traffic else None),
+            "frac": achieved / peak, "traffic": traffic,
             "peak_source": peak_note,
             "algorithmic": {"bytes_per_launch": m["bytes"] / launches,
                             "flops_per_launch": (m["flops"] / launches if m["flops"] else None)}}

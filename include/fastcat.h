@@ -387,11 +387,27 @@ int fc_surrogate_get(fc_handle *h, float *state);
 int fc_surrogate_set(fc_handle *h, const float *state);
 
 /* ln T of n rays from their path lengths by the surrogate, falling back to
- * the exact energy sum for rays outside the training box; *n_fallback (host,
+ * the exact energy sum for rays outside the training box (and, with a guard
+ * set, for rays attenuated beyond its threshold); *n_fallback (host,
  * may be NULL; non-NULL synchronises the stream) receives how many fell
  * back.  Errors: FC_ESTATE, FC_EINVAL, FC_ETIMEOUT, FC_ECUDA. */
 int fc_surrogate_eval(fc_handle *h, const float *L, int64_t n, float *lnT, int64_t *n_fallback,
                       void *stream);
+
+/* Per-ray guard of the surrogate, judged by the exact energy sum: from n
+ * rays with path lengths L and exact ln T (device, e.g. the training data),
+ * evaluate the network alone, take the smallest baseline attenuation
+ * -ln sum_k a_k exp(-sum_m mu_km L_m) among the rays whose |ln T error|
+ * exceeds tol, and from then on have fc_surrogate_eval (and
+ * fc_surrogate_project) evaluate every ray attenuated at least that much
+ * with the exact sum (counted in *n_fallback).  *threshold (host, may be
+ * NULL) receives it; +inf when no ray exceeded tol.  tol <= 0 removes the
+ * guard.  The guard belongs to the handle, not to the
+ * fc_surrogate_get/set state: set it again after fc_surrogate_set.
+ * Instrumentation of the learned surrogate (the paper has no counterpart).
+ * Errors: FC_ESTATE, FC_EINVAL, FC_ETIMEOUT, FC_ENOMEM, FC_ECUDA. */
+int fc_surrogate_guard(fc_handle *h, const float *L, const float *lnT, int64_t n, double tol,
+                       double *threshold, void *stream);
 
 /* Projection with the surrogate in place of the energy loop: the
  * projector's path lengths for projections angle_begin .. + angle_count - 1

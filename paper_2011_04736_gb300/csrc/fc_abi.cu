@@ -159,6 +159,7 @@ struct fc_handle {
     double *d_cnr_work = nullptr;   // CNR stage partials
     // learned surrogate of the energy integral
     bool has_sur = false, sur_fitted = false;
+    double sur_guard = INFINITY;   // fc_surrogate_guard threshold (baseline attenuation)
     int sur_step = 0;
     float *d_P = nullptr, *d_m1 = nullptr, *d_m2 = nullptr, *d_grad = nullptr;
     __nv_bfloat16 *d_W1b = nullptr, *d_W2b = nullptr, *d_W3b = nullptr, *d_W2Tb = nullptr,
@@ -1269,6 +1270,7 @@ static void fill_sur_params(fc_handle *h, fc::SurrogateParams *p)
     p->P = h->d_P;
     p->n_mat = h->n_mat;
     p->n_e = h->n_e;
+    p->guard = (float)h->sur_guard;
     for (int e = 0; e < h->n_e; ++e) {
         p->wd[e] = h->wd[e];
         for (int m = 0; m < fc::kMaxMat; ++m) p->mu2[e][m] = h->mu2[(size_t)e * fc::kMaxMat + m];
@@ -1588,6 +1590,49 @@ int fc_surrogate_eval(fc_handle *h, const float *L, int64_t n, float *lnT, int64
         *n_fallback = c;
         return sur_read_err(h, s, "fc_surrogate_eval");
     }
+    return FC_OK;
+}
+
+int fc_surrogate_guard(fc_handle *h, const float *L, const float *lnT, int64_t n, double tol,
+                       double *threshold, void *stream)
+{
+    if (!h) return fail(FC_EINVAL, "fc_surrogate_guard: null handle");
+    if (!(tol > 0.0)) {
+        h->sur_guard = INFINITY;
+        if (threshold) *threshold = INFINITY;
+        return FC_OK;
+    }
+    int rc = sur_check_data(h, "fc_surrogate_guard", L, lnT, true, n);
+    if (rc) return rc;
+    DeviceGuard dgd(h->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    float *ys = nullptr;
+    FC_CK(dev_malloc((void **)&ys, (size_t)n * sizeof(float)));
+    fc::SurrogateParams p;
+    fill_sur_params(h, &p);
+    p.guard = INFINITY;                            // the network alone
+    // best = 0x7fffffff (bytes ff ff ff 7f): no ray beyond tol yet
+    cudaError_t e = cudaMemsetAsync(h->d_cnt, 0xff, sizeof(int), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(reinterpret_cast<char *>(h->d_cnt) + 3, 0x7f, 1, s);
+    if (e == cudaSuccess) e = fc::launch_mlp_eval(p, L, n, ys, h->d_cnt + 1, h->d_err, s);
+    if (e == cudaSuccess)
+        e = fc::launch_guard_scan(p, L, lnT, ys, n, (float)tol, reinterpret_cast<int *>(h->d_cnt), s);
+    int best = 0x7fffffff;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&best, h->d_cnt, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(ys);
+    FC_CK(e);
+    rc = sur_read_err(h, s, "fc_surrogate_guard");
+    if (rc) return rc;
+    if (best == 0x7fffffff) {
+        h->sur_guard = INFINITY;
+    } else {
+        const int bits = best >= 0 ? best : best ^ 0x7fffffff;
+        float v;
+        memcpy(&v, &bits, sizeof(v));
+        h->sur_guard = v;
+    }
+    if (threshold) *threshold = h->sur_guard;
     return FC_OK;
 }
 

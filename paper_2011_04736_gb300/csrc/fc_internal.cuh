@@ -205,6 +205,7 @@ struct SurrogateParams {
     const __nv_bfloat16 *W2Tb, *W3Tb;  // [in][out]
     const float *P;             // packed fp32 parameters
     int n_mat, n_e;
+    float guard;                // rays whose baseline attenuation reaches it are evaluated exactly
     float wd[kMaxBins];
     float mu2[kMaxBins][kMaxMat];
 };
@@ -223,6 +224,11 @@ cudaError_t launch_mlp_eval(const SurrogateParams &p, const float *L, long long 
                             unsigned int *n_fallback, int *err, cudaStream_t s);
 cudaError_t launch_energy_sum_lengths(const SurrogateParams &p, const float *L, long long n,
                                       float *lnT, cudaStream_t s);
+// Smallest baseline attenuation among the rays whose surrogate ln T (ys)
+// misses the exact y by more than tol, as an order-preserving integer
+// atomically minimised into *best (set it to 0x7fffffff first).
+cudaError_t launch_guard_scan(const SurrogateParams &p, const float *L, const float *y,
+                              const float *ys, long long n, float tol, int *best, cudaStream_t s);
 cudaError_t launch_exp(const float *x, float *y, long long n, cudaStream_t s);
 cudaError_t launch_mlp_lmax(const float *L, long long n, int n_mat, unsigned int *mx,
                             cudaStream_t s);

@@ -318,7 +318,9 @@ k_mlp_eval(const __grid_constant__ SurrogateParams p, const float *__restrict__ 
         }
         if (valid) {
             float y = ylin + res;
-            if (outside) {
+            // outside the training box, or attenuated as strongly as a ray
+            // the guard saw miss the tolerance: the exact sum decides
+            if (outside || -ylin >= p.guard) {
                 y = exact_lnT(Lr, p.wd, p.mu2, p.n_e);
                 ++my_fallback;
             }
@@ -332,6 +334,41 @@ k_mlp_eval(const __grid_constant__ SurrogateParams p, const float *__restrict__ 
     tc::fence_before_sync();
     __syncthreads();
     if (r < 32) tc::tmem_dealloc(tb, 128);
+}
+
+// Order-preserving integer image of a float (smaller float, smaller int).
+__device__ __forceinline__ int ordered_int(float v)
+{
+    const int b = __float_as_int(v);
+    return b >= 0 ? b : b ^ 0x7fffffff;
+}
+
+__global__ void __launch_bounds__(256)
+k_guard_scan(const __grid_constant__ SurrogateParams p, const float *__restrict__ L,
+             const float *__restrict__ y, const float *__restrict__ ys, long long n, float tol,
+             int *best)
+{
+    int mine = 0x7fffffff;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        if (!(fabsf(ys[i] - y[i]) > tol)) continue;
+        float Lr[kMaxMat];
+#pragma unroll
+        for (int m = 0; m < kMaxMat; ++m) Lr[m] = m < p.n_mat ? L[i * p.n_mat + m] : 0.0f;
+        mine = min(mine, ordered_int(-group_base(Lr, p.P + kOffGa)));
+    }
+    for (int o = 16; o > 0; o >>= 1) mine = min(mine, __shfl_xor_sync(0xffffffffu, mine, o));
+    if ((threadIdx.x & 31) == 0 && mine != 0x7fffffff) atomicMin(best, mine);
+}
+
+cudaError_t launch_guard_scan(const SurrogateParams &p, const float *L, const float *y,
+                              const float *ys, long long n, float tol, int *best, cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    long long blocks = (n + 255) / 256;
+    if (blocks > sm_count() * 8) blocks = sm_count() * 8;
+    k_guard_scan<<<(int)blocks, 256, 0, s>>>(p, L, y, ys, n, tol, best);
+    return cudaGetLastError();
 }
 
 // Exact ln T of each ray from its path lengths (the plain energy-sum path).

@@ -35,7 +35,8 @@ ENTRY_POINTS = ("fc_create", "fc_destroy", "fc_last_error", "fc_set_geometry", "
                 "fc_energy_sum_lengths", "fc_cnr_grad", "fc_surrogate_project",
                 "fc_dose_estimate", "fc_fluence_for_dose", "fc_set_noise_order",
                 "fc_set_energy_groups", "fc_deconvolve_rl", "fc_detector_mtf",
-                "fc_set_backprojector", "fc_backprojector_in_use", "fc_inject_fault")
+                "fc_set_backprojector", "fc_backprojector_in_use", "fc_inject_fault",
+                "fc_surrogate_guard")
 FC_STATIC_SCRATCH_FLOATS = 8 << 20
 FC_SURROGATE_PARAMS = 34305
 FC_SURROGATE_STATE = 34305 + 52 + 2 * 34305 + 1
@@ -127,6 +128,7 @@ def load():
         "fc_set_backprojector": (I, [P, I]),
         "fc_backprojector_in_use": (I, [P, ctypes.POINTER(I)]),
         "fc_inject_fault": (I, [I, ctypes.c_int64]),
+        "fc_surrogate_guard": (I, [P, P, P, ctypes.c_int64, ctypes.c_double, P, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -411,6 +413,15 @@ def fc_surrogate_eval(h, L, lnT, stream=None, count_fallback=True):
     _check(load().fc_surrogate_eval(h, _dev(L, "L"), lnT.numel(), _dev(lnT, "lnT"),
                                     ctypes.byref(c) if count_fallback else None, _stream(stream)))
     return c.value
+
+
+def fc_surrogate_guard(h, L, lnT, tol, stream=None):
+    """Set the per-ray guard from data (device L [n][n_mat], exact lnT [n]);
+    returns the baseline-attenuation threshold (inf: none)."""
+    thr = ctypes.c_double(0.0)
+    _check(load().fc_surrogate_guard(h, _dev(L, "L"), _dev(lnT, "lnT"), lnT.numel(), float(tol),
+                                     ctypes.byref(thr), _stream(stream)))
+    return thr.value
 
 
 def fc_surrogate_project(h, angle_begin, angle_count, out, stream=None):

@@ -8,6 +8,9 @@ Adam, then reports on all rays:
 
 * accuracy: |ln T_surrogate - ln T_exact| (max, p99.9, p99, mean) and the
   number of rays that fell back to the exact sum;
+* the per-ray guard: the baseline-attenuation threshold set from the
+  training rays whose error exceeds 1e-3, the fraction of all rays it sends
+  to the exact sum, and the error left on every ray;
 * speed: energy stage alone (exact energy sum from L vs surrogate from L)
   and whole projection (projector with fused exact sum vs path-length
   emission + surrogate), CUDA events on the launching stream;
@@ -28,7 +31,7 @@ from . import workloads as W
 
 
 def run(steps=20000, batch=65536, n_train=1 << 24, lr=2e-3, workload="head_surrogate",
-        chunk_angles=40, verbose=True):
+        chunk_angles=40, guard_tol=1e-3, verbose=True):
     import torch
     from . import fastcat as fc
     fc.load()
@@ -76,12 +79,27 @@ def run(steps=20000, batch=65536, n_train=1 << 24, lr=2e-3, workload="head_surro
                            "p99_abs_dlnT": q[0], "mean_abs_dlnT": float(err.mean()),
                            "fallback_rays": int(nfb),
                            "rays_within_1e-3": float((err <= 1e-3).float().mean())}
+        # per-ray guard judged by the exact sum: threshold from the training
+        # set (rays whose error exceeds 1e-3 there), then every ray again
+        thr = fc.fc_surrogate_guard(h, Lt, yt, guard_tol, stream)
+        nfb_g = fc.fc_surrogate_eval(h, L, ys, stream)
+        torch.cuda.synchronize()
+        err_g = (ys - y).abs()
+        out["guard"] = {"tol": guard_tol, "threshold_baseline_attenuation": thr,
+                        "fallback_rays": int(nfb_g), "fallback_fraction": nfb_g / n,
+                        "max_abs_dlnT": float(err_g.max()),
+                        "rays_within_tol": float((err_g <= guard_tol).float().mean()),
+                        "rays_beyond_tol": int((err_g > guard_tol).sum())}
         # speed (library CUDA-event tracer, per kernel): energy stage alone,
         # and projector with the fused exact sum vs path-length emission +
         # surrogate
         T = torch.empty((chunk_angles, g.n_v, g.n_u), dtype=torch.float32, device="cuda")
         reps = 3
         fc.fc_profile_enable(h, True)
+        for _ in range(reps):
+            fc.fc_surrogate_eval(h, L, ys, stream, count_fallback=False)
+        t_guarded = fc.fc_profile_read(h)["surrogate_eval"][0] / reps
+        fc.fc_surrogate_guard(h, Lt, yt, 0.0, stream)        # the network alone
         for _ in range(reps):
             fc.fc_energy_sum_lengths(h, L, y, stream)
             fc.fc_surrogate_eval(h, L, ys, stream, count_fallback=False)
@@ -98,6 +116,8 @@ def run(steps=20000, batch=65536, n_train=1 << 24, lr=2e-3, workload="head_surro
         t_len = kt["lengths"][0] / reps
         out["speed_ms"] = {"energy_exact": t_exact, "energy_surrogate": t_sur,
                            "energy_speedup": t_exact / t_sur,
+                           "energy_surrogate_guarded": t_guarded,
+                           "energy_speedup_guarded": t_exact / t_guarded,
                            "project_exact_fused": t_proj, "project_lengths_only": t_len,
                            "project_surrogate": t_len + t_sur,
                            "project_speedup": t_proj / (t_len + t_sur)}

@@ -64,17 +64,20 @@ def test_traffic_record_is_ignored_once_the_source_changes(tmp_path, monkeypatch
     (tmp_path / "profiles").mkdir()
     (src / "k.cu").write_text("kernel v1\n")
     sha = hashlib.sha256(b"kernel v1\n").hexdigest()[:16]
-    rec = {"kernels": {"noise": {"source": "k.cu", "source_sha": sha, "dram_bytes_per_launch": 123}}}
+    rec = {"kernels": {"noise": {"source": "k.cu", "source_sha": sha,
+                                 "dram": {"workload": "catphan_kv", "bytes_per_launch": 123}}}}
     (tmp_path / "profiles" / "ncu_traffic.json").write_text(json.dumps(rec))
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
-    assert bench._traffic("noise") == 123
-    assert bench._traffic("project") is None
+    assert bench._traffic("noise", "catphan_kv") == 123
+    assert bench._traffic("noise", "paper_mv") is None        # another workload
+    assert bench._traffic("project", "catphan_kv") is None
     (src / "k.cu").write_text("kernel v2\n")
-    assert bench._traffic("noise") is None
+    assert bench._traffic("noise", "catphan_kv") is None
 
 
 def test_committed_traffic_record_names_existing_sources():
     rec = json.load(open(os.path.join(bench.ROOT, "profiles", "ncu_traffic.json")))
     for name, ent in rec["kernels"].items():
         assert os.path.exists(os.path.join(bench.ROOT, "paper_2011_04736_gb300", "csrc", ent["source"])), name
-        assert ent["dram_bytes_per_launch"] > 0
+        assert ent["dram"]["bytes_per_launch"] > 0
+        assert ent["inst"]["warp_inst_per_launch"] > 0 and ent["inst"]["units_per_launch"] > 0

@@ -74,7 +74,36 @@ def test_energy_sum_lengths_matches_oracle(fc, orc):
     assert np.max(np.abs(got - T) / T) <= 1e-4
 
 
-def test_surrogate_eval_matches_oracle(fc, orc):
+# Error model of the tensor-core evaluation against the float64 oracle with
+# the same bf16 weights (both multiply bf16(W)):
+#   inputs and activations carried as bf16 hi + lo: |x - (hi + lo)| <= 2^-17 |x|;
+#   sigma(z) = (1 + tanh.approx(z / 2)) / 2 on the MUFU: relative error of
+#   tanh.approx <= 2^-10.9, so |d SiLU| <= |z| 2^-11.9 |tanh(z / 2)|;
+#   binary32 accumulation over 128 terms: <= 2^-16 sum |w_j h_j| (loose);
+#   the four-group baseline with __expf / __logf: <= 2e-6 absolute.
+# Propagated layer by layer with |W| (elementwise absolute values) and
+# |SiLU'| <= 1.1, this gives a per-ray bound on |ln T_gpu - ln T_oracle|.
+def _eval_bound(mlp, P, cache):
+    p = mlp.unpack(P)
+    W1, W2, W3 = (np.abs(mlp.bf16(p[k])) for k in ("W1", "W2", "W3"))
+    split, tanh_rel, acc_rel = 2.0 ** -17, 2.0 ** -10.9, 2.0 ** -16
+
+    def act_err(z, dz_in):
+        t = np.abs(np.tanh(0.5 * z))
+        return 1.1 * dz_in + np.abs(z) * 0.5 * tanh_rel * t
+
+    x = cache["x"]
+    dz1 = np.abs(x) @ W1.T * split + acc_rel * (np.abs(x) @ W1.T)
+    dh1 = act_err(cache["z1"], dz1) + split * np.abs(cache["h1"])
+    dz2 = dh1 @ W2.T + acc_rel * (np.abs(cache["h1"]) @ W2.T)
+    dh2 = act_err(cache["z2"], dz2) + split * np.abs(cache["h2"])
+    dz3 = dh2 @ W3.T + acc_rel * (np.abs(cache["h2"]) @ W3.T)
+    dh3 = act_err(cache["z3"], dz3)
+    w4 = np.abs(p["w4"])
+    return dh3 @ w4 + acc_rel * (np.abs(cache["h3"]) @ w4) + 2e-6
+
+
+def test_surrogate_eval_matches_oracle(fc, orc, precision):
     from oracle import mlp
     wl = _head_small()
     lab = wl.make_phantom()
@@ -90,14 +119,18 @@ def test_surrogate_eval_matches_oracle(fc, orc):
     finally:
         sc.close()
     assert nfb == 0
-    ref, cache = mlp.forward(st[:mlp.N_PACKED].astype(np.float64), L.astype(np.float32))
+    P = st[:mlp.N_PACKED].astype(np.float64)
+    ref, cache = mlp.forward(P, L.astype(np.float32))
     got = out.cpu().numpy()
-    # bf16 activations (relative 2^-9) feeding 128-term sums, tanh-based sigma
-    scale = np.max(np.abs(cache["h3"] @ mlp.unpack(st[:mlp.N_PACKED])["w4"])) + 1.0
-    assert np.max(np.abs(got - ref)) <= 2e-2 * scale, np.max(np.abs(got - ref))
+    bound = _eval_bound(mlp, P, cache)
+    err = np.abs(got - ref)
+    precision("surrogate ln T vs oracle MLP", "%d rays, random weights" % len(L),
+              np.max(err / bound), 1.0, "of the derived per-ray bound")
+    precision("surrogate ln T vs oracle MLP", "same (absolute)", err.max(), float(bound.max()), "abs")
+    assert np.all(err <= bound), (err.max(), np.max(err / bound))
 
 
-def test_surrogate_gradient_matches_oracle(fc, orc):
+def test_surrogate_gradient_matches_oracle(fc, orc, precision):
     from oracle import mlp
     wl = _head_small()
     lab = wl.make_phantom()
@@ -114,13 +147,23 @@ def test_surrogate_gradient_matches_oracle(fc, orc):
         sc.close()
     lref, gref = mlp.loss_and_grad(st[:mlp.N_PACKED].astype(np.float64), L.astype(np.float32),
                                    y.astype(np.float32))
+    precision("surrogate loss vs oracle", "1024 rays, random weights", abs(loss - lref) / lref, 2e-2)
     assert loss == pytest.approx(lref, rel=2e-2)
+    # The errors of the backward pass are those of its inputs: sigma and
+    # SiLU' from tanh.approx (2^-10.9 relative), the residuals and
+    # activations stored as single bf16 values for the weight-gradient GEMMs
+    # (2^-9 relative each), so a gradient entry carries a few 2^-9 relative
+    # error, not systematic in sign: 2e-2 norm-wise per block, cosine >= 0.9995.
+    worst = 0.0
     for name in ("W1", "b1", "W2", "b2", "W3", "b3", "w4", "b4"):
         a, b = mlp.OFF[name]
         ga, gr = g[a:b].astype(np.float64), gref[a:b]
         rel = np.linalg.norm(ga - gr) / max(np.linalg.norm(gr), 1e-30)
         cos = ga @ gr / max(np.linalg.norm(ga) * np.linalg.norm(gr), 1e-30)
-        assert rel <= 5e-2 and cos >= 0.998, (name, rel, cos)
+        worst = max(worst, rel)
+        assert rel <= 2e-2 and cos >= 0.9995, (name, rel, cos)
+    precision("surrogate gradient vs oracle", "1024 rays, worst parameter block", worst, 2e-2,
+              "relative (norm)")
 
 
 @pytest.fixture(scope="module")
@@ -212,3 +255,30 @@ def test_surrogate_project_matches_exact_projection(fc, trained):
     d = (torch.log(Ts) - torch.log(Te)).abs()
     assert float(d.max()) < 1e-2 and float(torch.quantile(d.ravel()[:1 << 20], 0.99)) < 2e-3
     assert np.array_equal(host, Ts[3:5].cpu().numpy())
+
+
+def test_surrogate_guard_judges_every_ray(fc, trained, precision):
+    """The per-ray guard, set from the data with exact ln T: afterwards every
+    ray of that data is within tol (rays the network misses by more are
+    evaluated exactly), the fallback count is reported, and tol <= 0 removes
+    the guard again."""
+    wl, sc, L, y, _ = trained
+    out = torch.empty_like(y)
+    try:
+        fc.fc_surrogate_eval(sc.h, L, out)
+        torch.cuda.synchronize()
+        raw = (out - y).abs()
+        tol = float(torch.quantile(raw[: 1 << 20], 0.9))   # a tolerance the network misses often
+        thr = fc.fc_surrogate_guard(sc.h, L, y, tol)
+        assert np.isfinite(thr)
+        nfb = fc.fc_surrogate_eval(sc.h, L, out)
+        torch.cuda.synchronize()
+        err = (out - y).abs()
+        precision("surrogate ln T, guarded", "small head scan, tol %.1e, %.1f%% of rays exact"
+                  % (tol, 100.0 * nfb / y.numel()), float(err.max()) / tol, 1.0, "of tol")
+        assert float(err.max()) <= tol
+        assert (raw > tol).sum().item() <= nfb < y.numel()
+        assert fc.fc_surrogate_guard(sc.h, L, y, 0.0) == float("inf")
+        assert fc.fc_surrogate_eval(sc.h, L, out) == 0
+    finally:
+        fc.fc_surrogate_guard(sc.h, L, y, 0.0)
