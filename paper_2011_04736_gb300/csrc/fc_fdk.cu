@@ -14,7 +14,7 @@
 // in a zero-padded layout so the bilinear taps need no bounds tests.
 // Backprojection: one thread per (x, y) column and chunk of z; per angle
 // the column's detector abscissa and weight are computed once and the z
-// loop walks the detector column linearly.  Partial sums over 64 angles are
+// loop walks the detector column linearly.  Partial sums over 256 angles are
 // kept in binary32 and folded into binary64 accumulators.
 #include <math.h>
 
@@ -242,7 +242,7 @@ void fdk_row_range(const DevGeom &g, int *v_lo, int *v_hi)
 }
 
 namespace {
-constexpr int kFold = 64;        // angles per binary32 partial sum
+constexpr int kFold = 256;       // angles per binary32 partial sum
 // floor(v) of 0 <= v < 2^22 as the low bits of v + 2^23 rounded toward -inf
 constexpr float kTwo23 = 8388608.0f;
 constexpr int kSlabMaxNz = 16;   // slices the thin-slab kernel keeps per thread

@@ -73,10 +73,11 @@ __device__ __forceinline__ int band_t() { return (int)blockIdx.x * kBandCta + (i
 
 // Per-material path lengths L of pixel ray (iu, iv) of projection k; returns
 // whether the ray meets the voxel box.  TEST_ONLY: return after the box test
-// (L not computed).
-template <bool TEST_ONLY = false>
+// (L not computed).  SMEM_BRICKS: the brick map is read from the CTA's
+// shared-memory copy sb instead of global memory.
+template <bool TEST_ONLY = false, bool SMEM_BRICKS = false>
 __device__ __forceinline__ bool trace_ray(const ProjParams &p, int iu, int iv, int k,
-                                          float (&L)[kMaxMat])
+                                          float (&L)[kMaxMat], const uint8_t *sb = nullptr)
 {
     const DevGeom &g = p.g;
 #pragma unroll
@@ -161,7 +162,7 @@ __device__ __forceinline__ bool trace_ray(const ProjParams &p, int iu, int iv, i
             for (int cb = nbx + nby + nbz + 3; cb > 0; --cb) {
                 const float tmin = fminf(tcx, fminf(tcy, tcz));
                 const float t_exit = fmaxf(tmin, t_cur);
-                const int bl = __ldg(p.bricks + bi);
+                const int bl = SMEM_BRICKS ? (int)sb[bi] : (int)__ldg(p.bricks + bi);
                 if (bl != kMixed) {
                     if (bl != cur) {
                         add_run(L, cur, t_cur - t_run);
@@ -280,14 +281,32 @@ __device__ __forceinline__ float energy_T(const ProjParams &p, bool hit, const f
 // a queue in shared memory (one aggregated append per warp); phase 2 hands
 // the queue out to the warps 32 rays at a time, so every lane walks a ray
 // that meets the voxels.  T of a ray does not depend on which thread traces
-// it.
+// it.  The brick map (one byte per 8 x 8 x 16 voxels: 16 KB for 1024^2 x 16
+// voxels) is copied into shared memory by every CTA when it fits, so the
+// walk's coarse steps read it there; the labels of mixed bricks stay in
+// L2 / L1 (the whole label volume of the thin slab is 10 MB, resident in L2).
 constexpr int kCompact = 2048;
+constexpr int kSmemBricks = 16384;   // largest brick map staged in shared memory
+
+__device__ __forceinline__ bool stage_bricks(const ProjParams &p, uint8_t *sb, int tid)
+{
+    const DevGeom &g = p.g;
+    const int nb = ((g.nx + kBrick - 1) / kBrick) * ((g.ny + kBrick - 1) / kBrick) *
+                   ((g.nz + kBrickZ - 1) / kBrickZ);
+    if (nb > kSmemBricks) return false;
+    const int n16 = nb / 16;   // the map is a cudaMalloc allocation: 16-byte aligned
+    for (int i = tid; i < n16; i += 256)
+        reinterpret_cast<uint4 *>(sb)[i] = __ldg(reinterpret_cast<const uint4 *>(p.bricks) + i);
+    for (int i = n16 * 16 + tid; i < nb; i += 256) sb[i] = __ldg(p.bricks + i);
+    return true;
+}
 
 __global__ void __launch_bounds__(256)
 k_project_compact(const __grid_constant__ ProjParams p, float *__restrict__ T, int r0, int R)
 {
     __shared__ int queue[kCompact];
     __shared__ int q_len, q_head;
+    __shared__ __align__(16) uint8_t sb[kSmemBricks];
     const DevGeom &g = p.g;
     const int tid = threadIdx.y * 32 + threadIdx.x, lane = threadIdx.x;
     const int kl = blockIdx.z;
@@ -297,6 +316,7 @@ k_project_compact(const __grid_constant__ ProjParams p, float *__restrict__ T, i
         q_len = 0;
         q_head = 0;
     }
+    const bool smem_bricks = stage_bricks(p, sb, tid);
     __syncthreads();
     for (int c = tid; c < kCompact; c += 256) {       // a warp takes 32 consecutive rays
         int iu = 0, iv = 0;
@@ -322,7 +342,8 @@ k_project_compact(const __grid_constant__ ProjParams p, float *__restrict__ T, i
             int iu, iv;
             band_ray(queue[i], r0, R, g.n_u, iu, iv);
             float L[kMaxMat];
-            const bool hit = trace_ray<false>(p, iu, iv, k, L);
+            const bool hit = smem_bricks ? trace_ray<false, true>(p, iu, iv, k, L, sb)
+                                         : trace_ray<false>(p, iu, iv, k, L);
             T[((size_t)k * g.n_v + iv) * g.n_u + iu] = energy_T(p, hit, L);
         }
     }
