@@ -409,6 +409,15 @@ int fc_surrogate_eval(fc_handle *h, const float *L, int64_t n, float *lnT, int64
 int fc_surrogate_guard(fc_handle *h, const float *L, const float *lnT, int64_t n, double tol,
                        double *threshold, void *stream);
 
+/* The logistic function sigma(z) = 1 / (1 + exp(-z)) of the surrogate's SiLU
+ * activations, evaluated on the GPU exactly as its kernels evaluate it
+ * (binary32, (1 + tanh(z / 2)) / 2 with the hardware tanh approximation), for
+ * n values z (device) into sigma (device; may alias z).  Lets a test measure
+ * the activations' error against the exact function (no handle; runs on
+ * the current device).  Errors: FC_EINVAL (n < 0, NULL pointer with n > 0),
+ * FC_ECUDA. */
+int fc_surrogate_sigma(const float *z, float *sigma, int64_t n, void *stream);
+
 /* Projection with the surrogate in place of the energy loop: the
  * projector's path lengths for projections angle_begin .. + angle_count - 1
  * are fed to the surrogate and T = exp(ln T) of every ray is written to out

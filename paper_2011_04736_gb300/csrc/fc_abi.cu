@@ -1636,6 +1636,14 @@ int fc_surrogate_guard(fc_handle *h, const float *L, const float *lnT, int64_t n
     return FC_OK;
 }
 
+int fc_surrogate_sigma(const float *z, float *sigma, int64_t n, void *stream)
+{
+    if (n < 0) return fail(FC_EINVAL, "fc_surrogate_sigma: n = %lld < 0", (long long)n);
+    if (n > 0 && (!z || !sigma)) return fail(FC_EINVAL, "fc_surrogate_sigma: NULL pointer");
+    FC_CK(fc::launch_sigma_probe(z, sigma, n, (cudaStream_t)stream));
+    return FC_OK;
+}
+
 int fc_surrogate_project(fc_handle *h, int angle_begin, int angle_count, float *out, int out_where,
                          void *stream)
 {

@@ -229,6 +229,7 @@ cudaError_t launch_energy_sum_lengths(const SurrogateParams &p, const float *L, 
 // atomically minimised into *best (set it to 0x7fffffff first).
 cudaError_t launch_guard_scan(const SurrogateParams &p, const float *L, const float *y,
                               const float *ys, long long n, float tol, int *best, cudaStream_t s);
+cudaError_t launch_sigma_probe(const float *z, float *s, long long n, cudaStream_t st);
 cudaError_t launch_exp(const float *x, float *y, long long n, cudaStream_t s);
 cudaError_t launch_mlp_lmax(const float *L, long long n, int n_mat, unsigned int *mx,
                             cudaStream_t s);

@@ -53,16 +53,16 @@ __device__ __forceinline__ float tanh_fast(float x)
     return y;
 }
 
-// SiLU(z) = z sigma(z), sigma(z) = (1 + tanh(z / 2)) / 2
-__device__ __forceinline__ float silu(float z)
-{
-    return z * fmaf(0.5f, tanh_fast(0.5f * z), 0.5f);
-}
+// sigma(z) = (1 + tanh(z / 2)) / 2, the logistic function
+__device__ __forceinline__ float sigma_fast(float z) { return fmaf(0.5f, tanh_fast(0.5f * z), 0.5f); }
+
+// SiLU(z) = z sigma(z)
+__device__ __forceinline__ float silu(float z) { return z * sigma_fast(z); }
 
 // d SiLU / dz = sigma + z sigma (1 - sigma)
 __device__ __forceinline__ float dsilu(float z)
 {
-    const float s = fmaf(0.5f, tanh_fast(0.5f * z), 0.5f);
+    const float s = sigma_fast(z);
     return fmaf(z * s, 1.0f - s, s);
 }
 
@@ -98,37 +98,62 @@ __device__ __forceinline__ void issue_gemm(uint32_t d, const unsigned char *a, u
     }
 }
 
-// CTA-wide: make shared-memory writes visible to the tensor core and order
-// tensor-memory accesses around the barrier.
-__device__ __forceinline__ void sync_for_mma()
+// Barrier of the threads that share a tile: bar 0 is the whole CTA
+// (__syncthreads), bar > 0 the named barrier of one 128-thread group.
+__device__ __forceinline__ void tile_sync(int bar)
+{
+    if (bar == 0)
+        __syncthreads();
+    else
+        asm volatile("bar.sync %0, 128;" :: "r"(bar) : "memory");
+}
+
+// tile_sync that also returns whether ok holds on every thread of the barrier.
+__device__ __forceinline__ bool tile_sync_and(int bar, bool ok)
+{
+    if (bar == 0) return __syncthreads_and(ok);
+    uint32_t all;
+    asm volatile("{\n\t.reg .pred p, q;\n\t"
+                 "setp.ne.u32 q, %1, 0;\n\t"
+                 "bar.red.and.pred p, %2, 128, q;\n\t"
+                 "selp.u32 %0, 1, 0, p;\n\t}"
+                 : "=r"(all) : "r"((uint32_t)ok), "r"(bar) : "memory");
+    return all != 0;
+}
+
+// Make shared-memory writes visible to the tensor core and order
+// tensor-memory accesses around the barrier of the tile's threads.
+__device__ __forceinline__ void sync_for_mma(int bar = 0)
 {
     tc::fence_async_smem();
     tc::fence_before_sync();
-    __syncthreads();
+    tile_sync(bar);
     tc::fence_after_sync();
 }
 
-// Thread 0 issues a GEMM and commits; everyone waits for it.  Returns false
-// (and records the timeout) if the wait bound is exhausted.
+// The first thread of the tile's group issues a GEMM and commits; the group
+// waits for it.  Returns false (and records the timeout) if the wait bound
+// is exhausted.
 __device__ __forceinline__ bool run_gemm(uint32_t d, const unsigned char *a, uint32_t kgsa,
                                          const unsigned char *b, uint32_t kgsb, int K, int N,
-                                         uint64_t *mbar, uint32_t &phase, int *err)
+                                         uint64_t *mbar, uint32_t &phase, int *err, int bar = 0)
 {
-    if (threadIdx.x == 0) {
+    if ((threadIdx.x & 127) == 0) {
         issue_gemm(d, a, kgsa, b, kgsb, K, N, false);
         tc::mma_commit(mbar);
     }
     const bool ok = tc::mbar_wait(mbar, phase, kPolls);
     phase ^= 1u;
     tc::fence_after_sync();
-    if (!ok && threadIdx.x == 0) atomicExch(err, FC_ETIMEOUT);
-    return __syncthreads_and(ok);
+    if (!ok && (threadIdx.x & 127) == 0) atomicExch(err, FC_ETIMEOUT);
+    return tile_sync_and(bar, ok);
 }
 
-// Per-lane TMEM address of this thread's row, column col.
+// Per-lane TMEM address of this thread's row (row = thread index within its
+// 128-thread group; a warp reaches the lanes of its index mod 4), column col.
 __device__ __forceinline__ uint32_t trow(uint32_t tbase, int col)
 {
-    return tbase + ((uint32_t)(threadIdx.x & ~31) << 16) + (uint32_t)col;
+    return tbase + ((uint32_t)(threadIdx.x & 96) << 16) + (uint32_t)col;
 }
 
 // Epilogue: h = SiLU(acc + bias) of this thread's row -> row r of the
@@ -137,7 +162,7 @@ __device__ __forceinline__ uint32_t trow(uint32_t tbase, int col)
 __device__ __forceinline__ void epi_silu(uint32_t tacc, const float *bias, unsigned char *dst,
                                          unsigned char *dlo, bf16 *ht, size_t ldh, size_t col)
 {
-    const int r = threadIdx.x;
+    const int r = threadIdx.x & 127;
 #pragma unroll 1
     for (int c0 = 0; c0 < kH; c0 += 16) {
         float v[16];
@@ -180,7 +205,7 @@ __device__ __forceinline__ void stage_x(unsigned char *sX, const float (&Lr)[kMa
         const __nv_bfloat162 hb = *reinterpret_cast<const __nv_bfloat162 *>(&q[k]);
         q[k + 4] = pack2(a - __low2float(hb), b - __high2float(hb));
     }
-    const int r = threadIdx.x;
+    const int r = threadIdx.x & 127;
     *reinterpret_cast<uint4 *>(sX + tc::kmajor_off(r, 0, kKgs128)) = make_uint4(q[0], q[1], q[2], q[3]);
     *reinterpret_cast<uint4 *>(sX + tc::kmajor_off(r, 8, kKgs128)) = make_uint4(q[4], q[5], q[6], q[7]);
     if (xt) {
@@ -193,13 +218,14 @@ __device__ __forceinline__ void stage_x(unsigned char *sX, const float (&Lr)[kMa
     }
 }
 
-// Thread 0 issues D = A_hi B^T + A_lo B^T (K = 128) and commits; everyone
-// waits.  Returns false (and records the timeout) if the wait bound expires.
+// The group's first thread issues D = A_hi B^T + A_lo B^T (K = 128) and
+// commits; the group waits.  Returns false (and records the timeout) if the
+// wait bound expires.
 __device__ __forceinline__ bool run_gemm_split(uint32_t d, const unsigned char *ahi,
                                                const unsigned char *alo, const unsigned char *b,
-                                               uint64_t *mbar, uint32_t &phase, int *err)
+                                               uint64_t *mbar, uint32_t &phase, int *err, int bar = 0)
 {
-    if (threadIdx.x == 0) {
+    if ((threadIdx.x & 127) == 0) {
         issue_gemm(d, ahi, kKgs128, b, kKgs128, kH, kH, false);
         issue_gemm(d, alo, kKgs128, b, kKgs128, kH, kH, true);
         tc::mma_commit(mbar);
@@ -207,8 +233,8 @@ __device__ __forceinline__ bool run_gemm_split(uint32_t d, const unsigned char *
     const bool ok = tc::mbar_wait(mbar, phase, kPolls);
     phase ^= 1u;
     tc::fence_after_sync();
-    if (!ok && threadIdx.x == 0) atomicExch(err, FC_ETIMEOUT);
-    return __syncthreads_and(ok);
+    if (!ok && (threadIdx.x & 127) == 0) atomicExch(err, FC_ETIMEOUT);
+    return tile_sync_and(bar, ok);
 }
 
 // Exact ln T from path lengths: the projector's energy-integral epilogue.
@@ -244,51 +270,64 @@ __device__ __forceinline__ float group_base(const float (&L)[kMaxMat], const flo
     return __logf(s);
 }
 
-// shared-memory map of the inference kernel (bytes)
-constexpr int kInfW1 = 0, kInfW2 = 4096, kInfW3 = 4096 + 32768, kInfX = 4096 + 2 * 32768,
-              kInfH = kInfX + 4096, kInfHlo = kInfH + 32768, kInfF = kInfHlo + 32768;
+// shared-memory map of the inference kernel (bytes): the weights once, then
+// per group of 128 threads its own X / H / Hlo operands
+constexpr int kInfGroups = 2;
+constexpr int kInfW1 = 0, kInfW2 = 4096, kInfW3 = 4096 + 32768, kInfG0 = 4096 + 2 * 32768;
+constexpr int kInfX = 0, kInfH = 4096, kInfHlo = kInfH + 32768, kInfGroupBytes = kInfHlo + 32768;
+constexpr int kInfF = kInfG0 + kInfGroups * kInfGroupBytes;
 constexpr int kInfSmem = kInfF + (4 * kH + 2 * kMaxMat + kMlpGroups * (kMaxMat + 1) + 8) * 4;
 
 }  // namespace
 
 // ---------------------------------------------------------------- inference
-__global__ void __launch_bounds__(128)
+// Two groups of 128 threads (4 warps each) share the resident weights and
+// the tensor core, each working through its own tiles of 128 rays with its
+// own operands in shared memory, accumulator in tensor memory (columns
+// 128 g .. 128 g + 127), mbarrier and named barrier: while one group runs
+// its SiLU epilogue on the CUDA cores the other group's MMAs run.
+__global__ void __launch_bounds__(128 * kInfGroups)
 k_mlp_eval(const __grid_constant__ SurrogateParams p, const float *__restrict__ L, long long n,
            float *__restrict__ lnT, unsigned int *n_fallback, int *err)
 {
     extern __shared__ __align__(1024) unsigned char smem[];
-    __shared__ uint64_t mbar;
+    __shared__ uint64_t mbar[kInfGroups];
     __shared__ uint32_t tbase_s;
+    const int g = threadIdx.x >> 7;                 // group
+    const int r = threadIdx.x & 127;                // row of the group's tile
+    const int bar = 1 + g;                          // the group's named barrier
     unsigned char *sW1 = smem + kInfW1, *sW2 = smem + kInfW2, *sW3 = smem + kInfW3;
-    unsigned char *sX = smem + kInfX, *sH = smem + kInfH, *sHlo = smem + kInfHlo;
+    unsigned char *grp_smem = smem + kInfG0 + g * kInfGroupBytes;
+    unsigned char *sX = grp_smem + kInfX, *sH = grp_smem + kInfH, *sHlo = grp_smem + kInfHlo;
     float *fb = reinterpret_cast<float *>(smem + kInfF);
     float *b1 = fb, *b2 = fb + kH, *b3 = fb + 2 * kH, *w4 = fb + 3 * kH;
     float *scale = fb + 4 * kH, *box = scale + kMaxMat, *grp = box + kMaxMat;
-    const int r = threadIdx.x;
-    if (r < 32) tc::tmem_alloc(&tbase_s, 128);
-    if (r == 0) tc::mbar_init(&mbar, 1);
+    if (threadIdx.x < 32) tc::tmem_alloc(&tbase_s, 128 * kInfGroups);
+    if (threadIdx.x < kInfGroups) tc::mbar_init(&mbar[threadIdx.x], 1);
     stage_kmajor(sW1, p.W1b, kH, kInP, kKgs128);
     stage_kmajor(sW2, p.W2b, kH, kH, kKgs128);
     stage_kmajor(sW3, p.W3b, kH, kH, kKgs128);
     const float *P = p.P;
-    for (int i = r; i < kH; i += blockDim.x) {
+    for (int i = threadIdx.x; i < kH; i += blockDim.x) {
         b1[i] = P[kOffB1 + i];
         b2[i] = P[kOffB2 + i];
         b3[i] = P[kOffB3 + i];
         w4[i] = P[kOffW4 + i];
     }
-    if (r < kMaxMat) {
-        scale[r] = P[kOffScale + r];
-        box[r] = P[kOffBox + r];
+    if (threadIdx.x < kMaxMat) {
+        scale[threadIdx.x] = P[kOffScale + threadIdx.x];
+        box[threadIdx.x] = P[kOffBox + threadIdx.x];
     }
-    if (r < kMlpGroups * (kMaxMat + 1)) grp[r] = P[kOffGa + r];
+    if (threadIdx.x < kMlpGroups * (kMaxMat + 1)) grp[threadIdx.x] = P[kOffGa + threadIdx.x];
     const float b4 = P[kOffB4];
-    sync_for_mma();
-    const uint32_t tb = tbase_s;
+    sync_for_mma();                                  // whole CTA
+    const uint32_t tb = tbase_s + 128u * (uint32_t)g;
+    uint64_t *mb = &mbar[g];
     uint32_t phase = 0;
     unsigned int my_fallback = 0;
     const long long ntiles = (n + 127) / 128;
-    for (long long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    for (long long tile = (long long)blockIdx.x * kInfGroups + g; tile < ntiles;
+         tile += (long long)gridDim.x * kInfGroups) {
         const long long i = tile * 128 + r;
         const bool valid = i < n;
         float Lr[kMaxMat];
@@ -300,14 +339,14 @@ k_mlp_eval(const __grid_constant__ SurrogateParams p, const float *__restrict__ 
         }
         const float ylin = group_base(Lr, grp);
         stage_x(sX, Lr, scale, nullptr, 0, 0);
-        sync_for_mma();
-        if (!run_gemm(tb, sX, kKgs128, sW1, kKgs128, kInP, kH, &mbar, phase, err)) break;
+        sync_for_mma(bar);
+        if (!run_gemm(tb, sX, kKgs128, sW1, kKgs128, kInP, kH, mb, phase, err, bar)) break;
         epi_silu(trow(tb, 0), b1, sH, sHlo, nullptr, 0, 0);
-        sync_for_mma();
-        if (!run_gemm_split(tb, sH, sHlo, sW2, &mbar, phase, err)) break;
+        sync_for_mma(bar);
+        if (!run_gemm_split(tb, sH, sHlo, sW2, mb, phase, err, bar)) break;
         epi_silu(trow(tb, 0), b2, sH, sHlo, nullptr, 0, 0);
-        sync_for_mma();
-        if (!run_gemm_split(tb, sH, sHlo, sW3, &mbar, phase, err)) break;
+        sync_for_mma(bar);
+        if (!run_gemm_split(tb, sH, sHlo, sW3, mb, phase, err, bar)) break;
         float res = b4;
 #pragma unroll 1
         for (int c0 = 0; c0 < kH; c0 += 16) {
@@ -327,13 +366,13 @@ k_mlp_eval(const __grid_constant__ SurrogateParams p, const float *__restrict__ 
             lnT[i] = y;
         }
         tc::fence_before_sync();
-        __syncthreads();
+        tile_sync(bar);
         tc::fence_after_sync();
     }
     if (my_fallback) atomicAdd(n_fallback, my_fallback);
     tc::fence_before_sync();
-    __syncthreads();
-    if (r < 32) tc::tmem_dealloc(tb, 128);
+    __syncthreads();                                 // both groups done with tensor memory
+    if (threadIdx.x < 32) tc::tmem_dealloc(tbase_s, 128 * kInfGroups);
 }
 
 // Order-preserving integer image of a float (smaller float, smaller int).
@@ -368,6 +407,25 @@ cudaError_t launch_guard_scan(const SurrogateParams &p, const float *L, const fl
     long long blocks = (n + 255) / 256;
     if (blocks > sm_count() * 8) blocks = sm_count() * 8;
     k_guard_scan<<<(int)blocks, 256, 0, s>>>(p, L, y, ys, n, tol, best);
+    return cudaGetLastError();
+}
+
+// sigma of every element, as the surrogate kernels evaluate it (the error
+// of the activations is measured through this kernel).
+__global__ void __launch_bounds__(256) k_sigma_probe(const float *__restrict__ z, float *__restrict__ s,
+                                                     long long n)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+        s[i] = sigma_fast(z[i]);
+}
+
+cudaError_t launch_sigma_probe(const float *z, float *s, long long n, cudaStream_t st)
+{
+    if (n <= 0) return cudaSuccess;
+    long long blocks = (n + 255) / 256;
+    if (blocks > sm_count() * 8) blocks = sm_count() * 8;
+    k_sigma_probe<<<(int)blocks, 256, 0, st>>>(z, s, n);
     return cudaGetLastError();
 }
 
@@ -739,9 +797,10 @@ cudaError_t launch_mlp_eval(const SurrogateParams &p, const float *L, long long 
                                          kInfSmem);
     if (e != cudaSuccess) return e;
     const long long ntiles = (n + 127) / 128;
+    const long long want = (ntiles + kInfGroups - 1) / kInfGroups;
     const int sms = sm_count();
-    const int grid = (int)(ntiles < sms ? ntiles : sms);   // one CTA per SM (141 KB smem)
-    k_mlp_eval<<<grid, 128, kInfSmem, s>>>(p, L, n, lnT, n_fallback, err);
+    const int grid = (int)(want < sms ? want : sms);   // one CTA per SM (207 KB smem)
+    k_mlp_eval<<<grid, 128 * kInfGroups, kInfSmem, s>>>(p, L, n, lnT, n_fallback, err);
     return cudaGetLastError();
 }
 

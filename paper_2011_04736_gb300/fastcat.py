@@ -36,7 +36,7 @@ ENTRY_POINTS = ("fc_create", "fc_destroy", "fc_last_error", "fc_set_geometry", "
                 "fc_dose_estimate", "fc_fluence_for_dose", "fc_set_noise_order",
                 "fc_set_energy_groups", "fc_deconvolve_rl", "fc_detector_mtf",
                 "fc_set_backprojector", "fc_backprojector_in_use", "fc_inject_fault",
-                "fc_surrogate_guard")
+                "fc_surrogate_guard", "fc_surrogate_sigma")
 FC_STATIC_SCRATCH_FLOATS = 8 << 20
 FC_SURROGATE_PARAMS = 34305
 FC_SURROGATE_STATE = 34305 + 52 + 2 * 34305 + 1
@@ -129,6 +129,7 @@ def load():
         "fc_backprojector_in_use": (I, [P, ctypes.POINTER(I)]),
         "fc_inject_fault": (I, [I, ctypes.c_int64]),
         "fc_surrogate_guard": (I, [P, P, P, ctypes.c_int64, ctypes.c_double, P, P]),
+        "fc_surrogate_sigma": (I, [P, P, ctypes.c_int64, P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -422,6 +423,14 @@ def fc_surrogate_guard(h, L, lnT, tol, stream=None):
     _check(load().fc_surrogate_guard(h, _dev(L, "L"), _dev(lnT, "lnT"), lnT.numel(), float(tol),
                                      ctypes.byref(thr), _stream(stream)))
     return thr.value
+
+
+def fc_surrogate_sigma(z, out, stream=None):
+    """sigma(z) of device float32 z into out, as the surrogate kernels
+    evaluate it (the activations' error is measured through this)."""
+    if str(z.dtype) != "torch.float32" or str(out.dtype) != "torch.float32" or out.numel() < z.numel():
+        raise ValueError("fc_surrogate_sigma: out must be float32 with at least z.numel() elements")
+    return _check(load().fc_surrogate_sigma(_dev(z, "z"), _dev(out, "out"), z.numel(), _stream(stream)))
 
 
 def fc_surrogate_project(h, angle_begin, angle_count, out, stream=None):
