@@ -59,6 +59,16 @@ __device__ __forceinline__ float sigma_fast(float z) { return fmaf(0.5f, tanh_fa
 // SiLU(z) = z sigma(z)
 __device__ __forceinline__ float silu(float z) { return z * sigma_fast(z); }
 
+// SiLU of a pair with packed binary32 arithmetic (each element rounded as
+// the scalar silu rounds it).
+__device__ __forceinline__ float2 silu2(float2 z)
+{
+    const float2 half = make_float2(0.5f, 0.5f);
+    const float2 hz = __fmul2_rn(z, half);
+    const float2 t = make_float2(tanh_fast(hz.x), tanh_fast(hz.y));
+    return __fmul2_rn(z, __ffma2_rn(half, t, half));
+}
+
 // d SiLU / dz = sigma + z sigma (1 - sigma)
 __device__ __forceinline__ float dsilu(float z)
 {
@@ -98,96 +108,113 @@ __device__ __forceinline__ void issue_gemm(uint32_t d, const unsigned char *a, u
     }
 }
 
-// Barrier of the threads that share a tile: bar 0 is the whole CTA
-// (__syncthreads), bar > 0 the named barrier of one 128-thread group.
-__device__ __forceinline__ void tile_sync(int bar)
+// Barrier of the nt threads that share a tile: bar 0 is the whole CTA
+// (__syncthreads), bar > 0 the named barrier of one group of nt threads.
+__device__ __forceinline__ void tile_sync(int bar, int nt = 128)
 {
     if (bar == 0)
         __syncthreads();
     else
-        asm volatile("bar.sync %0, 128;" :: "r"(bar) : "memory");
+        asm volatile("bar.sync %0, %1;" :: "r"(bar), "r"(nt) : "memory");
 }
 
 // tile_sync that also returns whether ok holds on every thread of the barrier.
-__device__ __forceinline__ bool tile_sync_and(int bar, bool ok)
+__device__ __forceinline__ bool tile_sync_and(int bar, bool ok, int nt = 128)
 {
     if (bar == 0) return __syncthreads_and(ok);
     uint32_t all;
     asm volatile("{\n\t.reg .pred p, q;\n\t"
                  "setp.ne.u32 q, %1, 0;\n\t"
-                 "bar.red.and.pred p, %2, 128, q;\n\t"
+                 "bar.red.and.pred p, %2, %3, q;\n\t"
                  "selp.u32 %0, 1, 0, p;\n\t}"
-                 : "=r"(all) : "r"((uint32_t)ok), "r"(bar) : "memory");
+                 : "=r"(all) : "r"((uint32_t)ok), "r"(bar), "r"(nt) : "memory");
     return all != 0;
 }
 
 // Make shared-memory writes visible to the tensor core and order
 // tensor-memory accesses around the barrier of the tile's threads.
-__device__ __forceinline__ void sync_for_mma(int bar = 0)
+__device__ __forceinline__ void sync_for_mma(int bar = 0, int nt = 128)
 {
     tc::fence_async_smem();
     tc::fence_before_sync();
-    tile_sync(bar);
+    tile_sync(bar, nt);
     tc::fence_after_sync();
 }
 
-// The first thread of the tile's group issues a GEMM and commits; the group
-// waits for it.  Returns false (and records the timeout) if the wait bound
-// is exhausted.
+// The first thread of the tile's group (nt threads, a power of two) issues a
+// GEMM and commits; the group waits for it.  Returns false (and records the
+// timeout) if the wait bound is exhausted.
 __device__ __forceinline__ bool run_gemm(uint32_t d, const unsigned char *a, uint32_t kgsa,
                                          const unsigned char *b, uint32_t kgsb, int K, int N,
-                                         uint64_t *mbar, uint32_t &phase, int *err, int bar = 0)
+                                         uint64_t *mbar, uint32_t &phase, int *err, int bar = 0,
+                                         int nt = 128)
 {
-    if ((threadIdx.x & 127) == 0) {
+    const bool issuer = (threadIdx.x & (nt - 1)) == 0;
+    if (issuer) {
         issue_gemm(d, a, kgsa, b, kgsb, K, N, false);
         tc::mma_commit(mbar);
     }
     const bool ok = tc::mbar_wait(mbar, phase, kPolls);
     phase ^= 1u;
     tc::fence_after_sync();
-    if (!ok && (threadIdx.x & 127) == 0) atomicExch(err, FC_ETIMEOUT);
-    return tile_sync_and(bar, ok);
+    if (!ok && issuer) atomicExch(err, FC_ETIMEOUT);
+    return tile_sync_and(bar, ok, nt);
 }
 
-// Per-lane TMEM address of this thread's row (row = thread index within its
-// 128-thread group; a warp reaches the lanes of its index mod 4), column col.
+// Per-lane TMEM address of this thread's row (row = thread index mod 128; a
+// warp reaches the lanes of its index mod 4), column col.
 __device__ __forceinline__ uint32_t trow(uint32_t tbase, int col)
 {
     return tbase + ((uint32_t)(threadIdx.x & 96) << 16) + (uint32_t)col;
 }
 
-// Epilogue: h = SiLU(acc + bias) of this thread's row -> row r of the
-// K-major operands dst (bf16(h)) and dlo (bf16(h - bf16(h))), and, if
-// ht != nullptr, the feature-major global copy ht[j * ldh + col] of bf16(h).
+// Epilogue: h = SiLU(acc + bias) of this thread's row, columns [c_lo, c_hi)
+// (CW columns per tensor-memory load, c_hi - c_lo a multiple of CW) -> row
+// r of the K-major operands dst (bf16(h)) and dlo (bf16(h - bf16(h))), and,
+// if ht != nullptr, the feature-major global copy ht[j * ldh + col] of
+// bf16(h).
+template <int CW = 16>
 __device__ __forceinline__ void epi_silu(uint32_t tacc, const float *bias, unsigned char *dst,
-                                         unsigned char *dlo, bf16 *ht, size_t ldh, size_t col)
+                                         unsigned char *dlo, bf16 *ht, size_t ldh, size_t col,
+                                         int c_lo = 0, int c_hi = kH)
 {
+    static_assert(CW == 16 || CW == 32, "16 or 32 columns per load");
     const int r = threadIdx.x & 127;
 #pragma unroll 1
-    for (int c0 = 0; c0 < kH; c0 += 16) {
-        float v[16];
-        tc::tmem_ld16(tacc + c0, v);
-        uint32_t p[8], q[8];
+    for (int cl = c_lo; cl < c_hi; cl += CW) {
+        float vw[CW];
+        if constexpr (CW == 32)
+            tc::tmem_ld32(tacc + cl, vw);
+        else
+            tc::tmem_ld16(tacc + cl, vw);
 #pragma unroll
-        for (int i = 0; i < 8; ++i) {
-            const float a = silu(v[2 * i] + bias[c0 + 2 * i]);
-            const float b = silu(v[2 * i + 1] + bias[c0 + 2 * i + 1]);
-            p[i] = pack2(a, b);
-            const __nv_bfloat162 hb = *reinterpret_cast<const __nv_bfloat162 *>(&p[i]);
-            q[i] = pack2(a - __low2float(hb), b - __high2float(hb));
-            if (ht) {
-                ht[(size_t)(c0 + 2 * i) * ldh + col] = hb.x;
-                ht[(size_t)(c0 + 2 * i + 1) * ldh + col] = hb.y;
+        for (int hh = 0; hh < CW / 16; ++hh) {
+            const int c0 = cl + 16 * hh;
+            const float *v = vw + 16 * hh;
+            uint32_t p[8], q[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const float2 h = silu2(__fadd2_rn(make_float2(v[2 * i], v[2 * i + 1]),
+                                                  *reinterpret_cast<const float2 *>(bias + c0 + 2 * i)));
+                p[i] = pack2(h.x, h.y);
+                const __nv_bfloat162 hb = *reinterpret_cast<const __nv_bfloat162 *>(&p[i]);
+                // h - bf16(h), exact (the multiply by -1 is exact)
+                const float2 lo = __ffma2_rn(__bfloat1622float2(hb), make_float2(-1.0f, -1.0f), h);
+                q[i] = pack2(lo.x, lo.y);
+                if (ht) {
+                    ht[(size_t)(c0 + 2 * i) * ldh + col] = hb.x;
+                    ht[(size_t)(c0 + 2 * i + 1) * ldh + col] = hb.y;
+                }
             }
+            *reinterpret_cast<uint4 *>(dst + tc::kmajor_off(r, c0, kKgs128)) =
+                make_uint4(p[0], p[1], p[2], p[3]);
+            *reinterpret_cast<uint4 *>(dst + tc::kmajor_off(r, c0 + 8, kKgs128)) =
+                make_uint4(p[4], p[5], p[6], p[7]);
+            *reinterpret_cast<uint4 *>(dlo + tc::kmajor_off(r, c0, kKgs128)) =
+                make_uint4(q[0], q[1], q[2], q[3]);
+            *reinterpret_cast<uint4 *>(dlo + tc::kmajor_off(r, c0 + 8, kKgs128)) =
+                make_uint4(q[4], q[5], q[6], q[7]);
         }
-        *reinterpret_cast<uint4 *>(dst + tc::kmajor_off(r, c0, kKgs128)) =
-            make_uint4(p[0], p[1], p[2], p[3]);
-        *reinterpret_cast<uint4 *>(dst + tc::kmajor_off(r, c0 + 8, kKgs128)) =
-            make_uint4(p[4], p[5], p[6], p[7]);
-        *reinterpret_cast<uint4 *>(dlo + tc::kmajor_off(r, c0, kKgs128)) =
-            make_uint4(q[0], q[1], q[2], q[3]);
-        *reinterpret_cast<uint4 *>(dlo + tc::kmajor_off(r, c0 + 8, kKgs128)) =
-            make_uint4(q[4], q[5], q[6], q[7]);
     }
 }
 
@@ -223,9 +250,11 @@ __device__ __forceinline__ void stage_x(unsigned char *sX, const float (&Lr)[kMa
 // wait bound expires.
 __device__ __forceinline__ bool run_gemm_split(uint32_t d, const unsigned char *ahi,
                                                const unsigned char *alo, const unsigned char *b,
-                                               uint64_t *mbar, uint32_t &phase, int *err, int bar = 0)
+                                               uint64_t *mbar, uint32_t &phase, int *err, int bar = 0,
+                                               int nt = 128)
 {
-    if ((threadIdx.x & 127) == 0) {
+    const bool issuer = (threadIdx.x & (nt - 1)) == 0;
+    if (issuer) {
         issue_gemm(d, ahi, kKgs128, b, kKgs128, kH, kH, false);
         issue_gemm(d, alo, kKgs128, b, kKgs128, kH, kH, true);
         tc::mma_commit(mbar);
@@ -233,8 +262,8 @@ __device__ __forceinline__ bool run_gemm_split(uint32_t d, const unsigned char *
     const bool ok = tc::mbar_wait(mbar, phase, kPolls);
     phase ^= 1u;
     tc::fence_after_sync();
-    if (!ok && (threadIdx.x & 127) == 0) atomicExch(err, FC_ETIMEOUT);
-    return tile_sync_and(bar, ok);
+    if (!ok && issuer) atomicExch(err, FC_ETIMEOUT);
+    return tile_sync_and(bar, ok, nt);
 }
 
 // Exact ln T from path lengths: the projector's energy-integral epilogue.
@@ -275,30 +304,39 @@ __device__ __forceinline__ float group_base(const float (&L)[kMaxMat], const flo
 constexpr int kInfGroups = 2;
 constexpr int kInfW1 = 0, kInfW2 = 4096, kInfW3 = 4096 + 32768, kInfG0 = 4096 + 2 * 32768;
 constexpr int kInfX = 0, kInfH = 4096, kInfHlo = kInfH + 32768, kInfGroupBytes = kInfHlo + 32768;
-constexpr int kInfF = kInfG0 + kInfGroups * kInfGroupBytes;
+constexpr int kInfGroupThreads = 256;     // two threads per row: columns 0-63 and 64-127
+constexpr int kInfPart = kInfG0 + kInfGroups * kInfGroupBytes;   // [groups][128] partial sums
+constexpr int kInfF = kInfPart + kInfGroups * 128 * 4;
 constexpr int kInfSmem = kInfF + (4 * kH + 2 * kMaxMat + kMlpGroups * (kMaxMat + 1) + 8) * 4;
 
 }  // namespace
 
 // ---------------------------------------------------------------- inference
-// Two groups of 128 threads (4 warps each) share the resident weights and
+// Two groups of 256 threads (8 warps each) share the resident weights and
 // the tensor core, each working through its own tiles of 128 rays with its
 // own operands in shared memory, accumulator in tensor memory (columns
 // 128 g .. 128 g + 127), mbarrier and named barrier: while one group runs
-// its SiLU epilogue on the CUDA cores the other group's MMAs run.
-__global__ void __launch_bounds__(128 * kInfGroups)
+// its SiLU epilogue on the CUDA cores the other group's MMAs run.  Within a
+// group, row r is served by two threads (warps 0-3 and 4-7 reach the same
+// tensor-memory lanes), one for hidden units 0-63 and one for 64-127; the
+// first owns the ray (inputs, baseline, result, fallback).
+__global__ void __launch_bounds__(kInfGroupThreads * kInfGroups)
 k_mlp_eval(const __grid_constant__ SurrogateParams p, const float *__restrict__ L, long long n,
            float *__restrict__ lnT, unsigned int *n_fallback, int *err)
 {
     extern __shared__ __align__(1024) unsigned char smem[];
     __shared__ uint64_t mbar[kInfGroups];
     __shared__ uint32_t tbase_s;
-    const int g = threadIdx.x >> 7;                 // group
+    constexpr int NT = kInfGroupThreads;
+    const int g = threadIdx.x / NT;                 // group
     const int r = threadIdx.x & 127;                // row of the group's tile
+    const bool owner = (threadIdx.x & (NT - 1)) < 128;
+    const int c_lo = owner ? 0 : kH / 2, c_hi = c_lo + kH / 2;
     const int bar = 1 + g;                          // the group's named barrier
     unsigned char *sW1 = smem + kInfW1, *sW2 = smem + kInfW2, *sW3 = smem + kInfW3;
     unsigned char *grp_smem = smem + kInfG0 + g * kInfGroupBytes;
     unsigned char *sX = grp_smem + kInfX, *sH = grp_smem + kInfH, *sHlo = grp_smem + kInfHlo;
+    float *part = reinterpret_cast<float *>(smem + kInfPart) + g * 128;
     float *fb = reinterpret_cast<float *>(smem + kInfF);
     float *b1 = fb, *b2 = fb + kH, *b3 = fb + 2 * kH, *w4 = fb + 3 * kH;
     float *scale = fb + 4 * kH, *box = scale + kMaxMat, *grp = box + kMaxMat;
@@ -326,37 +364,56 @@ k_mlp_eval(const __grid_constant__ SurrogateParams p, const float *__restrict__ 
     uint32_t phase = 0;
     unsigned int my_fallback = 0;
     const long long ntiles = (n + 127) / 128;
-    for (long long tile = (long long)blockIdx.x * kInfGroups + g; tile < ntiles;
-         tile += (long long)gridDim.x * kInfGroups) {
+    const long long stride = (long long)gridDim.x * kInfGroups;
+    // inputs of the group's next tile, loaded one tile ahead by the owner
+    float Ln[kMaxMat];
+    {
+        const long long i0 = ((long long)blockIdx.x * kInfGroups + g) * 128 + r;
+#pragma unroll
+        for (int m = 0; m < kMaxMat; ++m)
+            Ln[m] = (owner && i0 < n && m < p.n_mat) ? L[i0 * p.n_mat + m] : 0.0f;
+    }
+    for (long long tile = (long long)blockIdx.x * kInfGroups + g; tile < ntiles; tile += stride) {
         const long long i = tile * 128 + r;
         const bool valid = i < n;
         float Lr[kMaxMat];
         bool outside = false;
+        float ylin = 0.0f;
 #pragma unroll
-        for (int m = 0; m < kMaxMat; ++m) {
-            Lr[m] = (valid && m < p.n_mat) ? L[i * p.n_mat + m] : 0.0f;
-            outside = outside || Lr[m] > box[m];
+        for (int m = 0; m < kMaxMat; ++m) Lr[m] = Ln[m];
+        if (owner) {
+#pragma unroll
+            for (int m = 0; m < kMaxMat; ++m) outside = outside || Lr[m] > box[m];
+            ylin = group_base(Lr, grp);
+            stage_x(sX, Lr, scale, nullptr, 0, 0);
+            const long long in = i + stride * 128;
+#pragma unroll
+            for (int m = 0; m < kMaxMat; ++m) Ln[m] = (in < n && m < p.n_mat) ? L[in * p.n_mat + m] : 0.0f;
         }
-        const float ylin = group_base(Lr, grp);
-        stage_x(sX, Lr, scale, nullptr, 0, 0);
-        sync_for_mma(bar);
-        if (!run_gemm(tb, sX, kKgs128, sW1, kKgs128, kInP, kH, mb, phase, err, bar)) break;
-        epi_silu(trow(tb, 0), b1, sH, sHlo, nullptr, 0, 0);
-        sync_for_mma(bar);
-        if (!run_gemm_split(tb, sH, sHlo, sW2, mb, phase, err, bar)) break;
-        epi_silu(trow(tb, 0), b2, sH, sHlo, nullptr, 0, 0);
-        sync_for_mma(bar);
-        if (!run_gemm_split(tb, sH, sHlo, sW3, mb, phase, err, bar)) break;
-        float res = b4;
+        sync_for_mma(bar, NT);
+        if (!run_gemm(tb, sX, kKgs128, sW1, kKgs128, kInP, kH, mb, phase, err, bar, NT)) break;
+        epi_silu<32>(trow(tb, 0), b1, sH, sHlo, nullptr, 0, 0, c_lo, c_hi);
+        sync_for_mma(bar, NT);
+        if (!run_gemm_split(tb, sH, sHlo, sW2, mb, phase, err, bar, NT)) break;
+        epi_silu<32>(trow(tb, 0), b2, sH, sHlo, nullptr, 0, 0, c_lo, c_hi);
+        sync_for_mma(bar, NT);
+        if (!run_gemm_split(tb, sH, sHlo, sW3, mb, phase, err, bar, NT)) break;
+        float res = owner ? b4 : 0.0f;
 #pragma unroll 1
-        for (int c0 = 0; c0 < kH; c0 += 16) {
-            float v[16];
-            tc::tmem_ld16(trow(tb, c0), v);
+        for (int c0 = c_lo; c0 < c_hi; c0 += 32) {
+            float v[32];
+            tc::tmem_ld32(trow(tb, c0), v);
 #pragma unroll
-            for (int j = 0; j < 16; ++j) res = fmaf(w4[c0 + j], silu(v[j] + b3[c0 + j]), res);
+            for (int j = 0; j < 32; ++j) res = fmaf(w4[c0 + j], silu(v[j] + b3[c0 + j]), res);
         }
-        if (valid) {
-            float y = ylin + res;
+        if (!owner) part[r] = res;
+        // the partial sums exchanged; every tensor-memory read of this tile
+        // is complete before the group's next MMA
+        tc::fence_before_sync();
+        tile_sync(bar, NT);
+        tc::fence_after_sync();
+        if (owner && valid) {
+            float y = ylin + (res + part[r]);
             // outside the training box, or attenuated as strongly as a ray
             // the guard saw miss the tolerance: the exact sum decides
             if (outside || -ylin >= p.guard) {
@@ -365,9 +422,6 @@ k_mlp_eval(const __grid_constant__ SurrogateParams p, const float *__restrict__ 
             }
             lnT[i] = y;
         }
-        tc::fence_before_sync();
-        tile_sync(bar);
-        tc::fence_after_sync();
     }
     if (my_fallback) atomicAdd(n_fallback, my_fallback);
     tc::fence_before_sync();
@@ -799,8 +853,8 @@ cudaError_t launch_mlp_eval(const SurrogateParams &p, const float *L, long long 
     const long long ntiles = (n + 127) / 128;
     const long long want = (ntiles + kInfGroups - 1) / kInfGroups;
     const int sms = sm_count();
-    const int grid = (int)(want < sms ? want : sms);   // one CTA per SM (207 KB smem)
-    k_mlp_eval<<<grid, 128 * kInfGroups, kInfSmem, s>>>(p, L, n, lnT, n_fallback, err);
+    const int grid = (int)(want < sms ? want : sms);   // one CTA per SM (208 KB smem)
+    k_mlp_eval<<<grid, kInfGroupThreads * kInfGroups, kInfSmem, s>>>(p, L, n, lnT, n_fallback, err);
     return cudaGetLastError();
 }
 
