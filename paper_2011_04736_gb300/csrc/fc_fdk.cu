@@ -95,6 +95,89 @@ __device__ __forceinline__ void ramp_row(const float *sx, int n, float inv_tau, 
     }
 }
 
+// Padded row for the filter: position P = j + off holds sample j (zeros
+// elsewhere; off = jm, the largest odd offset, or 1 for a one-pixel row, so
+// that P is even for even outputs at every odd offset), stored as pairs
+// (P even, P + 1) with one spare pair after every 8 (a warp's 8-byte loads at
+// a pair stride of 8 then hit distinct banks).
+__host__ __device__ __forceinline__ int pidx(int P) { return 2 * ((P >> 1) + (P >> 4)) + (P & 1); }
+
+// Padded positions the filter reads: up to the last output's window end,
+// (n - 1) + 2 ntap + 16 with ntap = jm + 1 <= n (even count).
+__host__ __device__ __forceinline__ int filt_span(int n) { return (n + 2 * n + kFiltOut + 2 + 1) & ~1; }
+
+__device__ __forceinline__ int filt_off(int jm) { return jm >= 1 ? jm : 1; }
+
+// Ram-Lak filtered row (the ramp_row sums, term for term in the same order)
+// from the pair-skewed row sp: 16 outputs per thread as 8 pairs updated by
+// packed binary32 FMAs (each element rounded as a scalar fma), a window of
+// 8 sample pairs advancing one pair per odd offset, and per warp only the
+// offsets at which some output of the warp meets a sample inside the row
+// (the others would add h * 0 to every output).
+template <class Out>
+__device__ __forceinline__ void ramp_row_pairs(const float *sp, int n, float inv_tau, Out out)
+{
+    const int jm = ((n - 1) & 1) ? n - 1 : n - 2;
+    const int ntap = jm >= 1 ? (jm + 1) : 0;
+    const int off = filt_off(jm);
+    const float2 *sp2 = reinterpret_cast<const float2 *>(sp);
+    const int lane = threadIdx.x & 31;
+    for (int i0 = threadIdx.x * kFiltOut; i0 < n; i0 += blockDim.x * kFiltOut) {
+        float2 acc[kFiltOut / 2];
+#pragma unroll
+        for (int k = 0; k < kFiltOut / 2; ++k)
+            acc[k] = make_float2(0.25f * sp[pidx(i0 + 2 * k + off)], 0.25f * sp[pidx(i0 + 2 * k + 1 + off)]);
+        // offsets j = -jm + 2 m, m in [m_lo, m_hi): some output of the warp
+        // (outputs [iw0, iw1]) meets a sample j' in [0, n)
+        const int iw0 = i0 - kFiltOut * lane;
+        const int iw1 = min(iw0 + 32 * kFiltOut - 1, n - 1);
+        const int m_lo = max(0, (jm - iw1 + 1) >> 1);
+        const int m_hi = min(ntap, ((n - 1 - iw0 + jm) >> 1) + 1);
+        if (m_lo < m_hi) {
+            // window pair k holds samples at P = i0 + 2 (m + k), + 1 (off = jm
+            // here: ntap > 0 needs jm >= 1)
+            const int pb = (i0 >> 1) + m_lo;            // pair index of window pair 0
+            float2 win[kFiltOut / 2];
+#pragma unroll
+            for (int k = 0; k < kFiltOut / 2; ++k) win[k] = sp2[(pb + k) + ((pb + k) >> 3)];
+            int m = m_lo;
+            for (; m + kFiltOut / 2 <= m_hi; m += kFiltOut / 2) {
+#pragma unroll
+                for (int q = 0; q < kFiltOut / 2; ++q) {
+                    const int j = -jm + 2 * (m + q);
+                    const int aj = j < 0 ? -j : j;
+                    const float h = c_ramp_odd[aj >> 1];
+                    const float2 h2 = make_float2(h, h);
+#pragma unroll
+                    for (int k = 0; k < kFiltOut / 2; ++k)
+                        acc[k] = __ffma2_rn(h2, win[(k + q) % (kFiltOut / 2)], acc[k]);
+                    const int pn = pb + (m - m_lo) + q + kFiltOut / 2;
+                    win[q] = sp2[pn + (pn >> 3)];
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < kFiltOut / 2; ++q) {
+                if (m + q < m_hi) {
+                    const int j = -jm + 2 * (m + q);
+                    const int aj = j < 0 ? -j : j;
+                    const float h = c_ramp_odd[aj >> 1];
+                    const float2 h2 = make_float2(h, h);
+#pragma unroll
+                    for (int k = 0; k < kFiltOut / 2; ++k)
+                        acc[k] = __ffma2_rn(h2, win[(k + q) % (kFiltOut / 2)], acc[k]);
+                    const int pn = pb + (m - m_lo) + q + kFiltOut / 2;
+                    win[q] = sp2[pn + (pn >> 3)];
+                }
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < kFiltOut / 2; ++k) {
+            if (i0 + 2 * k < n) out(i0 + 2 * k, acc[k].x * inv_tau);
+            if (i0 + 2 * k + 1 < n) out(i0 + 2 * k + 1, acc[k].y * inv_tau);
+        }
+    }
+}
+
 // rows [v_lo, v_hi] of every projection; blockIdx.x = projection * nrows + r.
 // The filtered row goes to shared memory, then out as (value, next value -
 // value) pairs over padded columns 0..n (the zero column before the row and
@@ -113,23 +196,24 @@ k_fdk_filter(const __grid_constant__ FdkParams p, const float *__restrict__ coun
     const int iv = p.v_lo + r;
     const size_t row = ((size_t)k * g.n_v + iv) * n;
     float2 *dst = filt + ((size_t)k * p.ph + (r + 1)) * p.pw;
-    // padded row: index n + j holds q[j], zeros in [0, n) and [2n, 3n + pad)
+    // padded row: position jm + j holds q[j], zeros elsewhere (pair-skewed)
     const float vi = ((float)iv - g.cv) * g.dv * p.mag;
     const float sad2v = g.sad * g.sad + vi * vi;
-    const int span = 3 * n + kFiltOut + 2;
+    const int off = filt_off(((n - 1) & 1) ? n - 1 : n - 2);
+    const int span = filt_span(n);
     for (int i = threadIdx.x; i < span; i += blockDim.x) {
         float val = 0.0f;
-        const int j = i - n;
+        const int j = i - off;
         if (j >= 0 && j < n) {
             const float ui = ((float)j - g.cu) * g.du * p.mag;
             const float K = fmaxf(counts[row + j], 1.0f);
             val = (p.log_flood - logf(K)) * (g.sad * rsqrtf(sad2v + ui * ui));
         }
-        sx[skew(i)] = val;
+        sx[pidx(i)] = val;
     }
     __syncthreads();
-    float *fo = sx + span + span / 32 + 2;          // filtered row, index i + 1 = padded column
-    ramp_row(sx, n, 1.0f / p.tau, [&](int i, float v) { fo[i + 1] = v; });
+    float *fo = sx + pidx(span) + 2;                // filtered row, index i + 1 = padded column
+    ramp_row_pairs(sx, n, 1.0f / p.tau, [&](int i, float v) { fo[i + 1] = v; });
     if (threadIdx.x == 0) {
         fo[0] = 0.0f;
         fo[n + 1] = 0.0f;
@@ -145,8 +229,8 @@ cudaError_t launch_fdk_filter(const FdkParams &p, const float *counts, float2 *f
     if (p.g.n_u > kMaxFiltTaps) return cudaErrorInvalidValue;
     cudaError_t e = upload_ramp_taps();
     if (e != cudaSuccess) return e;
-    const int span = 3 * p.g.n_u + kFiltOut + 2;
-    const size_t smem = (size_t)(span + span / 32 + 2 + p.g.n_u + 2) * sizeof(float);
+    const int span = filt_span(p.g.n_u);
+    const size_t smem = (size_t)(2 * ((span >> 1) + (span >> 4)) + 4 + p.g.n_u + 2) * sizeof(float);
     if (smem > 48 * 1024) {
         e = cudaFuncSetAttribute(k_fdk_filter, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)smem);

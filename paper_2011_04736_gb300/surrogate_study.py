@@ -14,8 +14,9 @@ Adam, then reports on all rays:
 * speed: energy stage alone (exact energy sum from L vs surrogate from L)
   and whole projection (projector with fused exact sum vs path-length
   emission + surrogate), CUDA events on the launching stream;
-* the exact energy-sum time against the number of energy bins, and the bin
-  count at which the surrogate's constant cost equals it.
+* the exact energy-sum time against the number of energy bins, the
+  surrogate's speed-up at each, and the bin count at which the surrogate's
+  constant cost equals it (interpolated between measured counts).
 
     python -m paper_2011_04736_gb300.surrogate_study [--steps 20000] [--batch 65536]
 """
@@ -137,10 +138,15 @@ def run(steps=20000, batch=65536, n_train=1 << 24, lr=2e-3, workload="head_surro
             fc.fc_profile_enable(h, False)
         del w_mu
         ks = sorted(curve)
-        slope = (curve[ks[-1]] - curve[ks[0]]) / (ks[-1] - ks[0])
-        icpt = curve[ks[0]] - slope * ks[0]
         out["exact_ms_vs_bins"] = curve
-        out["crossover_bins"] = (t_sur - icpt) / slope if slope > 0 else None
+        out["surrogate_speedup_vs_bins"] = {k: curve[k] / t_sur for k in ks}
+        # bin count where the exact sum costs as much as the surrogate:
+        # linear interpolation between the two measured counts around it
+        cross = None
+        for a, b in zip(ks, ks[1:]):
+            if curve[a] <= t_sur < curve[b]:
+                cross = a + (t_sur - curve[a]) * (b - a) / (curve[b] - curve[a])
+        out["crossover_bins"] = cross
     sc.close()
     if verbose:
         print(json.dumps(out, indent=1))
