@@ -7,9 +7,10 @@
 //   mu = arc / (2 N) * sum_k (SAD / U)^2 * bilinear(f_k; u(x), v(x))
 //
 // Filter: one CTA per detector row; the weighted row sits zero-padded in
-// shared memory and each thread produces 16 adjacent outputs from a sliding
-// register window that advances two samples per odd tap (16 FMAs per two
-// shared loads).  Only rows the backprojector can sample are filtered and
+// shared memory as sample pairs and each thread produces 16 adjacent outputs
+// from a sliding register window of 8 pairs that advances one pair per odd
+// tap (8 packed FMAs per 8-byte shared load).  Only rows the backprojector
+// can sample are filtered and
 // stored (a conservative bound on the rows the voxel slab projects onto),
 // in a zero-padded layout so the bilinear taps need no bounds tests.
 // Backprojection: one thread per (x, y) column and chunk of z; per angle
@@ -28,7 +29,6 @@ constexpr int kFiltThreads = 128;
 constexpr int kMaxFiltTaps = 8192;        // odd taps for rows up to 8192 pixels
 __constant__ float c_ramp_odd[kMaxFiltTaps];   // -1 / (pi^2 j^2) for j = 1, 3, 5, ...
 
-__device__ __forceinline__ int skew(int i) { return i + (i >> 5); }
 }  // namespace
 
 // Upload the tau-free odd Ram-Lak taps once per process.
@@ -46,55 +46,6 @@ cudaError_t upload_ramp_taps()
     return e;
 }
 
-// Ram-Lak filtered row from the staged zero-padded row sx (index n + j holds
-// sample j, zeros around it): calls out(i, v) for i in [0, n) with
-// v = (x[i] / 4 + sum over odd j of -x[i + j] / (pi j)^2) / tau.
-template <class Out>
-__device__ __forceinline__ void ramp_row(const float *sx, int n, float inv_tau, Out out)
-{
-    // odd offsets j in [-jm, jm], jm = largest odd <= n - 1
-    const int jm = ((n - 1) & 1) ? n - 1 : n - 2;
-    const int ntap = jm >= 1 ? (jm + 1) : 0;   // number of odd offsets (both signs)
-    for (int i0 = threadIdx.x * kFiltOut; i0 < n; i0 += blockDim.x * kFiltOut) {
-        float acc[kFiltOut];
-#pragma unroll
-        for (int o = 0; o < kFiltOut; ++o) acc[o] = 0.25f * sx[skew(n + i0 + o)];
-        if (ntap > 0) {
-            // window holds x[base + t .. base + t + 15] (padded indices) at
-            // slots (t mod 16); t advances by 2 per odd offset j = -jm + t
-            const int base = n + i0 - jm;
-            float win[kFiltOut];
-#pragma unroll
-            for (int o = 0; o < kFiltOut; ++o) win[o] = sx[skew(base + o)];
-            int m = 0;  // offset index: j = -jm + 2 m
-            for (; m + kFiltOut / 2 <= ntap; m += kFiltOut / 2) {
-#pragma unroll
-                for (int q = 0; q < kFiltOut / 2; ++q) {
-                    const int j = -jm + 2 * (m + q);
-                    const int aj = j < 0 ? -j : j;
-                    const float h = c_ramp_odd[aj >> 1];
-#pragma unroll
-                    for (int o = 0; o < kFiltOut; ++o)
-                        acc[o] = fmaf(h, win[(o + 2 * q) % kFiltOut], acc[o]);
-                    win[(2 * q) % kFiltOut] = sx[skew(base + 2 * (m + q) + kFiltOut)];
-                    win[(2 * q + 1) % kFiltOut] = sx[skew(base + 2 * (m + q) + kFiltOut + 1)];
-                }
-            }
-            for (; m < ntap; ++m) {
-                const int j = -jm + 2 * m;
-                const int aj = j < 0 ? -j : j;
-                const float h = c_ramp_odd[aj >> 1];
-#pragma unroll
-                for (int o = 0; o < kFiltOut; ++o)
-                    acc[o] = fmaf(h, sx[skew(base + 2 * m + o)], acc[o]);
-            }
-        }
-#pragma unroll
-        for (int o = 0; o < kFiltOut; ++o)
-            if (i0 + o < n) out(i0 + o, acc[o] * inv_tau);
-    }
-}
-
 // Padded row for the filter: position P = j + off holds sample j (zeros
 // elsewhere; off = jm, the largest odd offset, or 1 for a one-pixel row, so
 // that P is even for even outputs at every odd offset), stored as pairs
@@ -108,12 +59,14 @@ __host__ __device__ __forceinline__ int filt_span(int n) { return (n + 2 * n + k
 
 __device__ __forceinline__ int filt_off(int jm) { return jm >= 1 ? jm : 1; }
 
-// Ram-Lak filtered row (the ramp_row sums, term for term in the same order)
-// from the pair-skewed row sp: 16 outputs per thread as 8 pairs updated by
-// packed binary32 FMAs (each element rounded as a scalar fma), a window of
-// 8 sample pairs advancing one pair per odd offset, and per warp only the
+// Ram-Lak filtered row from the pair-skewed row sp: calls out(i, v) for i in
+// [0, n) with v = (x[i] / 4 + sum over odd j of -x[i + j] / (pi j)^2) / tau,
+// each output summed in binary32 from x[i] / 4 through the odd offsets in
+// ascending order (-jm, ..., jm).  16 outputs per thread as 8 pairs updated
+// by packed binary32 FMAs (each element rounded as a scalar fma), a window
+// of 8 sample pairs advancing one pair per odd offset, and per warp only the
 // offsets at which some output of the warp meets a sample inside the row
-// (the others would add h * 0 to every output).
+// (the others would add h * 0, leaving every output unchanged).
 template <class Out>
 __device__ __forceinline__ void ramp_row_pairs(const float *sp, int n, float inv_tau, Out out)
 {
@@ -196,7 +149,7 @@ k_fdk_filter(const __grid_constant__ FdkParams p, const float *__restrict__ coun
     const int iv = p.v_lo + r;
     const size_t row = ((size_t)k * g.n_v + iv) * n;
     float2 *dst = filt + ((size_t)k * p.ph + (r + 1)) * p.pw;
-    // padded row: position jm + j holds q[j], zeros elsewhere (pair-skewed)
+    // padded row: position off + j holds q[j], zeros elsewhere (pair-skewed)
     const float vi = ((float)iv - g.cv) * g.dv * p.mag;
     const float sad2v = g.sad * g.sad + vi * vi;
     const int off = filt_off(((n - 1) & 1) ? n - 1 : n - 2);
@@ -262,15 +215,16 @@ k_filter_adjoint(const __grid_constant__ FdkParams p, const float *__restrict__ 
     const int r = (int)(blockIdx.x % nrows);
     const int iv = p.v_lo + r;
     const float *src = gf + ((size_t)k * p.ph + (r + 1)) * p.pw + 1;
-    const int span = 3 * n + kFiltOut + 2;
+    const int off = filt_off(((n - 1) & 1) ? n - 1 : n - 2);
+    const int span = filt_span(n);
     for (int i = threadIdx.x; i < span; i += blockDim.x) {
-        const int j = i - n;
-        sx[skew(i)] = j >= 0 && j < n ? src[j] : 0.0f;
+        const int j = i - off;
+        sx[pidx(i)] = j >= 0 && j < n ? src[j] : 0.0f;
     }
     __syncthreads();
     const float vi = ((float)iv - g.cv) * g.dv * p.mag;
     const size_t row = ((size_t)k * g.n_v + iv) * n;
-    ramp_row(sx, n, 1.0f / p.tau, [&](int iu, float gq) {
+    ramp_row_pairs(sx, n, 1.0f / p.tau, [&](int iu, float gq) {
         const float ui = ((float)iu - g.cu) * g.du * p.mag;
         const float cosw = g.sad * rsqrtf(g.sad * g.sad + ui * ui + vi * vi);
         const size_t idx = row + iu;
@@ -293,8 +247,8 @@ cudaError_t launch_filter_adjoint(const FdkParams &p, const float *gf, const flo
     if (p.g.n_u > kMaxFiltTaps) return cudaErrorInvalidValue;
     cudaError_t e = upload_ramp_taps();
     if (e != cudaSuccess) return e;
-    const int span = 3 * p.g.n_u + kFiltOut + 2;
-    const size_t smem = (size_t)(span + span / 32 + 2) * sizeof(float);
+    const int span = filt_span(p.g.n_u);
+    const size_t smem = (size_t)(2 * ((span >> 1) + (span >> 4)) + 4) * sizeof(float);
     if (smem > 48 * 1024) {
         e = cudaFuncSetAttribute(k_filter_adjoint, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)smem);

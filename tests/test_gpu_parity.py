@@ -353,6 +353,29 @@ def test_reconstruct_ragged_volume(fc, orc):
     assert np.max(np.abs(vol - vref)) <= 5e-4 * mu_w
 
 
+@pytest.mark.parametrize("n_u", [1, 2, 5, 33, 97, 600])
+def test_reconstruct_detector_widths(fc, orc, n_u):
+    """Edge cases of the ramp filter's row layout and per-warp offset range:
+    a one-pixel row, even and odd widths, rows of one and of two warps.
+    Reconstruction of random counts against the oracle's FDK."""
+    wl = W.scaled(W.WORKLOADS["small_kv"], n_u=n_u, n_v=6, n_angles=9, nx=8, ny=7, nz=3,
+                  dx=0.05, dy=0.05, dz=0.05, du=0.08, dv=0.08)
+    g = wl.geom
+    counts = (np.random.default_rng(n_u).uniform(0.3, 1.0, (g.n_angles, g.n_v, g.n_u)) *
+              wl.n0).astype(np.float32)
+    sc = _scanner(fc, wl, None)
+    try:
+        vol = torch.empty((g.nz, g.ny, g.nx), dtype=torch.float64, device="cuda")
+        fc.fc_reconstruct(sc.h, counts, vol_mu=vol)
+        torch.cuda.synchronize()
+        got = vol.cpu().numpy()
+    finally:
+        sc.close()
+    vref = orc.fdk(g, counts.astype(np.float64), orc.i_flood(wl.n0, wl.spr))
+    assert np.max(np.abs(vref)) > 0.0
+    assert np.max(np.abs(got - vref)) <= 5e-4 * np.max(np.abs(vref)), np.max(np.abs(got - vref))
+
+
 def test_beer_lambert_single_bin_uniform(fc):
     """One energy bin, D = 1, uniform water box: T = exp(-mu * chord)."""
     wl = W.scaled(W.WORKLOADS["small_kv"], n_u=33, n_v=9, n_angles=5, nx=16, ny=16, nz=16,
