@@ -133,6 +133,7 @@ struct fc_handle {
     // device buffers
     float2 *d_trig = nullptr;
     uint8_t *d_labels = nullptr;   // caller layout [nz][ny][nx]
+    uint8_t *d_labels_zf = nullptr;   // the same, z fastest [ny][nx][nz] (projector walk)
     uint8_t *d_bricks = nullptr;   // 8x8x16 brick map: uniform label or mixed
     float *d_T = nullptr, *d_tp = nullptr, *d_ts = nullptr, *d_counts = nullptr;
     float2 *d_filt = nullptr;   // filtered rows as (value, next - value) pairs
@@ -181,6 +182,7 @@ struct fc_handle {
     {
         dfree(d_trig);
         dfree(d_labels);
+        dfree(d_labels_zf);
         dfree(d_bricks);
         dfree(d_T);
         dfree(d_tp);
@@ -501,6 +503,7 @@ int fc_set_geometry(fc_handle *h, const fc_geometry *g)
     }
     if (!same_vol) {
         dfree(h->d_labels);
+        dfree(h->d_labels_zf);
         dfree(h->d_bricks);
         h->has_phantom = false;
     }
@@ -552,6 +555,7 @@ int fc_set_phantom(fc_handle *h, const uint8_t *labels, int n_mat, int where, vo
     DeviceGuard dgd(h->device);
     cudaStream_t s = (cudaStream_t)stream;
     if (!h->d_labels) FC_CK(dev_malloc((void **)&h->d_labels, h->vol_elems));
+    if (!h->d_labels_zf) FC_CK(dev_malloc((void **)&h->d_labels_zf, h->vol_elems));
     if (!h->d_bricks)
         FC_CK(dev_malloc((void **)&h->d_bricks,
                          (size_t)((h->g.nx + fc::kBrick - 1) / fc::kBrick) *
@@ -559,6 +563,7 @@ int fc_set_phantom(fc_handle *h, const uint8_t *labels, int n_mat, int where, vo
                              ((h->g.nz + fc::kBrickZ - 1) / fc::kBrickZ)));
     FC_CK(cudaMemcpyAsync(h->d_labels, labels, h->vol_elems,
                           where == FC_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, s));
+    FC_CK(fc::launch_labels_zfast(h->d_labels, h->d_labels_zf, h->g.nx, h->g.ny, h->g.nz, s));
     FC_CK(cudaMemsetAsync(h->d_flag, 0, sizeof(unsigned int), s));
     FC_CK(fc::launch_brick_map(h->d_labels, h->d_bricks, h->g.nx, h->g.ny, h->g.nz, n_mat,
                                h->d_flag, s));
@@ -648,6 +653,7 @@ static int fill_proj_params(fc_handle *h, int a0, int na, fc::ProjParams *p)
     p->g = h->dg;
     p->trig = h->d_trig;
     p->labels = h->d_labels;
+    p->labels_zf = h->d_labels_zf;
     p->bricks = h->d_bricks;
     p->angle0 = a0;
     p->n_angles_launch = na;

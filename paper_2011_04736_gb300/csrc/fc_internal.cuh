@@ -35,6 +35,7 @@ struct ProjParams {
     DevGeom g;
     const float2 *trig;     // [n_angles] (cos, sin) of each angle
     const uint8_t *labels;  // [nz][ny][nx]
+    const uint8_t *labels_zf;  // the same labels z fastest: [ny][nx][nz] (the walk reads these)
     const uint8_t *bricks;  // [ceil(nz/kBrickZ)][ceil(ny/kBrick)][ceil(nx/kBrick)]: uniform label or kMixed
     int angle0;             // absolute index of the first angle of the launch
     int n_angles_launch;
@@ -323,6 +324,8 @@ cudaError_t launch_mtf(const MtfParams &p, double *work, double *freq, double *m
 cudaError_t launch_dose(const ProjParams &p, const DoseParams &d, double *part,
                         unsigned long long *count, double *out, cudaStream_t s);
 int dose_blocks(const ProjParams &p);
+cudaError_t launch_labels_zfast(const uint8_t *labels, uint8_t *labels_zf, int nx, int ny, int nz,
+                                cudaStream_t s);
 cudaError_t launch_brick_map(const uint8_t *labels, uint8_t *bricks, int nx, int ny, int nz,
                              int n_mat, unsigned int *bad, cudaStream_t s);
 

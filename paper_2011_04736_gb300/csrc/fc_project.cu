@@ -127,7 +127,7 @@ __device__ __forceinline__ bool trace_ray(const ProjParams &p, int iu, int iv, i
         if (TEST_ONLY) return hit;
         if (hit) {
             const float px = fmaf(t_in, dx, Ax), py = fmaf(t_in, dy, Ay), pz = fmaf(t_in, dz, Az);
-            const int nx = g.nx, ny = g.ny, nz = g.nz, nxy = g.nx * g.ny;
+            const int nx = g.nx, ny = g.ny, nz = g.nz;
             const int ix0 = clampi((int)floorf((px - g.lox) * g.idx), 0, nx - 1);
             const int iy0 = clampi((int)floorf((py - g.loy) * g.idy), 0, ny - 1);
             const int iz0 = clampi((int)floorf((pz - g.loz) * g.idz), 0, nz - 1);
@@ -150,7 +150,11 @@ __device__ __forceinline__ bool trace_ray(const ProjParams &p, int iu, int iv, i
             float tcx = plane_t(cpx, vx, bx_, sx);
             float tcy = plane_t(cpy, vy, by_, sy);
             float tcz = plane_t(cpz, vz, bz_, sz);
-            int cur = __ldg(p.labels + (iz0 * ny + iy0) * nx + ix0);
+            // labels z fastest: voxel (x, y, z) at (y nx + x) nz + z, so the
+            // rays of one detector column (a warp's lanes, a slice or less
+            // apart) read neighbouring bytes
+            const int zsx = nz, zsy = nx * nz;
+            int cur = __ldg(p.labels_zf + (iy0 * nx + ix0) * nz + iz0);
             float t_run = t_in, t_cur = t_in;
             // Coarse passes: each advances one brick index by one step along
             // the ray, so at most nbx + nby + nbz passes occur before an index
@@ -190,8 +194,8 @@ __device__ __forceinline__ bool trace_ray(const ProjParams &p, int iu, int iv, i
                     float tfx = plane_t(fx, vx, bx_, sx);
                     float tfy = plane_t(fy, vy, by_, sy);
                     float tfz = plane_t(fz, vz, bz_, sz);
-                    int id = jz * nxy + jy * nx + jx;
-                    int lab = __ldg(p.labels + id);
+                    int id = (jy * nx + jx) * nz + jz;
+                    int lab = __ldg(p.labels_zf + id);
                     if (lab != cur) {
                         add_run(L, cur, t_cur - t_run);
                         t_run = t_cur;
@@ -201,13 +205,13 @@ __device__ __forceinline__ bool trace_ray(const ProjParams &p, int iu, int iv, i
                         const float tn = fminf(tfx, fminf(tfy, tfz));
                         if (tn >= t_exit) break;
                         if (tfx == tn) {
-                            fx += sx; id += sx; tfx = fmaf((float)fx, vx, bx_);
+                            fx += sx; id += sx * zsx; tfx = fmaf((float)fx, vx, bx_);
                         } else if (tfy == tn) {
-                            fy += sy; id += sy * nx; tfy = fmaf((float)fy, vy, by_);
+                            fy += sy; id += sy * zsy; tfy = fmaf((float)fy, vy, by_);
                         } else {
-                            fz += sz; id += sz * nxy; tfz = fmaf((float)fz, vz, bz_);
+                            fz += sz; id += sz; tfz = fmaf((float)fz, vz, bz_);
                         }
-                        lab = __ldg(p.labels + id);
+                        lab = __ldg(p.labels_zf + id);
                         if (lab != cur) {
                             const float tb = fmaxf(tn, t_run);
                             add_run(L, cur, tb - t_run);
@@ -778,6 +782,26 @@ __global__ void k_brick_map(const uint8_t *__restrict__ lab, uint8_t *__restrict
             bricks[b] = uniform ? (uint8_t)first : (uint8_t)kMixed;
         }
     }
+}
+
+// Labels [nz][ny][nx] -> [ny][nx][nz] (z fastest), one output byte per thread.
+__global__ void __launch_bounds__(256) k_labels_zfast(const uint8_t *__restrict__ src, uint8_t *__restrict__ dst,
+                                                      int nx, int ny, int nz)
+{
+    const long long n = (long long)nx * ny * nz;
+    for (long long o = blockIdx.x * (long long)blockDim.x + threadIdx.x; o < n;
+         o += (long long)gridDim.x * blockDim.x) {
+        const long long col = o / nz;            // y nx + x
+        const int z = (int)(o - col * nz);
+        dst[o] = src[(long long)z * nx * ny + col];
+    }
+}
+
+cudaError_t launch_labels_zfast(const uint8_t *labels, uint8_t *labels_zf, int nx, int ny, int nz,
+                                cudaStream_t s)
+{
+    k_labels_zfast<<<sm_count() * 8, 256, 0, s>>>(labels, labels_zf, nx, ny, nz);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_brick_map(const uint8_t *labels, uint8_t *bricks, int nx, int ny, int nz,
