@@ -304,11 +304,97 @@ void chunked_launch_shape(const FdkParams &p, int *zc_out, dim3 *grid)
 }
 }  // namespace
 
+namespace {
+__device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
+// a - b, exactly as a binary32 subtraction rounds it (b * -1 is exact)
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, f2(-1.0f), a); }
+}  // namespace
+
+// kZc z values per thread, kZc even: the same arithmetic as the scalar body
+// below, issued as packed binary32 pairs over the z values (z, z + kZc / 2)
+// (each element rounded as the scalar instruction rounds it, so the volume
+// is identical), binary64 sums in shared memory.
+template <int kZc>
+__device__ __forceinline__ void backproject_body_pairs(const FdkParams &p, const float2 *__restrict__ f,
+                                                       double *__restrict__ vol)
+{
+    constexpr int NA = kZc / 2;
+    __shared__ double accd[kZc][256];
+    const DevGeom &g = p.g;
+    const int t = threadIdx.y * 32 + threadIdx.x;
+    const int ix = blockIdx.x * 32 + threadIdx.x;
+    const int iy = blockIdx.y * 8 + threadIdx.y;
+    const int iz0 = blockIdx.z * kZc;
+#pragma unroll
+    for (int z = 0; z < kZc; ++z) accd[z][t] = 0.0;
+    if (ix >= g.nx || iy >= g.ny) return;   // no block-wide barrier follows
+    const float x = ((float)ix - 0.5f * (float)(g.nx - 1)) * g.dx;
+    const float y = ((float)iy - 0.5f * (float)(g.ny - 1)) * g.dy;
+    const float z0 = ((float)iz0 - 0.5f * (float)(g.nz - 1)) * g.dz;
+    const int nzc = min(kZc, g.nz - iz0);
+    const unsigned plane = (unsigned)p.ph * (unsigned)p.pw;
+    const float cu1 = g.cu + 1.0f, cv1 = g.cv - (float)p.v_lo + 1.0f;
+    const float umax = (float)(p.pw - 2), vmaxp = (float)(p.ph - 2);
+    const float sdd_du = g.sdd / g.du, sdd_dv = g.sdd / g.dv;
+    const int two23 = __float_as_int(kTwo23);
+    for (int kb = 0; kb < g.n_angles; kb += kFold) {
+        const int ke = min(g.n_angles, kb + kFold);
+        float2 acc[NA];
+#pragma unroll
+        for (int i = 0; i < NA; ++i) acc[i] = make_float2(0.0f, 0.0f);
+#pragma unroll 2
+        for (int k = kb; k < ke; ++k) {
+            const float2 cs = p.trig[k];
+            const float U = g.sad - (x * cs.x + y * cs.y);
+            const float ru = y * cs.x - x * cs.y;
+            float iU;                                   // hardware reciprocal + one Newton step
+            asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(iU) : "f"(U));
+            iU = fmaf(iU, fmaf(-U, iU, 1.0f), iU);
+            const float fu = fminf(fmaxf(fmaf(ru * iU, sdd_du, cu1), 0.0f), umax);
+            const float2 w2 = f2((g.sad * iU) * (g.sad * iU));
+            const float2 fv0 = f2(fmaf(z0 * iU, sdd_dv, cv1));
+            const float2 dfv = f2(g.dz * iU * sdd_dv);
+            const float tu = __fadd_rd(fu, kTwo23);     // 2^23 + floor(fu)
+            const float au = fu - (tu - kTwo23);
+            const unsigned cofs = (unsigned)k * (unsigned)plane + (unsigned)(__float_as_int(tu) - two23);
+#pragma unroll
+            for (int i = 0; i < NA; ++i) {
+                // z values past a ragged last chunk are computed on clamped,
+                // in-buffer coordinates and never stored
+                float2 fv = __ffma2_rn(make_float2((float)i, (float)(i + NA)), dfv, fv0);
+                fv.x = fminf(fmaxf(fv.x, 0.0f), vmaxp);
+                fv.y = fminf(fmaxf(fv.y, 0.0f), vmaxp);
+                const float2 tv = __fadd2_rd(fv, f2(kTwo23));
+                const float2 av = sub2(fv, __fadd2_rn(tv, f2(-kTwo23)));
+                const unsigned oa = (unsigned)(__float_as_int(tv.x) - two23) * (unsigned)p.pw + cofs;
+                const unsigned ob = (unsigned)(__float_as_int(tv.y) - two23) * (unsigned)p.pw + cofs;
+                const float2 a0 = __ldg(f + oa), a1 = __ldg(f + (oa + (unsigned)p.pw));
+                const float2 b0 = __ldg(f + ob), b1 = __ldg(f + (ob + (unsigned)p.pw));
+                const float2 top = make_float2(fmaf(au, a0.y, a0.x), fmaf(au, b0.y, b0.x));
+                const float2 bot = make_float2(fmaf(au, a1.y, a1.x), fmaf(au, b1.y, b1.x));
+                acc[i] = __ffma2_rn(w2, __ffma2_rn(av, sub2(bot, top), top), acc[i]);
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < NA; ++i) {
+            accd[i][t] += (double)acc[i].x;
+            accd[i + NA][t] += (double)acc[i].y;
+        }
+    }
+#pragma unroll
+    for (int z = 0; z < kZc; ++z)
+        if (z < nzc) vol[((size_t)(iz0 + z) * g.ny + iy) * g.nx + ix] = accd[z][t] * p.scale;
+}
+
 // kZc z values per thread (the launcher balances the z chunks).
 template <int kZc>
 __device__ __forceinline__ void backproject_body(const FdkParams &p, const float2 *__restrict__ f,
                                                  double *__restrict__ vol)
 {
+    if constexpr (kZc % 2 == 0) {
+        backproject_body_pairs<kZc>(p, f, vol);
+        return;
+    }
     const DevGeom &g = p.g;
     const int ix = blockIdx.x * 32 + threadIdx.x;
     const int iy = blockIdx.y * 8 + threadIdx.y;
@@ -387,7 +473,10 @@ __global__ void __launch_bounds__(256) k_backproject(const __grid_constant__ Fdk
 }
 
 template <int kZc>
-__global__ void __launch_bounds__(256, 8) k_backproject_dense(const __grid_constant__ FdkParams p,
+// (6 resident CTAs for the packed bodies of 6 or 8 z values: at 8 their
+// binary32 pairs spill)
+__global__ void __launch_bounds__(256, (kZc % 2 == 0 && kZc >= 6) ? 6 : 8)
+k_backproject_dense(const __grid_constant__ FdkParams p,
                                                               const float2 *__restrict__ f,
                                                               double *__restrict__ vol)
 {
@@ -416,11 +505,6 @@ __global__ void __launch_bounds__(256, 8) k_backproject_dense(const __grid_const
 // rows cut at a detector edge, or a detector narrower than the volume's
 // shadow).  The reciprocal of U is the hardware approximation refined by one
 // Newton-Raphson step, r' = r (2 - U r), within an ulp or so of 1 / U.
-namespace {
-__device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
-// a - b, exactly as a binary32 subtraction rounds it (b * -1 is exact)
-__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, f2(-1.0f), a); }
-}  // namespace
 
 template <int NZ, bool CLAMP>
 __global__ void __launch_bounds__(256)
