@@ -322,8 +322,10 @@ __device__ __forceinline__ void backproject_body_pairs(const FdkParams &p, const
     __shared__ double accd[kZc][256];
     const DevGeom &g = p.g;
     const int t = threadIdx.y * 32 + threadIdx.x;
-    const int ix = blockIdx.x * 32 + threadIdx.x;
-    const int iy = blockIdx.y * 8 + threadIdx.y;
+    // a warp covers 8 x 4 voxels of the CTA's 32 x 8 (its taps then span
+    // fewer detector columns and, through the perspective, fewer rows)
+    const int ix = blockIdx.x * 32 + (threadIdx.y % 4) * 8 + threadIdx.x % 8;
+    const int iy = blockIdx.y * 8 + (threadIdx.y / 4) * 4 + threadIdx.x / 8;
     const int iz0 = blockIdx.z * kZc;
 #pragma unroll
     for (int z = 0; z < kZc; ++z) accd[z][t] = 0.0;
@@ -396,8 +398,10 @@ __device__ __forceinline__ void backproject_body(const FdkParams &p, const float
         return;
     }
     const DevGeom &g = p.g;
-    const int ix = blockIdx.x * 32 + threadIdx.x;
-    const int iy = blockIdx.y * 8 + threadIdx.y;
+    // a warp covers 8 x 4 voxels of the CTA's 32 x 8 (its taps then span
+    // fewer detector columns and, through the perspective, fewer rows)
+    const int ix = blockIdx.x * 32 + (threadIdx.y % 4) * 8 + threadIdx.x % 8;
+    const int iy = blockIdx.y * 8 + (threadIdx.y / 4) * 4 + threadIdx.x / 8;
     const int iz0 = blockIdx.z * kZc;
     if (ix >= g.nx || iy >= g.ny) return;
     const float x = ((float)ix - 0.5f * (float)(g.nx - 1)) * g.dx;
@@ -515,8 +519,9 @@ k_backproject_slab(const __grid_constant__ FdkParams p, const float2 *__restrict
     __shared__ double accd[NZ][256];
     const DevGeom &g = p.g;
     const int t = threadIdx.y * 32 + threadIdx.x;
-    const int ix = blockIdx.x * 32 + threadIdx.x;
-    const int iy = blockIdx.y * 8 + threadIdx.y;
+    // a warp covers 8 x 4 voxel columns of the CTA's 32 x 8
+    const int ix = blockIdx.x * 32 + (threadIdx.y % 4) * 8 + threadIdx.x % 8;
+    const int iy = blockIdx.y * 8 + (threadIdx.y / 4) * 4 + threadIdx.x / 8;
 #pragma unroll
     for (int z = 0; z < NZ; ++z) accd[z][t] = 0.0;
     if (ix >= g.nx || iy >= g.ny) return;   // no block-wide barrier follows
