@@ -9,6 +9,16 @@
 
 namespace fc {
 
+// 2^x by the hardware approximation (ex2.approx.ftz; subnormal results are
+// flushed to zero), the energy integral's exponential.  Its error enters T
+// through the parity tests against the binary64 oracle (<= 1e-4 relative).
+__device__ __forceinline__ float exp2_hw(float x)
+{
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 constexpr int kMaxMat = FC_MAX_MATERIALS;
 constexpr int kMaxBins = FC_MAX_BINS;
 constexpr int kMaxTaps = 2 * 256 + 1;  // 2 * ceil(4 * FC_MAX_SIGMA_PX) + 1

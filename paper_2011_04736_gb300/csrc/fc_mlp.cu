@@ -275,7 +275,7 @@ __device__ __forceinline__ float exact_lnT(const float (&L)[kMaxMat], const floa
         float a = 0.0f;
 #pragma unroll
         for (int m = 0; m < kMaxMat; ++m) a = fmaf(mu2[e][m], L[m], a);
-        const float term = wd[e] * exp2f(-a);
+        const float term = wd[e] * exp2_hw(-a);
         const float y = term - comp;
         const float t = sum + y;
         comp = (t - sum) - y;

@@ -264,7 +264,7 @@ __device__ __forceinline__ float energy_T(const ProjParams &p, bool hit, const f
             float a = 0.0f;
 #pragma unroll
             for (int m = 0; m < kMaxMat; ++m) a = fmaf(p.mu2[e][m], L[m], a);
-            const float term = p.wd[e] * exp2f(-a);
+            const float term = p.wd[e] * exp2_hw(-a);
             const float y = term - comp;
             const float t = sum + y;
             comp = (t - sum) - y;
@@ -530,7 +530,7 @@ k_project_groups(const __grid_constant__ ProjParams p, float *__restrict__ P, in
             float a = 0.0f;
 #pragma unroll
             for (int m = 0; m < kMaxMat; ++m) a = fmaf(p.mu2[e][m], L[m], a);
-            const float term = p.wd[e] * exp2f(-a);
+            const float term = p.wd[e] * exp2_hw(-a);
             const float y = term - comp;
             const float t = sum + y;
             comp = (t - sum) - y;
