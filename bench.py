@@ -625,7 +625,9 @@ def _extras(args, fc, torch, n_sm, mhz):
             return {"workload": "head_surrogate: 256^3 voxels, 360 projections of 512x512, "
                                 "120 bins, %d rays" % r["rays"],
                     "train": r["train"], "accuracy": r["accuracy"], "guard": r["guard"],
-                    "speed_ms": r["speed_ms"], "crossover_bins": r["crossover_bins"]}
+                    "speed_ms": r["speed_ms"], "exact_ms_vs_bins": r["exact_ms_vs_bins"],
+                    "surrogate_speedup_vs_bins": r["surrogate_speedup_vs_bins"],
+                    "crossover_bins": r["crossover_bins"]}
         jobs.append(("surrogate", sur))
     if args.extra:
         jobs = [j for j in jobs if j[0] in args.extra]
