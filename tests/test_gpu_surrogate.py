@@ -318,6 +318,22 @@ def test_surrogate_fallback_outside_box(fc, trained):
     assert torch.equal(out, exact)
 
 
+def test_surrogate_eval_ragged_batches(fc, trained):
+    """Every ray's result is independent of the batch it is evaluated in:
+    batches of 1, 127, 129 and 383 rays (one tile, a tile and a ray, three
+    tiles shared unevenly by the kernel's two groups) reproduce, bit for bit,
+    the same rays evaluated inside the whole scan."""
+    wl, sc, L, y, _ = trained
+    full = torch.empty_like(y)
+    fc.fc_surrogate_eval(sc.h, L, full)
+    for n in (1, 127, 129, 383):
+        start = 1000 + 7 * n
+        part = torch.empty(n, device="cuda")
+        fc.fc_surrogate_eval(sc.h, L[start:start + n].contiguous(), part)
+        torch.cuda.synchronize()
+        assert torch.equal(part, full[start:start + n]), n
+
+
 def test_surrogate_checkpoint_roundtrip(fc, trained):
     wl, sc, L, y, _ = trained
     st = fc.fc_surrogate_get(sc.h)
