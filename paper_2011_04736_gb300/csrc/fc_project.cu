@@ -15,8 +15,10 @@
 // registers and feed the energy integral
 //     T = sum_E (w D)_E exp(-sum_m mu_m(E) L_m)        (w D normalised)
 // evaluated with exp2 and a compensated (Kahan) sum over the energy bins.
-// A warp covers 32 consecutive pixels of one detector row, so the T stores
-// are coalesced 128-byte rows.
+// A warp covers 32 consecutive rays of one detector column (the band order
+// below), so each lane's T store lands in its own detector row: one store
+// per ray, a small part of the walk's cost; the rows of T that the band
+// does not cover are written by a store-only kernel in float4 rows.
 //
 // Numerics: the ray is represented by its point A closest to the rotation
 // axis and a unit direction, both rotated from the gantry frame, so every
