@@ -233,8 +233,9 @@ int fc_reconstruct(fc_handle *h, const float *counts, int counts_where,
  * counterpart; every variant computes the same backprojection of
  * fc_reconstruct, Sec. II.G, the sums differing only in rounding).
  *   FC_BP_AUTO          (default) the fastest applicable for the geometry:
- *                       FC_BP_SLAB where it applies, else FC_BP_CHUNKED_DENSE
- *                       for grids of two or more waves, else FC_BP_CHUNKED;
+ *                       FC_BP_SLAB_SYM, else FC_BP_SLAB, else
+ *                       FC_BP_CHUNKED_DENSE for grids of two or more waves,
+ *                       else FC_BP_CHUNKED;
  *   FC_BP_CHUNKED       one thread per (x, y) column and chunk of z slices,
  *                       four bilinear taps per voxel update;
  *   FC_BP_CHUNKED_DENSE the same body capped at 32 registers (8 CTAs per SM);
@@ -243,6 +244,15 @@ int fc_reconstruct(fc_handle *h, const float *counts, int counts_where,
  *                       when nz <= 16 and the z pitch projects to at most 0.98
  *                       detector rows at every voxel (dz SDD / (SAD - r_max)
  *                       <= 0.98 dv, r_max the half-diagonal of the volume).
+ *   FC_BP_SLAB_SYM      the thin-slab walk for the four columns that a
+ *                       quarter turn about the axis maps onto one another,
+ *                       one column set-up serving projections k, k + N/4,
+ *                       k + N/2 and k + 3N/4.  Applies where FC_BP_SLAB does
+ *                       and the scan is a full circle (arc_rad = 2 pi within
+ *                       1e-12 relative) of n_angles divisible by 4 over a
+ *                       grid with nx = ny even and dx_cm = dy_cm.  The
+ *                       volume is written with binary64 atomic adds (two per
+ *                       voxel onto zero: deterministic).
  * fc_reconstruct and fc_cnr_grad fail with FC_EINVAL when the requested
  * variant does not apply (for every variant: when the stored filtered rows,
  * n_angles x (reachable rows + 3) x (n_u + 3, rounded up to 4), reach 2^31
@@ -254,6 +264,7 @@ int fc_reconstruct(fc_handle *h, const float *counts, int counts_where,
 #define FC_BP_CHUNKED       1
 #define FC_BP_CHUNKED_DENSE 2
 #define FC_BP_SLAB          3
+#define FC_BP_SLAB_SYM      4
 int fc_set_backprojector(fc_handle *h, int variant);
 int fc_backprojector_in_use(fc_handle *h, int *variant);
 

@@ -1047,10 +1047,26 @@ int fc_set_noise_order(fc_handle *h, int order)
 int fc_set_backprojector(fc_handle *h, int variant)
 {
     if (!h) return fail(FC_EINVAL, "fc_set_backprojector: null handle");
-    if (variant < FC_BP_AUTO || variant > FC_BP_SLAB)
+    if (variant < FC_BP_AUTO || variant > FC_BP_SLAB_SYM)
         return fail(FC_EINVAL, "fc_set_backprojector: unknown variant %d", variant);
     h->bp_request = variant;
     return FC_OK;
+}
+
+// Projections per half / quarter turn of a full-circle scan (0 when the
+// scan is not a full circle or n_angles is not divisible by 2 / 4).
+// Whether a quarter turn about the axis maps the voxel grid onto itself.
+static bool g_sym_quarter_ok(const fc_geometry &g)
+{
+    return g.nx == g.ny && g.nx % 2 == 0 && g.dx_cm == g.dy_cm;
+}
+
+static int fdk_sym_turn(const fc_geometry &g, int parts)
+{
+    const double two_pi = 2.0 * M_PI;
+    if (g.n_angles < parts || g.n_angles % parts != 0) return 0;
+    if (!(fabs(g.arc_rad - two_pi) <= 1e-12 * two_pi)) return 0;
+    return g.n_angles / parts;
 }
 
 // FdkParams of the handle's geometry (no buffers touched).
@@ -1066,6 +1082,7 @@ static void fill_fdk_params(const fc_handle *h, fc::FdkParams *p)
     fc::fdk_row_range(h->dg, &p->v_lo, &p->v_hi);
     p->pw = fdk_row_pitch(h->g.n_u);
     p->ph = p->v_hi - p->v_lo + 1 + 3;
+    p->sym_quarter = g_sym_quarter_ok(h->g) ? fdk_sym_turn(h->g, 4) : 0;
 }
 
 int fc_backprojector_in_use(fc_handle *h, int *variant)
@@ -1778,6 +1795,7 @@ int fc_cnr_grad(fc_handle *h, const double *logits, const double *D, const doubl
     fc::fdk_row_range(h->dg, &pf.v_lo, &pf.v_hi);
     pf.pw = fdk_row_pitch(h->g.n_u);
     pf.ph = pf.v_hi - pf.v_lo + 1 + 3;
+    pf.sym_quarter = g_sym_quarter_ok(h->g) ? fdk_sym_turn(h->g, 4) : 0;
     fc::CnrParams cp;
     memset(&cp, 0, sizeof(cp));
     cp.g = h->dg;

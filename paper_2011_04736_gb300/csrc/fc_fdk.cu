@@ -287,6 +287,7 @@ constexpr int kSlabMaxNz = 16;   // slices the thin-slab kernel keeps per thread
 // largest projected z pitch (detector rows) the thin-slab kernel takes: the
 // row index may then advance by at most one per slice, rounding included
 constexpr double kSlabMaxStep = 0.98;
+constexpr int kSymMaxRun = 5;      // slices per thread of the quarter-turn kernel (more spill)
 
 // Chunked kernel: z values per thread as many as possible (the per-angle
 // column set-up is shared by them) while keeping about 48 resident warps
@@ -599,6 +600,168 @@ k_backproject_slab(const __grid_constant__ FdkParams p, const float2 *__restrict
     for (int z = 0; z < NZ; ++z) vol[((size_t)z * g.ny + iy) * g.nx + ix] = accd[z][t] * p.scale;
 }
 
+// Thin slabs of a full-circle scan of a square grid centred on the axis:
+// turning a voxel column by a quarter turn about the axis while the gantry
+// turns by a quarter turn leaves its geometry unchanged (U = SAD - (x cos +
+// y sin) and the detector abscissa y cos - x sin are invariant under
+// (x, y, theta) -> (-y, x, theta + pi/2)).  With N projections equally
+// spaced over 2 pi and N a multiple of 4, projection k + N/4 is projection k
+// turned by a quarter turn, so the column set-up of base column c at
+// projection k (U, 1 / U, the detector abscissa and its fraction, the
+// weight) and every slice's row index and row fraction also hold for the
+// turned columns R^t c at projections k + t N / 4 (mod N), t = 1, 2, 3, with
+// R (ix, iy) = (n-1-iy, ix).  One thread takes a base column of the quadrant
+// ix, iy < n / 2 (the four quadrants are the orbits of an even n); per
+// projection it computes that geometry once and then loads, interpolates
+// and sums the taps of the four columns, the sums as packed binary32 pairs
+// (each element rounded as the scalar instruction rounds it).  A slice
+// whose row index equals the previous slice's reuses both interpolated rows
+// and loads nothing.  A thread takes one of R balanced runs of consecutive
+// slices (at most NS) and one half of the projections (grid z = 2 R; the
+// halves on separate CTAs make more, shorter CTAs, so the last round of
+// resident CTAs is less empty).  The projections are walked in segments of
+// at most kFold in which no turned projection index wraps past N, so each
+// column's projection is a fixed offset from k there; binary32 sums over a
+// segment are folded into binary64 sums in shared memory.  Every voxel then
+// receives exactly two atomic binary64 adds onto a zeroed volume, whose sum
+// x + y does not depend on their order.  Floors, reciprocal and clamps as
+// in k_backproject_slab.
+template <int NS, bool CLAMP>
+__global__ void __launch_bounds__(256, 4)
+k_backproject_sym(const __grid_constant__ FdkParams p, const float2 *__restrict__ f,
+                  double *__restrict__ vol)
+{
+    __shared__ double accd[4 * NS][256];
+    const DevGeom &g = p.g;
+    const int n = g.nx, NZ = g.nz;
+    const int t = threadIdx.y * 32 + threadIdx.x;
+    const int ix = blockIdx.x * 32 + (threadIdx.y % 4) * 8 + threadIdx.x % 8;
+    const int iy = blockIdx.y * 8 + (threadIdx.y / 4) * 4 + threadIdx.x / 8;
+#pragma unroll
+    for (int i = 0; i < 4 * NS; ++i) accd[i][t] = 0.0;
+    if (ix >= n / 2 || iy >= n / 2) return;   // no block-wide barrier follows
+    // grid z = (half of the projections) x (run of slices); run r of R holds
+    // slices [r NZ / R, (r + 1) NZ / R)
+    const int R = (int)gridDim.z / 2;
+    const int run = (int)blockIdx.z % R, half = (int)blockIdx.z / R;
+    const int zb = run * NZ / R;
+    const int ns = (run + 1) * NZ / R - zb;
+    const float x = ((float)ix - 0.5f * (float)(n - 1)) * g.dx;
+    const float y = ((float)iy - 0.5f * (float)(n - 1)) * g.dy;
+    const float zc = (-0.5f * (float)(NZ - 1) + (float)zb) * g.dz;   // the run's first slice
+    const unsigned plane = (unsigned)p.ph * (unsigned)p.pw;
+    const float cu1 = g.cu + 1.0f, cv1 = g.cv - (float)p.v_lo + 1.0f;
+    const float umax = (float)(p.pw - 2), vmaxp = (float)(p.ph - 2);
+    const float sdd_du = g.sdd / g.du, sdd_dv = g.sdd / g.dv, dz_dv = g.dz * (g.sdd / g.dv);
+    const int two23 = __float_as_int(kTwo23);
+    const int N = g.n_angles, Q = N / 4;     // projections per quarter turn
+    const int kend = (half + 1) * (N / 2);
+    // segments of at most kFold projections in which no turned projection
+    // index k + u Q wraps past N (k within one quarter [b Q, (b + 1) Q))
+    for (int kb = half * (N / 2); kb < kend;) {
+        const int blk = kb / Q;
+        const int ke = min(min(kend, kb + kFold), (blk + 1) * Q);
+        // offset of column u's projection from projection k: (u Q - N [blk + u >= 4]) planes
+        const unsigned d1 = (unsigned)(Q - (blk >= 3 ? N : 0)) * plane;
+        const unsigned d2 = (unsigned)(2 * Q - (blk >= 2 ? N : 0)) * plane;
+        const unsigned d3 = (unsigned)(3 * Q - (blk >= 1 ? N : 0)) * plane;
+        float2 a01[NS], a23[NS];
+#pragma unroll
+        for (int i = 0; i < NS; ++i) a01[i] = a23[i] = make_float2(0.0f, 0.0f);
+        for (int k = kb; k < ke; ++k) {
+            const float2 cs = p.trig[k];
+            const float U = g.sad - (x * cs.x + y * cs.y);
+            const float ru = y * cs.x - x * cs.y;
+            float iU;
+            asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(iU) : "f"(U));
+            iU = fmaf(iU, fmaf(-U, iU, 1.0f), iU);
+            float fu = fmaf(ru * iU, sdd_du, cu1);
+            if (CLAMP) fu = fminf(fmaxf(fu, 0.0f), umax);
+            const float tu = __fadd_rd(fu, kTwo23);          // 2^23 + floor(fu)
+            const float au = fu - (tu - kTwo23);
+            const float2 w2 = f2((g.sad * iU) * (g.sad * iU));
+            const float fv0 = fmaf(zc * iU, sdd_dv, cv1);
+            const float dfv = dz_dv * iU;
+            // element offsets of row r + 1 of the column in each column's
+            // projection: (2^23 + r) pw + o_u in 32-bit modular arithmetic
+            // (the true offsets are below 2^31)
+            const unsigned o0 = (unsigned)k * plane + (unsigned)(__float_as_int(tu) - two23) +
+                                (unsigned)(1 - two23) * (unsigned)p.pw;
+            const unsigned o1 = o0 + d1, o2 = o0 + d2, o3 = o0 + d3;
+            float2 lo01, lo23, hi01, hi23;
+            int jp = 0;
+#pragma unroll
+            for (int i = 0; i < NS; ++i) {
+                if (i < ns) {
+                    float fv = fmaf((float)i, dfv, fv0);
+                    if (CLAMP) fv = fminf(fmaxf(fv, 0.0f), vmaxp);
+                    const float tv = __fadd_rd(fv, kTwo23);      // 2^23 + floor(fv)
+                    const float2 av = f2(fv - (tv - kTwo23));
+                    const int j = __float_as_int(tv);
+                    const unsigned r = (unsigned)j * (unsigned)p.pw;
+                    if (i == 0) {
+                        // rows j and j + 1 of each column
+                        const unsigned rl = r - (unsigned)p.pw;
+                        const float2 p0 = __ldg(f + (rl + o0)), p1 = __ldg(f + (rl + o1));
+                        const float2 p2 = __ldg(f + (rl + o2)), p3 = __ldg(f + (rl + o3));
+                        const float2 q0 = __ldg(f + (r + o0)), q1 = __ldg(f + (r + o1));
+                        const float2 q2 = __ldg(f + (r + o2)), q3 = __ldg(f + (r + o3));
+                        lo01.x = fmaf(au, p0.y, p0.x);
+                        lo01.y = fmaf(au, p1.y, p1.x);
+                        lo23.x = fmaf(au, p2.y, p2.x);
+                        lo23.y = fmaf(au, p3.y, p3.x);
+                        hi01.x = fmaf(au, q0.y, q0.x);
+                        hi01.y = fmaf(au, q1.y, q1.x);
+                        hi23.x = fmaf(au, q2.y, q2.x);
+                        hi23.y = fmaf(au, q3.y, q3.x);
+                    } else if (j != jp) {
+                        // the row advanced: the old row j + 1 is row j; load the new row j + 1
+                        const float2 q0 = __ldg(f + (r + o0)), q1 = __ldg(f + (r + o1));
+                        const float2 q2 = __ldg(f + (r + o2)), q3 = __ldg(f + (r + o3));
+                        lo01 = hi01;
+                        lo23 = hi23;
+                        hi01.x = fmaf(au, q0.y, q0.x);
+                        hi01.y = fmaf(au, q1.y, q1.x);
+                        hi23.x = fmaf(au, q2.y, q2.x);
+                        hi23.y = fmaf(au, q3.y, q3.x);
+                    }
+                    jp = j;
+                    a01[i] = __ffma2_rn(w2, __ffma2_rn(av, sub2(hi01, lo01), lo01), a01[i]);
+                    a23[i] = __ffma2_rn(w2, __ffma2_rn(av, sub2(hi23, lo23), lo23), a23[i]);
+                }
+            }
+        }
+        // one sum at a time (the compiler otherwise hoists every shared load
+        // and conversion of the fold and spills)
+#pragma unroll
+        for (int i = 0; i < NS; ++i) {
+            accd[4 * i + 0][t] += (double)a01[i].x;
+            asm volatile("" ::: "memory");
+            accd[4 * i + 1][t] += (double)a01[i].y;
+            asm volatile("" ::: "memory");
+            accd[4 * i + 2][t] += (double)a23[i].x;
+            asm volatile("" ::: "memory");
+            accd[4 * i + 3][t] += (double)a23[i].y;
+            asm volatile("" ::: "memory");
+        }
+        kb = ke;
+    }
+#pragma unroll
+    for (int i = 0; i < NS; ++i) {
+        if (i < ns) {
+            const size_t zo = (size_t)(zb + i) * n;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                // the orbit's columns c, R c, R^2 c, R^3 c
+                const int cx = u == 0 ? ix : u == 1 ? n - 1 - iy : u == 2 ? n - 1 - ix : iy;
+                const int cy = u == 0 ? iy : u == 1 ? ix : u == 2 ? n - 1 - iy : n - 1 - ix;
+                atomicAdd(vol + (zo + cy) * n + cx, accd[4 * i + u][t] * p.scale);
+                asm volatile("" ::: "memory");
+            }
+        }
+    }
+}
+
 // Whether a voxel can project outside the stored filtered rows (fdk_row_range
 // cut them at a detector edge) or outside the detector columns with less
 // than two pixels to spare (|u| <= SDD r_max / (SAD - r_max) at the voxels).
@@ -624,14 +787,60 @@ double fdk_slab_row_step(const DevGeom &g)
     return (double)g.dz * (double)g.sdd / umin / (double)g.dv;
 }
 
+template <int S>
+static int sym_occupancy(bool clamp)
+{
+    int n = 0;
+    const cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &n, clamp ? (const void *)k_backproject_sym<S, true> : (const void *)k_backproject_sym<S, false>, 256, 0);
+    return (e == cudaSuccess && n > 0) ? n : 1;
+}
+
+// Slice runs of the quarter-turn kernel: the number of balanced runs (at
+// most kSymMaxRun slices each) whose grid, in whole rounds of resident
+// CTAs, issues the fewest instructions per SM (a column set-up of about 30
+// instructions per projection and run, about 28 per slice; a short last
+// round costs as much as a full one).
+static void sym_launch_shape(const FdkParams &p, bool clamp, int *ns_out, dim3 *grid)
+{
+    const int tx = (p.g.nx / 2 + 31) / 32, ty = (p.g.nx / 2 + 7) / 8;
+    const long tiles = (long)tx * ty;
+    double best = 0.0;
+    int br = 0;
+    for (int runs = (p.g.nz + kSymMaxRun - 1) / kSymMaxRun; runs <= p.g.nz; ++runs) {
+        const int ns = (p.g.nz + runs - 1) / runs;
+        int occ = 1;
+        switch (ns) {
+        case 1: occ = sym_occupancy<1>(clamp); break;
+        case 2: occ = sym_occupancy<2>(clamp); break;
+        case 3: occ = sym_occupancy<3>(clamp); break;
+        case 4: occ = sym_occupancy<4>(clamp); break;
+        default: occ = sym_occupancy<5>(clamp); break;
+        }
+        const long slots = (long)occ * sm_count();
+        const long rounds = (tiles * runs * 2 + slots - 1) / slots;
+        const double cost = (double)rounds * (30.0 + 28.0 * ns);
+        if (br == 0 || cost < best) {
+            best = cost;
+            br = runs;
+        }
+    }
+    *ns_out = (p.g.nz + br - 1) / br;
+    *grid = dim3(tx, ty, 2 * br);
+}
+
 int backproject_variant(const FdkParams &p, int request)
 {
     // every kernel addresses the filtered rows with 32-bit element offsets
     if ((double)p.g.n_angles * p.ph * p.pw >= 2147483648.0) return -1;
     const bool slab_ok = p.g.nz <= kSlabMaxNz && fdk_slab_row_step(p.g) <= kSlabMaxStep;
+    const bool sym_ok = slab_ok && p.sym_quarter > 0 && 4 * p.sym_quarter == p.g.n_angles &&
+                        p.g.nx == p.g.ny && p.g.nx % 2 == 0;
+    if (request == FC_BP_SLAB_SYM) return sym_ok ? FC_BP_SLAB_SYM : -1;
     if (request == FC_BP_SLAB) return slab_ok ? FC_BP_SLAB : -1;
     if (request == FC_BP_CHUNKED || request == FC_BP_CHUNKED_DENSE) return request;
     if (request != FC_BP_AUTO) return -1;
+    if (sym_ok) return FC_BP_SLAB_SYM;
     if (slab_ok) return FC_BP_SLAB;
     int zc;
     dim3 grid;
@@ -647,6 +856,28 @@ int backproject_variant(const FdkParams &p, int request)
 cudaError_t launch_backproject(const FdkParams &p, const float2 *filt, double *vol, int variant,
                                cudaStream_t s)
 {
+    if (variant == FC_BP_SLAB_SYM) {
+        const bool clamp = slab_needs_clamp(p.g);
+        int ns;
+        dim3 grid;
+        sym_launch_shape(p, clamp, &ns, &grid);
+        const dim3 block(32, 8);
+        // the two halves add onto zero
+        const cudaError_t e = cudaMemsetAsync(vol, 0, sizeof(double) * (size_t)p.g.nx * p.g.ny * p.g.nz, s);
+        if (e != cudaSuccess) return e;
+#define FC_BPY(S)                                                                             \
+    case S:                                                                                   \
+        if (clamp) k_backproject_sym<S, true><<<grid, block, 0, s>>>(p, filt, vol);           \
+        else k_backproject_sym<S, false><<<grid, block, 0, s>>>(p, filt, vol);                \
+        break;
+        switch (ns) {
+        FC_BPY(1) FC_BPY(2) FC_BPY(3) FC_BPY(4) FC_BPY(5)
+        default:
+            return cudaErrorInvalidValue;
+        }
+#undef FC_BPY
+        return cudaGetLastError();
+    }
     if (variant == FC_BP_SLAB) {
         dim3 block(32, 8);
         dim3 grid((p.g.nx + 31) / 32, (p.g.ny + 7) / 8);

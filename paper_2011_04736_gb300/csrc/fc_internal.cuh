@@ -169,6 +169,8 @@ struct FdkParams {
     double scale;           // arc / (2 n_angles)
     int v_lo, v_hi;         // reachable detector rows
     int pw, ph;             // padded row length (n_u + 3 rounded up to 4), padded rows (v_hi - v_lo + 1) + 3
+    int sym_quarter;        // n_angles / 4 for a full-circle scan of n_angles divisible by 4 over a
+                            // square grid with an even side and dx = dy (quarter-turn symmetry), else 0
 };
 
 void fdk_row_range(const DevGeom &g, int *v_lo, int *v_hi);

@@ -1,8 +1,9 @@
 """GPU parity of the FDK backprojector variants (fc_set_backprojector)
-against the FP64 oracle: the chunked kernel, its 32-register variant and the
-thin-slab kernel, each forced on small ragged cases and on the full
-paper-scale grid (1024^2 x 10 voxels, 720 projections).  Tolerance
-|d mu| <= 5e-4 mu_water (0.5 HU)."""
+against the FP64 oracle: the chunked kernel, its 32-register variant, the
+thin-slab kernel and its quarter-turn form (one column set-up shared by the
+four columns a quarter turn maps onto one another), each forced on small
+ragged cases and on the full paper-scale grid (1024^2 x 10 voxels, 720
+projections).  Tolerance |d mu| <= 5e-4 mu_water (0.5 HU)."""
 import math
 
 import numpy as np
@@ -81,6 +82,61 @@ def test_variants_thin_slab(fc, orc, nz):
     assert d <= 1e-5 * scale, d / scale
 
 
+@pytest.mark.parametrize("nz,n_u", [(10, 96), (1, 96), (16, 96), (7, 96), (10, 40)])
+def test_quarter_turn_thin_slab(fc, orc, nz, n_u):
+    """The quarter-turn kernel on a square grid with an even side (38: a
+    19 x 19 quadrant of base columns, ragged against the 32 x 8 CTA tile)
+    and 24 projections over 360 degrees; n_u = 40 leaves the volume's shadow
+    wider than the detector (the clamped coordinates).  Compared with the
+    oracle and with the thin-slab kernel."""
+    wl = _thin_slab(nx=38, ny=38, nz=nz)
+    wl = W.scaled(wl, n_u=n_u)
+    g = wl.geom
+    assert fc_step(g) <= 0.98 and g.n_angles % 4 == 0 and abs(g.arc - 2 * math.pi) < 1e-15
+    lab = np.random.default_rng(60 + nz).integers(0, 7, size=(g.nz, g.ny, g.nx)).astype(np.uint8)
+    counts = _oracle_counts(orc, wl, lab)
+    vref = orc.fdk(g, counts.astype(np.float64), orc.i_flood(wl.n0, wl.spr))
+    scale = float(np.max(np.abs(vref)))
+    vols = {}
+    for req in (fc.FC_BP_AUTO, fc.FC_BP_SLAB_SYM, fc.FC_BP_SLAB):
+        vol, used = _recon(fc, wl, counts, req)
+        assert used == (fc.FC_BP_SLAB_SYM if req == fc.FC_BP_AUTO else req)
+        err = np.max(np.abs(vol - vref))
+        assert err <= MU_TOL * scale, (req, err / scale)
+        vols[req] = vol
+    # the same sums in another order and from rotated trigonometry
+    d = np.max(np.abs(vols[fc.FC_BP_SLAB_SYM] - vols[fc.FC_BP_SLAB]))
+    assert d <= 1e-5 * scale, d / scale
+    # deterministic: the two halves of the projections add onto zero
+    vol2, _ = _recon(fc, wl, counts, fc.FC_BP_SLAB_SYM)
+    assert np.array_equal(vol2, vols[fc.FC_BP_SLAB_SYM])
+
+
+@pytest.mark.parametrize("change", ["angles", "arc", "rect", "odd", "pitch"])
+def test_quarter_turn_refused_without_symmetry(fc, change):
+    """Without the quarter-turn symmetry (projections not a multiple of 4,
+    a partial arc, a rectangular or odd grid, unequal x and y pitch) the
+    kernel is refused and the default falls back to the thin-slab kernel."""
+    kw = {"angles": dict(n_angles=22), "arc": dict(arc=1.5 * math.pi),
+          "rect": dict(nx=38, ny=36), "odd": dict(nx=37, ny=37), "pitch": dict(nx=38, ny=38, dy=0.085)}[change]
+    base = dict(nx=38, ny=38)
+    base.update({k: v for k, v in kw.items() if k in ("nx", "ny")})
+    wl = _thin_slab(**base)
+    rest = {k: v for k, v in kw.items() if k not in ("nx", "ny")}
+    if rest:
+        wl = W.scaled(wl, **rest)
+    assert fc_step(wl.geom) <= 0.98
+    sc = fc.Scanner(wl, noise=False)
+    try:
+        assert fc.fc_backprojector_in_use(sc.h) == fc.FC_BP_SLAB
+        fc.fc_set_backprojector(sc.h, fc.FC_BP_SLAB_SYM)
+        with pytest.raises(fc.FastcatError) as ei:
+            fc.fc_backprojector_in_use(sc.h)
+        assert ei.value.code == fc.FC_EINVAL
+    finally:
+        sc.close()
+
+
 def fc_step(g):
     """Largest projected z pitch in detector rows (host restatement of the
     condition the slab kernel needs)."""
@@ -147,8 +203,9 @@ def test_full_paper_mv_reconstruct_variants(fc, orc, precision):
     projections of 1024 x 768): synthetic counts on the rows the volume
     projects onto, flood elsewhere.  The oracle reconstructs from a
     32-row detector centred like the full one (the same pixel centres; no
-    voxel projects outside it); every voxel of the slab kernel (the
-    default here) and of the 32-register chunked kernel is compared."""
+    voxel projects outside it); every voxel of the quarter-turn kernel (the
+    default here), the thin-slab kernel and the 32-register chunked kernel
+    is compared."""
     wl = W.WORKLOADS["paper_mv"]
     g = wl.geom
     flood = wl.n0 * (1.0 + wl.spr)
@@ -166,9 +223,9 @@ def test_full_paper_mv_reconstruct_variants(fc, orc, precision):
     mu_w = float(np.mean(vref[W.water_roi_mask(g)]))
     counts = torch.full((g.n_angles, g.n_v, g.n_u), flood, dtype=torch.float32, device="cuda")
     counts[:, r0:r0 + crop] = torch.from_numpy(band).cuda()
-    for req in (fc.FC_BP_AUTO, fc.FC_BP_CHUNKED_DENSE):
+    for req in (fc.FC_BP_AUTO, fc.FC_BP_SLAB, fc.FC_BP_CHUNKED_DENSE):
         vol, used = _recon(fc, wl, counts, req, lab=np.zeros((g.nz, g.ny, g.nx), np.uint8))
-        assert used == (fc.FC_BP_SLAB if req == fc.FC_BP_AUTO else req)
+        assert used == (fc.FC_BP_SLAB_SYM if req == fc.FC_BP_AUTO else req)
         err = np.max(np.abs(vol - vref))
         precision("mu (FDK)", "paper_mv every voxel, %s" % fc.FC_BP_NAMES[used], err / mu_w, MU_TOL,
                   "of mu_water")
