@@ -261,8 +261,12 @@ def _kernel_models(wl):
         "blur_cols": {"bytes": 8 * bpx_c + 4 * px, "flops": 2 * taps * bpx_c, "bound": "hbm"},
         # reachable rows: counts read, filtered written; odd taps + centre
         "fdk_filter": {"bytes": 8 * fpx, "flops": 2 * (odd + 1) * fpx, "bound": "alu"},
-        # filtered reachable rows read once, FP64 volume written once
-        "backproject": {"bytes": 4 * fpx + 8 * g.n_voxels, "flops": None, "bound": "hbm"},
+        # filtered reachable rows read once, FP64 volume written once; per
+        # voxel update 14 flops: v coordinate (fma), its fraction, three
+        # linear interpolations (sub + fma each), the weighted sum (fma); the
+        # per-(column, projection) set-up shared by the slices is not counted
+        "backproject": {"bytes": 4 * fpx + 8 * g.n_voxels, "flops": 14 * g.n_voxels * g.n_angles,
+                        "bound": "alu"},
         "hu": {"bytes": 8 * 2 * g.n_voxels + 4 * g.n_voxels, "flops": None, "bound": "hbm"},
         # rates read, counts written
         "noise": {"bytes": 8 * px, "flops": None, "bound": "hbm"},
@@ -757,9 +761,13 @@ def _path_rates(fc, h, wl, kernels, n_sm, mhz, angle_stride=1):
     if "backproject" in kernels:
         t = kernels["backproject"]["ms_per_step"] / 1e3
         upd = g.n_voxels * g.n_angles
+        m = _kernel_models(wl)["backproject"]
+        hbm = float(_peaks()[0]["hbm_gbs"])
         out["backprojector"] = {
             "variant": fc.FC_BP_NAMES.get(fc.fc_backprojector_in_use(h)),
             "voxel_updates_per_s": upd / t,
+            # the algorithmic bytes against HBM (the filtered rows stay in L1 / L2)
+            "hbm": {"achieved_gbs": m["bytes"] / t / 1e9, "peak_gbs": hbm, "frac": m["bytes"] / t / 1e9 / hbm},
             "issue": _issue("backproject", wl, upd, t, n_sm, mhz)}
     return out
 
@@ -880,6 +888,9 @@ def main(argv=None):
     ap.add_argument("--angles", type=int, default=None,
                     help="profile a smaller case: the workload's first N projections (same "
                          "angular step); the bench line then names the reduced workload")
+    ap.add_argument("--coarse", type=int, default=None,
+                    help="profile a smaller case: N projections spread over the workload's "
+                         "whole arc (a full circle stays a full circle)")
     ap.add_argument("--cpu-angles", type=int, default=64,
                     help="projections in the oracle CPU-baseline sample")
     ap.add_argument("--ref-angles", type=int, default=8,
@@ -907,6 +918,15 @@ def main(argv=None):
         W.WORKLOADS[name] = dataclasses.replace(
             W.scaled(base, n_angles=args.angles, arc=base.geom.arc * args.angles / base.geom.n_angles),
             name=name)
+        args.workload = name
+    if args.coarse is not None:
+        if args.angles is not None:
+            ap.error("--coarse and --angles exclude each other")
+        base = W.WORKLOADS[args.workload]
+        if not 1 <= args.coarse <= base.geom.n_angles:
+            ap.error("--coarse must be in [1, %d]" % base.geom.n_angles)
+        name = "%s_%dc" % (args.workload, args.coarse)
+        W.WORKLOADS[name] = dataclasses.replace(W.scaled(base, n_angles=args.coarse), name=name)
         args.workload = name
     if args.impl == "reference":
         return run_reference(args)
