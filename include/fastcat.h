@@ -52,6 +52,9 @@ extern "C" {
 /* where a pointer lives */
 #define FC_HOST   0
 #define FC_DEVICE 1
+/* Host destination in page-locked memory, filled asynchronously (accepted
+ * by fc_reconstruct's outputs; see fc_wait_outputs). */
+#define FC_HOST_ASYNC 2
 
 /* what fc_project returns */
 #define FC_OUT_NONE      0  /* keep results on the device only */
@@ -114,7 +117,11 @@ int fc_set_geometry(fc_handle *h, const fc_geometry *g);
 /* Labelled phantom (Sec. II.D: integer array 0 .. n-1 plus a material map).
  * labels: uint8 [nz][ny][nx] in host (where = FC_HOST) or device memory;
  * copied into the handle.  Every label must be < n_mat; violations are
- * detected on the device and reported as FC_EINVAL.
+ * reported as FC_EINVAL (host labels: checked on the host before the copy,
+ * which stays queued on `stream` without waiting, so the host buffer must
+ * stay unchanged until the stream reaches it, and page-locked memory makes
+ * the copy asynchronous; device labels: checked on the device, the call
+ * waits for the check).
  * Errors: FC_ESTATE (no geometry), FC_EINVAL, FC_ECUDA. */
 int fc_set_phantom(fc_handle *h, const uint8_t *labels, int n_mat, int where,
                    void *stream);
@@ -224,10 +231,28 @@ int fc_set_energy_groups(fc_handle *h, const fc_energy_groups *g);
  * counts: [n_angles][n_v][n_u] float in host or device memory, or NULL to
  * use the handle's last FC_OUT_COUNTS result.  vol_mu (double [nz][ny][nx],
  * 1/cm) and vol_hu (float, HU normalised on the water region) may each be
- * NULL; `out_where` applies to both.
+ * NULL; `out_where` (FC_HOST, FC_DEVICE or FC_HOST_ASYNC, see
+ * fc_wait_outputs) applies to both.
  * Errors: FC_ESTATE, FC_EINVAL, FC_ECUDA. */
 int fc_reconstruct(fc_handle *h, const float *counts, int counts_where,
                    double *vol_mu, float *vol_hu, int out_where, void *stream);
+
+/* Wait for the results of earlier fc_reconstruct calls made with out_where =
+ * FC_HOST_ASYNC (library plumbing: the paper has no counterpart).  With
+ * FC_HOST_ASYNC, vol_mu / vol_hu must be page-locked host memory (e.g.
+ * cudaHostAlloc; pageable memory is refused with FC_EINVAL): the call queues
+ * the device-to-host copies on a stream of the handle's own, ordered after
+ * the results are complete on `stream`, and returns without waiting, so the
+ * copies overlap the caller's next calls on `stream` (the next fc_project,
+ * the next filter).  The host buffers hold the results once
+ * fc_wait_outputs returns; until then they must not be read or freed.  A
+ * later call that rewrites the volume (fc_reconstruct before its
+ * backprojection, fc_cnr_grad) makes its stream wait on the device for the
+ * queued copies; fc_set_geometry and fc_destroy wait on the host.  Returns
+ * FC_OK at once when nothing is queued.
+ * Errors: FC_EINVAL (null handle), FC_ECUDA, FC_ETIMEOUT (as fc_project's
+ * host outputs report it). */
+int fc_wait_outputs(fc_handle *h);
 
 /* FDK backprojector variant (instrumentation and testing: the paper has no
  * counterpart; every variant computes the same backprojection of

@@ -177,6 +177,11 @@ struct fc_handle {
     double *d_dose = nullptr;   // dose estimate: partial sums, result, label counts
     uint16_t *d_hankel = nullptr;   // tensor-core blur band matrices
     unsigned int *d_blur_err = nullptr;
+    // FC_HOST_ASYNC outputs of fc_reconstruct: copied on the handle's own
+    // stream after ev_done; ev_copied marks the last queued copy's end
+    cudaStream_t copy_s = nullptr;
+    cudaEvent_t ev_done = nullptr, ev_copied = nullptr;
+    bool copy_pending = false;
 
     void free_all()
     {
@@ -230,6 +235,27 @@ struct fc_handle {
         dfree(d_loss);
         dfree(d_sL);
         dfree(d_slnT);
+        if (copy_s) cudaStreamDestroy(copy_s);
+        if (ev_done) cudaEventDestroy(ev_done);
+        if (ev_copied) cudaEventDestroy(ev_copied);
+        copy_s = nullptr;
+        ev_done = ev_copied = nullptr;
+        copy_pending = false;
+    }
+
+    // Before the device volume or HU image is written again: make `s` wait
+    // for the queued asynchronous copy-out of the previous results.
+    cudaError_t order_after_copy(cudaStream_t s) const
+    {
+        return copy_pending ? cudaStreamWaitEvent(s, ev_copied, 0) : cudaSuccess;
+    }
+
+    // Host wait for the queued copy-out (before buffers are freed).
+    cudaError_t drain_copy()
+    {
+        if (!copy_pending) return cudaSuccess;
+        copy_pending = false;
+        return cudaEventSynchronize(ev_copied);
     }
 };
 
@@ -455,6 +481,7 @@ int fc_destroy(fc_handle *h)
 {
     if (!h) return FC_OK;
     DeviceGuard dgd(h->device);
+    (void)h->drain_copy();
     h->free_all();
     delete h;
     return FC_OK;
@@ -482,6 +509,7 @@ int fc_set_geometry(fc_handle *h, const fc_geometry *g)
     if (vox >= ((size_t)1 << 31))
         return fail(FC_EINVAL, "fc_set_geometry: %zu voxels exceed the 2^31 index range", vox);
     DeviceGuard dgd(h->device);
+    FC_CK(h->drain_copy());   // buffers below may be freed
     const bool same_vol = h->has_geom && h->g.nx == g->nx && h->g.ny == g->ny && h->g.nz == g->nz;
     if (proj != h->proj_elems || !h->has_geom) {
         dfree(h->d_T);
@@ -561,18 +589,31 @@ int fc_set_phantom(fc_handle *h, const uint8_t *labels, int n_mat, int where, vo
                          (size_t)((h->g.nx + fc::kBrick - 1) / fc::kBrick) *
                              ((h->g.ny + fc::kBrick - 1) / fc::kBrick) *
                              ((h->g.nz + fc::kBrickZ - 1) / fc::kBrickZ)));
+    if (where == FC_HOST) {
+        // host labels are checked here, before the copy, so the call need
+        // not wait for the device (the copy and kernels stay queued on s)
+        uint8_t mx = 0;
+        for (size_t i = 0; i < h->vol_elems; ++i) mx = labels[i] > mx ? labels[i] : mx;
+        if (mx >= n_mat) {
+            h->has_phantom = false;
+            return fail(FC_EINVAL, "fc_set_phantom: a label is >= n_mat (%d)", n_mat);
+        }
+    }
     FC_CK(cudaMemcpyAsync(h->d_labels, labels, h->vol_elems,
                           where == FC_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, s));
     FC_CK(fc::launch_labels_zfast(h->d_labels, h->d_labels_zf, h->g.nx, h->g.ny, h->g.nz, s));
     FC_CK(cudaMemsetAsync(h->d_flag, 0, sizeof(unsigned int), s));
     FC_CK(fc::launch_brick_map(h->d_labels, h->d_bricks, h->g.nx, h->g.ny, h->g.nz, n_mat,
                                h->d_flag, s));
-    unsigned int bad = 0;
-    FC_CK(cudaMemcpyAsync(&bad, h->d_flag, sizeof(bad), cudaMemcpyDeviceToHost, s));
-    FC_CK(cudaStreamSynchronize(s));
-    if (bad) {
-        h->has_phantom = false;
-        return fail(FC_EINVAL, "fc_set_phantom: a label is >= n_mat (%d)", n_mat);
+    if (where == FC_DEVICE) {
+        // device labels: the brick-map kernel flags a label >= n_mat
+        unsigned int bad = 0;
+        FC_CK(cudaMemcpyAsync(&bad, h->d_flag, sizeof(bad), cudaMemcpyDeviceToHost, s));
+        FC_CK(cudaStreamSynchronize(s));
+        if (bad) {
+            h->has_phantom = false;
+            return fail(FC_EINVAL, "fc_set_phantom: a label is >= n_mat (%d)", n_mat);
+        }
     }
     h->phantom_mat = n_mat;
     h->has_phantom = true;
@@ -1188,9 +1229,20 @@ int fc_reconstruct(fc_handle *h, const float *counts, int counts_where, double *
     if (!counts && !h->has_counts) return fail(FC_ESTATE, "fc_reconstruct: no counts simulated yet");
     if (counts && counts_where != FC_HOST && counts_where != FC_DEVICE)
         return fail(FC_EINVAL, "fc_reconstruct: bad counts_where");
-    if ((vol_mu || vol_hu) && out_where != FC_HOST && out_where != FC_DEVICE)
+    if ((vol_mu || vol_hu) && out_where != FC_HOST && out_where != FC_DEVICE && out_where != FC_HOST_ASYNC)
         return fail(FC_EINVAL, "fc_reconstruct: bad out_where");
     DeviceGuard dgd(h->device);
+    if (out_where == FC_HOST_ASYNC) {
+        // the asynchronous copy needs page-locked host memory
+        for (const void *ptr : {(const void *)vol_mu, (const void *)vol_hu}) {
+            if (!ptr) continue;
+            cudaPointerAttributes a;
+            if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess || a.type != cudaMemoryTypeHost) {
+                cudaGetLastError();
+                return fail(FC_EINVAL, "fc_reconstruct: FC_HOST_ASYNC needs page-locked host memory");
+            }
+        }
+    }
     cudaStream_t s = (cudaStream_t)stream;
     int rc = ensure_recon_buffers(h, s);
     if (rc) return rc;
@@ -1216,6 +1268,8 @@ int fc_reconstruct(fc_handle *h, const float *counts, int counts_where, double *
         if (bpv < 0)
             return fail(FC_EINVAL, "fc_reconstruct: backprojector variant %d does not apply to this geometry",
                         h->bp_request);
+        // the previous results may still be on their way to the host
+        FC_CK(h->order_after_copy(s));
         Trace t(h, FC_K_BACKPROJECT, 1, s);
         FC_CK(fc::launch_backproject(p, h->d_filt, h->d_vol, bpv, s));
         t.end();
@@ -1227,6 +1281,22 @@ int fc_reconstruct(fc_handle *h, const float *counts, int counts_where, double *
         FC_CK(fc::launch_hu(h->dg, h->d_vol, h->d_hu, h->d_part, (float)h->water_r, zc, s));
         t.end();
     }
+    if ((vol_mu || vol_hu) && out_where == FC_HOST_ASYNC) {
+        if (!h->copy_s) FC_CK(cudaStreamCreateWithFlags(&h->copy_s, cudaStreamNonBlocking));
+        if (!h->ev_done) FC_CK(cudaEventCreateWithFlags(&h->ev_done, cudaEventDisableTiming));
+        if (!h->ev_copied) FC_CK(cudaEventCreateWithFlags(&h->ev_copied, cudaEventDisableTiming));
+        FC_CK(cudaEventRecord(h->ev_done, s));
+        FC_CK(cudaStreamWaitEvent(h->copy_s, h->ev_done, 0));
+        if (vol_mu)
+            FC_CK(cudaMemcpyAsync(vol_mu, h->d_vol, h->vol_elems * sizeof(double), cudaMemcpyDeviceToHost,
+                                  h->copy_s));
+        if (vol_hu)
+            FC_CK(cudaMemcpyAsync(vol_hu, h->d_hu, h->vol_elems * sizeof(float), cudaMemcpyDeviceToHost,
+                                  h->copy_s));
+        FC_CK(cudaEventRecord(h->ev_copied, h->copy_s));
+        h->copy_pending = true;
+        return FC_OK;
+    }
     if (vol_mu) {
         rc = copy_out(vol_mu, out_where, h->d_vol, h->vol_elems * sizeof(double), s);
         if (rc) return rc;
@@ -1237,6 +1307,15 @@ int fc_reconstruct(fc_handle *h, const float *counts, int counts_where, double *
     }
     if ((vol_mu || vol_hu) && out_where == FC_HOST) return check_blur_err(h, s, "fc_reconstruct");
     return FC_OK;
+}
+
+int fc_wait_outputs(fc_handle *h)
+{
+    if (!h) return fail(FC_EINVAL, "fc_wait_outputs: null handle");
+    if (!h->copy_pending) return FC_OK;
+    DeviceGuard dgd(h->device);
+    FC_CK(h->drain_copy());
+    return check_blur_err(h, h->copy_s, "fc_wait_outputs");
 }
 
 int fc_profile_enable(fc_handle *h, int enable)
@@ -1736,6 +1815,7 @@ int fc_cnr_grad(fc_handle *h, const double *logits, const double *D, const doubl
         if (!(rho_nominal[m] > 0.0)) return fail(FC_EINVAL, "fc_cnr_grad: nominal densities must be > 0");
     DeviceGuard dgd(h->device);
     cudaStream_t s = (cudaStream_t)stream;
+    FC_CK(h->order_after_copy(s));   // the volume and HU buffers are rewritten
     int rc = ensure_proj_buffers(h);
     if (rc) return rc;
     rc = ensure_recon_buffers(h, s);

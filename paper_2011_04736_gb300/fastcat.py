@@ -18,7 +18,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "lib", "libfastcat.so")
 
 FC_OK, FC_EINVAL, FC_ENOMEM, FC_ECUDA, FC_ESTATE, FC_ETIMEOUT = 0, -1, -2, -3, -4, -5
-FC_HOST, FC_DEVICE = 0, 1
+FC_HOST, FC_DEVICE, FC_HOST_ASYNC = 0, 1, 2
 FC_OUT_NONE, FC_OUT_PRIMARY, FC_OUT_INTENSITY, FC_OUT_COUNTS = 0, 1, 2, 3
 FC_NOISE_AFTER_BLUR, FC_NOISE_BEFORE_PSF = 0, 1
 FC_BP_AUTO, FC_BP_CHUNKED, FC_BP_CHUNKED_DENSE, FC_BP_SLAB, FC_BP_SLAB_SYM = 0, 1, 2, 3, 4
@@ -37,7 +37,7 @@ ENTRY_POINTS = ("fc_create", "fc_destroy", "fc_last_error", "fc_set_geometry", "
                 "fc_dose_estimate", "fc_fluence_for_dose", "fc_set_noise_order",
                 "fc_set_energy_groups", "fc_deconvolve_rl", "fc_detector_mtf",
                 "fc_set_backprojector", "fc_backprojector_in_use", "fc_inject_fault",
-                "fc_surrogate_guard", "fc_surrogate_sigma")
+                "fc_surrogate_guard", "fc_surrogate_sigma", "fc_wait_outputs")
 FC_STATIC_SCRATCH_FLOATS = 8 << 20
 FC_SURROGATE_PARAMS = 34305
 FC_SURROGATE_STATE = 34305 + 52 + 2 * 34305 + 1
@@ -103,6 +103,7 @@ def load():
         "fc_set_spectrum_detector": (I, [P, ctypes.POINTER(fc_spectrum_detector)]),
         "fc_project": (I, [P, I, I, I, P, I, P]),
         "fc_reconstruct": (I, [P, P, I, P, P, I, P]),
+        "fc_wait_outputs": (I, [P]),
         "fc_set_water_roi": (I, [P, ctypes.c_double, ctypes.c_double]),
         "fc_poisson": (I, [P, P, I, I, I, I, ctypes.c_uint64, P]),
         "fc_project_lengths": (I, [P, I, I, P, P]),
@@ -214,14 +215,24 @@ def fc_project(h, angle_begin, angle_count, out_kind, out=None, stream=None):
     return _check(load().fc_project(h, angle_begin, angle_count, out_kind, p, where, _stream(stream)))
 
 
-def fc_reconstruct(h, counts=None, vol_mu=None, vol_hu=None, stream=None):
+def fc_reconstruct(h, counts=None, vol_mu=None, vol_hu=None, stream=None, async_host=False):
+    """async_host: host outputs (page-locked) are filled asynchronously
+    (FC_HOST_ASYNC); read them after fc_wait_outputs(h)."""
     cp, cw = _ptr(counts)
     mp, mw = _ptr(vol_mu)
     hp, hw = _ptr(vol_hu)
     if mp is not None and hp is not None and mw != hw:
         raise ValueError("vol_mu and vol_hu must both be host or both be device buffers")
     ow = mw if mp is not None else hw
+    if async_host:
+        if ow != FC_HOST:
+            raise ValueError("async_host applies to host outputs")
+        ow = FC_HOST_ASYNC
     return _check(load().fc_reconstruct(h, cp, cw, mp, hp, ow, _stream(stream)))
+
+
+def fc_wait_outputs(h):
+    return _check(load().fc_wait_outputs(h))
 
 
 def fc_set_water_roi(h, radius_cm, z_margin):
