@@ -239,7 +239,7 @@ def _kernel_models(wl):
     lo, hi = _reach_rows(g)
     rows = hi - lo + 1
     fpx = g.n_angles * rows * g.n_u
-    odd = g.n_u if (g.n_u - 1) % 2 == 1 else g.n_u - 1
+    fftl = 1 << max(1, int(math.ceil(math.log2(2 * g.n_u - 1)))) if g.n_u > 1 else 2
     row_rows, col_rows = _blur_rows(wl)
     bpx_r = g.n_angles * row_rows * g.n_u      # pixels the row pass computes
     bpx_c = g.n_angles * col_rows * g.n_u      # pixels the column pass computes
@@ -259,8 +259,11 @@ def _kernel_models(wl):
         "blur_rows": {"bytes": 12 * bpx_r, "flops": 2 * taps * bpx_r, "bound": "hbm"},
         # intermediates read on the computed tiles, every output pixel written
         "blur_cols": {"bytes": 8 * bpx_c + 4 * px, "flops": 2 * taps * bpx_c, "bound": "hbm"},
-        # reachable rows: counts read, filtered written; odd taps + centre
-        "fdk_filter": {"bytes": 8 * fpx, "flops": 2 * (odd + 1) * fpx, "bound": "alu"},
+        # reachable rows: counts read, filtered written; two rows per complex
+        # FFT of length L (>= 2 n_u - 1): a forward and an inverse transform
+        # of 5 L log2 L flops each and the spectrum product (2 L), per row pair
+        "fdk_filter": {"bytes": 8 * fpx, "flops": (fpx // g.n_u) * (5 * fftl * int(math.log2(fftl)) + fftl),
+                       "bound": "alu"},
         # filtered reachable rows read once, FP64 volume written once; per
         # voxel update 14 flops: v coordinate (fma), its fraction, three
         # linear interpolations (sub + fma each), the weighted sum (fma); the

@@ -182,6 +182,10 @@ struct fc_handle {
     cudaStream_t copy_s = nullptr;
     cudaEvent_t ev_done = nullptr, ev_copied = nullptr;
     bool copy_pending = false;
+    // FFT ramp filter tables (twiddles, Ram-Lak response) for fft_n samples
+    float2 *d_fft_tw = nullptr;
+    float *d_fft_k = nullptr;
+    int fft_n = 0;
 
     void free_all()
     {
@@ -235,6 +239,9 @@ struct fc_handle {
         dfree(d_loss);
         dfree(d_sL);
         dfree(d_slnT);
+        dfree(d_fft_tw);
+        dfree(d_fft_k);
+        fft_n = 0;
         if (copy_s) cudaStreamDestroy(copy_s);
         if (ev_done) cudaEventDestroy(ev_done);
         if (ev_copied) cudaEventDestroy(ev_copied);
@@ -519,6 +526,9 @@ int fc_set_geometry(fc_handle *h, const fc_geometry *g)
         h->has_counts = false;
     }
     dfree(h->d_filt);  // its size follows the reachable detector rows
+    dfree(h->d_fft_tw);   // the filter tables follow n_u and tau
+    dfree(h->d_fft_k);
+    h->fft_n = 0;
     dfree(h->d_I);
     dfree(h->d_gI);
     dfree(h->d_gT);
@@ -1110,6 +1120,29 @@ static int fdk_sym_turn(const fc_geometry &g, int parts)
     return g.n_angles / parts;
 }
 
+// The FFT ramp filter's tables for the handle's geometry (built on first
+// use after fc_set_geometry), pointed to by p.
+static int ensure_fft_tables(fc_handle *h, fc::FdkParams *p)
+{
+    p->fft_log2 = fc::fdk_fft_log2(h->g.n_u);
+    if (!h->d_fft_k || h->fft_n != h->g.n_u) {
+        std::vector<float2> tw;
+        std::vector<float> kbr;
+        fc::fdk_fft_tables(h->g.n_u, h->g.du_cm * h->g.sad_cm / h->g.sdd_cm, &tw, &kbr);
+        dfree(h->d_fft_tw);
+        dfree(h->d_fft_k);
+        h->fft_n = 0;
+        FC_CK(dev_malloc((void **)&h->d_fft_tw, tw.size() * sizeof(float2)));
+        FC_CK(dev_malloc((void **)&h->d_fft_k, kbr.size() * sizeof(float)));
+        FC_CK(cudaMemcpy(h->d_fft_tw, tw.data(), tw.size() * sizeof(float2), cudaMemcpyHostToDevice));
+        FC_CK(cudaMemcpy(h->d_fft_k, kbr.data(), kbr.size() * sizeof(float), cudaMemcpyHostToDevice));
+        h->fft_n = h->g.n_u;
+    }
+    p->fft_tw = h->d_fft_tw;
+    p->fft_k = h->d_fft_k;
+    return FC_OK;
+}
+
 // FdkParams of the handle's geometry (no buffers touched).
 static void fill_fdk_params(const fc_handle *h, fc::FdkParams *p)
 {
@@ -1258,6 +1291,8 @@ int fc_reconstruct(fc_handle *h, const float *counts, int counts_where, double *
     // flood: T = 1 through the detector model (single kernel: N0 (1 + SPR);
     // energy groups: N0, the scatter profile needing a phantom)
     fill_fdk_params(h, &p);
+    rc = ensure_fft_tables(h, &p);
+    if (rc) return rc;
     {
         Trace t(h, FC_K_FDK_FILTER, 1, s);
         FC_CK(fc::launch_fdk_filter(p, src, h->d_filt, s));
@@ -1876,6 +1911,10 @@ int fc_cnr_grad(fc_handle *h, const double *logits, const double *D, const doubl
     pf.pw = fdk_row_pitch(h->g.n_u);
     pf.ph = pf.v_hi - pf.v_lo + 1 + 3;
     pf.sym_quarter = g_sym_quarter_ok(h->g) ? fdk_sym_turn(h->g, 4) : 0;
+    pf.fft_tw = nullptr;
+    pf.fft_k = nullptr;
+    rc = ensure_fft_tables(h, &pf);
+    if (rc) return rc;
     fc::CnrParams cp;
     memset(&cp, 0, sizeof(cp));
     cp.g = h->dg;

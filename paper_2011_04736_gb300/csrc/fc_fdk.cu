@@ -6,13 +6,12 @@
 //   f  = tau * (h * q),  Ram-Lak h[0] = 1/(4 tau^2), h[odd n] = -1/(pi n tau)^2
 //   mu = arc / (2 N) * sum_k (SAD / U)^2 * bilinear(f_k; u(x), v(x))
 //
-// Filter: one CTA per detector row; the weighted row sits zero-padded in
-// shared memory as sample pairs and each thread produces 16 adjacent outputs
-// from a sliding register window of 8 pairs that advances one pair per odd
-// tap (8 packed FMAs per 8-byte shared load).  Only rows the backprojector
-// can sample are filtered and
-// stored (a conservative bound on the rows the voxel slab projects onto),
-// in a zero-padded layout so the bilinear taps need no bounds tests.
+// Filter: the weighted rows the backprojector can sample (a conservative
+// bound on the rows the voxel slab projects onto), two rows per CTA as the
+// real and imaginary parts of one FFT of a power-of-two length in shared
+// memory, times the Ram-Lak spectrum, inverse FFT; stored in a zero-padded
+// layout of (value, next value - value) pairs so the bilinear taps need no
+// bounds tests.  The adjoint's transposed filter sums the taps directly.
 // Backprojection: one thread per (x, y) column and chunk of z; per angle
 // the column's detector abscissa and weight are computed once and the z
 // loop walks the detector column linearly.  Partial sums over 256 angles are
@@ -131,48 +130,158 @@ __device__ __forceinline__ void ramp_row_pairs(const float *sp, int n, float inv
     }
 }
 
-// rows [v_lo, v_hi] of every projection; blockIdx.x = projection * nrows + r.
-// The filtered row goes to shared memory, then out as (value, next value -
-// value) pairs over padded columns 0..n (the zero column before the row and
-// the one after it included), so a bilinear tap pair is one 8-byte load and
-// the u interpolation one FMA.
-__global__ void __launch_bounds__(kFiltThreads)
-k_fdk_filter(const __grid_constant__ FdkParams p, const float *__restrict__ counts,
-             float2 *__restrict__ filt)
+// DIF butterfly: (u, v) -> (u + v, (u - v) w)
+__device__ __forceinline__ void cbfly_dif(float2 &u, float2 &v, float2 w)
 {
-    extern __shared__ float sx[];
+    const float dx = u.x - v.x, dy = u.y - v.y;
+    u = make_float2(u.x + v.x, u.y + v.y);
+    v = make_float2(dx * w.x - dy * w.y, dx * w.y + dy * w.x);
+}
+
+// DIT butterfly with the conjugate twiddle: (u, v) -> (u + v conj(w), u - v conj(w))
+__device__ __forceinline__ void cbfly_dit_conj(float2 &u, float2 &v, float2 w)
+{
+    const float vx = v.x * w.x + v.y * w.y, vy = v.y * w.x - v.x * w.y;
+    v = make_float2(u.x - vx, u.y - vy);
+    u = make_float2(u.x + vx, u.y + vy);
+}
+
+__global__ void __launch_bounds__(256)
+k_fdk_filter_fft(const __grid_constant__ FdkParams p, const float *__restrict__ counts,
+                 float2 *__restrict__ filt)
+{
+    extern __shared__ float2 z[];
     const DevGeom &g = p.g;
-    const int n = g.n_u;
+    const int n = g.n_u, L = 1 << p.fft_log2, H = L >> 1;
     const int nrows = p.v_hi - p.v_lo + 1;
-    const int k = blockIdx.x / nrows;
-    const int r = (int)(blockIdx.x % nrows);
-    const int iv = p.v_lo + r;
-    const size_t row = ((size_t)k * g.n_v + iv) * n;
-    float2 *dst = filt + ((size_t)k * p.ph + (r + 1)) * p.pw;
-    // padded row: position off + j holds q[j], zeros elsewhere (pair-skewed)
-    const float vi = ((float)iv - g.cv) * g.dv * p.mag;
-    const float sad2v = g.sad * g.sad + vi * vi;
-    const int off = filt_off(((n - 1) & 1) ? n - 1 : n - 2);
-    const int span = filt_span(n);
-    for (int i = threadIdx.x; i < span; i += blockDim.x) {
-        float val = 0.0f;
-        const int j = i - off;
-        if (j >= 0 && j < n) {
-            const float ui = ((float)j - g.cu) * g.du * p.mag;
-            const float K = fmaxf(counts[row + j], 1.0f);
-            val = (p.log_flood - logf(K)) * (g.sad * rsqrtf(sad2v + ui * ui));
+    const long R = (long)g.n_angles * nrows;
+    const long ra = 2L * blockIdx.x;   // rows ra and ra + 1 of this CTA (the second may be past the end)
+    const float *src[2];
+    float d2[2];                        // SAD^2 + v^2 of each row
+#pragma unroll
+    for (int t = 0; t < 2; ++t) {
+        const long row = ra + t < R ? ra + t : ra;
+        const int k = (int)(row / nrows), iv = p.v_lo + (int)(row % nrows);
+        const float vi = ((float)iv - g.cv) * g.dv * p.mag;
+        src[t] = counts + ((size_t)k * g.n_v + iv) * n;
+        d2[t] = g.sad * g.sad + vi * vi;
+    }
+    const bool two = ra + 1 < R;
+    for (int j = threadIdx.x; j < L; j += blockDim.x) {
+        float a = 0.0f, b = 0.0f;
+        if (j < n) {
+            const float ui = ((float)j - g.cu) * g.du * p.mag, u2 = ui * ui;
+            a = (p.log_flood - logf(fmaxf(__ldg(src[0] + j), 1.0f))) * (g.sad * rsqrtf(d2[0] + u2));
+            if (two) b = (p.log_flood - logf(fmaxf(__ldg(src[1] + j), 1.0f))) * (g.sad * rsqrtf(d2[1] + u2));
         }
-        sx[pidx(i)] = val;
+        z[j] = make_float2(a, b);
     }
     __syncthreads();
-    float *fo = sx + pidx(span) + 2;                // filtered row, index i + 1 = padded column
-    ramp_row_pairs(sx, n, 1.0f / p.tau, [&](int i, float v) { fo[i + 1] = v; });
-    if (threadIdx.x == 0) {
-        fo[0] = 0.0f;
-        fo[n + 1] = 0.0f;
+    const float2 *tw = p.fft_tw;
+    // forward, decimation in frequency: stages of half-width h = H, H/2, ..., 1,
+    // two at a time (h and h/2 on the four elements a, a + h/2, a + h, a + 3h/2)
+    int h = H;
+    for (; h >= 2; h >>= 2) {
+        const int h2 = h >> 1, s1 = H / h;
+        for (int q = threadIdx.x; q < (L >> 2); q += blockDim.x) {
+            const int pos = q & (h2 - 1);
+            const int a = ((q - pos) << 2) + pos;
+            float2 x0 = z[a], x1 = z[a + h2], x2 = z[a + h], x3 = z[a + h + h2];
+            cbfly_dif(x0, x2, __ldg(tw + pos * s1));
+            cbfly_dif(x1, x3, __ldg(tw + (pos + h2) * s1));
+            const float2 w2 = __ldg(tw + 2 * pos * s1);
+            cbfly_dif(x0, x1, w2);
+            cbfly_dif(x2, x3, w2);
+            z[a] = x0;
+            z[a + h2] = x1;
+            z[a + h] = x2;
+            z[a + h + h2] = x3;
+        }
+        __syncthreads();
+    }
+    if (h == 1) {   // odd log2 L: the last radix-2 stage (twiddle 1)
+        for (int q = threadIdx.x; q < H; q += blockDim.x) {
+            float2 x0 = z[2 * q], x1 = z[2 * q + 1];
+            z[2 * q] = make_float2(x0.x + x1.x, x0.y + x1.y);
+            z[2 * q + 1] = make_float2(x0.x - x1.x, x0.y - x1.y);
+        }
+        __syncthreads();
+    }
+    for (int r = threadIdx.x; r < L; r += blockDim.x) {
+        const float k = __ldg(p.fft_k + r);
+        const float2 v = z[r];
+        z[r] = make_float2(v.x * k, v.y * k);
     }
     __syncthreads();
-    for (int c = threadIdx.x; c <= n; c += blockDim.x) dst[c] = make_float2(fo[c], fo[c + 1] - fo[c]);
+    // inverse, decimation in time with conjugate twiddles: half-widths
+    // h = 1, 2, ..., H, two at a time (h and 2h on a, a + h, a + 2h, a + 3h)
+    h = 1;
+    if (p.fft_log2 & 1) {
+        for (int q = threadIdx.x; q < H; q += blockDim.x) {
+            float2 x0 = z[2 * q], x1 = z[2 * q + 1];
+            z[2 * q] = make_float2(x0.x + x1.x, x0.y + x1.y);
+            z[2 * q + 1] = make_float2(x0.x - x1.x, x0.y - x1.y);
+        }
+        __syncthreads();
+        h = 2;
+    }
+    for (; h < L; h <<= 2) {
+        const int s1 = H / h, s2 = s1 >> 1;
+        for (int q = threadIdx.x; q < (L >> 2); q += blockDim.x) {
+            const int pos = q & (h - 1);
+            const int a = ((q - pos) << 2) + pos;
+            float2 x0 = z[a], x1 = z[a + h], x2 = z[a + 2 * h], x3 = z[a + 3 * h];
+            const float2 w1 = __ldg(tw + pos * s1);
+            cbfly_dit_conj(x0, x1, w1);
+            cbfly_dit_conj(x2, x3, w1);
+            cbfly_dit_conj(x0, x2, __ldg(tw + pos * s2));
+            cbfly_dit_conj(x1, x3, __ldg(tw + (pos + h) * s2));
+            z[a] = x0;
+            z[a + h] = x1;
+            z[a + 2 * h] = x2;
+            z[a + 3 * h] = x3;
+        }
+        __syncthreads();
+    }
+    // (value, next value - value) pairs over padded columns 0..n: column c
+    // holds output c - 1, columns 0 and n + 1 are zero
+    for (int half = 0; half < 2; ++half) {
+        const long row = ra + half;
+        if (row >= R) break;
+        const int k = (int)(row / nrows), r = (int)(row % nrows);
+        float2 *dst = filt + ((size_t)k * p.ph + (r + 1)) * p.pw;
+        for (int c = threadIdx.x; c <= n; c += blockDim.x) {
+            const float y0 = c >= 1 ? (half ? z[c - 1].y : z[c - 1].x) : 0.0f;
+            const float y1 = c < n ? (half ? z[c].y : z[c].x) : 0.0f;
+            dst[c] = make_float2(y0, y1 - y0);
+        }
+    }
+}
+
+int fdk_fft_log2(int n_u)
+{
+    int l = 1;
+    while ((1 << l) < 2 * n_u - 1) ++l;
+    return l;
+}
+
+void fdk_fft_tables(int n_u, double tau, std::vector<float2> *tw, std::vector<float> *kbr)
+{
+    const int lg = fdk_fft_log2(n_u), L = 1 << lg;
+    std::vector<double> cs(L);
+    for (int t = 0; t < L; ++t) cs[t] = cos(2.0 * M_PI * t / L);
+    tw->resize(L / 2);
+    for (int t = 0; t < L / 2; ++t) (*tw)[t] = make_float2((float)cs[t], (float)-sin(2.0 * M_PI * t / L));
+    const int jm = ((n_u - 1) & 1) ? n_u - 1 : n_u - 2;
+    kbr->resize(L);
+    for (int r = 0; r < L; ++r) {
+        unsigned m = 0;   // frequency at bit-reversed position r
+        for (int b = 0; b < lg; ++b)
+            if (r >> b & 1) m |= 1u << (lg - 1 - b);
+        double K = 0.25;
+        for (int j = 1; j <= jm; j += 2) K -= 2.0 * cs[(size_t)j * m % L] / (M_PI * M_PI * (double)j * j);
+        (*kbr)[r] = (float)(K / ((double)L * tau));
+    }
 }
 
 cudaError_t launch_fdk_filter(const FdkParams &p, const float *counts, float2 *filt, cudaStream_t s)
@@ -180,21 +289,17 @@ cudaError_t launch_fdk_filter(const FdkParams &p, const float *counts, float2 *f
     const int nrows = p.v_hi - p.v_lo + 1;
     if (nrows <= 0 || p.g.n_angles <= 0) return cudaSuccess;
     if (p.g.n_u > kMaxFiltTaps) return cudaErrorInvalidValue;
-    cudaError_t e = upload_ramp_taps();
-    if (e != cudaSuccess) return e;
-    const int span = filt_span(p.g.n_u);
-    const size_t smem = (size_t)(2 * ((span >> 1) + (span >> 4)) + 4 + p.g.n_u + 2) * sizeof(float);
+    if (!p.fft_k || !p.fft_tw) return cudaErrorInvalidValue;
+    const int L = 1 << p.fft_log2;
+    const size_t smem = (size_t)L * sizeof(float2);
     if (smem > 48 * 1024) {
-        e = cudaFuncSetAttribute(k_fdk_filter, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)smem);
+        const cudaError_t e =
+            cudaFuncSetAttribute(k_fdk_filter_fft, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
-    const size_t blocks = (size_t)p.g.n_angles * nrows;
-    // one thread per 16 outputs of the row (whole warps, at most kFiltThreads):
-    // short rows leave no idle warps in the CTA
-    int threads = ((p.g.n_u + kFiltOut - 1) / kFiltOut + 31) / 32 * 32;
-    threads = threads > kFiltThreads ? kFiltThreads : threads;
-    k_fdk_filter<<<(unsigned)blocks, threads, smem, s>>>(p, counts, filt);
+    const long rows = (long)p.g.n_angles * nrows;
+    const int threads = L / 2 < 256 ? L / 2 : 256;
+    k_fdk_filter_fft<<<(unsigned)((rows + 1) / 2), threads, smem, s>>>(p, counts, filt);
     return cudaGetLastError();
 }
 

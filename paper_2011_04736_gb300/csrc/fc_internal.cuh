@@ -1,5 +1,6 @@
 // Internal declarations shared by the CUDA translation units of libfastcat.
 #pragma once
+#include <vector>
 
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -169,6 +170,9 @@ struct FdkParams {
     double scale;           // arc / (2 n_angles)
     int v_lo, v_hi;         // reachable detector rows
     int pw, ph;             // padded row length (n_u + 3 rounded up to 4), padded rows (v_hi - v_lo + 1) + 3
+    const float2 *fft_tw;   // FFT filter: twiddles exp(-2 pi i k / L), k < L / 2
+    const float *fft_k;     // FFT filter: Ram-Lak response / (L tau) at bit-reversed frequency index
+    int fft_log2;           // log2 L, L the transform length (>= 2 n_u - 1)
     int sym_quarter;        // n_angles / 4 for a full-circle scan of n_angles divisible by 4 over a
                             // square grid with an even side and dx = dy (quarter-turn symmetry), else 0
 };
@@ -307,6 +311,13 @@ cudaError_t launch_blur_transpose(const BlurParams &p, const float *gin, float *
                                   float *gout, int n_img, cudaStream_t s);
 cudaError_t launch_poisson(const float *lam, float *out, int n_img, int n_v, int n_u,
                            int angle0, uint64_t seed, cudaStream_t s);
+// Tables of the FFT ramp filter for rows of n_u samples: log2 of the
+// transform length L (the smallest power of two >= 2 n_u - 1), the L / 2
+// twiddles and the L values of the Ram-Lak response / (L tau) in the
+// bit-reversed order the forward transform leaves the spectrum in.
+int fdk_fft_log2(int n_u);
+void fdk_fft_tables(int n_u, double tau, std::vector<float2> *tw, std::vector<float> *kbr);
+
 cudaError_t launch_fdk_filter(const FdkParams &p, const float *counts, float2 *filt,
                               cudaStream_t s);
 cudaError_t launch_backproject(const FdkParams &p, const float2 *filt, double *vol, int variant,
