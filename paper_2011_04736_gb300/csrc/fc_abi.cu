@@ -740,16 +740,28 @@ static int blur_params(const fc_handle *h, double psf, double sc, double n0, dou
     return FC_OK;
 }
 
+// Rows of a blurred image left unwritten because they hold one constant
+// (c_hi < 0: every row written).
+struct ConstRows {
+    int c_lo = 0, c_hi = -1;
+    float cst = 0.0f;
+};
+
+// cr != nullptr: the output feeds a consumer that takes the constant rows
+// from *cr (the noise draw), so the band kernel need not store them.
 static int run_blur(fc_handle *h, const float *in, float *out, size_t off, int n, double psf,
-                    double sc, double n0, double spr, cudaStream_t s, int one_lo = 0, int one_hi = -1)
+                    double sc, double n0, double spr, cudaStream_t s, int one_lo = 0, int one_hi = -1,
+                    ConstRows *cr = nullptr)
 {
     fc::BlurParams b;
     int rc = blur_params(h, psf, sc, n0, spr, &b);
     if (rc) return rc;
+    if (cr) cr->c_hi = -1;
     if (one_hi >= 0 && in != out && fc::blur_band_supported(b, one_lo, one_hi)) {
         // the input differs from 1 on a narrow band of rows only
+        if (cr) fc::blur_band_rows(b, one_lo, one_hi, &cr->c_lo, &cr->c_hi, &cr->cst);
         Trace t(h, FC_K_BLUR_BAND, 1, s);
-        FC_CK(fc::launch_blur_band(b, in, out, n, one_lo, one_hi, s));
+        FC_CK(fc::launch_blur_band(b, in, out, n, one_lo, one_hi, s, cr == nullptr));
         t.end();
         return FC_OK;
     }
@@ -1069,13 +1081,16 @@ int fc_project(fc_handle *h, int angle_begin, int angle_count, int out_kind, flo
         rc = run_blur(h, h->d_counts + off, h->d_counts + off, off, angle_count, h->psf, 0.0, 1.0, 0.0, s);
         if (rc) return rc;
     } else {
+        // with noise the intensity is an intermediate: the band blur leaves
+        // its constant rows to the sampler, which takes that rate there
+        ConstRows cr;
         rc = run_blur(h, h->d_T + off, h->d_counts + off, off, angle_count, h->psf, h->sc, h->n0, h->spr, s,
-                      one_lo, one_hi);
+                      one_lo, one_hi, noise ? &cr : nullptr);
         if (rc) return rc;
         if (noise) {
             Trace t(h, FC_K_NOISE, 1, s);
             FC_CK(fc::launch_poisson(h->d_counts + off, h->d_counts + off, angle_count, h->g.n_v,
-                                     h->g.n_u, angle_begin, h->seed, s));
+                                     h->g.n_u, angle_begin, h->seed, s, cr.c_lo, cr.c_hi, cr.cst));
             t.end();
         }
     }

@@ -42,7 +42,7 @@ constexpr int kRun = 8;           // outputs per thread and task (register tile)
 template <int HB>
 __global__ void __launch_bounds__(kThreads)
 k_blur_band(const __grid_constant__ BlurParams bp, const float *__restrict__ T, float *__restrict__ out,
-            int b0, int hb, float cst)
+            int b0, int hb, float cst, int write_const)
 {
     extern __shared__ float sm[];
     const int R = bp.rp > bp.rs ? bp.rp : bp.rs;
@@ -159,8 +159,9 @@ k_blur_band(const __grid_constant__ BlurParams bp, const float *__restrict__ T, 
             }
         }
     }
-    // constant rows [0, c_lo) and [c_hi, n_v) of the tile
-    const int n_const = c_lo + (n_v - c_hi);
+    // constant rows [0, c_lo) and [c_hi, n_v) of the tile (left to the
+    // consumer when it takes them as cst itself)
+    const int n_const = write_const ? c_lo + (n_v - c_hi) : 0;
     const bool vec = (n_u & 3) == 0;
     for (int e = tid; e < n_const * (kTW / 4); e += kThreads) {
         const int rr = e / (kTW / 4), x = 4 * (e - rr * (kTW / 4));
@@ -195,28 +196,39 @@ bool blur_band_supported(const BlurParams &bp, int b_lo, int b_hi)
     return band_smem(bp, hb, hb <= 16 ? 16 : 32) <= kBandSmemLimit;
 }
 
+void blur_band_rows(const BlurParams &bp, int b_lo, int b_hi, int *c_lo, int *c_hi, float *cst)
+{
+    const int R = bp.rp > bp.rs ? bp.rp : bp.rs;
+    *c_lo = b_lo - R > 0 ? b_lo - R : 0;
+    *c_hi = b_hi + R < bp.n_v ? b_hi + R : bp.n_v;
+    double sp = 0.0, ss = 0.0;
+    for (int j = 0; j <= 2 * bp.rp; ++j) sp += bp.gp[j];
+    for (int j = 0; j <= 2 * bp.rs; ++j) ss += bp.gs[j];
+    *cst = (float)((double)bp.n0 * (sp * sp + (double)bp.spr * ss * ss));
+}
+
 cudaError_t launch_blur_band(const BlurParams &bp, const float *T, float *out, int n_img, int b_lo,
-                             int b_hi, cudaStream_t s)
+                             int b_hi, cudaStream_t s, bool write_const)
 {
     if (n_img <= 0) return cudaSuccess;
     if (!blur_band_supported(bp, b_lo, b_hi) || n_img > 65535) return cudaErrorInvalidValue;
     const int hb = b_hi - b_lo;
-    double sp = 0.0, ss = 0.0;
-    for (int j = 0; j <= 2 * bp.rp; ++j) sp += bp.gp[j];
-    for (int j = 0; j <= 2 * bp.rs; ++j) ss += bp.gs[j];
-    const float cst = (float)((double)bp.n0 * (sp * sp + (double)bp.spr * ss * ss));
+    int c_lo, c_hi;
+    float cst;
+    blur_band_rows(bp, b_lo, b_hi, &c_lo, &c_hi, &cst);
+    const int wc = write_const ? 1 : 0;
     const dim3 grid((bp.n_u + kTW - 1) / kTW, n_img);
     cudaError_t e;
     if (hb <= 16) {
         const size_t smem = band_smem(bp, hb, 16);
         e = cudaFuncSetAttribute(k_blur_band<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        k_blur_band<16><<<grid, kThreads, smem, s>>>(bp, T, out, b_lo, hb, cst);
+        k_blur_band<16><<<grid, kThreads, smem, s>>>(bp, T, out, b_lo, hb, cst, wc);
     } else {
         const size_t smem = band_smem(bp, hb, 32);
         e = cudaFuncSetAttribute(k_blur_band<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        k_blur_band<32><<<grid, kThreads, smem, s>>>(bp, T, out, b_lo, hb, cst);
+        k_blur_band<32><<<grid, kThreads, smem, s>>>(bp, T, out, b_lo, hb, cst, wc);
     }
     return cudaGetLastError();
 }

@@ -379,7 +379,7 @@ struct DrawQueue {
 
 __global__ void __launch_bounds__(32 * kWarps, 5)
 k_poisson(const float *lam, float *out, int n_v, int n_u, int angle0,
-          const __grid_constant__ noise::PhiloxKeys seed)
+          const __grid_constant__ noise::PhiloxKeys seed, int c_lo, int c_hi, float cst)
 {
     __shared__ DrawQueue q_all[kWarps];
     DrawQueue &q = q_all[threadIdx.y];
@@ -400,7 +400,9 @@ k_poisson(const float *lam, float *out, int n_v, int n_u, int angle0,
         bool pending = false;
         if (iu < n_u) {
             float r;
-            if (noise::poisson_begin(lam[row + iu], (uint32_t)iu, (uint32_t)iv, kabs, seed, st, r)) {
+            // rows outside [c_lo, c_hi) have the rate cst (not read)
+            const float lv = (iv >= c_lo && iv < c_hi) ? lam[row + iu] : cst;
+            if (noise::poisson_begin(lv, (uint32_t)iu, (uint32_t)iv, kabs, seed, st, r)) {
                 out[row + iu] = r;
             } else {
                 const int o = noise::ptrs_quick(st, r, kf, us, V);
@@ -461,13 +463,17 @@ k_poisson(const float *lam, float *out, int n_v, int n_u, int angle0,
 }
 
 cudaError_t launch_poisson(const float *lam, float *out, int n_img, int n_v, int n_u, int angle0,
-                           uint64_t seed, cudaStream_t s)
+                           uint64_t seed, cudaStream_t s, int c_lo, int c_hi, float cst)
 {
+    if (c_hi < 0) {
+        c_lo = 0;
+        c_hi = n_v;
+    }
     if ((size_t)n_img * n_v * n_u == 0) return cudaSuccess;
     if ((n_v + kWarps - 1) / kWarps > 65535 || n_img > 65535) return cudaErrorInvalidValue;
     dim3 block(32, kWarps);
     dim3 grid((n_u + 32 * kPer - 1) / (32 * kPer), (n_v + kWarps - 1) / kWarps, n_img);
-    k_poisson<<<grid, block, 0, s>>>(lam, out, n_v, n_u, angle0, noise::philox_keys(seed));
+    k_poisson<<<grid, block, 0, s>>>(lam, out, n_v, n_u, angle0, noise::philox_keys(seed), c_lo, c_hi, cst);
     return cudaGetLastError();
 }
 

@@ -309,8 +309,12 @@ cudaError_t launch_blur_cols(const BlurParams &p, const float *tp, const float *
 // transposed blur: gout = n0 (G_psf^T + spr G_scatter^T) gin (tp, ts scratch)
 cudaError_t launch_blur_transpose(const BlurParams &p, const float *gin, float *tp, float *ts,
                                   float *gout, int n_img, cudaStream_t s);
+// Poisson counts of rates lam; with c_hi >= 0, the rows outside [c_lo, c_hi)
+// of every image take the rate cst instead of reading lam (out is written
+// everywhere).
 cudaError_t launch_poisson(const float *lam, float *out, int n_img, int n_v, int n_u,
-                           int angle0, uint64_t seed, cudaStream_t s);
+                           int angle0, uint64_t seed, cudaStream_t s, int c_lo = 0, int c_hi = -1,
+                           float cst = 0.0f);
 // Tables of the FFT ramp filter for rows of n_u samples: log2 of the
 // transform length L (the smallest power of two >= 2 n_u - 1), the L / 2
 // twiddles and the L values of the Ram-Lak response / (L tau) in the
@@ -334,10 +338,13 @@ int blur_tc_rows_launches(const BlurParams &bp, int one_lo, int one_hi);
 void blur_tc_rows_read(const BlurParams &bp, int one_lo, int one_hi, int *lo, int *hi);
 int blur_tc_cols_launches(const BlurParams &bp, int one_lo, int one_hi);
 // Blur of an input that is 1 outside the rows [b_lo, b_hi) (fc_blur_band.cu):
-// one kernel reading only those rows and writing every output pixel.
+// one kernel reading only those rows and writing every output pixel, or,
+// with write_const false, only the rows [c_lo, c_hi) near the band, the
+// others holding the constant cst (blur_band_rows gives both).
 bool blur_band_supported(const BlurParams &bp, int b_lo, int b_hi);
+void blur_band_rows(const BlurParams &bp, int b_lo, int b_hi, int *c_lo, int *c_hi, float *cst);
 cudaError_t launch_blur_band(const BlurParams &bp, const float *T, float *out, int n_img, int b_lo,
-                             int b_hi, cudaStream_t s);
+                             int b_hi, cudaStream_t s, bool write_const = true);
 cudaError_t launch_blur_tc_cols(const BlurParams &bp, const float *tp, const float *ts, float *out,
                                 const uint16_t *hankel, unsigned int *err, int n_img, cudaStream_t s,
                                 int one_lo = 0, int one_hi = -1);
