@@ -258,6 +258,152 @@ k_fdk_filter_fft(const __grid_constant__ FdkParams p, const float *__restrict__ 
     }
 }
 
+// One pass of R radix-2 stages on groups of 2^R points at stride q (q =
+// 2^lq) held in registers, 8 points per thread: forward (decimation in
+// frequency, stages of half-width q 2^(R-1) down to q) or inverse
+// (decimation in time with conjugate twiddles, half-widths q up to
+// q 2^(R-1)).  Group g holds the points grp (q 2^R) + pos + m q, pos = g mod q.
+template <int R, bool INV>
+__device__ __forceinline__ void fft_pass(float2 *z, int t, int q, int lq, const float2 *__restrict__ tw, int H)
+{
+    constexpr int NG = 8 >> R, SZ = 1 << R;
+#pragma unroll
+    for (int gi = 0; gi < NG; ++gi) {
+        const int g = t * NG + gi, pos = g & (q - 1), base = ((g >> lq) << (lq + R)) + pos;
+        float2 x[SZ];
+#pragma unroll
+        for (int m = 0; m < SZ; ++m) x[m] = z[base + m * q];
+#pragma unroll
+        for (int jj = 0; jj < R; ++jj) {
+            const int j = INV ? jj : R - 1 - jj;
+            const int span = 1 << j, st = H >> (lq + j);     // st = H / (half-width)
+#pragma unroll
+            for (int m = 0; m < SZ; ++m) {
+                if (m & span) continue;
+                const float2 w = __ldg(tw + (pos + (m & (2 * span - 1)) * q) * st);
+                if (INV)
+                    cbfly_dit_conj(x[m], x[m + span], w);
+                else
+                    cbfly_dif(x[m], x[m + span], w);
+            }
+        }
+#pragma unroll
+        for (int m = 0; m < SZ; ++m) z[base + m * q] = x[m];
+    }
+}
+
+// The last three forward stages (half-widths 4, 2, 1), the product with the
+// spectrum (bit-reversed order) and the first three inverse stages on the 8
+// consecutive points of one thread, in registers.
+__device__ __forceinline__ void fft_mid(float2 *z, int t, const float2 *__restrict__ tw,
+                                        const float *__restrict__ kbr, int H)
+{
+    const int base = t * 8;
+    float2 x[8];
+#pragma unroll
+    for (int m = 0; m < 8; ++m) x[m] = z[base + m];
+#pragma unroll
+    for (int j = 2; j >= 0; --j) {
+        const int span = 1 << j;
+#pragma unroll
+        for (int m = 0; m < 8; ++m)
+            if (!(m & span)) cbfly_dif(x[m], x[m + span], __ldg(tw + (m & (2 * span - 1)) * (H >> j)));
+    }
+#pragma unroll
+    for (int m = 0; m < 8; ++m) {
+        const float k = __ldg(kbr + base + m);
+        x[m] = make_float2(x[m].x * k, x[m].y * k);
+    }
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        const int span = 1 << j;
+#pragma unroll
+        for (int m = 0; m < 8; ++m)
+            if (!(m & span)) cbfly_dit_conj(x[m], x[m + span], __ldg(tw + (m & (2 * span - 1)) * (H >> j)));
+    }
+#pragma unroll
+    for (int m = 0; m < 8; ++m) z[base + m] = x[m];
+}
+
+// The FFT filter for 64 <= L <= 2048 (rows of 17 to 1024 samples), L / 8
+// threads each holding 8 points per pass: passes of up to three stages in
+// registers, the middle one fused with the spectrum product, so a row pair
+// costs about 2 (log2 L - 3) / 3 + 3 barriers instead of one per two stages.
+// Same operator, weighting, twiddles and output layout as k_fdk_filter_fft.
+__global__ void __launch_bounds__(256)
+k_fdk_filter_fft8(const __grid_constant__ FdkParams p, const float *__restrict__ counts,
+                  float2 *__restrict__ filt)
+{
+    extern __shared__ float2 z[];
+    const DevGeom &g = p.g;
+    const int n = g.n_u, lg = p.fft_log2, L = 1 << lg, H = L >> 1;
+    const int nrows = p.v_hi - p.v_lo + 1;
+    const long R = (long)g.n_angles * nrows;
+    const long ra = 2L * blockIdx.x;
+    const float *src[2];
+    float d2[2];
+#pragma unroll
+    for (int t = 0; t < 2; ++t) {
+        const long row = ra + t < R ? ra + t : ra;
+        const int k = (int)(row / nrows), iv = p.v_lo + (int)(row % nrows);
+        const float vi = ((float)iv - g.cv) * g.dv * p.mag;
+        src[t] = counts + ((size_t)k * g.n_v + iv) * n;
+        d2[t] = g.sad * g.sad + vi * vi;
+    }
+    const bool two = ra + 1 < R;
+    for (int j = threadIdx.x; j < L; j += blockDim.x) {
+        float a = 0.0f, b = 0.0f;
+        if (j < n) {
+            const float ui = ((float)j - g.cu) * g.du * p.mag, u2 = ui * ui;
+            a = (p.log_flood - logf(fmaxf(__ldg(src[0] + j), 1.0f))) * (g.sad * rsqrtf(d2[0] + u2));
+            if (two) b = (p.log_flood - logf(fmaxf(__ldg(src[1] + j), 1.0f))) * (g.sad * rsqrtf(d2[1] + u2));
+        }
+        z[j] = make_float2(a, b);
+    }
+    __syncthreads();
+    const float2 *tw = p.fft_tw;
+    const int t = threadIdx.x;
+    // forward stages of half-width H down to 8, three per pass from the top
+    int F = lg - 3, lq = lg - 1;                 // lq: log2 of the top stage's half-width
+    while (F > 0) {
+        const int Rs = F < 3 ? F : 3;
+        lq -= Rs - 1;
+        const int q = 1 << lq;
+        if (Rs == 3) fft_pass<3, false>(z, t, q, lq, tw, H);
+        else if (Rs == 2) fft_pass<2, false>(z, t, q, lq, tw, H);
+        else fft_pass<1, false>(z, t, q, lq, tw, H);
+        __syncthreads();
+        lq -= 1;
+        F -= Rs;
+    }
+    fft_mid(z, t, tw, p.fft_k, H);
+    __syncthreads();
+    // inverse stages of half-width 8 up to H, three per pass from the bottom
+    F = lg - 3;
+    lq = 3;
+    while (F > 0) {
+        const int Rs = F < 3 ? F : 3;
+        const int q = 1 << lq;
+        if (Rs == 3) fft_pass<3, true>(z, t, q, lq, tw, H);
+        else if (Rs == 2) fft_pass<2, true>(z, t, q, lq, tw, H);
+        else fft_pass<1, true>(z, t, q, lq, tw, H);
+        __syncthreads();
+        lq += Rs;
+        F -= Rs;
+    }
+    for (int half = 0; half < 2; ++half) {
+        const long row = ra + half;
+        if (row >= R) break;
+        const int k = (int)(row / nrows), r = (int)(row % nrows);
+        float2 *dst = filt + ((size_t)k * p.ph + (r + 1)) * p.pw;
+        for (int c = threadIdx.x; c <= n; c += blockDim.x) {
+            const float y0 = c >= 1 ? (half ? z[c - 1].y : z[c - 1].x) : 0.0f;
+            const float y1 = c < n ? (half ? z[c].y : z[c].x) : 0.0f;
+            dst[c] = make_float2(y0, y1 - y0);
+        }
+    }
+}
+
 int fdk_fft_log2(int n_u)
 {
     int l = 1;
@@ -298,6 +444,10 @@ cudaError_t launch_fdk_filter(const FdkParams &p, const float *counts, float2 *f
         if (e != cudaSuccess) return e;
     }
     const long rows = (long)p.g.n_angles * nrows;
+    if (p.fft_log2 >= 6 && p.fft_log2 <= 11) {
+        k_fdk_filter_fft8<<<(unsigned)((rows + 1) / 2), L / 8, smem, s>>>(p, counts, filt);
+        return cudaGetLastError();
+    }
     const int threads = L / 2 < 256 ? L / 2 : 256;
     k_fdk_filter_fft<<<(unsigned)((rows + 1) / 2), threads, smem, s>>>(p, counts, filt);
     return cudaGetLastError();
