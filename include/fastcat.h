@@ -259,8 +259,8 @@ int fc_wait_outputs(fc_handle *h);
  * fc_reconstruct, Sec. II.G, the sums differing only in rounding).
  *   FC_BP_AUTO          (default) the fastest applicable for the geometry:
  *                       FC_BP_SLAB_SYM, else FC_BP_SLAB, else
- *                       FC_BP_CHUNKED_DENSE for grids of two or more waves,
- *                       else FC_BP_CHUNKED;
+ *                       FC_BP_CHUNKED_SYM, else FC_BP_CHUNKED_DENSE for
+ *                       grids of two or more waves, else FC_BP_CHUNKED;
  *   FC_BP_CHUNKED       one thread per (x, y) column and chunk of z slices,
  *                       four bilinear taps per voxel update;
  *   FC_BP_CHUNKED_DENSE the same body capped at 32 registers (8 CTAs per SM);
@@ -278,6 +278,10 @@ int fc_wait_outputs(fc_handle *h);
  *                       grid with nx = ny even and dx_cm = dy_cm.  The
  *                       volume is written with binary64 atomic adds (two per
  *                       voxel onto zero: deterministic).
+ *   FC_BP_CHUNKED_SYM   the same quarter-turn sharing for any slab thickness
+ *                       (every slice loads its two detector rows): applies
+ *                       where the quarter-turn symmetry holds (as for
+ *                       FC_BP_SLAB_SYM, without the thin-slab condition).
  * fc_reconstruct and fc_cnr_grad fail with FC_EINVAL when the requested
  * variant does not apply (for every variant: when the stored filtered rows,
  * n_angles x (reachable rows + 3) x (n_u + 3, rounded up to 4), reach 2^31
@@ -290,6 +294,7 @@ int fc_wait_outputs(fc_handle *h);
 #define FC_BP_CHUNKED_DENSE 2
 #define FC_BP_SLAB          3
 #define FC_BP_SLAB_SYM      4
+#define FC_BP_CHUNKED_SYM   5
 int fc_set_backprojector(fc_handle *h, int variant);
 int fc_backprojector_in_use(fc_handle *h, int *variant);
 

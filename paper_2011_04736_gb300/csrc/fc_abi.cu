@@ -1113,7 +1113,7 @@ int fc_set_noise_order(fc_handle *h, int order)
 int fc_set_backprojector(fc_handle *h, int variant)
 {
     if (!h) return fail(FC_EINVAL, "fc_set_backprojector: null handle");
-    if (variant < FC_BP_AUTO || variant > FC_BP_SLAB_SYM)
+    if (variant < FC_BP_AUTO || variant > FC_BP_CHUNKED_SYM)
         return fail(FC_EINVAL, "fc_set_backprojector: unknown variant %d", variant);
     h->bp_request = variant;
     return FC_OK;

@@ -21,10 +21,10 @@ FC_OK, FC_EINVAL, FC_ENOMEM, FC_ECUDA, FC_ESTATE, FC_ETIMEOUT = 0, -1, -2, -3, -
 FC_HOST, FC_DEVICE, FC_HOST_ASYNC = 0, 1, 2
 FC_OUT_NONE, FC_OUT_PRIMARY, FC_OUT_INTENSITY, FC_OUT_COUNTS = 0, 1, 2, 3
 FC_NOISE_AFTER_BLUR, FC_NOISE_BEFORE_PSF = 0, 1
-FC_BP_AUTO, FC_BP_CHUNKED, FC_BP_CHUNKED_DENSE, FC_BP_SLAB, FC_BP_SLAB_SYM = 0, 1, 2, 3, 4
+FC_BP_AUTO, FC_BP_CHUNKED, FC_BP_CHUNKED_DENSE, FC_BP_SLAB, FC_BP_SLAB_SYM, FC_BP_CHUNKED_SYM = 0, 1, 2, 3, 4, 5
 FC_FAULT_NONE, FC_FAULT_ALLOC, FC_FAULT_BLUR_TIMEOUT = 0, 1, 2
 FC_BP_NAMES = {FC_BP_CHUNKED: "chunked", FC_BP_CHUNKED_DENSE: "chunked_dense", FC_BP_SLAB: "slab",
-               FC_BP_SLAB_SYM: "slab_sym"}
+               FC_BP_SLAB_SYM: "slab_sym", FC_BP_CHUNKED_SYM: "chunked_sym"}
 FC_MAX_MATERIALS, FC_MAX_BINS = 8, 256
 
 # every entry point declared in include/fastcat.h

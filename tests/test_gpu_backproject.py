@@ -112,6 +112,33 @@ def test_quarter_turn_thin_slab(fc, orc, nz, n_u):
     assert np.array_equal(vol2, vols[fc.FC_BP_SLAB_SYM])
 
 
+@pytest.mark.parametrize("n_u", [128, 240])
+def test_quarter_turn_chunked(fc, orc, n_u):
+    """The quarter-turn kernel on a thick slab (the z pitch projects to about
+    five detector rows: every slice loads its two rows), 38 x 38 x 12 voxels
+    over 24 projections; n_u = 128 leaves the volume's shadow wider than the
+    detector (clamped coordinates).  Compared with the oracle and with the
+    chunked kernel, repeated bit for bit."""
+    wl = W.scaled(W.WORKLOADS["small_kv"], n_angles=24, nx=38, ny=38, nz=12, n_u=n_u)
+    g = wl.geom
+    assert fc_step(g) > 1.0
+    lab = np.random.default_rng(70 + n_u).integers(0, 7, size=(g.nz, g.ny, g.nx)).astype(np.uint8)
+    counts = _oracle_counts(orc, wl, lab)
+    vref = orc.fdk(g, counts.astype(np.float64), orc.i_flood(wl.n0, wl.spr))
+    scale = float(np.max(np.abs(vref)))
+    vols = {}
+    for req in (fc.FC_BP_AUTO, fc.FC_BP_CHUNKED_SYM, fc.FC_BP_CHUNKED):
+        vol, used = _recon(fc, wl, counts, req)
+        assert used == (fc.FC_BP_CHUNKED_SYM if req == fc.FC_BP_AUTO else req)
+        err = np.max(np.abs(vol - vref))
+        assert err <= MU_TOL * scale, (req, err / scale)
+        vols[req] = vol
+    d = np.max(np.abs(vols[fc.FC_BP_CHUNKED_SYM] - vols[fc.FC_BP_CHUNKED]))
+    assert d <= 1e-5 * scale, d / scale
+    vol2, _ = _recon(fc, wl, counts, fc.FC_BP_CHUNKED_SYM)
+    assert np.array_equal(vol2, vols[fc.FC_BP_CHUNKED_SYM])
+
+
 @pytest.mark.parametrize("change", ["angles", "arc", "rect", "odd", "pitch"])
 def test_quarter_turn_refused_without_symmetry(fc, change):
     """Without the quarter-turn symmetry (projections not a multiple of 4,
@@ -129,10 +156,11 @@ def test_quarter_turn_refused_without_symmetry(fc, change):
     sc = fc.Scanner(wl, noise=False)
     try:
         assert fc.fc_backprojector_in_use(sc.h) == fc.FC_BP_SLAB
-        fc.fc_set_backprojector(sc.h, fc.FC_BP_SLAB_SYM)
-        with pytest.raises(fc.FastcatError) as ei:
-            fc.fc_backprojector_in_use(sc.h)
-        assert ei.value.code == fc.FC_EINVAL
+        for req in (fc.FC_BP_SLAB_SYM, fc.FC_BP_CHUNKED_SYM):
+            fc.fc_set_backprojector(sc.h, req)
+            with pytest.raises(fc.FastcatError) as ei:
+                fc.fc_backprojector_in_use(sc.h)
+            assert ei.value.code == fc.FC_EINVAL
     finally:
         sc.close()
 
