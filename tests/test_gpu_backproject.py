@@ -139,6 +139,24 @@ def test_quarter_turn_chunked(fc, orc, n_u):
     assert np.array_equal(vol2, vols[fc.FC_BP_CHUNKED_SYM])
 
 
+def test_quarter_turn_thin_slab_unequal_runs(fc, orc):
+    """A 256 x 256 x 11 thin slab: 11 slices do not split into equal runs of
+    at most 5, so the quarter-turn kernel takes runs of unequal length (the
+    form with the run-length test in its slice loop)."""
+    wl = _thin_slab(nx=256, ny=256, nz=11, n_angles=24)
+    g = wl.geom
+    assert fc_step(g) <= 0.98
+    lab = np.random.default_rng(81).integers(0, 7, size=(g.nz, g.ny, g.nx)).astype(np.uint8)
+    counts = _oracle_counts(orc, wl, lab)
+    vref = orc.fdk(g, counts.astype(np.float64), orc.i_flood(wl.n0, wl.spr))
+    scale = float(np.max(np.abs(vref)))
+    vol, used = _recon(fc, wl, counts, fc.FC_BP_AUTO)
+    assert used == fc.FC_BP_SLAB_SYM
+    assert np.max(np.abs(vol - vref)) <= MU_TOL * scale
+    vs, _ = _recon(fc, wl, counts, fc.FC_BP_SLAB)
+    assert np.max(np.abs(vol - vs)) <= 1e-5 * scale
+
+
 @pytest.mark.parametrize("change", ["angles", "arc", "rect", "odd", "pitch"])
 def test_quarter_turn_refused_without_symmetry(fc, change):
     """Without the quarter-turn symmetry (projections not a multiple of 4,
