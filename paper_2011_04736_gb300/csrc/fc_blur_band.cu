@@ -159,20 +159,29 @@ k_blur_band(const __grid_constant__ BlurParams bp, const float *__restrict__ T, 
             }
         }
     }
-    // constant rows [0, c_lo) and [c_hi, n_v) of the tile (left to the
-    // consumer when it takes them as cst itself)
-    const int n_const = write_const ? c_lo + (n_v - c_hi) : 0;
-    const bool vec = (n_u & 3) == 0;
-    for (int e = tid; e < n_const * (kTW / 4); e += kThreads) {
-        const int rr = e / (kTW / 4), x = 4 * (e - rr * (kTW / 4));
-        const int c = rr < c_lo ? rr : c_hi + (rr - c_lo);
-        float *dst = out + img + (size_t)c * n_u + x0 + x;
-        if (vec && x0 + x + 4 <= n_u) {
-            *reinterpret_cast<float4 *>(dst) = make_float4(cst, cst, cst, cst);
+    // constant rows: the image's rows [0, c_lo) and [c_hi, n_v) are two
+    // contiguous address ranges; the projection's CTAs split them into
+    // contiguous chunks written in address order (whole DRAM pages rather
+    // than 512-byte row segments at the row pitch), unless the consumer
+    // takes them as cst itself
+    if (write_const) {
+        const size_t n0 = (size_t)c_lo * n_u, n1 = (size_t)(n_v - c_hi) * n_u, ntot = n0 + n1;
+        const size_t hi0 = (size_t)c_hi * n_u;
+        const bool vec = (n_u & 3) == 0;     // both ranges and the image start on 16 bytes
+        if (vec) {
+            const size_t nq = ntot / 4;       // float4 items (n0 is a multiple of 4)
+            const size_t per = (nq + gridDim.x - 1) / gridDim.x;
+            const size_t q0 = (size_t)blockIdx.x * per, q1 = q0 + per < nq ? q0 + per : nq;
+            const float4 c4 = make_float4(cst, cst, cst, cst);
+            for (size_t q = q0 + tid; q < q1; q += kThreads) {
+                const size_t e = 4 * q;
+                const size_t pos = e < n0 ? e : hi0 + (e - n0);
+                *reinterpret_cast<float4 *>(out + img + pos) = c4;
+            }
         } else {
-#pragma unroll
-            for (int q = 0; q < 4; ++q)
-                if (x0 + x + q < n_u) dst[q] = cst;
+            const size_t per = (ntot + gridDim.x - 1) / gridDim.x;
+            const size_t e0 = (size_t)blockIdx.x * per, e1 = e0 + per < ntot ? e0 + per : ntot;
+            for (size_t e = e0 + tid; e < e1; e += kThreads) out[img + (e < n0 ? e : hi0 + (e - n0))] = cst;
         }
     }
 }
