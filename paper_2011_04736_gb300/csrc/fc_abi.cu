@@ -137,6 +137,7 @@ struct fc_handle {
     uint8_t *d_bricks = nullptr;   // 8x8x16 brick map: uniform label or mixed
     float *d_T = nullptr, *d_tp = nullptr, *d_ts = nullptr, *d_counts = nullptr;
     float2 *d_filt = nullptr;   // filtered rows as (value, next - value) pairs
+    int filt_quad = -1;         // their layout (FdkParams::filt_quad) since the last zeroing; -1: none yet
     double *d_vol = nullptr;
     float *d_hu = nullptr;
     double *d_part = nullptr;
@@ -309,11 +310,22 @@ int ensure_recon_buffers(fc_handle *h, cudaStream_t s)
         h->filt_elems = (size_t)h->g.n_angles * (hi - lo + 1 + 3) * fdk_row_pitch(h->g.n_u);
         FC_CK(dev_malloc((void **)&h->d_filt, h->filt_elems * sizeof(float2)));
         FC_CK(cudaMemsetAsync(h->d_filt, 0, h->filt_elems * sizeof(float2), s));
+        h->filt_quad = -1;
     }
     if (!h->d_counts) FC_CK(dev_malloc((void **)&h->d_counts, h->proj_elems * sizeof(float)));
     if (!h->d_vol) FC_CK(dev_malloc((void **)&h->d_vol, h->vol_elems * sizeof(double)));
     if (!h->d_hu) FC_CK(dev_malloc((void **)&h->d_hu, h->vol_elems * sizeof(float)));
     if (!h->d_part) FC_CK(dev_malloc((void **)&h->d_part, 2 * 256 * sizeof(double)));
+    return FC_OK;
+}
+
+// Before filtering in `quad` layout: the zero padding of one layout is data
+// in the other, so a change of layout re-zeroes the buffer.
+int filt_layout(fc_handle *h, int quad, cudaStream_t s)
+{
+    if (h->filt_quad == quad) return FC_OK;
+    if (h->filt_quad >= 0) FC_CK(cudaMemsetAsync(h->d_filt, 0, h->filt_elems * sizeof(float2), s));
+    h->filt_quad = quad;
     return FC_OK;
 }
 
@@ -1308,16 +1320,19 @@ int fc_reconstruct(fc_handle *h, const float *counts, int counts_where, double *
     fill_fdk_params(h, &p);
     rc = ensure_fft_tables(h, &p);
     if (rc) return rc;
+    const int bpv = fc::backproject_variant(p, h->bp_request);
+    if (bpv < 0)
+        return fail(FC_EINVAL, "fc_reconstruct: backprojector variant %d does not apply to this geometry",
+                    h->bp_request);
+    p.filt_quad = fc::backproject_reads_quad(p, bpv) ? 1 : 0;
+    rc = filt_layout(h, p.filt_quad, s);
+    if (rc) return rc;
     {
         Trace t(h, FC_K_FDK_FILTER, 1, s);
         FC_CK(fc::launch_fdk_filter(p, src, h->d_filt, s));
         t.end();
     }
     {
-        const int bpv = fc::backproject_variant(p, h->bp_request);
-        if (bpv < 0)
-            return fail(FC_EINVAL, "fc_reconstruct: backprojector variant %d does not apply to this geometry",
-                        h->bp_request);
         // the previous results may still be on their way to the host
         FC_CK(h->order_after_copy(s));
         Trace t(h, FC_K_BACKPROJECT, 1, s);
@@ -1916,6 +1931,7 @@ int fc_cnr_grad(fc_handle *h, const double *logits, const double *D, const doubl
     b.n0 = (float)h->n0;
     b.spr = (float)h->spr;
     fc::FdkParams pf;
+    memset(&pf, 0, sizeof(pf));
     pf.g = h->dg;
     pf.trig = h->d_trig;
     pf.log_flood = (float)log(h->n0 * (1.0 + h->spr));
@@ -1948,11 +1964,14 @@ int fc_cnr_grad(fc_handle *h, const double *logits, const double *D, const doubl
     FC_CK(fc::launch_blur_rows(b, h->d_T, h->d_tp, h->d_ts, na, s));
     FC_CK(fc::launch_blur_cols(b, h->d_tp, h->d_ts, h->d_I, na, s));
     FC_CK(fc::launch_noise_gauss(h->d_I, z, h->d_counts, np, s));
-    FC_CK(fc::launch_fdk_filter(pf, h->d_counts, h->d_filt, s));
     {
         const int bpv = fc::backproject_variant(pf, h->bp_request);
         if (bpv < 0) return fail(FC_EINVAL, "fc_cnr_grad: backprojector variant %d does not apply to this geometry",
                                  h->bp_request);
+        pf.filt_quad = fc::backproject_reads_quad(pf, bpv) ? 1 : 0;
+        rc = filt_layout(h, pf.filt_quad, s);
+        if (rc) return rc;
+        FC_CK(fc::launch_fdk_filter(pf, h->d_counts, h->d_filt, s));
         FC_CK(fc::launch_backproject(pf, h->d_filt, h->d_vol, bpv, s));
     }
     if (!h->d_cnr_work) FC_CK(dev_malloc((void **)&h->d_cnr_work, fc::cnr_work_doubles() * sizeof(double)));

@@ -146,6 +146,54 @@ __device__ __forceinline__ void cbfly_dit_conj(float2 &u, float2 &v, float2 w)
     u = make_float2(u.x + vx, u.y + vy);
 }
 
+// Projection and reachable-row index of row `row` of the filters' flattened
+// row order: (projection, row) in the plain layout; (k mod Q, row, k div Q)
+// in the quarter-interleaved one, so the two rows of a CTA (ra even) are
+// quarters b and b + 1 (b even) of the same cell row.
+__device__ __forceinline__ void filt_row(const FdkParams &p, long row, int nrows, int *k, int *r)
+{
+    if (p.filt_quad) {
+        const long cell = row >> 2;
+        *k = (int)(row & 3) * p.sym_quarter + (int)(cell / nrows);
+        *r = (int)(cell % nrows);
+    } else {
+        *k = (int)(row / nrows);
+        *r = (int)(row % nrows);
+    }
+}
+
+// (value, next value - value) pairs over padded columns 0..n of the CTA's
+// rows ra (z[].x) and ra + 1 (z[].y): column c holds output c - 1, columns 0
+// and n + 1 are zero.  Quarter-interleaved: both rows go to one 16-byte half
+// of each cell, (v_b, v_b+1, d_b, d_b+1).
+__device__ __forceinline__ void filt_store(const FdkParams &p, const float2 *z, long ra, long R, int nrows,
+                                           int n, float2 *filt)
+{
+    if (p.filt_quad) {
+        const long cell = ra >> 2;
+        const int kq = (int)(cell / nrows), r = (int)(cell % nrows);
+        float4 *dst = reinterpret_cast<float4 *>(filt) + 2 * (((size_t)kq * p.ph + (r + 1)) * p.pw) +
+                      ((ra >> 1) & 1);
+        for (int c = threadIdx.x; c <= n; c += blockDim.x) {
+            const float2 y0 = c >= 1 ? z[c - 1] : make_float2(0.0f, 0.0f);
+            const float2 y1 = c < n ? z[c] : make_float2(0.0f, 0.0f);
+            dst[2 * c] = make_float4(y0.x, y0.y, y1.x - y0.x, y1.y - y0.y);
+        }
+        return;
+    }
+    for (int half = 0; half < 2; ++half) {
+        const long row = ra + half;
+        if (row >= R) break;
+        const int k = (int)(row / nrows), r = (int)(row % nrows);
+        float2 *dst = filt + ((size_t)k * p.ph + (r + 1)) * p.pw;
+        for (int c = threadIdx.x; c <= n; c += blockDim.x) {
+            const float y0 = c >= 1 ? (half ? z[c - 1].y : z[c - 1].x) : 0.0f;
+            const float y1 = c < n ? (half ? z[c].y : z[c].x) : 0.0f;
+            dst[c] = make_float2(y0, y1 - y0);
+        }
+    }
+}
+
 __global__ void __launch_bounds__(256)
 k_fdk_filter_fft(const __grid_constant__ FdkParams p, const float *__restrict__ counts,
                  float2 *__restrict__ filt)
@@ -161,7 +209,9 @@ k_fdk_filter_fft(const __grid_constant__ FdkParams p, const float *__restrict__ 
 #pragma unroll
     for (int t = 0; t < 2; ++t) {
         const long row = ra + t < R ? ra + t : ra;
-        const int k = (int)(row / nrows), iv = p.v_lo + (int)(row % nrows);
+        int k, r;
+        filt_row(p, row, nrows, &k, &r);
+        const int iv = p.v_lo + r;
         const float vi = ((float)iv - g.cv) * g.dv * p.mag;
         src[t] = counts + ((size_t)k * g.n_v + iv) * n;
         d2[t] = g.sad * g.sad + vi * vi;
@@ -243,19 +293,7 @@ k_fdk_filter_fft(const __grid_constant__ FdkParams p, const float *__restrict__ 
         }
         __syncthreads();
     }
-    // (value, next value - value) pairs over padded columns 0..n: column c
-    // holds output c - 1, columns 0 and n + 1 are zero
-    for (int half = 0; half < 2; ++half) {
-        const long row = ra + half;
-        if (row >= R) break;
-        const int k = (int)(row / nrows), r = (int)(row % nrows);
-        float2 *dst = filt + ((size_t)k * p.ph + (r + 1)) * p.pw;
-        for (int c = threadIdx.x; c <= n; c += blockDim.x) {
-            const float y0 = c >= 1 ? (half ? z[c - 1].y : z[c - 1].x) : 0.0f;
-            const float y1 = c < n ? (half ? z[c].y : z[c].x) : 0.0f;
-            dst[c] = make_float2(y0, y1 - y0);
-        }
-    }
+    filt_store(p, z, ra, R, nrows, n, filt);
 }
 
 // One pass of R radix-2 stages on groups of 2^R points at stride q (q =
@@ -345,7 +383,9 @@ k_fdk_filter_fft8(const __grid_constant__ FdkParams p, const float *__restrict__
 #pragma unroll
     for (int t = 0; t < 2; ++t) {
         const long row = ra + t < R ? ra + t : ra;
-        const int k = (int)(row / nrows), iv = p.v_lo + (int)(row % nrows);
+        int k, r;
+        filt_row(p, row, nrows, &k, &r);
+        const int iv = p.v_lo + r;
         const float vi = ((float)iv - g.cv) * g.dv * p.mag;
         src[t] = counts + ((size_t)k * g.n_v + iv) * n;
         d2[t] = g.sad * g.sad + vi * vi;
@@ -391,17 +431,7 @@ k_fdk_filter_fft8(const __grid_constant__ FdkParams p, const float *__restrict__
         lq += Rs;
         F -= Rs;
     }
-    for (int half = 0; half < 2; ++half) {
-        const long row = ra + half;
-        if (row >= R) break;
-        const int k = (int)(row / nrows), r = (int)(row % nrows);
-        float2 *dst = filt + ((size_t)k * p.ph + (r + 1)) * p.pw;
-        for (int c = threadIdx.x; c <= n; c += blockDim.x) {
-            const float y0 = c >= 1 ? (half ? z[c - 1].y : z[c - 1].x) : 0.0f;
-            const float y1 = c < n ? (half ? z[c].y : z[c].x) : 0.0f;
-            dst[c] = make_float2(y0, y1 - y0);
-        }
-    }
+    filt_store(p, z, ra, R, nrows, n, filt);
 }
 
 int fdk_fft_log2(int n_u)
@@ -869,7 +899,13 @@ k_backproject_slab(const __grid_constant__ FdkParams p, const float2 *__restrict
 // ix, iy < n / 2 (the four quadrants are the orbits of an even n); per
 // projection it computes that geometry once and then loads, interpolates
 // and sums the taps of the four columns, the sums as packed binary32 pairs
-// (each element rounded as the scalar instruction rounds it).  THIN (the
+// (each element rounded as the scalar instruction rounds it).  QUAD (thin
+// slabs whose voxel pitch projects to at most a detector column): the
+// filtered rows are quarter-interleaved, so the four columns' taps at one
+// detector position are one 32-byte cell, two 16-byte loads from one
+// address whose (value, difference) halves feed the packed interpolations
+// directly (otherwise four 8-byte loads from four projections, each
+// interpolated on its own).  THIN (the
 // z pitch projects to less than one detector row): a slice whose row index
 // equals the previous slice's reuses both interpolated rows and loads
 // nothing, one whose row advanced loads only the new row j + 1; otherwise
@@ -885,7 +921,7 @@ k_backproject_slab(const __grid_constant__ FdkParams p, const float2 *__restrict
 // receives exactly two atomic binary64 adds onto a zeroed volume, whose sum
 // x + y does not depend on their order.  Floors, reciprocal and clamps as
 // in k_backproject_slab.
-template <int NS, bool CLAMP, bool THIN, bool FULL>
+template <int NS, bool CLAMP, bool THIN, bool FULL, bool QUAD>
 __global__ void __launch_bounds__(256, 4)
 k_backproject_sym(const __grid_constant__ FdkParams p, const float2 *__restrict__ f,
                   double *__restrict__ vol)
@@ -915,12 +951,15 @@ k_backproject_sym(const __grid_constant__ FdkParams p, const float2 *__restrict_
     const int two23 = __float_as_int(kTwo23);
     const int N = g.n_angles, Q = N / 4;     // projections per quarter turn
     const int kend = (half + 1) * (N / 2);
+    const float4 *fq = reinterpret_cast<const float4 *>(f);   // two per cell
     // segments of at most kFold projections in which no turned projection
     // index k + u Q wraps past N (k within one quarter [b Q, (b + 1) Q))
     for (int kb = half * (N / 2); kb < kend;) {
         const int blk = kb / Q;
         const int ke = min(min(kend, kb + kFold), (blk + 1) * Q);
-        // offset of column u's projection from projection k: (u Q - N [blk + u >= 4]) planes
+        // column u reads projection k + u Q (mod N): QUAD, slot (blk + u) mod 4
+        // of the cells of k mod Q (the sums are kept by slot); otherwise
+        // (u Q - N [blk + u >= 4]) planes from projection k
         const unsigned d1 = (unsigned)(Q - (blk >= 3 ? N : 0)) * plane;
         const unsigned d2 = (unsigned)(2 * Q - (blk >= 2 ? N : 0)) * plane;
         const unsigned d3 = (unsigned)(3 * Q - (blk >= 1 ? N : 0)) * plane;
@@ -939,14 +978,14 @@ k_backproject_sym(const __grid_constant__ FdkParams p, const float2 *__restrict_
             const float tu = __fadd_rd(fu, kTwo23);          // 2^23 + floor(fu)
             const float au = fu - (tu - kTwo23);
             const float2 w2 = f2((g.sad * iU) * (g.sad * iU));
+            const float2 au2 = f2(au);
             const float fv0 = fmaf(zc * iU, sdd_dv, cv1);
             const float dfv = dz_dv * iU;
-            // element offsets of row r + 1 of the column in each column's
-            // projection: (2^23 + r) pw + o_u in 32-bit modular arithmetic
-            // (the true offsets are below 2^31)
-            const unsigned o0 = (unsigned)k * plane + (unsigned)(__float_as_int(tu) - two23) +
-                                (unsigned)(1 - two23) * (unsigned)p.pw;
-            const unsigned o1 = o0 + d1, o2 = o0 + d2, o3 = o0 + d3;
+            // offset of row r + 1 of the column (QUAD: in cells of k mod Q;
+            // otherwise in pairs of projection k): (2^23 + r) pw + o in 32-bit
+            // modular arithmetic (the true offsets are below 2^31)
+            const unsigned o = (unsigned)(QUAD ? k - blk * Q : k) * plane +
+                               (unsigned)(__float_as_int(tu) - two23) + (unsigned)(1 - two23) * (unsigned)p.pw;
             float2 lo01, lo23, hi01, hi23;
             int jp = 0;
 #pragma unroll
@@ -958,13 +997,13 @@ k_backproject_sym(const __grid_constant__ FdkParams p, const float2 *__restrict_
                     const float2 av = f2(fv - (tv - kTwo23));
                     const int j = __float_as_int(tv);
                     const unsigned r = (unsigned)j * (unsigned)p.pw;
-                    if (i == 0 || !THIN) {
+                    if (!QUAD && (i == 0 || !THIN)) {
                         // rows j and j + 1 of each column
-                        const unsigned rl = r - (unsigned)p.pw;
-                        const float2 p0 = __ldg(f + (rl + o0)), p1 = __ldg(f + (rl + o1));
-                        const float2 p2 = __ldg(f + (rl + o2)), p3 = __ldg(f + (rl + o3));
-                        const float2 q0 = __ldg(f + (r + o0)), q1 = __ldg(f + (r + o1));
-                        const float2 q2 = __ldg(f + (r + o2)), q3 = __ldg(f + (r + o3));
+                        const unsigned rl = r - (unsigned)p.pw + o;
+                        const float2 p0 = __ldg(f + rl), p1 = __ldg(f + (rl + d1));
+                        const float2 p2 = __ldg(f + (rl + d2)), p3 = __ldg(f + (rl + d3));
+                        const float2 q0 = __ldg(f + (r + o)), q1 = __ldg(f + (r + o + d1));
+                        const float2 q2 = __ldg(f + (r + o + d2)), q3 = __ldg(f + (r + o + d3));
                         lo01.x = fmaf(au, p0.y, p0.x);
                         lo01.y = fmaf(au, p1.y, p1.x);
                         lo23.x = fmaf(au, p2.y, p2.x);
@@ -973,16 +1012,33 @@ k_backproject_sym(const __grid_constant__ FdkParams p, const float2 *__restrict_
                         hi01.y = fmaf(au, q1.y, q1.x);
                         hi23.x = fmaf(au, q2.y, q2.x);
                         hi23.y = fmaf(au, q3.y, q3.x);
-                    } else if (j != jp) {
+                    } else if (!QUAD && j != jp) {
                         // the row advanced: the old row j + 1 is row j; load the new row j + 1
-                        const float2 q0 = __ldg(f + (r + o0)), q1 = __ldg(f + (r + o1));
-                        const float2 q2 = __ldg(f + (r + o2)), q3 = __ldg(f + (r + o3));
+                        const float2 q0 = __ldg(f + (r + o)), q1 = __ldg(f + (r + o + d1));
+                        const float2 q2 = __ldg(f + (r + o + d2)), q3 = __ldg(f + (r + o + d3));
                         lo01 = hi01;
                         lo23 = hi23;
                         hi01.x = fmaf(au, q0.y, q0.x);
                         hi01.y = fmaf(au, q1.y, q1.x);
                         hi23.x = fmaf(au, q2.y, q2.x);
                         hi23.y = fmaf(au, q3.y, q3.x);
+                    } else if (QUAD && (i == 0 || !THIN)) {
+                        // rows j and j + 1 of each slot: value + au difference
+                        const float4 *cl = fq + 2u * (r - (unsigned)p.pw + o), *ch = fq + 2u * (r + o);
+                        const float4 pa = __ldg(cl), pb = __ldg(cl + 1);
+                        const float4 qa = __ldg(ch), qb = __ldg(ch + 1);
+                        lo01 = __ffma2_rn(au2, make_float2(pa.z, pa.w), make_float2(pa.x, pa.y));
+                        lo23 = __ffma2_rn(au2, make_float2(pb.z, pb.w), make_float2(pb.x, pb.y));
+                        hi01 = __ffma2_rn(au2, make_float2(qa.z, qa.w), make_float2(qa.x, qa.y));
+                        hi23 = __ffma2_rn(au2, make_float2(qb.z, qb.w), make_float2(qb.x, qb.y));
+                    } else if (QUAD && j != jp) {
+                        // the row advanced: the old row j + 1 is row j; load the new row j + 1
+                        const float4 *ch = fq + 2u * (r + o);
+                        const float4 qa = __ldg(ch), qb = __ldg(ch + 1);
+                        lo01 = hi01;
+                        lo23 = hi23;
+                        hi01 = __ffma2_rn(au2, make_float2(qa.z, qa.w), make_float2(qa.x, qa.y));
+                        hi23 = __ffma2_rn(au2, make_float2(qb.z, qb.w), make_float2(qb.x, qb.y));
                     }
                     jp = j;
                     a01[i] = __ffma2_rn(w2, __ffma2_rn(av, sub2(hi01, lo01), lo01), a01[i]);
@@ -990,17 +1046,19 @@ k_backproject_sym(const __grid_constant__ FdkParams p, const float2 *__restrict_
                 }
             }
         }
-        // one sum at a time (the compiler otherwise hoists every shared load
-        // and conversion of the fold and spills)
+        // QUAD: slot s holds column (s - blk) mod 4; one sum at a time (the
+        // compiler otherwise hoists every shared load and conversion of the
+        // fold and spills)
+        const int c0 = QUAD ? (4 - blk) & 3 : 0;
 #pragma unroll
         for (int i = 0; i < NS; ++i) {
-            accd[4 * i + 0][t] += (double)a01[i].x;
+            accd[4 * i + c0][t] += (double)a01[i].x;
             asm volatile("" ::: "memory");
-            accd[4 * i + 1][t] += (double)a01[i].y;
+            accd[4 * i + ((c0 + 1) & 3)][t] += (double)a01[i].y;
             asm volatile("" ::: "memory");
-            accd[4 * i + 2][t] += (double)a23[i].x;
+            accd[4 * i + ((c0 + 2) & 3)][t] += (double)a23[i].x;
             asm volatile("" ::: "memory");
-            accd[4 * i + 3][t] += (double)a23[i].y;
+            accd[4 * i + ((c0 + 3) & 3)][t] += (double)a23[i].y;
             asm volatile("" ::: "memory");
         }
         kb = ke;
@@ -1052,8 +1110,8 @@ static int sym_occupancy(bool clamp)
     int n = 0;
     const cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
         &n,
-        clamp ? (const void *)k_backproject_sym<S, true, THIN, false>
-              : (const void *)k_backproject_sym<S, false, THIN, false>,
+        clamp ? (const void *)k_backproject_sym<S, true, THIN, false, false>
+              : (const void *)k_backproject_sym<S, false, THIN, false, false>,
         256, 0);
     return (e == cudaSuccess && n > 0) ? n : 1;
 }
@@ -1125,11 +1183,28 @@ int backproject_variant(const FdkParams &p, int request)
     return (long)grid.x * grid.y * grid.z >= 2L * sm_count() * 6 ? FC_BP_CHUNKED_DENSE : FC_BP_CHUNKED;
 }
 
+// The thin-slab quarter-turn kernel reads quarter-interleaved filtered rows
+// where the in-plane voxel pitch projects to at most one detector column at
+// the axis: a warp's 8 x 4 columns then sample few distinct cells, and the
+// packed loads save instructions (paper-scale MV case, 0.6 columns per
+// voxel: 3.65 -> 3.08 ms).  Where the pitch projects to ~2 columns, each
+// lane reads its own 32-byte cell and the L1 sectors per tap row outnumber
+// those of four 8-byte loads from four projections (the thick-volume form
+// measured 0.278 -> 0.434 ms on catphan_kv, 2.3 columns per voxel, and
+// 4.88 -> 7.15 ms on the head-like scan, 1.9), so those read the plain rows.
+bool backproject_reads_quad(const FdkParams &p, int variant)
+{
+    return variant == FC_BP_SLAB_SYM && (double)p.g.dx * p.g.sdd <= (double)p.g.du * p.g.sad;
+}
+
 cudaError_t launch_backproject(const FdkParams &p, const float2 *filt, double *vol, int variant,
                                cudaStream_t s)
 {
     if (variant == FC_BP_SLAB_SYM || variant == FC_BP_CHUNKED_SYM) {
         const bool clamp = slab_needs_clamp(p.g), thin = variant == FC_BP_SLAB_SYM;
+        // the filter wrote the layout this variant reads
+        if ((p.filt_quad != 0) != backproject_reads_quad(p, variant)) return cudaErrorInvalidValue;
+        const bool quad = p.filt_quad != 0;
         int ns;
         bool full;
         dim3 grid;
@@ -1138,13 +1213,14 @@ cudaError_t launch_backproject(const FdkParams &p, const float2 *filt, double *v
         // the two halves add onto zero
         const cudaError_t e = cudaMemsetAsync(vol, 0, sizeof(double) * (size_t)p.g.nx * p.g.ny * p.g.nz, s);
         if (e != cudaSuccess) return e;
-#define FC_BPY_F(S, C, T)                                                                     \
-    (full ? (k_backproject_sym<S, C, T, true><<<grid, block, 0, s>>>(p, filt, vol), 0)           \
-          : (k_backproject_sym<S, C, T, false><<<grid, block, 0, s>>>(p, filt, vol), 0))
+#define FC_BPY_F(S, C, T, Q)                                                                  \
+    (full ? (k_backproject_sym<S, C, T, true, Q><<<grid, block, 0, s>>>(p, filt, vol), 0)        \
+          : (k_backproject_sym<S, C, T, false, Q><<<grid, block, 0, s>>>(p, filt, vol), 0))
 #define FC_BPY(S)                                                                             \
     case S:                                                                                   \
-        if (thin) (void)(clamp ? FC_BPY_F(S, true, true) : FC_BPY_F(S, false, true));         \
-        else (void)(clamp ? FC_BPY_F(S, true, false) : FC_BPY_F(S, false, false));            \
+        if (thin && quad) (void)(clamp ? FC_BPY_F(S, true, true, true) : FC_BPY_F(S, false, true, true)); \
+        else if (thin) (void)(clamp ? FC_BPY_F(S, true, true, false) : FC_BPY_F(S, false, true, false)); \
+        else (void)(clamp ? FC_BPY_F(S, true, false, false) : FC_BPY_F(S, false, false, false)); \
         break;
         switch (ns) {
         FC_BPY(1) FC_BPY(2) FC_BPY(3) FC_BPY(4) FC_BPY(5)

@@ -160,7 +160,13 @@ constexpr size_t kBlurTcHankelMax = 2 * 2 * 64 * (15 + (128 + 2 * 256) / 8);  //
 // backprojector can reach, [v_lo, v_hi], in a zero-padded layout
 // [angle][1 + (v_hi - v_lo + 1) + 2][1 + n_u + 2] of (value, next value -
 // value) pairs: one zero row / column before and two after, so bilinear taps
-// need no bounds tests and a tap pair is one 8-byte load.
+// need no bounds tests and a tap pair is one 8-byte load.  For the
+// quarter-turn backprojectors (filt_quad = 1) the four projections k, k + Q,
+// k + 2Q, k + 3Q (Q = n_angles / 4) share one 32-byte cell per padded
+// (row, column): [k mod Q][row][column] of (v_0, v_1, d_0, d_1, v_2, v_3,
+// d_2, d_3), v_b the value and d_b the difference of projection
+// (k mod Q) + b Q, so the four taps of one detector position are two
+// 16-byte loads from one address.
 struct FdkParams {
     DevGeom g;
     const float2 *trig;
@@ -175,7 +181,12 @@ struct FdkParams {
     int fft_log2;           // log2 L, L the transform length (>= 2 n_u - 1)
     int sym_quarter;        // n_angles / 4 for a full-circle scan of n_angles divisible by 4 over a
                             // square grid with an even side and dx = dy (quarter-turn symmetry), else 0
+    int filt_quad;          // 1: filtered rows in the quarter-interleaved cells (needs sym_quarter > 0)
 };
+
+// Whether a backprojector variant reads the quarter-interleaved filtered
+// rows for this geometry (the filter then writes them so).
+bool backproject_reads_quad(const FdkParams &p, int variant);
 
 void fdk_row_range(const DevGeom &g, int *v_lo, int *v_hi);
 

@@ -82,17 +82,30 @@ def test_variants_thin_slab(fc, orc, nz):
     assert d <= 1e-5 * scale, d / scale
 
 
-@pytest.mark.parametrize("nz,n_u", [(10, 96), (1, 96), (16, 96), (7, 96), (10, 40)])
-def test_quarter_turn_thin_slab(fc, orc, nz, n_u):
+def quad_layout(g):
+    """Whether the thin-slab quarter-turn kernel reads the filtered rows
+    interleaved by quarter turn: the in-plane voxel pitch projects to at
+    most one detector column at the axis."""
+    return g.dx * g.sdd <= g.du * g.sad
+
+
+@pytest.mark.parametrize("nz,n_u,dxy", [(10, 96, 0.09), (1, 96, 0.09), (16, 96, 0.09), (7, 96, 0.09),
+                                        (10, 40, 0.09), (10, 96, 0.03), (1, 96, 0.03), (16, 96, 0.03),
+                                        (7, 96, 0.03), (10, 24, 0.03)])
+def test_quarter_turn_thin_slab(fc, orc, nz, n_u, dxy):
     """The quarter-turn kernel on a square grid with an even side (38: a
     19 x 19 quadrant of base columns, ragged against the 32 x 8 CTA tile)
-    and 24 projections over 360 degrees; n_u = 40 leaves the volume's shadow
-    wider than the detector (the clamped coordinates).  Compared with the
-    oracle and with the thin-slab kernel."""
+    and 24 projections over 360 degrees; n_u = 40 (24 at the finer pitch)
+    leaves the volume's shadow wider than the detector (the clamped
+    coordinates).  The 0.09 cm voxel pitch projects to 2.25 detector
+    columns (filtered rows in projection order), the 0.03 cm pitch to 0.75
+    (filtered rows interleaved by quarter turn).  Compared with the oracle
+    and with the thin-slab kernel."""
     wl = _thin_slab(nx=38, ny=38, nz=nz)
-    wl = W.scaled(wl, n_u=n_u)
+    wl = W.scaled(wl, n_u=n_u, dx=dxy, dy=dxy)
     g = wl.geom
     assert fc_step(g) <= 0.98 and g.n_angles % 4 == 0 and abs(g.arc - 2 * math.pi) < 1e-15
+    assert quad_layout(g) == (dxy < 0.05)
     lab = np.random.default_rng(60 + nz).integers(0, 7, size=(g.nz, g.ny, g.nx)).astype(np.uint8)
     counts = _oracle_counts(orc, wl, lab)
     vref = orc.fdk(g, counts.astype(np.float64), orc.i_flood(wl.n0, wl.spr))
@@ -139,13 +152,48 @@ def test_quarter_turn_chunked(fc, orc, n_u):
     assert np.array_equal(vol2, vols[fc.FC_BP_CHUNKED_SYM])
 
 
-def test_quarter_turn_thin_slab_unequal_runs(fc, orc):
+@pytest.mark.parametrize("thick", [False, True])
+def test_variant_switch_on_one_handle(fc, orc, thick):
+    """The quarter-turn kernels read the filtered rows interleaved by quarter
+    turn, the others in projection order, and the zero padding of one layout
+    holds data in the other: one handle switched between a quarter-turn
+    kernel and a plain one (and back) gives, every time, the volume of a
+    fresh handle bit for bit, with a detector narrower than the volume's
+    shadow (the clamped taps read the padding)."""
+    if thick:
+        wl = W.scaled(W.WORKLOADS["small_kv"], n_angles=24, nx=38, ny=38, nz=12, n_u=128)
+        sym, plain = fc.FC_BP_CHUNKED_SYM, fc.FC_BP_CHUNKED
+    else:
+        wl = W.scaled(_thin_slab(nx=38, ny=38, nz=10), n_u=24, dx=0.03, dy=0.03)
+        sym, plain = fc.FC_BP_SLAB_SYM, fc.FC_BP_SLAB
+    g = wl.geom
+    assert quad_layout(g) != thick
+    lab = np.random.default_rng(90 + thick).integers(0, 7, size=(g.nz, g.ny, g.nx)).astype(np.uint8)
+    counts = _oracle_counts(orc, wl, lab)
+    fresh = {v: _recon(fc, wl, counts, v, lab)[0] for v in (sym, plain)}
+    sc = fc.Scanner(wl, labels=lab, noise=False)
+    try:
+        vol = torch.empty((g.nz, g.ny, g.nx), dtype=torch.float64, device="cuda")
+        for v in (sym, plain, sym, plain):
+            fc.fc_set_backprojector(sc.h, v)
+            assert fc.fc_backprojector_in_use(sc.h) == v
+            fc.fc_reconstruct(sc.h, counts, vol_mu=vol)
+            torch.cuda.synchronize()
+            assert np.array_equal(vol.cpu().numpy(), fresh[v]), v
+    finally:
+        sc.close()
+
+
+@pytest.mark.parametrize("dxy", [0.09, 0.03])
+def test_quarter_turn_thin_slab_unequal_runs(fc, orc, dxy):
     """A 256 x 256 x 11 thin slab: 11 slices do not split into equal runs of
     at most 5, so the quarter-turn kernel takes runs of unequal length (the
-    form with the run-length test in its slice loop)."""
-    wl = _thin_slab(nx=256, ny=256, nz=11, n_angles=24)
+    form with the run-length test in its slice loop); with filtered rows in
+    projection order (0.09 cm voxels) and interleaved by quarter turn (0.03
+    cm, the volume's shadow wider than the detector)."""
+    wl = W.scaled(_thin_slab(nx=256, ny=256, nz=11, n_angles=24), dx=dxy, dy=dxy)
     g = wl.geom
-    assert fc_step(g) <= 0.98
+    assert fc_step(g) <= 0.98 and quad_layout(g) == (dxy < 0.05)
     lab = np.random.default_rng(81).integers(0, 7, size=(g.nz, g.ny, g.nx)).astype(np.uint8)
     counts = _oracle_counts(orc, wl, lab)
     vref = orc.fdk(g, counts.astype(np.float64), orc.i_flood(wl.n0, wl.spr))
