@@ -34,6 +34,64 @@ constexpr int kThreads = 256;
 constexpr int kRun = 8;           // outputs per thread and task (register tile)
 }  // namespace
 
+// Column sums of one task (kRun adjacent output rows from c0, columns x and
+// x + 1 of the tile): the optical-spread (PSF) and scatter sums over the band
+// rows of A, then I = n0 (psf + spr sc) + cst.  PSF false: the optical
+// spread's taps are all zero for these rows and its sums are left out.
+template <int HB, bool PSF>
+__device__ __forceinline__ void band_column_sums(const BlurParams &bp, const float *Ap, const float *As,
+                                                 const float *Gp, const float *Gs, int off, int b0, int c0,
+                                                 int c_hi, int x, int x0, int n_u, float cst, float *img)
+{
+    // band row j meets output row c0 + o through tap b0 + j - c0 - o,
+    // padded index off + b0 + j - c0 - o = gp[j + kRun - 1 - o] below
+    const float *gp = Gp + off + b0 - c0 - (kRun - 1), *gs = Gs + off + b0 - c0 - (kRun - 1);
+    float2 accp[kRun], accs[kRun];
+#pragma unroll
+    for (int o = 0; o < kRun; ++o) accp[o] = accs[o] = make_float2(0.0f, 0.0f);
+#pragma unroll 1
+    for (int jb = 0; jb < HB; jb += kRun) {     // rows hb.. of A are zero
+        // taps of this block of kRun band rows: gp[jb + i], i < 2 kRun - 1
+        float tp[2 * kRun - 1], ts[2 * kRun - 1];
+#pragma unroll
+        for (int i = 0; i < 2 * kRun - 1; ++i) {
+            if (PSF) tp[i] = gp[jb + i];
+            ts[i] = gs[jb + i];
+        }
+#pragma unroll
+        for (int q = 0; q < kRun; ++q) {
+            const float2 as = *reinterpret_cast<const float2 *>(As + (jb + q) * kTW + x);
+            float2 ap = make_float2(0.0f, 0.0f);
+            if (PSF) ap = *reinterpret_cast<const float2 *>(Ap + (jb + q) * kTW + x);
+#pragma unroll
+            for (int o = 0; o < kRun; ++o) {
+                const float b = ts[q + kRun - 1 - o];
+                if (PSF) {
+                    const float a = tp[q + kRun - 1 - o];
+                    accp[o].x = fmaf(a, ap.x, accp[o].x);
+                    accp[o].y = fmaf(a, ap.y, accp[o].y);
+                }
+                accs[o].x = fmaf(b, as.x, accs[o].x);
+                accs[o].y = fmaf(b, as.y, accs[o].y);
+            }
+        }
+    }
+#pragma unroll
+    for (int o = 0; o < kRun; ++o) {
+        const int c = c0 + o;
+        if (c >= c_hi) break;
+        const float vx = fmaf(bp.n0, fmaf(bp.spr, accs[o].x, accp[o].x), cst);
+        const float vy = fmaf(bp.n0, fmaf(bp.spr, accs[o].y, accp[o].y), cst);
+        float *dst = img + (size_t)c * n_u + x0 + x;
+        if (x0 + x + 1 < n_u && (n_u & 1) == 0) {
+            *reinterpret_cast<float2 *>(dst) = make_float2(vx, vy);
+        } else {
+            if (x0 + x < n_u) dst[0] = vx;
+            if (x0 + x + 1 < n_u) dst[1] = vy;
+        }
+    }
+}
+
 // Work split: row passes as tasks of kRun adjacent outputs of one band row
 // (a sliding window of D in registers: one shared load per tap for kRun
 // FMAs); column sums as tasks of kRun adjacent output rows x 2 columns (per
@@ -115,49 +173,15 @@ k_blur_band(const __grid_constant__ BlurParams bp, const float *__restrict__ T, 
     for (int task = tid; task < n_runs * (kTW / 2); task += kThreads) {
         const int run = task / (kTW / 2), x = 2 * (task - run * (kTW / 2));
         const int c0 = c_lo + run * kRun;
-        // band row j meets output row c0 + o through tap b0 + j - c0 - o,
-        // padded index off + b0 + j - c0 - o = gp[j + kRun - 1 - o] below
-        const float *gp = Gp + off + b0 - c0 - (kRun - 1), *gs = Gs + off + b0 - c0 - (kRun - 1);
-        float2 accp[kRun], accs[kRun];
-#pragma unroll
-        for (int o = 0; o < kRun; ++o) accp[o] = accs[o] = make_float2(0.0f, 0.0f);
-#pragma unroll 1
-        for (int jb = 0; jb < HB; jb += kRun) {     // rows hb.. of A are zero
-            // taps of this block of kRun band rows: gp[jb + i], i < 2 kRun - 1
-            float tp[2 * kRun - 1], ts[2 * kRun - 1];
-#pragma unroll
-            for (int i = 0; i < 2 * kRun - 1; ++i) {
-                tp[i] = gp[jb + i];
-                ts[i] = gs[jb + i];
-            }
-#pragma unroll
-            for (int q = 0; q < kRun; ++q) {
-                const float2 ap = *reinterpret_cast<const float2 *>(Ap + (jb + q) * kTW + x);
-                const float2 as = *reinterpret_cast<const float2 *>(As + (jb + q) * kTW + x);
-#pragma unroll
-                for (int o = 0; o < kRun; ++o) {
-                    const float a = tp[q + kRun - 1 - o], b = ts[q + kRun - 1 - o];
-                    accp[o].x = fmaf(a, ap.x, accp[o].x);
-                    accp[o].y = fmaf(a, ap.y, accp[o].y);
-                    accs[o].x = fmaf(b, as.x, accs[o].x);
-                    accs[o].y = fmaf(b, as.y, accs[o].y);
-                }
-            }
-        }
-#pragma unroll
-        for (int o = 0; o < kRun; ++o) {
-            const int c = c0 + o;
-            if (c >= c_hi) break;
-            const float vx = fmaf(bp.n0, fmaf(bp.spr, accs[o].x, accp[o].x), cst);
-            const float vy = fmaf(bp.n0, fmaf(bp.spr, accs[o].y, accp[o].y), cst);
-            float *dst = out + img + (size_t)c * n_u + x0 + x;
-            if (x0 + x + 1 < n_u && (n_u & 1) == 0) {
-                *reinterpret_cast<float2 *>(dst) = make_float2(vx, vy);
-            } else {
-                if (x0 + x < n_u) dst[0] = vx;
-                if (x0 + x + 1 < n_u) dst[1] = vy;
-            }
-        }
+        // the optical spread reaches output rows [b0 - rp, b0 + hb + rp) only;
+        // elsewhere its sums are exact zeros and are skipped (the same value:
+        // fma(spr, s, +0) rounds as spr s).  Uniform over a warp: the 64 tasks
+        // of a run are consecutive.
+        const bool psf = c0 + kRun > b0 - bp.rp && c0 < b0 + hb + bp.rp;
+        if (psf)
+            band_column_sums<HB, true>(bp, Ap, As, Gp, Gs, off, b0, c0, c_hi, x, x0, n_u, cst, out + img);
+        else
+            band_column_sums<HB, false>(bp, Ap, As, Gp, Gs, off, b0, c0, c_hi, x, x0, n_u, cst, out + img);
     }
     // constant rows: the image's rows [0, c_lo) and [c_hi, n_v) are two
     // contiguous address ranges; the projection's CTAs split them into
