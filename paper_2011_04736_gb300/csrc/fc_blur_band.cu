@@ -97,8 +97,10 @@ __device__ __forceinline__ void band_column_sums(const BlurParams &bp, const flo
 // FMAs); column sums as tasks of kRun adjacent output rows x 2 columns (per
 // band row one pair of A values and one new tap per kernel, 4 kRun FMAs);
 // the constant rows as float4 stores.
+// 4 CTAs per SM (64 registers, a 20-byte spill) against 3 at the 79
+// registers the compiler takes unbounded: paper-scale 0.458 -> 0.427 ms.
 template <int HB>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, 4)
 k_blur_band(const __grid_constant__ BlurParams bp, const float *__restrict__ T, float *__restrict__ out,
             int b0, int hb, float cst, int write_const)
 {

@@ -1340,10 +1340,24 @@ __global__ void k_hu(DevGeom g, const double *__restrict__ vol, const double *__
     }
     const double m = scnt[0] > 0.0 ? ssum[0] / scnt[0] : 0.0;
     const double k = m != 0.0 ? 1000.0 / m : 0.0;    // HU = 1000 (mu - mu_w) / mu_w
-    const size_t n = (size_t)g.nx * g.ny * g.nz;
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n;
-         i += (size_t)gridDim.x * blockDim.x)
-        hu[i] = (float)((vol[i] - m) * k);
+    // per voxel in binary32, HU = mu k - mu_w k as one fma: the result is
+    // binary32 anyway, and the rounding of mu and of the two products moves
+    // it by ~1e-4 HU, while GB300's binary64 rate made the binary64 form the
+    // kernel's bound
+    const float kf = (float)k, bf = (float)(-m * k);
+    // four voxels per thread and pass (two 16-byte loads, one 16-byte store:
+    // more bytes in flight per warp than one 8-byte load), then the tail;
+    // both buffers are the handle's (256-byte aligned)
+    const size_t n = (size_t)g.nx * g.ny * g.nz, n4 = n / 4;
+    const size_t i0 = blockIdx.x * (size_t)blockDim.x + threadIdx.x, step = (size_t)gridDim.x * blockDim.x;
+    const double2 *v2 = reinterpret_cast<const double2 *>(vol);
+    float4 *h4 = reinterpret_cast<float4 *>(hu);
+    for (size_t i = i0; i < n4; i += step) {
+        const double2 a = __ldg(v2 + 2 * i), b = __ldg(v2 + 2 * i + 1);
+        h4[i] = make_float4(fmaf((float)a.x, kf, bf), fmaf((float)a.y, kf, bf), fmaf((float)b.x, kf, bf),
+                            fmaf((float)b.y, kf, bf));
+    }
+    for (size_t i = 4 * n4 + i0; i < n; i += step) hu[i] = fmaf((float)vol[i], kf, bf);
 }
 
 cudaError_t launch_hu(const DevGeom &g, const double *vol, float *hu, double *partials, float radius,
